@@ -1,0 +1,276 @@
+"""ctypes loader for the CPU oracle (oracle/asterx_oracle.cpp).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's CPU-baseline leg are the only
+users.  The product library never imports this package.  Arrays follow the layout of the workloads module:
+float64, shape (Nz+1, Ny+1, Nx+1) per field, stacked as (9, ...) for the state (D, Sx, Sy, Sz, tau, Ax, Ay,
+Az, Psi), (5, ...) for the primitives (rho, press, velx, vely, velz) and (16, ...) for the vertex metric.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "asterx_oracle.cpp")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compiles the oracle with g++ (-O2, no floating-point contraction, portable flags)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp,
+                               _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OParams(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("rho_atm", ctypes.c_double), ("K_atm", ctypes.c_double),
+                ("gamma_atm", ctypes.c_double), ("c2p_tol", ctypes.c_double), ("c2p_maxiter", ctypes.c_int),
+                ("brent_maxiter", ctypes.c_int), ("W_max", ctypes.c_double), ("recon", ctypes.c_int),
+                ("gauge", ctypes.c_int), ("xi_lorenz", ctypes.c_double), ("use_fallback", ctypes.c_int)]
+
+
+class OBlock(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("g", ctypes.c_int), ("x0", ctypes.c_double * 3),
+                ("dx", ctypes.c_double * 3), ("bc", ctypes.c_int * 3)]
+
+
+class OStats(ctypes.Structure):
+    _fields_ = [("n_noble", ctypes.c_ulonglong), ("n_fallback", ctypes.c_ulonglong),
+                ("n_atm", ctypes.c_ulonglong), ("n_failed", ctypes.c_ulonglong), ("iters", ctypes.c_ulonglong)]
+
+    def asdict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_lib = None
+_P = ctypes.POINTER(ctypes.c_double)
+_PP = ctypes.POINTER(_P)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        L = _lib
+        L.oracle_abi_version.restype = ctypes.c_int
+        for name in ("oracle_ghost_fill_state", "oracle_ghost_fill_prims"):
+            getattr(L, name).argtypes = [ctypes.POINTER(OBlock), _PP]
+        L.oracle_prim2con.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP]
+        L.oracle_con2prim.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP,
+                                      ctypes.c_void_p, ctypes.POINTER(OStats)]
+        L.oracle_rhs.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP,
+                                 ctypes.c_double, ctypes.POINTER(ctypes.c_ulonglong)]
+        L.oracle_face_B.argtypes = [ctypes.POINTER(OBlock), _PP, _PP]
+        L.oracle_rk_stage.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, ctypes.c_int,
+                                      ctypes.c_double, _PP, _PP, _PP, _PP, _PP, ctypes.c_void_p,
+                                      ctypes.POINTER(OStats)]
+        L.oracle_point_prim2con.argtypes = [ctypes.POINTER(OParams), _P, _P, _P, _P, _P]
+        L.oracle_point_wave_speeds.argtypes = [ctypes.POINTER(OParams), _P, _P, _P, ctypes.c_int, _P]
+        L.oracle_point_c2p.argtypes = [ctypes.POINTER(OParams), _P, _P, _P, _P, _P, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int)]
+        L.oracle_point_c2p.restype = ctypes.c_int
+        L.oracle_batch_c2p.argtypes = [ctypes.POINTER(OParams), ctypes.c_long, _P, _P, _P, _P, _P, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_batch_prim2con.argtypes = [ctypes.POINTER(OParams), ctypes.c_long, _P, _P, _P, _P]
+        L.oracle_point_recon.argtypes = [ctypes.c_int, _P, _P, _P]
+        L.oracle_point_sources.argtypes = [ctypes.POINTER(OParams), _P, _P, _P, _P, _P, _P, _P]
+        L.oracle_grid_sources.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP]
+    return _lib
+
+
+# ------------------------------------------------------------------------------------------------------------
+
+
+def params_struct(p: dict) -> OParams:
+    return OParams(p["gamma"], p["rho_atm"], p["K_atm"], p["gamma_atm"], p["c2p_tol"], int(p["c2p_maxiter"]),
+                   int(p["brent_maxiter"]), p["W_max"], int(p["recon"]), int(p["gauge"]), p["xi_lorenz"],
+                   int(p["use_fallback"]))
+
+
+def block_struct(w) -> OBlock:
+    b = OBlock()
+    for d in range(3):
+        b.n[d] = int(w.n[d])
+        b.x0[d] = float(w.x0[d])
+        b.dx[d] = float(w.dx[d])
+        b.bc[d] = int(w.bc[d])
+    b.g = int(w.g)
+    return b
+
+
+def _ptrs(arr: np.ndarray):
+    assert arr.dtype == np.float64 and arr.flags.c_contiguous
+    n = arr.shape[0]
+    t = (_P * n)(*[arr[v].ctypes.data_as(_P) for v in range(n)])
+    return t
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_P)
+
+
+def metric_array(w) -> np.ndarray:
+    from paper_2406_11669_gb300.workloads import METRIC_NAMES
+    return np.ascontiguousarray(np.stack([w.metric[k] for k in METRIC_NAMES]))
+
+
+def prims_array(w) -> np.ndarray:
+    from paper_2406_11669_gb300.workloads import PRIM_NAMES
+    return np.ascontiguousarray(np.stack([w.prims[k] for k in PRIM_NAMES]))
+
+
+def initial_state(w):
+    """(U, prims): the state with D, S, tau from the oracle's own prim->cons and A, Psi from the workload."""
+    P = prims_array(w)
+    U = np.zeros((9,) + w.shape)
+    U[5] = w.A["Ax"]
+    U[6] = w.A["Ay"]
+    U[7] = w.A["Az"]
+    U[8] = w.Psi
+    M = metric_array(w)
+    prim2con(w, M, U, P)
+    return U, P
+
+
+def ghost_fill_state(w, U):
+    lib().oracle_ghost_fill_state(ctypes.byref(block_struct(w)), _ptrs(U))
+
+
+def ghost_fill_prims(w, P):
+    lib().oracle_ghost_fill_prims(ctypes.byref(block_struct(w)), _ptrs(P))
+
+
+def prim2con(w, M, U, P, params=None):
+    pp = params_struct(params or w.params)
+    lib().oracle_prim2con(ctypes.byref(pp), ctypes.byref(block_struct(w)), _ptrs(M), _ptrs(U), _ptrs(P))
+
+
+def con2prim(w, M, U, P, params=None):
+    pp = params_struct(params or w.params)
+    flags = np.zeros(w.shape, dtype=np.int8)
+    st = OStats()
+    lib().oracle_con2prim(ctypes.byref(pp), ctypes.byref(block_struct(w)), _ptrs(M), _ptrs(U), _ptrs(P),
+                          flags.ctypes.data, ctypes.byref(st))
+    return flags, st.asdict()
+
+
+def face_B(w, U):
+    Bf = np.zeros((3,) + w.shape)
+    lib().oracle_face_B(ctypes.byref(block_struct(w)), _ptrs(U), _ptrs(Bf))
+    return Bf
+
+
+def rhs(w, M, U, P, dt=None, params=None):
+    """dU/dt of the 9 state fields (state and primitives must have their ghosts filled)."""
+    pp = params_struct(params or w.params)
+    dU = np.zeros((9,) + w.shape)
+    it = (ctypes.c_ulonglong * 2)()
+    lib().oracle_rhs(ctypes.byref(pp), ctypes.byref(block_struct(w)), _ptrs(M), _ptrs(U), _ptrs(P), _ptrs(dU),
+                     float(dt if dt is not None else w.dt), it)
+    return dU, (int(it[0]), int(it[1]))
+
+
+def rk_stage(w, M, stage, dt, Un, Us, Unext, Uacc, P, params=None):
+    pp = params_struct(params or w.params)
+    flags = np.zeros(w.shape, dtype=np.int8)
+    st = OStats()
+    lib().oracle_rk_stage(ctypes.byref(pp), ctypes.byref(block_struct(w)), _ptrs(M), int(stage), float(dt),
+                          _ptrs(Un), _ptrs(Us), _ptrs(Unext), _ptrs(Uacc), _ptrs(P), flags.ctypes.data,
+                          ctypes.byref(st))
+    return flags, st.asdict()
+
+
+def rk4_step(w, M, U, P, dt=None, params=None):
+    """One classical RK4 step; returns (U_next, stats summed over the four stages).  U is ghost-filled and
+    may be reset to the atmosphere in place by the first stage's recovery; P is updated in place."""
+    dt = float(dt if dt is not None else w.dt)
+    Uacc = np.zeros_like(U)
+    Us = U
+    tot = None
+    for s in range(4):
+        Unext = Us.copy()  # entries outside the owned ranges stay defined; owned entries are overwritten
+        _, st = rk_stage(w, M, s, dt, U, Us, Unext, Uacc, P, params)
+        tot = st if tot is None else {k: tot[k] + st[k] for k in tot}
+        Us = Unext
+    return Us, tot
+
+
+def point_prim2con(params, m16, prim5, B3):
+    cons = np.zeros(5)
+    fl = np.zeros(15)
+    lib().oracle_point_prim2con(ctypes.byref(params_struct(params)), _p(np.ascontiguousarray(m16, float)),
+                                _p(np.ascontiguousarray(prim5, float)), _p(np.ascontiguousarray(B3, float)),
+                                _p(cons), _p(fl))
+    return cons, fl.reshape(3, 5)
+
+
+def point_wave_speeds(params, m16, prim5, B3, d):
+    lam = np.zeros(2)
+    lib().oracle_point_wave_speeds(ctypes.byref(params_struct(params)), _p(np.ascontiguousarray(m16, float)),
+                                   _p(np.ascontiguousarray(prim5, float)), _p(np.ascontiguousarray(B3, float)),
+                                   int(d), _p(lam))
+    return lam[0], lam[1]
+
+
+def point_c2p(params, m16, cons5, B3, guess5, which=0):
+    out = np.zeros(5)
+    it = ctypes.c_int(0)
+    flag = lib().oracle_point_c2p(ctypes.byref(params_struct(params)), _p(np.ascontiguousarray(m16, float)),
+                                  _p(np.ascontiguousarray(cons5, float)), _p(np.ascontiguousarray(B3, float)),
+                                  _p(np.ascontiguousarray(guess5, float)), _p(out), int(which), ctypes.byref(it))
+    return flag, out, it.value
+
+
+def batch_c2p(params, m16, cons5, B3, guess5, which=0):
+    """Recovery of n undensitised states: arrays (n,16), (n,5), (n,3), (n,5) -> (flags, prims, iters)."""
+    n = cons5.shape[0]
+    out = np.zeros((n, 5))
+    flags = np.zeros(n, dtype=np.int32)
+    iters = np.zeros(n, dtype=np.int32)
+    lib().oracle_batch_c2p(ctypes.byref(params_struct(params)), n, _p(np.ascontiguousarray(m16, float)),
+                           _p(np.ascontiguousarray(cons5, float)), _p(np.ascontiguousarray(B3, float)),
+                           _p(np.ascontiguousarray(guess5, float)), _p(out), int(which), flags.ctypes.data,
+                           iters.ctypes.data)
+    return flags, out, iters
+
+
+def batch_prim2con(params, m16, prim5, B3):
+    n = prim5.shape[0]
+    out = np.zeros((n, 5))
+    lib().oracle_batch_prim2con(ctypes.byref(params_struct(params)), n, _p(np.ascontiguousarray(m16, float)),
+                                _p(np.ascontiguousarray(prim5, float)), _p(np.ascontiguousarray(B3, float)),
+                                _p(out))
+    return out
+
+
+def point_recon(scheme, a5):
+    aL = np.zeros(1)
+    aR = np.zeros(1)
+    lib().oracle_point_recon(int(scheme), _p(np.ascontiguousarray(a5, float)), _p(aL), _p(aR))
+    return aL[0], aR[0]
+
+
+def point_sources(params, m16, dalp, dbeta, dg, prim5, B3):
+    src = np.zeros(5)
+    lib().oracle_point_sources(ctypes.byref(params_struct(params)), _p(np.ascontiguousarray(m16, float)),
+                               _p(np.ascontiguousarray(dalp, float)), _p(np.ascontiguousarray(dbeta, float)),
+                               _p(np.ascontiguousarray(dg, float)), _p(np.ascontiguousarray(prim5, float)),
+                               _p(np.ascontiguousarray(B3, float)), _p(src))
+    return src
+
+
+def grid_sources(w, M, U, P, params=None):
+    pp = params_struct(params or w.params)
+    src = np.zeros((5,) + w.shape)
+    lib().oracle_grid_sources(ctypes.byref(pp), ctypes.byref(block_struct(w)), _ptrs(M), _ptrs(U), _ptrs(P),
+                              _ptrs(src))
+    return src

@@ -1,0 +1,1552 @@
+// CPU oracle for the GRMHD method-of-lines RK stage of AsterX (arXiv:2406.11669).
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, FP64 reference that the CUDA path is checked
+// against.  Only the test suite, the smoke check and the benchmark's CPU-baseline leg may load it.  It
+// shares no code, header or table with the CUDA library (paper_2406_11669_gb300/csrc) and the product path
+// never calls it.
+//
+// Style: every step is written out literally in the order the paper states it, per cell / per face /
+// per edge, with temporaries in full-size arrays and no fusion, hoisting or blocking.  Pointwise physics is
+// templated on the scalar type R so that a flop-counting type can be substituted (R = double for results).
+// Citations name the paper's sections and equation labels.
+//
+// Readings of the paper that this file takes (all listed in the repository's design notes):
+//  * Densitised evolution (Eq. fluxconseqs): U = sqrt(gamma) (D, S_j, tau); fluxes are alpha sqrt(gamma) F^i.
+//  * E = -v~ x B~ (induction, Eq. inductioneq) and dA/dt = -E - grad G_A (Eq. Ainductioneqs); the
+//    second line of Eq. recastedAvec carries the opposite sign of the v x B term and is not followed.
+//  * Source terms in 3+1 form with the input K_ij; equal to Eq. grmhdsrc for a static metric.
+//  * Ideal-gas eps recovery of Eq. Noble2D epsilon uses the adiabatic index Gamma (printed "1/gamma").
+//  * Palenzuela eps-hat uses t^2/x^2 (the derivation from Eq. Noble2D energy; printed "t^2/x").
+//  * Palenzuela lower bracket raised to max(1 + q - s, 1) because x = hW >= 1.
+//  * Wave speeds: extreme roots of the magnetosonic quartic, multiplied through by c_s^2, found by Newton
+//    from the light-cone speeds; G = gamma^dd - (lambda + beta^d)^2 / alpha^2.
+//  * Reconstructed variables: rho, p, W v^i and the transverse cell-centre B (undensitised).
+//  * 4th-order Lagrange interpolation of the vertex metric; near the edge of the padded array the 4-point
+//    stencil is shifted inward (still 4th order).
+//  * UCT face->edge reconstruction is PPM (Sec. 3.4 (ii)); a_+-(edge) = max over the two adjacent faces.
+//  * Copy (Neumann) BCs copy the nearest owned value, except the edge potential A_i, which is extrapolated
+//    linearly along the boundary normal.
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+namespace asterx_oracle {
+
+// ------------------------------------------------------------------------------------------------------
+// Flop-counting scalar.  + - * / sqrt each count one flop; divisions and square roots are also counted apart.
+
+struct Flops {
+  unsigned long long add = 0, mul = 0, div = 0, sqrt = 0;
+};
+static Flops g_flops;
+
+struct Fc {
+  double v;
+  Fc() : v(0.0) {}
+  Fc(double x) : v(x) {}
+};
+inline Fc operator+(Fc a, Fc b) { g_flops.add++; return Fc(a.v + b.v); }
+inline Fc operator-(Fc a, Fc b) { g_flops.add++; return Fc(a.v - b.v); }
+inline Fc operator*(Fc a, Fc b) { g_flops.mul++; return Fc(a.v * b.v); }
+inline Fc operator/(Fc a, Fc b) { g_flops.div++; return Fc(a.v / b.v); }
+inline Fc operator-(Fc a) { return Fc(-a.v); }
+inline Fc& operator+=(Fc& a, Fc b) { a = a + b; return a; }
+inline Fc& operator-=(Fc& a, Fc b) { a = a - b; return a; }
+inline Fc& operator*=(Fc& a, Fc b) { a = a * b; return a; }
+inline bool operator<(Fc a, Fc b) { return a.v < b.v; }
+inline bool operator>(Fc a, Fc b) { return a.v > b.v; }
+inline bool operator<=(Fc a, Fc b) { return a.v <= b.v; }
+inline bool operator>=(Fc a, Fc b) { return a.v >= b.v; }
+inline bool operator==(Fc a, Fc b) { return a.v == b.v; }
+inline bool operator!=(Fc a, Fc b) { return a.v != b.v; }
+inline Fc sqrt(Fc a) { g_flops.sqrt++; return Fc(std::sqrt(a.v)); }
+inline Fc fabs(Fc a) { return Fc(std::fabs(a.v)); }
+inline double val(Fc a) { return a.v; }
+inline double val(double a) { return a; }
+inline bool finite(double a) { return std::isfinite(a); }
+inline bool finite(Fc a) { return std::isfinite(a.v); }
+using std::fabs;
+using std::sqrt;
+
+template <class R> inline R rmax(R a, R b) { return (a < b) ? b : a; }
+template <class R> inline R rmin(R a, R b) { return (b < a) ? b : a; }
+
+// ------------------------------------------------------------------------------------------------------
+// ABI structs (mirrored by ctypes in oracle/__init__.py)
+
+struct OParams {
+  double gamma;       // ideal-gas adiabatic index (Sec. 3.7)
+  double rho_atm;     // atmosphere density floor (Sec. 3.6)
+  double K_atm;       // atmosphere polytrope constant
+  double gamma_atm;   // atmosphere polytrope exponent
+  double c2p_tol;     // Noble Newton tolerance
+  int c2p_maxiter;
+  int brent_maxiter;
+  double W_max;       // Lorentz-factor cap used on failure paths of the recovery
+  int recon;          // 0 minmod, 1 PPM, 2 WENO-Z
+  int gauge;          // 0 generalised Lorenz, 1 algebraic
+  double xi_lorenz;   // Lorenz damping; 0 => 1.5/dt
+  int use_fallback;   // Palenzuela fallback on/off
+};
+
+struct OBlock {
+  int n[3];
+  int g;
+  double x0[3];
+  double dx[3];
+  int bc[3];  // 0 periodic, 1 copy
+};
+
+struct OStats {
+  unsigned long long n_noble, n_fallback, n_atm, n_failed, iters;
+};
+
+enum { RECON_MINMOD = 0, RECON_PPM = 1, RECON_WENOZ = 2 };
+enum { BC_PERIODIC = 0, BC_COPY = 1 };
+enum { GAUGE_LORENZ = 0, GAUGE_ALGEBRAIC = 1 };
+
+// ------------------------------------------------------------------------------------------------------
+// Grid indexing: every field spans the vertex-index box [0, N]^3, N = n + 2g, x fastest.
+
+struct Grid {
+  int n[3], g, N[3];
+  long s[3];
+  double dx[3];
+  int bc[3];
+  explicit Grid(const OBlock& b) {
+    g = b.g;
+    for (int d = 0; d < 3; d++) {
+      n[d] = b.n[d];
+      N[d] = b.n[d] + 2 * b.g;
+      dx[d] = b.dx[d];
+      bc[d] = b.bc[d];
+    }
+    s[0] = 1;
+    s[1] = N[0] + 1;
+    s[2] = (long)(N[0] + 1) * (N[1] + 1);
+  }
+  long size() const { return (long)(N[0] + 1) * (N[1] + 1) * (N[2] + 1); }
+  long at(int i, int j, int k) const { return i + s[1] * j + s[2] * k; }
+  long at(const int p[3]) const { return at(p[0], p[1], p[2]); }
+};
+
+typedef std::vector<double> Field;
+
+// ------------------------------------------------------------------------------------------------------
+// 3+1 metric at a point (Sec. 2.1, Eq. lineelement): lapse, shift, 3-metric, its inverse and determinant.
+
+template <class R> struct Metric3 {
+  R alp, beta[3], g[3][3], K[3][3];
+  R gu[3][3], sqrtg;
+};
+
+template <class R> void metric_complete(Metric3<R>& m) {
+  // determinant and inverse by cofactors
+  R c00 = m.g[1][1] * m.g[2][2] - m.g[1][2] * m.g[2][1];
+  R c01 = m.g[1][2] * m.g[2][0] - m.g[1][0] * m.g[2][2];
+  R c02 = m.g[1][0] * m.g[2][1] - m.g[1][1] * m.g[2][0];
+  R det = m.g[0][0] * c00 + m.g[0][1] * c01 + m.g[0][2] * c02;
+  R c11 = m.g[0][0] * m.g[2][2] - m.g[0][2] * m.g[2][0];
+  R c12 = m.g[0][1] * m.g[2][0] - m.g[0][0] * m.g[2][1];
+  R c22 = m.g[0][0] * m.g[1][1] - m.g[0][1] * m.g[1][0];
+  m.gu[0][0] = c00 / det;
+  m.gu[0][1] = c01 / det;
+  m.gu[0][2] = c02 / det;
+  m.gu[1][0] = m.gu[0][1];
+  m.gu[1][1] = c11 / det;
+  m.gu[1][2] = c12 / det;
+  m.gu[2][0] = m.gu[0][2];
+  m.gu[2][1] = m.gu[1][2];
+  m.gu[2][2] = c22 / det;
+  m.sqrtg = sqrt(det);
+}
+
+// The 16 vertex fields, in ABI order: alp, beta^x,y,z, g_xx,xy,xz,yy,yz,zz, K_xx,xy,xz,yy,yz,zz.
+static const int SYM[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+
+struct VertexMetric {
+  const double* f[16];
+};
+
+// 4-point Lagrange weights for the midpoint between nodes p and p+1 of the node set s..s+3 (Sec. 3.2: the
+// vertex metric is interpolated to centres and faces at 4th order).  Near the end of the padded array the
+// stencil start s is shifted so that all four nodes exist.
+static void lagrange_mid(int p, int Nv, int* start, double w[4]) {
+  int s = p - 1;
+  if (s < 0) s = 0;
+  if (s > Nv - 3) s = Nv - 3;
+  const double t = (p - s) + 0.5;  // target position in node units
+  for (int a = 0; a < 4; a++) {
+    double num = 1.0, den = 1.0;
+    for (int b = 0; b < 4; b++) {
+      if (b == a) continue;
+      num *= (t - b);
+      den *= (double)(a - b);
+    }
+    w[a] = num / den;
+  }
+  *start = s;
+}
+
+// Staggered 4th-order first derivative at the midpoint p+1/2 from nodes p-1..p+2:
+// (f(p-1) - 27 f(p) + 27 f(p+1) - f(p+2)) / (24 h).
+static const double DER4[4] = {1.0 / 24.0, -27.0 / 24.0, 27.0 / 24.0, -1.0 / 24.0};
+
+// Interpolate the vertex metric to a point that is at vertex index along axes where half[d] == 0 and at the
+// midpoint p+1/2 along axes where half[d] == 1.  If dflag >= 0, the axis dflag (which must be a half axis)
+// takes the staggered derivative stencil instead, and the result is d/dx^dflag of the field.
+static double vertex_interp(const Grid& G, const double* f, const int p[3], const int half[3], int dflag) {
+  int st[3];
+  double w[3][4];
+  int cnt[3];
+  for (int d = 0; d < 3; d++) {
+    if (!half[d]) {
+      st[d] = p[d];
+      cnt[d] = 1;
+      w[d][0] = 1.0;
+    } else if (d == dflag) {
+      st[d] = p[d] - 1;
+      cnt[d] = 4;
+      for (int a = 0; a < 4; a++) w[d][a] = DER4[a] / G.dx[d];
+    } else {
+      lagrange_mid(p[d], G.N[d], &st[d], w[d]);
+      cnt[d] = 4;
+    }
+  }
+  double acc = 0.0;
+  for (int c = 0; c < cnt[2]; c++) {
+    double accy = 0.0;
+    for (int b = 0; b < cnt[1]; b++) {
+      double accx = 0.0;
+      for (int a = 0; a < cnt[0]; a++) accx += w[0][a] * f[G.at(st[0] + a, st[1] + b, st[2] + c)];
+      accy += w[1][b] * accx;
+    }
+    acc += w[2][c] * accy;
+  }
+  return acc;
+}
+
+static Metric3<double> metric_at(const Grid& G, const VertexMetric& vm, const int p[3], const int half[3]) {
+  Metric3<double> m;
+  m.alp = vertex_interp(G, vm.f[0], p, half, -1);
+  for (int a = 0; a < 3; a++) m.beta[a] = vertex_interp(G, vm.f[1 + a], p, half, -1);
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) {
+      m.g[a][b] = vertex_interp(G, vm.f[4 + SYM[a][b]], p, half, -1);
+      m.K[a][b] = vertex_interp(G, vm.f[10 + SYM[a][b]], p, half, -1);
+    }
+  metric_complete(m);
+  return m;
+}
+
+static Metric3<double> metric_at_centre(const Grid& G, const VertexMetric& vm, int i, int j, int k) {
+  const int p[3] = {i, j, k};
+  const int half[3] = {1, 1, 1};
+  return metric_at(G, vm, p, half);
+}
+
+static Metric3<double> metric_at_face(const Grid& G, const VertexMetric& vm, int d, int i, int j, int k) {
+  const int p[3] = {i, j, k};
+  int half[3] = {1, 1, 1};
+  half[d] = 0;
+  return metric_at(G, vm, p, half);
+}
+
+static Metric3<double> metric_at_vertex(const Grid& G, const VertexMetric& vm, int i, int j, int k) {
+  const int p[3] = {i, j, k};
+  const int half[3] = {0, 0, 0};
+  return metric_at(G, vm, p, half);
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Primitive -> conserved map and fluxes (Sec. 2.2, Eqs. eulerianB, grmhdeqs, cons).
+
+template <class R> struct Prim {
+  R rho, press, eps, vel[3], B[3];  // v^i Eulerian, B^i undensitised Eulerian
+};
+
+template <class R> struct Cons {
+  R D, S[3], tau;  // densitised by sqrt(gamma)
+};
+
+// Comoving-frame quantities of a primitive state (Eq. eulerianB and the covariant b_i below Eq. Noble2D z).
+template <class R> struct Comoving {
+  R W, vlow[3], h, Blow[3], B2, Bv, b0, bup[3], blow[3], b2, u0, uup[3];
+};
+
+template <class R> Comoving<R> comoving(const Metric3<R>& m, const Prim<R>& P) {
+  Comoving<R> c;
+  R v2 = R(0.0);
+  for (int a = 0; a < 3; a++) {
+    c.vlow[a] = m.g[a][0] * P.vel[0] + m.g[a][1] * P.vel[1] + m.g[a][2] * P.vel[2];
+  }
+  for (int a = 0; a < 3; a++) v2 += P.vel[a] * c.vlow[a];
+  c.W = R(1.0) / sqrt(R(1.0) - v2);
+  c.h = R(1.0) + P.eps + P.press / P.rho;
+  c.B2 = R(0.0);
+  c.Bv = R(0.0);
+  for (int a = 0; a < 3; a++) {
+    c.Blow[a] = m.g[a][0] * P.B[0] + m.g[a][1] * P.B[1] + m.g[a][2] * P.B[2];
+  }
+  for (int a = 0; a < 3; a++) {
+    c.B2 += P.B[a] * c.Blow[a];
+    c.Bv += P.B[a] * c.vlow[a];
+  }
+  c.u0 = c.W / m.alp;
+  for (int a = 0; a < 3; a++) c.uup[a] = c.W * (P.vel[a] - m.beta[a] / m.alp);
+  c.b0 = c.W * c.Bv / m.alp;
+  for (int a = 0; a < 3; a++) c.bup[a] = (P.B[a] + m.alp * c.b0 * c.uup[a]) / c.W;
+  for (int a = 0; a < 3; a++) c.blow[a] = c.Blow[a] / c.W + m.alp * c.b0 * c.vlow[a];
+  c.b2 = (c.B2 + m.alp * m.alp * c.b0 * c.b0) / (c.W * c.W);
+  return c;
+}
+
+template <class R> Cons<R> prim2con(const Metric3<R>& m, const Prim<R>& P, const Comoving<R>& c) {
+  Cons<R> U;
+  const R rhohb = P.rho * c.h + c.b2;
+  U.D = m.sqrtg * (P.rho * c.W);
+  for (int a = 0; a < 3; a++)
+    U.S[a] = m.sqrtg * (rhohb * c.W * c.W * c.vlow[a] - m.alp * c.b0 * c.blow[a]);
+  U.tau = m.sqrtg * (rhohb * c.W * c.W - (P.press + R(0.5) * c.b2) - m.alp * m.alp * c.b0 * c.b0 - P.rho * c.W);
+  return U;
+}
+
+// alpha sqrt(gamma) F^d for the five hydro variables (Eq. grmhdeqs), with v~^d = alpha v^d - beta^d.
+template <class R> void flux(const Metric3<R>& m, const Prim<R>& P, const Comoving<R>& c, const Cons<R>& U, int d,
+                             R F[5]) {
+  const R vt = m.alp * P.vel[d] - m.beta[d];
+  const R asg = m.alp * m.sqrtg;
+  const R ptot = P.press + R(0.5) * c.b2;
+  F[0] = U.D * vt;
+  for (int a = 0; a < 3; a++) {
+    F[1 + a] = U.S[a] * vt - asg * c.blow[a] * P.B[d] / c.W;
+    if (a == d) F[1 + a] = F[1 + a] + asg * ptot;
+  }
+  F[4] = U.tau * vt + asg * ptot * P.vel[d] - asg * m.alp * c.b0 * P.B[d] / c.W;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Fast magnetosonic speeds along d (Sec. 3.3: extreme roots of the quartic, refs. therein).
+// With phi_mu = (-lambda, delta^d_mu): a = u.phi, Bc = b.phi, G = g^{mu nu} phi phi = gamma^dd - (lambda +
+// beta^d)^2/alpha^2.  The quartic  rho h (1/cs2 - 1) a^4 - (rho h + b^2/cs2) a^2 G + Bc^2 G = 0  is used
+// multiplied by cs2 (same roots, finite for cs2 = 0).  Newton from each light-cone speed converges
+// monotonically to the outermost root on that side.
+
+template <class R> struct Quartic {
+  R e, cs2, b2, u0, ud, b0, bd, alp, betad, gdd;
+  R eval(R lam, R* dq) const {
+    const R a = ud - lam * u0;
+    const R Bc = bd - lam * b0;
+    const R lb = lam + betad;
+    const R G = gdd - lb * lb / (alp * alp);
+    const R dG = R(-2.0) * lb / (alp * alp);
+    const R c4 = e * (R(1.0) - cs2);
+    const R c2 = e * cs2 + b2;
+    const R a2 = a * a;
+    const R q = c4 * a2 * a2 - c2 * a2 * G + cs2 * Bc * Bc * G;
+    *dq = R(4.0) * c4 * a2 * a * (-u0) - c2 * (R(2.0) * a * (-u0) * G + a2 * dG) +
+          cs2 * (R(2.0) * Bc * (-b0) * G + Bc * Bc * dG);
+    return q;
+  }
+};
+
+template <class R> void wave_speeds(const Metric3<R>& m, const Prim<R>& P, const Comoving<R>& c, double gamma, int d,
+                                    R* lam_minus, R* lam_plus, int* iters) {
+  Quartic<R> Q;
+  Q.e = P.rho * c.h;
+  Q.cs2 = R(gamma * (gamma - 1.0)) * P.eps / c.h;  // ideal gas: cs^2 = Gamma (Gamma-1) eps / h
+  Q.b2 = c.b2;
+  Q.u0 = c.u0;
+  Q.ud = c.uup[d];
+  Q.b0 = c.b0;
+  Q.bd = c.bup[d];
+  Q.alp = m.alp;
+  Q.betad = m.beta[d];
+  Q.gdd = m.gu[d][d];
+  const R width = m.alp * sqrt(m.gu[d][d]);
+  int it_total = 0;
+  for (int side = 0; side < 2; side++) {
+    const R sgn = (side == 0) ? R(1.0) : R(-1.0);
+    R lam = -m.beta[d] + sgn * width;  // light-cone speed on this side
+    for (int it = 0; it < 60; it++) {
+      R dq;
+      R q = Q.eval(lam, &dq);
+      it_total++;
+      if (dq == R(0.0)) break;
+      const R step = q / dq;
+      lam = lam - step;
+      if (fabs(step) <= R(1e-13) * (fabs(lam) + width)) break;
+    }
+    if (side == 0) *lam_plus = lam;
+    else *lam_minus = lam;
+  }
+  if (iters) *iters = it_total;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Reconstruction (Sec. 3.3, ReconX): per cell, the values at its lower (aL) and upper (aR) faces from the
+// five cell averages a[0..4] = a_{i-2..i+2}.
+
+template <class R> R minmod(R x, R y) {
+  if (x * y <= R(0.0)) return R(0.0);
+  return (fabs(x) <= fabs(y)) ? x : y;
+}
+
+template <class R> void recon_minmod(const R a[5], R* aL, R* aR) {
+  const R slope = minmod(a[2] - a[1], a[3] - a[2]);
+  *aL = a[2] - R(0.5) * slope;
+  *aR = a[2] + R(0.5) * slope;
+}
+
+// Colella & Woodward (1984) PPM without flattening or steepening: van-Leer limited slopes, the 4th-order
+// interface value, then the monotonicity constraints on the parabola of the cell.
+template <class R> R ppm_slope(R am, R a0, R ap) {
+  if ((ap - a0) * (a0 - am) <= R(0.0)) return R(0.0);
+  const R c = R(0.5) * (ap - am);
+  R s = rmin(fabs(c), rmin(R(2.0) * fabs(a0 - am), R(2.0) * fabs(ap - a0)));
+  return (c < R(0.0)) ? -s : s;
+}
+
+template <class R> void recon_ppm(const R a[5], R* aL, R* aR) {
+  const R dm = ppm_slope(a[0], a[1], a[2]);
+  const R d0 = ppm_slope(a[1], a[2], a[3]);
+  const R dp = ppm_slope(a[2], a[3], a[4]);
+  R l = a[1] + R(0.5) * (a[2] - a[1]) - (d0 - dm) / R(6.0);  // a_{i-1/2}
+  R r = a[2] + R(0.5) * (a[3] - a[2]) - (dp - d0) / R(6.0);  // a_{i+1/2}
+  const R ai = a[2];
+  if ((r - ai) * (ai - l) <= R(0.0)) {
+    l = ai;
+    r = ai;
+  } else {
+    const R dlr = r - l;
+    const R mid = ai - R(0.5) * (l + r);
+    if (dlr * mid > dlr * dlr / R(6.0)) {
+      l = R(3.0) * ai - R(2.0) * r;
+    } else if (-(dlr * dlr) / R(6.0) > dlr * mid) {
+      r = R(3.0) * ai - R(2.0) * l;
+    }
+  }
+  *aL = l;
+  *aR = r;
+}
+
+// WENO-Z (Borges et al. 2008), fifth order, epsilon = 1e-40, power p = 2.  Value at the upper face of the
+// middle cell of s[0..4]; the lower face is the same formula on the mirrored stencil.
+template <class R> R wenoz_upper(R s0, R s1, R s2, R s3, R s4) {
+  const R q0 = (R(2.0) * s0 - R(7.0) * s1 + R(11.0) * s2) / R(6.0);
+  const R q1 = (-s1 + R(5.0) * s2 + R(2.0) * s3) / R(6.0);
+  const R q2 = (R(2.0) * s2 + R(5.0) * s3 - s4) / R(6.0);
+  const R t0a = s0 - R(2.0) * s1 + s2, t0b = s0 - R(4.0) * s1 + R(3.0) * s2;
+  const R t1a = s1 - R(2.0) * s2 + s3, t1b = s1 - s3;
+  const R t2a = s2 - R(2.0) * s3 + s4, t2b = R(3.0) * s2 - R(4.0) * s3 + s4;
+  const R b0 = R(13.0 / 12.0) * t0a * t0a + R(0.25) * t0b * t0b;
+  const R b1 = R(13.0 / 12.0) * t1a * t1a + R(0.25) * t1b * t1b;
+  const R b2 = R(13.0 / 12.0) * t2a * t2a + R(0.25) * t2b * t2b;
+  const R tau5 = fabs(b0 - b2);
+  const R eps = R(1e-40);
+  const R r0 = tau5 / (b0 + eps), r1 = tau5 / (b1 + eps), r2 = tau5 / (b2 + eps);
+  const R w0 = R(0.1) * (R(1.0) + r0 * r0);
+  const R w1 = R(0.6) * (R(1.0) + r1 * r1);
+  const R w2 = R(0.3) * (R(1.0) + r2 * r2);
+  return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+}
+
+template <class R> void recon_wenoz(const R a[5], R* aL, R* aR) {
+  *aR = wenoz_upper(a[0], a[1], a[2], a[3], a[4]);
+  *aL = wenoz_upper(a[4], a[3], a[2], a[1], a[0]);
+}
+
+template <class R> void recon_cell(int scheme, const R a[5], R* aL, R* aR) {
+  if (scheme == RECON_MINMOD) recon_minmod(a, aL, aR);
+  else if (scheme == RECON_PPM) recon_ppm(a, aL, aR);
+  else recon_wenoz(a, aL, aR);
+}
+
+// ------------------------------------------------------------------------------------------------------
+// HLLE (Eq. HLLEfluxes): c_max = max(0, c+_l, c+_r), c_min = -min(0, c-_l, c-_r).
+
+template <class R> void hlle(const R FL[5], const R FR[5], const R UL[5], const R UR[5], R cmax, R cmin, R out[5]) {
+  const R den = cmax + cmin;
+  for (int v = 0; v < 5; v++) {
+    if (den > R(0.0))
+      out[v] = (cmin * FR[v] + cmax * FL[v] - cmax * cmin * (UR[v] - UL[v])) / den;
+    else
+      out[v] = R(0.5) * (FL[v] + FR[v]);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Face solve: from the reconstructed left/right states and the face metric, the HLLE flux of the 5 hydro
+// variables and the data that upwind constrained transport needs at this face (Eq. uct1, uct2).
+
+struct FaceInput {
+  double rho[2], press[2], u[2][3], Bt[2][3];  // side 0 = left, 1 = right; u = W v; Bt: transverse B only
+  double Bn;                                    // densitised normal field at the face (staggered)
+};
+
+template <class R> struct FaceOut {
+  R F[5];
+  R vbar[3];  // upwind v~ components (the normal one unused)
+  R cmax, cmin;
+  int iters;
+};
+
+template <class R> FaceOut<R> face_solve(const Metric3<R>& m, const FaceInput& in, double gamma, int d) {
+  FaceOut<R> out;
+  R U[2][5], F[2][5], lp[2], lm[2], vt[2][3];
+  out.iters = 0;
+  for (int s = 0; s < 2; s++) {
+    Prim<R> P;
+    P.rho = R(in.rho[s]);
+    P.press = R(in.press[s]);
+    P.eps = P.press / (R(gamma - 1.0) * P.rho);  // ideal gas (Sec. 3.7)
+    // W from u^i = W v^i: W^2 = 1 + gamma_ij u^i u^j
+    R uu = R(0.0);
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) uu += m.g[a][b] * R(in.u[s][a]) * R(in.u[s][b]);
+    const R W = sqrt(R(1.0) + uu);
+    for (int a = 0; a < 3; a++) P.vel[a] = R(in.u[s][a]) / W;
+    for (int a = 0; a < 3; a++) P.B[a] = (a == d) ? R(in.Bn) / m.sqrtg : R(in.Bt[s][a]);
+    Comoving<R> c = comoving(m, P);
+    Cons<R> Us = prim2con(m, P, c);
+    flux(m, P, c, Us, d, F[s]);
+    U[s][0] = Us.D;
+    U[s][1] = Us.S[0];
+    U[s][2] = Us.S[1];
+    U[s][3] = Us.S[2];
+    U[s][4] = Us.tau;
+    int it = 0;
+    wave_speeds(m, P, c, gamma, d, &lm[s], &lp[s], &it);
+    out.iters += it;
+    for (int a = 0; a < 3; a++) vt[s][a] = m.alp * P.vel[a] - m.beta[a];
+  }
+  out.cmax = rmax(R(0.0), rmax(lp[0], lp[1]));
+  out.cmin = -rmin(R(0.0), rmin(lm[0], lm[1]));
+  hlle(F[0], F[1], U[0], U[1], out.cmax, out.cmin, out.F);
+  const R den = out.cmax + out.cmin;
+  for (int a = 0; a < 3; a++) {
+    if (a == d) {
+      out.vbar[a] = R(0.0);
+    } else if (den > R(0.0)) {
+      out.vbar[a] = (out.cmax * vt[0][a] + out.cmin * vt[1][a]) / den;
+    } else {
+      out.vbar[a] = R(0.5) * (vt[0][a] + vt[1][a]);
+    }
+  }
+  return out;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Primitive recovery (Sec. 3.5): Noble 2D Newton on (z, v^2), Palenzuela 1D Brent on x = hW, atmosphere.
+
+struct C2POut {
+  double rho, press, vel[3];
+  int flag;   // 0 Noble, 1 Palenzuela, 2 atmosphere, -1 both failed (atmosphere applied)
+  int iters;  // Noble iterations
+  bool reset; // conserved variables must be reset to the atmosphere
+};
+
+struct C2PIn {
+  double Dtilde;         // densitised D~ = sqrt(gamma) D, for the atmosphere test
+  double D, S[3], tau;   // undensitised
+  double B[3];           // undensitised centre field
+  double guess_rho, guess_press, guess_vel[3];
+};
+
+// Noble et al. 2006 residuals, Eqs. (Noble2D momentum) and (Noble2D energy), with the ideal-gas pressure
+// p(z, v^2) = (Gamma-1)/Gamma (z (1 - v^2) - D sqrt(1 - v^2)) that follows from z = rho h W^2, h = 1 + Gamma eps.
+template <class R> void noble_residual(R z, R v2, R D, R tau, R S2, R B2, R BS, double gamma, R f[2], R J[2][2]) {
+  const R gf = R((gamma - 1.0) / gamma);
+  const R sq = sqrt(R(1.0) - v2);
+  const R p = gf * (z * (R(1.0) - v2) - D * sq);
+  const R dp_dz = gf * (R(1.0) - v2);
+  const R dp_dv2 = gf * (-z + R(0.5) * D / sq);
+  const R Bz = B2 + z;
+  f[0] = v2 * Bz * Bz - BS * BS * (B2 + R(2.0) * z) / (z * z) - S2;
+  f[1] = tau + D - R(0.5) * B2 * (R(1.0) + v2) + BS * BS / (R(2.0) * z * z) - z + p;
+  J[0][0] = R(2.0) * v2 * Bz + R(2.0) * BS * BS * Bz / (z * z * z);
+  J[0][1] = Bz * Bz;
+  J[1][0] = -BS * BS / (z * z * z) - R(1.0) + dp_dz;
+  J[1][1] = R(-0.5) * B2 + dp_dv2;
+}
+
+// velocity from Eq. (Noble2D v): v^i = gamma^ij S_j / (z + B^2) + (B^j S_j) B^i / (z (z + B^2))
+static void noble_velocity(const Metric3<double>& m, const C2PIn& in, double z, double B2, double BS, double v[3]) {
+  for (int a = 0; a < 3; a++) {
+    double Su = m.gu[a][0] * in.S[0] + m.gu[a][1] * in.S[1] + m.gu[a][2] * in.S[2];
+    v[a] = Su / (z + B2) + BS * in.B[a] / (z * (z + B2));
+  }
+}
+
+static bool bad(double x) { return !std::isfinite(x) || x < 0.0; }
+
+static bool c2p_noble(const Metric3<double>& m, const C2PIn& in, const OParams& P, double S2, double B2, double BS,
+                      C2POut* out) {
+  const double gamma = P.gamma;
+  const double v2max = 1.0 - 1.0 / (P.W_max * P.W_max);
+  // initial guess from the previous primitives
+  double gv2 = 0.0;
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) gv2 += m.g[a][b] * in.guess_vel[a] * in.guess_vel[b];
+  if (!(gv2 >= 0.0)) gv2 = 0.0;
+  if (gv2 > v2max) gv2 = v2max;
+  const double gW = 1.0 / std::sqrt(1.0 - gv2);
+  const double geps = in.guess_press / ((gamma - 1.0) * in.guess_rho);
+  const double gh = 1.0 + geps + in.guess_press / in.guess_rho;
+  double z = in.guess_rho * gh * gW * gW;
+  double v2 = gv2;
+  if (!(z > 0.0) || !std::isfinite(z)) return false;
+  bool conv = false;
+  int it;
+  for (it = 1; it <= P.c2p_maxiter; it++) {
+    double f[2], J[2][2];
+    noble_residual<double>(z, v2, in.D, in.tau, S2, B2, BS, gamma, f, J);
+    const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double dz = (-f[0] * J[1][1] + J[0][1] * f[1]) / det;
+    const double dv2 = (-J[0][0] * f[1] + J[1][0] * f[0]) / det;
+    // damped step: a step that would make z non-positive halves z instead (z = rho h W^2 > 0)
+    const bool damped = !(z + dz > 0.0);
+    z = damped ? 0.5 * z : z + dz;
+    v2 += dv2;
+    if (v2 < 0.0) v2 = 0.0;
+    if (v2 > v2max) v2 = v2max;
+    if (!std::isfinite(z) || !std::isfinite(v2)) break;
+    if (!damped && std::fabs(dz) <= P.c2p_tol * std::fabs(z) && std::fabs(dv2) <= P.c2p_tol) {
+      conv = true;
+      break;
+    }
+  }
+  out->iters = (it > P.c2p_maxiter) ? P.c2p_maxiter : it;
+  if (!conv || !(z > 0.0) || !(v2 >= 0.0) || !(v2 < 1.0)) return false;
+  const double W = 1.0 / std::sqrt(1.0 - v2);
+  const double rho = in.D / W;
+  double v[3];
+  noble_velocity(m, in, z, B2, BS, v);
+  const double eps = (z / (rho * W * W) - 1.0) / gamma;  // Eq. (Noble2D epsilon) with the adiabatic index
+  const double press = (gamma - 1.0) * rho * eps;
+  if (bad(rho) || bad(eps) || bad(press)) return false;
+  for (int a = 0; a < 3; a++)
+    if (!std::isfinite(v[a])) return false;
+  out->rho = rho;
+  out->press = press;
+  for (int a = 0; a < 3; a++) out->vel[a] = v[a];
+  return true;
+}
+
+// Palenzuela et al. 2015 function f(x) = x - h^ W^ (Eq. Palenzuela Brent), with W^, rho^, eps^ from x.
+struct PalenzuelaFn {
+  double q, r, s, t, D, gamma, v2max;
+  double W, rho, eps, press;
+  double operator()(double x) {
+    double v2 = (r * x * x + t * t * (2.0 * x + s)) / (x * x * (x + s) * (x + s));
+    if (v2 > v2max) v2 = v2max;
+    if (v2 < 0.0) v2 = 0.0;
+    W = 1.0 / std::sqrt(1.0 - v2);
+    rho = D / W;
+    eps = -1.0 + (x / W) * (1.0 - W * W) + W * (1.0 + q - s + 0.5 * (t * t / (x * x) + s / (W * W)));
+    if (eps < 0.0) eps = 0.0;
+    press = (gamma - 1.0) * rho * eps;
+    const double h = 1.0 + eps + press / rho;
+    return x - h * W;
+  }
+};
+
+// Brent's method (Brent 1973, "Algorithms for Minimization without Derivatives", ch. 4): keep a bracket
+// [b, c] with a sign change, b the best iterate; try inverse quadratic interpolation (or the secant when only
+// two points are distinct) and fall back to bisection whenever the interpolated step is not safely inside
+// the bracket or does not shrink fast enough.
+template <class F> static bool brent_root(F& f, double lo, double hi, double xtol, int maxiter, double* root) {
+  double a = lo, b = hi;
+  double fa = f(a), fb = f(b);
+  if (!std::isfinite(fa) || !std::isfinite(fb)) return false;
+  if ((fa > 0.0 && fb > 0.0) || (fa < 0.0 && fb < 0.0)) return false;
+  double c = a, fc = fa;
+  double step = b - a, prev_step = step;
+  for (int it = 0; it < maxiter; it++) {
+    if ((fb > 0.0 && fc > 0.0) || (fb < 0.0 && fc < 0.0)) {
+      c = a;  // re-establish the bracket [b, c]
+      fc = fa;
+      step = prev_step = b - a;
+    }
+    if (std::fabs(fc) < std::fabs(fb)) {  // make b the better end
+      a = b; b = c; c = a;
+      fa = fb; fb = fc; fc = fa;
+    }
+    const double tol = 2.0 * 2.220446049250313e-16 * std::fabs(b) + 0.5 * xtol;
+    const double half = 0.5 * (c - b);
+    if (std::fabs(half) <= tol || fb == 0.0) {
+      *root = b;
+      return true;
+    }
+    bool bisect = true;
+    if (std::fabs(prev_step) >= tol && std::fabs(fa) > std::fabs(fb)) {
+      double num, den;
+      const double sb = fb / fa;
+      if (a == c) {  // secant through a, b
+        num = 2.0 * half * sb;
+        den = 1.0 - sb;
+      } else {       // inverse quadratic interpolation through a, b, c
+        const double qa = fa / fc, rb = fb / fc;
+        num = sb * (2.0 * half * qa * (qa - rb) - (b - a) * (rb - 1.0));
+        den = (qa - 1.0) * (rb - 1.0) * (sb - 1.0);
+      }
+      if (num > 0.0) den = -den;
+      else num = -num;
+      const double lim1 = 3.0 * half * den - std::fabs(tol * den);
+      const double lim2 = std::fabs(prev_step * den);
+      if (2.0 * num < (lim1 < lim2 ? lim1 : lim2)) {
+        prev_step = step;
+        step = num / den;
+        bisect = false;
+      }
+    }
+    if (bisect) {
+      step = half;
+      prev_step = step;
+    }
+    a = b;
+    fa = fb;
+    if (std::fabs(step) > tol) b += step;
+    else b += (half > 0.0 ? tol : -tol);
+    fb = f(b);
+    if (!std::isfinite(fb)) return false;
+  }
+  return false;
+}
+
+static bool c2p_palenzuela(const Metric3<double>& m, const C2PIn& in, const OParams& P, double S2, double B2,
+                           double BS, C2POut* out) {
+  PalenzuelaFn f;
+  f.q = in.tau / in.D;
+  f.r = S2 / (in.D * in.D);
+  f.s = B2 / in.D;
+  f.t = BS / std::pow(in.D, 1.5);
+  f.D = in.D;
+  f.gamma = P.gamma;
+  f.v2max = 1.0 - 1.0 / (P.W_max * P.W_max);
+  double lo = 1.0 + f.q - f.s;
+  if (lo < 1.0) lo = 1.0;
+  const double hi = 2.0 + 2.0 * f.q - f.s;
+  if (!(hi > lo)) return false;
+  double x;
+  if (!brent_root(f, lo, hi, 1e-15 * hi, P.brent_maxiter, &x)) return false;
+  f(x);  // primitives at the root
+  const double z = in.D * x;  // z = rho W x (Eq. Noble2D z with x = hW)
+  double v[3];
+  noble_velocity(m, in, z, B2, BS, v);
+  if (bad(f.rho) || bad(f.eps) || bad(f.press)) return false;
+  for (int a = 0; a < 3; a++)
+    if (!std::isfinite(v[a])) return false;
+  out->rho = f.rho;
+  out->press = f.press;
+  for (int a = 0; a < 3; a++) out->vel[a] = v[a];
+  return true;
+}
+
+// Atmosphere (Sec. 3.6): rho = rho_atm, polytropic p and eps, v = 0.
+static void atmosphere(const OParams& P, C2POut* out) {
+  out->rho = P.rho_atm;
+  out->press = P.K_atm * std::pow(P.rho_atm, P.gamma_atm);
+  out->vel[0] = out->vel[1] = out->vel[2] = 0.0;
+  out->reset = true;
+}
+
+static C2POut c2p_cell(const Metric3<double>& m, const C2PIn& in, const OParams& P) {
+  C2POut out;
+  out.flag = 0;
+  out.iters = 0;
+  out.reset = false;
+  // atmosphere test on the densitised density before the recovery: D~ < sqrt(gamma) rho_atm
+  if (!(in.Dtilde >= m.sqrtg * P.rho_atm)) {
+    atmosphere(P, &out);
+    out.flag = 2;
+    return out;
+  }
+  double S2 = 0.0, B2 = 0.0, BS = 0.0;
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) {
+      S2 += m.gu[a][b] * in.S[a] * in.S[b];
+      B2 += m.g[a][b] * in.B[a] * in.B[b];
+    }
+  for (int a = 0; a < 3; a++) BS += in.B[a] * in.S[a];
+  bool ok = c2p_noble(m, in, P, S2, B2, BS, &out);
+  if (ok) {
+    out.flag = 0;
+  } else if (P.use_fallback) {
+    ok = c2p_palenzuela(m, in, P, S2, B2, BS, &out);
+    if (ok) out.flag = 1;
+  }
+  if (!ok) {
+    atmosphere(P, &out);
+    out.flag = -1;
+    return out;
+  }
+  if (out.rho < P.rho_atm) {
+    atmosphere(P, &out);
+    out.flag = 2;
+  }
+  return out;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Ghost zones (Sec. 3.8): periodic wrap, or copy of the nearest owned value (linear extrapolation for A).
+
+// stagger: 1 if the quantity is cell-like along `axis`, 0 if vertex-like.
+static void fill_axis(const Grid& G, double* f, int axis, int cell_like, bool linear) {
+  const int n = G.n[axis], g = G.g, Nn = G.N[axis];
+  const int lo = g;
+  const int hi = (cell_like || G.bc[axis] == BC_PERIODIC) ? g + n - 1 : g + n;  // owned index range [lo, hi]
+  const int a1 = (axis + 1) % 3, a2 = (axis + 2) % 3;
+  for (int q2 = 0; q2 <= G.N[a2]; q2++)
+    for (int q1 = 0; q1 <= G.N[a1]; q1++)
+      for (int i = 0; i <= Nn; i++) {
+        if (i >= lo && i <= hi) continue;
+        int p[3];
+        p[axis] = i;
+        p[a1] = q1;
+        p[a2] = q2;
+        double v;
+        if (G.bc[axis] == BC_PERIODIC) {
+          int src = (i < lo) ? i + n : i - n;
+          int q[3] = {p[0], p[1], p[2]};
+          q[axis] = src;
+          v = f[G.at(q)];
+        } else {
+          int e0 = (i < lo) ? lo : hi;
+          int e1 = (i < lo) ? lo + 1 : hi - 1;
+          int q0[3] = {p[0], p[1], p[2]}, q1v[3] = {p[0], p[1], p[2]};
+          q0[axis] = e0;
+          q1v[axis] = e1;
+          if (linear && hi > lo) {  // linear extrapolation needs two owned layers; one layer copies
+            const double f0 = f[G.at(q0)], f1 = f[G.at(q1v)];
+            v = f0 + (double)(i < lo ? lo - i : i - hi) * (f0 - f1);
+          } else {
+            v = f[G.at(q0)];
+          }
+        }
+        f[G.at(p)] = v;
+      }
+}
+
+// cell_like[field][axis] for D, Sx, Sy, Sz, tau, Ax, Ay, Az, Psi
+static const int STATE_CELL_LIKE[9][3] = {{1, 1, 1}, {1, 1, 1}, {1, 1, 1}, {1, 1, 1}, {1, 1, 1},
+                                          {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 0, 0}};
+
+static void ghost_fill_state(const Grid& G, double* const U[9]) {
+  for (int axis = 0; axis < 3; axis++)
+    for (int v = 0; v < 9; v++) fill_axis(G, U[v], axis, STATE_CELL_LIKE[v][axis], v >= 5 && v <= 7);
+}
+
+static void ghost_fill_prims(const Grid& G, double* const P[5]) {
+  for (int axis = 0; axis < 3; axis++)
+    for (int v = 0; v < 5; v++) fill_axis(G, P[v], axis, 1, false);
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Magnetic field from the vector potential (Sec. 3.4, Eq. BEulerian): B~^i = [ijk] d_j A_k on faces, by
+// second-order differences of the edge values.  Cell-centre B^i = (B~^i_- + B~^i_+) / (2 sqrt(gamma_c)).
+
+static void face_B(const Grid& G, const double* Ax, const double* Ay, const double* Az, Field Bf[3]) {
+  for (int d = 0; d < 3; d++) Bf[d].assign(G.size(), 0.0);
+  const double ix = 1.0 / G.dx[0], iy = 1.0 / G.dx[1], iz = 1.0 / G.dx[2];
+  for (int k = 0; k <= G.N[2]; k++)
+    for (int j = 0; j <= G.N[1]; j++)
+      for (int i = 0; i <= G.N[0]; i++) {
+        const long c = G.at(i, j, k);
+        if (j < G.N[1] && k < G.N[2])  // x-face (i, j+1/2, k+1/2)
+          Bf[0][c] = (Az[G.at(i, j + 1, k)] - Az[c]) * iy - (Ay[G.at(i, j, k + 1)] - Ay[c]) * iz;
+        if (i < G.N[0] && k < G.N[2])  // y-face (i+1/2, j, k+1/2)
+          Bf[1][c] = (Ax[G.at(i, j, k + 1)] - Ax[c]) * iz - (Az[G.at(i + 1, j, k)] - Az[c]) * ix;
+        if (i < G.N[0] && j < G.N[1])  // z-face (i+1/2, j+1/2, k)
+          Bf[2][c] = (Ay[G.at(i + 1, j, k)] - Ay[c]) * ix - (Ax[G.at(i, j + 1, k)] - Ax[c]) * iy;
+      }
+}
+
+static void centre_B(const Grid& G, const VertexMetric& vm, const Field Bf[3], Field Bc[3]) {
+  for (int d = 0; d < 3; d++) Bc[d].assign(G.size(), 0.0);
+  for (int k = 0; k < G.N[2]; k++)
+    for (int j = 0; j < G.N[1]; j++)
+      for (int i = 0; i < G.N[0]; i++) {
+        const Metric3<double> m = metric_at_centre(G, vm, i, j, k);
+        const long c = G.at(i, j, k);
+        for (int d = 0; d < 3; d++) {
+          const long c1 = c + G.s[d];
+          Bc[d][c] = 0.5 * (Bf[d][c] + Bf[d][c1]) / m.sqrtg;
+        }
+      }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Source terms (Eq. grmhdsrc, written in 3+1 form with the input K_ij; K = -1/2 L_n gamma, Sec. 2.1):
+//   tau~ : alpha sqrt(g) [T^00 (b^i b^j K_ij - b^i d_i alpha) + T^0i (2 b^j K_ij - d_i alpha) + T^ij K_ij]
+//   S~_i : alpha sqrt(g) [-T^00 alpha d_i alpha + T^0_k d_i beta^k + 1/2 (T^00 b^j b^k + 2 T^0j b^k + T^jk) d_i g_jk]
+// (b = beta here), with T^{mu nu} of Eq. tmunu.
+
+template <class R> struct MetricDeriv {
+  R dalp[3], dbeta[3][3], dg[3][3][3];  // d_i alpha, d_i beta^j, d_i gamma_jk
+};
+
+template <class R> void source_terms(const Metric3<R>& m, const MetricDeriv<R>& dm, const Prim<R>& P, R src[5]) {
+  Comoving<R> c = comoving(m, P);
+  const R a2 = m.alp * m.alp;
+  R guu[4][4];  // inverse 4-metric
+  guu[0][0] = R(-1.0) / a2;
+  for (int i = 0; i < 3; i++) {
+    guu[0][i + 1] = m.beta[i] / a2;
+    guu[i + 1][0] = guu[0][i + 1];
+    for (int j = 0; j < 3; j++) guu[i + 1][j + 1] = m.gu[i][j] - m.beta[i] * m.beta[j] / a2;
+  }
+  R u[4], b[4];
+  u[0] = c.u0;
+  b[0] = c.b0;
+  for (int i = 0; i < 3; i++) {
+    u[i + 1] = c.uup[i];
+    b[i + 1] = c.bup[i];
+  }
+  const R rhohb = P.rho * c.h + c.b2;
+  const R ptot = P.press + R(0.5) * c.b2;
+  R T[4][4];
+  for (int mu = 0; mu < 4; mu++)
+    for (int nu = 0; nu < 4; nu++) T[mu][nu] = rhohb * u[mu] * u[nu] + ptot * guu[mu][nu] - b[mu] * b[nu];
+  R betalow[3];
+  for (int k = 0; k < 3; k++) betalow[k] = m.g[k][0] * m.beta[0] + m.g[k][1] * m.beta[1] + m.g[k][2] * m.beta[2];
+  R T0low[3];  // T^0_k = g_k0 T^00 + g_kj T^0j
+  for (int k = 0; k < 3; k++) {
+    T0low[k] = betalow[k] * T[0][0];
+    for (int j = 0; j < 3; j++) T0low[k] += m.g[k][j] * T[0][j + 1];
+  }
+  const R asg = m.alp * m.sqrtg;
+  // energy
+  R st = R(0.0);
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) st += T[0][0] * m.beta[i] * m.beta[j] * m.K[i][j];
+  for (int i = 0; i < 3; i++) st -= T[0][0] * m.beta[i] * dm.dalp[i];
+  for (int i = 0; i < 3; i++) {
+    R bk = R(0.0);
+    for (int j = 0; j < 3; j++) bk += R(2.0) * m.beta[j] * m.K[i][j];
+    st += T[0][i + 1] * (bk - dm.dalp[i]);
+  }
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) st += T[i + 1][j + 1] * m.K[i][j];
+  src[0] = R(0.0);
+  src[4] = asg * st;
+  // momentum
+  for (int i = 0; i < 3; i++) {
+    R s = -T[0][0] * m.alp * dm.dalp[i];
+    for (int k = 0; k < 3; k++) s += T0low[k] * dm.dbeta[i][k];
+    for (int j = 0; j < 3; j++)
+      for (int k = 0; k < 3; k++)
+        s += R(0.5) * (T[0][0] * m.beta[j] * m.beta[k] + R(2.0) * T[0][j + 1] * m.beta[k] + T[j + 1][k + 1]) *
+             dm.dg[i][j][k];
+    src[1 + i] = asg * s;
+  }
+}
+
+static MetricDeriv<double> metric_deriv_at_centre(const Grid& G, const VertexMetric& vm, int i, int j, int k) {
+  MetricDeriv<double> dm;
+  const int p[3] = {i, j, k};
+  const int half[3] = {1, 1, 1};
+  for (int d = 0; d < 3; d++) {
+    dm.dalp[d] = vertex_interp(G, vm.f[0], p, half, d);
+    for (int a = 0; a < 3; a++) dm.dbeta[d][a] = vertex_interp(G, vm.f[1 + a], p, half, d);
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) dm.dg[d][a][b] = vertex_interp(G, vm.f[4 + SYM[a][b]], p, half, d);
+  }
+  return dm;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// The right-hand side of one stage (Sec. 3.9 workflow: reconstruct, Riemann solve, sources; Sec. 3.4 for
+// the potentials).  Inputs: state with ghosts filled and primitives with ghosts filled.
+
+struct RhsStats {
+  unsigned long long speed_iters, faces;
+};
+
+struct FaceData {
+  Field F[5], vbar[3], cmax, cmin;
+};
+
+static void compute_faces(const Grid& G, const VertexMetric& vm, const OParams& P, double* const prim[5],
+                          const Field Bf[3], const Field Bc[3], int d, FaceData& fd, RhsStats* st) {
+  for (int v = 0; v < 5; v++) fd.F[v].assign(G.size(), 0.0);
+  for (int v = 0; v < 3; v++) fd.vbar[v].assign(G.size(), 0.0);
+  fd.cmax.assign(G.size(), 0.0);
+  fd.cmin.assign(G.size(), 0.0);
+  // reconstructed variables at every cell: rho, p, u^x, u^y, u^z (u = W v) and the centre B
+  Field cellvar[8];
+  for (int v = 0; v < 8; v++) cellvar[v].assign(G.size(), 0.0);
+  for (int k = 0; k < G.N[2]; k++)
+    for (int j = 0; j < G.N[1]; j++)
+      for (int i = 0; i < G.N[0]; i++) {
+        const long c = G.at(i, j, k);
+        const Metric3<double> m = metric_at_centre(G, vm, i, j, k);
+        double v2 = 0.0;
+        for (int a = 0; a < 3; a++)
+          for (int b = 0; b < 3; b++) v2 += m.g[a][b] * prim[2 + a][c] * prim[2 + b][c];
+        const double W = 1.0 / std::sqrt(1.0 - v2);
+        cellvar[0][c] = prim[0][c];
+        cellvar[1][c] = prim[1][c];
+        for (int a = 0; a < 3; a++) cellvar[2 + a][c] = W * prim[2 + a][c];
+        for (int a = 0; a < 3; a++) cellvar[5 + a][c] = Bc[a][c];
+      }
+  const int a1 = (d + 1) % 3, a2 = (d + 2) % 3;
+  for (int q2 = 0; q2 < G.N[a2]; q2++)
+    for (int q1 = 0; q1 < G.N[a1]; q1++)
+      for (int f = G.g; f <= G.g + G.n[d]; f++) {
+        int p[3];
+        p[d] = f;
+        p[a1] = q1;
+        p[a2] = q2;
+        const long fc = G.at(p);
+        FaceInput in;
+        for (int s = 0; s < 2; s++) {
+          // left state: upper face value of cell f-1; right state: lower face value of cell f
+          const int cell = f - 1 + s;
+          double stencil[8][5];
+          for (int t = 0; t < 5; t++) {
+            int q[3] = {p[0], p[1], p[2]};
+            q[d] = cell - 2 + t;
+            const long cc = G.at(q);
+            for (int v = 0; v < 8; v++) stencil[v][t] = cellvar[v][cc];
+          }
+          double rec[8];
+          for (int v = 0; v < 8; v++) {
+            if (v >= 5 && v - 5 == d) {
+              rec[v] = 0.0;  // normal B is the staggered face value, not reconstructed
+              continue;
+            }
+            double aL, aR;
+            recon_cell<double>(P.recon, stencil[v], &aL, &aR);
+            rec[v] = (s == 0) ? aR : aL;
+          }
+          in.rho[s] = rec[0];
+          in.press[s] = rec[1];
+          for (int a = 0; a < 3; a++) in.u[s][a] = rec[2 + a];
+          for (int a = 0; a < 3; a++) in.Bt[s][a] = rec[5 + a];
+        }
+        in.Bn = Bf[d][fc];
+        const Metric3<double> m = metric_at_face(G, vm, d, p[0], p[1], p[2]);
+        FaceOut<double> o = face_solve<double>(m, in, P.gamma, d);
+        for (int v = 0; v < 5; v++) fd.F[v][fc] = o.F[v];
+        for (int a = 0; a < 3; a++) fd.vbar[a][fc] = o.vbar[a];
+        fd.cmax[fc] = o.cmax;
+        fd.cmin[fc] = o.cmin;
+        if (st) {
+          st->speed_iters += o.iters;
+          st->faces++;
+        }
+      }
+}
+
+// PPM value at the interface between stencil positions 2 and 3 of f[0..5]: left = upper value of cell 2
+// (stencil 0..4), right = lower value of cell 3 (stencil 1..5).
+static void ppm_interface(const double f[6], double* L, double* R) {
+  double aL, aR;
+  recon_ppm<double>(f, &aL, &aR);
+  *L = aR;
+  recon_ppm<double>(f + 1, &aL, &aR);
+  *R = aL;
+}
+
+static double hll_edge(double ap, double am, double vL, double BL, double vR, double BR) {
+  const double den = ap + am;
+  if (den > 0.0) return (ap * vL * BL + am * vR * BR - ap * am * (BR - BL)) / den;
+  return 0.5 * (vL * BL + vR * BR);
+}
+
+// Upwind constrained transport (Sec. 3.4, Eqs. uct1, uct2, eq3.20) for the edge along e at vertex-index
+// position p, with (e, d1, d2) cyclic:  E_e = -HLL_d1(v^d1 B~^d2) + HLL_d2(v^d2 B~^d1), the products
+// reconstructed (PPM) to the edge from the faces normal to d2 (resp. d1), and a^d_+- at the edge the maximum
+// over the two d-faces sharing the edge.
+static double uct_E(const Grid& G, const FaceData fd[3], const Field Bf[3], int e, const int p[3]) {
+  const int d1 = (e + 1) % 3, d2 = (e + 2) % 3;
+  double term[2];
+  for (int t = 0; t < 2; t++) {
+    const int dr = (t == 0) ? d1 : d2;    // direction of reconstruction / upwinding
+    const int df = (t == 0) ? d2 : d1;    // normal of the faces that carry the data
+    double vs[6], bs[6];
+    for (int s = 0; s < 6; s++) {
+      int q[3] = {p[0], p[1], p[2]};
+      q[dr] = p[dr] - 3 + s;
+      const long c = G.at(q);
+      vs[s] = fd[df].vbar[dr][c];
+      bs[s] = Bf[df][c];
+    }
+    double vL, vR, BL, BR;
+    ppm_interface(vs, &vL, &vR);
+    ppm_interface(bs, &BL, &BR);
+    // speeds along dr: the two dr-faces sharing the edge are at p - e_df and p
+    int q0[3] = {p[0], p[1], p[2]};
+    q0[df] -= 1;
+    const long c0 = G.at(q0), c1 = G.at(p);
+    const double ap = std::fmax(fd[dr].cmax[c0], fd[dr].cmax[c1]);
+    const double am = std::fmax(fd[dr].cmin[c0], fd[dr].cmin[c1]);
+    term[t] = hll_edge(ap, am, vL, BL, vR, BR);
+  }
+  return -term[0] + term[1];
+}
+
+struct RhsOut {
+  double* const* dU;  // 9 fields (D, Sx, Sy, Sz, tau at cells; Ax, Ay, Az at edges; Psi at vertices)
+};
+
+static void rhs(const Grid& G, const VertexMetric& vm, const OParams& P, double dt, double* const U[9],
+                double* const prim[5], double* const dU[9], RhsStats* st) {
+  Field Bf[3], Bc[3];
+  face_B(G, U[5], U[6], U[7], Bf);
+  centre_B(G, vm, Bf, Bc);
+  FaceData fd[3];
+  for (int d = 0; d < 3; d++) compute_faces(G, vm, P, prim, Bf, Bc, d, fd[d], st);
+  const int g = G.g;
+  // hydro: flux divergence plus sources at interior cells
+  for (int k = g; k < g + G.n[2]; k++)
+    for (int j = g; j < g + G.n[1]; j++)
+      for (int i = g; i < g + G.n[0]; i++) {
+        const long c = G.at(i, j, k);
+        double r[5] = {0, 0, 0, 0, 0};
+        for (int d = 0; d < 3; d++) {
+          const long c1 = c + G.s[d];
+          for (int v = 0; v < 5; v++) r[v] -= (fd[d].F[v][c1] - fd[d].F[v][c]) / G.dx[d];
+        }
+        const Metric3<double> m = metric_at_centre(G, vm, i, j, k);
+        const MetricDeriv<double> dm = metric_deriv_at_centre(G, vm, i, j, k);
+        Prim<double> pr;
+        pr.rho = prim[0][c];
+        pr.press = prim[1][c];
+        pr.eps = pr.press / ((P.gamma - 1.0) * pr.rho);
+        for (int a = 0; a < 3; a++) {
+          pr.vel[a] = prim[2 + a][c];
+          pr.B[a] = Bc[a][c];
+        }
+        double src[5];
+        source_terms<double>(m, dm, pr, src);
+        for (int v = 0; v < 5; v++) dU[v][c] = r[v] + src[v];
+      }
+  // potentials: G_A and F_Psi at vertices, from the vertex average of the edge A_j (Sec. 3.4)
+  Field GA(G.size(), 0.0), FPsi[3];
+  for (int d = 0; d < 3; d++) FPsi[d].assign(G.size(), 0.0);
+  const bool lorenz = (P.gauge == GAUGE_LORENZ);
+  for (int k = 1; k <= G.N[2]; k++)
+    for (int j = 1; j <= G.N[1]; j++)
+      for (int i = 1; i <= G.N[0]; i++) {
+        const long c = G.at(i, j, k);
+        const Metric3<double> m = metric_at_vertex(G, vm, i, j, k);
+        double Av[3];
+        for (int a = 0; a < 3; a++) Av[a] = 0.5 * (U[5 + a][c - G.s[a]] + U[5 + a][c]);
+        const double psi = U[8][c];
+        double bA = 0.0;
+        for (int a = 0; a < 3; a++) bA += m.beta[a] * Av[a];
+        GA[c] = lorenz ? (m.alp * psi / m.sqrtg - bA) : 0.0;
+        for (int a = 0; a < 3; a++) {
+          double Aup = m.gu[a][0] * Av[0] + m.gu[a][1] * Av[1] + m.gu[a][2] * Av[2];
+          FPsi[a][c] = m.alp * m.sqrtg * Aup - m.beta[a] * psi;
+        }
+      }
+  // dA_e/dt = -E_e - d_e G_A on edges
+  for (int e = 0; e < 3; e++) {
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; a++) {
+      lo[a] = g;
+      hi[a] = (a == e) ? g + G.n[a] - 1 : g + G.n[a];
+    }
+    for (int k = lo[2]; k <= hi[2]; k++)
+      for (int j = lo[1]; j <= hi[1]; j++)
+        for (int i = lo[0]; i <= hi[0]; i++) {
+          const int p[3] = {i, j, k};
+          const long c = G.at(p);
+          const double E = uct_E(G, fd, Bf, e, p);
+          const double dG = (GA[c + G.s[e]] - GA[c]) / G.dx[e];
+          dU[5 + e][c] = -E - dG;
+        }
+  }
+  // dPsi/dt = -d_j F_Psi^j - xi alpha Psi at vertices (Eq. recastedScalarPot)
+  const double xi = (P.xi_lorenz > 0.0) ? P.xi_lorenz : 1.5 / dt;
+  for (int k = g; k <= g + G.n[2]; k++)
+    for (int j = g; j <= g + G.n[1]; j++)
+      for (int i = g; i <= g + G.n[0]; i++) {
+        const long c = G.at(i, j, k);
+        if (!lorenz) {
+          dU[8][c] = 0.0;
+          continue;
+        }
+        double div = 0.0;
+        for (int a = 0; a < 3; a++) div += (FPsi[a][c + G.s[a]] - FPsi[a][c - G.s[a]]) / (2.0 * G.dx[a]);
+        dU[8][c] = -div - xi * vm.f[0][c] * U[8][c];
+      }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Recovery over the interior cells of a block.
+
+static void con2prim(const Grid& G, const VertexMetric& vm, const OParams& P, double* const U[9],
+                     double* const prim[5], signed char* flags, OStats* stats) {
+  Field Bf[3], Bc[3];
+  face_B(G, U[5], U[6], U[7], Bf);
+  centre_B(G, vm, Bf, Bc);
+  const int g = G.g;
+  for (int k = g; k < g + G.n[2]; k++)
+    for (int j = g; j < g + G.n[1]; j++)
+      for (int i = g; i < g + G.n[0]; i++) {
+        const long c = G.at(i, j, k);
+        const Metric3<double> m = metric_at_centre(G, vm, i, j, k);
+        C2PIn in;
+        in.Dtilde = U[0][c];
+        in.D = U[0][c] / m.sqrtg;
+        for (int a = 0; a < 3; a++) in.S[a] = U[1 + a][c] / m.sqrtg;
+        in.tau = U[4][c] / m.sqrtg;
+        for (int a = 0; a < 3; a++) in.B[a] = Bc[a][c];
+        in.guess_rho = prim[0][c];
+        in.guess_press = prim[1][c];
+        for (int a = 0; a < 3; a++) in.guess_vel[a] = prim[2 + a][c];
+        C2POut o = c2p_cell(m, in, P);
+        prim[0][c] = o.rho;
+        prim[1][c] = o.press;
+        for (int a = 0; a < 3; a++) prim[2 + a][c] = o.vel[a];
+        if (flags) flags[c] = (signed char)o.flag;
+        if (stats) {
+          stats->iters += o.iters;
+          if (o.flag == 0) stats->n_noble++;
+          else if (o.flag == 1) stats->n_fallback++;
+          else if (o.flag == 2) stats->n_atm++;
+          else stats->n_failed++;
+        }
+        if (o.reset) {
+          // conserved variables reset from the atmosphere primitives with B kept (Sec. 3.6)
+          Prim<double> pr;
+          pr.rho = o.rho;
+          pr.press = o.press;
+          pr.eps = o.press / ((P.gamma_atm - 1.0) * o.rho);
+          for (int a = 0; a < 3; a++) {
+            pr.vel[a] = 0.0;
+            pr.B[a] = Bc[a][c];
+          }
+          Comoving<double> cm = comoving(m, pr);
+          Cons<double> uc = prim2con(m, pr, cm);
+          U[0][c] = uc.D;
+          for (int a = 0; a < 3; a++) U[1 + a][c] = uc.S[a];
+          U[4][c] = uc.tau;
+        }
+      }
+}
+
+// Conserved variables at all cells from primitives (initial data, Sec. 3.9 and Eq. cons).
+static void prim2con_grid(const Grid& G, const VertexMetric& vm, const OParams& P, double* const U[9],
+                          double* const prim[5]) {
+  Field Bf[3], Bc[3];
+  face_B(G, U[5], U[6], U[7], Bf);
+  centre_B(G, vm, Bf, Bc);
+  for (int k = 0; k < G.N[2]; k++)
+    for (int j = 0; j < G.N[1]; j++)
+      for (int i = 0; i < G.N[0]; i++) {
+        const long c = G.at(i, j, k);
+        const Metric3<double> m = metric_at_centre(G, vm, i, j, k);
+        Prim<double> pr;
+        pr.rho = prim[0][c];
+        pr.press = prim[1][c];
+        pr.eps = pr.press / ((P.gamma - 1.0) * pr.rho);
+        for (int a = 0; a < 3; a++) {
+          pr.vel[a] = prim[2 + a][c];
+          pr.B[a] = Bc[a][c];
+        }
+        Comoving<double> cm = comoving(m, pr);
+        Cons<double> uc = prim2con(m, pr, cm);
+        U[0][c] = uc.D;
+        for (int a = 0; a < 3; a++) U[1 + a][c] = uc.S[a];
+        U[4][c] = uc.tau;
+      }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Classical RK4 stage (method of lines): k_s = L(U_s); U_{s+1} = U_n + c_{s+1} dt k_s, c = (1/2, 1/2, 1);
+// U_acc accumulates b_s dt k_s, b = (1/6, 1/3, 1/3, 1/6); the last stage writes U_n + U_acc + dt/6 k_3.
+// Stage order (Sec. 3.9): ghost fill U_s, con2prim on the interior, ghost fill primitives, RHS, combine.
+
+static void owned_range(const Grid& G, int v, int lo[3], int hi[3]) {
+  for (int a = 0; a < 3; a++) {
+    lo[a] = G.g;
+    hi[a] = STATE_CELL_LIKE[v][a] ? G.g + G.n[a] - 1 : G.g + G.n[a];
+  }
+}
+
+static void rk_stage(const Grid& G, const VertexMetric& vm, const OParams& P, int stage, double dt,
+                     double* const Un[9], double* const Us[9], double* const Unext[9], double* const Uacc[9],
+                     double* const prim[5], signed char* flags, OStats* stats) {
+  ghost_fill_state(G, Us);
+  con2prim(G, vm, P, Us, prim, flags, stats);
+  ghost_fill_prims(G, prim);
+  std::vector<Field> k(9, Field(G.size(), 0.0));
+  double* kp[9];
+  for (int v = 0; v < 9; v++) kp[v] = k[v].data();
+  rhs(G, vm, P, dt, Us, prim, kp, nullptr);
+  static const double cnext[3] = {0.5, 0.5, 1.0};
+  static const double bw[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  for (int v = 0; v < 9; v++) {
+    int lo[3], hi[3];
+    owned_range(G, v, lo, hi);
+    for (int kk = lo[2]; kk <= hi[2]; kk++)
+      for (int j = lo[1]; j <= hi[1]; j++)
+        for (int i = lo[0]; i <= hi[0]; i++) {
+          const long c = G.at(i, j, kk);
+          const double kv = k[v][c];
+          if (stage == 0) {
+            Uacc[v][c] = bw[0] * dt * kv;
+            Unext[v][c] = Un[v][c] + cnext[0] * dt * kv;
+          } else if (stage < 3) {
+            Uacc[v][c] = Uacc[v][c] + bw[stage] * dt * kv;
+            Unext[v][c] = Un[v][c] + cnext[stage] * dt * kv;
+          } else {
+            Unext[v][c] = Un[v][c] + Uacc[v][c] + bw[3] * dt * kv;
+          }
+        }
+  }
+}
+
+}  // namespace asterx_oracle
+
+// ------------------------------------------------------------------------------------------------------
+// C entry points for the test suite (ctypes).
+
+using namespace asterx_oracle;
+
+static VertexMetric vmetric(const double* const* m) {
+  VertexMetric vm;
+  for (int a = 0; a < 16; a++) vm.f[a] = m[a];
+  return vm;
+}
+
+extern "C" {
+
+int oracle_abi_version(void) { return 1; }
+
+void oracle_ghost_fill_state(const OBlock* b, double* const* U) {
+  Grid G(*b);
+  ghost_fill_state(G, U);
+}
+
+void oracle_ghost_fill_prims(const OBlock* b, double* const* P) {
+  Grid G(*b);
+  ghost_fill_prims(G, P);
+}
+
+void oracle_prim2con(const OParams* p, const OBlock* b, const double* const* metric, double* const* U,
+                     double* const* prim) {
+  Grid G(*b);
+  prim2con_grid(G, vmetric(metric), *p, U, prim);
+}
+
+void oracle_con2prim(const OParams* p, const OBlock* b, const double* const* metric, double* const* U,
+                     double* const* prim, signed char* flags, OStats* stats) {
+  Grid G(*b);
+  con2prim(G, vmetric(metric), *p, U, prim, flags, stats);
+}
+
+void oracle_rhs(const OParams* p, const OBlock* b, const double* const* metric, double* const* U,
+                double* const* prim, double* const* dU, double dt, unsigned long long* speed_iters) {
+  Grid G(*b);
+  RhsStats st{0, 0};
+  rhs(G, vmetric(metric), *p, dt, U, prim, dU, &st);
+  if (speed_iters) {
+    speed_iters[0] = st.speed_iters;
+    speed_iters[1] = st.faces;
+  }
+}
+
+void oracle_face_B(const OBlock* b, double* const* U, double* const* Bf) {
+  Grid G(*b);
+  Field f[3];
+  face_B(G, U[5], U[6], U[7], f);
+  for (int d = 0; d < 3; d++) std::memcpy(Bf[d], f[d].data(), sizeof(double) * G.size());
+}
+
+void oracle_rk_stage(const OParams* p, const OBlock* b, const double* const* metric, int stage, double dt,
+                     double* const* Un, double* const* Us, double* const* Unext, double* const* Uacc,
+                     double* const* prim, signed char* flags, OStats* stats) {
+  Grid G(*b);
+  rk_stage(G, vmetric(metric), *p, stage, dt, Un, Us, Unext, Uacc, prim, flags, stats);
+}
+
+// Pointwise helpers for the pins of the test suite.
+
+void oracle_point_prim2con(const OParams* p, const double* m16, const double* prim5, const double* B3,
+                           double* cons5, double* flux15) {
+  Metric3<double> m;
+  m.alp = m16[0];
+  for (int a = 0; a < 3; a++) m.beta[a] = m16[1 + a];
+  for (int a = 0; a < 3; a++)
+    for (int c = 0; c < 3; c++) {
+      m.g[a][c] = m16[4 + SYM[a][c]];
+      m.K[a][c] = m16[10 + SYM[a][c]];
+    }
+  metric_complete(m);
+  Prim<double> pr;
+  pr.rho = prim5[0];
+  pr.press = prim5[1];
+  pr.eps = pr.press / ((p->gamma - 1.0) * pr.rho);
+  for (int a = 0; a < 3; a++) {
+    pr.vel[a] = prim5[2 + a];
+    pr.B[a] = B3[a];
+  }
+  Comoving<double> c = comoving(m, pr);
+  Cons<double> U = prim2con(m, pr, c);
+  cons5[0] = U.D;
+  for (int a = 0; a < 3; a++) cons5[1 + a] = U.S[a];
+  cons5[4] = U.tau;
+  if (flux15)
+    for (int d = 0; d < 3; d++) flux(m, pr, c, U, d, flux15 + 5 * d);
+}
+
+void oracle_point_wave_speeds(const OParams* p, const double* m16, const double* prim5, const double* B3, int d,
+                              double* lam) {
+  Metric3<double> m;
+  m.alp = m16[0];
+  for (int a = 0; a < 3; a++) m.beta[a] = m16[1 + a];
+  for (int a = 0; a < 3; a++)
+    for (int c = 0; c < 3; c++) {
+      m.g[a][c] = m16[4 + SYM[a][c]];
+      m.K[a][c] = m16[10 + SYM[a][c]];
+    }
+  metric_complete(m);
+  Prim<double> pr;
+  pr.rho = prim5[0];
+  pr.press = prim5[1];
+  pr.eps = pr.press / ((p->gamma - 1.0) * pr.rho);
+  for (int a = 0; a < 3; a++) {
+    pr.vel[a] = prim5[2 + a];
+    pr.B[a] = B3[a];
+  }
+  Comoving<double> c = comoving(m, pr);
+  int it;
+  wave_speeds(m, pr, c, p->gamma, d, &lam[0], &lam[1], &it);
+}
+
+// c2p of one undensitised state (cons5 = D, S_i, tau; B3 undensitised) with the solver chosen by `which`:
+// 0 = full chain, 1 = Noble only, 2 = Palenzuela only.  Returns the flag (or -9 if the solver failed).
+int oracle_point_c2p(const OParams* p, const double* m16, const double* cons5, const double* B3,
+                     const double* guess5, double* prim5, int which, int* iters) {
+  Metric3<double> m;
+  m.alp = m16[0];
+  for (int a = 0; a < 3; a++) m.beta[a] = m16[1 + a];
+  for (int a = 0; a < 3; a++)
+    for (int c = 0; c < 3; c++) {
+      m.g[a][c] = m16[4 + SYM[a][c]];
+      m.K[a][c] = m16[10 + SYM[a][c]];
+    }
+  metric_complete(m);
+  C2PIn in;
+  in.D = cons5[0];
+  in.Dtilde = cons5[0] * m.sqrtg;
+  for (int a = 0; a < 3; a++) in.S[a] = cons5[1 + a];
+  in.tau = cons5[4];
+  for (int a = 0; a < 3; a++) in.B[a] = B3[a];
+  in.guess_rho = guess5[0];
+  in.guess_press = guess5[1];
+  for (int a = 0; a < 3; a++) in.guess_vel[a] = guess5[2 + a];
+  C2POut o;
+  o.iters = 0;
+  o.flag = 0;
+  o.reset = false;
+  int flag;
+  if (which == 0) {
+    o = c2p_cell(m, in, *p);
+    flag = o.flag;
+  } else {
+    double S2 = 0.0, B2 = 0.0, BS = 0.0;
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) {
+        S2 += m.gu[a][b] * in.S[a] * in.S[b];
+        B2 += m.g[a][b] * in.B[a] * in.B[b];
+      }
+    for (int a = 0; a < 3; a++) BS += in.B[a] * in.S[a];
+    bool ok = (which == 1) ? c2p_noble(m, in, *p, S2, B2, BS, &o) : c2p_palenzuela(m, in, *p, S2, B2, BS, &o);
+    flag = ok ? (which == 1 ? 0 : 1) : -9;
+  }
+  prim5[0] = o.rho;
+  prim5[1] = o.press;
+  for (int a = 0; a < 3; a++) prim5[2 + a] = o.vel[a];
+  if (iters) *iters = o.iters;
+  return flag;
+}
+
+// Batched version of oracle_point_c2p over n independent states (arrays of 16, 5, 3, 5 doubles per state).
+void oracle_batch_c2p(const OParams* p, long n, const double* m16, const double* cons5, const double* B3,
+                      const double* guess5, double* prim5, int which, int* flags, int* iters) {
+  for (long q = 0; q < n; q++)
+    flags[q] = oracle_point_c2p(p, m16 + 16 * q, cons5 + 5 * q, B3 + 3 * q, guess5 + 5 * q, prim5 + 5 * q, which,
+                                iters ? iters + q : nullptr);
+}
+
+// Batched prim->cons over n states (undensitised output when the metric is flat; densitised in general).
+void oracle_batch_prim2con(const OParams* p, long n, const double* m16, const double* prim5, const double* B3,
+                           double* cons5) {
+  for (long q = 0; q < n; q++) oracle_point_prim2con(p, m16 + 16 * q, prim5 + 5 * q, B3 + 3 * q, cons5 + 5 * q,
+                                                     nullptr);
+}
+
+// Reconstruction of one cell from five values: returns the lower and upper face values.
+void oracle_point_recon(int scheme, const double* a5, double* aL, double* aR) {
+  recon_cell<double>(scheme, a5, aL, aR);
+}
+
+// Sources at one point from an explicit metric, its derivatives and the primitives (for the 4-covariant pin).
+void oracle_point_sources(const OParams* p, const double* m16, const double* dalp3, const double* dbeta9,
+                          const double* dg27, const double* prim5, const double* B3, double* src5) {
+  Metric3<double> m;
+  m.alp = m16[0];
+  for (int a = 0; a < 3; a++) m.beta[a] = m16[1 + a];
+  for (int a = 0; a < 3; a++)
+    for (int c = 0; c < 3; c++) {
+      m.g[a][c] = m16[4 + SYM[a][c]];
+      m.K[a][c] = m16[10 + SYM[a][c]];
+    }
+  metric_complete(m);
+  MetricDeriv<double> dm;
+  for (int i = 0; i < 3; i++) {
+    dm.dalp[i] = dalp3[i];
+    for (int a = 0; a < 3; a++) dm.dbeta[i][a] = dbeta9[3 * i + a];
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) dm.dg[i][a][b] = dg27[9 * i + 3 * a + b];
+  }
+  Prim<double> pr;
+  pr.rho = prim5[0];
+  pr.press = prim5[1];
+  pr.eps = pr.press / ((p->gamma - 1.0) * pr.rho);
+  for (int a = 0; a < 3; a++) {
+    pr.vel[a] = prim5[2 + a];
+    pr.B[a] = B3[a];
+  }
+  source_terms<double>(m, dm, pr, src5);
+}
+
+// Sources at the interior cells of a grid from the vertex metric (4th-order interpolation and derivatives).
+void oracle_grid_sources(const OParams* p, const OBlock* b, const double* const* metric, double* const* U,
+                         double* const* prim, double* const* src) {
+  Grid G(*b);
+  VertexMetric vm = vmetric(metric);
+  Field Bf[3], Bc[3];
+  face_B(G, U[5], U[6], U[7], Bf);
+  centre_B(G, vm, Bf, Bc);
+  for (int k = G.g; k < G.g + G.n[2]; k++)
+    for (int j = G.g; j < G.g + G.n[1]; j++)
+      for (int i = G.g; i < G.g + G.n[0]; i++) {
+        const long c = G.at(i, j, k);
+        const Metric3<double> m = metric_at_centre(G, vm, i, j, k);
+        const MetricDeriv<double> dm = metric_deriv_at_centre(G, vm, i, j, k);
+        Prim<double> pr;
+        pr.rho = prim[0][c];
+        pr.press = prim[1][c];
+        pr.eps = pr.press / ((p->gamma - 1.0) * pr.rho);
+        for (int a = 0; a < 3; a++) {
+          pr.vel[a] = prim[2 + a][c];
+          pr.B[a] = Bc[a][c];
+        }
+        double s[5];
+        source_terms<double>(m, dm, pr, s);
+        for (int v = 0; v < 5; v++) src[v][c] = s[v];
+      }
+}
+
+}  // extern "C"
