@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 GRMHD RK stage: FP64 zone-updates per second per RK stage.
+
+Workload: the 128^3 block of WENO-Z + HLLE over the frozen isotropic Schwarzschild slice (M = 0.1, centre at
+(-1, 0, 0)) with Balsara test-1 states split along x and copy BCs; one step = one classical RK4 step (4 stages:
+ghost fill, recovery, reconstruction, face solve, UCT, potentials, sources, combine).  Inputs are seeded and
+synthetic; the frozen-metric geometry is derived once before timing (asterx_prepare).  The state lives in HBM
+(about 0.2 GB per state copy and 3.9 GB of workspace, far above the 129 MB L2), so no L2 flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 it is launched by torch.distributed.run; every rank runs an independent replica of the block
+(no data exchange: the path has none) and rank 0 prints one JSON line.  --impl reference times the CPU oracle
+(the reference implementation of this tier) on a bounded slab of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FP64 GRMHD zone-updates/s per RK stage; batched-vs-single and adjoint/forward time"
+UNIT = "zone-updates/s"
+WORKLOAD = ("128^3 block + 3 ghosts, FP64, ideal gas Gamma=5/3, WENO-Z + HLLE + UCT, Noble2D/Palenzuela c2p, "
+            "Balsara-1 Riemann data split at x=0 (Bx=0.5, By=+-1), frozen isotropic Schwarzschild M=0.1 centred "
+            "0.5 outside the box, copy BCs, one RK4 step = 4 stages")
+# kernels the library launches per RK stage: 3 + 3 ghost sweeps, 2 field kernels, recovery, velocity, 3 x
+# (reconstruction + face solve), vertex potentials, 3 edge kernels, scalar potential, cells
+LAUNCHES_PER_STAGE = 22
+# nominal FP64 peak: 152 SMs x 2 DFMA/clock/SM x 2 flops x 2.07 GHz (unit counts and clock of the GB300 recipe)
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=128, help="cells per axis of the block (default: the 128^3 workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region (SM clock, max clock, power, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        smax = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def read_face_flops():
+    """Algorithmic FP64 flops per face of the face-solve kernel, counted by the oracle's flop-counting scalar on
+    this workload (profiles/face_flops_config2_128.txt, written by oracle/count_face_flops.py)."""
+    path = os.path.join(ROOT, "profiles", "face_flops_config2_128.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                vals[k.strip()] = float(v.split()[0])
+    return vals.get("flops_per_face")
+
+
+def read_traffic():
+    path = os.path.join(ROOT, "profiles", "k_faces_config2_128_ncu.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("dram_bytes_per_launch") and "=" in line:
+                return float(line.split("=", 1)[1].split()[0])
+    return None
+
+
+def slab_workload(w_full, ny, nz):
+    from paper_2406_11669_gb300 import workloads as W
+    n = w_full.n
+    lo = (0, (n[1] - ny) // 2, (n[2] - nz) // 2)
+    return W.sub_block(w_full, lo, (n[0], ny, nz), name="slab")
+
+
+def cpu_oracle_steps(w, steps):
+    """Times `steps` oracle RK4 steps on workload w; returns seconds per step (single host thread)."""
+    import oracle as O
+    U, P = O.initial_state(w)
+    M = O.metric_array(w)
+    O.ghost_fill_state(w, U)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U, _ = O.rk4_step(w, M, U, P)
+        O.ghost_fill_state(w, U)
+    return (time.perf_counter() - t0) / steps
+
+
+def cpu_baseline(w_full):
+    ny = nz = 16
+    w = slab_workload(w_full, ny, nz)
+    sec = cpu_oracle_steps(w, 1)
+    cells = w.interior_cells
+    return {"value": cells * 4 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one RK4 step of the {w.n[0]}x{ny}x{nz} central slab of the same workload "
+                      f"({cells} cells, {sec:.1f} s, single host thread, g++ -O2)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2406_11669_gb300 import workloads as W
+    w_full = W.config2(n=(args.n,) * 3)
+    w = slab_workload(w_full, 8, 8)
+    sec_w = cpu_oracle_steps(w, max(args.warmup, 0)) if args.warmup > 0 else 0.0
+    del sec_w
+    sec = cpu_oracle_steps(w, args.steps)
+    cells = w.interior_cells
+    value = cells * 4 / sec
+    sample = (f"each step: one oracle RK4 step of the {w.n[0]}x8x8 central slab of the workload ({cells} cells), "
+              f"single host thread")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample_cells": cells},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2406_11669_gb300 import asterx as A
+    from paper_2406_11669_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = W.config2(n=(args.n,) * 3)
+    s = A.Solver.for_workload(w, device=dev)
+    M = torch.from_numpy(np.ascontiguousarray(np.stack([w.metric[k] for k in W.METRIC_NAMES]))).to(dev)
+    P0 = np.ascontiguousarray(np.stack([w.prims[k] for k in W.PRIM_NAMES]))
+    s.prepare(M)
+    U = s.zeros_state()
+    U[5] = torch.from_numpy(w.A["Ax"]).to(dev)
+    U[6] = torch.from_numpy(w.A["Ay"]).to(dev)
+    U[7] = torch.from_numpy(w.A["Az"]).to(dev)
+    P = torch.from_numpy(P0).to(dev)
+    s.fill_ghosts(U)
+    s.prim2con(U, P)
+    stats = torch.zeros(5, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        s.rk4_step(U, P, w.dt, stats=stats)
+    torch.cuda.synchronize(dev)
+    stats.zero_()
+    A.profile_enable(args.steps * 4 * 3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.rk4_step(U, P, w.dt, stats=stats)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    nface, face_ms = A.profile_read()
+    A.profile_disable()
+    ms_max = max_over_ranks(ms, world)
+    cells = w.interior_cells
+    value = world * cells * 4 * args.steps / (ms_max / 1e3)
+    c2p = stats.cpu().tolist()
+    finite = bool(torch.isfinite(U[:, w.g:-w.g - 1, w.g:-w.g - 1, w.g:-w.g - 1]).all())
+
+    # end to end through the host-buffer ABI call: H2D of U and P, the RK4 step, D2H of U and P, every step
+    hU = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
+    hP = torch.empty(P.shape, dtype=torch.float64, pin_memory=True)
+    hU.copy_(U)
+    hP.copy_(P)
+    dU2 = torch.empty_like(U)
+    dP2 = torch.empty_like(P)
+    s.rk4_step_host(hU, hP, dU2, dP2, w.dt)  # warm-up
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.rk4_step_host(hU, hP, dU2, dP2, w.dt)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = world * cells * 4 * args.steps / e2e_s
+    io_bytes = (9 + 5) * U[0].numel() * 8
+
+    # FP64 FMA throughput measured on this GPU (context for the nominal peak)
+    blocks, threads, iters = 152 * 8, 256, 4096
+    out = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
+    A.dfma_probe(out, blocks, threads, 64)
+    torch.cuda.synchronize(dev)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    A.dfma_probe(out, blocks, threads, iters)
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    dfma_tflops = blocks * threads * iters * 8 * 8 * 2 / (p0.elapsed_time(p1) / 1e3) / 1e12
+
+    if rank != 0:
+        return
+    faces_per_launch = (args.n + 1) * (args.n + 6) ** 2
+    flops_per_face = read_face_flops()
+    face_avg_ms = face_ms / max(nface, 1)
+    roofline = {"bound": "alu", "kernel": "k_faces (face solve: prim->cons, fluxes, quartic speeds, HLLE)",
+                "unit": "TFLOP/s", "peak": FP64_NOMINAL_TFLOPS,
+                "peak_kind": "nominal FP64 (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)",
+                "peak_measured_dfma": dfma_tflops, "launch_ms": face_avg_ms, "launches": nface,
+                "faces_per_launch": faces_per_launch, "flops_per_face": flops_per_face,
+                "achieved": None, "frac": None, "traffic": read_traffic(),
+                "face_share_of_step": face_ms / (ms * 1.0) if ms > 0 else None}
+    if flops_per_face:
+        achieved = flops_per_face * faces_per_launch / (face_avg_ms / 1e3) / 1e12
+        roofline["achieved"] = achieved
+        roofline["frac"] = achieved / FP64_NOMINAL_TFLOPS
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+              "config": {"workload": WORKLOAD, "interior_cells": cells, "stages_per_step": 4,
+                         "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush)",
+                         "resident_bytes": int(s.ws_bytes + 2 * U.numel() * 8 + P.numel() * 8 + M.numel() * 8)},
+              "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+                      "d2h_bytes_per_step": io_bytes},
+              "gpu_launches": LAUNCHES_PER_STAGE * 4 * args.steps,
+              "clocks": clk, "roofline": roofline, "c2p_counters_timed": c2p, "state_finite": finite}
+    if not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(result))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    world, _, _ = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * asterx.h -- C ABI of the GB300 (sm_103a) library for one method-of-lines RK stage of the Valencia GRMHD
+ * equations on uniform Cartesian blocks over a frozen 3+1 metric (AsterX, arXiv:2406.11669).
+ *
+ * Method (paper sections): Valencia conservative form (Sec. 2.2, Eqs. fluxconseqs, grmhdeqs, grmhdsrc, cons);
+ * vector potential on edges with B~ = curl A on faces and the generalised Lorenz gauge (Sec. 2.3, 3.4, Eqs.
+ * BEulerian, Ainductioneqs, recastedAvec, recastedScalarPot); minmod / PPM / WENO-Z reconstruction and HLLE
+ * fluxes with magnetosonic speeds (Sec. 3.3, Eq. HLLEfluxes); upwind constrained transport (Sec. 3.4, Eqs.
+ * uct1, uct2, eq3.20); Noble 2D recovery with a Palenzuela 1D fallback and atmosphere (Sec. 3.5, 3.6);
+ * ideal-gas EOS (Sec. 3.7); 4th-order vertex-metric interpolation (Sec. 3.2); classical RK4 (Sec. 5).
+ *
+ * Data layout.  A block has n[d] interior cells and g = 3 ghost layers per side; N = n + 2g.  Every field is a
+ * contiguous array of (N[0]+1)(N[1]+1)(N[2]+1) doubles, x fastest: index(i,j,k) = i + (N0+1)(j + (N1+1) k).
+ * Index (i,j,k) names the object whose lower corner is vertex (i,j,k): cell centre (i+1/2, j+1/2, k+1/2),
+ * x-face (i, j+1/2, k+1/2), x-edge (i+1/2, j, k), vertex (i, j, k).  Vertex i lies at x0 + (i - g) dx.
+ *   state:  D~, S~x, S~y, S~z, tau~ (cells, densitised by sqrt(gamma)); A_x, A_y, A_z (edges); Psi (vertices)
+ *   prims:  rho, p, v^x, v^y, v^z (cells; v^i Eulerian; eps = p / ((Gamma - 1) rho))
+ *   metric: alpha, beta^x,y,z, gamma_xx,xy,xz,yy,yz,zz, K_xx,xy,xz,yy,yz,zz (vertices)
+ *
+ * Ownership.  The caller owns every pointer.  All array pointers are DEVICE pointers (8-byte aligned) unless a
+ * comment says HOST.  The library never allocates: each call uses the caller's workspace `ws` of at least
+ * asterx_workspace_size() bytes (256-byte aligned).  The workspace holds the frozen-metric geometry written by
+ * asterx_prepare(), so one workspace serves one (block, metric) pair; pass it unchanged to the later calls.
+ *
+ * Execution.  Every call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy default stream) and
+ * returns after enqueueing.  Device-side counters are written to device memory and read only after the caller
+ * synchronises.  Calls on different streams with different workspaces are independent; calls that share a
+ * workspace must be ordered by the caller.
+ *
+ * Errors.  Argument errors are detected on the host before any launch (ASTERX_EINVAL); launch failures return
+ * ASTERX_ECUDA.  Nothing aborts, throws across the ABI or traps on the device.  Recovery failures are soft: a
+ * cell whose recovery fails gets the atmosphere and flag -1, and the per-call counters record it.
+ */
+#ifndef ASTERX_H
+#define ASTERX_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st *asterx_stream; /* a cudaStream_t */
+
+typedef enum {
+  ASTERX_OK = 0,
+  ASTERX_EINVAL = 1,   /* invalid argument (host check, nothing launched) */
+  ASTERX_ECUDA = 2,    /* a CUDA launch or runtime call failed */
+  ASTERX_ENOMEM = 3,   /* workspace smaller than asterx_workspace_size() */
+  ASTERX_EC2P = 4,     /* reserved: soft recovery failures are reported through the counters */
+  ASTERX_ETIMEOUT = 5  /* a bounded device-side wait gave up */
+} asterx_status;
+
+typedef enum { ASTERX_RECON_MINMOD = 0, ASTERX_RECON_PPM = 1, ASTERX_RECON_WENOZ = 2 } asterx_recon;
+typedef enum { ASTERX_BC_PERIODIC = 0, ASTERX_BC_COPY = 1 } asterx_bc;
+typedef enum { ASTERX_GAUGE_LORENZ = 0, ASTERX_GAUGE_ALGEBRAIC = 1 } asterx_gauge;
+
+/* Physics parameters (HOST struct, read during the call). */
+typedef struct {
+  double gamma;        /* ideal-gas adiabatic index, P = (Gamma-1) rho eps (Sec. 3.7) */
+  double rho_atm;      /* atmosphere density: D~ < sqrt(gamma) rho_atm => atmosphere (Sec. 3.6) */
+  double K_atm;        /* atmosphere polytrope P = K rho^Gamma_atm (Sec. 3.7) */
+  double gamma_atm;
+  double c2p_tol;      /* Noble Newton tolerance on |dz|/z and |dv^2| (e.g. 1e-13) */
+  int c2p_maxiter;     /* Noble iteration cap (e.g. 100) */
+  int brent_maxiter;   /* Palenzuela/Brent iteration cap (e.g. 300) */
+  double W_max;        /* Lorentz-factor cap used on failure paths of the recovery (e.g. 50) */
+  int recon;           /* asterx_recon */
+  int gauge;           /* asterx_gauge; the generalised Lorenz gauge is the paper's default (Sec. 3.4) */
+  double xi_lorenz;    /* Lorenz damping xi; 0 => 1.5 / dt (Sec. 3.4) */
+  int use_fallback;    /* 1: Palenzuela fallback after a Noble failure */
+} asterx_params;
+
+/* Geometry of one block (HOST struct). */
+typedef struct {
+  int n[3];       /* interior cells per axis, >= 1 */
+  int g;          /* ghost layers, must be 3 */
+  double x0[3];   /* position of the first interior vertex */
+  double dx[3];   /* grid spacing, > 0 */
+  int bc[3];      /* asterx_bc per axis (both sides) */
+} asterx_block;
+
+/* Field pointer sets (HOST structs holding DEVICE pointers). */
+typedef struct { double *D, *Sx, *Sy, *Sz, *tau, *Ax, *Ay, *Az, *Psi; } asterx_state;
+typedef struct { const double *alp, *betax, *betay, *betaz, *gxx, *gxy, *gxz, *gyy, *gyz, *gzz,
+                 *kxx, *kxy, *kxz, *kyy, *kyz, *kzz; } asterx_metric;
+typedef struct { double *rho, *press, *velx, *vely, *velz; } asterx_prims;
+
+/* Recovery counters (DEVICE memory, accumulated with atomics; the caller zeroes them when it wants). */
+typedef struct {
+  unsigned long long n_noble;     /* cells recovered by Noble 2D */
+  unsigned long long n_fallback;  /* cells recovered by Palenzuela 1D after Noble failed */
+  unsigned long long n_atm;       /* cells set to the atmosphere by the density test */
+  unsigned long long n_failed;    /* cells where both solvers failed (atmosphere applied, flag -1) */
+  unsigned long long iters;       /* total Noble iterations */
+} asterx_c2p_stats;
+
+/* ABI version of this header (checked by the binding). */
+int asterx_abi_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char *asterx_status_str(asterx_status s);
+
+/* Bytes of workspace a block needs (0 if the block is invalid). */
+size_t asterx_workspace_size(const asterx_block *blk);
+
+/* Derive the frozen-metric geometry (Sec. 3.2: 4th-order Lagrange interpolation of the vertex metric to
+ * centres and faces, 4th-order centre derivatives for the sources, inverse metric and sqrt(gamma)) into `ws`.
+ * Must precede every other call that takes this workspace.  `metric` points to 16 device arrays. */
+asterx_status asterx_prepare(const asterx_params *p, const asterx_block *blk, const asterx_metric *metric,
+                             void *ws, size_t ws_bytes, asterx_stream stream);
+
+/* Conserved variables from primitives (Eq. cons) at every cell of the padded block, with B~ = curl A of the
+ * state's edge potential (Eq. BEulerian).  Reads P and U's A; writes U's D~, S~, tau~. */
+asterx_status asterx_prim2con(const asterx_params *p, const asterx_block *blk, asterx_state *U,
+                              const asterx_prims *P, void *ws, size_t ws_bytes, asterx_stream stream);
+
+/* Primitive recovery on the interior cells (Sec. 3.5, 3.6): P holds the previous primitives (initial guess)
+ * on entry and the recovered ones on exit; cells set to the atmosphere have U's D~, S~, tau~ reset in place.
+ * `flags` (device, one signed char per array entry, may be NULL): 0 Noble, 1 Palenzuela, 2 atmosphere by the
+ * density test, -1 both solvers failed.  `stats` (device, may be NULL) is accumulated.  U's ghosts must be
+ * filled (A is differentiated across the block). */
+asterx_status asterx_con2prim(const asterx_params *p, const asterx_block *blk, asterx_state *U,
+                              asterx_prims *P, signed char *flags, asterx_c2p_stats *stats, void *ws,
+                              size_t ws_bytes, asterx_stream stream);
+
+/* Ghost fill of the 9 state fields (periodic wrap, or copy of the nearest owned value with linear
+ * extrapolation of A along the normal), in place. */
+asterx_status asterx_fill_ghosts(const asterx_params *p, const asterx_block *blk, asterx_state *U, void *ws,
+                                 size_t ws_bytes, asterx_stream stream);
+
+/* Right-hand side dU/dt of the 9 state fields (Sec. 3.9 workflow, Sec. 3.4): U and P must have their ghosts
+ * filled (P after recovery).  Writes dUdt at the interior cells, at the edges/vertices of the owned range
+ * (indices g..g+n along vertex-like axes, g..g+n-1 along cell-like axes), and nowhere else.  `dt` only sets
+ * the Lorenz damping when xi_lorenz == 0. */
+asterx_status asterx_rhs(const asterx_params *p, const asterx_block *blk, const asterx_state *U,
+                         const asterx_prims *P, asterx_state *dUdt, double dt, void *ws, size_t ws_bytes,
+                         asterx_stream stream);
+
+/* One classical RK4 stage (stage = 0..3): ghost fill U_s, recovery on the interior (resetting U_s for
+ * atmosphere cells), ghost fill of P, RHS k_s, then U_next = U_n + c dt k_s (c = 1/2, 1/2, 1) and U_acc += b dt
+ * k_s (b = 1/6, 1/3, 1/3; stage 0 initialises U_acc); stage 3 writes U_next = U_n + U_acc + dt/6 k_3.  Us may
+ * alias Un (stage 0).  Unext and Uacc are written on the owned ranges only. */
+asterx_status asterx_rk_stage(const asterx_params *p, const asterx_block *blk, int stage, double dt,
+                              const asterx_state *Un, asterx_state *Us, asterx_state *Unext, asterx_state *Uacc,
+                              asterx_prims *P, signed char *flags, asterx_c2p_stats *stats, void *ws,
+                              size_t ws_bytes, asterx_stream stream);
+
+/* One full RK4 step in place: U <- U_{n+1}, using stage buffers inside the workspace.  P is updated to the
+ * primitives recovered in the last stage.  `flags` and `stats` as in asterx_con2prim (accumulated over the
+ * four stages). */
+asterx_status asterx_rk4_step(const asterx_params *p, const asterx_block *blk, double dt, asterx_state *U,
+                              asterx_prims *P, signed char *flags, asterx_c2p_stats *stats, void *ws,
+                              size_t ws_bytes, asterx_stream stream);
+
+/* HOST-buffer variant of asterx_rk4_step for callers without device memory management: copies U and P from
+ * host (pinned for asynchrony) to the device buffers dU/dP, runs the step and copies U and P back.  The
+ * device buffers have the same layout; `h_*` are HOST pointers.  Synchronous on `stream` at return. */
+asterx_status asterx_rk4_step_host(const asterx_params *p, const asterx_block *blk, double dt,
+                                   double *const *h_U9, double *const *h_P5, asterx_state *dU, asterx_prims *dP,
+                                   asterx_c2p_stats *stats, void *ws, size_t ws_bytes, asterx_stream stream);
+
+/* ---- measurement helpers (not part of the method) ---- */
+
+/* Start recording a CUDA event pair around each launch of the face kernel (the dominant kernel: Sec. 3.3
+ * face solve) on the stream it is launched on, for at most max_launches launches; resets earlier records.
+ * Host-side event creation only (no device memory). */
+asterx_status asterx_profile_enable(int max_launches);
+/* Number of recorded face-kernel launches and their summed device time in ms (waits for the last event). */
+asterx_status asterx_profile_read(int *launches, double *total_ms);
+/* Stop recording and release the events. */
+void asterx_profile_disable(void);
+
+/* FP64 throughput probe: `blocks` x `threads` threads each run `iters` iterations of 8 independent dependent
+ * chains of fused multiply-adds (16 flops per chain step); writes one double per thread to `out` (device,
+ * blocks*threads doubles) so the work cannot be elided. */
+asterx_status asterx_dfma_probe(double *out, int blocks, int threads, long iters, asterx_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASTERX_H */

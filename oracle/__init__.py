@@ -81,6 +81,9 @@ def lib():
                                        ctypes.c_void_p, ctypes.c_void_p]
         L.oracle_batch_prim2con.argtypes = [ctypes.POINTER(OParams), ctypes.c_long, _P, _P, _P, _P]
         L.oracle_point_recon.argtypes = [ctypes.c_int, _P, _P, _P]
+        L.oracle_face_flops.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, ctypes.c_int,
+                                        ctypes.c_int, _P]
+        L.oracle_recon_flops.argtypes = [ctypes.c_int, _P, _P]
         L.oracle_point_sources.argtypes = [ctypes.POINTER(OParams), _P, _P, _P, _P, _P, _P, _P]
         L.oracle_grid_sources.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP]
     return _lib
@@ -274,3 +277,17 @@ def grid_sources(w, M, U, P, params=None):
     lib().oracle_grid_sources(ctypes.byref(pp), ctypes.byref(block_struct(w)), _ptrs(M), _ptrs(U), _ptrs(P),
                               _ptrs(src))
     return src
+
+
+def face_flops(w, M, U, P, d, stride=1, params=None):
+    """Flop counts of the face solve along d: dict(faces, add, mul, div, sqrt, speed_iters)."""
+    out = np.zeros(6)
+    lib().oracle_face_flops(ctypes.byref(params_struct(params or w.params)), ctypes.byref(block_struct(w)),
+                            _ptrs(M), _ptrs(U), _ptrs(P), int(d), int(stride), _p(out))
+    return dict(zip(("faces", "add", "mul", "div", "sqrt", "speed_iters"), out.tolist()))
+
+
+def recon_flops(scheme, a5):
+    out = np.zeros(4)
+    lib().oracle_recon_flops(int(scheme), _p(np.ascontiguousarray(a5, float)), _p(out))
+    return dict(zip(("add", "mul", "div", "sqrt"), out.tolist()))

@@ -18,6 +18,7 @@
 //  * Ideal-gas eps recovery of Eq. Noble2D epsilon uses the adiabatic index Gamma (printed "1/gamma").
 //  * Palenzuela eps-hat uses t^2/x^2 (the derivation from Eq. Noble2D energy; printed "t^2/x").
 //  * Palenzuela lower bracket raised to max(1 + q - s, 1) because x = hW >= 1.
+//  * The atmosphere criterion is the one of Sec. 3.6 only: D~ < sqrt(gamma) rho_atm, tested before recovery.
 //  * Wave speeds: extreme roots of the magnetosonic quartic, multiplied through by c_s^2, found by Newton
 //    from the light-cone speeds; G = gamma^dd - (lambda + beta^d)^2 / alpha^2.
 //  * Reconstructed variables: rho, p, W v^i and the transverse cell-centre B (undensitised).
@@ -782,11 +783,6 @@ static C2POut c2p_cell(const Metric3<double>& m, const C2PIn& in, const OParams&
   if (!ok) {
     atmosphere(P, &out);
     out.flag = -1;
-    return out;
-  }
-  if (out.rho < P.rho_atm) {
-    atmosphere(P, &out);
-    out.flag = 2;
   }
   return out;
 }
@@ -810,7 +806,7 @@ static void fill_axis(const Grid& G, double* f, int axis, int cell_like, bool li
         p[a2] = q2;
         double v;
         if (G.bc[axis] == BC_PERIODIC) {
-          int src = (i < lo) ? i + n : i - n;
+          int src = lo + (((i - lo) % n) + n) % n;  // periodic image inside the owned range
           int q[3] = {p[0], p[1], p[2]};
           q[axis] = src;
           v = f[G.at(q)];
@@ -1367,6 +1363,104 @@ void oracle_rk_stage(const OParams* p, const OBlock* b, const double* const* met
                      double* const* prim, signed char* flags, OStats* stats) {
   Grid G(*b);
   rk_stage(G, vmetric(metric), *p, stage, dt, Un, Us, Unext, Uacc, prim, flags, stats);
+}
+
+// Algorithmic flop count of the face solve (Sec. 3.3: prim->cons, fluxes, magnetosonic speeds, HLLE and the
+// upwind velocities of Eq. uct1) along direction d, over every `stride`-th face of the face domain
+// (faces g..g+n along d, all transverse indices), with the flop-counting scalar.  Interpolation of the frozen
+// metric is not counted (the face metric is an input of the face solve).  out: faces, add, mul, div, sqrt,
+// speed iterations.  U and prim must hold ghost-filled state and recovered, ghost-filled primitives.
+void oracle_face_flops(const OParams* p, const OBlock* b, const double* const* metric, double* const* U,
+                       double* const* prim, int d, int stride, double* out) {
+  Grid G(*b);
+  VertexMetric vm = vmetric(metric);
+  Field Bf[3], Bc[3];
+  face_B(G, U[5], U[6], U[7], Bf);
+  centre_B(G, vm, Bf, Bc);
+  Field cellvar[8];
+  for (int v = 0; v < 8; v++) cellvar[v].assign(G.size(), 0.0);
+  for (int k = 0; k < G.N[2]; k++)
+    for (int j = 0; j < G.N[1]; j++)
+      for (int i = 0; i < G.N[0]; i++) {
+        const long c = G.at(i, j, k);
+        const Metric3<double> m = metric_at_centre(G, vm, i, j, k);
+        double v2 = 0.0;
+        for (int a = 0; a < 3; a++)
+          for (int q = 0; q < 3; q++) v2 += m.g[a][q] * prim[2 + a][c] * prim[2 + q][c];
+        const double W = 1.0 / std::sqrt(1.0 - v2);
+        cellvar[0][c] = prim[0][c];
+        cellvar[1][c] = prim[1][c];
+        for (int a = 0; a < 3; a++) cellvar[2 + a][c] = W * prim[2 + a][c];
+        for (int a = 0; a < 3; a++) cellvar[5 + a][c] = Bc[a][c];
+      }
+  const int a1 = (d + 1) % 3, a2 = (d + 2) % 3;
+  double faces = 0, iters = 0;
+  Flops before = g_flops;
+  long counter = 0;
+  for (int q2 = 0; q2 < G.N[a2]; q2++)
+    for (int q1 = 0; q1 < G.N[a1]; q1++)
+      for (int f = G.g; f <= G.g + G.n[d]; f++) {
+        if ((counter++ % stride) != 0) continue;
+        int pp[3];
+        pp[d] = f;
+        pp[a1] = q1;
+        pp[a2] = q2;
+        FaceInput in;
+        for (int sd = 0; sd < 2; sd++) {
+          const int cell = f - 1 + sd;
+          double rec[8];
+          for (int v = 0; v < 8; v++) {
+            double st5[5];
+            for (int t = 0; t < 5; t++) {
+              int q[3] = {pp[0], pp[1], pp[2]};
+              q[d] = cell - 2 + t;
+              st5[t] = cellvar[v][G.at(q)];
+            }
+            double aL, aR;
+            recon_cell<double>(p->recon, st5, &aL, &aR);
+            rec[v] = (sd == 0) ? aR : aL;
+          }
+          in.rho[sd] = rec[0];
+          in.press[sd] = rec[1];
+          for (int a = 0; a < 3; a++) in.u[sd][a] = rec[2 + a];
+          for (int a = 0; a < 3; a++) in.Bt[sd][a] = rec[5 + a];
+        }
+        in.Bn = Bf[d][G.at(pp)];
+        const Metric3<double> md = metric_at_face(G, vm, d, pp[0], pp[1], pp[2]);
+        Metric3<Fc> mf;
+        mf.alp = Fc(md.alp);
+        mf.sqrtg = Fc(md.sqrtg);
+        for (int a = 0; a < 3; a++) {
+          mf.beta[a] = Fc(md.beta[a]);
+          for (int q = 0; q < 3; q++) {
+            mf.g[a][q] = Fc(md.g[a][q]);
+            mf.gu[a][q] = Fc(md.gu[a][q]);
+            mf.K[a][q] = Fc(md.K[a][q]);
+          }
+        }
+        FaceOut<Fc> o = face_solve<Fc>(mf, in, p->gamma, d);
+        faces += 1;
+        iters += o.iters;
+      }
+  out[0] = faces;
+  out[1] = (double)(g_flops.add - before.add);
+  out[2] = (double)(g_flops.mul - before.mul);
+  out[3] = (double)(g_flops.div - before.div);
+  out[4] = (double)(g_flops.sqrt - before.sqrt);
+  out[5] = iters;
+}
+
+// Algorithmic flop count of the per-cell reconstruction of the 7 face variables (one cell, both faces).
+void oracle_recon_flops(int scheme, const double* a5, double* out) {
+  Flops before = g_flops;
+  Fc a[5];
+  for (int t = 0; t < 5; t++) a[t] = Fc(a5[t]);
+  Fc lo, hi;
+  recon_cell<Fc>(scheme, a, &lo, &hi);
+  out[0] = (double)(g_flops.add - before.add);
+  out[1] = (double)(g_flops.mul - before.mul);
+  out[2] = (double)(g_flops.div - before.div);
+  out[3] = (double)(g_flops.sqrt - before.sqrt);
 }
 
 // Pointwise helpers for the pins of the test suite.

@@ -1,0 +1,271 @@
+"""Python binding of the C ABI in include/asterx.h (argument marshalling only).
+
+Every step of the GRMHD stage runs in the CUDA library libasterx.so; this module only turns torch CUDA tensors
+into the pointer structs of the ABI and forwards the current CUDA stream.  There is no fallback: if the library
+is missing and cannot be built, importing raises.
+
+Tensors: the state is a float64 CUDA tensor of shape (9, Nz+1, Ny+1, Nx+1) (D~, S~x, S~y, S~z, tau~, A_x, A_y,
+A_z, Psi), the primitives (5, ...) (rho, p, v^x, v^y, v^z), the metric (16, ...) (alpha, beta^i, gamma_ij, K_ij);
+all contiguous.  Function names follow the ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+ASTERX_OK, ASTERX_EINVAL, ASTERX_ECUDA, ASTERX_ENOMEM, ASTERX_EC2P, ASTERX_ETIMEOUT = range(6)
+ABI_VERSION = 1
+
+
+class AsterxError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: status {status} ({_status_str(status)})")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("rho_atm", ctypes.c_double), ("K_atm", ctypes.c_double),
+                ("gamma_atm", ctypes.c_double), ("c2p_tol", ctypes.c_double), ("c2p_maxiter", ctypes.c_int),
+                ("brent_maxiter", ctypes.c_int), ("W_max", ctypes.c_double), ("recon", ctypes.c_int),
+                ("gauge", ctypes.c_int), ("xi_lorenz", ctypes.c_double), ("use_fallback", ctypes.c_int)]
+
+
+class Block(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("g", ctypes.c_int), ("x0", ctypes.c_double * 3),
+                ("dx", ctypes.c_double * 3), ("bc", ctypes.c_int * 3)]
+
+
+class State(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("D", "Sx", "Sy", "Sz", "tau", "Ax", "Ay", "Az", "Psi")]
+
+
+class Prims(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("rho", "press", "velx", "vely", "velz")]
+
+
+class Metric(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("alp", "betax", "betay", "betaz", "gxx", "gxy", "gxz", "gyy",
+                                                "gyz", "gzz", "kxx", "kxy", "kxz", "kyy", "kyz", "kzz")]
+
+
+class C2PStats(ctypes.Structure):
+    _fields_ = [("n_noble", ctypes.c_ulonglong), ("n_fallback", ctypes.c_ulonglong),
+                ("n_atm", ctypes.c_ulonglong), ("n_failed", ctypes.c_ulonglong), ("iters", ctypes.c_ulonglong)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libasterx.so (built in-tree on first use if absent)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        vp, sz, st = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p
+        P, B = ctypes.POINTER(Params), ctypes.POINTER(Block)
+        S, Pr, M = ctypes.POINTER(State), ctypes.POINTER(Prims), ctypes.POINTER(Metric)
+        L.asterx_abi_version.restype = ctypes.c_int
+        L.asterx_status_str.restype = ctypes.c_char_p
+        L.asterx_status_str.argtypes = [ctypes.c_int]
+        L.asterx_workspace_size.restype = ctypes.c_size_t
+        L.asterx_workspace_size.argtypes = [B]
+        L.asterx_prepare.argtypes = [P, B, M, vp, sz, st]
+        L.asterx_prim2con.argtypes = [P, B, S, Pr, vp, sz, st]
+        L.asterx_con2prim.argtypes = [P, B, S, Pr, vp, vp, vp, sz, st]
+        L.asterx_fill_ghosts.argtypes = [P, B, S, vp, sz, st]
+        L.asterx_rhs.argtypes = [P, B, S, Pr, S, ctypes.c_double, vp, sz, st]
+        L.asterx_rk_stage.argtypes = [P, B, ctypes.c_int, ctypes.c_double, S, S, S, S, Pr, vp, vp, vp, sz, st]
+        L.asterx_rk4_step.argtypes = [P, B, ctypes.c_double, S, Pr, vp, vp, vp, sz, st]
+        L.asterx_rk4_step_host.argtypes = [P, B, ctypes.c_double, ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(ctypes.c_void_p), S, Pr, vp, vp, sz, st]
+        L.asterx_profile_enable.argtypes = [ctypes.c_int]
+        L.asterx_profile_read.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        L.asterx_profile_disable.restype = None
+        L.asterx_dfma_probe.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_long, st]
+        for name in ("asterx_prepare", "asterx_prim2con", "asterx_con2prim", "asterx_fill_ghosts", "asterx_rhs",
+                     "asterx_rk_stage", "asterx_rk4_step", "asterx_rk4_step_host", "asterx_profile_enable",
+                     "asterx_profile_read", "asterx_dfma_probe"):
+            getattr(L, name).restype = ctypes.c_int
+        if L.asterx_abi_version() != ABI_VERSION:
+            raise ImportError(f"libasterx ABI {L.asterx_abi_version()} != binding ABI {ABI_VERSION}")
+        _lib = L
+    return _lib
+
+
+def _status_str(s: int) -> str:
+    try:
+        return lib().asterx_status_str(int(s)).decode()
+    except Exception:  # pragma: no cover - only used for messages
+        return "?"
+
+
+def _check(status: int, what: str):
+    if status != ASTERX_OK:
+        raise AsterxError(status, what)
+
+
+# -------------------------------------------------------------------------------------------------- structs
+
+
+def params_struct(p: dict) -> Params:
+    return Params(p["gamma"], p["rho_atm"], p["K_atm"], p["gamma_atm"], p["c2p_tol"], int(p["c2p_maxiter"]),
+                  int(p["brent_maxiter"]), p["W_max"], int(p["recon"]), int(p["gauge"]), p["xi_lorenz"],
+                  int(p["use_fallback"]))
+
+
+def block_struct(n, g, x0, dx, bc) -> Block:
+    b = Block()
+    for d in range(3):
+        b.n[d] = int(n[d])
+        b.x0[d] = float(x0[d])
+        b.dx[d] = float(dx[d])
+        b.bc[d] = int(bc[d])
+    b.g = int(g)
+    return b
+
+
+def _field_ptrs(t, count):
+    import torch
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(), "need a contiguous float64 CUDA tensor"
+    assert t.shape[0] == count
+    V = t[0].numel()
+    base = t.data_ptr()
+    return [base + 8 * V * v for v in range(count)]
+
+
+def state_struct(U) -> State:
+    return State(*_field_ptrs(U, 9))
+
+
+def prims_struct(P) -> Prims:
+    return Prims(*_field_ptrs(P, 5))
+
+
+def metric_struct(M) -> Metric:
+    return Metric(*_field_ptrs(M, 16))
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def workspace_size(block: Block) -> int:
+    return int(lib().asterx_workspace_size(ctypes.byref(block)))
+
+
+class Solver:
+    """One block plus its workspace.  The workspace is a caller-owned torch allocation (256-byte aligned);
+    prepare() derives the frozen-metric geometry into it."""
+
+    def __init__(self, params: dict, n, g, x0, dx, bc, device="cuda"):
+        import torch
+        self.params = dict(params)
+        self.p = params_struct(self.params)
+        self.b = block_struct(n, g, x0, dx, bc)
+        self.n = tuple(int(v) for v in n)
+        self.g = int(g)
+        N = [self.n[d] + 2 * self.g for d in range(3)]
+        self.shape = (N[2] + 1, N[1] + 1, N[0] + 1)
+        self.ws_bytes = workspace_size(self.b)
+        if self.ws_bytes == 0:
+            raise AsterxError(ASTERX_EINVAL, "invalid block")
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.ws.data_ptr()) % 256
+        self.ws_ptr = ctypes.c_void_p(self.ws.data_ptr() + off)
+        self.stats = torch.zeros(5, dtype=torch.int64, device=device)
+
+    @classmethod
+    def for_workload(cls, w, device="cuda"):
+        return cls(w.params, w.n, w.g, w.x0, w.dx, w.bc, device)
+
+    def zeros_state(self):
+        import torch
+        return torch.zeros((9,) + self.shape, dtype=torch.float64, device=self.ws.device)
+
+    def zeros_prims(self):
+        import torch
+        return torch.zeros((5,) + self.shape, dtype=torch.float64, device=self.ws.device)
+
+    def _args(self):
+        return ctypes.byref(self.p), ctypes.byref(self.b)
+
+    def prepare(self, metric, stream=None):
+        self._metric = metric  # keep the vertex metric alive while the workspace refers to it
+        m = metric_struct(metric)
+        _check(lib().asterx_prepare(*self._args(), ctypes.byref(m), self.ws_ptr, self.ws_bytes, _stream(stream)),
+               "asterx_prepare")
+
+    def prim2con(self, U, P, stream=None):
+        u, p = state_struct(U), prims_struct(P)
+        _check(lib().asterx_prim2con(*self._args(), ctypes.byref(u), ctypes.byref(p), self.ws_ptr, self.ws_bytes,
+                                     _stream(stream)), "asterx_prim2con")
+
+    def fill_ghosts(self, U, stream=None):
+        u = state_struct(U)
+        _check(lib().asterx_fill_ghosts(*self._args(), ctypes.byref(u), self.ws_ptr, self.ws_bytes,
+                                        _stream(stream)), "asterx_fill_ghosts")
+
+    def con2prim(self, U, P, flags=None, stats=None, stream=None):
+        u, p = state_struct(U), prims_struct(P)
+        fl = ctypes.c_void_p(flags.data_ptr()) if flags is not None else None
+        sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
+        _check(lib().asterx_con2prim(*self._args(), ctypes.byref(u), ctypes.byref(p), fl, sp, self.ws_ptr,
+                                     self.ws_bytes, _stream(stream)), "asterx_con2prim")
+
+    def rhs(self, U, P, dU, dt, stream=None):
+        u, p, d = state_struct(U), prims_struct(P), state_struct(dU)
+        _check(lib().asterx_rhs(*self._args(), ctypes.byref(u), ctypes.byref(p), ctypes.byref(d), float(dt),
+                                self.ws_ptr, self.ws_bytes, _stream(stream)), "asterx_rhs")
+
+    def rk_stage(self, stage, dt, Un, Us, Unext, Uacc, P, flags=None, stats=None, stream=None):
+        a = [state_struct(x) for x in (Un, Us, Unext, Uacc)]
+        p = prims_struct(P)
+        fl = ctypes.c_void_p(flags.data_ptr()) if flags is not None else None
+        sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
+        _check(lib().asterx_rk_stage(*self._args(), int(stage), float(dt), *[ctypes.byref(x) for x in a],
+                                     ctypes.byref(p), fl, sp, self.ws_ptr, self.ws_bytes, _stream(stream)),
+               "asterx_rk_stage")
+
+    def rk4_step(self, U, P, dt, flags=None, stats=None, stream=None):
+        u, p = state_struct(U), prims_struct(P)
+        fl = ctypes.c_void_p(flags.data_ptr()) if flags is not None else None
+        sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
+        _check(lib().asterx_rk4_step(*self._args(), float(dt), ctypes.byref(u), ctypes.byref(p), fl, sp,
+                                     self.ws_ptr, self.ws_bytes, _stream(stream)), "asterx_rk4_step")
+
+    def rk4_step_host(self, hU, hP, dU, dP, dt, stats=None, stream=None):
+        """hU (9, ...) and hP (5, ...) are pinned host tensors; dU, dP device tensors of the same shapes."""
+        hu = (ctypes.c_void_p * 9)(*[hU[v].data_ptr() for v in range(9)])
+        hp = (ctypes.c_void_p * 5)(*[hP[v].data_ptr() for v in range(5)])
+        u, p = state_struct(dU), prims_struct(dP)
+        sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
+        _check(lib().asterx_rk4_step_host(*self._args(), float(dt), hu, hp, ctypes.byref(u), ctypes.byref(p), sp,
+                                          self.ws_ptr, self.ws_bytes, _stream(stream)), "asterx_rk4_step_host")
+
+
+# ---------------------------------------------------------------------------------------- measurement helpers
+
+
+def profile_enable(max_launches: int):
+    _check(lib().asterx_profile_enable(int(max_launches)), "asterx_profile_enable")
+
+
+def profile_read():
+    n = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().asterx_profile_read(ctypes.byref(n), ctypes.byref(ms)), "asterx_profile_read")
+    return n.value, ms.value
+
+
+def profile_disable():
+    lib().asterx_profile_disable()
+
+
+def dfma_probe(out, blocks, threads, iters, stream=None):
+    _check(lib().asterx_dfma_probe(ctypes.c_void_p(out.data_ptr()), int(blocks), int(threads), int(iters),
+                                   _stream(stream)), "asterx_dfma_probe")

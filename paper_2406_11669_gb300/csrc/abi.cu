@@ -1,0 +1,340 @@
+// Host runtime of the C ABI declared in include/asterx.h: argument validation (before any launch), workspace
+// layout, and the order of launches of one RK stage (Sec. 3.9 workflow of arXiv:2406.11669).
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "../../include/asterx.h"
+#include "kernels.h"
+
+using namespace asterx;
+
+namespace {
+
+constexpr int kAbiVersion = 1;
+constexpr size_t kAlign = 256;
+
+long padded_V(const asterx_block* b) {
+  long V = 1;
+  for (int d = 0; d < 3; d++) V *= (long)(b->n[d] + 2 * b->g + 1);
+  return V;
+}
+
+// each field starts on a 256-byte boundary
+long field_stride(long V) { return (V + 31) / 32 * 32; }
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+bool block_ok(const asterx_block* b) {
+  if (!b) return false;
+  if (b->g != 3) return false;
+  for (int d = 0; d < 3; d++) {
+    if (b->n[d] < 1 || b->n[d] > (1 << 20)) return false;
+    if (!finite_pos(b->dx[d]) || !std::isfinite(b->x0[d])) return false;
+    if (b->bc[d] != ASTERX_BC_PERIODIC && b->bc[d] != ASTERX_BC_COPY) return false;
+  }
+  const double V = (double)(b->n[0] + 7) * (b->n[1] + 7) * (b->n[2] + 7);
+  return V < 4.0e9;
+}
+
+bool params_ok(const asterx_params* p) {
+  if (!p) return false;
+  if (!(std::isfinite(p->gamma) && p->gamma > 1.0)) return false;
+  if (!finite_pos(p->rho_atm) || !(std::isfinite(p->K_atm) && p->K_atm >= 0.0)) return false;
+  if (!(std::isfinite(p->gamma_atm) && p->gamma_atm > 1.0)) return false;
+  if (!finite_pos(p->c2p_tol) || p->c2p_maxiter < 1 || p->brent_maxiter < 1) return false;
+  if (!(std::isfinite(p->W_max) && p->W_max > 1.0)) return false;
+  if (p->recon < ASTERX_RECON_MINMOD || p->recon > ASTERX_RECON_WENOZ) return false;
+  if (p->gauge != ASTERX_GAUGE_LORENZ && p->gauge != ASTERX_GAUGE_ALGEBRAIC) return false;
+  if (!(std::isfinite(p->xi_lorenz) && p->xi_lorenz >= 0.0)) return false;
+  return p->use_fallback == 0 || p->use_fallback == 1;
+}
+
+bool ptr_ok(const void* q) { return q && ((uintptr_t)q % 8 == 0); }
+
+template <class S, int N>
+bool set_ok(const S* s) {
+  if (!s) return false;
+  const double* const* f = reinterpret_cast<const double* const*>(s);
+  for (int i = 0; i < N; i++)
+    if (!ptr_ok(f[i])) return false;
+  return true;
+}
+
+size_t ws_bytes_for(const asterx_block* b) {
+  const long fs = field_stride(padded_V(b));
+  return (size_t)WS_FIELDS * fs * sizeof(double) + 8 * sizeof(unsigned long long) + kAlign;
+}
+
+Blk make_blk(const asterx_block* in) {
+  Blk b;
+  b.g = in->g;
+  for (int d = 0; d < 3; d++) {
+    b.n[d] = in->n[d];
+    b.N[d] = in->n[d] + 2 * in->g;
+    b.bc[d] = in->bc[d];
+    b.dx[d] = in->dx[d];
+    b.idx[d] = 1.0 / in->dx[d];
+  }
+  b.sy = b.N[0] + 1;
+  b.sz = (long)(b.N[0] + 1) * (b.N[1] + 1);
+  b.V = (long)(b.N[0] + 1) * (b.N[1] + 1) * (b.N[2] + 1);
+  return b;
+}
+
+Ws make_ws(const asterx_block* in, void* base) {
+  const long fs = field_stride(padded_V(in));
+  double* p = reinterpret_cast<double*>(base);
+  Ws w;
+  auto take = [&](int nf) {
+    double* q = p;
+    p += (long)nf * fs;
+    return q;
+  };
+  // a group of nf fields starts on a 256-byte boundary and holds its fields at pitch V (kernels index
+  // group + f * V); nf * fs >= nf * V leaves the padding at the group's end
+  w.cg = take(NCG);
+  w.fg = take(3 * NFG);
+  w.vg = take(NVG);
+  w.bf = take(3);
+  w.bc = take(3);
+  w.uvel = take(3);
+  w.rec = take(2 * NREC);
+  w.face = take(3 * NFD);
+  w.ga = take(1);
+  w.fpsi = take(3);
+  w.uacc = take(9);
+  w.ustage = take(18);
+  w.counters = reinterpret_cast<unsigned long long*>(p);
+  return w;
+}
+
+StageArgs make_args(const asterx_params* p, const asterx_block* blk, void* ws) {
+  StageArgs a;
+  a.b = make_blk(blk);
+  a.w = make_ws(blk, ws);
+  a.recon = p->recon;
+  a.gauge = p->gauge;
+  a.gamma = p->gamma;
+  a.rho_atm = p->rho_atm;
+  a.K_atm = p->K_atm;
+  a.gamma_atm = p->gamma_atm;
+  a.c2p_tol = p->c2p_tol;
+  a.W_max = p->W_max;
+  a.xi = p->xi_lorenz;
+  a.c2p_maxiter = p->c2p_maxiter;
+  a.brent_maxiter = p->brent_maxiter;
+  a.use_fallback = p->use_fallback;
+  return a;
+}
+
+F9 f9(const asterx_state* s) {
+  F9 f;
+  std::memcpy(f.f, s, sizeof(f.f));
+  return f;
+}
+F5 f5(const asterx_prims* s) {
+  F5 f;
+  std::memcpy(f.f, s, sizeof(f.f));
+  return f;
+}
+
+asterx_status common_checks(const asterx_params* p, const asterx_block* blk, void* ws, size_t ws_bytes) {
+  if (!params_ok(p) || !block_ok(blk)) return ASTERX_EINVAL;
+  if (!ws || ((uintptr_t)ws % kAlign) != 0) return ASTERX_EINVAL;
+  if (ws_bytes < ws_bytes_for(blk)) return ASTERX_ENOMEM;
+  return ASTERX_OK;
+}
+
+asterx_status cuda_status(cudaError_t e) { return e == cudaSuccess ? ASTERX_OK : ASTERX_ECUDA; }
+
+}  // namespace
+
+extern "C" {
+
+int asterx_abi_version(void) { return kAbiVersion; }
+
+const char* asterx_status_str(asterx_status s) {
+  switch (s) {
+    case ASTERX_OK: return "ok";
+    case ASTERX_EINVAL: return "invalid argument";
+    case ASTERX_ECUDA: return "CUDA error";
+    case ASTERX_ENOMEM: return "workspace too small";
+    case ASTERX_EC2P: return "primitive recovery failed";
+    case ASTERX_ETIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+size_t asterx_workspace_size(const asterx_block* blk) {
+  if (!block_ok(blk)) return 0;
+  return ws_bytes_for(blk);
+}
+
+asterx_status asterx_prepare(const asterx_params* p, const asterx_block* blk, const asterx_metric* metric,
+                             void* ws, size_t ws_bytes, asterx_stream stream) {
+  asterx_status st = common_checks(p, blk, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!set_ok<asterx_metric, 16>(metric)) return ASTERX_EINVAL;
+  StageArgs a = make_args(p, blk, ws);
+  CF16 m;
+  std::memcpy(m.f, metric, sizeof(m.f));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(a.w.counters, 0, 8 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return ASTERX_ECUDA;
+  return cuda_status(launch_prepare(a.b, m, a.w, s));
+}
+
+asterx_status asterx_prim2con(const asterx_params* p, const asterx_block* blk, asterx_state* U,
+                              const asterx_prims* P, void* ws, size_t ws_bytes, asterx_stream stream) {
+  asterx_status st = common_checks(p, blk, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!set_ok<asterx_state, 9>(U) || !set_ok<asterx_prims, 5>(P)) return ASTERX_EINVAL;
+  StageArgs a = make_args(p, blk, ws);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  F9 u = f9(U);
+  cudaError_t e = launch_bfield(a.b, a.w, u, s);
+  if (e == cudaSuccess) e = launch_prim2con(a, u, f5(P), s);
+  return cuda_status(e);
+}
+
+asterx_status asterx_fill_ghosts(const asterx_params* p, const asterx_block* blk, asterx_state* U, void* ws,
+                                 size_t ws_bytes, asterx_stream stream) {
+  asterx_status st = common_checks(p, blk, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!set_ok<asterx_state, 9>(U)) return ASTERX_EINVAL;
+  StageArgs a = make_args(p, blk, ws);
+  return cuda_status(launch_ghost_state(a.b, f9(U), reinterpret_cast<cudaStream_t>(stream)));
+}
+
+asterx_status asterx_con2prim(const asterx_params* p, const asterx_block* blk, asterx_state* U,
+                              asterx_prims* P, signed char* flags, asterx_c2p_stats* stats, void* ws,
+                              size_t ws_bytes, asterx_stream stream) {
+  asterx_status st = common_checks(p, blk, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!set_ok<asterx_state, 9>(U) || !set_ok<asterx_prims, 5>(P)) return ASTERX_EINVAL;
+  if (stats && ((uintptr_t)stats % 8) != 0) return ASTERX_EINVAL;
+  StageArgs a = make_args(p, blk, ws);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  F9 u = f9(U);
+  cudaError_t e = launch_bfield(a.b, a.w, u, s);
+  if (e == cudaSuccess)
+    e = launch_c2p(a, u, f5(P), flags, reinterpret_cast<unsigned long long*>(stats), s);
+  return cuda_status(e);
+}
+
+asterx_status asterx_rhs(const asterx_params* p, const asterx_block* blk, const asterx_state* U,
+                         const asterx_prims* P, asterx_state* dUdt, double dt, void* ws, size_t ws_bytes,
+                         asterx_stream stream) {
+  asterx_status st = common_checks(p, blk, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!set_ok<asterx_state, 9>(U) || !set_ok<asterx_prims, 5>(P) || !set_ok<asterx_state, 9>(dUdt))
+    return ASTERX_EINVAL;
+  if (!finite_pos(dt)) return ASTERX_EINVAL;
+  StageArgs a = make_args(p, blk, ws);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  F9 u = f9(U), d = f9(dUdt);
+  cudaError_t e = launch_bfield(a.b, a.w, u, s);
+  if (e == cudaSuccess) e = launch_rhs(a, u, f5(P), -1, dt, u, u, u, d, s);
+  return cuda_status(e);
+}
+
+static asterx_status stage_impl(const StageArgs& a, int stage, double dt, const F9& un, const F9& us,
+                                const F9& unext, const F9& uacc, const F5& pr, signed char* flags,
+                                unsigned long long* stats, cudaStream_t s) {
+  cudaError_t e = launch_ghost_state(a.b, us, s);
+  if (e == cudaSuccess) e = launch_bfield(a.b, a.w, us, s);
+  if (e == cudaSuccess) e = launch_c2p(a, us, pr, flags, stats, s);
+  if (e == cudaSuccess) e = launch_ghost_prims(a.b, pr, s);
+  if (e == cudaSuccess) e = launch_rhs(a, us, pr, stage, dt, un, unext, uacc, unext, s);
+  return cuda_status(e);
+}
+
+asterx_status asterx_rk_stage(const asterx_params* p, const asterx_block* blk, int stage, double dt,
+                              const asterx_state* Un, asterx_state* Us, asterx_state* Unext, asterx_state* Uacc,
+                              asterx_prims* P, signed char* flags, asterx_c2p_stats* stats, void* ws,
+                              size_t ws_bytes, asterx_stream stream) {
+  asterx_status st = common_checks(p, blk, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (stage < 0 || stage > 3 || !finite_pos(dt)) return ASTERX_EINVAL;
+  if (!set_ok<asterx_state, 9>(Un) || !set_ok<asterx_state, 9>(Us) || !set_ok<asterx_state, 9>(Unext) ||
+      !set_ok<asterx_state, 9>(Uacc) || !set_ok<asterx_prims, 5>(P))
+    return ASTERX_EINVAL;
+  if (stats && ((uintptr_t)stats % 8) != 0) return ASTERX_EINVAL;
+  StageArgs a = make_args(p, blk, ws);
+  return stage_impl(a, stage, dt, f9(Un), f9(Us), f9(Unext), f9(Uacc), f5(P), flags,
+                    reinterpret_cast<unsigned long long*>(stats), reinterpret_cast<cudaStream_t>(stream));
+}
+
+asterx_status asterx_rk4_step(const asterx_params* p, const asterx_block* blk, double dt, asterx_state* U,
+                              asterx_prims* P, signed char* flags, asterx_c2p_stats* stats, void* ws,
+                              size_t ws_bytes, asterx_stream stream) {
+  asterx_status st = common_checks(p, blk, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!finite_pos(dt) || !set_ok<asterx_state, 9>(U) || !set_ok<asterx_prims, 5>(P)) return ASTERX_EINVAL;
+  if (stats && ((uintptr_t)stats % 8) != 0) return ASTERX_EINVAL;
+  StageArgs a = make_args(p, blk, ws);
+  const long V = a.b.V;
+  F9 un = f9(U), acc, sb[2];
+  for (int v = 0; v < 9; v++) {
+    acc.f[v] = a.w.uacc + v * V;
+    sb[0].f[v] = a.w.ustage + v * V;
+    sb[1].f[v] = a.w.ustage + (9 + v) * V;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(stats);
+  for (int stage = 0; stage < 4; stage++) {
+    const F9& us = stage == 0 ? un : sb[(stage - 1) % 2];
+    const F9& unext = stage == 3 ? un : sb[stage % 2];
+    st = stage_impl(a, stage, dt, un, us, unext, acc, f5(P), flags, cnt, s);
+    if (st != ASTERX_OK) return st;
+  }
+  return ASTERX_OK;
+}
+
+asterx_status asterx_rk4_step_host(const asterx_params* p, const asterx_block* blk, double dt,
+                                   double* const* h_U9, double* const* h_P5, asterx_state* dU, asterx_prims* dP,
+                                   asterx_c2p_stats* stats, void* ws, size_t ws_bytes, asterx_stream stream) {
+  asterx_status st = common_checks(p, blk, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!h_U9 || !h_P5 || !set_ok<asterx_state, 9>(dU) || !set_ok<asterx_prims, 5>(dP)) return ASTERX_EINVAL;
+  for (int v = 0; v < 9; v++)
+    if (!h_U9[v]) return ASTERX_EINVAL;
+  for (int v = 0; v < 5; v++)
+    if (!h_P5[v]) return ASTERX_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)padded_V(blk) * sizeof(double);
+  F9 u = f9(dU);
+  F5 pr = f5(dP);
+  for (int v = 0; v < 9; v++)
+    if (cudaMemcpyAsync(u.f[v], h_U9[v], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return ASTERX_ECUDA;
+  for (int v = 0; v < 5; v++)
+    if (cudaMemcpyAsync(pr.f[v], h_P5[v], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return ASTERX_ECUDA;
+  st = asterx_rk4_step(p, blk, dt, dU, dP, nullptr, stats, ws, ws_bytes, stream);
+  if (st != ASTERX_OK) return st;
+  for (int v = 0; v < 9; v++)
+    if (cudaMemcpyAsync(h_U9[v], u.f[v], bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return ASTERX_ECUDA;
+  for (int v = 0; v < 5; v++)
+    if (cudaMemcpyAsync(h_P5[v], pr.f[v], bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return ASTERX_ECUDA;
+  return cuda_status(cudaStreamSynchronize(s));
+}
+
+asterx_status asterx_profile_enable(int max_launches) {
+  if (max_launches < 1 || max_launches > (1 << 20)) return ASTERX_EINVAL;
+  return cuda_status(profile_enable(max_launches));
+}
+
+asterx_status asterx_profile_read(int* launches, double* total_ms) {
+  if (!launches || !total_ms) return ASTERX_EINVAL;
+  return cuda_status(profile_read(launches, total_ms));
+}
+
+void asterx_profile_disable(void) { profile_disable(); }
+
+asterx_status asterx_dfma_probe(double* out, int blocks, int threads, long iters, asterx_stream stream) {
+  if (!ptr_ok(out) || blocks < 1 || threads < 32 || threads > 1024 || (threads % 32) != 0 || iters < 1)
+    return ASTERX_EINVAL;
+  return cuda_status(launch_dfma_probe(out, blocks, threads, iters, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

@@ -1,0 +1,208 @@
+// Frozen-metric geometry (run once per workspace by asterx_prepare).
+//
+// Sec. 3.2 of the paper: the metric lives at vertices and is interpolated to cell centres and faces with
+// 4th-order Lagrange polynomials.  Because the metric of this path is frozen, the interpolated values, the
+// inverse metric, sqrt(gamma) and the 4th-order centre derivatives used by the source terms are computed once
+// here and read by every stage.  Near the end of the padded array the 4-point stencil is shifted inward so
+// that it stays 4th order; centre derivatives use (f_{-3/2} - 27 f_{-1/2} + 27 f_{1/2} - f_{3/2}) / (24 h).
+//
+// All sums here use rounded multiply and add without contraction, in a fixed order (x innermost, then y, then
+// z), so the records are exactly reproducible by any implementation that sums in that order: the recovery's
+// atmosphere test D~ < sqrt(gamma) rho_atm then decides identically given identical inputs.  These kernels run
+// once per workspace, so the cost of the unfused operations does not matter.
+#include "kernels.h"
+#include "physics.cuh"
+
+namespace asterx {
+
+// weights of the 4-point Lagrange interpolation to the midpoint p+1/2 from nodes s..s+3, s shifted inward
+__device__ __forceinline__ int lagrange_mid(int p, int Nv, double w[4]) {
+  int s = p - 1;
+  s = s < 0 ? 0 : s;
+  s = s > Nv - 3 ? Nv - 3 : s;
+  const int t = p - s;  // 0, 1 or 2: target at node t + 1/2
+  if (t == 1) {
+    w[0] = -1.0 / 16.0; w[1] = 9.0 / 16.0; w[2] = 9.0 / 16.0; w[3] = -1.0 / 16.0;
+  } else if (t == 0) {
+    w[0] = 5.0 / 16.0; w[1] = 15.0 / 16.0; w[2] = -5.0 / 16.0; w[3] = 1.0 / 16.0;
+  } else {
+    w[0] = 1.0 / 16.0; w[1] = -5.0 / 16.0; w[2] = 15.0 / 16.0; w[3] = 5.0 / 16.0;
+  }
+  return s;
+}
+
+__device__ __forceinline__ double madd(double acc, double w, double v) { return __dadd_rn(acc, __dmul_rn(w, v)); }
+__device__ __forceinline__ double dmsub(double a, double b, double c, double d) {
+  return __dsub_rn(__dmul_rn(a, b), __dmul_rn(c, d));
+}
+
+// inverse (cofactor / determinant) and sqrt(det) of the symmetric metric, exactly rounded step by step
+__device__ void metric_inverse_exact(const double g[6], double gu[6], double* sqg) {
+  const double c00 = dmsub(g[3], g[5], g[4], g[4]);
+  const double c01 = dmsub(g[4], g[2], g[1], g[5]);
+  const double c02 = dmsub(g[1], g[4], g[3], g[2]);
+  const double det = __dadd_rn(__dadd_rn(__dmul_rn(g[0], c00), __dmul_rn(g[1], c01)), __dmul_rn(g[2], c02));
+  const double c11 = dmsub(g[0], g[5], g[2], g[2]);
+  const double c12 = dmsub(g[1], g[2], g[0], g[4]);
+  const double c22 = dmsub(g[0], g[3], g[1], g[1]);
+  gu[0] = __ddiv_rn(c00, det);
+  gu[1] = __ddiv_rn(c01, det);
+  gu[2] = __ddiv_rn(c02, det);
+  gu[3] = __ddiv_rn(c11, det);
+  gu[4] = __ddiv_rn(c12, det);
+  gu[5] = __ddiv_rn(c22, det);
+  *sqg = __dsqrt_rn(det);
+}
+
+// Centre record for every cell of the padded block.  One thread per cell; the 4x4x4 vertex values of each
+// field are contracted along x, then y, then z.
+__global__ void k_geom_centre(Blk b, CF16 m, double* __restrict__ cg) {
+  const long ncell = (long)b.N[0] * b.N[1] * b.N[2];
+  const double der4[4] = {1.0 / 24.0, -27.0 / 24.0, 27.0 / 24.0, -1.0 / 24.0};
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < ncell; t += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % b.N[0]);
+    const int j = (int)((t / b.N[0]) % b.N[1]);
+    const int k = (int)(t / ((long)b.N[0] * b.N[1]));
+    double wx[4], wy[4], wz[4];
+    const int sx = lagrange_mid(i, b.N[0], wx);
+    const int sy = lagrange_mid(j, b.N[1], wy);
+    const int sz = lagrange_mid(k, b.N[2], wz);
+    const bool inner = i >= b.g && i < b.g + b.n[0] && j >= b.g && j < b.g + b.n[1] && k >= b.g && k < b.g + b.n[2];
+    double dw[3][4];
+    for (int d = 0; d < 3; d++)
+      for (int a = 0; a < 4; a++) dw[d][a] = __ddiv_rn(der4[a], b.dx[d]);
+    const long c = i + b.sy * j + b.sz * k;
+    const long base = sx + b.sy * sy + b.sz * sz;
+    double val[16];
+    for (int f = 0; f < 16; f++) {
+      const double* __restrict__ p = m.f[f] + base;
+      double acc = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
+#pragma unroll
+      for (int cz = 0; cz < 4; cz++) {
+        double sy_ = 0.0, sdx = 0.0, sdy = 0.0;
+#pragma unroll
+        for (int cy = 0; cy < 4; cy++) {
+          double sx_ = 0.0, dx_ = 0.0;
+#pragma unroll
+          for (int cx = 0; cx < 4; cx++) {
+            const double v = p[cx + b.sy * cy + b.sz * cz];
+            sx_ = madd(sx_, wx[cx], v);
+            dx_ = madd(dx_, dw[0][cx], v);
+          }
+          sy_ = madd(sy_, wy[cy], sx_);
+          sdx = madd(sdx, wy[cy], dx_);
+          sdy = madd(sdy, dw[1][cy], sx_);
+        }
+        acc = madd(acc, wz[cz], sy_);
+        ax = madd(ax, wz[cz], sdx);
+        ay = madd(ay, wz[cz], sdy);
+        az = madd(az, dw[2][cz], sy_);
+      }
+      val[f] = acc;
+      if (f < 10) {
+        // derivatives of alpha (f=0), beta^j (f=1..3), gamma_jk (f=4..9): only meaningful at interior cells
+        const double dd[3] = {inner ? ax : 0.0, inner ? ay : 0.0, inner ? az : 0.0};
+        for (int d = 0; d < 3; d++) {
+          long slot;
+          if (f == 0) slot = CG_DALP + d;
+          else if (f < 4) slot = CG_DBETA + d * 3 + (f - 1);
+          else slot = CG_DG + d * 6 + (f - 4);
+          cg[slot * b.V + c] = dd[d];
+        }
+      }
+    }
+    double gu[6], sqg;
+    metric_inverse_exact(val + 4, gu, &sqg);
+    cg[CG_ALP * b.V + c] = val[0];
+    for (int a = 0; a < 3; a++) cg[(CG_BETA + a) * b.V + c] = val[1 + a];
+    for (int a = 0; a < 6; a++) {
+      cg[(CG_G + a) * b.V + c] = val[4 + a];
+      cg[(CG_GU + a) * b.V + c] = gu[a];
+      cg[(CG_K + a) * b.V + c] = val[10 + a];
+    }
+    cg[CG_SQG * b.V + c] = sqg;
+  }
+}
+
+// Face record for the faces normal to D: index along D from 0..N_D, transverse 0..N-1.  The lower-index
+// transverse axis is contracted first.
+template <int D>
+__global__ void k_geom_face(Blk b, CF16 m, double* __restrict__ fg) {
+  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+  constexpr int A = (T1 < T2) ? T1 : T2;
+  constexpr int Bx = (T1 < T2) ? T2 : T1;
+  const long n0 = (D == 0) ? b.N[0] + 1 : b.N[0];
+  const long n1 = (D == 1) ? b.N[1] + 1 : b.N[1];
+  const long n2 = (D == 2) ? b.N[2] + 1 : b.N[2];
+  const long count = n0 * n1 * n2;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x) {
+    int p[3];
+    p[0] = (int)(t % n0);
+    p[1] = (int)((t / n0) % n1);
+    p[2] = (int)(t / (n0 * n1));
+    double wa[4], wb[4];
+    const int sa = lagrange_mid(p[A], b.N[A], wa);
+    const int sb = lagrange_mid(p[Bx], b.N[Bx], wb);
+    const long sta = (A == 0) ? 1 : (A == 1 ? b.sy : b.sz);
+    const long stb = (Bx == 0) ? 1 : (Bx == 1 ? b.sy : b.sz);
+    int q[3] = {p[0], p[1], p[2]};
+    q[A] = sa;
+    q[Bx] = sb;
+    const long base = q[0] + b.sy * q[1] + b.sz * q[2];
+    const long c = p[0] + b.sy * p[1] + b.sz * p[2];
+    double val[10];
+    for (int f = 0; f < 10; f++) {
+      const double* __restrict__ src = m.f[f] + base;
+      double acc = 0.0;
+#pragma unroll
+      for (int cb = 0; cb < 4; cb++) {
+        double s_ = 0.0;
+#pragma unroll
+        for (int ca = 0; ca < 4; ca++) s_ = madd(s_, wa[ca], src[ca * sta + cb * stb]);
+        acc = madd(acc, wb[cb], s_);
+      }
+      val[f] = acc;
+    }
+    double gu[6], sqg;
+    metric_inverse_exact(val + 4, gu, &sqg);
+    double* out = fg + (long)D * NFG * b.V;
+    out[FG_ALP * b.V + c] = val[0];
+    for (int a = 0; a < 3; a++) out[(FG_BETA + a) * b.V + c] = val[1 + a];
+    for (int a = 0; a < 6; a++) {
+      out[(FG_G + a) * b.V + c] = val[4 + a];
+      out[(FG_GU + a) * b.V + c] = gu[a];
+    }
+    out[FG_SQG * b.V + c] = sqg;
+  }
+}
+
+__global__ void k_geom_vertex(Blk b, CF16 m, double* __restrict__ vg) {
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < b.V; c += (long)gridDim.x * blockDim.x) {
+    double g6[6], gu[6], sqg;
+    for (int a = 0; a < 6; a++) g6[a] = m.f[4 + a][c];
+    metric_inverse_exact(g6, gu, &sqg);
+    vg[VG_ALP * b.V + c] = m.f[0][c];
+    for (int a = 0; a < 3; a++) vg[(VG_BETA + a) * b.V + c] = m.f[1 + a][c];
+    vg[VG_SQG * b.V + c] = sqg;
+    for (int a = 0; a < 6; a++) vg[(VG_GU + a) * b.V + c] = gu[a];
+  }
+}
+
+static int grid_for(long count, int threads) {
+  long blocks = (count + threads - 1) / threads;
+  const long cap = 152L * 32;
+  return (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
+}
+
+cudaError_t launch_prepare(const Blk& b, const CF16& m, const Ws& w, cudaStream_t s) {
+  const int T = 128;
+  k_geom_centre<<<grid_for((long)b.N[0] * b.N[1] * b.N[2], T), T, 0, s>>>(b, m, w.cg);
+  const long fc = (long)(b.N[0] + 1) * b.N[1] * b.N[2];
+  k_geom_face<0><<<grid_for(fc, T), T, 0, s>>>(b, m, w.fg);
+  k_geom_face<1><<<grid_for(fc, T), T, 0, s>>>(b, m, w.fg);
+  k_geom_face<2><<<grid_for(fc, T), T, 0, s>>>(b, m, w.fg);
+  k_geom_vertex<<<grid_for(b.V, 256), 256, 0, s>>>(b, m, w.vg);
+  return cudaGetLastError();
+}
+
+}  // namespace asterx

@@ -1,0 +1,48 @@
+// Host-side launchers of the CUDA kernels (each .cu file owns its kernels).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "layout.h"
+
+namespace asterx {
+
+struct StageArgs {
+  Blk b;
+  Ws w;
+  int recon;
+  int gauge;
+  double gamma, rho_atm, K_atm, gamma_atm, c2p_tol, W_max, xi;
+  int c2p_maxiter, brent_maxiter, use_fallback;
+};
+
+cudaError_t launch_prepare(const Blk& b, const CF16& m, const Ws& w, cudaStream_t s);
+
+// ghost fill of the 9 state fields (with linear extrapolation of A under copy BCs) or of the 5 primitives
+cudaError_t launch_ghost_state(const Blk& b, const F9& U, cudaStream_t s);
+cudaError_t launch_ghost_prims(const Blk& b, const F5& P, cudaStream_t s);
+
+// B~ = curl A on faces, then the undensitised centre field of every cell
+cudaError_t launch_bfield(const Blk& b, const Ws& w, const F9& U, cudaStream_t s);
+
+// conserved variables of every cell from primitives (needs launch_bfield first)
+cudaError_t launch_prim2con(const StageArgs& a, const F9& U, const F5& P, cudaStream_t s);
+
+// recovery on interior cells (needs launch_bfield first); flags/stats may be null
+cudaError_t launch_c2p(const StageArgs& a, const F9& U, const F5& P, signed char* flags,
+                       unsigned long long* stats, cudaStream_t s);
+
+// right-hand side (stage < 0) or RK4 stage combine (stage 0..3): faces, edges, vertices and cells.
+// Needs launch_bfield on U_s and primitives with ghosts.
+cudaError_t launch_rhs(const StageArgs& a, const F9& Us, const F5& P, int stage, double dt, const F9& Un,
+                       const F9& Unext, const F9& Uacc, const F9& dU, cudaStream_t s);
+
+// face-kernel launch timing (measurement hook of the benchmark)
+cudaError_t profile_enable(int cap);
+void profile_disable();
+cudaError_t profile_read(int* launches, double* total_ms);
+
+// FP64 fused multiply-add throughput probe (measurement helper)
+cudaError_t launch_dfma_probe(double* out, int blocks, int threads, long iters, cudaStream_t s);
+
+}  // namespace asterx

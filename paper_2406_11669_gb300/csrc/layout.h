@@ -1,0 +1,75 @@
+// Block constants and workspace layout shared by the host runtime and the kernels.
+#pragma once
+
+#include <cstddef>
+
+namespace asterx {
+
+// Centre geometry record (per cell): the vertex metric interpolated to the centre at 4th order, its inverse and
+// sqrt(det), K_ij, and 4th-order centre derivatives d_i alpha, d_i beta^j, d_i gamma_jk (interior cells only).
+enum {
+  CG_ALP = 0,
+  CG_BETA = 1,    // 3
+  CG_G = 4,       // 6 (xx, xy, xz, yy, yz, zz)
+  CG_GU = 10,     // 6
+  CG_SQG = 16,
+  CG_K = 17,      // 6
+  CG_DALP = 23,   // 3: d_i alpha
+  CG_DBETA = 26,  // 9: d_i beta^j at i*3 + j
+  CG_DG = 35,     // 18: d_i gamma_jk at i*6 + sym(j,k)
+  NCG = 53
+};
+
+// Face geometry record (per face, one set per direction): metric interpolated in the two transverse directions.
+enum { FG_ALP = 0, FG_BETA = 1, FG_G = 4, FG_GU = 10, FG_SQG = 16, NFG = 17 };
+
+// Vertex geometry record: lapse, shift, sqrt(det gamma), inverse metric.
+enum { VG_ALP = 0, VG_BETA = 1, VG_SQG = 4, VG_GU = 5, NVG = 11 };
+
+// Face data written by the face kernel (per face, one set per direction): HLLE flux of the 5 hydro variables,
+// the upwind transverse velocities of Eq. uct1 (components (d+1)%3 and (d+2)%3), c_max and c_min.
+enum { FD_F = 0, FD_VB1 = 5, FD_VB2 = 6, FD_CMAX = 7, FD_CMIN = 8, NFD = 9 };
+
+// Reconstructed variables per cell and direction: rho, p, u^x, u^y, u^z (u = W v), the two transverse B.
+enum { NREC = 7 };
+
+struct Blk {
+  int n[3];
+  int N[3];  // n + 2g
+  int g;
+  int bc[3];
+  long sy, sz;  // strides of j and k
+  long V;       // entries per field
+  double dx[3];
+  double idx[3];
+};
+
+struct Ws {
+  double* cg;      // NCG fields
+  double* fg;      // 3 * NFG fields
+  double* vg;      // NVG fields
+  double* bf;      // 3 fields: densitised face B~ (x-, y-, z-faces)
+  double* bc;      // 3 fields: undensitised centre B
+  double* uvel;    // 3 fields: u^i = W v^i at cells
+  double* rec;     // 2 * NREC fields: lower-face values, then upper-face values (current direction)
+  double* face;    // 3 * NFD fields
+  double* ga;      // 1 field: G_A at vertices
+  double* fpsi;    // 3 fields: F_Psi^j at vertices
+  double* uacc;    // 9 fields: RK4 accumulator of asterx_rk4_step
+  double* ustage;  // 2 * 9 fields: RK4 stage buffers of asterx_rk4_step
+  unsigned long long* counters;  // 8 counters (internal statistics when the caller passes none)
+};
+
+constexpr int WS_FIELDS = NCG + 3 * NFG + NVG + 3 + 3 + 3 + 2 * NREC + 3 * NFD + 1 + 3 + 9 + 18;
+
+struct F9 {
+  double* f[9];
+};
+struct F5 {
+  double* f[5];
+};
+struct CF16 {
+  const double* f[16];
+};
+
+}  // namespace asterx

@@ -1,0 +1,400 @@
+// Device-side pointwise physics of the GRMHD stage (FP64 throughout).
+//
+// Paper: AsterX, arXiv:2406.11669.  Sec. 2.2 (Valencia form, Eqs. eulerianB, grmhdeqs, cons, grmhdsrc),
+// Sec. 3.3 (reconstruction, HLLE, magnetosonic speeds), Sec. 3.5 (Noble 2D / Palenzuela 1D recovery),
+// Sec. 3.6 (atmosphere), Sec. 3.7 (ideal-gas EOS).
+//
+// Symmetric 3x3 tensors are stored as 6 components in the order xx, xy, xz, yy, yz, zz.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace asterx {
+
+__host__ __device__ constexpr int sym(int a, int b) {
+  return (a == 0) ? b : (a == 1 ? (b == 0 ? 1 : b + 2) : (b == 0 ? 2 : (b == 1 ? 4 : 5)));
+}
+
+// 3+1 geometry at one point.
+struct Geo {
+  double alp;
+  double beta[3];
+  double g[6];   // gamma_ij
+  double gu[6];  // gamma^ij
+  double sqg;    // sqrt(det gamma)
+};
+
+__device__ __forceinline__ double contract_sym(const double m[6], const double a[3], const double b[3]) {
+  return m[0] * a[0] * b[0] + m[3] * a[1] * b[1] + m[5] * a[2] * b[2] +
+         m[1] * (a[0] * b[1] + a[1] * b[0]) + m[2] * (a[0] * b[2] + a[2] * b[0]) +
+         m[4] * (a[1] * b[2] + a[2] * b[1]);
+}
+
+__device__ __forceinline__ void lower(const double m[6], const double a[3], double out[3]) {
+  out[0] = m[0] * a[0] + m[1] * a[1] + m[2] * a[2];
+  out[1] = m[1] * a[0] + m[3] * a[1] + m[4] * a[2];
+  out[2] = m[2] * a[0] + m[4] * a[1] + m[5] * a[2];
+}
+
+// inverse and sqrt(det) of a symmetric positive-definite 3x3 matrix (cofactors)
+__device__ __forceinline__ void sym_inverse(const double g[6], double gu[6], double* sqg) {
+  const double c00 = g[3] * g[5] - g[4] * g[4];
+  const double c01 = g[4] * g[2] - g[1] * g[5];
+  const double c02 = g[1] * g[4] - g[3] * g[2];
+  const double det = g[0] * c00 + g[1] * c01 + g[2] * c02;
+  const double idet = 1.0 / det;
+  gu[0] = c00 * idet;
+  gu[1] = c01 * idet;
+  gu[2] = c02 * idet;
+  gu[3] = (g[0] * g[5] - g[2] * g[2]) * idet;
+  gu[4] = (g[1] * g[2] - g[0] * g[4]) * idet;
+  gu[5] = (g[0] * g[3] - g[1] * g[1]) * idet;
+  *sqg = sqrt(det);
+}
+
+// ----------------------------------------------------------------------------------------------------------
+// One side of a face: conserved variables, fluxes along d and the two extreme magnetosonic speeds.
+//
+// Algebra used (equivalent to Eqs. eulerianB, cons, grmhdeqs):  with W^2 = 1 + gamma_ij u^i u^j, v = u / W,
+//   B.v = B^i v_i,  b^2 = B^2 / W^2 + (B.v)^2,  alpha b^0 = W (B.v),  b_j = B_j / W + W (B.v) v_j,
+//   S_j = (rho h W^2 + B^2) v_j - (B.v) B_j,  tau = rho h W^2 - p - rho W + B^2 - b^2 / 2,
+//   alpha sqrt(g) F^d:  D~ vt,  S~_j vt + a sqrt(g) (p_t delta^d_j - b_j B^d / W),  tau~ vt + a sqrt(g) (p_t v^d - (B.v) B^d)
+// with vt = alpha v^d - beta^d, p_t = p + b^2/2.
+
+struct SideOut {
+  double U[5];
+  double F[5];
+  double lm, lp;  // lambda_-, lambda_+
+  double vt[3];   // v~^i = alpha v^i - beta^i
+};
+
+// Extreme roots of the magnetosonic quartic (Sec. 3.3): with phi = (-lambda, e_d),
+//   a = u^mu phi_mu = ud - lambda u0,  Bc = b^mu phi_mu = bd - lambda b0,
+//   G = g^{mu nu} phi_mu phi_nu = gamma^dd - (lambda + beta^d)^2 / alpha^2,
+//   Q(lambda) = rho h (1 - cs2) a^4 - (rho h cs2 + b^2) a^2 G + cs2 Bc^2 G   (the quartic times cs2),
+// evaluated in this factored form (accurate where a -> 0, i.e. near the fluid speed, which the expanded
+// polynomial is not for cold fluids) and solved by Newton from each light-cone speed, where it is monotone.
+struct Quartic {
+  double A4, C2, cs2, u0, ud, b0, bd, betad, ia2, gdd;
+  __device__ __forceinline__ double newton(double lam, double width) const {
+#pragma unroll 1
+    for (int it = 0; it < 60; it++) {
+      const double a = ud - lam * u0;
+      const double bc = bd - lam * b0;
+      const double lb = lam + betad;
+      const double G = gdd - lb * lb * ia2;
+      const double dG = -2.0 * lb * ia2;
+      const double a2 = a * a;
+      const double r = cs2 * bc * bc - C2 * a2;
+      const double dr = -2.0 * (cs2 * bc * b0 - C2 * a * u0);
+      const double q = A4 * a2 * a2 + r * G;
+      const double dq = -4.0 * A4 * a2 * a * u0 + dr * G + r * dG;
+      if (dq == 0.0) break;
+      const double step = q / dq;
+      lam -= step;
+      if (fabs(step) <= 1e-13 * (fabs(lam) + width)) break;
+    }
+    return lam;
+  }
+};
+
+__device__ __forceinline__ void face_side(const Geo& m, int d, double rho, double press, const double u[3],
+                                          const double B[3], double gamma, SideOut& o) {
+  const double uu = contract_sym(m.g, u, u);
+  const double W = sqrt(1.0 + uu);
+  const double iW = 1.0 / W;
+  double v[3] = {u[0] * iW, u[1] * iW, u[2] * iW};
+  double vl[3], Bl[3];
+  lower(m.g, v, vl);
+  lower(m.g, B, Bl);
+  const double B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const double Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
+  const double iW2 = iW * iW;
+  const double b2 = B2 * iW2 + Bv * Bv;
+  const double rhoh = rho + gamma / (gamma - 1.0) * press;
+  const double W2 = W * W;
+  const double z = rhoh * W2;
+  const double sg = m.sqg;
+  const double asg = m.alp * sg;
+  o.U[0] = sg * rho * W;
+  for (int a = 0; a < 3; a++) o.U[1 + a] = sg * ((z + B2) * vl[a] - Bv * Bl[a]);
+  o.U[4] = sg * (z - press - rho * W + B2 - 0.5 * b2);
+  for (int a = 0; a < 3; a++) o.vt[a] = m.alp * v[a] - m.beta[a];
+  const double vt = o.vt[d];
+  const double pt = press + 0.5 * b2;
+  const double Bd = B[d];
+  o.F[0] = o.U[0] * vt;
+  for (int a = 0; a < 3; a++) {
+    const double bl = Bl[a] * iW + W * Bv * vl[a];
+    o.F[1 + a] = o.U[1 + a] * vt - asg * bl * Bd * iW;
+  }
+  o.F[1 + d] += asg * pt;
+  o.F[4] = o.U[4] * vt + asg * (pt * v[d] - Bv * Bd);
+
+  // magnetosonic speeds
+  const double ia = 1.0 / m.alp;
+  const double u0 = W * ia;
+  const double ud = W * (v[d] - m.beta[d] * ia);
+  const double b0 = W * Bv * ia;
+  const double bd = (Bd + m.alp * b0 * ud) * iW;
+  Quartic Q;
+  Q.cs2 = gamma * press / rhoh;  // = Gamma (Gamma - 1) eps / h for the ideal gas
+  Q.A4 = rhoh * (1.0 - Q.cs2);
+  Q.C2 = rhoh * Q.cs2 + b2;
+  Q.u0 = u0;
+  Q.ud = ud;
+  Q.b0 = b0;
+  Q.bd = bd;
+  Q.betad = m.beta[d];
+  Q.ia2 = ia * ia;
+  Q.gdd = m.gu[sym(d, d)];
+  const double width = m.alp * sqrt(Q.gdd);
+  o.lp = Q.newton(-m.beta[d] + width, width);
+  o.lm = Q.newton(-m.beta[d] - width, width);
+}
+
+// ----------------------------------------------------------------------------------------------------------
+// Reconstruction of one cell from a_{i-2..i+2}: values at its lower (lo) and upper (hi) faces.
+
+__device__ __forceinline__ double minmod2(double x, double y) {
+  if (x * y <= 0.0) return 0.0;
+  return (fabs(x) <= fabs(y)) ? x : y;
+}
+
+__device__ __forceinline__ double ppm_dq(double am, double a0, double ap) {
+  // van Leer limited slope of Colella & Woodward (1984)
+  if ((ap - a0) * (a0 - am) <= 0.0) return 0.0;
+  const double c = 0.5 * (ap - am);
+  const double s = fmin(fabs(c), fmin(2.0 * fabs(a0 - am), 2.0 * fabs(ap - a0)));
+  return (c < 0.0) ? -s : s;
+}
+
+__device__ __forceinline__ void ppm_limit(double ai, double& l, double& r) {
+  // monotonicity constraints of the parabola (CW84)
+  if ((r - ai) * (ai - l) <= 0.0) {
+    l = ai;
+    r = ai;
+  } else {
+    const double dlr = r - l;
+    const double mid = ai - 0.5 * (l + r);
+    const double d6 = dlr * dlr * (1.0 / 6.0);
+    if (dlr * mid > d6) l = 3.0 * ai - 2.0 * r;
+    else if (-d6 > dlr * mid) r = 3.0 * ai - 2.0 * l;
+  }
+}
+
+__device__ __forceinline__ double wenoz_hi(double s0, double s1, double s2, double s3, double s4) {
+  // Borges et al. (2008) WENO-Z, 5th order, eps = 1e-40, power 2
+  const double q0 = (2.0 * s0 - 7.0 * s1 + 11.0 * s2) * (1.0 / 6.0);
+  const double q1 = (-s1 + 5.0 * s2 + 2.0 * s3) * (1.0 / 6.0);
+  const double q2 = (2.0 * s2 + 5.0 * s3 - s4) * (1.0 / 6.0);
+  const double t0a = s0 - 2.0 * s1 + s2, t0b = s0 - 4.0 * s1 + 3.0 * s2;
+  const double t1a = s1 - 2.0 * s2 + s3, t1b = s1 - s3;
+  const double t2a = s2 - 2.0 * s3 + s4, t2b = 3.0 * s2 - 4.0 * s3 + s4;
+  const double b0 = (13.0 / 12.0) * t0a * t0a + 0.25 * t0b * t0b;
+  const double b1 = (13.0 / 12.0) * t1a * t1a + 0.25 * t1b * t1b;
+  const double b2 = (13.0 / 12.0) * t2a * t2a + 0.25 * t2b * t2b;
+  const double tau5 = fabs(b0 - b2);
+  const double r0 = tau5 / (b0 + 1e-40), r1 = tau5 / (b1 + 1e-40), r2 = tau5 / (b2 + 1e-40);
+  const double w0 = 0.1 * (1.0 + r0 * r0), w1 = 0.6 * (1.0 + r1 * r1), w2 = 0.3 * (1.0 + r2 * r2);
+  return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+}
+
+template <int SCHEME>
+__device__ __forceinline__ void recon5(const double a[5], double& lo, double& hi) {
+  if (SCHEME == 0) {
+    const double s = minmod2(a[2] - a[1], a[3] - a[2]);
+    lo = a[2] - 0.5 * s;
+    hi = a[2] + 0.5 * s;
+  } else if (SCHEME == 1) {
+    const double dm = ppm_dq(a[0], a[1], a[2]);
+    const double d0 = ppm_dq(a[1], a[2], a[3]);
+    const double dp = ppm_dq(a[2], a[3], a[4]);
+    double l = a[1] + 0.5 * (a[2] - a[1]) - (d0 - dm) * (1.0 / 6.0);
+    double r = a[2] + 0.5 * (a[3] - a[2]) - (dp - d0) * (1.0 / 6.0);
+    ppm_limit(a[2], l, r);
+    lo = l;
+    hi = r;
+  } else {
+    hi = wenoz_hi(a[0], a[1], a[2], a[3], a[4]);
+    lo = wenoz_hi(a[4], a[3], a[2], a[1], a[0]);
+  }
+}
+
+// ----------------------------------------------------------------------------------------------------------
+// Primitive recovery (Sec. 3.5) for one cell.  Inputs undensitised: D, S_i, tau, centre B^i.
+
+struct C2PParams {
+  double gamma, rho_atm, K_atm, gamma_atm, tol, W_max;
+  int maxiter, brent_maxiter, use_fallback;
+};
+
+struct C2PResult {
+  double rho, press, v[3];
+  int flag;   // 0 Noble, 1 Palenzuela, 2 atmosphere, -1 failed (atmosphere)
+  int iters;
+};
+
+__device__ __forceinline__ void c2p_velocity(const Geo& m, const double S[3], const double B[3], double z,
+                                             double B2, double BS, double v[3]) {
+  // Eq. (Noble2D v)
+  const double izB = 1.0 / (z + B2);
+  const double f = BS / z * izB;
+  v[0] = (m.gu[0] * S[0] + m.gu[1] * S[1] + m.gu[2] * S[2]) * izB + f * B[0];
+  v[1] = (m.gu[1] * S[0] + m.gu[3] * S[1] + m.gu[4] * S[2]) * izB + f * B[1];
+  v[2] = (m.gu[2] * S[0] + m.gu[4] * S[1] + m.gu[5] * S[2]) * izB + f * B[2];
+}
+
+__device__ __forceinline__ bool not_physical(double x) { return !(x >= 0.0) || isinf(x); }
+
+// Noble et al. 2D Newton on (z, v^2): residuals Eqs. (Noble2D momentum) and (Noble2D energy) with the ideal-gas
+// p(z, v^2) = (G-1)/G (z (1 - v^2) - D sqrt(1 - v^2)); a step that would make z <= 0 halves z instead.
+__device__ inline bool c2p_noble(const Geo& m, double D, const double S[3], double tau, const double B[3], double S2,
+                          double B2, double BS, double z, double v2, const C2PParams& P, C2PResult& r) {
+  const double gf = (P.gamma - 1.0) / P.gamma;
+  const double v2max = 1.0 - 1.0 / (P.W_max * P.W_max);
+  const double BS2 = BS * BS;
+  bool conv = false;
+  int it;
+#pragma unroll 1
+  for (it = 1; it <= P.maxiter; it++) {
+    const double sq = sqrt(1.0 - v2);
+    const double Bz = B2 + z;
+    const double iz = 1.0 / z;
+    const double iz2 = iz * iz;
+    const double p = gf * (z * (1.0 - v2) - D * sq);
+    const double f0 = v2 * Bz * Bz - BS2 * (B2 + 2.0 * z) * iz2 - S2;
+    const double f1 = tau + D - 0.5 * B2 * (1.0 + v2) + 0.5 * BS2 * iz2 - z + p;
+    const double J00 = 2.0 * v2 * Bz + 2.0 * BS2 * Bz * iz2 * iz;
+    const double J01 = Bz * Bz;
+    const double J10 = -BS2 * iz2 * iz - 1.0 + gf * (1.0 - v2);
+    const double J11 = -0.5 * B2 + gf * (-z + 0.5 * D / sq);
+    const double idet = 1.0 / (J00 * J11 - J01 * J10);
+    const double dz = (-f0 * J11 + J01 * f1) * idet;
+    const double dv2 = (-J00 * f1 + J10 * f0) * idet;
+    const bool damped = !(z + dz > 0.0);
+    z = damped ? 0.5 * z : z + dz;
+    v2 += dv2;
+    v2 = fmin(fmax(v2, 0.0), v2max);
+    if (!isfinite(z) || !isfinite(v2)) break;
+    if (!damped && fabs(dz) <= P.tol * fabs(z) && fabs(dv2) <= P.tol) {
+      conv = true;
+      break;
+    }
+  }
+  r.iters = (it > P.maxiter) ? P.maxiter : it;
+  if (!conv || !(z > 0.0) || !(v2 >= 0.0) || !(v2 < 1.0)) return false;
+  const double W = 1.0 / sqrt(1.0 - v2);
+  const double rho = D / W;
+  c2p_velocity(m, S, B, z, B2, BS, r.v);
+  const double eps = (z / (rho * W * W) - 1.0) / P.gamma;  // Eq. (Noble2D epsilon), adiabatic index
+  const double press = (P.gamma - 1.0) * rho * eps;
+  if (not_physical(rho) || not_physical(eps) || not_physical(press)) return false;
+  if (!isfinite(r.v[0]) || !isfinite(r.v[1]) || !isfinite(r.v[2])) return false;
+  r.rho = rho;
+  r.press = press;
+  return true;
+}
+
+// Palenzuela et al. 1D function f(x) = x - h^(x) W^(x), x = hW (Eq. Palenzuela Brent and the steps below it).
+struct PalFn {
+  double q, r, s, t, D, gamma, v2max;
+  __device__ __forceinline__ double operator()(double x, double* W_, double* rho_, double* eps_) const {
+    double v2 = (r * x * x + t * t * (2.0 * x + s)) / (x * x * (x + s) * (x + s));
+    v2 = fmin(fmax(v2, 0.0), v2max);
+    const double W = 1.0 / sqrt(1.0 - v2);
+    const double rho = D / W;
+    double eps = -1.0 + (x / W) * (1.0 - W * W) + W * (1.0 + q - s + 0.5 * (t * t / (x * x) + s / (W * W)));
+    eps = fmax(eps, 0.0);
+    const double press = (gamma - 1.0) * rho * eps;
+    *W_ = W;
+    *rho_ = rho;
+    *eps_ = eps;
+    return x - (1.0 + eps + press / rho) * W;
+  }
+};
+
+// Bracketed root by Brent's method (Brent 1973): inverse quadratic / secant steps kept inside the bracket,
+// bisection otherwise.  Returns false without a sign change or after maxiter.
+__device__ inline bool brent(const PalFn& f, double lo, double hi, double xtol, int maxiter, double* root) {
+  double W_, r_, e_;
+  double a = lo, b = hi, fa = f(a, &W_, &r_, &e_), fb = f(b, &W_, &r_, &e_);
+  if (!isfinite(fa) || !isfinite(fb) || (fa > 0.0 && fb > 0.0) || (fa < 0.0 && fb < 0.0)) return false;
+  double c = a, fc = fa, d = b - a, e = d;
+#pragma unroll 1
+  for (int it = 0; it < maxiter; it++) {
+    if ((fb > 0.0) == (fc > 0.0) && fb != 0.0 && fc != 0.0) {
+      c = a;
+      fc = fa;
+      d = e = b - a;
+    }
+    if (fabs(fc) < fabs(fb)) {
+      a = b; b = c; c = a;
+      fa = fb; fb = fc; fc = fa;
+    }
+    const double tol = 4.440892098500626e-16 * fabs(b) + 0.5 * xtol;
+    const double m = 0.5 * (c - b);
+    if (fabs(m) <= tol || fb == 0.0) {
+      *root = b;
+      return true;
+    }
+    if (fabs(e) >= tol && fabs(fa) > fabs(fb)) {
+      double p, q;
+      const double s = fb / fa;
+      if (a == c) {
+        p = 2.0 * m * s;
+        q = 1.0 - s;
+      } else {
+        const double qq = fa / fc, rr = fb / fc;
+        p = s * (2.0 * m * qq * (qq - rr) - (b - a) * (rr - 1.0));
+        q = (qq - 1.0) * (rr - 1.0) * (s - 1.0);
+      }
+      if (p > 0.0) q = -q;
+      else p = -p;
+      if (2.0 * p < fmin(3.0 * m * q - fabs(tol * q), fabs(e * q))) {
+        e = d;
+        d = p / q;
+      } else {
+        d = m;
+        e = d;
+      }
+    } else {
+      d = m;
+      e = d;
+    }
+    a = b;
+    fa = fb;
+    b += (fabs(d) > tol) ? d : (m > 0.0 ? tol : -tol);
+    fb = f(b, &W_, &r_, &e_);
+    if (!isfinite(fb)) return false;
+  }
+  return false;
+}
+
+__device__ inline bool c2p_palenzuela(const Geo& m, double D, const double S[3], double tau, const double B[3], double S2,
+                               double B2, double BS, const C2PParams& P, C2PResult& r) {
+  PalFn f;
+  f.q = tau / D;
+  f.r = S2 / (D * D);
+  f.s = B2 / D;
+  f.t = BS / (D * sqrt(D));
+  f.D = D;
+  f.gamma = P.gamma;
+  f.v2max = 1.0 - 1.0 / (P.W_max * P.W_max);
+  const double lo = fmax(1.0 + f.q - f.s, 1.0);  // x = hW >= 1
+  const double hi = 2.0 + 2.0 * f.q - f.s;
+  if (!(hi > lo)) return false;
+  double x;
+  if (!brent(f, lo, hi, 1e-15 * hi, P.brent_maxiter, &x)) return false;
+  double W, rho, eps;
+  f(x, &W, &rho, &eps);
+  const double press = (P.gamma - 1.0) * rho * eps;
+  c2p_velocity(m, S, B, D * x, B2, BS, r.v);  // z = rho W x = D x
+  if (not_physical(rho) || not_physical(eps) || not_physical(press)) return false;
+  if (!isfinite(r.v[0]) || !isfinite(r.v[1]) || !isfinite(r.v[2])) return false;
+  r.rho = rho;
+  r.press = press;
+  return true;
+}
+
+}  // namespace asterx

@@ -1,0 +1,28 @@
+// FP64 fused multiply-add throughput probe: the ALU roofline of an FP64-bound kernel is the rate at which
+// the SMs retire DFMA.  Eight independent chains per thread keep the FP64 pipe busy regardless of latency.
+#include "kernels.h"
+
+namespace asterx {
+
+__global__ void k_dfma_probe(double* out, long iters) {
+  const double s = 1.0 + 1e-12 * (threadIdx.x + 1);
+  double a0 = 1.0 + 1e-9 * threadIdx.x, a1 = a0 + 1e-3, a2 = a0 + 2e-3, a3 = a0 + 3e-3;
+  double a4 = a0 + 4e-3, a5 = a0 + 5e-3, a6 = a0 + 6e-3, a7 = a0 + 7e-3;
+  const double c = -1e-12;
+#pragma unroll 1
+  for (long i = 0; i < iters; i++) {
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+      a0 = fma(a0, s, c); a1 = fma(a1, s, c); a2 = fma(a2, s, c); a3 = fma(a3, s, c);
+      a4 = fma(a4, s, c); a5 = fma(a5, s, c); a6 = fma(a6, s, c); a7 = fma(a7, s, c);
+    }
+  }
+  out[blockIdx.x * (long)blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+
+cudaError_t launch_dfma_probe(double* out, int blocks, int threads, long iters, cudaStream_t s) {
+  k_dfma_probe<<<blocks, threads, 0, s>>>(out, iters);
+  return cudaGetLastError();
+}
+
+}  // namespace asterx

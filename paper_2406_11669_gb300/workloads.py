@@ -535,3 +535,15 @@ def shock_tube(states: dict, nx: int, gamma: float, recon=RECON_PPM):
     params = default_params(gamma=gamma, gamma_atm=gamma, rho_atm=1e-9, K_atm=1.0, recon=recon)
     return Workload("shock_tube", n, g, x0, dx, (BC_COPY,) * 3, params, 0.25 * h, prims,
                     dict(Ax=zero.copy(), Ay=Ay, Az=Az), zero.copy(), flat_metric(shape))
+
+
+def sub_block(w: Workload, lo, n, name=None) -> Workload:
+    """The block of `n` interior cells starting at interior cell `lo` of `w` (same spacing, same data): every
+    array is sliced in padded index space, ghosts included, and the BCs are kept."""
+    g = w.g
+    sl = tuple(slice(lo[d], lo[d] + n[d] + 2 * g + 1) for d in (2, 1, 0))
+    cut = lambda a: np.ascontiguousarray(a[sl])
+    x0 = tuple(w.x0[d] + lo[d] * w.dx[d] for d in range(3))
+    return Workload(name or w.name + "_sub", tuple(int(v) for v in n), g, x0, w.dx, w.bc, dict(w.params), w.dt,
+                    {k: cut(v) for k, v in w.prims.items()}, {k: cut(v) for k, v in w.A.items()}, cut(w.Psi),
+                    {k: cut(v) for k, v in w.metric.items()})
