@@ -116,6 +116,7 @@ StageArgs make_args(const asterx_params* p, const asterx_block* blk, void* ws) {
   a.recon = p->recon;
   a.gauge = p->gauge;
   a.gamma = p->gamma;
+  a.gfac = p->gamma / (p->gamma - 1.0);
   a.rho_atm = p->rho_atm;
   a.K_atm = p->K_atm;
   a.gamma_atm = p->gamma_atm;

@@ -173,6 +173,7 @@ __global__ void k_geom_face(Blk b, CF16 m, double* __restrict__ fg) {
       out[(FG_GU + a) * b.V + c] = gu[a];
     }
     out[FG_SQG * b.V + c] = sqg;
+    out[FG_IALP * b.V + c] = 1.0 / val[0];
   }
 }
 

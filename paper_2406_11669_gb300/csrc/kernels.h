@@ -13,6 +13,7 @@ struct StageArgs {
   int recon;
   int gauge;
   double gamma, rho_atm, K_atm, gamma_atm, c2p_tol, W_max, xi;
+  double gfac;  // Gamma / (Gamma - 1)
   int c2p_maxiter, brent_maxiter, use_fallback;
 };
 

@@ -98,8 +98,10 @@ struct Quartic {
   }
 };
 
-__device__ __forceinline__ void face_side(const Geo& m, int d, double rho, double press, const double u[3],
-                                          const double B[3], double gamma, SideOut& o) {
+// gfac = Gamma / (Gamma - 1), ia = 1 / alpha (both hoisted by the caller)
+__device__ __forceinline__ void face_side(const Geo& m, double ia, int d, double rho, double press,
+                                          const double u[3], const double B[3], double gamma, double gfac,
+                                          SideOut& o) {
   const double uu = contract_sym(m.g, u, u);
   const double W = sqrt(1.0 + uu);
   const double iW = 1.0 / W;
@@ -111,7 +113,7 @@ __device__ __forceinline__ void face_side(const Geo& m, int d, double rho, doubl
   const double Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
   const double iW2 = iW * iW;
   const double b2 = B2 * iW2 + Bv * Bv;
-  const double rhoh = rho + gamma / (gamma - 1.0) * press;
+  const double rhoh = rho + gfac * press;
   const double W2 = W * W;
   const double z = rhoh * W2;
   const double sg = m.sqg;
@@ -132,7 +134,6 @@ __device__ __forceinline__ void face_side(const Geo& m, int d, double rho, doubl
   o.F[4] = o.U[4] * vt + asg * (pt * v[d] - Bv * Bd);
 
   // magnetosonic speeds
-  const double ia = 1.0 / m.alp;
   const double u0 = W * ia;
   const double ud = W * (v[d] - m.beta[d] * ia);
   const double b0 = W * Bv * ia;
@@ -149,8 +150,23 @@ __device__ __forceinline__ void face_side(const Geo& m, int d, double rho, doubl
   Q.ia2 = ia * ia;
   Q.gdd = m.gu[sym(d, d)];
   const double width = m.alp * sqrt(Q.gdd);
-  o.lp = Q.newton(-m.beta[d] + width, width);
-  o.lm = Q.newton(-m.beta[d] - width, width);
+  // Starting points: the lab-frame speeds of an isotropic wave with the perpendicular fast speed
+  // c^2 = cs^2 + cA^2 - cs^2 cA^2 (cA^2 = b^2 / (rho h + b^2)), which bounds the fast magnetosonic speed in
+  // every direction, so both starts lie outside the extreme roots and Newton converges monotonically from
+  // there (as from the light cone, but from much closer).  Clamped to the light cone.
+  const double ca2 = b2 / (rhoh + b2);
+  const double c2 = Q.cs2 + ca2 - Q.cs2 * ca2;
+  const double v2 = 1.0 - iW2;
+  const double den = 1.0 - v2 * c2;
+  const double disc = fmax((1.0 - v2) * (Q.gdd * den - v[d] * v[d] * (1.0 - c2)), 0.0);
+  const double spread = sqrt(c2 * disc);
+  const double idn = m.alp / den;
+  const double mid = v[d] * (1.0 - c2);
+  const double lc = -m.beta[d];
+  const double lp0 = fmin((mid + spread) * idn - m.beta[d] + 1e-12 * width, lc + width);
+  const double lm0 = fmax((mid - spread) * idn - m.beta[d] - 1e-12 * width, lc - width);
+  o.lp = Q.newton(lp0, width);
+  o.lm = Q.newton(lm0, width);
 }
 
 // ----------------------------------------------------------------------------------------------------------
@@ -183,21 +199,46 @@ __device__ __forceinline__ void ppm_limit(double ai, double& l, double& r) {
   }
 }
 
-__device__ __forceinline__ double wenoz_hi(double s0, double s1, double s2, double s3, double s4) {
-  // Borges et al. (2008) WENO-Z, 5th order, eps = 1e-40, power 2
-  const double q0 = (2.0 * s0 - 7.0 * s1 + 11.0 * s2) * (1.0 / 6.0);
-  const double q1 = (-s1 + 5.0 * s2 + 2.0 * s3) * (1.0 / 6.0);
-  const double q2 = (2.0 * s2 + 5.0 * s3 - s4) * (1.0 / 6.0);
-  const double t0a = s0 - 2.0 * s1 + s2, t0b = s0 - 4.0 * s1 + 3.0 * s2;
-  const double t1a = s1 - 2.0 * s2 + s3, t1b = s1 - s3;
-  const double t2a = s2 - 2.0 * s3 + s4, t2b = 3.0 * s2 - 4.0 * s3 + s4;
-  const double b0 = (13.0 / 12.0) * t0a * t0a + 0.25 * t0b * t0b;
-  const double b1 = (13.0 / 12.0) * t1a * t1a + 0.25 * t1b * t1b;
-  const double b2 = (13.0 / 12.0) * t2a * t2a + 0.25 * t2b * t2b;
-  const double tau5 = fabs(b0 - b2);
-  const double r0 = tau5 / (b0 + 1e-40), r1 = tau5 / (b1 + 1e-40), r2 = tau5 / (b2 + 1e-40);
-  const double w0 = 0.1 * (1.0 + r0 * r0), w1 = 0.6 * (1.0 + r1 * r1), w2 = 0.3 * (1.0 + r2 * r2);
-  return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+// WENO-Z values at both faces of the middle cell of s[0..4].  The lower face uses the mirrored stencil, whose
+// smoothness indicators are those of the upper face in reverse order, so the three indicators and the three
+// ratios tau5 / (beta_k + eps) are shared; the three reciprocals come from one division.
+__device__ __forceinline__ void wenoz_both(const double s[5], double& lo, double& hi) {
+  const double t0a = s[0] - 2.0 * s[1] + s[2], t0b = s[0] - 4.0 * s[1] + 3.0 * s[2];
+  const double t1a = s[1] - 2.0 * s[2] + s[3], t1b = s[1] - s[3];
+  const double t2a = s[2] - 2.0 * s[3] + s[4], t2b = 3.0 * s[2] - 4.0 * s[3] + s[4];
+  const double e0 = (13.0 / 12.0) * t0a * t0a + 0.25 * t0b * t0b + 1e-40;
+  const double e1 = (13.0 / 12.0) * t1a * t1a + 0.25 * t1b * t1b + 1e-40;
+  const double e2 = (13.0 / 12.0) * t2a * t2a + 0.25 * t2b * t2b + 1e-40;
+  const double tau5 = fabs(e0 - e2);
+  const double e01 = e0 * e1;
+  const double inv = 1.0 / (e01 * e2);
+  double r0, r1, r2;
+  if (isfinite(inv) && inv > 0.0) {
+    r0 = tau5 * (inv * (e1 * e2));
+    r1 = tau5 * (inv * (e0 * e2));
+    r2 = tau5 * (inv * e01);
+  } else {  // product out of range: three divisions
+    r0 = tau5 / e0;
+    r1 = tau5 / e1;
+    r2 = tau5 / e2;
+  }
+  const double z0 = 1.0 + r0 * r0, z1 = 1.0 + r1 * r1, z2 = 1.0 + r2 * r2;
+  // upper face: linear weights (1/10, 6/10, 3/10) on the sub-stencils ending at, centred on, starting at i
+  {
+    const double q0 = (2.0 * s[0] - 7.0 * s[1] + 11.0 * s[2]) * (1.0 / 6.0);
+    const double q1 = (-s[1] + 5.0 * s[2] + 2.0 * s[3]) * (1.0 / 6.0);
+    const double q2 = (2.0 * s[2] + 5.0 * s[3] - s[4]) * (1.0 / 6.0);
+    const double w0 = 0.1 * z0, w1 = 0.6 * z1, w2 = 0.3 * z2;
+    hi = (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+  }
+  // lower face: mirrored stencil, indicator k of the mirror is indicator 2-k here
+  {
+    const double q0 = (2.0 * s[4] - 7.0 * s[3] + 11.0 * s[2]) * (1.0 / 6.0);
+    const double q1 = (-s[3] + 5.0 * s[2] + 2.0 * s[1]) * (1.0 / 6.0);
+    const double q2 = (2.0 * s[2] + 5.0 * s[1] - s[0]) * (1.0 / 6.0);
+    const double w0 = 0.1 * z2, w1 = 0.6 * z1, w2 = 0.3 * z0;
+    lo = (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+  }
 }
 
 template <int SCHEME>
@@ -216,8 +257,7 @@ __device__ __forceinline__ void recon5(const double a[5], double& lo, double& hi
     lo = l;
     hi = r;
   } else {
-    hi = wenoz_hi(a[0], a[1], a[2], a[3], a[4]);
-    lo = wenoz_hi(a[4], a[3], a[2], a[1], a[0]);
+    wenoz_both(a, lo, hi);
   }
 }
 

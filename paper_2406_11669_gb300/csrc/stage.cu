@@ -198,7 +198,7 @@ __device__ __forceinline__ void load_geo_centre(const Blk& b, const double* __re
 // ----------------------------------------------------------------------------------------------------------
 // Conserved variables from primitives at every cell (initial data, Eq. cons).
 
-__global__ void k_prim2con(Blk b, Ws w, F9 U, F5 P, double gamma) {
+__global__ void k_prim2con(Blk b, Ws w, F9 U, F5 P, double gamma, double gfac) {
   Box box = make_box(0, b.N[0] - 1, 0, b.N[1] - 1, 0, b.N[2] - 1);
   GRID_LOOP(t, box.count()) {
     int i, j, k;
@@ -211,14 +211,15 @@ __global__ void k_prim2con(Blk b, Ws w, F9 U, F5 P, double gamma) {
     const double u[3] = {W * v[0], W * v[1], W * v[2]};
     const double B[3] = {w.bc[c], w.bc[b.V + c], w.bc[2 * b.V + c]};
     SideOut o;
-    face_side(m, 0, P.f[0][c], P.f[1][c], u, B, gamma, o);
+    face_side(m, 1.0 / m.alp, 0, P.f[0][c], P.f[1][c], u, B, gamma, gfac, o);
     for (int a = 0; a < 5; a++) U.f[a][c] = o.U[a];
   }
 }
 
 cudaError_t launch_prim2con(const StageArgs& a, const F9& U, const F5& P, cudaStream_t s) {
   const int T = 128;
-  k_prim2con<<<grid_for((long)a.b.N[0] * a.b.N[1] * a.b.N[2], T), T, 0, s>>>(a.b, a.w, U, P, a.gamma);
+  k_prim2con<<<grid_for((long)a.b.N[0] * a.b.N[1] * a.b.N[2], T), T, 0, s>>>(a.b, a.w, U, P, a.gamma,
+                                                                               a.gfac);
   return cudaGetLastError();
 }
 
@@ -397,7 +398,7 @@ __global__ void k_recon(Blk b, Ws w, F5 P) {
 // Face solve along D for faces g..g+n along D and all transverse indices: left state = upper value of cell
 // f-1, right state = lower value of cell f; HLLE (Eq. HLLEfluxes) and the upwind velocities of Eq. uct1.
 template <int D>
-__global__ void __launch_bounds__(128) k_faces(Blk b, Ws w, double gamma) {
+__global__ void __launch_bounds__(128) k_faces(Blk b, Ws w, double gamma, double gfac) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   int lo[3] = {0, 0, 0}, hi[3] = {b.N[0] - 1, b.N[1] - 1, b.N[2] - 1};
   lo[D] = b.g;
@@ -418,6 +419,7 @@ __global__ void __launch_bounds__(128) k_faces(Blk b, Ws w, double gamma) {
       m.gu[a] = fg[(FG_GU + a) * b.V + c];
     }
     m.sqg = fg[FG_SQG * b.V + c];
+    const double ia = fg[FG_IALP * b.V + c];
     const double Bn = w.bf[D * b.V + c] / m.sqg;
     SideOut s[2];
 #pragma unroll
@@ -429,7 +431,7 @@ __global__ void __launch_bounds__(128) k_faces(Blk b, Ws w, double gamma) {
       B[D] = Bn;
       B[T1] = r[5 * b.V];
       B[T2] = r[6 * b.V];
-      face_side(m, D, r[0], r[b.V], u, B, gamma, s[side]);
+      face_side(m, ia, D, r[0], r[b.V], u, B, gamma, gfac, s[side]);
     }
     const double cmax = fmax(0.0, fmax(s[0].lp, s[1].lp));
     const double cmin = -fmin(0.0, fmin(s[0].lm, s[1].lm));
@@ -580,7 +582,7 @@ __global__ void k_psi(Blk b, Ws w, F9 Us, int lorenz, double xi, int stage, doub
 //   S~_i: alpha sqrt(g) [-T^00 alpha d_i alpha + T^0_k d_i b^k + 1/2 (T^00 b^j b^k + 2 T^0j b^k + T^jk) d_i g_jk]
 // (b = beta) with T^{mu nu} = (rho h + b^2) u u + (p + b^2/2) g^{mu nu} - b b (Eq. tmunu).
 __device__ __forceinline__ void sources(const Geo& m, const double* __restrict__ cg, long V, long c, double rho,
-                                        double press, const double v[3], const double B[3], double gamma,
+                                        double press, const double v[3], const double B[3], double gfac,
                                         double src[5]) {
   double vl[3], Bl[3];
   lower(m.g, v, vl);
@@ -591,7 +593,7 @@ __device__ __forceinline__ void sources(const Geo& m, const double* __restrict__
   const double ia = 1.0 / m.alp;
   const double iW = 1.0 / W;
   const double b2 = B2 * iW * iW + Bv * Bv;
-  const double rhoh = rho + gamma / (gamma - 1.0) * press;
+  const double rhoh = rho + gfac * press;
   const double e = rhoh + b2;
   const double pt = press + 0.5 * b2;
   double u[4], bb[4];
@@ -642,7 +644,7 @@ __device__ __forceinline__ void sources(const Geo& m, const double* __restrict__
 }
 
 // Interior cells: dU/dt = -sum_d (F_d(+) - F_d(-)) / dx_d + S (Eq. fluxconseqs, densitised).
-__global__ void __launch_bounds__(128) k_cells(Blk b, Ws w, F5 P, double gamma, int stage, double dt, F9 Un,
+__global__ void __launch_bounds__(128) k_cells(Blk b, Ws w, F5 P, double gfac, int stage, double dt, F9 Un,
                                                  F9 Unext, F9 Uacc, F9 dU) {
   Box box = make_box(b.g, b.g + b.n[0] - 1, b.g, b.g + b.n[1] - 1, b.g, b.g + b.n[2] - 1);
   GRID_LOOP(t, box.count()) {
@@ -662,7 +664,7 @@ __global__ void __launch_bounds__(128) k_cells(Blk b, Ws w, F5 P, double gamma, 
     const double v[3] = {P.f[2][c], P.f[3][c], P.f[4][c]};
     const double B[3] = {w.bc[c], w.bc[b.V + c], w.bc[2 * b.V + c]};
     double src[5];
-    sources(m, w.cg, b.V, c, P.f[0][c], P.f[1][c], v, B, gamma, src);
+    sources(m, w.cg, b.V, c, P.f[0][c], P.f[1][c], v, B, gfac, src);
 #pragma unroll
     for (int q = 0; q < 5; q++) combine(stage, dt, c, q, r[q] + src[q], Un, Unext, Uacc, dU);
   }
@@ -730,7 +732,7 @@ static void launch_dir(const StageArgs& a, const F5& P, cudaStream_t s) {
   long fc = (long)b.N[0] * b.N[1] * b.N[2] / b.N[D] * (b.n[D] + 1);
   const bool mark = g_prof.on && g_prof.n < g_prof.cap;
   if (mark) cudaEventRecord(g_prof.ev[2 * g_prof.n], s);
-  k_faces<D><<<grid_for(fc, T), T, 0, s>>>(b, a.w, a.gamma);
+  k_faces<D><<<grid_for(fc, T), T, 0, s>>>(b, a.w, a.gamma, a.gfac);
   if (mark) cudaEventRecord(g_prof.ev[2 * g_prof.n++ + 1], s);
 }
 
@@ -750,7 +752,7 @@ cudaError_t launch_rhs(const StageArgs& a, const F9& Us, const F5& P, int stage,
   k_edges<2><<<grid_for(ec, T), T, 0, s>>>(b, a.w, stage, dt, Un, Unext, Uacc, dU);
   const double xi = a.xi > 0.0 ? a.xi : 1.5 / dt;
   k_psi<<<grid_for(ec, T), T, 0, s>>>(b, a.w, Us, lorenz, xi, stage, dt, Un, Unext, Uacc, dU);
-  k_cells<<<grid_for((long)b.n[0] * b.n[1] * b.n[2], T), T, 0, s>>>(b, a.w, P, a.gamma, stage, dt, Un, Unext,
+  k_cells<<<grid_for((long)b.n[0] * b.n[1] * b.n[2], T), T, 0, s>>>(b, a.w, P, a.gfac, stage, dt, Un, Unext,
                                                                      Uacc, dU);
   return cudaGetLastError();
 }
