@@ -1,0 +1,86 @@
+"""The C ABI library without a GPU: it loads, exports every function include/asterx.h declares, sizes
+workspaces, and rejects invalid arguments on the host before any CUDA call (ASTERX_EINVAL / ASTERX_ENOMEM)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2406_11669_gb300 import asterx as A
+from paper_2406_11669_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "asterx.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(asterx_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported():
+    L = A.lib()
+    names = declared_functions()
+    assert len(names) >= 16
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_abi_version_and_status_strings():
+    L = A.lib()
+    assert L.asterx_abi_version() == A.ABI_VERSION
+    assert L.asterx_status_str(A.ASTERX_EINVAL) == b"invalid argument"
+
+
+def test_workspace_size_and_invalid_blocks():
+    good = A.block_struct((32, 32, 32), 3, (0, 0, 0), (1 / 32,) * 3, (0, 0, 0))
+    assert A.workspace_size(good) > 39 ** 3 * 8 * 150
+    for bad in (A.block_struct((0, 32, 32), 3, (0, 0, 0), (1 / 32,) * 3, (0, 0, 0)),
+                A.block_struct((32, 32, 32), 2, (0, 0, 0), (1 / 32,) * 3, (0, 0, 0)),
+                A.block_struct((32, 32, 32), 3, (0, 0, 0), (0.0, 1.0, 1.0), (0, 0, 0)),
+                A.block_struct((32, 32, 32), 3, (0, 0, 0), (1 / 32,) * 3, (0, 2, 0))):
+        assert A.workspace_size(bad) == 0
+
+
+def _params(**kw):
+    return A.params_struct(W.default_params(**kw))
+
+
+@pytest.mark.parametrize("change", [dict(gamma=1.0), dict(rho_atm=0.0), dict(recon=7), dict(gauge=3),
+                                    dict(c2p_maxiter=0), dict(W_max=1.0), dict(use_fallback=2)])
+def test_invalid_params_rejected_on_host(change):
+    L = A.lib()
+    p = _params(**change)
+    b = A.block_struct((8, 8, 8), 3, (0, 0, 0), (0.1,) * 3, (0, 0, 0))
+    st = A.State(*([8] * 9))
+    pr = A.Prims(*([8] * 5))
+    ws_bytes = A.workspace_size(b)
+    rc = L.asterx_con2prim(ctypes.byref(p), ctypes.byref(b), ctypes.byref(st), ctypes.byref(pr), None, None,
+                           ctypes.c_void_p(256), ws_bytes, None)
+    assert rc == A.ASTERX_EINVAL
+
+
+def test_small_workspace_and_bad_pointers_rejected():
+    L = A.lib()
+    p = _params()
+    b = A.block_struct((8, 8, 8), 3, (0, 0, 0), (0.1,) * 3, (0, 0, 0))
+    st = A.State(*([8] * 9))
+    pr = A.Prims(*([8] * 5))
+    need = A.workspace_size(b)
+    rc = L.asterx_rk4_step(ctypes.byref(p), ctypes.byref(b), ctypes.c_double(0.01), ctypes.byref(st),
+                           ctypes.byref(pr), None, None, ctypes.c_void_p(256), need - 8, None)
+    assert rc == A.ASTERX_ENOMEM
+    bad = A.State(*([8] * 8 + [0]))  # a null field pointer
+    rc = L.asterx_rk4_step(ctypes.byref(p), ctypes.byref(b), ctypes.c_double(0.01), ctypes.byref(bad),
+                           ctypes.byref(pr), None, None, ctypes.c_void_p(256), need, None)
+    assert rc == A.ASTERX_EINVAL
+    rc = L.asterx_rk_stage(ctypes.byref(p), ctypes.byref(b), 4, ctypes.c_double(0.01), ctypes.byref(st),
+                           ctypes.byref(st), ctypes.byref(st), ctypes.byref(st), ctypes.byref(pr), None, None,
+                           ctypes.c_void_p(256), need, None)
+    assert rc == A.ASTERX_EINVAL  # stage out of range
+    rc = L.asterx_rk4_step(ctypes.byref(p), ctypes.byref(b), ctypes.c_double(-1.0), ctypes.byref(st),
+                           ctypes.byref(pr), None, None, ctypes.c_void_p(256), need, None)
+    assert rc == A.ASTERX_EINVAL  # dt <= 0
+    rc = L.asterx_rk4_step(ctypes.byref(p), ctypes.byref(b), ctypes.c_double(0.01), ctypes.byref(st),
+                           ctypes.byref(pr), None, None, ctypes.c_void_p(100), need, None)
+    assert rc == A.ASTERX_EINVAL  # workspace not 256-byte aligned
