@@ -161,6 +161,32 @@ asterx_status asterx_rk4_step_host(const asterx_params *p, const asterx_block *b
                                    double *const *h_U9, double *const *h_P5, asterx_state *dU, asterx_prims *dP,
                                    asterx_c2p_stats *stats, void *ws, size_t ws_bytes, asterx_stream stream);
 
+/* ---- recovery for callers that cannot allocate device memory (the paper has no counterpart) ----
+ *
+ * Some callers cannot call cudaMalloc: a plugin inside a host application that owns all device memory and
+ * hands out only the buffers it manages, or a time-critical loop that must not allocate because cudaMalloc
+ * can synchronise the device and can fail in the middle of a run.  For them this entry point runs the same
+ * recovery as asterx_con2prim (same kernels, same results) without a caller workspace: the scratch it needs
+ * (the frozen-metric centre record, the face field B~ and the centre field B) lives in one fixed-size array
+ * in the library's own device memory, which every GPU that loads the library holds until the process exits
+ * ((53 + 6) * ASTERX_NOALLOC_MAX_ENTRIES doubles, about 31 MB).  The caller still passes the inputs and
+ * outputs: the vertex metric, the state U (ghosts filled; D~, S~, tau~ reset in place for atmosphere
+ * cells), the primitives P (guess in, result out), and optional flags and counters as in asterx_con2prim.
+ * It allocates nothing and calls no allocating routine.
+ *
+ * Limits and rules:
+ *  - the padded block (n[0]+7)(n[1]+7)(n[2]+7) may hold at most ASTERX_NOALLOC_MAX_ENTRIES entries per field
+ *    (for example 33^3 interior cells); larger blocks return ASTERX_EINVAL before anything is launched;
+ *  - every call shares the one array, which keeps the last call's contents; calls that overlap on the GPU
+ *    (different streams, or different host threads without ordering) race on it and must be serialised by
+ *    the caller;
+ *  - the first call on each device looks up the array's device address (cudaGetSymbolAddress) with that
+ *    device current; make that first call before any stream capture. */
+#define ASTERX_NOALLOC_MAX_ENTRIES 65536L
+asterx_status asterx_con2prim_noalloc(const asterx_params *p, const asterx_block *blk,
+                                      const asterx_metric *metric, asterx_state *U, asterx_prims *P,
+                                      signed char *flags, asterx_c2p_stats *stats, asterx_stream stream);
+
 /* ---- measurement helpers (not part of the method) ---- */
 
 /* Start recording a CUDA event pair around each launch of the face kernel (the dominant kernel: Sec. 3.3

@@ -81,6 +81,8 @@ def lib():
         L.asterx_rk4_step.argtypes = [P, B, ctypes.c_double, S, Pr, vp, vp, vp, sz, st]
         L.asterx_rk4_step_host.argtypes = [P, B, ctypes.c_double, ctypes.POINTER(ctypes.c_void_p),
                                            ctypes.POINTER(ctypes.c_void_p), S, Pr, vp, vp, sz, st]
+        L.asterx_con2prim_noalloc.argtypes = [P, B, M, S, Pr, vp, vp, st]
+        L.asterx_con2prim_noalloc.restype = ctypes.c_int
         L.asterx_profile_enable.argtypes = [ctypes.c_int]
         L.asterx_profile_read.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
         L.asterx_profile_disable.restype = None
@@ -269,3 +271,17 @@ def profile_disable():
 def dfma_probe(out, blocks, threads, iters, stream=None):
     _check(lib().asterx_dfma_probe(ctypes.c_void_p(out.data_ptr()), int(blocks), int(threads), int(iters),
                                    _stream(stream)), "asterx_dfma_probe")
+
+
+NOALLOC_MAX_ENTRIES = 65536
+
+
+def con2prim_noalloc(params: dict, n, g, x0, dx, bc, metric, U, P, flags=None, stats=None, stream=None):
+    """asterx_con2prim_noalloc: the recovery with its scratch in the library's fixed device array (no caller
+    workspace); see include/asterx.h for the size limit and the sharing rules."""
+    p, b = params_struct(params), block_struct(n, g, x0, dx, bc)
+    m, u, pr = metric_struct(metric), state_struct(U), prims_struct(P)
+    fl = ctypes.c_void_p(flags.data_ptr()) if flags is not None else None
+    sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
+    return lib().asterx_con2prim_noalloc(ctypes.byref(p), ctypes.byref(b), ctypes.byref(m), ctypes.byref(u),
+                                         ctypes.byref(pr), fl, sp, _stream(stream))

@@ -195,6 +195,12 @@ static int grid_for(long count, int threads) {
   return (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
 }
 
+cudaError_t launch_prepare_centre(const Blk& b, const CF16& m, double* cg, cudaStream_t s) {
+  const int T = 128;
+  k_geom_centre<<<grid_for((long)b.N[0] * b.N[1] * b.N[2], T), T, 0, s>>>(b, m, cg);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prepare(const Blk& b, const CF16& m, const Ws& w, cudaStream_t s) {
   const int T = 128;
   k_geom_centre<<<grid_for((long)b.N[0] * b.N[1] * b.N[2], T), T, 0, s>>>(b, m, w.cg);

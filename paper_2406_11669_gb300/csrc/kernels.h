@@ -18,6 +18,8 @@ struct StageArgs {
 };
 
 cudaError_t launch_prepare(const Blk& b, const CF16& m, const Ws& w, cudaStream_t s);
+// only the centre record (NCG fields at cg)
+cudaError_t launch_prepare_centre(const Blk& b, const CF16& m, double* cg, cudaStream_t s);
 
 // ghost fill of the 9 state fields (with linear extrapolation of A under copy BCs) or of the 5 primitives
 cudaError_t launch_ghost_state(const Blk& b, const F9& U, cudaStream_t s);
