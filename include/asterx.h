@@ -161,6 +161,38 @@ asterx_status asterx_rk4_step_host(const asterx_params *p, const asterx_block *b
                                    double *const *h_U9, double *const *h_P5, asterx_state *dU, asterx_prims *dP,
                                    asterx_c2p_stats *stats, void *ws, size_t ws_bytes, asterx_stream stream);
 
+/* ---- batched step over many blocks of uneven sizes ----
+ *
+ * Many AMR-like blocks advance together: every kernel of the stage is launched once for all blocks, over the
+ * concatenation of the blocks' item spaces (cells, faces, edges), so small blocks do not each pay a launch per
+ * kernel and the GPU sees one large balanced launch.  The blocks are independent (no exchange between them;
+ * each keeps its own boundary conditions).  The per-block physics is exactly asterx_rk4_step's. */
+typedef struct {
+  asterx_block blk;      /* the block's geometry */
+  asterx_metric metric;  /* its frozen vertex metric (device) */
+  asterx_state U;        /* its state (device; advanced in place) */
+  asterx_prims P;        /* its primitives (device; guess in, last recovery out) */
+} asterx_batch_block;
+
+/* Bytes of the pooled workspace of a batch (0 if a block is invalid): the per-block workspaces plus the
+ * device block tables. */
+size_t asterx_batch_workspace_size(const asterx_batch_block *blocks, int nblocks);
+
+/* Derive every block's frozen-metric geometry into its slice of the pooled workspace and upload the block
+ * tables (host `blocks` array read during the call; returns after the upload has completed on `stream`). */
+asterx_status asterx_batch_prepare(const asterx_params *p, const asterx_batch_block *blocks, int nblocks,
+                                   void *ws, size_t ws_bytes, asterx_stream stream);
+
+/* Ghost fill of every block's state and its conserved variables from its primitives (Eq. cons). */
+asterx_status asterx_batch_prim2con(const asterx_params *p, const asterx_batch_block *blocks, int nblocks,
+                                    void *ws, size_t ws_bytes, asterx_stream stream);
+
+/* `nsteps` classical RK4 steps of every block (the same `blocks` array as asterx_batch_prepare); `stats`
+ * (device, may be NULL) accumulates the recovery counters of all blocks and stages. */
+asterx_status asterx_batched_step(const asterx_params *p, const asterx_batch_block *blocks, int nblocks,
+                                  double dt, int nsteps, asterx_c2p_stats *stats, void *ws, size_t ws_bytes,
+                                  asterx_stream stream);
+
 /* ---- recovery for callers that cannot allocate device memory (the paper has no counterpart) ----
  *
  * Some callers cannot call cudaMalloc: a plugin inside a host application that owns all device memory and

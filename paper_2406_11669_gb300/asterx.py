@@ -50,6 +50,10 @@ class Metric(ctypes.Structure):
                                                 "gyz", "gzz", "kxx", "kxy", "kxz", "kyy", "kyz", "kzz")]
 
 
+class BatchBlock(ctypes.Structure):
+    _fields_ = [("blk", Block), ("metric", Metric), ("U", State), ("P", Prims)]
+
+
 class C2PStats(ctypes.Structure):
     _fields_ = [("n_noble", ctypes.c_ulonglong), ("n_fallback", ctypes.c_ulonglong),
                 ("n_atm", ctypes.c_ulonglong), ("n_failed", ctypes.c_ulonglong), ("iters", ctypes.c_ulonglong)]
@@ -81,6 +85,14 @@ def lib():
         L.asterx_rk4_step.argtypes = [P, B, ctypes.c_double, S, Pr, vp, vp, vp, sz, st]
         L.asterx_rk4_step_host.argtypes = [P, B, ctypes.c_double, ctypes.POINTER(ctypes.c_void_p),
                                            ctypes.POINTER(ctypes.c_void_p), S, Pr, vp, vp, sz, st]
+        BB = ctypes.POINTER(BatchBlock)
+        L.asterx_batch_workspace_size.restype = ctypes.c_size_t
+        L.asterx_batch_workspace_size.argtypes = [BB, ctypes.c_int]
+        L.asterx_batch_prepare.argtypes = [P, BB, ctypes.c_int, vp, sz, st]
+        L.asterx_batch_prim2con.argtypes = [P, BB, ctypes.c_int, vp, sz, st]
+        L.asterx_batched_step.argtypes = [P, BB, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, vp, sz, st]
+        for name in ("asterx_batch_prepare", "asterx_batch_prim2con", "asterx_batched_step"):
+            getattr(L, name).restype = ctypes.c_int
         L.asterx_con2prim_noalloc.argtypes = [P, B, M, S, Pr, vp, vp, st]
         L.asterx_con2prim_noalloc.restype = ctypes.c_int
         L.asterx_profile_enable.argtypes = [ctypes.c_int]
@@ -285,3 +297,41 @@ def con2prim_noalloc(params: dict, n, g, x0, dx, bc, metric, U, P, flags=None, s
     sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
     return lib().asterx_con2prim_noalloc(ctypes.byref(p), ctypes.byref(b), ctypes.byref(m), ctypes.byref(u),
                                          ctypes.byref(pr), fl, sp, _stream(stream))
+
+
+class Batch:
+    """Many blocks advanced together by asterx_batched_step.  `blocks` is a list of (n, g, x0, dx, bc, metric,
+    U, P) with device tensors; all share `params`.  The pooled workspace is one torch allocation."""
+
+    def __init__(self, params: dict, blocks, device="cuda"):
+        import torch
+        self.params = dict(params)
+        self.p = params_struct(self.params)
+        self.keep = blocks  # tensors stay alive while the tables refer to them
+        arr = (BatchBlock * len(blocks))()
+        for i, (n, g, x0, dx, bc, M, U, P) in enumerate(blocks):
+            arr[i].blk = block_struct(n, g, x0, dx, bc)
+            arr[i].metric = metric_struct(M)
+            arr[i].U = state_struct(U)
+            arr[i].P = prims_struct(P)
+        self.arr = arr
+        self.nb = len(blocks)
+        self.ws_bytes = int(lib().asterx_batch_workspace_size(arr, self.nb))
+        if self.ws_bytes == 0:
+            raise AsterxError(ASTERX_EINVAL, "invalid batch")
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.ws.data_ptr()) % 256
+        self.ws_ptr = ctypes.c_void_p(self.ws.data_ptr() + off)
+
+    def prepare(self, stream=None):
+        _check(lib().asterx_batch_prepare(ctypes.byref(self.p), self.arr, self.nb, self.ws_ptr, self.ws_bytes,
+                                          _stream(stream)), "asterx_batch_prepare")
+
+    def prim2con(self, stream=None):
+        _check(lib().asterx_batch_prim2con(ctypes.byref(self.p), self.arr, self.nb, self.ws_ptr, self.ws_bytes,
+                                           _stream(stream)), "asterx_batch_prim2con")
+
+    def step(self, dt, nsteps=1, stats=None, stream=None):
+        sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
+        _check(lib().asterx_batched_step(ctypes.byref(self.p), self.arr, self.nb, float(dt), int(nsteps), sp,
+                                         self.ws_ptr, self.ws_bytes, _stream(stream)), "asterx_batched_step")

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include "../../include/asterx.h"
 #include "kernels.h"
@@ -318,6 +319,149 @@ asterx_status asterx_rk4_step_host(const asterx_params* p, const asterx_block* b
   for (int v = 0; v < 5; v++)
     if (cudaMemcpyAsync(h_P5[v], pr.f[v], bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return ASTERX_ECUDA;
   return cuda_status(cudaStreamSynchronize(s));
+}
+
+// ----------------------------------------------------------------------------------------------------------
+// Batched step.  Pooled workspace layout: [4 stage tables of nb BlockRec | NKIND x (nb+1) item offsets |
+// per-block workspaces, each on a 256-byte boundary].
+
+static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static size_t batch_header_bytes(int nb) {
+  return round_up(4 * (size_t)nb * sizeof(BlockRec) + (size_t)NKIND * (nb + 1) * sizeof(long), kAlign);
+}
+
+static bool batch_blocks_ok(const asterx_batch_block* blocks, int nb) {
+  if (!blocks || nb < 1 || nb > (1 << 20)) return false;
+  for (int i = 0; i < nb; i++)
+    if (!block_ok(&blocks[i].blk) || !set_ok<asterx_state, 9>(&blocks[i].U) ||
+        !set_ok<asterx_prims, 5>(&blocks[i].P) || !set_ok<asterx_metric, 16>(&blocks[i].metric))
+      return false;
+  return true;
+}
+
+static size_t batch_bytes(const asterx_batch_block* blocks, int nb) {
+  size_t tot = batch_header_bytes(nb);
+  for (int i = 0; i < nb; i++) tot += round_up(ws_bytes_for(&blocks[i].blk), kAlign);
+  return tot + kAlign;
+}
+
+// start of block i's workspace inside the pool
+static char* block_ws(const asterx_batch_block* blocks, int nb, void* ws, int i) {
+  size_t off = batch_header_bytes(nb);
+  for (int q = 0; q < i; q++) off += round_up(ws_bytes_for(&blocks[q].blk), kAlign);
+  return static_cast<char*>(ws) + off;
+}
+
+static asterx_status batch_checks(const asterx_params* p, const asterx_batch_block* blocks, int nb, void* ws,
+                                  size_t ws_bytes) {
+  if (!params_ok(p) || !batch_blocks_ok(blocks, nb)) return ASTERX_EINVAL;
+  if (!ws || ((uintptr_t)ws % kAlign) != 0) return ASTERX_EINVAL;
+  if (ws_bytes < batch_bytes(blocks, nb)) return ASTERX_ENOMEM;
+  return ASTERX_OK;
+}
+
+static void batch_totals(const asterx_batch_block* blocks, int nb, long* totals, long* offsets /* may be null */) {
+  for (int k = 0; k < NKIND; k++) {
+    long acc = 0;
+    for (int i = 0; i < nb; i++) {
+      if (offsets) offsets[(long)k * (nb + 1) + i] = acc;
+      acc += kind_count(k, make_blk(&blocks[i].blk));
+    }
+    if (offsets) offsets[(long)k * (nb + 1) + nb] = acc;
+    totals[k] = acc;
+  }
+}
+
+size_t asterx_batch_workspace_size(const asterx_batch_block* blocks, int nblocks) {
+  if (!batch_blocks_ok(blocks, nblocks)) return 0;
+  return batch_bytes(blocks, nblocks);
+}
+
+asterx_status asterx_batch_prepare(const asterx_params* p, const asterx_batch_block* blocks, int nblocks,
+                                   void* ws, size_t ws_bytes, asterx_stream stream) {
+  asterx_status st = batch_checks(p, blocks, nblocks, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int nb = nblocks;
+  std::vector<BlockRec> tabs(4 * (size_t)nb);
+  std::vector<long> offsets((size_t)NKIND * (nb + 1));
+  long totals[NKIND];
+  batch_totals(blocks, nb, totals, offsets.data());
+  for (int i = 0; i < nb; i++) {
+    const asterx_batch_block& bb = blocks[i];
+    StageArgs a = make_args(p, &bb.blk, block_ws(blocks, nb, ws, i));
+    CF16 m;
+    std::memcpy(m.f, &bb.metric, sizeof(m.f));
+    cudaError_t e = launch_prepare(a.b, m, a.w, s);
+    if (e != cudaSuccess) return ASTERX_ECUDA;
+    F9 u = f9(&bb.U), acc, sb[2];
+    for (int v = 0; v < 9; v++) {
+      acc.f[v] = a.w.uacc + v * a.b.V;
+      sb[0].f[v] = a.w.ustage + v * a.b.V;
+      sb[1].f[v] = a.w.ustage + (9 + v) * a.b.V;
+    }
+    for (int stage = 0; stage < 4; stage++) {
+      BlockRec& r = tabs[(size_t)stage * nb + i];
+      std::memset(&r, 0, sizeof(r));
+      r.b = a.b;
+      r.w = a.w;
+      r.Un = u;
+      r.Us = stage == 0 ? u : sb[(stage - 1) % 2];
+      r.Unext = stage == 3 ? u : sb[stage % 2];
+      r.Uacc = acc;
+      r.dU = r.Unext;
+      r.P = f5(&bb.P);
+      r.flags = nullptr;
+    }
+  }
+  char* hdr = static_cast<char*>(ws);
+  cudaError_t e = cudaMemcpyAsync(hdr, tabs.data(), tabs.size() * sizeof(BlockRec), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hdr + 4 * (size_t)nb * sizeof(BlockRec), offsets.data(), offsets.size() * sizeof(long),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host tables go out of scope
+  return cuda_status(e);
+}
+
+asterx_status asterx_batch_prim2con(const asterx_params* p, const asterx_batch_block* blocks, int nblocks,
+                                    void* ws, size_t ws_bytes, asterx_stream stream) {
+  asterx_status st = batch_checks(p, blocks, nblocks, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int i = 0; i < nblocks; i++) {
+    StageArgs a = make_args(p, &blocks[i].blk, block_ws(blocks, nblocks, ws, i));
+    F9 u = f9(&blocks[i].U);
+    cudaError_t e = launch_ghost_state(a.b, u, s);
+    if (e == cudaSuccess) e = launch_bfield(a.b, a.w, u, s);
+    if (e == cudaSuccess) e = launch_prim2con(a, u, f5(&blocks[i].P), s);
+    if (e != cudaSuccess) return ASTERX_ECUDA;
+  }
+  return ASTERX_OK;
+}
+
+asterx_status asterx_batched_step(const asterx_params* p, const asterx_batch_block* blocks, int nblocks, double dt,
+                                  int nsteps, asterx_c2p_stats* stats, void* ws, size_t ws_bytes,
+                                  asterx_stream stream) {
+  asterx_status st = batch_checks(p, blocks, nblocks, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!finite_pos(dt) || nsteps < 0) return ASTERX_EINVAL;
+  if (stats && ((uintptr_t)stats % 8) != 0) return ASTERX_EINVAL;
+  const int nb = nblocks;
+  long totals[NKIND];
+  batch_totals(blocks, nb, totals, nullptr);
+  // the stage-independent parameters are those of the first block's arguments (the same params for all)
+  StageArgs a = make_args(p, &blocks[0].blk, block_ws(blocks, nb, ws, 0));
+  const BlockRec* tab = reinterpret_cast<const BlockRec*>(ws);
+  const long* off = reinterpret_cast<const long*>(static_cast<char*>(ws) + 4 * (size_t)nb * sizeof(BlockRec));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int step = 0; step < nsteps; step++)
+    for (int stage = 0; stage < 4; stage++) {
+      cudaError_t e = launch_batch_stage(a, tab + (size_t)stage * nb, off, totals, nb, stage, dt,
+                                         reinterpret_cast<unsigned long long*>(stats), s);
+      if (e != cudaSuccess) return ASTERX_ECUDA;
+    }
+  return ASTERX_OK;
 }
 
 asterx_status asterx_profile_enable(int max_launches) {

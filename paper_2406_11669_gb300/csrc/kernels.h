@@ -40,6 +40,11 @@ cudaError_t launch_c2p(const StageArgs& a, const F9& U, const F5& P, signed char
 cudaError_t launch_rhs(const StageArgs& a, const F9& Us, const F5& P, int stage, double dt, const F9& Un,
                        const F9& Unext, const F9& Uacc, const F9& dU, cudaStream_t s);
 
+// one RK4 stage of every block of a device table (one launch per kernel); tab holds nb records of this stage,
+// off the NKIND * (nb + 1) item offsets (device), host_total the NKIND totals (host)
+cudaError_t launch_batch_stage(const StageArgs& a, const BlockRec* tab, const long* off, const long* host_total,
+                               int nb, int stage, double dt, unsigned long long* stats, cudaStream_t s);
+
 // face-kernel launch timing (measurement hook of the benchmark)
 cudaError_t profile_enable(int cap);
 void profile_disable();

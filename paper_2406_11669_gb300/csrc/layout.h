@@ -72,4 +72,56 @@ struct CF16 {
   const double* f[16];
 };
 
+// Everything one block needs during one stage: geometry, workspace, and the field sets the stage reads and
+// writes.  A single-block launch passes one record by value; a batched launch reads records from a device
+// table (one table per RK stage, since the stage buffers differ).
+struct BlockRec {
+  Blk b;
+  Ws w;
+  F9 Un, Us, Unext, Uacc, dU;
+  F5 P;
+  signed char* flags;
+};
+
+// Item spaces of the kernels (per block).  The batched launches concatenate the blocks' item spaces in
+// table order; off[kind][blk] is the first item of block blk.
+enum Kind {
+  KIND_GHOST_X = 0, KIND_GHOST_Y, KIND_GHOST_Z,
+  KIND_VERTS_ALL,    // (N+1)^3: face B~
+  KIND_CELLS_ALL,    // N^3: centre B, u, prim->cons
+  KIND_INTERIOR,     // n^3: recovery, cell update
+  KIND_RECON_X, KIND_RECON_Y, KIND_RECON_Z,
+  KIND_FACES_X, KIND_FACES_Y, KIND_FACES_Z,
+  KIND_VERTEX,       // (n+3)^3: G_A, F_Psi
+  KIND_EDGES_X, KIND_EDGES_Y, KIND_EDGES_Z,
+  KIND_PSI,          // (n+1)^3
+  NKIND
+};
+
+__host__ __device__ inline long kind_count(int kind, const Blk& b) {
+  const long N0 = b.N[0], N1 = b.N[1], N2 = b.N[2];
+  const long n0 = b.n[0], n1 = b.n[1], n2 = b.n[2];
+  const long slots = 2L * b.g + 1;
+  switch (kind) {
+    case KIND_GHOST_X: return slots * (N1 + 1) * (N2 + 1);
+    case KIND_GHOST_Y: return slots * (N2 + 1) * (N0 + 1);
+    case KIND_GHOST_Z: return slots * (N0 + 1) * (N1 + 1);
+    case KIND_VERTS_ALL: return (N0 + 1) * (N1 + 1) * (N2 + 1);
+    case KIND_CELLS_ALL: return N0 * N1 * N2;
+    case KIND_INTERIOR: return n0 * n1 * n2;
+    case KIND_RECON_X: return (n0 + 2) * N1 * N2;
+    case KIND_RECON_Y: return N0 * (n1 + 2) * N2;
+    case KIND_RECON_Z: return N0 * N1 * (n2 + 2);
+    case KIND_FACES_X: return (n0 + 1) * N1 * N2;
+    case KIND_FACES_Y: return N0 * (n1 + 1) * N2;
+    case KIND_FACES_Z: return N0 * N1 * (n2 + 1);
+    case KIND_VERTEX: return (n0 + 3) * (n1 + 3) * (n2 + 3);
+    case KIND_EDGES_X: return n0 * (n1 + 1) * (n2 + 1);
+    case KIND_EDGES_Y: return (n0 + 1) * n1 * (n2 + 1);
+    case KIND_EDGES_Z: return (n0 + 1) * (n1 + 1) * n2;
+    case KIND_PSI: return (n0 + 1) * (n1 + 1) * (n2 + 1);
+  }
+  return 0;
+}
+
 }  // namespace asterx

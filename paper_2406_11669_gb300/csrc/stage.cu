@@ -9,7 +9,12 @@
 //
 // Every intermediate lives in the workspace: the path is bound by FP64 arithmetic, not by HBM, so each
 // quantity is computed once and re-read rather than recomputed.
+//
+// Each kernel body is a functor run(record, consts, t) over the block's own item space (t = 0 .. count-1).
+// A single-block launch loops over one record's items; a batched launch loops over the items of every block
+// of a device table (block found by binary search over the per-kind prefix offsets), so both run the same code.
 #include <cstdio>
+#include <cstring>
 
 #include "kernels.h"
 #include "physics.cuh"
@@ -47,106 +52,148 @@ __host__ __device__ inline Box make_box(int l0, int h0, int l1, int h1, int l2, 
 __device__ __forceinline__ long lin(const Blk& b, int i, int j, int k) { return i + b.sy * j + b.sz * k; }
 __device__ __forceinline__ long stride(const Blk& b, int d) { return d == 0 ? 1 : (d == 1 ? b.sy : b.sz); }
 
+// Constants shared by every block of one launch.
+struct StageConsts {
+  double gamma, gfac, dt, xi;
+  int stage, lorenz;
+  C2PParams cp;
+  unsigned long long* stats;
+};
+
+// ----------------------------------------------------------------------------------------------------------
+// Launch machinery: one record by value, or a device table of records with per-kind prefix offsets.
+
+template <class Body>
+__global__ void __launch_bounds__(128) k_single(BlockRec r, StageConsts k, long count) {
+  GRID_LOOP(t, count) Body::run(r, k, t);
+}
+
+__device__ __forceinline__ int find_block(const long* __restrict__ off, int nb, long T) {
+  int lo = 0, hi = nb;  // largest lo with off[lo] <= T
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= T) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <class Body>
+__global__ void __launch_bounds__(128) k_batch(const BlockRec* __restrict__ tab, const long* __restrict__ off,
+                                                 int nb, StageConsts k) {
+  const long total = off[nb];
+  GRID_LOOP(T, total) {
+    const int blk = find_block(off, nb, T);
+    Body::run(tab[blk], k, T - off[blk]);
+  }
+}
+
+struct Single {
+  BlockRec r;
+  long count(int kind) const { return kind_count(kind, r.b); }
+};
+
+struct Batch {
+  const BlockRec* tab;     // device, nb records of this stage
+  const long* off;         // device, NKIND * (nb + 1) offsets
+  const long* host_total;  // host, NKIND totals
+  int nb;
+  long count(int kind) const { return host_total[kind]; }
+};
+
+template <class Body>
+void launch(const Single& t, const StageConsts& k, int kind, cudaStream_t s) {
+  const long n = t.count(kind);
+  if (n > 0) k_single<Body><<<grid_for(n, 128), 128, 0, s>>>(t.r, k, n);
+}
+
+template <class Body>
+void launch(const Batch& t, const StageConsts& k, int kind, cudaStream_t s) {
+  const long n = t.count(kind);
+  if (n > 0) k_batch<Body><<<grid_for(n, 128), 128, 0, s>>>(t.tab, t.off + (long)kind * (t.nb + 1), t.nb, k);
+}
+
 // ----------------------------------------------------------------------------------------------------------
 // Ghost zones (Sec. 3.8): periodic wrap, or copy of the nearest owned value; the edge potential A is
 // extrapolated linearly along the normal under copy BCs (when at least two owned layers exist).
 // A field's owned index range along an axis is [g, g+n-1] if it is cell-like there (or periodic), [g, g+n]
 // if it is vertex-like with copy BCs.  Sweeps run x, then y, then z, each over the full range of the others.
 
-struct GhostSet {
-  double* f[9];
-  int cell_like[9];  // bit a set: cell-like along axis a
-  int linear[9];
-  int nf;
+template <int AX, int NF>
+__device__ __forceinline__ void ghost_point(const Blk& b, long t, double* const* f, const int* cell_like,
+                                            const int* linear) {
+  constexpr int A1 = (AX + 1) % 3, A2 = (AX + 2) % 3;
+  const int g = b.g, n = b.n[AX], Nn = b.N[AX];
+  const long m1 = b.N[A1] + 1;
+  const int slots = 2 * g + 1;
+  const long st = stride(b, AX);
+  const int q = (int)(t % slots);
+  const long r = t / slots;
+  const int q1 = (int)(r % m1);
+  const int q2 = (int)(r / m1);
+  const int i = (q < g) ? q : Nn - 2 * g + q;
+  int p[3];
+  p[AX] = 0;
+  p[A1] = q1;
+  p[A2] = q2;
+  const long base = lin(b, p[0], p[1], p[2]);
+#pragma unroll
+  for (int fi = 0; fi < NF; fi++) {
+    const bool cl = (cell_like[fi] >> AX) & 1;
+    const int lo = g;
+    const int hi = (cl || b.bc[AX] == 0) ? g + n - 1 : g + n;
+    if (i >= lo && i <= hi) continue;
+    double* __restrict__ a = f[fi] + base;
+    double v;
+    if (b.bc[AX] == 0) {
+      const int src = lo + (((i - lo) % n) + n) % n;
+      v = a[src * st];
+    } else {
+      const int e0 = (i < lo) ? lo : hi;
+      const double f0 = a[e0 * st];
+      if (linear[fi] && hi > lo) {
+        const int e1 = (i < lo) ? lo + 1 : hi - 1;
+        const double f1 = a[e1 * st];
+        // unfused rounded operations: the extrapolated value is reproducible exactly
+        v = __dadd_rn(f0, __dmul_rn((double)(i < lo ? lo - i : i - hi), __dsub_rn(f0, f1)));
+      } else {
+        v = f0;
+      }
+    }
+    a[i * st] = v;
+  }
+}
+
+template <int AX>
+struct GhostState {  // the 9 state fields of U_s (record field Us)
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts&, long t) {
+    const int cl[9] = {7, 7, 7, 7, 7, 1, 2, 4, 0};
+    const int lin_[9] = {0, 0, 0, 0, 0, 1, 1, 1, 0};
+    ghost_point<AX, 9>(r.b, t, r.Us.f, cl, lin_);
+  }
 };
 
 template <int AX>
-__global__ void k_ghost(Blk b, GhostSet s) {
-  constexpr int A1 = (AX + 1) % 3, A2 = (AX + 2) % 3;
-  const int g = b.g, n = b.n[AX], Nn = b.N[AX];
-  const long m1 = b.N[A1] + 1, m2 = b.N[A2] + 1;
-  const int slots = 2 * g + 1;
-  const long count = slots * m1 * m2;
-  const long st = stride(b, AX);
-  GRID_LOOP(t, count) {
-    const int q = (int)(t % slots);
-    const long r = t / slots;
-    const int q1 = (int)(r % m1);
-    const int q2 = (int)(r / m1);
-    const int i = (q < g) ? q : Nn - 2 * g + q;
-    int p[3];
-    p[AX] = 0;
-    p[A1] = q1;
-    p[A2] = q2;
-    const long base = lin(b, p[0], p[1], p[2]);
-    for (int f = 0; f < s.nf; f++) {
-      const bool cl = (s.cell_like[f] >> AX) & 1;
-      const int lo = g;
-      const int hi = (cl || b.bc[AX] == 0) ? g + n - 1 : g + n;
-      if (i >= lo && i <= hi) continue;
-      double* __restrict__ a = s.f[f] + base;
-      double v;
-      if (b.bc[AX] == 0) {
-        const int src = lo + (((i - lo) % n) + n) % n;
-        v = a[src * st];
-      } else {
-        const int e0 = (i < lo) ? lo : hi;
-        const double f0 = a[e0 * st];
-        if (s.linear[f] && hi > lo) {
-          const int e1 = (i < lo) ? lo + 1 : hi - 1;
-          const double f1 = a[e1 * st];
-          v = __dadd_rn(f0, __dmul_rn((double)(i < lo ? lo - i : i - hi), __dsub_rn(f0, f1)));
-        } else {
-          v = f0;
-        }
-      }
-      a[i * st] = v;
-    }
+struct GhostPrims {  // the 5 primitives (record field P)
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts&, long t) {
+    const int cl[5] = {7, 7, 7, 7, 7};
+    const int lin_[5] = {0, 0, 0, 0, 0};
+    ghost_point<AX, 5>(r.b, t, r.P.f, cl, lin_);
   }
-}
-
-static const int STATE_CELL_LIKE[9] = {7, 7, 7, 7, 7, 1, 2, 4, 0};
-
-cudaError_t launch_ghost_state(const Blk& b, const F9& U, cudaStream_t s) {
-  GhostSet gs;
-  for (int f = 0; f < 9; f++) {
-    gs.f[f] = U.f[f];
-    gs.cell_like[f] = STATE_CELL_LIKE[f];
-    gs.linear[f] = (f >= 5 && f <= 7);
-  }
-  gs.nf = 9;
-  const int T = 256;
-  const int slots = 2 * b.g + 1;
-  k_ghost<0><<<grid_for((long)slots * (b.N[1] + 1) * (b.N[2] + 1), T), T, 0, s>>>(b, gs);
-  k_ghost<1><<<grid_for((long)slots * (b.N[2] + 1) * (b.N[0] + 1), T), T, 0, s>>>(b, gs);
-  k_ghost<2><<<grid_for((long)slots * (b.N[0] + 1) * (b.N[1] + 1), T), T, 0, s>>>(b, gs);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_ghost_prims(const Blk& b, const F5& P, cudaStream_t s) {
-  GhostSet gs;
-  for (int f = 0; f < 5; f++) {
-    gs.f[f] = P.f[f];
-    gs.cell_like[f] = 7;
-    gs.linear[f] = 0;
-  }
-  gs.nf = 5;
-  const int T = 256;
-  const int slots = 2 * b.g + 1;
-  k_ghost<0><<<grid_for((long)slots * (b.N[1] + 1) * (b.N[2] + 1), T), T, 0, s>>>(b, gs);
-  k_ghost<1><<<grid_for((long)slots * (b.N[2] + 1) * (b.N[0] + 1), T), T, 0, s>>>(b, gs);
-  k_ghost<2><<<grid_for((long)slots * (b.N[0] + 1) * (b.N[1] + 1), T), T, 0, s>>>(b, gs);
-  return cudaGetLastError();
-}
+};
 
 // ----------------------------------------------------------------------------------------------------------
 // B~^i = [ijk] d_j A_k on faces (Eq. BEulerian, second-order differences of the edge values), then the
 // undensitised centre field B^i = (B~^i_- + B~^i_+) / (2 sqrt(gamma_c)) (Sec. 3.1).
 
-__global__ void k_bface(Blk b, const double* __restrict__ Ax, const double* __restrict__ Ay,
-                        const double* __restrict__ Az, double* __restrict__ bf) {
-  Box box = make_box(0, b.N[0], 0, b.N[1], 0, b.N[2]);
-  GRID_LOOP(t, box.count()) {
+struct BFace {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts&, long t) {
+    const Blk& b = r.b;
+    const double* __restrict__ Ax = r.Us.f[5];
+    const double* __restrict__ Ay = r.Us.f[6];
+    const double* __restrict__ Az = r.Us.f[7];
+    double* __restrict__ bf = r.w.bf;
+    Box box = make_box(0, b.N[0], 0, b.N[1], 0, b.N[2]);
     int i, j, k;
     box.at(t, i, j, k);
     const long c = lin(b, i, j, k);
@@ -162,28 +209,23 @@ __global__ void k_bface(Blk b, const double* __restrict__ Ax, const double* __re
       bf[2 * b.V + c] = __dsub_rn(__dmul_rn(__dsub_rn(Ay[c + 1], Ay[c]), b.idx[0]),
                                   __dmul_rn(__dsub_rn(Ax[c + b.sy], Ax[c]), b.idx[1]));
   }
-}
+};
 
-__global__ void k_bcentre(Blk b, const double* __restrict__ bf, const double* __restrict__ cg,
-                          double* __restrict__ bc) {
-  Box box = make_box(0, b.N[0] - 1, 0, b.N[1] - 1, 0, b.N[2] - 1);
-  GRID_LOOP(t, box.count()) {
+struct BCentre {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts&, long t) {
+    const Blk& b = r.b;
+    const double* __restrict__ bf = r.w.bf;
+    double* __restrict__ bc = r.w.bc;
+    Box box = make_box(0, b.N[0] - 1, 0, b.N[1] - 1, 0, b.N[2] - 1);
     int i, j, k;
     box.at(t, i, j, k);
     const long c = lin(b, i, j, k);
-    const double sqg = cg[CG_SQG * b.V + c];
+    const double sqg = r.w.cg[CG_SQG * b.V + c];
     bc[c] = 0.5 * (bf[c] + bf[c + 1]) / sqg;
     bc[b.V + c] = 0.5 * (bf[b.V + c] + bf[b.V + c + b.sy]) / sqg;
     bc[2 * b.V + c] = 0.5 * (bf[2 * b.V + c] + bf[2 * b.V + c + b.sz]) / sqg;
   }
-}
-
-cudaError_t launch_bfield(const Blk& b, const Ws& w, const F9& U, cudaStream_t s) {
-  const int T = 256;
-  k_bface<<<grid_for(b.V, T), T, 0, s>>>(b, U.f[5], U.f[6], U.f[7], w.bf);
-  k_bcentre<<<grid_for((long)b.N[0] * b.N[1] * b.N[2], T), T, 0, s>>>(b, w.bf, w.cg, w.bc);
-  return cudaGetLastError();
-}
+};
 
 __device__ __forceinline__ void load_geo_centre(const Blk& b, const double* __restrict__ cg, long c, Geo& m) {
   m.alp = cg[CG_ALP * b.V + c];
@@ -196,192 +238,207 @@ __device__ __forceinline__ void load_geo_centre(const Blk& b, const double* __re
 }
 
 // ----------------------------------------------------------------------------------------------------------
-// Conserved variables from primitives at every cell (initial data, Eq. cons).
+// Conserved variables from primitives at every cell (initial data, Eq. cons).  Writes record field Us.
 
-__global__ void k_prim2con(Blk b, Ws w, F9 U, F5 P, double gamma, double gfac) {
-  Box box = make_box(0, b.N[0] - 1, 0, b.N[1] - 1, 0, b.N[2] - 1);
-  GRID_LOOP(t, box.count()) {
-    int i, j, k;
-    box.at(t, i, j, k);
-    const long c = lin(b, i, j, k);
+struct Prim2Con {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts& k, long t) {
+    const Blk& b = r.b;
+    Box box = make_box(0, b.N[0] - 1, 0, b.N[1] - 1, 0, b.N[2] - 1);
+    int i, j, kk;
+    box.at(t, i, j, kk);
+    const long c = lin(b, i, j, kk);
     Geo m;
-    load_geo_centre(b, w.cg, c, m);
-    const double v[3] = {P.f[2][c], P.f[3][c], P.f[4][c]};
+    load_geo_centre(b, r.w.cg, c, m);
+    const double v[3] = {r.P.f[2][c], r.P.f[3][c], r.P.f[4][c]};
     const double W = 1.0 / sqrt(1.0 - contract_sym(m.g, v, v));
     const double u[3] = {W * v[0], W * v[1], W * v[2]};
-    const double B[3] = {w.bc[c], w.bc[b.V + c], w.bc[2 * b.V + c]};
+    const double B[3] = {r.w.bc[c], r.w.bc[b.V + c], r.w.bc[2 * b.V + c]};
     SideOut o;
-    face_side(m, 1.0 / m.alp, 0, P.f[0][c], P.f[1][c], u, B, gamma, gfac, o);
-    for (int a = 0; a < 5; a++) U.f[a][c] = o.U[a];
+    face_side(m, 1.0 / m.alp, 0, r.P.f[0][c], r.P.f[1][c], u, B, k.gamma, k.gfac, o);
+    for (int a = 0; a < 5; a++) r.Us.f[a][c] = o.U[a];
   }
-}
-
-cudaError_t launch_prim2con(const StageArgs& a, const F9& U, const F5& P, cudaStream_t s) {
-  const int T = 128;
-  k_prim2con<<<grid_for((long)a.b.N[0] * a.b.N[1] * a.b.N[2], T), T, 0, s>>>(a.b, a.w, U, P, a.gamma,
-                                                                               a.gfac);
-  return cudaGetLastError();
-}
+};
 
 // ----------------------------------------------------------------------------------------------------------
 // Primitive recovery on interior cells (Sec. 3.5, 3.6): atmosphere if D~ < sqrt(gamma) rho_atm, else Noble 2D
-// seeded by the previous primitives, Palenzuela 1D fallback, atmosphere with flag -1 if both fail.
+// seeded by the previous primitives, Palenzuela 1D fallback, atmosphere with flag -1 if both fail.  The state
+// is record field Us (atmosphere resets in place), the primitives field P.
+
+struct C2PCount {
+  unsigned long long noble, fb, atm, fail, it;
+};
+
+__device__ __forceinline__ C2PCount c2p_cell(const BlockRec& r, const C2PParams& cp, long t) {
+  const Blk& b = r.b;
+  Box box = make_box(b.g, b.g + b.n[0] - 1, b.g, b.g + b.n[1] - 1, b.g, b.g + b.n[2] - 1);
+  int i, j, k;
+  box.at(t, i, j, k);
+  const long c = lin(b, i, j, k);
+  Geo m;
+  load_geo_centre(b, r.w.cg, c, m);
+  const F9& U = r.Us;
+  const F5& P = r.P;
+  const double Dt = U.f[0][c];
+  const double B[3] = {r.w.bc[c], r.w.bc[b.V + c], r.w.bc[2 * b.V + c]};
+  C2PResult res;
+  res.iters = 0;
+  bool ok = false;
+  bool atm = !(Dt >= m.sqg * cp.rho_atm);
+  int flag = 2;
+  if (!atm) {
+    const double D = Dt / m.sqg;
+    const double S[3] = {U.f[1][c] / m.sqg, U.f[2][c] / m.sqg, U.f[3][c] / m.sqg};
+    const double tau = U.f[4][c] / m.sqg;
+    double Bl[3];
+    lower(m.g, B, Bl);
+    const double B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+    const double S2 = contract_sym(m.gu, S, S);
+    const double BS = B[0] * S[0] + B[1] * S[1] + B[2] * S[2];
+    // initial guess from the previous primitives
+    const double grho = P.f[0][c], gp = P.f[1][c];
+    const double gv[3] = {P.f[2][c], P.f[3][c], P.f[4][c]};
+    const double v2max = 1.0 - 1.0 / (cp.W_max * cp.W_max);
+    double gv2 = contract_sym(m.g, gv, gv);
+    if (!(gv2 >= 0.0)) gv2 = 0.0;
+    if (gv2 > v2max) gv2 = v2max;
+    const double gW = 1.0 / sqrt(1.0 - gv2);
+    const double geps = gp / ((cp.gamma - 1.0) * grho);
+    const double gh = 1.0 + geps + gp / grho;
+    const double z0 = grho * gh * gW * gW;
+    if (z0 > 0.0 && isfinite(z0)) ok = c2p_noble(m, D, S, tau, B, S2, B2, BS, z0, gv2, cp, res);
+    flag = 0;
+    if (!ok && cp.use_fallback) {
+      ok = c2p_palenzuela(m, D, S, tau, B, S2, B2, BS, cp, res);
+      flag = 1;
+    }
+    if (!ok) {
+      flag = -1;
+      atm = true;
+    }
+  }
+  if (atm) {
+    res.rho = cp.rho_atm;
+    res.press = cp.K_atm * pow(cp.rho_atm, cp.gamma_atm);
+    res.v[0] = res.v[1] = res.v[2] = 0.0;
+    // conserved variables of the atmosphere state (v = 0, W = 1, b^2 = B^2), field kept (Sec. 3.6)
+    double Bl[3];
+    lower(m.g, B, Bl);
+    const double B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+    U.f[0][c] = m.sqg * res.rho;
+    U.f[1][c] = 0.0;
+    U.f[2][c] = 0.0;
+    U.f[3][c] = 0.0;
+    U.f[4][c] = m.sqg * (res.press / (cp.gamma_atm - 1.0) + 0.5 * B2);
+  }
+  P.f[0][c] = res.rho;
+  P.f[1][c] = res.press;
+  P.f[2][c] = res.v[0];
+  P.f[3][c] = res.v[1];
+  P.f[4][c] = res.v[2];
+  if (r.flags) r.flags[c] = (signed char)flag;
+  C2PCount out = {0, 0, 0, 0, (unsigned long long)res.iters};
+  if (flag == 0) out.noble = 1;
+  else if (flag == 1) out.fb = 1;
+  else if (flag == 2) out.atm = 1;
+  else out.fail = 1;
+  return out;
+}
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
 
-__global__ void k_c2p(Blk b, Ws w, F9 U, F5 P, C2PParams cp, signed char* __restrict__ flags,
-                      unsigned long long* __restrict__ stats) {
-  Box box = make_box(b.g, b.g + b.n[0] - 1, b.g, b.g + b.n[1] - 1, b.g, b.g + b.n[2] - 1);
-  const long count = box.count();
-  // the grid-stride loop is padded to whole warps so that the counter reduction sees full warps
-  const long padded = (count + 31) / 32 * 32;
-  GRID_LOOP(t, padded) {
-    unsigned long long c_noble = 0, c_fb = 0, c_atm = 0, c_fail = 0, c_it = 0;
-    if (t < count) {
-      int i, j, k;
-      box.at(t, i, j, k);
-      const long c = lin(b, i, j, k);
-      Geo m;
-      load_geo_centre(b, w.cg, c, m);
-      const double Dt = U.f[0][c];
-      const double B[3] = {w.bc[c], w.bc[b.V + c], w.bc[2 * b.V + c]};
-      C2PResult r;
-      r.iters = 0;
-      bool ok = false;
-      bool atm = !(Dt >= m.sqg * cp.rho_atm);
-      int flag = 2;
-      if (!atm) {
-        const double D = Dt / m.sqg;
-        const double S[3] = {U.f[1][c] / m.sqg, U.f[2][c] / m.sqg, U.f[3][c] / m.sqg};
-        const double tau = U.f[4][c] / m.sqg;
-        double Bl[3];
-        lower(m.g, B, Bl);
-        const double B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
-        const double S2 = contract_sym(m.gu, S, S);
-        const double BS = B[0] * S[0] + B[1] * S[1] + B[2] * S[2];
-        // initial guess from the previous primitives
-        const double grho = P.f[0][c], gp = P.f[1][c];
-        const double gv[3] = {P.f[2][c], P.f[3][c], P.f[4][c]};
-        const double v2max = 1.0 - 1.0 / (cp.W_max * cp.W_max);
-        double gv2 = contract_sym(m.g, gv, gv);
-        if (!(gv2 >= 0.0)) gv2 = 0.0;
-        if (gv2 > v2max) gv2 = v2max;
-        const double gW = 1.0 / sqrt(1.0 - gv2);
-        const double geps = gp / ((cp.gamma - 1.0) * grho);
-        const double gh = 1.0 + geps + gp / grho;
-        const double z0 = grho * gh * gW * gW;
-        if (z0 > 0.0 && isfinite(z0)) ok = c2p_noble(m, D, S, tau, B, S2, B2, BS, z0, gv2, cp, r);
-        flag = 0;
-        if (!ok && cp.use_fallback) {
-          ok = c2p_palenzuela(m, D, S, tau, B, S2, B2, BS, cp, r);
-          flag = 1;
-        }
-        if (!ok) {
-          flag = -1;
-          atm = true;
-        }
-      }
-      if (atm) {
-        r.rho = cp.rho_atm;
-        r.press = cp.K_atm * pow(cp.rho_atm, cp.gamma_atm);
-        r.v[0] = r.v[1] = r.v[2] = 0.0;
-        // conserved variables of the atmosphere state (v = 0, W = 1, b^2 = B^2), field kept (Sec. 3.6)
-        double Bl[3];
-        lower(m.g, B, Bl);
-        const double B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
-        U.f[0][c] = m.sqg * r.rho;
-        U.f[1][c] = 0.0;
-        U.f[2][c] = 0.0;
-        U.f[3][c] = 0.0;
-        U.f[4][c] = m.sqg * (r.press / (cp.gamma_atm - 1.0) + 0.5 * B2);
-      }
-      P.f[0][c] = r.rho;
-      P.f[1][c] = r.press;
-      P.f[2][c] = r.v[0];
-      P.f[3][c] = r.v[1];
-      P.f[4][c] = r.v[2];
-      if (flags) flags[c] = (signed char)flag;
-      c_it = r.iters;
-      if (flag == 0) c_noble = 1;
-      else if (flag == 1) c_fb = 1;
-      else if (flag == 2) c_atm = 1;
-      else c_fail = 1;
-    }
-    if (stats) {
-      c_noble = warp_sum(c_noble);
-      c_fb = warp_sum(c_fb);
-      c_atm = warp_sum(c_atm);
-      c_fail = warp_sum(c_fail);
-      c_it = warp_sum(c_it);
-      if ((threadIdx.x & 31) == 0) {
-        if (c_noble) atomicAdd(stats + 0, c_noble);
-        if (c_fb) atomicAdd(stats + 1, c_fb);
-        if (c_atm) atomicAdd(stats + 2, c_atm);
-        if (c_fail) atomicAdd(stats + 3, c_fail);
-        if (c_it) atomicAdd(stats + 4, c_it);
-      }
-    }
+__device__ __forceinline__ void add_counts(C2PCount c, unsigned long long* stats) {
+  c.noble = warp_sum(c.noble);
+  c.fb = warp_sum(c.fb);
+  c.atm = warp_sum(c.atm);
+  c.fail = warp_sum(c.fail);
+  c.it = warp_sum(c.it);
+  if ((threadIdx.x & 31) == 0) {
+    if (c.noble) atomicAdd(stats + 0, c.noble);
+    if (c.fb) atomicAdd(stats + 1, c.fb);
+    if (c.atm) atomicAdd(stats + 2, c.atm);
+    if (c.fail) atomicAdd(stats + 3, c.fail);
+    if (c.it) atomicAdd(stats + 4, c.it);
   }
 }
 
-cudaError_t launch_c2p(const StageArgs& a, const F9& U, const F5& P, signed char* flags,
-                       unsigned long long* stats, cudaStream_t s) {
-  C2PParams cp;
-  cp.gamma = a.gamma;
-  cp.rho_atm = a.rho_atm;
-  cp.K_atm = a.K_atm;
-  cp.gamma_atm = a.gamma_atm;
-  cp.tol = a.c2p_tol;
-  cp.W_max = a.W_max;
-  cp.maxiter = a.c2p_maxiter;
-  cp.brent_maxiter = a.brent_maxiter;
-  cp.use_fallback = a.use_fallback;
-  const int T = 128;  // a multiple of 32: whole warps take part in the counter reduction
-  const long count = (long)a.b.n[0] * a.b.n[1] * a.b.n[2];
-  k_c2p<<<grid_for(count, T), T, 0, s>>>(a.b, a.w, U, P, cp, flags, stats);
-  return cudaGetLastError();
+// The grid-stride loops are padded to whole warps so that the counter reduction sees full warps (the block
+// size is a multiple of 32 and so is the padded count).
+__global__ void __launch_bounds__(128) k_c2p_single(BlockRec r, StageConsts k, long count) {
+  const long padded = (count + 31) / 32 * 32;
+  GRID_LOOP(t, padded) {
+    C2PCount c = {0, 0, 0, 0, 0};
+    if (t < count) c = c2p_cell(r, k.cp, t);
+    if (k.stats) add_counts(c, k.stats);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_c2p_batch(const BlockRec* __restrict__ tab, const long* __restrict__ off,
+                                                     int nb, StageConsts k) {
+  const long total = off[nb];
+  const long padded = (total + 31) / 32 * 32;
+  GRID_LOOP(T, padded) {
+    C2PCount c = {0, 0, 0, 0, 0};
+    if (T < total) {
+      const int blk = find_block(off, nb, T);
+      c = c2p_cell(tab[blk], k.cp, T - off[blk]);
+    }
+    if (k.stats) add_counts(c, k.stats);
+  }
+}
+
+static void launch_c2p_kind(const Single& t, const StageConsts& k, cudaStream_t s) {
+  const long n = t.count(KIND_INTERIOR);
+  if (n > 0) k_c2p_single<<<grid_for(n, 128), 128, 0, s>>>(t.r, k, n);
+}
+
+static void launch_c2p_kind(const Batch& t, const StageConsts& k, cudaStream_t s) {
+  const long n = t.count(KIND_INTERIOR);
+  if (n > 0)
+    k_c2p_batch<<<grid_for(n, 128), 128, 0, s>>>(t.tab, t.off + (long)KIND_INTERIOR * (t.nb + 1), t.nb, k);
 }
 
 // ----------------------------------------------------------------------------------------------------------
 // u^i = W v^i at every cell (the reconstructed velocity variable).
 
-__global__ void k_uvel(Blk b, Ws w, F5 P) {
-  Box box = make_box(0, b.N[0] - 1, 0, b.N[1] - 1, 0, b.N[2] - 1);
-  GRID_LOOP(t, box.count()) {
+struct UVel {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts&, long t) {
+    const Blk& b = r.b;
+    Box box = make_box(0, b.N[0] - 1, 0, b.N[1] - 1, 0, b.N[2] - 1);
     int i, j, k;
     box.at(t, i, j, k);
     const long c = lin(b, i, j, k);
     double g6[6];
-    for (int a = 0; a < 6; a++) g6[a] = w.cg[(CG_G + a) * b.V + c];
-    const double v[3] = {P.f[2][c], P.f[3][c], P.f[4][c]};
+    for (int a = 0; a < 6; a++) g6[a] = r.w.cg[(CG_G + a) * b.V + c];
+    const double v[3] = {r.P.f[2][c], r.P.f[3][c], r.P.f[4][c]};
     const double W = 1.0 / sqrt(1.0 - contract_sym(g6, v, v));
-    w.uvel[c] = W * v[0];
-    w.uvel[b.V + c] = W * v[1];
-    w.uvel[2 * b.V + c] = W * v[2];
+    r.w.uvel[c] = W * v[0];
+    r.w.uvel[b.V + c] = W * v[1];
+    r.w.uvel[2 * b.V + c] = W * v[2];
   }
-}
+};
 
 // ----------------------------------------------------------------------------------------------------------
 // Reconstruction along D of each cell once (cells g-1 .. g+n along D, all transverse cells): the values at the
 // cell's lower and upper D-faces of rho, p, u^x, u^y, u^z and the two transverse centre B components.
 
 template <int D, int SCHEME>
-__global__ void k_recon(Blk b, Ws w, F5 P) {
-  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-  int lo[3] = {0, 0, 0}, hi[3] = {b.N[0] - 1, b.N[1] - 1, b.N[2] - 1};
-  lo[D] = b.g - 1;
-  hi[D] = b.g + b.n[D];
-  Box box = make_box(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
-  const long st = stride(b, D);
-  GRID_LOOP(t, box.count()) {
+struct Recon {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts&, long t) {
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    const Blk& b = r.b;
+    int lo[3] = {0, 0, 0}, hi[3] = {b.N[0] - 1, b.N[1] - 1, b.N[2] - 1};
+    lo[D] = b.g - 1;
+    hi[D] = b.g + b.n[D];
+    Box box = make_box(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
+    const long st = stride(b, D);
     int i, j, k;
     box.at(t, i, j, k);
     const long c = lin(b, i, j, k);
-    const double* src[NREC] = {P.f[0], P.f[1], w.uvel, w.uvel + b.V, w.uvel + 2 * b.V, w.bc + T1 * b.V,
-                               w.bc + T2 * b.V};
+    const double* src[NREC] = {r.P.f[0], r.P.f[1], r.w.uvel, r.w.uvel + b.V, r.w.uvel + 2 * b.V,
+                               r.w.bc + T1 * b.V, r.w.bc + T2 * b.V};
 #pragma unroll
     for (int v = 0; v < NREC; v++) {
       double a[5];
@@ -389,28 +446,29 @@ __global__ void k_recon(Blk b, Ws w, F5 P) {
       for (int s = 0; s < 5; s++) a[s] = src[v][c + (s - 2) * st];
       double l, h;
       recon5<SCHEME>(a, l, h);
-      w.rec[v * b.V + c] = l;
-      w.rec[(NREC + v) * b.V + c] = h;
+      r.w.rec[v * b.V + c] = l;
+      r.w.rec[(NREC + v) * b.V + c] = h;
     }
   }
-}
+};
 
 // Face solve along D for faces g..g+n along D and all transverse indices: left state = upper value of cell
 // f-1, right state = lower value of cell f; HLLE (Eq. HLLEfluxes) and the upwind velocities of Eq. uct1.
 template <int D>
-__global__ void __launch_bounds__(128) k_faces(Blk b, Ws w, double gamma, double gfac) {
-  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-  int lo[3] = {0, 0, 0}, hi[3] = {b.N[0] - 1, b.N[1] - 1, b.N[2] - 1};
-  lo[D] = b.g;
-  hi[D] = b.g + b.n[D];
-  Box box = make_box(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
-  const long st = stride(b, D);
-  const double* __restrict__ fg = w.fg + (long)D * NFG * b.V;
-  double* __restrict__ fd = w.face + (long)D * NFD * b.V;
-  GRID_LOOP(t, box.count()) {
-    int i, j, k;
-    box.at(t, i, j, k);
-    const long c = lin(b, i, j, k);
+struct Faces {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts& k, long t) {
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    const Blk& b = r.b;
+    int lo[3] = {0, 0, 0}, hi[3] = {b.N[0] - 1, b.N[1] - 1, b.N[2] - 1};
+    lo[D] = b.g;
+    hi[D] = b.g + b.n[D];
+    Box box = make_box(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
+    const long st = stride(b, D);
+    const double* __restrict__ fg = r.w.fg + (long)D * NFG * b.V;
+    double* __restrict__ fd = r.w.face + (long)D * NFD * b.V;
+    int i, j, kk;
+    box.at(t, i, j, kk);
+    const long c = lin(b, i, j, kk);
     Geo m;
     m.alp = fg[FG_ALP * b.V + c];
     for (int a = 0; a < 3; a++) m.beta[a] = fg[(FG_BETA + a) * b.V + c];
@@ -420,18 +478,18 @@ __global__ void __launch_bounds__(128) k_faces(Blk b, Ws w, double gamma, double
     }
     m.sqg = fg[FG_SQG * b.V + c];
     const double ia = fg[FG_IALP * b.V + c];
-    const double Bn = w.bf[D * b.V + c] / m.sqg;
+    const double Bn = r.w.bf[D * b.V + c] / m.sqg;
     SideOut s[2];
 #pragma unroll
     for (int side = 0; side < 2; side++) {
       const long cc = side == 0 ? c - st : c;
-      const double* __restrict__ r = w.rec + (side == 0 ? NREC : 0) * b.V + cc;
-      const double u[3] = {r[2 * b.V], r[3 * b.V], r[4 * b.V]};
+      const double* __restrict__ rr = r.w.rec + (side == 0 ? NREC : 0) * b.V + cc;
+      const double u[3] = {rr[2 * b.V], rr[3 * b.V], rr[4 * b.V]};
       double B[3];
       B[D] = Bn;
-      B[T1] = r[5 * b.V];
-      B[T2] = r[6 * b.V];
-      face_side(m, ia, D, r[0], r[b.V], u, B, gamma, gfac, s[side]);
+      B[T1] = rr[5 * b.V];
+      B[T2] = rr[6 * b.V];
+      face_side(m, ia, D, rr[0], rr[b.V], u, B, k.gamma, k.gfac, s[side]);
     }
     const double cmax = fmax(0.0, fmax(s[0].lp, s[1].lp));
     const double cmin = -fmin(0.0, fmin(s[0].lm, s[1].lm));
@@ -451,37 +509,39 @@ __global__ void __launch_bounds__(128) k_faces(Blk b, Ws w, double gamma, double
     fd[FD_CMAX * b.V + c] = cmax;
     fd[FD_CMIN * b.V + c] = cmin;
   }
-}
+};
 
 // ----------------------------------------------------------------------------------------------------------
 // RK4 combine (classical): stage < 0 writes dU/dt.
 
-__device__ __forceinline__ void combine(int stage, double dt, long c, int v, double k, const F9& Un,
-                                        const F9& Unext, const F9& Uacc, const F9& dU) {
+__device__ __forceinline__ void combine(int stage, double dt, long c, int v, double k, const BlockRec& r) {
   if (stage < 0) {
-    dU.f[v][c] = k;
+    r.dU.f[v][c] = k;
   } else if (stage == 0) {
-    Uacc.f[v][c] = (1.0 / 6.0) * dt * k;
-    Unext.f[v][c] = Un.f[v][c] + 0.5 * dt * k;
+    r.Uacc.f[v][c] = (1.0 / 6.0) * dt * k;
+    r.Unext.f[v][c] = r.Un.f[v][c] + 0.5 * dt * k;
   } else if (stage == 1) {
-    Uacc.f[v][c] = Uacc.f[v][c] + (1.0 / 3.0) * dt * k;
-    Unext.f[v][c] = Un.f[v][c] + 0.5 * dt * k;
+    r.Uacc.f[v][c] = r.Uacc.f[v][c] + (1.0 / 3.0) * dt * k;
+    r.Unext.f[v][c] = r.Un.f[v][c] + 0.5 * dt * k;
   } else if (stage == 2) {
-    Uacc.f[v][c] = Uacc.f[v][c] + (1.0 / 3.0) * dt * k;
-    Unext.f[v][c] = Un.f[v][c] + 1.0 * dt * k;
+    r.Uacc.f[v][c] = r.Uacc.f[v][c] + (1.0 / 3.0) * dt * k;
+    r.Unext.f[v][c] = r.Un.f[v][c] + 1.0 * dt * k;
   } else {
-    Unext.f[v][c] = Un.f[v][c] + Uacc.f[v][c] + (1.0 / 6.0) * dt * k;
+    r.Unext.f[v][c] = r.Un.f[v][c] + r.Uacc.f[v][c] + (1.0 / 6.0) * dt * k;
   }
 }
 
 // G_A = alpha Psi / sqrt(gamma) - beta^j A_j and F_Psi^j = alpha sqrt(gamma) gamma^jk A_k - beta^j Psi at
 // vertices, with A_j averaged from the two adjacent j-edges (Sec. 3.4).
-__global__ void k_vertex(Blk b, Ws w, F9 U, int lorenz) {
-  Box box = make_box(b.g - 1, b.g + b.n[0] + 1, b.g - 1, b.g + b.n[1] + 1, b.g - 1, b.g + b.n[2] + 1);
-  GRID_LOOP(t, box.count()) {
-    int i, j, k;
-    box.at(t, i, j, k);
-    const long c = lin(b, i, j, k);
+struct Vertex {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts& k, long t) {
+    const Blk& b = r.b;
+    const Ws& w = r.w;
+    const F9& U = r.Us;
+    Box box = make_box(b.g - 1, b.g + b.n[0] + 1, b.g - 1, b.g + b.n[1] + 1, b.g - 1, b.g + b.n[2] + 1);
+    int i, j, kk;
+    box.at(t, i, j, kk);
+    const long c = lin(b, i, j, kk);
     const double Av[3] = {0.5 * (U.f[5][c - 1] + U.f[5][c]), 0.5 * (U.f[6][c - b.sy] + U.f[6][c]),
                           0.5 * (U.f[7][c - b.sz] + U.f[7][c])};
     const double alp = w.vg[VG_ALP * b.V + c];
@@ -492,13 +552,13 @@ __global__ void k_vertex(Blk b, Ws w, F9 U, int lorenz) {
     for (int a = 0; a < 6; a++) gu[a] = w.vg[(VG_GU + a) * b.V + c];
     const double psi = U.f[8][c];
     const double bA = bx * Av[0] + by * Av[1] + bz * Av[2];
-    w.ga[c] = lorenz ? (alp * psi / sqg - bA) : 0.0;
+    w.ga[c] = k.lorenz ? (alp * psi / sqg - bA) : 0.0;
     const double as = alp * sqg;
     w.fpsi[c] = as * (gu[0] * Av[0] + gu[1] * Av[1] + gu[2] * Av[2]) - bx * psi;
     w.fpsi[b.V + c] = as * (gu[1] * Av[0] + gu[3] * Av[1] + gu[4] * Av[2]) - by * psi;
     w.fpsi[2 * b.V + c] = as * (gu[2] * Av[0] + gu[4] * Av[1] + gu[5] * Av[2]) - bz * psi;
   }
-}
+};
 
 // PPM value at the interface between stencil positions 2 and 3 of f[0..5]
 __device__ __forceinline__ void ppm_interface(const double f[6], double& L, double& R) {
@@ -514,16 +574,17 @@ __device__ __forceinline__ void ppm_interface(const double f[6], double& L, doub
 // products reconstructed with PPM to the edge from the faces normal to d2 (resp. d1), speeds a_+- at the edge
 // the maximum over the two faces sharing it; then dA_E/dt = -E_E - d_E G_A.
 template <int E>
-__global__ void __launch_bounds__(128) k_edges(Blk b, Ws w, int stage, double dt, F9 Un, F9 Unext, F9 Uacc,
-                                                 F9 dU) {
-  constexpr int D1 = (E + 1) % 3, D2 = (E + 2) % 3;
-  int lo[3] = {b.g, b.g, b.g}, hi[3] = {b.g + b.n[0], b.g + b.n[1], b.g + b.n[2]};
-  hi[E] -= 1;
-  Box box = make_box(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
-  GRID_LOOP(t, box.count()) {
-    int i, j, k;
-    box.at(t, i, j, k);
-    const long c = lin(b, i, j, k);
+struct Edges {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts& k, long t) {
+    constexpr int D1 = (E + 1) % 3, D2 = (E + 2) % 3;
+    const Blk& b = r.b;
+    const Ws& w = r.w;
+    int lo[3] = {b.g, b.g, b.g}, hi[3] = {b.g + b.n[0], b.g + b.n[1], b.g + b.n[2]};
+    hi[E] -= 1;
+    Box box = make_box(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
+    int i, j, kk;
+    box.at(t, i, j, kk);
+    const long c = lin(b, i, j, kk);
     double term[2];
 #pragma unroll
     for (int tt = 0; tt < 2; tt++) {
@@ -554,28 +615,29 @@ __global__ void __launch_bounds__(128) k_edges(Blk b, Ws w, int stage, double dt
     }
     const double Ee = -term[0] + term[1];
     const double dG = (w.ga[c + stride(b, E)] - w.ga[c]) / b.dx[E];
-    combine(stage, dt, c, 5 + E, -Ee - dG, Un, Unext, Uacc, dU);
+    combine(k.stage, k.dt, c, 5 + E, -Ee - dG, r);
   }
-}
+};
 
 // dPsi/dt = -d_j F_Psi^j - xi alpha Psi at vertices g..g+n (Eq. recastedScalarPot).
-__global__ void k_psi(Blk b, Ws w, F9 Us, int lorenz, double xi, int stage, double dt, F9 Un, F9 Unext, F9 Uacc,
-                      F9 dU) {
-  Box box = make_box(b.g, b.g + b.n[0], b.g, b.g + b.n[1], b.g, b.g + b.n[2]);
-  GRID_LOOP(t, box.count()) {
-    int i, j, k;
-    box.at(t, i, j, k);
-    const long c = lin(b, i, j, k);
-    double r = 0.0;
-    if (lorenz) {
+struct Psi {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts& k, long t) {
+    const Blk& b = r.b;
+    const Ws& w = r.w;
+    Box box = make_box(b.g, b.g + b.n[0], b.g, b.g + b.n[1], b.g, b.g + b.n[2]);
+    int i, j, kk;
+    box.at(t, i, j, kk);
+    const long c = lin(b, i, j, kk);
+    double rr = 0.0;
+    if (k.lorenz) {
       const double div = (w.fpsi[c + 1] - w.fpsi[c - 1]) / (2.0 * b.dx[0]) +
                          (w.fpsi[b.V + c + b.sy] - w.fpsi[b.V + c - b.sy]) / (2.0 * b.dx[1]) +
                          (w.fpsi[2 * b.V + c + b.sz] - w.fpsi[2 * b.V + c - b.sz]) / (2.0 * b.dx[2]);
-      r = -div - xi * w.vg[VG_ALP * b.V + c] * Us.f[8][c];
+      rr = -div - k.xi * w.vg[VG_ALP * b.V + c] * r.Us.f[8][c];
     }
-    combine(stage, dt, c, 8, r, Un, Unext, Uacc, dU);
+    combine(k.stage, k.dt, c, 8, rr, r);
   }
-}
+};
 
 // Source terms (Eq. grmhdsrc in 3+1 form with the input K_ij, K = -1/2 L_n gamma of Sec. 2.1):
 //   tau~: alpha sqrt(g) [T^00 (b^i b^j K_ij - b^i d_i alpha) + T^0i (2 b^j K_ij - d_i alpha) + T^ij K_ij]
@@ -644,33 +706,36 @@ __device__ __forceinline__ void sources(const Geo& m, const double* __restrict__
 }
 
 // Interior cells: dU/dt = -sum_d (F_d(+) - F_d(-)) / dx_d + S (Eq. fluxconseqs, densitised).
-__global__ void __launch_bounds__(128) k_cells(Blk b, Ws w, F5 P, double gfac, int stage, double dt, F9 Un,
-                                                 F9 Unext, F9 Uacc, F9 dU) {
-  Box box = make_box(b.g, b.g + b.n[0] - 1, b.g, b.g + b.n[1] - 1, b.g, b.g + b.n[2] - 1);
-  GRID_LOOP(t, box.count()) {
-    int i, j, k;
-    box.at(t, i, j, k);
-    const long c = lin(b, i, j, k);
-    double r[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+struct Cells {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts& k, long t) {
+    const Blk& b = r.b;
+    const Ws& w = r.w;
+    Box box = make_box(b.g, b.g + b.n[0] - 1, b.g, b.g + b.n[1] - 1, b.g, b.g + b.n[2] - 1);
+    int i, j, kk;
+    box.at(t, i, j, kk);
+    const long c = lin(b, i, j, kk);
+    double rr[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       const double* __restrict__ fd = w.face + (long)d * NFD * b.V;
       const long c1 = c + stride(b, d);
 #pragma unroll
-      for (int v = 0; v < 5; v++) r[v] -= (fd[(FD_F + v) * b.V + c1] - fd[(FD_F + v) * b.V + c]) / b.dx[d];
+      for (int v = 0; v < 5; v++) rr[v] -= (fd[(FD_F + v) * b.V + c1] - fd[(FD_F + v) * b.V + c]) / b.dx[d];
     }
     Geo m;
     load_geo_centre(b, w.cg, c, m);
-    const double v[3] = {P.f[2][c], P.f[3][c], P.f[4][c]};
+    const double v[3] = {r.P.f[2][c], r.P.f[3][c], r.P.f[4][c]};
     const double B[3] = {w.bc[c], w.bc[b.V + c], w.bc[2 * b.V + c]};
     double src[5];
-    sources(m, w.cg, b.V, c, P.f[0][c], P.f[1][c], v, B, gfac, src);
+    sources(m, w.cg, b.V, c, r.P.f[0][c], r.P.f[1][c], v, B, k.gfac, src);
 #pragma unroll
-    for (int q = 0; q < 5; q++) combine(stage, dt, c, q, r[q] + src[q], Un, Unext, Uacc, dU);
+    for (int q = 0; q < 5; q++) combine(k.stage, k.dt, c, q, rr[q] + src[q], r);
   }
-}
+};
 
-// Measurement hook: when enabled, an event pair brackets every face-kernel launch on its own stream.
+// ----------------------------------------------------------------------------------------------------------
+// Measurement hook: when enabled, an event pair brackets every face-kernel launch on its own stream (not
+// while the stream is being captured into a graph).
 namespace {
 struct FaceProfile {
   bool on = false;
@@ -679,6 +744,12 @@ struct FaceProfile {
   cudaEvent_t* ev = nullptr;  // 2 * cap events
 };
 FaceProfile g_prof;
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &st);
+  return st != cudaStreamCaptureStatusNone;
+}
 }  // namespace
 
 cudaError_t profile_enable(int cap) {
@@ -721,39 +792,168 @@ cudaError_t profile_read(int* launches, double* total_ms) {
   return cudaSuccess;
 }
 
-template <int D>
-static void launch_dir(const StageArgs& a, const F5& P, cudaStream_t s) {
-  const Blk& b = a.b;
-  long rc = (long)b.N[0] * b.N[1] * b.N[2] / b.N[D] * (b.n[D] + 2);
-  const int T = 128;
-  if (a.recon == 0) k_recon<D, 0><<<grid_for(rc, T), T, 0, s>>>(b, a.w, P);
-  else if (a.recon == 1) k_recon<D, 1><<<grid_for(rc, T), T, 0, s>>>(b, a.w, P);
-  else k_recon<D, 2><<<grid_for(rc, T), T, 0, s>>>(b, a.w, P);
-  long fc = (long)b.N[0] * b.N[1] * b.N[2] / b.N[D] * (b.n[D] + 1);
-  const bool mark = g_prof.on && g_prof.n < g_prof.cap;
+// ----------------------------------------------------------------------------------------------------------
+// Stage sequences, written once for both launch targets.
+
+static StageConsts consts_of(const StageArgs& a, int stage, double dt, unsigned long long* stats) {
+  StageConsts k;
+  k.gamma = a.gamma;
+  k.gfac = a.gfac;
+  k.dt = dt;
+  k.xi = a.xi > 0.0 ? a.xi : (dt > 0.0 ? 1.5 / dt : 0.0);
+  k.stage = stage;
+  k.lorenz = (a.gauge == 0);
+  k.cp.gamma = a.gamma;
+  k.cp.rho_atm = a.rho_atm;
+  k.cp.K_atm = a.K_atm;
+  k.cp.gamma_atm = a.gamma_atm;
+  k.cp.tol = a.c2p_tol;
+  k.cp.W_max = a.W_max;
+  k.cp.maxiter = a.c2p_maxiter;
+  k.cp.brent_maxiter = a.brent_maxiter;
+  k.cp.use_fallback = a.use_fallback;
+  k.stats = stats;
+  return k;
+}
+
+template <class T>
+static void seq_ghost_state(const T& t, const StageConsts& k, cudaStream_t s) {
+  launch<GhostState<0>>(t, k, KIND_GHOST_X, s);
+  launch<GhostState<1>>(t, k, KIND_GHOST_Y, s);
+  launch<GhostState<2>>(t, k, KIND_GHOST_Z, s);
+}
+
+template <class T>
+static void seq_ghost_prims(const T& t, const StageConsts& k, cudaStream_t s) {
+  launch<GhostPrims<0>>(t, k, KIND_GHOST_X, s);
+  launch<GhostPrims<1>>(t, k, KIND_GHOST_Y, s);
+  launch<GhostPrims<2>>(t, k, KIND_GHOST_Z, s);
+}
+
+template <class T>
+static void seq_bfield(const T& t, const StageConsts& k, cudaStream_t s) {
+  launch<BFace>(t, k, KIND_VERTS_ALL, s);
+  launch<BCentre>(t, k, KIND_CELLS_ALL, s);
+}
+
+template <int D, class T>
+static void seq_dir(const T& t, const StageConsts& k, int recon, cudaStream_t s) {
+  if (recon == 0) launch<Recon<D, 0>>(t, k, KIND_RECON_X + D, s);
+  else if (recon == 1) launch<Recon<D, 1>>(t, k, KIND_RECON_X + D, s);
+  else launch<Recon<D, 2>>(t, k, KIND_RECON_X + D, s);
+  const bool mark = g_prof.on && g_prof.n < g_prof.cap && !capturing(s);
   if (mark) cudaEventRecord(g_prof.ev[2 * g_prof.n], s);
-  k_faces<D><<<grid_for(fc, T), T, 0, s>>>(b, a.w, a.gamma, a.gfac);
+  launch<Faces<D>>(t, k, KIND_FACES_X + D, s);
   if (mark) cudaEventRecord(g_prof.ev[2 * g_prof.n++ + 1], s);
+}
+
+template <class T>
+static void seq_rhs(const T& t, const StageConsts& k, int recon, cudaStream_t s) {
+  launch<UVel>(t, k, KIND_CELLS_ALL, s);
+  seq_dir<0>(t, k, recon, s);
+  seq_dir<1>(t, k, recon, s);
+  seq_dir<2>(t, k, recon, s);
+  launch<Vertex>(t, k, KIND_VERTEX, s);
+  launch<Edges<0>>(t, k, KIND_EDGES_X, s);
+  launch<Edges<1>>(t, k, KIND_EDGES_Y, s);
+  launch<Edges<2>>(t, k, KIND_EDGES_Z, s);
+  launch<Psi>(t, k, KIND_PSI, s);
+  launch<Cells>(t, k, KIND_INTERIOR, s);
+}
+
+template <class T>
+static void seq_stage(const T& t, const StageConsts& k, int recon, cudaStream_t s) {
+  seq_ghost_state(t, k, s);
+  seq_bfield(t, k, s);
+  launch_c2p_kind(t, k, s);
+  seq_ghost_prims(t, k, s);
+  seq_rhs(t, k, recon, s);
+}
+
+static Single single_of(const Blk& b, const Ws& w) {
+  Single t;
+  std::memset(&t.r, 0, sizeof(t.r));
+  t.r.b = b;
+  t.r.w = w;
+  return t;
+}
+
+static StageConsts zero_consts() {
+  StageConsts k;
+  std::memset(&k, 0, sizeof(k));
+  return k;
+}
+
+// ----------------------------------------------------------------------------------------------------------
+// Single-block launchers (used by the C ABI).
+
+cudaError_t launch_ghost_state(const Blk& b, const F9& U, cudaStream_t s) {
+  Ws w;
+  std::memset(&w, 0, sizeof(w));
+  Single t = single_of(b, w);
+  t.r.Us = U;
+  seq_ghost_state(t, zero_consts(), s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ghost_prims(const Blk& b, const F5& P, cudaStream_t s) {
+  Ws w;
+  std::memset(&w, 0, sizeof(w));
+  Single t = single_of(b, w);
+  t.r.P = P;
+  seq_ghost_prims(t, zero_consts(), s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bfield(const Blk& b, const Ws& w, const F9& U, cudaStream_t s) {
+  Single t = single_of(b, w);
+  t.r.Us = U;
+  seq_bfield(t, zero_consts(), s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prim2con(const StageArgs& a, const F9& U, const F5& P, cudaStream_t s) {
+  Single t = single_of(a.b, a.w);
+  t.r.Us = U;
+  t.r.P = P;
+  launch<Prim2Con>(t, consts_of(a, -1, 0.0, nullptr), KIND_CELLS_ALL, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c2p(const StageArgs& a, const F9& U, const F5& P, signed char* flags,
+                       unsigned long long* stats, cudaStream_t s) {
+  Single t = single_of(a.b, a.w);
+  t.r.Us = U;
+  t.r.P = P;
+  t.r.flags = flags;
+  launch_c2p_kind(t, consts_of(a, -1, 0.0, stats), s);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rhs(const StageArgs& a, const F9& Us, const F5& P, int stage, double dt, const F9& Un,
                        const F9& Unext, const F9& Uacc, const F9& dU, cudaStream_t s) {
-  const Blk& b = a.b;
-  const int T = 128;
-  k_uvel<<<grid_for((long)b.N[0] * b.N[1] * b.N[2], T), T, 0, s>>>(b, a.w, P);
-  launch_dir<0>(a, P, s);
-  launch_dir<1>(a, P, s);
-  launch_dir<2>(a, P, s);
-  const int lorenz = (a.gauge == 0);
-  k_vertex<<<grid_for((long)(b.n[0] + 3) * (b.n[1] + 3) * (b.n[2] + 3), T), T, 0, s>>>(b, a.w, Us, lorenz);
-  const long ec = (long)(b.n[0] + 1) * (b.n[1] + 1) * (b.n[2] + 1);
-  k_edges<0><<<grid_for(ec, T), T, 0, s>>>(b, a.w, stage, dt, Un, Unext, Uacc, dU);
-  k_edges<1><<<grid_for(ec, T), T, 0, s>>>(b, a.w, stage, dt, Un, Unext, Uacc, dU);
-  k_edges<2><<<grid_for(ec, T), T, 0, s>>>(b, a.w, stage, dt, Un, Unext, Uacc, dU);
-  const double xi = a.xi > 0.0 ? a.xi : 1.5 / dt;
-  k_psi<<<grid_for(ec, T), T, 0, s>>>(b, a.w, Us, lorenz, xi, stage, dt, Un, Unext, Uacc, dU);
-  k_cells<<<grid_for((long)b.n[0] * b.n[1] * b.n[2], T), T, 0, s>>>(b, a.w, P, a.gfac, stage, dt, Un, Unext,
-                                                                     Uacc, dU);
+  Single t = single_of(a.b, a.w);
+  t.r.Us = Us;
+  t.r.P = P;
+  t.r.Un = Un;
+  t.r.Unext = Unext;
+  t.r.Uacc = Uacc;
+  t.r.dU = dU;
+  seq_rhs(t, consts_of(a, stage, dt, nullptr), a.recon, s);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------------------------------
+// Batched stage: every block of the table in one launch per kernel.
+
+cudaError_t launch_batch_stage(const StageArgs& a, const BlockRec* tab, const long* off, const long* host_total,
+                               int nb, int stage, double dt, unsigned long long* stats, cudaStream_t s) {
+  Batch t;
+  t.tab = tab;
+  t.off = off;
+  t.host_total = host_total;
+  t.nb = nb;
+  seq_stage(t, consts_of(a, stage, dt, stats), a.recon, s);
   return cudaGetLastError();
 }
 

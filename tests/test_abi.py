@@ -84,3 +84,22 @@ def test_small_workspace_and_bad_pointers_rejected():
     rc = L.asterx_rk4_step(ctypes.byref(p), ctypes.byref(b), ctypes.c_double(0.01), ctypes.byref(st),
                            ctypes.byref(pr), None, None, ctypes.c_void_p(100), need, None)
     assert rc == A.ASTERX_EINVAL  # workspace not 256-byte aligned
+
+
+def test_batch_workspace_size_and_validation():
+    L = A.lib()
+    arr = (A.BatchBlock * 2)()
+    for i, n in enumerate(((8, 12, 16), (16, 8, 8))):
+        arr[i].blk = A.block_struct(n, 3, (0, 0, 0), (0.1,) * 3, (1, 1, 1))
+        arr[i].metric = A.Metric(*([8] * 16))
+        arr[i].U = A.State(*([8] * 9))
+        arr[i].P = A.Prims(*([8] * 5))
+    size = L.asterx_batch_workspace_size(arr, 2)
+    single = sum(A.workspace_size(arr[i].blk) for i in range(2))
+    assert size > single
+    arr[1].blk = A.block_struct((0, 8, 8), 3, (0, 0, 0), (0.1,) * 3, (1, 1, 1))
+    assert L.asterx_batch_workspace_size(arr, 2) == 0
+    p = _params()
+    rc = L.asterx_batched_step(ctypes.byref(p), arr, 2, ctypes.c_double(0.01), 1, None, ctypes.c_void_p(256),
+                               size, None)
+    assert rc == A.ASTERX_EINVAL
