@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=128, help="cells per axis of the block (default: the 128^3 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch measurement")
+    ap.add_argument("--batch-blocks", type=int, default=512)
     return ap.parse_args()
 
 
@@ -176,6 +178,84 @@ def cpu_baseline(w_full):
     return {"value": cells * 4 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"one RK4 step of the {w.n[0]}x{ny}x{nz} central slab of the same workload "
                       f"({cells} cells, {sec:.1f} s, single host thread, g++ -O2)"}
+
+
+def _upload_block(w, dev):
+    import numpy as np
+    import torch
+
+    from paper_2406_11669_gb300 import workloads as W
+    M = torch.from_numpy(np.ascontiguousarray(np.stack([w.metric[k] for k in W.METRIC_NAMES]))).to(dev)
+    P = torch.from_numpy(np.ascontiguousarray(np.stack([w.prims[k] for k in W.PRIM_NAMES]))).to(dev)
+    U = torch.zeros((9,) + w.shape, dtype=torch.float64, device=dev)
+    U[5] = torch.from_numpy(w.A["Ax"]).to(dev)
+    U[6] = torch.from_numpy(w.A["Ay"]).to(dev)
+    U[7] = torch.from_numpy(w.A["Az"]).to(dev)
+    U[8] = torch.from_numpy(w.Psi).to(dev)
+    return M, U, P
+
+
+def run_batched(args, dev, stream):
+    """Uneven batch of the magnetised-star workload (512 blocks, n per axis in {16,24,32,48,64}, dx = 1/256,
+    PPM, Schwarzschild M = 0.2) in one batched step, against one block of equal total interior volume with the
+    same physics and generator.  Returns the rates (zone-updates/s per RK stage) and their ratio."""
+    import torch
+
+    from paper_2406_11669_gb300 import asterx as A
+    from paper_2406_11669_gb300 import workloads as W
+
+    lay = W.config3_layout(nblocks=args.batch_blocks)
+    entries = []
+    cells = 0
+    for n, o in lay:
+        w = W.config3_block(n, o)
+        M, U, P = _upload_block(w, dev)
+        entries.append((w.n, w.g, w.x0, w.dx, w.bc, M, U, P))
+        cells += w.interior_cells
+        params, dt = w.params, w.dt
+    batch = A.Batch(params, entries, device=dev)
+    batch.prepare()
+    batch.prim2con()
+    steps = max(1, min(args.steps, 3))
+    batch.step(dt, nsteps=1)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.step(dt, nsteps=steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_b = e0.elapsed_time(e1) / steps
+    pool_bytes = batch.ws_bytes
+    del batch, entries
+    torch.cuda.empty_cache()
+    # one block of the same total interior volume, centred on the star
+    side = int(round(cells ** (1.0 / 3.0)))
+    h = 1.0 / 256.0
+    w = W.config3_block((side, side, side), (-0.5 * side * h,) * 3)
+    M, U, P = _upload_block(w, dev)
+    s = A.Solver.for_workload(w, device=dev)
+    s.prepare(M)
+    s.fill_ghosts(U)
+    s.prim2con(U, P)
+    s.rk4_step(U, P, w.dt)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        s.rk4_step(U, P, w.dt)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_s = e0.elapsed_time(e1) / steps
+    single_cells = w.interior_cells
+    del s, M, U, P
+    torch.cuda.empty_cache()
+    rate_b = cells * 4 / (ms_b / 1e3)
+    rate_s = single_cells * 4 / (ms_s / 1e3)
+    return {"workload": f"{len(lay)} uneven blocks (n per axis in 16..64, seed 103), magnetised star, PPM, "
+                        f"Schwarzschild M=0.2, one batched launch per kernel",
+            "blocks": len(lay), "interior_cells": cells, "value": rate_b, "unit": UNIT, "ms_per_step": ms_b,
+            "steps": steps, "pool_bytes": int(pool_bytes),
+            "single_equal_volume": {"n": side, "interior_cells": single_cells, "value": rate_s, "ms_per_step": ms_s},
+            "batched_vs_single": rate_b / rate_s}
 
 
 def run_reference(args):
@@ -313,6 +393,8 @@ def run_ours(args):
                       "d2h_bytes_per_step": io_bytes},
               "gpu_launches": LAUNCHES_PER_STAGE * 4 * args.steps,
               "clocks": clk, "roofline": roofline, "c2p_counters_timed": c2p, "state_finite": finite}
+    if not args.no_batched:
+        result["batched"] = run_batched(args, dev, stream)
     if not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(result))

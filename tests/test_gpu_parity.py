@@ -188,3 +188,28 @@ def test_algebraic_gauge_parity():
         e, scale = rel_field_err(Ug, U1, w, v)
         if scale > 0:
             assert e <= 1e-12, (v, e)
+
+
+def test_rk4_step_graph_capture_replays_identically():
+    """asterx_rk4_step only enqueues kernels (no synchronisation, no allocation), so a caller can capture it in
+    a CUDA graph; replaying the graph gives the same result as the direct call."""
+    need_gpu()
+    w = WORKLOADS["config1"]
+    case = GpuCase(w)
+    U, P = O.initial_state(w)
+    O.ghost_fill_state(w, U)
+    Ua, Pa = case.dev(U), case.dev(P)
+    case.solver.rk4_step(Ua, Pa, w.dt)
+    Ub, Pb = case.dev(U), case.dev(P)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            case.solver.rk4_step(Ub, Pb, w.dt)
+    torch.cuda.current_stream().wait_stream(side)
+    Ub.copy_(case.dev(U))
+    Pb.copy_(case.dev(P))
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(Ua, Ub) and torch.equal(Pa, Pb)
