@@ -161,6 +161,33 @@ asterx_status asterx_rk4_step_host(const asterx_params *p, const asterx_block *b
                                    double *const *h_U9, double *const *h_P5, asterx_state *dU, asterx_prims *dP,
                                    asterx_c2p_stats *stats, void *ws, size_t ws_bytes, asterx_stream stream);
 
+/* ---- adjoint (vector-Jacobian products) ----
+ *
+ * Reverse-mode derivatives of the stage operator and of one RK4 step, for gradients of a scalar loss with
+ * respect to the state.  The adjoint recomputes the forward intermediates from the state it is given (a
+ * checkpoint), so the caller keeps one state per RK4 step.  Recovery and wave speeds are differentiated by the
+ * implicit-function theorem at the converged root; limiters, max/min and branch choices by the branch taken;
+ * atmosphere cells pass no derivative through the recovery.  FP64 atomics accumulate shared adjoints, so the
+ * last bits may differ from run to run.  Adjoint arrays use the state layout and cover the independent entries
+ * only: g..g+n-1 along cell-like axes and along periodic axes (there the vertex index g+n is the periodic image
+ * of g), g..g+n along vertex-like axes with copy BCs.  Adjoint inputs are read there only; outputs are zero
+ * everywhere else.  `aws` is a second, caller-owned
+ * workspace of asterx_adjoint_workspace_size() bytes (256-byte aligned); `ws` is the prepared forward one. */
+size_t asterx_adjoint_workspace_size(const asterx_block *blk);
+
+/* lam = (dL/dU)^T mu for the right-hand side L of asterx_rhs at state U (U unchanged; P: guess in, the
+ * primitives recovered from U out). */
+asterx_status asterx_rhs_adjoint(const asterx_params *p, const asterx_block *blk, double dt,
+                                 const asterx_state *U, asterx_prims *P, const asterx_state *mu,
+                                 asterx_state *lam, void *ws, size_t ws_bytes, void *aws, size_t aws_bytes,
+                                 asterx_stream stream);
+
+/* Adjoint of one classical RK4 step U_{n+1} = Phi(U_n): on entry lam holds dJ/dU_{n+1}, on exit dJ/dU_n.
+ * Un is the checkpoint of the step's input state (unchanged); P is a primitive guess (overwritten). */
+asterx_status asterx_rk4_step_adjoint(const asterx_params *p, const asterx_block *blk, double dt,
+                                      const asterx_state *Un, asterx_prims *P, asterx_state *lam, void *ws,
+                                      size_t ws_bytes, void *aws, size_t aws_bytes, asterx_stream stream);
+
 /* ---- batched step over many blocks of uneven sizes ----
  *
  * Many AMR-like blocks advance together: every kernel of the stage is launched once for all blocks, over the

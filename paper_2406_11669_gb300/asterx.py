@@ -93,6 +93,12 @@ def lib():
         L.asterx_batched_step.argtypes = [P, BB, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, vp, sz, st]
         for name in ("asterx_batch_prepare", "asterx_batch_prim2con", "asterx_batched_step"):
             getattr(L, name).restype = ctypes.c_int
+        L.asterx_adjoint_workspace_size.restype = ctypes.c_size_t
+        L.asterx_adjoint_workspace_size.argtypes = [B]
+        L.asterx_rhs_adjoint.argtypes = [P, B, ctypes.c_double, S, Pr, S, S, vp, sz, vp, sz, st]
+        L.asterx_rk4_step_adjoint.argtypes = [P, B, ctypes.c_double, S, Pr, S, vp, sz, vp, sz, st]
+        for name in ("asterx_rhs_adjoint", "asterx_rk4_step_adjoint"):
+            getattr(L, name).restype = ctypes.c_int
         L.asterx_con2prim_noalloc.argtypes = [P, B, M, S, Pr, vp, vp, st]
         L.asterx_con2prim_noalloc.restype = ctypes.c_int
         L.asterx_profile_enable.argtypes = [ctypes.c_int]
@@ -260,6 +266,31 @@ class Solver:
         sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
         _check(lib().asterx_rk4_step_host(*self._args(), float(dt), hu, hp, ctypes.byref(u), ctypes.byref(p), sp,
                                           self.ws_ptr, self.ws_bytes, _stream(stream)), "asterx_rk4_step_host")
+
+    def _adjoint_ws(self):
+        import torch
+        if getattr(self, "aws", None) is None:
+            self.aws_bytes = int(lib().asterx_adjoint_workspace_size(ctypes.byref(self.b)))
+            self.aws = torch.empty(self.aws_bytes + 256, dtype=torch.uint8, device=self.ws.device)
+            off = (-self.aws.data_ptr()) % 256
+            self.aws_ptr = ctypes.c_void_p(self.aws.data_ptr() + off)
+        return self.aws_ptr, self.aws_bytes
+
+    def rhs_adjoint(self, U, P, mu, lam, dt, stream=None):
+        """lam = (dL/dU)^T mu for the stage right-hand side L at U (adjoint workspace allocated on first use)."""
+        ap, ab = self._adjoint_ws()
+        u, p, m, l = state_struct(U), prims_struct(P), state_struct(mu), state_struct(lam)
+        _check(lib().asterx_rhs_adjoint(*self._args(), float(dt), ctypes.byref(u), ctypes.byref(p), ctypes.byref(m),
+                                        ctypes.byref(l), self.ws_ptr, self.ws_bytes, ap, ab, _stream(stream)),
+               "asterx_rhs_adjoint")
+
+    def rk4_step_adjoint(self, Un, P, lam, dt, stream=None):
+        """In place: lam = dJ/dU_{n+1} on entry, dJ/dU_n on exit, for the RK4 step taken from state Un."""
+        ap, ab = self._adjoint_ws()
+        u, p, l = state_struct(Un), prims_struct(P), state_struct(lam)
+        _check(lib().asterx_rk4_step_adjoint(*self._args(), float(dt), ctypes.byref(u), ctypes.byref(p),
+                                             ctypes.byref(l), self.ws_ptr, self.ws_bytes, ap, ab, _stream(stream)),
+               "asterx_rk4_step_adjoint")
 
 
 # ---------------------------------------------------------------------------------------- measurement helpers

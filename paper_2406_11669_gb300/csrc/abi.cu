@@ -464,6 +464,166 @@ asterx_status asterx_batched_step(const asterx_params* p, const asterx_batch_blo
   return ASTERX_OK;
 }
 
+// ----------------------------------------------------------------------------------------------------------
+// Adjoint.  Adjoint workspace: RK4 stage states Y0..Y3 (36 fields), forward accumulator (9), running adjoint
+// lambda (9), stage adjoint kbar (9), sum (9), the right-hand-side adjoint accumulators (ADJ_ACC_FIELDS),
+// reconstructed-value adjoints (2 NREC), forward right-hand side scratch (9), a state copy (9), recovery flags.
+
+namespace {
+constexpr int ADJ_FIELDS = 36 + 9 + 9 + 9 + 9 + ADJ_ACC_FIELDS + 2 * NREC + 9 + 9;
+
+struct AdjLayout {
+  F9 Ys[4], acc, lam, kbar, sum, dscr, ycopy;
+  double* accum;
+  double* lrec;
+  signed char* flags;
+};
+
+size_t adj_bytes_for(const asterx_block* b) {
+  const long V = padded_V(b);
+  const long fs = field_stride(V);
+  return (size_t)ADJ_FIELDS * fs * sizeof(double) + (size_t)fs * sizeof(double) + kAlign;
+}
+
+AdjLayout make_adj(const asterx_block* in, void* base) {
+  const long V = padded_V(in);
+  const long fs = field_stride(V);
+  double* p = reinterpret_cast<double*>(base);
+  auto take9 = [&]() {
+    F9 f;
+    for (int v = 0; v < 9; v++) f.f[v] = p + v * V;
+    p += 9 * fs;
+    return f;
+  };
+  AdjLayout L;
+  for (int s = 0; s < 4; s++) L.Ys[s] = take9();
+  L.acc = take9();
+  L.lam = take9();
+  L.kbar = take9();
+  L.sum = take9();
+  L.accum = p;
+  p += (long)ADJ_ACC_FIELDS * fs;
+  L.lrec = p;
+  p += 2L * NREC * fs;
+  L.dscr = take9();
+  L.ycopy = take9();
+  L.flags = reinterpret_cast<signed char*>(p);
+  return L;
+}
+
+AdjWs adj_ws(const AdjLayout& L, const Blk& b, const F9& Y, const F5& P, const F9& mu) {
+  AdjWs a;
+  a.Y = Y;
+  a.P = P;
+  a.mu = mu;
+  a.dscratch = L.dscr;
+  a.flags = L.flags;
+  double* q = L.accum;
+  a.lY_base = q;
+  a.lY = q; q += 9 * b.V;
+  a.lP = q; q += 5 * b.V;
+  a.lu = q; q += 3 * b.V;
+  a.lBc = q; q += 3 * b.V;
+  a.lBf = q; q += 3 * b.V;
+  a.lface = q; q += 3L * NFD * b.V;
+  a.lGA = q; q += b.V;
+  a.lFpsi = q; q += 3 * b.V;
+  a.lAv = q;
+  a.lrec = L.lrec;
+  return a;
+}
+
+F9 f9_from(double* base, long V) {
+  F9 f;
+  for (int v = 0; v < 9; v++) f.f[v] = base + v * V;
+  return f;
+}
+
+cudaError_t copy9(const F9& dst, const F9& src, long V, cudaStream_t s) {
+  for (int v = 0; v < 9; v++) {
+    cudaError_t e = cudaMemcpyAsync(dst.f[v], src.f[v], V * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+}  // namespace
+
+size_t asterx_adjoint_workspace_size(const asterx_block* blk) {
+  if (!block_ok(blk)) return 0;
+  return adj_bytes_for(blk);
+}
+
+static asterx_status adj_checks(const asterx_params* p, const asterx_block* blk, double dt, void* ws,
+                                size_t ws_bytes, void* aws, size_t aws_bytes) {
+  asterx_status st = common_checks(p, blk, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!finite_pos(dt)) return ASTERX_EINVAL;
+  if (!aws || ((uintptr_t)aws % kAlign) != 0) return ASTERX_EINVAL;
+  if (aws_bytes < adj_bytes_for(blk)) return ASTERX_ENOMEM;
+  return ASTERX_OK;
+}
+
+asterx_status asterx_rhs_adjoint(const asterx_params* p, const asterx_block* blk, double dt, const asterx_state* U,
+                                 asterx_prims* P, const asterx_state* mu, asterx_state* lam, void* ws,
+                                 size_t ws_bytes, void* aws, size_t aws_bytes, asterx_stream stream) {
+  asterx_status st = adj_checks(p, blk, dt, ws, ws_bytes, aws, aws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!set_ok<asterx_state, 9>(U) || !set_ok<asterx_prims, 5>(P) || !set_ok<asterx_state, 9>(mu) ||
+      !set_ok<asterx_state, 9>(lam))
+    return ASTERX_EINVAL;
+  StageArgs sa = make_args(p, blk, ws);
+  AdjLayout L = make_adj(blk, aws);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = copy9(L.ycopy, f9(U), sa.b.V, s);
+  if (e == cudaSuccess) e = copy9(L.kbar, f9(mu), sa.b.V, s);
+  if (e == cudaSuccess) e = launch_mask_owned9(sa.b, L.kbar, s);
+  AdjWs a = adj_ws(L, sa.b, L.ycopy, f5(P), L.kbar);
+  if (e == cudaSuccess) e = launch_rhs_adjoint(sa, a, dt, s);
+  if (e == cudaSuccess) e = copy9(f9(lam), f9_from(a.lY, sa.b.V), sa.b.V, s);
+  return cuda_status(e);
+}
+
+asterx_status asterx_rk4_step_adjoint(const asterx_params* p, const asterx_block* blk, double dt,
+                                      const asterx_state* Un, asterx_prims* P, asterx_state* lam, void* ws,
+                                      size_t ws_bytes, void* aws, size_t aws_bytes, asterx_stream stream) {
+  asterx_status st = adj_checks(p, blk, dt, ws, ws_bytes, aws, aws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!set_ok<asterx_state, 9>(Un) || !set_ok<asterx_prims, 5>(P) || !set_ok<asterx_state, 9>(lam))
+    return ASTERX_EINVAL;
+  StageArgs sa = make_args(p, blk, ws);
+  const Blk& b = sa.b;
+  AdjLayout L = make_adj(blk, aws);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // forward recompute of the stage states Y0..Y3 from the checkpoint
+  cudaError_t e = copy9(L.Ys[0], f9(Un), b.V, s);
+  for (int stage = 0; stage < 3 && e == cudaSuccess; stage++) {
+    const asterx_status r = stage_impl(sa, stage, dt, L.Ys[0], L.Ys[stage], L.Ys[stage + 1], L.acc, f5(P), nullptr,
+                                       nullptr, s);
+    if (r != ASTERX_OK) return r;
+  }
+  // reverse sweep: kbar_3 = dt/6 lam, Ybar_s = J_s^T kbar_s, kbar_{s-1} = b_{s-1} dt lam + c_s dt Ybar_s
+  if (e == cudaSuccess) e = copy9(L.lam, f9(lam), b.V, s);
+  if (e == cudaSuccess) e = launch_mask_owned9(b, L.lam, s);
+  if (e == cudaSuccess) e = copy9(L.sum, L.lam, b.V, s);
+  if (e == cudaSuccess) e = copy9(L.kbar, L.lam, b.V, s);
+  if (e == cudaSuccess) e = launch_axpby9(b, 0.0, L.lam, dt / 6.0, L.kbar, s);
+  const double blam[3] = {dt / 6.0, dt / 3.0, dt / 3.0};  // weight of lam in kbar_{s}, s = 0, 1, 2
+  const double cy[3] = {0.5 * dt, 0.5 * dt, dt};          // weight of Ybar_{s+1} in kbar_{s}
+  for (int stage = 3; stage >= 0 && e == cudaSuccess; stage--) {
+    AdjWs a = adj_ws(L, b, L.Ys[stage], f5(P), L.kbar);
+    e = launch_rhs_adjoint(sa, a, dt, s);
+    const F9 ybar = f9_from(a.lY, b.V);
+    if (e == cudaSuccess) e = launch_axpby9(b, 1.0, ybar, 1.0, L.sum, s);
+    if (stage > 0 && e == cudaSuccess) {
+      // kbar_{stage-1} = blam * lam + cy * ybar
+      e = copy9(L.kbar, ybar, b.V, s);
+      if (e == cudaSuccess) e = launch_axpby9(b, blam[stage - 1], L.lam, cy[stage - 1], L.kbar, s);
+    }
+  }
+  if (e == cudaSuccess) e = copy9(f9(lam), L.sum, b.V, s);
+  return cuda_status(e);
+}
+
 asterx_status asterx_profile_enable(int max_launches) {
   if (max_launches < 1 || max_launches > (1 << 20)) return ASTERX_EINVAL;
   return cuda_status(profile_enable(max_launches));

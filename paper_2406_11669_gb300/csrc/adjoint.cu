@@ -1,0 +1,760 @@
+// Adjoint (vector-Jacobian product) of the right-hand side of one RK stage, and of a classical RK4 step.
+//
+// Given mu = dJ/d(dU/dt) on the owned ranges, the kernels below return lambda = (dL/dY)^T mu for the stage
+// operator L(Y) of the forward path (ghost fill, B~ = curl A, recovery, reconstruction, face solve, UCT,
+// potentials, sources).  Each forward kernel has a reverse kernel, run in reverse order:
+//   cells (flux divergence, sources) -> scalar potential -> edges (UCT, grad G_A) -> vertex potentials ->
+//   face solves and reconstruction (per direction) -> u = W v -> primitive ghost fill -> recovery ->
+//   centre field -> curl -> state ghost fill.
+// Linear maps are transposed by hand.  Nonlinear pointwise maps take their local Jacobian from the same
+// templated device code as the forward path run with forward-mode dual numbers; the wave speeds and the
+// recovery are differentiated by the implicit-function theorem at the converged root (one Newton step in dual
+// arithmetic from the root for the speeds; the prim->cons Jacobian inverted at the root for the recovery).
+// Limiters, max/min and branch choices take the derivative of the branch taken.  Atmosphere cells (constant
+// primitives) pass no derivative through the recovery.
+//
+// Accumulations that several threads share use FP64 atomics, so the summation order (and the last bits of
+// lambda) may vary between runs.
+#include <cstring>
+
+#include "kernels.h"
+#include "physics.cuh"
+
+namespace asterx {
+
+static __host__ int agrid(long count, int threads) {
+  long blocks = (count + threads - 1) / threads;
+  const long cap = 152L * 64;
+  return (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
+}
+
+#define ALOOP(t, count) \
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < (count); t += (long)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ long alin(const Blk& b, int i, int j, int k) { return i + b.sy * j + b.sz * k; }
+__device__ __forceinline__ long astr(const Blk& b, int d) { return d == 0 ? 1 : (d == 1 ? b.sy : b.sz); }
+
+__device__ __forceinline__ void decode(long t, int lo0, int e0, int lo1, int e1, int lo2, int& i, int& j, int& k) {
+  i = lo0 + (int)(t % e0);
+  const long r = t / e0;
+  j = lo1 + (int)(r % e1);
+  k = lo2 + (int)(r / e1);
+}
+
+// ----------------------------------------------------------------------------------------------------------
+// Cells: dU_v/dt = -sum_d (F_d,v(c + e_d) - F_d,v(c)) / dx_d + S_v(P, B).  Flux part: each face gathers the
+// adjoints of its two cells (zero outside the interior).  Source part: Jacobian of the sources in (rho, p, v,
+// B) by dual numbers.
+
+__global__ void ka_flux_div(Blk b, AdjWs a, F9 mu, int D) {
+  // faces g..g+n along D, interior transverse
+  int lo[3] = {b.g, b.g, b.g}, e[3] = {b.n[0], b.n[1], b.n[2]};
+  e[D] = b.n[D] + 1;
+  const long count = (long)e[0] * e[1] * e[2];
+  const long st = astr(b, D);
+  ALOOP(t, count) {
+    int p[3];
+    decode(t, lo[0], e[0], lo[1], e[1], lo[2], p[0], p[1], p[2]);
+    const long c = alin(b, p[0], p[1], p[2]);
+    const bool left_in = p[D] - 1 >= b.g;          // cell c - e_D is interior
+    const bool right_in = p[D] <= b.g + b.n[D] - 1;  // cell c is interior
+    for (int v = 0; v < 5; v++) {
+      const double ml = left_in ? mu.f[v][c - st] : 0.0;
+      const double mr = right_in ? mu.f[v][c] : 0.0;
+      // F(c) enters dU(c) with +1/dx and dU(c - e_D) with -1/dx
+      a.lface[((long)D * NFD + FD_F + v) * b.V + c] = (mr - ml) / b.dx[D];
+    }
+  }
+}
+
+__device__ __forceinline__ void load_geo(const Blk& b, const double* __restrict__ cg, long c, Geo& m) {
+  m.alp = cg[CG_ALP * b.V + c];
+  for (int q = 0; q < 3; q++) m.beta[q] = cg[(CG_BETA + q) * b.V + c];
+  for (int q = 0; q < 6; q++) {
+    m.g[q] = cg[(CG_G + q) * b.V + c];
+    m.gu[q] = cg[(CG_GU + q) * b.V + c];
+  }
+  m.sqg = cg[CG_SQG * b.V + c];
+}
+
+__global__ void ka_sources(Blk b, Ws w, AdjWs a, F5 P, F9 mu, double gfac) {
+  const long count = (long)b.n[0] * b.n[1] * b.n[2];
+  ALOOP(t, count) {
+    int i, j, k;
+    decode(t, b.g, b.n[0], b.g, b.n[1], b.g, i, j, k);
+    const long c = alin(b, i, j, k);
+    Geo m;
+    load_geo(b, w.cg, c, m);
+    typedef Dual<8> D8;
+    const D8 rho = D8::seed(P.f[0][c], 0), press = D8::seed(P.f[1][c], 1);
+    const D8 v[3] = {D8::seed(P.f[2][c], 2), D8::seed(P.f[3][c], 3), D8::seed(P.f[4][c], 4)};
+    const D8 B[3] = {D8::seed(w.bc[c], 5), D8::seed(w.bc[b.V + c], 6), D8::seed(w.bc[2 * b.V + c], 7)};
+    D8 src[5];
+    sources(m, w.cg, b.V, c, rho, press, v, B, gfac, src);
+    double g8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int q = 1; q < 5; q++) {
+      const double mq = mu.f[q][c];
+      for (int r = 0; r < 8; r++) g8[r] += src[q].d[r] * mq;
+    }
+    for (int r = 0; r < 5; r++) a.lP[r * b.V + c] += g8[r];
+    for (int r = 0; r < 3; r++) a.lBc[r * b.V + c] += g8[5 + r];
+  }
+}
+
+// ----------------------------------------------------------------------------------------------------------
+// Scalar potential: dPsi = -sum_j (F^j(v+e_j) - F^j(v-e_j)) / (2 dx_j) - xi alpha Psi on vertices g..g+n.
+// lambda_FPsi^j(w) gathers the two vertices that difference it.
+
+__global__ void ka_psi(Blk b, Ws w, AdjWs a, F9 mu, double xi) {
+  // vertices g-1 .. g+n+1 (the F_Psi range)
+  const int n0 = b.n[0] + 3, n1 = b.n[1] + 3, n2 = b.n[2] + 3;
+  const long count = (long)n0 * n1 * n2;
+  ALOOP(t, count) {
+    int p[3];
+    decode(t, b.g - 1, n0, b.g - 1, n1, b.g - 1, p[0], p[1], p[2]);
+    const long c = alin(b, p[0], p[1], p[2]);
+    auto owned = [&](const int q[3]) {
+      return q[0] >= b.g && q[0] <= b.g + b.n[0] && q[1] >= b.g && q[1] <= b.g + b.n[1] && q[2] >= b.g &&
+             q[2] <= b.g + b.n[2];
+    };
+    for (int d = 0; d < 3; d++) {
+      int qm[3] = {p[0], p[1], p[2]}, qp[3] = {p[0], p[1], p[2]};
+      qm[d] -= 1;
+      qp[d] += 1;
+      const double mm = owned(qm) ? mu.f[8][c - astr(b, d)] : 0.0;
+      const double mp = owned(qp) ? mu.f[8][c + astr(b, d)] : 0.0;
+      // F^d(c) enters dPsi(c + e_d) with +1/(2dx) and dPsi(c - e_d) with -1/(2dx)
+      a.lFpsi[d * b.V + c] = (mp - mm) / (2.0 * b.dx[d]);
+    }
+    if (owned(p)) a.lY[8 * b.V + c] += -xi * w.vg[VG_ALP * b.V + c] * mu.f[8][c];
+  }
+}
+
+// ----------------------------------------------------------------------------------------------------------
+// Edges: dA_E = -E_E - (G_A(c + e_E) - G_A(c)) / dx_E.  lambda_G_A(v) gathers the edges that difference it.
+
+__global__ void ka_grad_ga(Blk b, AdjWs a, F9 mu) {
+  const int n0 = b.n[0] + 3, n1 = b.n[1] + 3, n2 = b.n[2] + 3;
+  const long count = (long)n0 * n1 * n2;
+  ALOOP(t, count) {
+    int p[3];
+    decode(t, b.g - 1, n0, b.g - 1, n1, b.g - 1, p[0], p[1], p[2]);
+    const long c = alin(b, p[0], p[1], p[2]);
+    double acc = 0.0;
+    for (int E = 0; E < 3; E++) {
+      // edges along E at q: owned range g..g+n-1 along E, g..g+n across
+      auto owned = [&](const int q[3]) {
+        for (int d = 0; d < 3; d++) {
+          const int hi = (d == E) ? b.g + b.n[d] - 1 : b.g + b.n[d];
+          if (q[d] < b.g || q[d] > hi) return false;
+        }
+        return true;
+      };
+      int qm[3] = {p[0], p[1], p[2]};
+      qm[E] -= 1;
+      const double m_here = owned(p) ? mu.f[5 + E][c] : 0.0;               // edge at c: +G(c)/dx
+      const double m_below = owned(qm) ? mu.f[5 + E][c - astr(b, E)] : 0.0;  // edge at c-e: -G(c)/dx
+      acc += (m_here - m_below) / b.dx[E];
+    }
+    a.lGA[c] = acc;
+  }
+}
+
+// UCT: E_E = -HLL_d1(v~^d1 B~^d2) + HLL_d2(v~^d2 B~^d1); lambda_E = -mu_A.  Each term's local Jacobian: PPM
+// interfaces by dual numbers (6 inputs), the HLL formula by hand, a_+- = max over the two faces (branch taken).
+template <int E>
+__global__ void ka_edges(Blk b, Ws w, AdjWs a, F9 mu) {
+  constexpr int D1 = (E + 1) % 3, D2 = (E + 2) % 3;
+  int lo[3] = {b.g, b.g, b.g}, ex[3] = {b.n[0] + 1, b.n[1] + 1, b.n[2] + 1};
+  ex[E] = b.n[E];
+  const long count = (long)ex[0] * ex[1] * ex[2];
+  ALOOP(t, count) {
+    int p[3];
+    decode(t, lo[0], ex[0], lo[1], ex[1], lo[2], p[0], p[1], p[2]);
+    const long c = alin(b, p[0], p[1], p[2]);
+    const double lE = -mu.f[5 + E][c];
+#pragma unroll
+    for (int tt = 0; tt < 2; tt++) {
+      const double sgn = tt == 0 ? -1.0 : 1.0;  // E = -term0 + term1
+      const int dr = tt == 0 ? D1 : D2;
+      const int df = tt == 0 ? D2 : D1;
+      const long sr = astr(b, dr);
+      const long sf = astr(b, df);
+      const int slot = (((df + 1) % 3) == dr) ? FD_VB1 : FD_VB2;
+      const long vb_off = ((long)df * NFD + slot) * b.V;
+      const long bn_off = (long)df * b.V;
+      typedef Dual<6> D6;
+      D6 vs[6], bs[6];
+      for (int s = 0; s < 6; s++) {
+        const long q = c + (s - 3) * sr;
+        vs[s] = D6::seed(w.face[vb_off + q], s);
+        bs[s] = D6::seed(w.bf[bn_off + q], s);
+      }
+      D6 l, h, vL, vR, BL, BR;
+      recon5<1>(vs, l, h);
+      vL = h;
+      recon5<1>(vs + 1, l, h);
+      vR = l;
+      recon5<1>(bs, l, h);
+      BL = h;
+      recon5<1>(bs + 1, l, h);
+      BR = l;
+      const long fdr = (long)dr * NFD * b.V;
+      const long c0 = c - sf;
+      const double apa = w.face[fdr + FD_CMAX * b.V + c0], apb = w.face[fdr + FD_CMAX * b.V + c];
+      const double ama = w.face[fdr + FD_CMIN * b.V + c0], amb = w.face[fdr + FD_CMIN * b.V + c];
+      const double ap = fmax(apa, apb), am = fmax(ama, amb);
+      const double den = ap + am;
+      const double lt = sgn * lE;  // adjoint of this term
+      double gvL, gvR, gBL, gBR, gap = 0.0, gam = 0.0;
+      if (den > 0.0) {
+        const double term = (ap * vL.v * BL.v + am * vR.v * BR.v - ap * am * (BR.v - BL.v)) / den;
+        gvL = ap * BL.v / den;
+        gBL = (ap * vL.v + ap * am) / den;
+        gvR = am * BR.v / den;
+        gBR = (am * vR.v - ap * am) / den;
+        gap = (vL.v * BL.v - am * (BR.v - BL.v) - term) / den;
+        gam = (vR.v * BR.v - ap * (BR.v - BL.v) - term) / den;
+      } else {
+        gvL = 0.5 * BL.v;
+        gBL = 0.5 * vL.v;
+        gvR = 0.5 * BR.v;
+        gBR = 0.5 * vR.v;
+      }
+      for (int s = 0; s < 6; s++) {
+        const long q = c + (s - 3) * sr;
+        const double dv = (gvL * vL.d[s] + gvR * vR.d[s]) * lt;
+        const double db = (gBL * BL.d[s] + gBR * BR.d[s]) * lt;
+        if (dv != 0.0) atomicAdd(&a.lface[vb_off + q], dv);
+        if (db != 0.0) atomicAdd(&a.lBf[bn_off + q], db);
+      }
+      if (gap != 0.0) atomicAdd(&a.lface[fdr + FD_CMAX * b.V + (apb > apa ? c : c0)], gap * lt);
+      if (gam != 0.0) atomicAdd(&a.lface[fdr + FD_CMIN * b.V + (amb > ama ? c : c0)], gam * lt);
+    }
+  }
+}
+
+// Vertex potentials: G_A = alpha Psi / sqrt(g) - beta^j Av_j, F^j = alpha sqrt(g) gamma^jk Av_k - beta^j Psi,
+// Av_j = (A_j(v - e_j) + A_j(v)) / 2.  First the vertex adjoints of Av and Psi, then each edge gathers the two
+// vertices that average it.
+__global__ void ka_vertex(Blk b, Ws w, AdjWs a, int lorenz) {
+  const int n0 = b.n[0] + 3, n1 = b.n[1] + 3, n2 = b.n[2] + 3;
+  const long count = (long)n0 * n1 * n2;
+  ALOOP(t, count) {
+    int p[3];
+    decode(t, b.g - 1, n0, b.g - 1, n1, b.g - 1, p[0], p[1], p[2]);
+    const long c = alin(b, p[0], p[1], p[2]);
+    const double alp = w.vg[VG_ALP * b.V + c];
+    const double be[3] = {w.vg[(VG_BETA + 0) * b.V + c], w.vg[(VG_BETA + 1) * b.V + c],
+                          w.vg[(VG_BETA + 2) * b.V + c]};
+    const double sqg = w.vg[VG_SQG * b.V + c];
+    double gu[6];
+    for (int q = 0; q < 6; q++) gu[q] = w.vg[(VG_GU + q) * b.V + c];
+    const double lg = lorenz ? a.lGA[c] : 0.0;
+    const double lf[3] = {a.lFpsi[c], a.lFpsi[b.V + c], a.lFpsi[2 * b.V + c]};
+    double lpsi = lorenz ? alp / sqg * lg : 0.0;
+    for (int d = 0; d < 3; d++) lpsi -= be[d] * lf[d];
+    a.lY[8 * b.V + c] += lpsi;
+    const double as = alp * sqg;
+    for (int k = 0; k < 3; k++) {
+      const double lak = -(lorenz ? be[k] * lg : 0.0) + as * (gu[sym(0, k)] * lf[0] + gu[sym(1, k)] * lf[1] +
+                                                             gu[sym(2, k)] * lf[2]);
+      a.lAv[k * b.V + c] = lak;
+    }
+  }
+}
+
+__global__ void ka_vertex_to_edges(Blk b, AdjWs a) {
+  // edges whose averaging vertex lies in g-1 .. g+n+1: along k the edge index g-2 .. g+n+1
+  const int n0 = b.n[0] + 4, n1 = b.n[1] + 4, n2 = b.n[2] + 4;
+  const long count = (long)n0 * n1 * n2;
+  ALOOP(t, count) {
+    int p[3];
+    decode(t, b.g - 2, n0, b.g - 2, n1, b.g - 2, p[0], p[1], p[2]);
+    const long c = alin(b, p[0], p[1], p[2]);
+    for (int k = 0; k < 3; k++) {
+      // edge A_k at p feeds Av_k at vertices p and p + e_k
+      double acc = 0.0;
+      for (int s = 0; s < 2; s++) {
+        int q[3] = {p[0], p[1], p[2]};
+        q[k] += s;
+        bool in = true;
+        for (int d = 0; d < 3; d++) in = in && q[d] >= b.g - 1 && q[d] <= b.g + b.n[d] + 1;
+        if (!in) continue;
+        acc += 0.5 * a.lAv[k * b.V + alin(b, q[0], q[1], q[2])];
+      }
+      if (acc != 0.0) a.lY[(5 + k) * b.V + c] += acc;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------------------------------
+// Face solve along D (faces g..g+n along D, all transverse): adjoints of (F^, v~bar, c_max, c_min) -> adjoints
+// of the reconstructed left/right states and of the face field B~.  HLLE by hand, each side's Jacobian by
+// dual numbers in (rho, p, u^x, u^y, u^z, B_t1, B_t2, B~_n).
+template <int D>
+__global__ void ka_faces(Blk b, Ws w, AdjWs a, double gamma, double gfac) {
+  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+  int lo[3] = {0, 0, 0}, ex[3] = {b.N[0], b.N[1], b.N[2]};
+  lo[D] = b.g;
+  ex[D] = b.n[D] + 1;
+  const long count = (long)ex[0] * ex[1] * ex[2];
+  const long st = astr(b, D);
+  const double* __restrict__ fg = w.fg + (long)D * NFG * b.V;
+  ALOOP(t, count) {
+    int p[3];
+    decode(t, lo[0], ex[0], lo[1], ex[1], lo[2], p[0], p[1], p[2]);
+    const long c = alin(b, p[0], p[1], p[2]);
+    Geo m;
+    m.alp = fg[FG_ALP * b.V + c];
+    for (int q = 0; q < 3; q++) m.beta[q] = fg[(FG_BETA + q) * b.V + c];
+    for (int q = 0; q < 6; q++) {
+      m.g[q] = fg[(FG_G + q) * b.V + c];
+      m.gu[q] = fg[(FG_GU + q) * b.V + c];
+    }
+    m.sqg = fg[FG_SQG * b.V + c];
+    const double ia = fg[FG_IALP * b.V + c];
+    const double width = fg[FG_WIDTH * b.V + c];
+    const double isqg = fg[FG_ISQG * b.V + c];
+    typedef Dual<8> D8;
+    SideOutT<D8> s[2];
+    for (int side = 0; side < 2; side++) {
+      const long cc = side == 0 ? c - st : c;
+      const double* __restrict__ rr = w.rec + (side == 0 ? NREC : 0) * b.V + cc;
+      const D8 rho = D8::seed(rr[0], 0), press = D8::seed(rr[b.V], 1);
+      const D8 u[3] = {D8::seed(rr[2 * b.V], 2), D8::seed(rr[3 * b.V], 3), D8::seed(rr[4 * b.V], 4)};
+      D8 B[3];
+      B[D] = D8::seed(w.bf[D * b.V + c], 7) * isqg;
+      B[T1] = D8::seed(rr[5 * b.V], 5);
+      B[T2] = D8::seed(rr[6 * b.V], 6);
+      face_side(m, ia, width, D, rho, press, u, B, gamma, gfac, s[side]);
+    }
+    const double* lf = a.lface + (long)D * NFD * b.V + c;
+    double lF[5], lvb[2];
+    for (int v = 0; v < 5; v++) lF[v] = lf[(FD_F + v) * b.V];
+    lvb[0] = lf[FD_VB1 * b.V];
+    lvb[1] = lf[FD_VB2 * b.V];
+    double lcmax = lf[FD_CMAX * b.V], lcmin = lf[FD_CMIN * b.V];
+    const double lpL = s[0].lp.v, lpR = s[1].lp.v, lmL = s[0].lm.v, lmR = s[1].lm.v;
+    const double cmax = fmax(0.0, fmax(lpL, lpR));
+    const double cmin = -fmin(0.0, fmin(lmL, lmR));
+    const double den = cmax + cmin;
+    // adjoints of the side outputs: U (5), F (5), lm, lp, vt_T1, vt_T2
+    double gU[2][5], gF[2][5], glp[2] = {0, 0}, glm[2] = {0, 0}, gvt[2][2];
+    if (den > 0.0) {
+      const double id = 1.0 / den;
+      for (int v = 0; v < 5; v++) {
+        const double dU = s[1].U[v].v - s[0].U[v].v;
+        const double Fh = (cmin * s[1].F[v].v + cmax * s[0].F[v].v - cmax * cmin * dU) * id;
+        gF[0][v] = cmax * id * lF[v];
+        gF[1][v] = cmin * id * lF[v];
+        gU[0][v] = cmax * cmin * id * lF[v];
+        gU[1][v] = -cmax * cmin * id * lF[v];
+        lcmax += (s[0].F[v].v - cmin * dU - Fh) * id * lF[v];
+        lcmin += (s[1].F[v].v - cmax * dU - Fh) * id * lF[v];
+      }
+      const double vtL[2] = {s[0].vt[T1].v, s[0].vt[T2].v}, vtR[2] = {s[1].vt[T1].v, s[1].vt[T2].v};
+      for (int q = 0; q < 2; q++) {
+        const double vb = (cmax * vtL[q] + cmin * vtR[q]) * id;
+        gvt[0][q] = cmax * id * lvb[q];
+        gvt[1][q] = cmin * id * lvb[q];
+        lcmax += (vtL[q] - vb) * id * lvb[q];
+        lcmin += (vtR[q] - vb) * id * lvb[q];
+      }
+    } else {
+      for (int v = 0; v < 5; v++) {
+        gF[0][v] = gF[1][v] = 0.5 * lF[v];
+        gU[0][v] = gU[1][v] = 0.0;
+      }
+      for (int q = 0; q < 2; q++) gvt[0][q] = gvt[1][q] = 0.5 * lvb[q];
+    }
+    // c_max = max(0, lp_L, lp_R), c_min = -min(0, lm_L, lm_R): the branch taken carries the derivative
+    if (cmax > 0.0) {
+      if (lpR > lpL) glp[1] = lcmax;
+      else glp[0] = lcmax;
+    }
+    if (cmin > 0.0) {
+      if (lmR < lmL) glm[1] = -lcmin;
+      else glm[0] = -lcmin;
+    }
+    double gin[2][8];
+    for (int side = 0; side < 2; side++) {
+      for (int r = 0; r < 8; r++) {
+        double acc = glp[side] * s[side].lp.d[r] + glm[side] * s[side].lm.d[r] +
+                     gvt[side][0] * s[side].vt[T1].d[r] + gvt[side][1] * s[side].vt[T2].d[r];
+        for (int v = 0; v < 5; v++) acc += gU[side][v] * s[side].U[v].d[r] + gF[side][v] * s[side].F[v].d[r];
+        gin[side][r] = acc;
+      }
+    }
+    // left state = upper values of cell c - e_D, right state = lower values of cell c (each used once)
+    for (int v = 0; v < NREC; v++) {
+      a.lrec[(NREC + v) * b.V + c - st] = gin[0][v];
+      a.lrec[v * b.V + c] = gin[1][v];
+    }
+    a.lBf[D * b.V + c] += gin[0][7] + gin[1][7];
+  }
+}
+
+// Reconstruction along D (cells g-1 .. g+n along D, all transverse): each cell's (lower, upper) values of the 7
+// variables from its 5-cell stencil; the adjoints scatter to the stencil cells.
+template <int D, int SCHEME>
+__global__ void ka_recon(Blk b, Ws w, AdjWs a) {
+  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+  int lo[3] = {0, 0, 0}, ex[3] = {b.N[0], b.N[1], b.N[2]};
+  lo[D] = b.g - 1;
+  ex[D] = b.n[D] + 2;
+  const long count = (long)ex[0] * ex[1] * ex[2];
+  const long st = astr(b, D);
+  ALOOP(t, count) {
+    int p[3];
+    decode(t, lo[0], ex[0], lo[1], ex[1], lo[2], p[0], p[1], p[2]);
+    const long c = alin(b, p[0], p[1], p[2]);
+    const double* src[NREC] = {a.P.f[0], a.P.f[1], w.uvel, w.uvel + b.V, w.uvel + 2 * b.V, w.bc + T1 * b.V,
+                               w.bc + T2 * b.V};
+    double* dst[NREC] = {a.lP, a.lP + b.V, a.lu, a.lu + b.V, a.lu + 2 * b.V, a.lBc + T1 * b.V, a.lBc + T2 * b.V};
+    for (int v = 0; v < NREC; v++) {
+      const double glo = a.lrec[v * b.V + c], ghi = a.lrec[(NREC + v) * b.V + c];
+      if (glo == 0.0 && ghi == 0.0) continue;
+      typedef Dual<5> D5;
+      D5 s5[5];
+      for (int s = 0; s < 5; s++) s5[s] = D5::seed(src[v][c + (s - 2) * st], s);
+      D5 l, h;
+      recon5<SCHEME>(s5, l, h);
+      for (int s = 0; s < 5; s++) {
+        const double g = l.d[s] * glo + h.d[s] * ghi;
+        if (g != 0.0) atomicAdd(&dst[v][c + (s - 2) * st], g);
+      }
+    }
+  }
+}
+
+// u^i = W v^i at every cell: lambda_v += (du/dv)^T lambda_u.
+__global__ void ka_uvel(Blk b, Ws w, AdjWs a) {
+  const long count = (long)b.N[0] * b.N[1] * b.N[2];
+  ALOOP(t, count) {
+    int i, j, k;
+    decode(t, 0, b.N[0], 0, b.N[1], 0, i, j, k);
+    const long c = alin(b, i, j, k);
+    const double lu[3] = {a.lu[c], a.lu[b.V + c], a.lu[2 * b.V + c]};
+    if (lu[0] == 0.0 && lu[1] == 0.0 && lu[2] == 0.0) continue;
+    double g6[6];
+    for (int q = 0; q < 6; q++) g6[q] = w.cg[(CG_G + q) * b.V + c];
+    typedef Dual<3> D3;
+    const D3 v[3] = {D3::seed(a.P.f[2][c], 0), D3::seed(a.P.f[3][c], 1), D3::seed(a.P.f[4][c], 2)};
+    const D3 W = 1.0 / sqrt(1.0 - contract_sym(g6, v, v));
+    for (int r = 0; r < 3; r++) {
+      double acc = 0.0;
+      for (int q = 0; q < 3; q++) acc += (W * v[q]).d[r] * lu[q];
+      a.lP[(2 + r) * b.V + c] += acc;
+    }
+  }
+}
+
+// Transpose of one ghost sweep along AX: every ghost entry hands its adjoint to the owned entries it was
+// copied or extrapolated from, then becomes zero.  Sweeps are transposed in the reverse order z, y, x.
+template <int AX>
+__device__ __forceinline__ void ka_ghost(Blk b, double* const* f, const int* cell_like, const int* linear, int nf) {
+  constexpr int A1 = (AX + 1) % 3, A2 = (AX + 2) % 3;
+  const int g = b.g, n = b.n[AX], Nn = b.N[AX];
+  const long m1 = b.N[A1] + 1, m2 = b.N[A2] + 1;
+  const int slots = 2 * g + 1;
+  const long st = astr(b, AX);
+  const long count = slots * m1 * m2;
+  ALOOP(t, count) {
+    const int q = (int)(t % slots);
+    const long r = t / slots;
+    const int q1 = (int)(r % m1);
+    const int q2 = (int)(r / m1);
+    const int i = (q < g) ? q : Nn - 2 * g + q;
+    int pp[3];
+    pp[AX] = 0;
+    pp[A1] = q1;
+    pp[A2] = q2;
+    const long base = alin(b, pp[0], pp[1], pp[2]);
+    for (int fi = 0; fi < nf; fi++) {
+      const bool cl = (cell_like[fi] >> AX) & 1;
+      const int lo = g;
+      const int hi = (cl || b.bc[AX] == 0) ? g + n - 1 : g + n;
+      if (i >= lo && i <= hi) continue;
+      double* aa = f[fi] + base;
+      const double lam = aa[i * st];
+      if (lam == 0.0) continue;
+      aa[i * st] = 0.0;
+      if (b.bc[AX] == 0) {
+        const int src = lo + (((i - lo) % n) + n) % n;
+        atomicAdd(&aa[src * st], lam);
+      } else {
+        const int e0 = (i < lo) ? lo : hi;
+        if (linear[fi] && hi > lo) {
+          const int e1 = (i < lo) ? lo + 1 : hi - 1;
+          const double kk = (double)(i < lo ? lo - i : i - hi);
+          atomicAdd(&aa[e0 * st], (1.0 + kk) * lam);
+          atomicAdd(&aa[e1 * st], -kk * lam);
+        } else {
+          atomicAdd(&aa[e0 * st], lam);
+        }
+      }
+    }
+  }
+}
+
+// Recovery by the implicit-function theorem at the root: prim2con(P, B) = U, so with Jp = d prim2con / dP and
+// Jb = d prim2con / dB (dual numbers through prim->cons), lambda_U += Jp^-T lambda_P and lambda_B -= Jb^T
+// Jp^-T lambda_P.  Interior cells; atmosphere cells (flag 2 or -1) pass nothing.
+__global__ void ka_c2p(Blk b, Ws w, AdjWs a, double gamma, double gfac) {
+  const long count = (long)b.n[0] * b.n[1] * b.n[2];
+  ALOOP(t, count) {
+    int i, j, k;
+    decode(t, b.g, b.n[0], b.g, b.n[1], b.g, i, j, k);
+    const long c = alin(b, i, j, k);
+    double lp[5];
+    bool any = false;
+    for (int r = 0; r < 5; r++) {
+      lp[r] = a.lP[r * b.V + c];
+      any = any || lp[r] != 0.0;
+    }
+    if (!any || a.flags[c] == 2 || a.flags[c] == -1) continue;
+    Geo m;
+    load_geo(b, w.cg, c, m);
+    typedef Dual<8> D8;
+    const D8 rho = D8::seed(a.P.f[0][c], 0), press = D8::seed(a.P.f[1][c], 1);
+    const D8 v[3] = {D8::seed(a.P.f[2][c], 2), D8::seed(a.P.f[3][c], 3), D8::seed(a.P.f[4][c], 4)};
+    const D8 B[3] = {D8::seed(w.bc[c], 5), D8::seed(w.bc[b.V + c], 6), D8::seed(w.bc[2 * b.V + c], 7)};
+    const D8 W = 1.0 / sqrt(1.0 - contract_sym(m.g, v, v));
+    const D8 u[3] = {W * v[0], W * v[1], W * v[2]};
+    SideOutT<D8> o;
+    face_side(m, 1.0 / m.alp, m.alp * sqrt(m.gu[0]), 0, rho, press, u, B, gamma, gfac, o);
+    // solve Jp^T x = lambda_P (5x5, partial pivoting); Jp[row q][col r] = dU_q / dP_r
+    double M[5][6];
+    for (int r = 0; r < 5; r++) {
+      for (int q = 0; q < 5; q++) M[r][q] = o.U[q].d[r];
+      M[r][5] = lp[r];
+    }
+    for (int col = 0; col < 5; col++) {
+      int piv = col;
+      for (int r = col + 1; r < 5; r++)
+        if (::fabs(M[r][col]) > ::fabs(M[piv][col])) piv = r;
+      if (piv != col)
+        for (int q = 0; q < 6; q++) {
+          const double tmp = M[col][q];
+          M[col][q] = M[piv][q];
+          M[piv][q] = tmp;
+        }
+      const double inv = 1.0 / M[col][col];
+      for (int r = col + 1; r < 5; r++) {
+        const double f = M[r][col] * inv;
+        for (int q = col; q < 6; q++) M[r][q] -= f * M[col][q];
+      }
+    }
+    double x[5];
+    for (int r = 4; r >= 0; r--) {
+      double acc = M[r][5];
+      for (int q = r + 1; q < 5; q++) acc -= M[r][q] * x[q];
+      x[r] = acc / M[r][r];
+    }
+    for (int q = 0; q < 5; q++) a.lY[q * b.V + c] += x[q];
+    for (int r = 0; r < 3; r++) {
+      double acc = 0.0;
+      for (int q = 0; q < 5; q++) acc += o.U[q].d[5 + r] * x[q];
+      a.lBc[r * b.V + c] -= acc;
+    }
+  }
+}
+
+// Centre field B^d(c) = (B~^d(c) + B~^d(c + e_d)) / (2 sqrt(g_c)): each face gathers its two cells.
+__global__ void ka_bcentre(Blk b, Ws w, AdjWs a) {
+  const long count = b.V;
+  ALOOP(t, count) {
+    int p[3];
+    decode(t, 0, b.N[0] + 1, 0, b.N[1] + 1, 0, p[0], p[1], p[2]);
+    const long c = alin(b, p[0], p[1], p[2]);
+    for (int d = 0; d < 3; d++) {
+      double acc = 0.0;
+      // cell c (if it exists) and cell c - e_d (if it exists)
+      bool cell_c = p[0] < b.N[0] && p[1] < b.N[1] && p[2] < b.N[2];
+      if (cell_c) acc += 0.5 * a.lBc[d * b.V + c] / w.cg[CG_SQG * b.V + c];
+      int q[3] = {p[0], p[1], p[2]};
+      q[d] -= 1;
+      bool cell_m = q[d] >= 0 && q[0] < b.N[0] && q[1] < b.N[1] && q[2] < b.N[2];
+      if (cell_m) {
+        const long cm = c - astr(b, d);
+        acc += 0.5 * a.lBc[d * b.V + cm] / w.cg[CG_SQG * b.V + cm];
+      }
+      if (acc != 0.0) a.lBf[d * b.V + c] += acc;
+    }
+  }
+}
+
+// B~ = curl A on faces (transposed): each edge gathers the faces that difference it.
+__global__ void ka_curl(Blk b, AdjWs a) {
+  const long count = b.V;
+  ALOOP(t, count) {
+    int p[3];
+    decode(t, 0, b.N[0] + 1, 0, b.N[1] + 1, 0, p[0], p[1], p[2]);
+    const long c = alin(b, p[0], p[1], p[2]);
+    const double* bx = a.lBf;
+    const double* by = a.lBf + b.V;
+    const double* bz = a.lBf + 2 * b.V;
+    // validity of a face entry: x-faces need j < N1, k < N2; y-faces i < N0, k < N2; z-faces i < N0, j < N1
+    auto fx = [&](int i, int j, int k) {
+      return (i >= 0 && j >= 0 && k >= 0 && i <= b.N[0] && j < b.N[1] && k < b.N[2]) ? bx[alin(b, i, j, k)] : 0.0;
+    };
+    auto fy = [&](int i, int j, int k) {
+      return (i >= 0 && j >= 0 && k >= 0 && i < b.N[0] && j <= b.N[1] && k < b.N[2]) ? by[alin(b, i, j, k)] : 0.0;
+    };
+    auto fz = [&](int i, int j, int k) {
+      return (i >= 0 && j >= 0 && k >= 0 && i < b.N[0] && j < b.N[1] && k <= b.N[2]) ? bz[alin(b, i, j, k)] : 0.0;
+    };
+    const int i = p[0], j = p[1], k = p[2];
+    // bx(c) = (Az(c+sy) - Az(c)) idy - (Ay(c+sz) - Ay(c)) idz
+    // by(c) = (Ax(c+sz) - Ax(c)) idz - (Az(c+1) - Az(c)) idx
+    // bz(c) = (Ay(c+1) - Ay(c)) idx - (Ax(c+sy) - Ax(c)) idy
+    const double lAx = (fy(i, j, k - 1) - fy(i, j, k)) * b.idx[2] - (fz(i, j - 1, k) - fz(i, j, k)) * b.idx[1];
+    const double lAy = (fz(i - 1, j, k) - fz(i, j, k)) * b.idx[0] - (fx(i, j, k - 1) - fx(i, j, k)) * b.idx[2];
+    const double lAz = (fx(i, j - 1, k) - fx(i, j, k)) * b.idx[1] - (fy(i - 1, j, k) - fy(i, j, k)) * b.idx[0];
+    a.lY[5 * b.V + c] += lAx;
+    a.lY[6 * b.V + c] += lAy;
+    a.lY[7 * b.V + c] += lAz;
+  }
+}
+
+struct GhostArgs {
+  double* f[9];
+  int cl[9];
+  int lin[9];
+};
+
+template <int AX>
+__global__ void ka_ghost_k(Blk b, GhostArgs g, int nf) {
+  ka_ghost<AX>(b, g.f, g.cl, g.lin, nf);
+}
+
+void launch_ghost_adjoint(const Blk& b, const AdjGhost& ag, int nf, cudaStream_t s) {
+  GhostArgs g;
+  for (int f = 0; f < nf; f++) {
+    g.f[f] = ag.f[f];
+    g.cl[f] = ag.cl[f];
+    g.lin[f] = ag.lin[f];
+  }
+  const int T = 128;
+  const int slots = 2 * b.g + 1;
+  ka_ghost_k<2><<<agrid((long)slots * (b.N[0] + 1) * (b.N[1] + 1), T), T, 0, s>>>(b, g, nf);
+  ka_ghost_k<1><<<agrid((long)slots * (b.N[2] + 1) * (b.N[0] + 1), T), T, 0, s>>>(b, g, nf);
+  ka_ghost_k<0><<<agrid((long)slots * (b.N[1] + 1) * (b.N[2] + 1), T), T, 0, s>>>(b, g, nf);
+}
+
+// elementwise helpers of the RK4 adjoint
+__global__ void ka_axpby9(Blk b, double alpha, F9 x, double beta, F9 y) {
+  ALOOP(t, 9 * b.V) {
+    const int f = (int)(t / b.V);
+    const long c = t - (long)f * b.V;
+    y.f[f][c] = alpha * x.f[f][c] + beta * y.f[f][c];
+  }
+}
+
+// Keeps the independent entries: g..g+n-1 along cell-like axes and along periodic axes (where the vertex index
+// g+n is the periodic image of g), g..g+n along vertex-like axes with copy BCs.
+__global__ void ka_mask_owned9(Blk b, F9 x) {
+  const int cl[9] = {7, 7, 7, 7, 7, 1, 2, 4, 0};
+  ALOOP(t, 9 * b.V) {
+    const int f = (int)(t / b.V);
+    const long c = t - (long)f * b.V;
+    int p[3];
+    decode(c, 0, b.N[0] + 1, 0, b.N[1] + 1, 0, p[0], p[1], p[2]);
+    bool own = true;
+    for (int d = 0; d < 3; d++) {
+      const int hi = (((cl[f] >> d) & 1) || b.bc[d] == 0) ? b.g + b.n[d] - 1 : b.g + b.n[d];
+      own = own && p[d] >= b.g && p[d] <= hi;
+    }
+    if (!own) x.f[f][c] = 0.0;
+  }
+}
+
+cudaError_t launch_axpby9(const Blk& b, double alpha, const F9& x, double beta, const F9& y, cudaStream_t s) {
+  ka_axpby9<<<agrid(9 * b.V, 256), 256, 0, s>>>(b, alpha, x, beta, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask_owned9(const Blk& b, const F9& x, cudaStream_t s) {
+  ka_mask_owned9<<<agrid(9 * b.V, 256), 256, 0, s>>>(b, x);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------------------------------
+// Orchestration of the VJP of the right-hand side at the state held in a.Y (ghost fill, recovery and the
+// forward intermediates are recomputed here); mu on owned ranges in a.mu; result in a.lY (owned ranges).
+
+template <int D>
+static void adjoint_dir(const StageArgs& sa, const AdjWs& a, cudaStream_t s) {
+  const Blk& b = sa.b;
+  const int T = 128;
+  launch_recon_dir(sa, a.P, D, s);  // forward reconstruction of this direction into the workspace
+  const long fc = (long)b.N[0] * b.N[1] * b.N[2] / b.N[D] * (b.n[D] + 1);
+  cudaMemsetAsync(a.lrec, 0, 2 * NREC * b.V * sizeof(double), s);
+  ka_faces<D><<<agrid(fc, T), T, 0, s>>>(b, sa.w, a, sa.gamma, sa.gfac);
+  const long rc = (long)b.N[0] * b.N[1] * b.N[2] / b.N[D] * (b.n[D] + 2);
+  if (sa.recon == 0) ka_recon<D, 0><<<agrid(rc, T), T, 0, s>>>(b, sa.w, a);
+  else if (sa.recon == 1) ka_recon<D, 1><<<agrid(rc, T), T, 0, s>>>(b, sa.w, a);
+  else ka_recon<D, 2><<<agrid(rc, T), T, 0, s>>>(b, sa.w, a);
+}
+
+cudaError_t launch_rhs_adjoint(const StageArgs& sa, const AdjWs& a, double dt, cudaStream_t s) {
+  const Blk& b = sa.b;
+  const int T = 128;
+  // forward recompute: ghost fill of Y, face/centre field, recovery (flags), primitive ghost fill, forward RHS
+  // intermediates (u, face data of every direction)
+  cudaError_t e = launch_ghost_state(b, a.Y, s);
+  if (e == cudaSuccess) e = launch_bfield(b, sa.w, a.Y, s);
+  if (e == cudaSuccess) e = launch_c2p(sa, a.Y, a.P, a.flags, nullptr, s);
+  if (e == cudaSuccess) e = launch_ghost_prims(b, a.P, s);
+  if (e == cudaSuccess) e = launch_rhs(sa, a.Y, a.P, -1, dt, a.Y, a.Y, a.Y, a.dscratch, s);
+  if (e != cudaSuccess) return e;
+  // adjoint accumulators
+  cudaMemsetAsync(a.lY_base, 0, (size_t)ADJ_ACC_FIELDS * b.V * sizeof(double), s);
+  const int lorenz = (sa.gauge == 0);
+  const double xi = sa.xi > 0.0 ? sa.xi : 1.5 / dt;
+  for (int D = 0; D < 3; D++) {
+    const long fc = (long)b.n[0] * b.n[1] * b.n[2] / b.n[D] * (b.n[D] + 1);
+    ka_flux_div<<<agrid(fc, T), T, 0, s>>>(b, a, a.mu, D);
+  }
+  ka_sources<<<agrid((long)b.n[0] * b.n[1] * b.n[2], T), T, 0, s>>>(b, sa.w, a, a.P, a.mu, sa.gfac);
+  const long vc = (long)(b.n[0] + 3) * (b.n[1] + 3) * (b.n[2] + 3);
+  if (lorenz) ka_psi<<<agrid(vc, T), T, 0, s>>>(b, sa.w, a, a.mu, xi);
+  ka_grad_ga<<<agrid(vc, T), T, 0, s>>>(b, a, a.mu);
+  const long ec = (long)(b.n[0] + 1) * (b.n[1] + 1) * (b.n[2] + 1);
+  ka_edges<0><<<agrid(ec, T), T, 0, s>>>(b, sa.w, a, a.mu);
+  ka_edges<1><<<agrid(ec, T), T, 0, s>>>(b, sa.w, a, a.mu);
+  ka_edges<2><<<agrid(ec, T), T, 0, s>>>(b, sa.w, a, a.mu);
+  ka_vertex<<<agrid(vc, T), T, 0, s>>>(b, sa.w, a, lorenz);
+  ka_vertex_to_edges<<<agrid((long)(b.n[0] + 4) * (b.n[1] + 4) * (b.n[2] + 4), T), T, 0, s>>>(b, a);
+  adjoint_dir<0>(sa, a, s);
+  adjoint_dir<1>(sa, a, s);
+  adjoint_dir<2>(sa, a, s);
+  ka_uvel<<<agrid((long)b.N[0] * b.N[1] * b.N[2], T), T, 0, s>>>(b, sa.w, a);
+  // primitive ghost fill, transposed (z, y, x)
+  {
+    AdjGhost g;
+    for (int f = 0; f < 5; f++) {
+      g.f[f] = a.lP + f * b.V;
+      g.cl[f] = 7;
+      g.lin[f] = 0;
+    }
+    launch_ghost_adjoint(b, g, 5, s);
+  }
+  ka_c2p<<<agrid((long)b.n[0] * b.n[1] * b.n[2], T), T, 0, s>>>(b, sa.w, a, sa.gamma, sa.gfac);
+  ka_bcentre<<<agrid(b.V, T), T, 0, s>>>(b, sa.w, a);
+  ka_curl<<<agrid(b.V, T), T, 0, s>>>(b, a);
+  {
+    AdjGhost g;
+    const int cl[9] = {7, 7, 7, 7, 7, 1, 2, 4, 0};
+    for (int f = 0; f < 9; f++) {
+      g.f[f] = a.lY + f * b.V;
+      g.cl[f] = cl[f];
+      g.lin[f] = (f >= 5 && f <= 7);
+    }
+    launch_ghost_adjoint(b, g, 9, s);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace asterx

@@ -174,6 +174,8 @@ __global__ void k_geom_face(Blk b, CF16 m, double* __restrict__ fg) {
     }
     out[FG_SQG * b.V + c] = sqg;
     out[FG_IALP * b.V + c] = 1.0 / val[0];
+    out[FG_ISQG * b.V + c] = 1.0 / sqg;
+    out[FG_WIDTH * b.V + c] = val[0] * sqrt(gu[sym(D, D)]);
   }
 }
 

@@ -45,6 +45,44 @@ cudaError_t launch_rhs(const StageArgs& a, const F9& Us, const F5& P, int stage,
 cudaError_t launch_batch_stage(const StageArgs& a, const BlockRec* tab, const long* off, const long* host_total,
                                int nb, int stage, double dt, unsigned long long* stats, cudaStream_t s);
 
+// ---- adjoint ----
+// accumulators cleared together at the start of each right-hand-side adjoint (contiguous, in this order)
+constexpr int ADJ_ACC_FIELDS = 9 + 5 + 3 + 3 + 3 + 3 * NFD + 1 + 3 + 3;
+
+struct AdjWs {
+  F9 Y;            // the state the right-hand side is linearised at (a copy; ghost-filled, atmosphere-reset)
+  F5 P;            // primitives recovered from Y (caller's buffers; the entry values are the guess)
+  F9 mu;           // adjoint of dU/dt (owned ranges read)
+  F9 dscratch;     // forward right-hand side of the recompute (unused)
+  signed char* flags;
+  double* lY_base;  // start of the ADJ_ACC_FIELDS accumulators
+  double* lY;       // 9: result, adjoint of Y
+  double* lP;       // 5: primitives
+  double* lu;       // 3: u = W v
+  double* lBc;      // 3: centre field
+  double* lBf;      // 3: face field B~
+  double* lface;    // 3 * NFD: face data
+  double* lGA;      // 1: G_A at vertices
+  double* lFpsi;    // 3: F_Psi at vertices
+  double* lAv;      // 3: vertex-averaged A
+  double* lrec;     // 2 * NREC: reconstructed values of the current direction
+};
+
+struct AdjGhost {
+  double* f[9];
+  int cl[9];
+  int lin[9];
+};
+
+// forward reconstruction of one direction into the workspace
+cudaError_t launch_recon_dir(const StageArgs& a, const F5& P, int D, cudaStream_t s);
+// lambda = (dL/dY)^T mu at the state a.Y (recomputes the forward intermediates)
+cudaError_t launch_rhs_adjoint(const StageArgs& sa, const AdjWs& a, double dt, cudaStream_t s);
+void launch_ghost_adjoint(const Blk& b, const AdjGhost& g, int nf, cudaStream_t s);
+// y = alpha x + beta y over every entry of 9 fields; zero the entries outside the owned ranges of 9 fields
+cudaError_t launch_axpby9(const Blk& b, double alpha, const F9& x, double beta, const F9& y, cudaStream_t s);
+cudaError_t launch_mask_owned9(const Blk& b, const F9& x, cudaStream_t s);
+
 // face-kernel launch timing (measurement hook of the benchmark)
 cudaError_t profile_enable(int cap);
 void profile_disable();

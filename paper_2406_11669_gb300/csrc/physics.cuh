@@ -9,6 +9,9 @@
 
 #include <cuda_runtime.h>
 
+#include "dual.cuh"
+#include "layout.h"
+
 namespace asterx {
 
 __host__ __device__ constexpr int sym(int a, int b) {
@@ -24,13 +27,15 @@ struct Geo {
   double sqg;    // sqrt(det gamma)
 };
 
-__device__ __forceinline__ double contract_sym(const double m[6], const double a[3], const double b[3]) {
+template <class T>
+__device__ __forceinline__ T contract_sym(const double m[6], const T a[3], const T b[3]) {
   return m[0] * a[0] * b[0] + m[3] * a[1] * b[1] + m[5] * a[2] * b[2] +
          m[1] * (a[0] * b[1] + a[1] * b[0]) + m[2] * (a[0] * b[2] + a[2] * b[0]) +
          m[4] * (a[1] * b[2] + a[2] * b[1]);
 }
 
-__device__ __forceinline__ void lower(const double m[6], const double a[3], double out[3]) {
+template <class T>
+__device__ __forceinline__ void lower(const double m[6], const T a[3], T out[3]) {
   out[0] = m[0] * a[0] + m[1] * a[1] + m[2] * a[2];
   out[1] = m[1] * a[0] + m[3] * a[1] + m[4] * a[2];
   out[2] = m[2] * a[0] + m[4] * a[1] + m[5] * a[2];
@@ -61,12 +66,14 @@ __device__ __forceinline__ void sym_inverse(const double g[6], double gu[6], dou
 //   alpha sqrt(g) F^d:  D~ vt,  S~_j vt + a sqrt(g) (p_t delta^d_j - b_j B^d / W),  tau~ vt + a sqrt(g) (p_t v^d - (B.v) B^d)
 // with vt = alpha v^d - beta^d, p_t = p + b^2/2.
 
-struct SideOut {
-  double U[5];
-  double F[5];
-  double lm, lp;  // lambda_-, lambda_+
-  double vt[3];   // v~^i = alpha v^i - beta^i
+template <class T>
+struct SideOutT {
+  T U[5];
+  T F[5];
+  T lm, lp;  // lambda_-, lambda_+
+  T vt[3];   // v~^i = alpha v^i - beta^i
 };
+using SideOut = SideOutT<double>;
 
 // Extreme roots of the magnetosonic quartic (Sec. 3.3): with phi = (-lambda, e_d),
 //   a = u^mu phi_mu = ud - lambda u0,  Bc = b^mu phi_mu = bd - lambda b0,
@@ -98,102 +105,148 @@ struct Quartic {
   }
 };
 
-// gfac = Gamma / (Gamma - 1), ia = 1 / alpha (both hoisted by the caller)
-__device__ __forceinline__ void face_side(const Geo& m, double ia, int d, double rho, double press,
-                                          const double u[3], const double B[3], double gamma, double gfac,
-                                          SideOut& o) {
-  const double uu = contract_sym(m.g, u, u);
-  const double W = sqrt(1.0 + uu);
-  const double iW = 1.0 / W;
-  double v[3] = {u[0] * iW, u[1] * iW, u[2] * iW};
-  double vl[3], Bl[3];
+// The same quartic with state-dependent coefficients of scalar type T: one Newton step from the converged root
+// lam (a constant) gives lam - Q/Q', whose derivative is the implicit-function derivative -Q_theta / Q_lam.
+template <class T>
+struct QuarticT {
+  T A4, C2, cs2, u0, ud, b0, bd;
+  double betad, ia2, gdd;
+  __device__ __forceinline__ T root_step(double lam) const {
+    const T a = ud - lam * u0;
+    const T bc = bd - lam * b0;
+    const double lb = lam + betad;
+    const double G = gdd - lb * lb * ia2;
+    const double dG = -2.0 * lb * ia2;
+    const T a2 = a * a;
+    const T r = cs2 * bc * bc - C2 * a2;
+    const T dr = -2.0 * (cs2 * bc * b0 - C2 * a * u0);
+    const T q = A4 * a2 * a2 + r * G;
+    const T dq = -4.0 * A4 * a2 * a * u0 + dr * G + r * dG;
+    return lam - q / dq;
+  }
+};
+
+// gfac = Gamma / (Gamma - 1), ia = 1 / alpha, width = alpha sqrt(gamma^dd) (hoisted by the caller)
+template <class T>
+__device__ __forceinline__ void face_side(const Geo& m, double ia, double width, int d, T rho, T press,
+                                          const T u[3], const T B[3], double gamma, double gfac,
+                                          SideOutT<T>& o) {
+  const T uu = contract_sym(m.g, u, u);
+  const T W = sqrt(1.0 + uu);
+  const T iW = 1.0 / W;
+  T v[3] = {u[0] * iW, u[1] * iW, u[2] * iW};
+  T vl[3], Bl[3];
   lower(m.g, v, vl);
   lower(m.g, B, Bl);
-  const double B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
-  const double Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
-  const double iW2 = iW * iW;
-  const double b2 = B2 * iW2 + Bv * Bv;
-  const double rhoh = rho + gfac * press;
-  const double W2 = W * W;
-  const double z = rhoh * W2;
+  const T B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const T Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
+  const T iW2 = iW * iW;
+  const T b2 = B2 * iW2 + Bv * Bv;
+  const T rhoh = rho + gfac * press;
+  const T W2 = W * W;
+  const T z = rhoh * W2;
   const double sg = m.sqg;
   const double asg = m.alp * sg;
   o.U[0] = sg * rho * W;
   for (int a = 0; a < 3; a++) o.U[1 + a] = sg * ((z + B2) * vl[a] - Bv * Bl[a]);
   o.U[4] = sg * (z - press - rho * W + B2 - 0.5 * b2);
   for (int a = 0; a < 3; a++) o.vt[a] = m.alp * v[a] - m.beta[a];
-  const double vt = o.vt[d];
-  const double pt = press + 0.5 * b2;
-  const double Bd = B[d];
+  const T vt = o.vt[d];
+  const T pt = press + 0.5 * b2;
+  const T Bd = B[d];
   o.F[0] = o.U[0] * vt;
   for (int a = 0; a < 3; a++) {
-    const double bl = Bl[a] * iW + W * Bv * vl[a];
+    const T bl = Bl[a] * iW + W * Bv * vl[a];
     o.F[1 + a] = o.U[1 + a] * vt - asg * bl * Bd * iW;
   }
   o.F[1 + d] += asg * pt;
   o.F[4] = o.U[4] * vt + asg * (pt * v[d] - Bv * Bd);
 
   // magnetosonic speeds
-  const double u0 = W * ia;
-  const double ud = W * (v[d] - m.beta[d] * ia);
-  const double b0 = W * Bv * ia;
-  const double bd = (Bd + m.alp * b0 * ud) * iW;
+  const T u0 = W * ia;
+  const T ud = W * (v[d] - m.beta[d] * ia);
+  const T b0 = W * Bv * ia;
+  const T bd = (Bd + m.alp * b0 * ud) * iW;
+  // one division for cs^2 = Gamma p / (rho h) (= Gamma (Gamma - 1) eps / h) and cA^2 = b^2 / (rho h + b^2)
+  const T ihb = 1.0 / (rhoh * (rhoh + b2));
+  const T cs2 = gamma * press * (rhoh + b2) * ihb;
+  const T ca2 = b2 * rhoh * ihb;
   Quartic Q;
-  Q.cs2 = gamma * press / rhoh;  // = Gamma (Gamma - 1) eps / h for the ideal gas
-  Q.A4 = rhoh * (1.0 - Q.cs2);
-  Q.C2 = rhoh * Q.cs2 + b2;
-  Q.u0 = u0;
-  Q.ud = ud;
-  Q.b0 = b0;
-  Q.bd = bd;
+  Q.cs2 = val(cs2);
+  Q.A4 = val(rhoh) * (1.0 - Q.cs2);
+  Q.C2 = val(rhoh) * Q.cs2 + val(b2);
+  Q.u0 = val(u0);
+  Q.ud = val(ud);
+  Q.b0 = val(b0);
+  Q.bd = val(bd);
   Q.betad = m.beta[d];
   Q.ia2 = ia * ia;
   Q.gdd = m.gu[sym(d, d)];
-  const double width = m.alp * sqrt(Q.gdd);
   // Starting points: the lab-frame speeds of an isotropic wave with the perpendicular fast speed
   // c^2 = cs^2 + cA^2 - cs^2 cA^2 (cA^2 = b^2 / (rho h + b^2)), which bounds the fast magnetosonic speed in
   // every direction, so both starts lie outside the extreme roots and Newton converges monotonically from
   // there (as from the light cone, but from much closer).  Clamped to the light cone.
-  const double ca2 = b2 / (rhoh + b2);
-  const double c2 = Q.cs2 + ca2 - Q.cs2 * ca2;
-  const double v2 = 1.0 - iW2;
+  const double c2 = Q.cs2 + val(ca2) - Q.cs2 * val(ca2);
+  const double v2 = 1.0 - val(iW2);
   const double den = 1.0 - v2 * c2;
-  const double disc = fmax((1.0 - v2) * (Q.gdd * den - v[d] * v[d] * (1.0 - c2)), 0.0);
+  const double vd = val(v[d]);
+  const double disc = fmax((1.0 - v2) * (Q.gdd * den - vd * vd * (1.0 - c2)), 0.0);
   const double spread = sqrt(c2 * disc);
   const double idn = m.alp / den;
-  const double mid = v[d] * (1.0 - c2);
+  const double mid = vd * (1.0 - c2);
   const double lc = -m.beta[d];
   const double lp0 = fmin((mid + spread) * idn - m.beta[d] + 1e-12 * width, lc + width);
   const double lm0 = fmax((mid - spread) * idn - m.beta[d] - 1e-12 * width, lc - width);
-  o.lp = Q.newton(lp0, width);
-  o.lm = Q.newton(lm0, width);
+  const double lp = Q.newton(lp0, width);
+  const double lm = Q.newton(lm0, width);
+  if constexpr (sizeof(T) == sizeof(double)) {
+    o.lp = lp;
+    o.lm = lm;
+  } else {
+    QuarticT<T> QT;
+    QT.cs2 = cs2;
+    QT.A4 = rhoh * (1.0 - cs2);
+    QT.C2 = rhoh * cs2 + b2;
+    QT.u0 = u0;
+    QT.ud = ud;
+    QT.b0 = b0;
+    QT.bd = bd;
+    QT.betad = Q.betad;
+    QT.ia2 = Q.ia2;
+    QT.gdd = Q.gdd;
+    o.lp = QT.root_step(lp);
+    o.lm = QT.root_step(lm);
+  }
 }
 
 // ----------------------------------------------------------------------------------------------------------
 // Reconstruction of one cell from a_{i-2..i+2}: values at its lower (lo) and upper (hi) faces.
 
-__device__ __forceinline__ double minmod2(double x, double y) {
-  if (x * y <= 0.0) return 0.0;
+template <class T>
+__device__ __forceinline__ T minmod2(T x, T y) {
+  if (x * y <= 0.0) return T(0.0);
   return (fabs(x) <= fabs(y)) ? x : y;
 }
 
-__device__ __forceinline__ double ppm_dq(double am, double a0, double ap) {
+template <class T>
+__device__ __forceinline__ T ppm_dq(T am, T a0, T ap) {
   // van Leer limited slope of Colella & Woodward (1984)
-  if ((ap - a0) * (a0 - am) <= 0.0) return 0.0;
-  const double c = 0.5 * (ap - am);
-  const double s = fmin(fabs(c), fmin(2.0 * fabs(a0 - am), 2.0 * fabs(ap - a0)));
+  if ((ap - a0) * (a0 - am) <= 0.0) return T(0.0);
+  const T c = 0.5 * (ap - am);
+  const T s = fmin(fabs(c), fmin(2.0 * fabs(a0 - am), 2.0 * fabs(ap - a0)));
   return (c < 0.0) ? -s : s;
 }
 
-__device__ __forceinline__ void ppm_limit(double ai, double& l, double& r) {
+template <class T>
+__device__ __forceinline__ void ppm_limit(T ai, T& l, T& r) {
   // monotonicity constraints of the parabola (CW84)
   if ((r - ai) * (ai - l) <= 0.0) {
     l = ai;
     r = ai;
   } else {
-    const double dlr = r - l;
-    const double mid = ai - 0.5 * (l + r);
-    const double d6 = dlr * dlr * (1.0 / 6.0);
+    const T dlr = r - l;
+    const T mid = ai - 0.5 * (l + r);
+    const T d6 = dlr * dlr * (1.0 / 6.0);
     if (dlr * mid > d6) l = 3.0 * ai - 2.0 * r;
     else if (-d6 > dlr * mid) r = 3.0 * ai - 2.0 * l;
   }
@@ -202,18 +255,19 @@ __device__ __forceinline__ void ppm_limit(double ai, double& l, double& r) {
 // WENO-Z values at both faces of the middle cell of s[0..4].  The lower face uses the mirrored stencil, whose
 // smoothness indicators are those of the upper face in reverse order, so the three indicators and the three
 // ratios tau5 / (beta_k + eps) are shared; the three reciprocals come from one division.
-__device__ __forceinline__ void wenoz_both(const double s[5], double& lo, double& hi) {
-  const double t0a = s[0] - 2.0 * s[1] + s[2], t0b = s[0] - 4.0 * s[1] + 3.0 * s[2];
-  const double t1a = s[1] - 2.0 * s[2] + s[3], t1b = s[1] - s[3];
-  const double t2a = s[2] - 2.0 * s[3] + s[4], t2b = 3.0 * s[2] - 4.0 * s[3] + s[4];
-  const double e0 = (13.0 / 12.0) * t0a * t0a + 0.25 * t0b * t0b + 1e-40;
-  const double e1 = (13.0 / 12.0) * t1a * t1a + 0.25 * t1b * t1b + 1e-40;
-  const double e2 = (13.0 / 12.0) * t2a * t2a + 0.25 * t2b * t2b + 1e-40;
-  const double tau5 = fabs(e0 - e2);
-  const double e01 = e0 * e1;
-  const double inv = 1.0 / (e01 * e2);
-  double r0, r1, r2;
-  if (isfinite(inv) && inv > 0.0) {
+template <class T>
+__device__ __forceinline__ void wenoz_both(const T s[5], T& lo, T& hi) {
+  const T t0a = s[0] - 2.0 * s[1] + s[2], t0b = s[0] - 4.0 * s[1] + 3.0 * s[2];
+  const T t1a = s[1] - 2.0 * s[2] + s[3], t1b = s[1] - s[3];
+  const T t2a = s[2] - 2.0 * s[3] + s[4], t2b = 3.0 * s[2] - 4.0 * s[3] + s[4];
+  const T e0 = (13.0 / 12.0) * t0a * t0a + 0.25 * t0b * t0b + 1e-40;
+  const T e1 = (13.0 / 12.0) * t1a * t1a + 0.25 * t1b * t1b + 1e-40;
+  const T e2 = (13.0 / 12.0) * t2a * t2a + 0.25 * t2b * t2b + 1e-40;
+  const T tau5 = fabs(e0 - e2);
+  const T e01 = e0 * e1;
+  const T inv = 1.0 / (e01 * e2);
+  T r0, r1, r2;
+  if (isfinite(val(inv)) && val(inv) > 0.0) {
     r0 = tau5 * (inv * (e1 * e2));
     r1 = tau5 * (inv * (e0 * e2));
     r2 = tau5 * (inv * e01);
@@ -222,37 +276,37 @@ __device__ __forceinline__ void wenoz_both(const double s[5], double& lo, double
     r1 = tau5 / e1;
     r2 = tau5 / e2;
   }
-  const double z0 = 1.0 + r0 * r0, z1 = 1.0 + r1 * r1, z2 = 1.0 + r2 * r2;
+  const T z0 = 1.0 + r0 * r0, z1 = 1.0 + r1 * r1, z2 = 1.0 + r2 * r2;
   // upper face: linear weights (1/10, 6/10, 3/10) on the sub-stencils ending at, centred on, starting at i
   {
-    const double q0 = (2.0 * s[0] - 7.0 * s[1] + 11.0 * s[2]) * (1.0 / 6.0);
-    const double q1 = (-s[1] + 5.0 * s[2] + 2.0 * s[3]) * (1.0 / 6.0);
-    const double q2 = (2.0 * s[2] + 5.0 * s[3] - s[4]) * (1.0 / 6.0);
-    const double w0 = 0.1 * z0, w1 = 0.6 * z1, w2 = 0.3 * z2;
+    const T q0 = (2.0 * s[0] - 7.0 * s[1] + 11.0 * s[2]) * (1.0 / 6.0);
+    const T q1 = (-s[1] + 5.0 * s[2] + 2.0 * s[3]) * (1.0 / 6.0);
+    const T q2 = (2.0 * s[2] + 5.0 * s[3] - s[4]) * (1.0 / 6.0);
+    const T w0 = 0.1 * z0, w1 = 0.6 * z1, w2 = 0.3 * z2;
     hi = (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
   }
   // lower face: mirrored stencil, indicator k of the mirror is indicator 2-k here
   {
-    const double q0 = (2.0 * s[4] - 7.0 * s[3] + 11.0 * s[2]) * (1.0 / 6.0);
-    const double q1 = (-s[3] + 5.0 * s[2] + 2.0 * s[1]) * (1.0 / 6.0);
-    const double q2 = (2.0 * s[2] + 5.0 * s[1] - s[0]) * (1.0 / 6.0);
-    const double w0 = 0.1 * z2, w1 = 0.6 * z1, w2 = 0.3 * z0;
+    const T q0 = (2.0 * s[4] - 7.0 * s[3] + 11.0 * s[2]) * (1.0 / 6.0);
+    const T q1 = (-s[3] + 5.0 * s[2] + 2.0 * s[1]) * (1.0 / 6.0);
+    const T q2 = (2.0 * s[2] + 5.0 * s[1] - s[0]) * (1.0 / 6.0);
+    const T w0 = 0.1 * z2, w1 = 0.6 * z1, w2 = 0.3 * z0;
     lo = (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
   }
 }
 
-template <int SCHEME>
-__device__ __forceinline__ void recon5(const double a[5], double& lo, double& hi) {
+template <int SCHEME, class T>
+__device__ __forceinline__ void recon5(const T a[5], T& lo, T& hi) {
   if (SCHEME == 0) {
-    const double s = minmod2(a[2] - a[1], a[3] - a[2]);
+    const T s = minmod2(a[2] - a[1], a[3] - a[2]);
     lo = a[2] - 0.5 * s;
     hi = a[2] + 0.5 * s;
   } else if (SCHEME == 1) {
-    const double dm = ppm_dq(a[0], a[1], a[2]);
-    const double d0 = ppm_dq(a[1], a[2], a[3]);
-    const double dp = ppm_dq(a[2], a[3], a[4]);
-    double l = a[1] + 0.5 * (a[2] - a[1]) - (d0 - dm) * (1.0 / 6.0);
-    double r = a[2] + 0.5 * (a[3] - a[2]) - (dp - d0) * (1.0 / 6.0);
+    const T dm = ppm_dq(a[0], a[1], a[2]);
+    const T d0 = ppm_dq(a[1], a[2], a[3]);
+    const T dp = ppm_dq(a[2], a[3], a[4]);
+    T l = a[1] + 0.5 * (a[2] - a[1]) - (d0 - dm) * (1.0 / 6.0);
+    T r = a[2] + 0.5 * (a[3] - a[2]) - (dp - d0) * (1.0 / 6.0);
     ppm_limit(a[2], l, r);
     lo = l;
     hi = r;
@@ -260,6 +314,72 @@ __device__ __forceinline__ void recon5(const double a[5], double& lo, double& hi
     wenoz_both(a, lo, hi);
   }
 }
+
+// Source terms (Eq. grmhdsrc in 3+1 form with the input K_ij, K = -1/2 L_n gamma of Sec. 2.1):
+//   tau~: alpha sqrt(g) [T^00 (b^i b^j K_ij - b^i d_i alpha) + T^0i (2 b^j K_ij - d_i alpha) + T^ij K_ij]
+//   S~_i: alpha sqrt(g) [-T^00 alpha d_i alpha + T^0_k d_i b^k + 1/2 (T^00 b^j b^k + 2 T^0j b^k + T^jk) d_i g_jk]
+// (b = beta) with T^{mu nu} = (rho h + b^2) u u + (p + b^2/2) g^{mu nu} - b b (Eq. tmunu); cg is the centre
+// geometry record (K_ij and the 4th-order metric derivatives at index c, field pitch V).
+template <class T>
+__device__ __forceinline__ void sources(const Geo& m, const double* __restrict__ cg, long V, long c, T rho, T press,
+                                          const T v[3], const T B[3], double gfac, T src[5]) {
+  T vl[3], Bl[3];
+  lower(m.g, v, vl);
+  lower(m.g, B, Bl);
+  const T W = 1.0 / sqrt(1.0 - (v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2]));
+  const T B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const T Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
+  const double ia = 1.0 / m.alp;
+  const T iW = 1.0 / W;
+  const T b2 = B2 * iW * iW + Bv * Bv;
+  const T rhoh = rho + gfac * press;
+  const T e = rhoh + b2;
+  const T pt = press + 0.5 * b2;
+  T u[4], bb[4];
+  u[0] = W * ia;
+  bb[0] = W * Bv * ia;
+  for (int q = 0; q < 3; q++) {
+    u[1 + q] = W * (v[q] - m.beta[q] * ia);
+    bb[1 + q] = (B[q] + m.alp * bb[0] * u[1 + q]) * iW;
+  }
+  const double ia2 = ia * ia;
+  const T T00 = e * u[0] * u[0] - pt * ia2 - bb[0] * bb[0];
+  T T0[3], Tij[6];
+  for (int q = 0; q < 3; q++) T0[q] = e * u[0] * u[1 + q] + pt * m.beta[q] * ia2 - bb[0] * bb[1 + q];
+  for (int q = 0; q < 3; q++)
+    for (int r = q; r < 3; r++)
+      Tij[sym(q, r)] = e * u[1 + q] * u[1 + r] + pt * (m.gu[sym(q, r)] - m.beta[q] * m.beta[r] * ia2) -
+                       bb[1 + q] * bb[1 + r];
+  double K[6], dalp[3];
+  for (int q = 0; q < 6; q++) K[q] = cg[(CG_K + q) * V + c];
+  for (int q = 0; q < 3; q++) dalp[q] = cg[(CG_DALP + q) * V + c];
+  double betal[3];
+  lower(m.g, m.beta, betal);
+  const double asg = m.alp * m.sqg;
+  double Kb[3];
+  for (int q = 0; q < 3; q++) Kb[q] = K[sym(q, 0)] * m.beta[0] + K[sym(q, 1)] * m.beta[1] + K[sym(q, 2)] * m.beta[2];
+  T st = T00 * (m.beta[0] * Kb[0] + m.beta[1] * Kb[1] + m.beta[2] * Kb[2]);
+  for (int q = 0; q < 3; q++) st += -T00 * m.beta[q] * dalp[q] + T0[q] * (2.0 * Kb[q] - dalp[q]);
+  st += Tij[0] * K[0] + Tij[3] * K[3] + Tij[5] * K[5] + 2.0 * (Tij[1] * K[1] + Tij[2] * K[2] + Tij[4] * K[4]);
+  src[0] = T(0.0);
+  src[4] = asg * st;
+  T T0l[3];
+  for (int q = 0; q < 3; q++)
+    T0l[q] = betal[q] * T00 + m.g[sym(q, 0)] * T0[0] + m.g[sym(q, 1)] * T0[1] + m.g[sym(q, 2)] * T0[2];
+  T M[6];
+  for (int q = 0; q < 3; q++)
+    for (int r = q; r < 3; r++)
+      M[sym(q, r)] = T00 * m.beta[q] * m.beta[r] + T0[q] * m.beta[r] + T0[r] * m.beta[q] + Tij[sym(q, r)];
+  for (int i = 0; i < 3; i++) {
+    T s = -T00 * m.alp * dalp[i];
+    for (int q = 0; q < 3; q++) s += T0l[q] * cg[(CG_DBETA + i * 3 + q) * V + c];
+    const double* dg = cg + (CG_DG + i * 6) * V + c;
+    s += 0.5 * (M[0] * dg[0] + M[3] * dg[3 * V] + M[5] * dg[5 * V]) + M[1] * dg[V] + M[2] * dg[2 * V] +
+         M[4] * dg[4 * V];
+    src[1 + i] = asg * s;
+  }
+}
+
 
 // ----------------------------------------------------------------------------------------------------------
 // Primitive recovery (Sec. 3.5) for one cell.  Inputs undensitised: D, S_i, tau, centre B^i.

@@ -254,7 +254,7 @@ struct Prim2Con {
     const double u[3] = {W * v[0], W * v[1], W * v[2]};
     const double B[3] = {r.w.bc[c], r.w.bc[b.V + c], r.w.bc[2 * b.V + c]};
     SideOut o;
-    face_side(m, 1.0 / m.alp, 0, r.P.f[0][c], r.P.f[1][c], u, B, k.gamma, k.gfac, o);
+    face_side(m, 1.0 / m.alp, m.alp * sqrt(m.gu[0]), 0, r.P.f[0][c], r.P.f[1][c], u, B, k.gamma, k.gfac, o);
     for (int a = 0; a < 5; a++) r.Us.f[a][c] = o.U[a];
   }
 };
@@ -478,7 +478,8 @@ struct Faces {
     }
     m.sqg = fg[FG_SQG * b.V + c];
     const double ia = fg[FG_IALP * b.V + c];
-    const double Bn = r.w.bf[D * b.V + c] / m.sqg;
+    const double width = fg[FG_WIDTH * b.V + c];
+    const double Bn = r.w.bf[D * b.V + c] * fg[FG_ISQG * b.V + c];
     SideOut s[2];
 #pragma unroll
     for (int side = 0; side < 2; side++) {
@@ -489,7 +490,7 @@ struct Faces {
       B[D] = Bn;
       B[T1] = rr[5 * b.V];
       B[T2] = rr[6 * b.V];
-      face_side(m, ia, D, rr[0], rr[b.V], u, B, k.gamma, k.gfac, s[side]);
+      face_side(m, ia, width, D, rr[0], rr[b.V], u, B, k.gamma, k.gfac, s[side]);
     }
     const double cmax = fmax(0.0, fmax(s[0].lp, s[1].lp));
     const double cmin = -fmin(0.0, fmin(s[0].lm, s[1].lm));
@@ -638,72 +639,6 @@ struct Psi {
     combine(k.stage, k.dt, c, 8, rr, r);
   }
 };
-
-// Source terms (Eq. grmhdsrc in 3+1 form with the input K_ij, K = -1/2 L_n gamma of Sec. 2.1):
-//   tau~: alpha sqrt(g) [T^00 (b^i b^j K_ij - b^i d_i alpha) + T^0i (2 b^j K_ij - d_i alpha) + T^ij K_ij]
-//   S~_i: alpha sqrt(g) [-T^00 alpha d_i alpha + T^0_k d_i b^k + 1/2 (T^00 b^j b^k + 2 T^0j b^k + T^jk) d_i g_jk]
-// (b = beta) with T^{mu nu} = (rho h + b^2) u u + (p + b^2/2) g^{mu nu} - b b (Eq. tmunu).
-__device__ __forceinline__ void sources(const Geo& m, const double* __restrict__ cg, long V, long c, double rho,
-                                        double press, const double v[3], const double B[3], double gfac,
-                                        double src[5]) {
-  double vl[3], Bl[3];
-  lower(m.g, v, vl);
-  lower(m.g, B, Bl);
-  const double W = 1.0 / sqrt(1.0 - (v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2]));
-  const double B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
-  const double Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
-  const double ia = 1.0 / m.alp;
-  const double iW = 1.0 / W;
-  const double b2 = B2 * iW * iW + Bv * Bv;
-  const double rhoh = rho + gfac * press;
-  const double e = rhoh + b2;
-  const double pt = press + 0.5 * b2;
-  double u[4], bb[4];
-  u[0] = W * ia;
-  bb[0] = W * Bv * ia;
-  for (int a = 0; a < 3; a++) {
-    u[1 + a] = W * (v[a] - m.beta[a] * ia);
-    bb[1 + a] = (B[a] + m.alp * bb[0] * u[1 + a]) * iW;
-  }
-  const double ia2 = ia * ia;
-  const double T00 = e * u[0] * u[0] - pt * ia2 - bb[0] * bb[0];
-  double T0[3], T[6];
-  for (int a = 0; a < 3; a++) T0[a] = e * u[0] * u[1 + a] + pt * m.beta[a] * ia2 - bb[0] * bb[1 + a];
-  for (int a = 0; a < 3; a++)
-    for (int q = a; q < 3; q++)
-      T[sym(a, q)] = e * u[1 + a] * u[1 + q] + pt * (m.gu[sym(a, q)] - m.beta[a] * m.beta[q] * ia2) -
-                     bb[1 + a] * bb[1 + q];
-  double K[6], dalp[3];
-  for (int a = 0; a < 6; a++) K[a] = cg[(CG_K + a) * V + c];
-  for (int a = 0; a < 3; a++) dalp[a] = cg[(CG_DALP + a) * V + c];
-  double betal[3];
-  lower(m.g, m.beta, betal);
-  const double asg = m.alp * m.sqg;
-  // energy
-  double Kb[3];  // K_ij beta^j
-  for (int a = 0; a < 3; a++) Kb[a] = K[sym(a, 0)] * m.beta[0] + K[sym(a, 1)] * m.beta[1] + K[sym(a, 2)] * m.beta[2];
-  double st = T00 * (m.beta[0] * Kb[0] + m.beta[1] * Kb[1] + m.beta[2] * Kb[2]);
-  for (int a = 0; a < 3; a++) st += -T00 * m.beta[a] * dalp[a] + T0[a] * (2.0 * Kb[a] - dalp[a]);
-  st += T[0] * K[0] + T[3] * K[3] + T[5] * K[5] + 2.0 * (T[1] * K[1] + T[2] * K[2] + T[4] * K[4]);
-  src[0] = 0.0;
-  src[4] = asg * st;
-  // momentum
-  double T0l[3];
-  for (int q = 0; q < 3; q++)
-    T0l[q] = betal[q] * T00 + m.g[sym(q, 0)] * T0[0] + m.g[sym(q, 1)] * T0[1] + m.g[sym(q, 2)] * T0[2];
-  double M[6];  // T^00 b^j b^k + T^0j b^k + T^0k b^j + T^jk (symmetrised)
-  for (int a = 0; a < 3; a++)
-    for (int q = a; q < 3; q++)
-      M[sym(a, q)] = T00 * m.beta[a] * m.beta[q] + T0[a] * m.beta[q] + T0[q] * m.beta[a] + T[sym(a, q)];
-  for (int i = 0; i < 3; i++) {
-    double s = -T00 * m.alp * dalp[i];
-    for (int q = 0; q < 3; q++) s += T0l[q] * cg[(CG_DBETA + i * 3 + q) * V + c];
-    const double* dg = cg + (CG_DG + i * 6) * V + c;
-    s += 0.5 * (M[0] * dg[0] + M[3] * dg[3 * V] + M[5] * dg[5 * V]) + M[1] * dg[V] + M[2] * dg[2 * V] +
-         M[4] * dg[4 * V];
-    src[1 + i] = asg * s;
-  }
-}
 
 // Interior cells: dU/dt = -sum_d (F_d(+) - F_d(-)) / dx_d + S (Eq. fluxconseqs, densitised).
 struct Cells {
@@ -940,6 +875,26 @@ cudaError_t launch_rhs(const StageArgs& a, const F9& Us, const F5& P, int stage,
   t.r.Uacc = Uacc;
   t.r.dU = dU;
   seq_rhs(t, consts_of(a, stage, dt, nullptr), a.recon, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recon_dir(const StageArgs& a, const F5& P, int D, cudaStream_t s) {
+  Single t = single_of(a.b, a.w);
+  t.r.P = P;
+  const StageConsts k = zero_consts();
+  if (D == 0) {
+    if (a.recon == 0) launch<Recon<0, 0>>(t, k, KIND_RECON_X, s);
+    else if (a.recon == 1) launch<Recon<0, 1>>(t, k, KIND_RECON_X, s);
+    else launch<Recon<0, 2>>(t, k, KIND_RECON_X, s);
+  } else if (D == 1) {
+    if (a.recon == 0) launch<Recon<1, 0>>(t, k, KIND_RECON_Y, s);
+    else if (a.recon == 1) launch<Recon<1, 1>>(t, k, KIND_RECON_Y, s);
+    else launch<Recon<1, 2>>(t, k, KIND_RECON_Y, s);
+  } else {
+    if (a.recon == 0) launch<Recon<2, 0>>(t, k, KIND_RECON_Z, s);
+    else if (a.recon == 1) launch<Recon<2, 1>>(t, k, KIND_RECON_Z, s);
+    else launch<Recon<2, 2>>(t, k, KIND_RECON_Z, s);
+  }
   return cudaGetLastError();
 }
 

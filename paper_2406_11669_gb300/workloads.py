@@ -275,6 +275,58 @@ def config4_target(w: Workload, seed=1104) -> np.ndarray:
     return T
 
 
+def _smooth_scalar(rng: Rng, nmodes: int, X, Y, Z, shape, amp):
+    """amp * sum of `nmodes` unit-amplitude-weighted sines with seeded wave vectors (|k_i| <= 2) and phases."""
+    out = np.zeros(shape)
+    for _ in range(nmodes):
+        k = rng.choice(np.arange(-2, 3), 3).astype(np.float64)
+        if not np.any(k):
+            k[2] = 1.0
+        a = float(rng.uniform(1, -1.0, 1.0)[0])
+        phi = float(rng.uniform(1, 0.0, 2.0 * math.pi)[0])
+        out += amp * a * np.sin(2.0 * math.pi * (k[0] * X + k[1] * Y + k[2] * Z) + phi)
+    return np.broadcast_to(out, shape).copy()
+
+
+def smooth_general(n=(12, 10, 11), seed=106, recon=RECON_PPM, bc=BC_PERIODIC, gauge=GAUGE_LORENZ) -> Workload:
+    """Periodic-in-form smooth data on [0,1]^3 in which every field varies in all three directions: rho, p from
+    3 modes each (5%), compressive velocity (|v| <= 0.2), |B| ~ 0.2, Psi ~ 0.02, and a general frozen metric
+    (lapse, shift, spatial metric and extrinsic curvature all perturbed by 2-3% with their own modes).  No
+    reconstruction limiter sits exactly at a branch point here, which makes it the workload for checking
+    derivatives against finite differences."""
+    g = 3
+    x0 = (0.0, 0.0, 0.0)
+    dx = tuple(1.0 / m for m in n)
+    N = [m + 2 * g for m in n]
+    shape = (N[2] + 1, N[1] + 1, N[0] + 1)
+    rng = Rng(seed)
+    Xc, Yc, Zc = positions(n, g, x0, dx, CELL)
+    rho = 1.0 + _smooth_scalar(rng, 3, Xc, Yc, Zc, shape, 0.05)
+    press = 0.8 + _smooth_scalar(rng, 3, Xc, Yc, Zc, shape, 0.05)
+    vm = _fourier_vector_modes(rng, 4, transverse=False)
+    v = _eval_vector_sin(vm, Xc, Yc, Zc, shape)
+    vmag = np.sqrt(v[0] ** 2 + v[1] ** 2 + v[2] ** 2).max()
+    v = [c * (0.2 / vmag) for c in v]
+    A = _fourier_potential(rng, 4, n, g, x0, dx, shape, 0.2)
+    Xv, Yv, Zv = positions(n, g, x0, dx, VERTEX)
+    psi = _smooth_scalar(rng, 2, Xv, Yv, Zv, shape, 0.02)
+    metric = flat_metric(shape)
+    metric["alp"] = 1.0 + _smooth_scalar(rng, 2, Xv, Yv, Zv, shape, 0.02)
+    for name in ("betax", "betay", "betaz"):
+        metric[name] = _smooth_scalar(rng, 2, Xv, Yv, Zv, shape, 0.03)
+    for name in ("gxx", "gxy", "gxz", "gyy", "gyz", "gzz"):
+        diag = name in ("gxx", "gyy", "gzz")
+        metric[name] = (1.0 if diag else 0.0) + _smooth_scalar(rng, 2, Xv, Yv, Zv, shape, 0.03 if diag else 0.015)
+    for name in METRIC_NAMES[10:]:
+        metric[name] = _smooth_scalar(rng, 2, Xv, Yv, Zv, shape, 0.02)
+    params = default_params(gamma=4.0 / 3.0, gamma_atm=4.0 / 3.0, rho_atm=1e-7, K_atm=1.0, recon=recon, gauge=gauge)
+    prims = dict(rho=rho, press=press, velx=v[0], vely=v[1], velz=v[2])
+    rname = {RECON_MINMOD: "minmod", RECON_PPM: "ppm", RECON_WENOZ: "wenoz"}[recon]
+    bname = "periodic" if bc == BC_PERIODIC else "copy"
+    return Workload(f"smooth_general_{rname}_{bname}", tuple(n), g, x0, dx, (bc,) * 3, params, 0.25 * min(dx), prims,
+                    A, psi, metric)
+
+
 def config2(n=(128, 128, 128), seed=102) -> Workload:
     """128^3 on [-1/2,1/2]^3, copy BCs, Gamma = 5/3, WENO-Z.  Table 1 test-1 states split at x = 0:
     left rho=1, p=1, right rho=0.125, p=0.1, v=0; densitised field B~x = 0.5, B~y = +1 (left) / -1 (right)

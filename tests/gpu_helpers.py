@@ -18,6 +18,16 @@ def owned(w, v):
     return tuple(sl)
 
 
+def independent(w, v):
+    """Like owned(), without the vertex index g+n along periodic axes (the periodic image of index g)."""
+    g, n = w.g, w.n
+    sl = []
+    for a in (2, 1, 0):
+        hi = g + n[a] - 1 if (CELL_LIKE[v][a] or w.bc[a] == W.BC_PERIODIC) else g + n[a]
+        sl.append(slice(g, hi + 1))
+    return tuple(sl)
+
+
 def interior(w):
     g, n = w.g, w.n
     return (slice(g, g + n[2]), slice(g, g + n[1]), slice(g, g + n[0]))

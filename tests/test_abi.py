@@ -103,3 +103,35 @@ def test_batch_workspace_size_and_validation():
     rc = L.asterx_batched_step(ctypes.byref(p), arr, 2, ctypes.c_double(0.01), 1, None, ctypes.c_void_p(256),
                                size, None)
     assert rc == A.ASTERX_EINVAL
+
+
+def test_adjoint_workspace_size_and_validation():
+    L = A.lib()
+    p = _params()
+    b = A.block_struct((8, 8, 8), 3, (0, 0, 0), (0.1,) * 3, (0, 0, 0))
+    V = 15 ** 3
+    size = L.asterx_adjoint_workspace_size(ctypes.byref(b))
+    assert size >= 161 * V * 8 + V  # stage states, adjoint accumulators, flags
+    bad_b = A.block_struct((8, 8, 8), 2, (0, 0, 0), (0.1,) * 3, (0, 0, 0))
+    assert L.asterx_adjoint_workspace_size(ctypes.byref(bad_b)) == 0
+    st = A.State(*([8] * 9))
+    pr = A.Prims(*([8] * 5))
+    need = A.workspace_size(b)
+    args = (ctypes.byref(p), ctypes.byref(b), ctypes.c_double(0.01), ctypes.byref(st), ctypes.byref(pr))
+    rc = L.asterx_rhs_adjoint(*args, ctypes.byref(st), ctypes.byref(st), ctypes.c_void_p(256), need,
+                              ctypes.c_void_p(512), size - 8, None)
+    assert rc == A.ASTERX_ENOMEM
+    rc = L.asterx_rhs_adjoint(*args, ctypes.byref(st), ctypes.byref(st), ctypes.c_void_p(256), need, None, size,
+                              None)
+    assert rc == A.ASTERX_EINVAL  # no adjoint workspace
+    rc = L.asterx_rk4_step_adjoint(*args, ctypes.byref(st), ctypes.c_void_p(256), need, ctypes.c_void_p(300),
+                                   size, None)
+    assert rc == A.ASTERX_EINVAL  # adjoint workspace not 256-byte aligned
+    bad = A.State(*([8] * 8 + [0]))
+    rc = L.asterx_rk4_step_adjoint(*args, ctypes.byref(bad), ctypes.c_void_p(256), need, ctypes.c_void_p(512),
+                                   size, None)
+    assert rc == A.ASTERX_EINVAL  # null adjoint field
+    rc = L.asterx_rk4_step_adjoint(ctypes.byref(p), ctypes.byref(b), ctypes.c_double(0.0), ctypes.byref(st),
+                                   ctypes.byref(pr), ctypes.byref(st), ctypes.c_void_p(256), need,
+                                   ctypes.c_void_p(512), size, None)
+    assert rc == A.ASTERX_EINVAL  # dt <= 0

@@ -1,0 +1,177 @@
+"""The adjoint (vector-Jacobian product) of the stage right-hand side and of one RK4 step, against central
+differences of the oracle's forward operator on the same inputs.
+
+For a weight mu on the outputs, the CUDA adjoint returns lam = (dL/dU)^T mu.  The oracle gives
+J(U) = <mu, L(U)> for any U, so for a direction v the directional derivative <lam, v> must equal
+(J(U + h v) - J(U - h v)) / 2h up to O(h^2) truncation and rounding of order eps |L| / h; with h between 1e-8
+and 1e-6 in units of each field's magnitude both stay below 1e-8 of sum |lam v|.  The limiters, max/min and
+recovery branches make L piecewise smooth: where a switching surface lies within h of the state the quotient is
+one-sided at that h, so each check takes the closest of three step sizes (a wrong adjoint is off at all of
+them).  Two kinds of check: one direction per field group (all independent entries of D~ | S~ | tau~ | A | Psi at
+once), and single entries at the middle and at the ends of every field's independent range (where the ghost zones and
+the boundary conditions act).  The workloads vary smoothly in every direction, so that no limiter sits exactly
+at a branch point; copy boundary conditions are checked with minmod, whose slopes in the ghost zones are exactly
+zero for every state.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_helpers import GpuCase, independent
+from paper_2406_11669_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HS = (1e-6, 1e-7, 1e-8)
+RTOL = 1e-6
+IN_GROUPS = [(0,), (1, 2, 3), (4,), (5, 6, 7), (8,)]
+
+CASES = {
+    "ppm_periodic_lorenz": dict(recon=W.RECON_PPM, bc=W.BC_PERIODIC, gauge=W.GAUGE_LORENZ),
+    "minmod_copy_lorenz": dict(recon=W.RECON_MINMOD, bc=W.BC_COPY, gauge=W.GAUGE_LORENZ),
+    "wenoz_periodic_algebraic": dict(recon=W.RECON_WENOZ, bc=W.BC_PERIODIC, gauge=W.GAUGE_ALGEBRAIC),
+}
+
+
+def need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def independent_mask(w):
+    m = np.zeros((9,) + w.shape, dtype=bool)
+    for v in range(9):
+        m[v][independent(w, v)] = True
+    return m
+
+
+class Problem:
+    """A workload with its oracle state, primitives and seeded weights."""
+
+    def __init__(self, w, seed):
+        self.w = w
+        self.M = O.metric_array(w)
+        U, P = O.initial_state(w)
+        O.ghost_fill_state(w, U)
+        self.U, self.P = U, P
+        self.mask = independent_mask(w)
+        rng = W.Rng(seed)
+        self.uscale = np.array([max(np.abs(U[v][independent(w, v)]).max(), 1e-3) for v in range(9)])
+        self.r_mu = rng.uniform(9 * int(np.prod(w.shape)), -1.0, 1.0).reshape((9,) + w.shape)
+        self.r_v = rng.uniform(9 * int(np.prod(w.shape)), -1.0, 1.0).reshape((9,) + w.shape)
+
+    def stage_rhs(self, U):
+        """L(U): the oracle's stage operator from the independent entries of U (ghost fill, recovery warm-started
+        from the unperturbed primitives, primitive ghost fill, right-hand side)."""
+        w = self.w
+        X = U.copy()
+        O.ghost_fill_state(w, X)
+        P = self.P.copy()
+        O.con2prim(w, self.M, X, P)
+        O.ghost_fill_prims(w, P)
+        dU, _ = O.rhs(w, self.M, X, P)
+        return np.where(self.mask, dU, 0.0)
+
+    def rk4(self, U):
+        X = U.copy()
+        O.ghost_fill_state(self.w, X)
+        U1, st = O.rk4_step(self.w, self.M, X, self.P.copy())
+        assert st["n_atm"] == 0 and st["n_failed"] == 0
+        return np.where(self.mask, U1, 0.0)
+
+    def mu_for(self, out):
+        """Weights on the independent outputs, each field scaled by 1 / its magnitude so that all fields count."""
+        sc = np.array([max(np.abs(out[v]).max(), 1e-300) for v in range(9)])
+        return np.where(self.mask, self.r_mu / sc[:, None, None, None], 0.0)
+
+
+def directional(F, mu, U, d, h):
+    """<mu, (F(U + h d) - F(U - h d)) / 2h>, the difference taken entry by entry before the weighted sum."""
+    return float(np.sum(mu * (F(U + h * d) - F(U - h * d)))) / (2.0 * h)
+
+
+def closest(F, mu, U, d, target, steps):
+    return min((directional(F, mu, U, d, h) for h in steps), key=lambda fd: abs(fd - target))
+
+
+def sample_entries(w, v, full):
+    """(z, y, x) indices: the two corners of the field's independent range, and (full) its middle and a mixed
+    corner."""
+    sl = independent(w, v)
+    lo = tuple(s.start for s in sl)
+    hi = tuple(s.stop - 1 for s in sl)
+    mid = tuple((a + b) // 2 for a, b in zip(lo, hi))
+    return [lo, hi, mid, (lo[0], mid[1], hi[2])] if full else [lo, hi]
+
+
+def check_vjp(prob, F, lam, full_entries=True):
+    """Compares lam with central differences of J(U) = <mu, F(U)>: per input group, then per sampled entry."""
+    w, U = prob.w, prob.U
+    mu = prob.mu_for(F(U))
+    for grp in IN_GROUPS:
+        d = np.zeros_like(U)
+        for v in grp:
+            d[v] = np.where(prob.mask[v], prob.r_v[v] * prob.uscale[v], 0.0)
+        ad = float(np.sum(lam * d))
+        fd = closest(F, mu, U, d, ad, HS)
+        scale = float(np.sum(np.abs(lam * d)))
+        assert abs(ad - fd) <= RTOL * scale, (grp, ad, fd, scale)
+    for v in range(9):
+        lmax = np.abs(lam[v][prob.mask[v]]).max()
+        for idx in sample_entries(w, v, full_entries):
+            d = np.zeros_like(U)
+            d[(v,) + idx] = prob.uscale[v]
+            ad = lam[(v,) + idx]
+            fd = closest(F, mu, U, d, ad * prob.uscale[v], HS[:2]) / prob.uscale[v]
+            assert abs(ad - fd) <= RTOL * max(lmax, abs(fd)), (v, idx, ad, fd, lmax)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_adjoint_matches_central_differences(name):
+    need_gpu()
+    w = W.smooth_general(**CASES[name])
+    prob = Problem(w, seed=2201)
+    mu = prob.mu_for(prob.stage_rhs(prob.U))
+    case = GpuCase(w)
+    lam_d = case.solver.zeros_state()
+    P_d = case.dev(prob.P)
+    case.solver.rhs_adjoint(case.dev(prob.U), P_d, case.dev(mu), lam_d, w.dt)
+    lam = case.host(lam_d)
+    assert np.all(lam[~prob.mask] == 0.0)
+    assert np.all(np.isfinite(lam))
+    check_vjp(prob, prob.stage_rhs, lam)
+
+
+@pytest.mark.parametrize("name", ["ppm_periodic_lorenz", "minmod_copy_lorenz"])
+def test_rk4_step_adjoint_matches_central_differences(name):
+    need_gpu()
+    w = W.smooth_general(n=(10, 9, 8), **CASES[name])
+    prob = Problem(w, seed=2202)
+    mu = prob.mu_for(prob.rk4(prob.U))
+    case = GpuCase(w)
+    lam_d = case.dev(mu)
+    case.solver.rk4_step_adjoint(case.dev(prob.U), case.dev(prob.P), lam_d, w.dt)
+    lam = case.host(lam_d)
+    assert np.all(lam[~prob.mask] == 0.0)
+    check_vjp(prob, prob.rk4, lam, full_entries=False)
+
+
+def test_rhs_adjoint_is_linear_in_the_weights():
+    """J^T (2 mu1 - 3 mu2) = 2 J^T mu1 - 3 J^T mu2 up to the summation order of the atomic accumulations."""
+    need_gpu()
+    w = W.smooth_general(**CASES["ppm_periodic_lorenz"])
+    prob = Problem(w, seed=2203)
+    case = GpuCase(w)
+    rng = W.Rng(77)
+    m1 = np.where(prob.mask, rng.uniform(prob.U.size, -1.0, 1.0).reshape(prob.U.shape), 0.0)
+    m2 = np.where(prob.mask, rng.uniform(prob.U.size, -1.0, 1.0).reshape(prob.U.shape), 0.0)
+    out = []
+    for m in (m1, m2, 2.0 * m1 - 3.0 * m2):
+        lam_d = case.solver.zeros_state()
+        case.solver.rhs_adjoint(case.dev(prob.U), case.dev(prob.P), case.dev(m), lam_d, w.dt)
+        out.append(case.host(lam_d))
+    comb = 2.0 * out[0] - 3.0 * out[1]
+    for v in range(9):
+        scale = np.abs(comb[v]).max()
+        assert np.abs(out[2][v] - comb[v]).max() <= 1e-12 * scale, v
