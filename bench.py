@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch measurement")
     ap.add_argument("--batch-blocks", type=int, default=512)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward measurement")
+    ap.add_argument("--adjoint-n", type=int, default=64, help="cells per axis of the adjoint workload")
     return ap.parse_args()
 
 
@@ -258,6 +260,75 @@ def run_batched(args, dev, stream):
             "batched_vs_single": rate_b / rate_s}
 
 
+def run_adjoint(args, dev, stream):
+    """The adjoint workload (64^3 periodic, weak-field lapse, PPM): time of one RK4 step forward against one
+    adjoint RK4 step (forward recompute of the four stage states from the checkpoint, then the four reversed
+    stages); then the whole gradient of J = 1/2 sum (D~_10 - T)^2 with respect to the initial primitives and
+    potentials (10 checkpointed steps forward, 10 adjoint steps, adjoint of the initial data)."""
+    import numpy as np
+    import torch
+
+    from paper_2406_11669_gb300 import asterx as A
+    from paper_2406_11669_gb300 import workloads as W
+
+    w = W.config4(n=(args.adjoint_n,) * 3)
+    M, U, P = _upload_block(w, dev)
+    s = A.Solver.for_workload(w, device=dev)
+    s.prepare(M)
+    s.fill_ghosts(U)
+    s.prim2con(U, P)
+    U0, P0 = U.clone(), P.clone()
+    lam = torch.zeros_like(U)
+    g = w.g
+    inter = (slice(g, g + w.n[2]), slice(g, g + w.n[1]), slice(g, g + w.n[0]))
+    lam[(0,) + inter] = 1e-3
+    reps = max(1, min(args.steps, 5))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # warm-up both directions (allocates the adjoint workspace)
+    s.rk4_step(U, P, w.dt)
+    s.rk4_step_adjoint(U0, P, lam, w.dt)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        s.rk4_step(U, P, w.dt)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_f = e0.elapsed_time(e1) / reps
+    e0.record(stream)
+    for _ in range(reps):
+        s.rk4_step_adjoint(U0, P, lam, w.dt)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_a = e0.elapsed_time(e1) / reps
+    # whole 10-step gradient
+    nsteps = 10
+    T = torch.from_numpy(W.config4_target(w)).to(dev)
+    ckpt = [torch.empty_like(U) for _ in range(nsteps)]
+    U.copy_(U0)
+    P.copy_(P0)
+    lamP = torch.zeros_like(P)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    s.rk4_steps_checkpointed(U, P, w.dt, ckpt)
+    lam.zero_()
+    lam[(0,) + inter] = U[(0,) + inter] - T[inter]
+    s.rk4_adjoint_steps(ckpt, P, lam, w.dt)
+    s.prim2con_adjoint(U0, P0, lam, lamP)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_grad = e0.elapsed_time(e1)
+    grad_finite = bool(torch.isfinite(lamP).all()) and bool(torch.isfinite(lam).all())
+    grad_norm = float(lamP[0][inter].abs().max())
+    ckpt_bytes = nsteps * U.numel() * 8
+    del ckpt, s, U, P, U0, P0, lam, lamP, M
+    torch.cuda.empty_cache()
+    return {"workload": f"{w.n[0]}^3 periodic, lapse 1 - 0.01 sin 2 pi x, PPM (seed 104)",
+            "forward_ms_per_step": ms_f, "adjoint_ms_per_step": ms_a, "adjoint_vs_forward": ms_a / ms_f,
+            "steps_timed": reps,
+            "gradient_10_steps": {"ms": ms_grad, "checkpoint_bytes": ckpt_bytes, "finite": grad_finite,
+                                  "max_abs_dJ_drho": grad_norm}}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -395,6 +466,8 @@ def run_ours(args):
               "clocks": clk, "roofline": roofline, "c2p_counters_timed": c2p, "state_finite": finite}
     if not args.no_batched:
         result["batched"] = run_batched(args, dev, stream)
+    if not args.no_adjoint:
+        result["adjoint"] = run_adjoint(args, dev, stream)
     if not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(result))

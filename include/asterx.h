@@ -188,6 +188,27 @@ asterx_status asterx_rk4_step_adjoint(const asterx_params *p, const asterx_block
                                       const asterx_state *Un, asterx_prims *P, asterx_state *lam, void *ws,
                                       size_t ws_bytes, void *aws, size_t aws_bytes, asterx_stream stream);
 
+/* Adjoint of the initial data U = (prim2con(P, B~ = curl A), A, Psi): lam holds dJ/dU on entry; on exit its
+ * fields A and Psi hold dJ/dA and dJ/dPsi (independent entries) and its hydro fields are zero, and lamP holds
+ * dJ/dP at the interior cells (zero elsewhere).  U supplies A (ghosts filled internally on a copy), P the
+ * primitives; neither is modified. */
+asterx_status asterx_prim2con_adjoint(const asterx_params *p, const asterx_block *blk, const asterx_state *U,
+                                      const asterx_prims *P, asterx_state *lam, asterx_prims *lamP, void *ws,
+                                      size_t ws_bytes, void *aws, size_t aws_bytes, asterx_stream stream);
+
+/* nsteps RK4 steps in place (asterx_rk4_step), saving the state before step k into ckpt[k] (a host array of
+ * nsteps device state structs, each of the block's padded size): the checkpoints of the adjoint below. */
+asterx_status asterx_rk4_steps_checkpointed(const asterx_params *p, const asterx_block *blk, double dt, int nsteps,
+                                            asterx_state *U, asterx_prims *P, const asterx_state *ckpt,
+                                            asterx_c2p_stats *stats, void *ws, size_t ws_bytes,
+                                            asterx_stream stream);
+
+/* Adjoint of nsteps RK4 steps from their checkpoints: lam = dJ/dU_N on entry, dJ/dU_0 on exit (steps reversed
+ * one by one with asterx_rk4_step_adjoint; P is a primitive guess, overwritten). */
+asterx_status asterx_rk4_adjoint_steps(const asterx_params *p, const asterx_block *blk, double dt, int nsteps,
+                                       const asterx_state *ckpt, asterx_prims *P, asterx_state *lam, void *ws,
+                                       size_t ws_bytes, void *aws, size_t aws_bytes, asterx_stream stream);
+
 /* ---- batched step over many blocks of uneven sizes ----
  *
  * Many AMR-like blocks advance together: every kernel of the stage is launched once for all blocks, over the

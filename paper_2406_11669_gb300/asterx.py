@@ -97,7 +97,11 @@ def lib():
         L.asterx_adjoint_workspace_size.argtypes = [B]
         L.asterx_rhs_adjoint.argtypes = [P, B, ctypes.c_double, S, Pr, S, S, vp, sz, vp, sz, st]
         L.asterx_rk4_step_adjoint.argtypes = [P, B, ctypes.c_double, S, Pr, S, vp, sz, vp, sz, st]
-        for name in ("asterx_rhs_adjoint", "asterx_rk4_step_adjoint"):
+        L.asterx_prim2con_adjoint.argtypes = [P, B, S, Pr, S, Pr, vp, sz, vp, sz, st]
+        L.asterx_rk4_steps_checkpointed.argtypes = [P, B, ctypes.c_double, ctypes.c_int, S, Pr, S, vp, vp, sz, st]
+        L.asterx_rk4_adjoint_steps.argtypes = [P, B, ctypes.c_double, ctypes.c_int, S, Pr, S, vp, sz, vp, sz, st]
+        for name in ("asterx_rhs_adjoint", "asterx_rk4_step_adjoint", "asterx_prim2con_adjoint",
+                     "asterx_rk4_steps_checkpointed", "asterx_rk4_adjoint_steps"):
             getattr(L, name).restype = ctypes.c_int
         L.asterx_con2prim_noalloc.argtypes = [P, B, M, S, Pr, vp, vp, st]
         L.asterx_con2prim_noalloc.restype = ctypes.c_int
@@ -291,6 +295,32 @@ class Solver:
         _check(lib().asterx_rk4_step_adjoint(*self._args(), float(dt), ctypes.byref(u), ctypes.byref(p),
                                              ctypes.byref(l), self.ws_ptr, self.ws_bytes, ap, ab, _stream(stream)),
                "asterx_rk4_step_adjoint")
+
+    def prim2con_adjoint(self, U, P, lam, lamP, stream=None):
+        """In place: lam = dJ/dU0 on entry; on exit fields A, Psi of lam hold dJ/dA, dJ/dPsi and lamP = dJ/dP."""
+        ap, ab = self._adjoint_ws()
+        u, p, l, lp = state_struct(U), prims_struct(P), state_struct(lam), prims_struct(lamP)
+        _check(lib().asterx_prim2con_adjoint(*self._args(), ctypes.byref(u), ctypes.byref(p), ctypes.byref(l),
+                                             ctypes.byref(lp), self.ws_ptr, self.ws_bytes, ap, ab, _stream(stream)),
+               "asterx_prim2con_adjoint")
+
+    def rk4_steps_checkpointed(self, U, P, dt, ckpt, stats=None, stream=None):
+        """len(ckpt) RK4 steps in place; ckpt[k] (device tensor of U's shape) receives the state before step k."""
+        arr = (State * len(ckpt))(*[state_struct(c) for c in ckpt])
+        u, p = state_struct(U), prims_struct(P)
+        sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
+        _check(lib().asterx_rk4_steps_checkpointed(*self._args(), float(dt), len(ckpt), ctypes.byref(u),
+                                                   ctypes.byref(p), arr, sp, self.ws_ptr, self.ws_bytes,
+                                                   _stream(stream)), "asterx_rk4_steps_checkpointed")
+
+    def rk4_adjoint_steps(self, ckpt, P, lam, dt, stream=None):
+        """In place: lam = dJ/dU_N on entry, dJ/dU_0 on exit, for the steps whose checkpoints are ckpt."""
+        ap, ab = self._adjoint_ws()
+        arr = (State * len(ckpt))(*[state_struct(c) for c in ckpt])
+        p, l = prims_struct(P), state_struct(lam)
+        _check(lib().asterx_rk4_adjoint_steps(*self._args(), float(dt), len(ckpt), arr, ctypes.byref(p),
+                                              ctypes.byref(l), self.ws_ptr, self.ws_bytes, ap, ab,
+                                              _stream(stream)), "asterx_rk4_adjoint_steps")
 
 
 # ---------------------------------------------------------------------------------------- measurement helpers

@@ -624,6 +624,61 @@ asterx_status asterx_rk4_step_adjoint(const asterx_params* p, const asterx_block
   return cuda_status(e);
 }
 
+asterx_status asterx_prim2con_adjoint(const asterx_params* p, const asterx_block* blk, const asterx_state* U,
+                                      const asterx_prims* P, asterx_state* lam, asterx_prims* lamP, void* ws,
+                                      size_t ws_bytes, void* aws, size_t aws_bytes, asterx_stream stream) {
+  asterx_status st = adj_checks(p, blk, 1.0, ws, ws_bytes, aws, aws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!set_ok<asterx_state, 9>(U) || !set_ok<asterx_prims, 5>(P) || !set_ok<asterx_state, 9>(lam) ||
+      !set_ok<asterx_prims, 5>(lamP))
+    return ASTERX_EINVAL;
+  StageArgs sa = make_args(p, blk, ws);
+  AdjLayout L = make_adj(blk, aws);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = copy9(L.ycopy, f9(U), sa.b.V, s);
+  if (e == cudaSuccess) e = copy9(L.kbar, f9(lam), sa.b.V, s);
+  if (e == cudaSuccess) e = launch_mask_owned9(sa.b, L.kbar, s);
+  AdjWs a = adj_ws(L, sa.b, L.ycopy, f5(const_cast<asterx_prims*>(P)), L.kbar);
+  if (e == cudaSuccess) e = launch_prim2con_adjoint(sa, a, L.kbar, f5(lamP), s);
+  if (e == cudaSuccess) e = copy9(f9(lam), f9_from(a.lY, sa.b.V), sa.b.V, s);
+  return cuda_status(e);
+}
+
+asterx_status asterx_rk4_steps_checkpointed(const asterx_params* p, const asterx_block* blk, double dt, int nsteps,
+                                            asterx_state* U, asterx_prims* P, const asterx_state* ckpt,
+                                            asterx_c2p_stats* stats, void* ws, size_t ws_bytes,
+                                            asterx_stream stream) {
+  asterx_status st = common_checks(p, blk, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!finite_pos(dt) || nsteps < 1 || !ckpt || !set_ok<asterx_state, 9>(U) || !set_ok<asterx_prims, 5>(P))
+    return ASTERX_EINVAL;
+  for (int k = 0; k < nsteps; k++)
+    if (!set_ok<asterx_state, 9>(&ckpt[k])) return ASTERX_EINVAL;
+  const long V = padded_V(blk);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int k = 0; k < nsteps; k++) {
+    if (copy9(f9(&ckpt[k]), f9(U), V, s) != cudaSuccess) return ASTERX_ECUDA;
+    st = asterx_rk4_step(p, blk, dt, U, P, nullptr, stats, ws, ws_bytes, stream);
+    if (st != ASTERX_OK) return st;
+  }
+  return ASTERX_OK;
+}
+
+asterx_status asterx_rk4_adjoint_steps(const asterx_params* p, const asterx_block* blk, double dt, int nsteps,
+                                       const asterx_state* ckpt, asterx_prims* P, asterx_state* lam, void* ws,
+                                       size_t ws_bytes, void* aws, size_t aws_bytes, asterx_stream stream) {
+  asterx_status st = adj_checks(p, blk, dt, ws, ws_bytes, aws, aws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (nsteps < 1 || !ckpt) return ASTERX_EINVAL;
+  for (int k = 0; k < nsteps; k++)
+    if (!set_ok<asterx_state, 9>(&ckpt[k])) return ASTERX_EINVAL;
+  for (int k = nsteps - 1; k >= 0; k--) {
+    st = asterx_rk4_step_adjoint(p, blk, dt, &ckpt[k], P, lam, ws, ws_bytes, aws, aws_bytes, stream);
+    if (st != ASTERX_OK) return st;
+  }
+  return ASTERX_OK;
+}
+
 asterx_status asterx_profile_enable(int max_launches) {
   if (max_launches < 1 || max_launches > (1 << 20)) return ASTERX_EINVAL;
   return cuda_status(profile_enable(max_launches));

@@ -680,6 +680,71 @@ cudaError_t launch_mask_owned9(const Blk& b, const F9& x, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Initial data: U_hydro = prim2con(P, B) at the interior cells (Eq. cons), B the centre field of curl A.
+// lamP = (dU/dP)^T lamU, lambda_B = (dU/dB)^T lamU, both from dual numbers through prim->cons.
+__global__ void ka_prim2con(Blk b, Ws w, AdjWs a, F9 lamU, F5 lamP, double gamma, double gfac) {
+  const long count = (long)b.n[0] * b.n[1] * b.n[2];
+  ALOOP(t, count) {
+    int i, j, k;
+    decode(t, b.g, b.n[0], b.g, b.n[1], b.g, i, j, k);
+    const long c = alin(b, i, j, k);
+    Geo m;
+    load_geo(b, w.cg, c, m);
+    typedef Dual<8> D8;
+    const D8 rho = D8::seed(a.P.f[0][c], 0), press = D8::seed(a.P.f[1][c], 1);
+    const D8 v[3] = {D8::seed(a.P.f[2][c], 2), D8::seed(a.P.f[3][c], 3), D8::seed(a.P.f[4][c], 4)};
+    const D8 B[3] = {D8::seed(w.bc[c], 5), D8::seed(w.bc[b.V + c], 6), D8::seed(w.bc[2 * b.V + c], 7)};
+    const D8 W = 1.0 / sqrt(1.0 - contract_sym(m.g, v, v));
+    const D8 u[3] = {W * v[0], W * v[1], W * v[2]};
+    SideOutT<D8> o;
+    face_side(m, 1.0 / m.alp, m.alp * sqrt(m.gu[0]), 0, rho, press, u, B, gamma, gfac, o);
+    double g8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int q = 0; q < 5; q++) {
+      const double l = lamU.f[q][c];
+      for (int r = 0; r < 8; r++) g8[r] += o.U[q].d[r] * l;
+    }
+    for (int r = 0; r < 5; r++) lamP.f[r][c] = g8[r];
+    for (int r = 0; r < 3; r++) a.lBc[r * b.V + c] = g8[5 + r];
+  }
+}
+
+__global__ void ka_zero5(Blk b, F5 x) {
+  ALOOP(t, 5 * b.V) {
+    const int f = (int)(t / b.V);
+    x.f[f][t - (long)f * b.V] = 0.0;
+  }
+}
+
+cudaError_t launch_prim2con_adjoint(const StageArgs& sa, const AdjWs& a, const F9& lamU, const F5& lamP,
+                                    cudaStream_t s) {
+  const Blk& b = sa.b;
+  const int T = 128;
+  cudaError_t e = launch_ghost_state(b, a.Y, s);
+  if (e == cudaSuccess) e = launch_bfield(b, sa.w, a.Y, s);
+  if (e != cudaSuccess) return e;
+  cudaMemsetAsync(a.lY_base, 0, (size_t)ADJ_ACC_FIELDS * b.V * sizeof(double), s);
+  ka_zero5<<<agrid(5 * b.V, 256), 256, 0, s>>>(b, lamP);
+  ka_prim2con<<<agrid((long)b.n[0] * b.n[1] * b.n[2], T), T, 0, s>>>(b, sa.w, a, lamU, lamP, sa.gamma, sa.gfac);
+  ka_bcentre<<<agrid(b.V, T), T, 0, s>>>(b, sa.w, a);
+  ka_curl<<<agrid(b.V, T), T, 0, s>>>(b, a);
+  F9 ly;
+  for (int v = 0; v < 9; v++) ly.f[v] = a.lY + v * b.V;
+  AdjGhost g;
+  const int cl[9] = {7, 7, 7, 7, 7, 1, 2, 4, 0};
+  for (int f = 0; f < 9; f++) {
+    g.f[f] = ly.f[f];
+    g.cl[f] = cl[f];
+    g.lin[f] = (f >= 5 && f <= 7);
+  }
+  launch_ghost_adjoint(b, g, 9, s);
+  // the potentials' own adjoints pass through unchanged: lY += lamU, then the hydro entries are cleared
+  e = launch_axpby9(b, 1.0, lamU, 1.0, ly, s);
+  if (e == cudaSuccess) e = launch_mask_owned9(b, ly, s);
+  if (e != cudaSuccess) return e;
+  for (int v = 0; v < 5; v++) cudaMemsetAsync(ly.f[v], 0, b.V * sizeof(double), s);
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------------------------------------------------
 // Orchestration of the VJP of the right-hand side at the state held in a.Y (ghost fill, recovery and the
 // forward intermediates are recomputed here); mu on owned ranges in a.mu; result in a.lY (owned ranges).

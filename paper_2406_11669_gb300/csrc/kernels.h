@@ -78,6 +78,10 @@ struct AdjGhost {
 cudaError_t launch_recon_dir(const StageArgs& a, const F5& P, int D, cudaStream_t s);
 // lambda = (dL/dY)^T mu at the state a.Y (recomputes the forward intermediates)
 cudaError_t launch_rhs_adjoint(const StageArgs& sa, const AdjWs& a, double dt, cudaStream_t s);
+// adjoint of the initial data U = (prim2con(P, B(A)), A, Psi) at the state a.Y (copy; ghost-filled here):
+// lamP (interior cells) and a.lY (A, Psi entries; independent ranges) from lamU
+cudaError_t launch_prim2con_adjoint(const StageArgs& sa, const AdjWs& a, const F9& lamU, const F5& lamP,
+                                    cudaStream_t s);
 void launch_ghost_adjoint(const Blk& b, const AdjGhost& g, int nf, cudaStream_t s);
 // y = alpha x + beta y over every entry of 9 fields; zero the entries outside the owned ranges of 9 fields
 cudaError_t launch_axpby9(const Blk& b, double alpha, const F9& x, double beta, const F9& y, cudaStream_t s);

@@ -175,3 +175,90 @@ def test_rhs_adjoint_is_linear_in_the_weights():
     for v in range(9):
         scale = np.abs(comb[v]).max()
         assert np.abs(out[2][v] - comb[v]).max() <= 1e-12 * scale, v
+
+
+def test_loss_gradient_through_steps_and_initial_data():
+    """Gradient of J = 1/2 sum_interior (D~_N - T)^2 after N = 2 RK4 steps with respect to the initial primitives,
+    and potentials: forward with checkpoints, reverse through the steps and the initial data (prim->cons with
+    B~ = curl A), against central differences of the oracle's whole pipeline at sampled entries."""
+    need_gpu()
+    nsteps = 2
+    w = W.smooth_general(n=(9, 8, 10), seed=107, **CASES["ppm_periodic_lorenz"])
+    M = O.metric_array(w)
+    P0 = O.prims_array(w)
+    base = np.zeros((9,) + w.shape)
+    base[5], base[6], base[7], base[8] = w.A["Ax"], w.A["Ay"], w.A["Az"], w.Psi
+    mask = independent_mask(w)
+    g, n = w.g, w.n
+    inter = (slice(g, g + n[2]), slice(g, g + n[1]), slice(g, g + n[0]))
+    rng = W.Rng(2204)
+    T = 1.0 + 0.01 * rng.uniform(int(np.prod(w.shape)), -1.0, 1.0).reshape(w.shape)
+
+    def loss(P, pot):
+        U = np.where(mask, pot, 0.0)
+        O.ghost_fill_state(w, U)
+        O.prim2con(w, M, U, P)
+        Pw = P.copy()
+        for _ in range(nsteps):
+            U, st = O.rk4_step(w, M, U, Pw)
+            assert st["n_atm"] == 0
+        return 0.5 * float(np.sum((U[0][inter] - T[inter]) ** 2))
+
+    case = GpuCase(w)
+    s = case.solver
+    U = case.dev(base)
+    s.fill_ghosts(U)
+    P = case.dev(P0)
+    s.prim2con(U, P)
+    U0 = U.clone()
+    ckpt = [s.zeros_state() for _ in range(nsteps)]
+    s.rk4_steps_checkpointed(U, P, w.dt, ckpt)
+    lam = torch.zeros_like(U)
+    Tt = case.dev(T)
+    ii = (0,) + inter
+    lam[ii] = U[ii] - Tt[inter]
+    s.rk4_adjoint_steps(ckpt, P, lam, w.dt)
+    lamP = s.zeros_prims()
+    s.prim2con_adjoint(U0, case.dev(P0), lam, lamP)
+    gP, gU = case.host(lamP), case.host(lam)
+    assert np.all(gU[:5] == 0.0) and np.all(gU[~mask] == 0.0)
+
+    def check(ad, gmax, quotient):
+        """ad against the difference quotient at h = 1e-5, and at 1e-6 if a switching point spoils the first.
+        (J is a sum of squares of small residuals, whose rounding swamps the quotient for h below 1e-6.)"""
+        fd = quotient(1e-5)
+        if abs(ad - fd) > 1e-6 * max(gmax, abs(fd)):
+            fd = quotient(1e-6)
+        return abs(ad - fd) <= 1e-6 * max(gmax, abs(fd)), fd
+
+    def perturbed(arr, v, idx, d):
+        x = arr.copy()
+        x[(v,) + idx] += d
+        return x
+
+    lo = tuple(sl.start for sl in inter)
+    hi = tuple(sl.stop - 1 for sl in inter)
+    mid = tuple((a + b) // 2 for a, b in zip(lo, hi))
+    for r in range(5):
+        scale = max(np.abs(P0[r][inter]).max(), 0.05)
+        gmax = np.abs(gP[r][inter]).max()
+        for idx in (lo, mid, hi):
+            ok, fd = check(gP[(r,) + idx], gmax, lambda h: (loss(perturbed(P0, r, idx, h * scale), base) -
+                                                            loss(perturbed(P0, r, idx, -h * scale), base)) /
+                           (2.0 * h * scale))
+            assert ok, (r, idx, gP[(r,) + idx], fd)
+    # Psi enters the update of A only through the discrete gradient of G_A, which the discrete curl annihilates,
+    # so D~ (and J) does not depend on it: its gradient is zero up to rounding
+    amax = max(np.abs(gU[v][independent(w, v)]).max() for v in (5, 6, 7))
+    assert np.abs(gU[8]).max() <= 1e-12 * amax
+    for v in (5, 6, 7):
+        sl = independent(w, v)
+        scale = max(np.abs(base[v][sl]).max(), 1e-3)
+        gmax = np.abs(gU[v][sl]).max()
+        lo_v = tuple(x.start for x in sl)
+        mid_v = tuple((x.start + x.stop - 1) // 2 for x in sl)
+        for idx in (lo_v, mid_v):
+            ok, fd = check(gU[(v,) + idx], gmax, lambda h: (loss(P0, perturbed(base, v, idx, h * scale)) -
+                                                            loss(P0, perturbed(base, v, idx, -h * scale))) /
+                           (2.0 * h * scale))
+            assert ok, (v, idx, gU[(v,) + idx], fd)
