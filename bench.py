@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--batch-blocks", type=int, default=512)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward measurement")
     ap.add_argument("--adjoint-n", type=int, default=64, help="cells per axis of the adjoint workload")
+    ap.add_argument("--profile-region", choices=("none", "forward", "adjoint"), default="none",
+                    help="bracket one extra forward RK4 step (main workload) or one adjoint step with "
+                         "cudaProfilerStart/Stop, for a profiler run with --profile-from-start off")
     return ap.parse_args()
 
 
@@ -300,6 +303,11 @@ def run_adjoint(args, dev, stream):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms_a = e0.elapsed_time(e1) / reps
+    if args.profile_region == "adjoint":
+        torch.cuda.profiler.start()
+        s.rk4_step_adjoint(U0, P, lam, w.dt)
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.stop()
     # whole 10-step gradient
     nsteps = 10
     T = torch.from_numpy(W.config4_target(w)).to(dev)
@@ -407,6 +415,11 @@ def run_ours(args):
     cells = w.interior_cells
     value = world * cells * 4 * args.steps / (ms_max / 1e3)
     c2p = stats.cpu().tolist()
+    if args.profile_region == "forward":
+        torch.cuda.profiler.start()
+        s.rk4_step(U, P, w.dt)
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.stop()
     finite = bool(torch.isfinite(U[:, w.g:-w.g - 1, w.g:-w.g - 1, w.g:-w.g - 1]).all())
 
     # end to end through the host-buffer ABI call: H2D of U and P, the RK4 step, D2H of U and P, every step

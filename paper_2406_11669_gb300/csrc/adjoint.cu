@@ -85,17 +85,11 @@ __global__ void ka_sources(Blk b, Ws w, AdjWs a, F5 P, F9 mu, double gfac) {
     const long c = alin(b, i, j, k);
     Geo m;
     load_geo(b, w.cg, c, m);
-    typedef Dual<8> D8;
-    const D8 rho = D8::seed(P.f[0][c], 0), press = D8::seed(P.f[1][c], 1);
-    const D8 v[3] = {D8::seed(P.f[2][c], 2), D8::seed(P.f[3][c], 3), D8::seed(P.f[4][c], 4)};
-    const D8 B[3] = {D8::seed(w.bc[c], 5), D8::seed(w.bc[b.V + c], 6), D8::seed(w.bc[2 * b.V + c], 7)};
-    D8 src[5];
-    sources(m, w.cg, b.V, c, rho, press, v, B, gfac, src);
-    double g8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int q = 1; q < 5; q++) {
-      const double mq = mu.f[q][c];
-      for (int r = 0; r < 8; r++) g8[r] += src[q].d[r] * mq;
-    }
+    const double v[3] = {P.f[2][c], P.f[3][c], P.f[4][c]};
+    const double B[3] = {w.bc[c], w.bc[b.V + c], w.bc[2 * b.V + c]};
+    const double mq[5] = {0.0, mu.f[1][c], mu.f[2][c], mu.f[3][c], mu.f[4][c]};
+    double g8[8];
+    sources_vjp(m, w.cg, b.V, c, P.f[0][c], P.f[1][c], v, B, gfac, mq, g8);
     for (int r = 0; r < 5; r++) a.lP[r * b.V + c] += g8[r];
     for (int r = 0; r < 3; r++) a.lBc[r * b.V + c] += g8[5 + r];
   }
@@ -290,8 +284,8 @@ __global__ void ka_vertex_to_edges(Blk b, AdjWs a) {
 
 // ----------------------------------------------------------------------------------------------------------
 // Face solve along D (faces g..g+n along D, all transverse): adjoints of (F^, v~bar, c_max, c_min) -> adjoints
-// of the reconstructed left/right states and of the face field B~.  HLLE by hand, each side's Jacobian by
-// dual numbers in (rho, p, u^x, u^y, u^z, B_t1, B_t2, B~_n).
+// of the reconstructed left/right states and of the face field B~.  The primal side solves run first (their
+// speeds set the HLLE weights), then HLLE is reversed by hand and each side by its reverse-mode VJP.
 template <int D>
 __global__ void ka_faces(Blk b, Ws w, AdjWs a, double gamma, double gfac) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
@@ -316,18 +310,18 @@ __global__ void ka_faces(Blk b, Ws w, AdjWs a, double gamma, double gfac) {
     const double ia = fg[FG_IALP * b.V + c];
     const double width = fg[FG_WIDTH * b.V + c];
     const double isqg = fg[FG_ISQG * b.V + c];
-    typedef Dual<8> D8;
-    SideOutT<D8> s[2];
+    SideOut s[2];
+    double rho[2], press[2], u[2][3], B[2][3];
     for (int side = 0; side < 2; side++) {
       const long cc = side == 0 ? c - st : c;
       const double* __restrict__ rr = w.rec + (side == 0 ? NREC : 0) * b.V + cc;
-      const D8 rho = D8::seed(rr[0], 0), press = D8::seed(rr[b.V], 1);
-      const D8 u[3] = {D8::seed(rr[2 * b.V], 2), D8::seed(rr[3 * b.V], 3), D8::seed(rr[4 * b.V], 4)};
-      D8 B[3];
-      B[D] = D8::seed(w.bf[D * b.V + c], 7) * isqg;
-      B[T1] = D8::seed(rr[5 * b.V], 5);
-      B[T2] = D8::seed(rr[6 * b.V], 6);
-      face_side(m, ia, width, D, rho, press, u, B, gamma, gfac, s[side]);
+      rho[side] = rr[0];
+      press[side] = rr[b.V];
+      for (int q = 0; q < 3; q++) u[side][q] = rr[(2 + q) * b.V];
+      B[side][D] = w.bf[D * b.V + c] * isqg;
+      B[side][T1] = rr[5 * b.V];
+      B[side][T2] = rr[6 * b.V];
+      face_side(m, ia, width, D, rho[side], press[side], u[side], B[side], gamma, gfac, s[side]);
     }
     const double* lf = a.lface + (long)D * NFD * b.V + c;
     double lF[5], lvb[2];
@@ -335,63 +329,68 @@ __global__ void ka_faces(Blk b, Ws w, AdjWs a, double gamma, double gfac) {
     lvb[0] = lf[FD_VB1 * b.V];
     lvb[1] = lf[FD_VB2 * b.V];
     double lcmax = lf[FD_CMAX * b.V], lcmin = lf[FD_CMIN * b.V];
-    const double lpL = s[0].lp.v, lpR = s[1].lp.v, lmL = s[0].lm.v, lmR = s[1].lm.v;
+    const double lpL = s[0].lp, lpR = s[1].lp, lmL = s[0].lm, lmR = s[1].lm;
     const double cmax = fmax(0.0, fmax(lpL, lpR));
     const double cmin = -fmin(0.0, fmin(lmL, lmR));
     const double den = cmax + cmin;
-    // adjoints of the side outputs: U (5), F (5), lm, lp, vt_T1, vt_T2
-    double gU[2][5], gF[2][5], glp[2] = {0, 0}, glm[2] = {0, 0}, gvt[2][2];
+    SideBar wb[2];
+    for (int side = 0; side < 2; side++) {
+      wb[side].lp = wb[side].lm = 0.0;
+      wb[side].vt[D] = 0.0;
+    }
     if (den > 0.0) {
       const double id = 1.0 / den;
       for (int v = 0; v < 5; v++) {
-        const double dU = s[1].U[v].v - s[0].U[v].v;
-        const double Fh = (cmin * s[1].F[v].v + cmax * s[0].F[v].v - cmax * cmin * dU) * id;
-        gF[0][v] = cmax * id * lF[v];
-        gF[1][v] = cmin * id * lF[v];
-        gU[0][v] = cmax * cmin * id * lF[v];
-        gU[1][v] = -cmax * cmin * id * lF[v];
-        lcmax += (s[0].F[v].v - cmin * dU - Fh) * id * lF[v];
-        lcmin += (s[1].F[v].v - cmax * dU - Fh) * id * lF[v];
+        const double dU = s[1].U[v] - s[0].U[v];
+        const double Fh = (cmin * s[1].F[v] + cmax * s[0].F[v] - cmax * cmin * dU) * id;
+        wb[0].F[v] = cmax * id * lF[v];
+        wb[1].F[v] = cmin * id * lF[v];
+        wb[0].U[v] = cmax * cmin * id * lF[v];
+        wb[1].U[v] = -cmax * cmin * id * lF[v];
+        lcmax += (s[0].F[v] - cmin * dU - Fh) * id * lF[v];
+        lcmin += (s[1].F[v] - cmax * dU - Fh) * id * lF[v];
       }
-      const double vtL[2] = {s[0].vt[T1].v, s[0].vt[T2].v}, vtR[2] = {s[1].vt[T1].v, s[1].vt[T2].v};
+      const int tq[2] = {T1, T2};
       for (int q = 0; q < 2; q++) {
-        const double vb = (cmax * vtL[q] + cmin * vtR[q]) * id;
-        gvt[0][q] = cmax * id * lvb[q];
-        gvt[1][q] = cmin * id * lvb[q];
-        lcmax += (vtL[q] - vb) * id * lvb[q];
-        lcmin += (vtR[q] - vb) * id * lvb[q];
+        const double vtL = s[0].vt[tq[q]], vtR = s[1].vt[tq[q]];
+        const double vb = (cmax * vtL + cmin * vtR) * id;
+        wb[0].vt[tq[q]] = cmax * id * lvb[q];
+        wb[1].vt[tq[q]] = cmin * id * lvb[q];
+        lcmax += (vtL - vb) * id * lvb[q];
+        lcmin += (vtR - vb) * id * lvb[q];
       }
     } else {
       for (int v = 0; v < 5; v++) {
-        gF[0][v] = gF[1][v] = 0.5 * lF[v];
-        gU[0][v] = gU[1][v] = 0.0;
+        wb[0].F[v] = wb[1].F[v] = 0.5 * lF[v];
+        wb[0].U[v] = wb[1].U[v] = 0.0;
       }
-      for (int q = 0; q < 2; q++) gvt[0][q] = gvt[1][q] = 0.5 * lvb[q];
+      wb[0].vt[T1] = wb[1].vt[T1] = 0.5 * lvb[0];
+      wb[0].vt[T2] = wb[1].vt[T2] = 0.5 * lvb[1];
     }
     // c_max = max(0, lp_L, lp_R), c_min = -min(0, lm_L, lm_R): the branch taken carries the derivative
     if (cmax > 0.0) {
-      if (lpR > lpL) glp[1] = lcmax;
-      else glp[0] = lcmax;
+      if (lpR > lpL) wb[1].lp = lcmax;
+      else wb[0].lp = lcmax;
     }
     if (cmin > 0.0) {
-      if (lmR < lmL) glm[1] = -lcmin;
-      else glm[0] = -lcmin;
-    }
-    double gin[2][8];
-    for (int side = 0; side < 2; side++) {
-      for (int r = 0; r < 8; r++) {
-        double acc = glp[side] * s[side].lp.d[r] + glm[side] * s[side].lm.d[r] +
-                     gvt[side][0] * s[side].vt[T1].d[r] + gvt[side][1] * s[side].vt[T2].d[r];
-        for (int v = 0; v < 5; v++) acc += gU[side][v] * s[side].U[v].d[r] + gF[side][v] * s[side].F[v].d[r];
-        gin[side][r] = acc;
-      }
+      if (lmR < lmL) wb[1].lm = -lcmin;
+      else wb[0].lm = -lcmin;
     }
     // left state = upper values of cell c - e_D, right state = lower values of cell c (each used once)
-    for (int v = 0; v < NREC; v++) {
-      a.lrec[(NREC + v) * b.V + c - st] = gin[0][v];
-      a.lrec[v * b.V + c] = gin[1][v];
+    double gBn = 0.0;
+    for (int side = 0; side < 2; side++) {
+      double gr, gp, gu[3], gB[3];
+      face_side_vjp(m, ia, D, rho[side], press[side], u[side], B[side], gamma, gfac, s[side].lp, s[side].lm,
+                    wb[side], gr, gp, gu, gB);
+      double* lr = a.lrec + (side == 0 ? NREC * b.V + c - st : c);
+      lr[0] = gr;
+      lr[b.V] = gp;
+      for (int q = 0; q < 3; q++) lr[(2 + q) * b.V] = gu[q];
+      lr[5 * b.V] = gB[T1];
+      lr[6 * b.V] = gB[T2];
+      gBn += gB[D];
     }
-    a.lBf[D * b.V + c] += gin[0][7] + gin[1][7];
+    a.lBf[D * b.V + c] += gBn * isqg;
   }
 }
 
@@ -753,26 +752,27 @@ template <int D>
 static void adjoint_dir(const StageArgs& sa, const AdjWs& a, cudaStream_t s) {
   const Blk& b = sa.b;
   const int T = 128;
-  launch_recon_dir(sa, a.P, D, s);  // forward reconstruction of this direction into the workspace
+  Ws w = sa.w;
+  w.rec = a.rec3[D];  // this direction's reconstruction, kept from the recompute
   const long fc = (long)b.N[0] * b.N[1] * b.N[2] / b.N[D] * (b.n[D] + 1);
   cudaMemsetAsync(a.lrec, 0, 2 * NREC * b.V * sizeof(double), s);
-  ka_faces<D><<<agrid(fc, T), T, 0, s>>>(b, sa.w, a, sa.gamma, sa.gfac);
+  ka_faces<D><<<agrid(fc, T), T, 0, s>>>(b, w, a, sa.gamma, sa.gfac);
   const long rc = (long)b.N[0] * b.N[1] * b.N[2] / b.N[D] * (b.n[D] + 2);
-  if (sa.recon == 0) ka_recon<D, 0><<<agrid(rc, T), T, 0, s>>>(b, sa.w, a);
-  else if (sa.recon == 1) ka_recon<D, 1><<<agrid(rc, T), T, 0, s>>>(b, sa.w, a);
-  else ka_recon<D, 2><<<agrid(rc, T), T, 0, s>>>(b, sa.w, a);
+  if (sa.recon == 0) ka_recon<D, 0><<<agrid(rc, T), T, 0, s>>>(b, w, a);
+  else if (sa.recon == 1) ka_recon<D, 1><<<agrid(rc, T), T, 0, s>>>(b, w, a);
+  else ka_recon<D, 2><<<agrid(rc, T), T, 0, s>>>(b, w, a);
 }
 
 cudaError_t launch_rhs_adjoint(const StageArgs& sa, const AdjWs& a, double dt, cudaStream_t s) {
   const Blk& b = sa.b;
   const int T = 128;
-  // forward recompute: ghost fill of Y, face/centre field, recovery (flags), primitive ghost fill, forward RHS
-  // intermediates (u, face data of every direction)
+  // forward recompute: ghost fill of Y, face/centre field, recovery (flags), primitive ghost fill, u and the
+  // reconstruction and face data of every direction (what the reverse kernels read; no right-hand side)
   cudaError_t e = launch_ghost_state(b, a.Y, s);
   if (e == cudaSuccess) e = launch_bfield(b, sa.w, a.Y, s);
   if (e == cudaSuccess) e = launch_c2p(sa, a.Y, a.P, a.flags, nullptr, s);
   if (e == cudaSuccess) e = launch_ghost_prims(b, a.P, s);
-  if (e == cudaSuccess) e = launch_rhs(sa, a.Y, a.P, -1, dt, a.Y, a.Y, a.Y, a.dscratch, s);
+  if (e == cudaSuccess) e = launch_face_data(sa, a.P, a.rec3, s);
   if (e != cudaSuccess) return e;
   // adjoint accumulators
   cudaMemsetAsync(a.lY_base, 0, (size_t)ADJ_ACC_FIELDS * b.V * sizeof(double), s);

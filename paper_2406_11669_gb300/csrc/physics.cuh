@@ -28,21 +28,21 @@ struct Geo {
 };
 
 template <class T>
-__device__ __forceinline__ T contract_sym(const double m[6], const T a[3], const T b[3]) {
+__host__ __device__ __forceinline__ T contract_sym(const double m[6], const T a[3], const T b[3]) {
   return m[0] * a[0] * b[0] + m[3] * a[1] * b[1] + m[5] * a[2] * b[2] +
          m[1] * (a[0] * b[1] + a[1] * b[0]) + m[2] * (a[0] * b[2] + a[2] * b[0]) +
          m[4] * (a[1] * b[2] + a[2] * b[1]);
 }
 
 template <class T>
-__device__ __forceinline__ void lower(const double m[6], const T a[3], T out[3]) {
+__host__ __device__ __forceinline__ void lower(const double m[6], const T a[3], T out[3]) {
   out[0] = m[0] * a[0] + m[1] * a[1] + m[2] * a[2];
   out[1] = m[1] * a[0] + m[3] * a[1] + m[4] * a[2];
   out[2] = m[2] * a[0] + m[4] * a[1] + m[5] * a[2];
 }
 
 // inverse and sqrt(det) of a symmetric positive-definite 3x3 matrix (cofactors)
-__device__ __forceinline__ void sym_inverse(const double g[6], double gu[6], double* sqg) {
+__host__ __device__ __forceinline__ void sym_inverse(const double g[6], double gu[6], double* sqg) {
   const double c00 = g[3] * g[5] - g[4] * g[4];
   const double c01 = g[4] * g[2] - g[1] * g[5];
   const double c02 = g[1] * g[4] - g[3] * g[2];
@@ -83,7 +83,7 @@ using SideOut = SideOutT<double>;
 // polynomial is not for cold fluids) and solved by Newton from each light-cone speed, where it is monotone.
 struct Quartic {
   double A4, C2, cs2, u0, ud, b0, bd, betad, ia2, gdd;
-  __device__ __forceinline__ double newton(double lam, double width) const {
+  __host__ __device__ __forceinline__ double newton(double lam, double width) const {
 #pragma unroll 1
     for (int it = 0; it < 60; it++) {
       const double a = ud - lam * u0;
@@ -111,7 +111,7 @@ template <class T>
 struct QuarticT {
   T A4, C2, cs2, u0, ud, b0, bd;
   double betad, ia2, gdd;
-  __device__ __forceinline__ T root_step(double lam) const {
+  __host__ __device__ __forceinline__ T root_step(double lam) const {
     const T a = ud - lam * u0;
     const T bc = bd - lam * b0;
     const double lb = lam + betad;
@@ -128,7 +128,7 @@ struct QuarticT {
 
 // gfac = Gamma / (Gamma - 1), ia = 1 / alpha, width = alpha sqrt(gamma^dd) (hoisted by the caller)
 template <class T>
-__device__ __forceinline__ void face_side(const Geo& m, double ia, double width, int d, T rho, T press,
+__host__ __device__ __forceinline__ void face_side(const Geo& m, double ia, double width, int d, T rho, T press,
                                           const T u[3], const T B[3], double gamma, double gfac,
                                           SideOutT<T>& o) {
   const T uu = contract_sym(m.g, u, u);
@@ -219,17 +219,189 @@ __device__ __forceinline__ void face_side(const Geo& m, double ia, double width,
   }
 }
 
+// Reverse mode of face_side: weights wb on its outputs (U, F, lambda_-, lambda_+, v~) give the gradient
+// wb . d(outputs) / d(rho, p, u^i, B^i).  The primal is recomputed from the inputs except for the two roots, which
+// the caller passes (as face_side returned them); the roots are differentiated by the implicit-function theorem,
+// d lambda = -(dQ/d theta) / (dQ/d lambda) for the quartic's state-dependent coefficients theta.
+struct SideBar {
+  double U[5], F[5], lm, lp, vt[3];
+};
+
+__host__ __device__ __forceinline__ void face_side_vjp(const Geo& m, double ia, int d, double rho, double press,
+                                                       const double u[3], const double B[3], double gamma,
+                                                       double gfac, double lp, double lm, const SideBar& wb,
+                                                       double& grho, double& gp, double gu[3], double gB[3]) {
+  // ---- primal
+  const double uu = contract_sym(m.g, u, u);
+  const double W = sqrt(1.0 + uu);
+  const double iW = 1.0 / W;
+  const double v[3] = {u[0] * iW, u[1] * iW, u[2] * iW};
+  double vl[3], Bl[3];
+  lower(m.g, v, vl);
+  lower(m.g, B, Bl);
+  const double B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const double Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
+  const double iW2 = iW * iW;
+  const double b2 = B2 * iW2 + Bv * Bv;
+  const double rhoh = rho + gfac * press;
+  const double W2 = W * W;
+  const double z = rhoh * W2;
+  const double sg = m.sqg;
+  const double asg = m.alp * sg;
+  double U[5];
+  U[0] = sg * rho * W;
+  for (int a = 0; a < 3; a++) U[1 + a] = sg * ((z + B2) * vl[a] - Bv * Bl[a]);
+  U[4] = sg * (z - press - rho * W + B2 - 0.5 * b2);
+  const double vtd = m.alp * v[d] - m.beta[d];
+  const double pt = press + 0.5 * b2;
+  const double Bd = B[d];
+  double bl[3];
+  for (int a = 0; a < 3; a++) bl[a] = Bl[a] * iW + W * Bv * vl[a];
+  const double u0 = W * ia;
+  const double ud = W * (v[d] - m.beta[d] * ia);
+  const double b0 = W * Bv * ia;
+  const double bd = (Bd + m.alp * b0 * ud) * iW;
+  const double cs2 = gamma * press / rhoh;
+  const double A4 = rhoh * (1.0 - cs2);
+  const double C2 = rhoh * cs2 + b2;
+  const double ia2 = ia * ia;
+  const double gdd = m.gu[sym(d, d)];
+  // ---- reverse
+  double bA4 = 0.0, bC2 = 0.0, bcs2 = 0.0, bu0 = 0.0, bud = 0.0, bb0 = 0.0, bbd = 0.0;
+  const double lam[2] = {lp, lm}, blam[2] = {wb.lp, wb.lm};
+  for (int k = 0; k < 2; k++) {
+    if (blam[k] == 0.0) continue;
+    const double L = lam[k];
+    const double a = ud - L * u0;
+    const double bc = bd - L * b0;
+    const double lb = L + m.beta[d];
+    const double G = gdd - lb * lb * ia2;
+    const double dG = -2.0 * lb * ia2;
+    const double a2 = a * a;
+    const double r = cs2 * bc * bc - C2 * a2;
+    const double dr = -2.0 * (cs2 * bc * b0 - C2 * a * u0);
+    const double dq = -4.0 * A4 * a2 * a * u0 + dr * G + r * dG;
+    const double sc = -blam[k] / dq;
+    const double Qa = 4.0 * A4 * a2 * a - 2.0 * C2 * a * G;
+    const double Qbc = 2.0 * cs2 * bc * G;
+    bA4 += sc * a2 * a2;
+    bC2 -= sc * a2 * G;
+    bcs2 += sc * bc * bc * G;
+    bud += sc * Qa;
+    bu0 -= sc * Qa * L;
+    bbd += sc * Qbc;
+    bb0 -= sc * Qbc * L;
+  }
+  double brhoh = bA4 * (1.0 - cs2) + bC2 * cs2;
+  bcs2 += bC2 * rhoh - bA4 * rhoh;
+  double bb2 = bC2;
+  double bp = bcs2 * gamma / rhoh;
+  brhoh -= bcs2 * cs2 / rhoh;
+  // bd = (Bd + alp b0 ud) / W
+  double bBd = bbd * iW;
+  bb0 += bbd * m.alp * ud * iW;
+  bud += bbd * m.alp * b0 * iW;
+  double biW = bbd * (Bd + m.alp * b0 * ud);
+  // b0 = W Bv / alp, ud = W (v^d - beta^d / alp), u0 = W / alp
+  double bW = bb0 * Bv * ia + bud * (v[d] - m.beta[d] * ia) + bu0 * ia;
+  double bBv = bb0 * W * ia;
+  double bv[3] = {0.0, 0.0, 0.0};
+  bv[d] += bud * W;
+  // fluxes
+  double bU[5], bvl[3] = {0.0, 0.0, 0.0}, bBl[3] = {0.0, 0.0, 0.0};
+  for (int q = 0; q < 5; q++) bU[q] = wb.U[q];
+  double bvtd = 0.0, bpt = 0.0;
+  bU[4] += wb.F[4] * vtd;
+  bvtd += wb.F[4] * U[4];
+  bpt += wb.F[4] * asg * v[d];
+  bv[d] += wb.F[4] * asg * pt;
+  bBv -= wb.F[4] * asg * Bd;
+  bBd -= wb.F[4] * asg * Bv;
+  bpt += wb.F[1 + d] * asg;
+  for (int a = 0; a < 3; a++) {
+    const double f = wb.F[1 + a];
+    bU[1 + a] += f * vtd;
+    bvtd += f * U[1 + a];
+    const double bbl = -f * asg * Bd * iW;
+    bBd -= f * asg * bl[a] * iW;
+    biW -= f * asg * bl[a] * Bd;
+    // bl = Bl / W + W Bv vl
+    bBl[a] += bbl * iW;
+    biW += bbl * Bl[a];
+    bW += bbl * Bv * vl[a];
+    bBv += bbl * W * vl[a];
+    bvl[a] += bbl * W * Bv;
+  }
+  bU[0] += wb.F[0] * vtd;
+  bvtd += wb.F[0] * U[0];
+  double bpress = bp + bpt;
+  bb2 += 0.5 * bpt;
+  // v~ = alp v - beta
+  for (int a = 0; a < 3; a++) bv[a] += wb.vt[a] * m.alp;
+  bv[d] += bvtd * m.alp;
+  // conserved variables
+  const double bU4 = bU[4] * sg;
+  double bz = bU4;
+  bpress -= bU4;
+  double brho = -bU4 * W;
+  bW -= bU4 * rho;
+  double bB2 = bU4;
+  bb2 -= 0.5 * bU4;
+  for (int a = 0; a < 3; a++) {
+    const double bs = bU[1 + a] * sg;
+    bz += bs * vl[a];
+    bB2 += bs * vl[a];
+    bvl[a] += bs * (z + B2);
+    bBv -= bs * Bl[a];
+    bBl[a] -= bs * Bv;
+  }
+  brho += bU[0] * sg * W;
+  bW += bU[0] * sg * rho;
+  // z = rho h W^2, rho h = rho + gfac p
+  brhoh += bz * W2;
+  bW += bz * rhoh * 2.0 * W;
+  brho += brhoh;
+  bpress += brhoh * gfac;
+  // b^2 = B^2 / W^2 + Bv^2
+  bB2 += bb2 * iW2;
+  biW += bb2 * B2 * 2.0 * iW;
+  bBv += bb2 * 2.0 * Bv;
+  // Bv = B . vl, B^2 = B . Bl, vl = g v, Bl = g B
+  double bB[3];
+  for (int i = 0; i < 3; i++) {
+    bB[i] = bBv * vl[i] + bB2 * Bl[i];
+    bvl[i] += bBv * B[i];
+    bBl[i] += bB2 * B[i];
+  }
+  double tmp[3];
+  lower(m.g, bBl, tmp);
+  for (int i = 0; i < 3; i++) bB[i] += tmp[i];
+  bB[d] += bBd;
+  lower(m.g, bvl, tmp);
+  for (int i = 0; i < 3; i++) bv[i] += tmp[i];
+  // v = u / W, W = sqrt(1 + u.g.u)
+  for (int a = 0; a < 3; a++) biW += bv[a] * u[a];
+  bW -= biW * iW2;
+  const double buu = bW * 0.5 * iW;
+  double gl[3];
+  lower(m.g, u, gl);
+  for (int a = 0; a < 3; a++) gu[a] = bv[a] * iW + 2.0 * buu * gl[a];
+  for (int i = 0; i < 3; i++) gB[i] = bB[i];
+  grho = brho;
+  gp = bpress;
+}
+
 // ----------------------------------------------------------------------------------------------------------
 // Reconstruction of one cell from a_{i-2..i+2}: values at its lower (lo) and upper (hi) faces.
 
 template <class T>
-__device__ __forceinline__ T minmod2(T x, T y) {
+__host__ __device__ __forceinline__ T minmod2(T x, T y) {
   if (x * y <= 0.0) return T(0.0);
   return (fabs(x) <= fabs(y)) ? x : y;
 }
 
 template <class T>
-__device__ __forceinline__ T ppm_dq(T am, T a0, T ap) {
+__host__ __device__ __forceinline__ T ppm_dq(T am, T a0, T ap) {
   // van Leer limited slope of Colella & Woodward (1984)
   if ((ap - a0) * (a0 - am) <= 0.0) return T(0.0);
   const T c = 0.5 * (ap - am);
@@ -238,7 +410,7 @@ __device__ __forceinline__ T ppm_dq(T am, T a0, T ap) {
 }
 
 template <class T>
-__device__ __forceinline__ void ppm_limit(T ai, T& l, T& r) {
+__host__ __device__ __forceinline__ void ppm_limit(T ai, T& l, T& r) {
   // monotonicity constraints of the parabola (CW84)
   if ((r - ai) * (ai - l) <= 0.0) {
     l = ai;
@@ -256,7 +428,7 @@ __device__ __forceinline__ void ppm_limit(T ai, T& l, T& r) {
 // smoothness indicators are those of the upper face in reverse order, so the three indicators and the three
 // ratios tau5 / (beta_k + eps) are shared; the three reciprocals come from one division.
 template <class T>
-__device__ __forceinline__ void wenoz_both(const T s[5], T& lo, T& hi) {
+__host__ __device__ __forceinline__ void wenoz_both(const T s[5], T& lo, T& hi) {
   const T t0a = s[0] - 2.0 * s[1] + s[2], t0b = s[0] - 4.0 * s[1] + 3.0 * s[2];
   const T t1a = s[1] - 2.0 * s[2] + s[3], t1b = s[1] - s[3];
   const T t2a = s[2] - 2.0 * s[3] + s[4], t2b = 3.0 * s[2] - 4.0 * s[3] + s[4];
@@ -296,7 +468,7 @@ __device__ __forceinline__ void wenoz_both(const T s[5], T& lo, T& hi) {
 }
 
 template <int SCHEME, class T>
-__device__ __forceinline__ void recon5(const T a[5], T& lo, T& hi) {
+__host__ __device__ __forceinline__ void recon5(const T a[5], T& lo, T& hi) {
   if (SCHEME == 0) {
     const T s = minmod2(a[2] - a[1], a[3] - a[2]);
     lo = a[2] - 0.5 * s;
@@ -321,7 +493,7 @@ __device__ __forceinline__ void recon5(const T a[5], T& lo, T& hi) {
 // (b = beta) with T^{mu nu} = (rho h + b^2) u u + (p + b^2/2) g^{mu nu} - b b (Eq. tmunu); cg is the centre
 // geometry record (K_ij and the 4th-order metric derivatives at index c, field pitch V).
 template <class T>
-__device__ __forceinline__ void sources(const Geo& m, const double* __restrict__ cg, long V, long c, T rho, T press,
+__host__ __device__ __forceinline__ void sources(const Geo& m, const double* __restrict__ cg, long V, long c, T rho, T press,
                                           const T v[3], const T B[3], double gfac, T src[5]) {
   T vl[3], Bl[3];
   lower(m.g, v, vl);
@@ -381,6 +553,136 @@ __device__ __forceinline__ void sources(const Geo& m, const double* __restrict__
 }
 
 
+// Reverse mode of sources: g = sum_{q=1..4} mu[q] d src_q / d(rho, p, v^i, B^i).  The sources are linear in the
+// stress-energy components, so the weights are first carried back to T^00, T^0i, T^ij (metric coefficients
+// only), then through T^{mu nu}(rho, p, v, B).
+__host__ __device__ __forceinline__ void sources_vjp(const Geo& m, const double* __restrict__ cg, long V, long c,
+                                                     double rho, double press, const double v[3],
+                                                     const double B[3], double gfac, const double mu[5],
+                                                     double g[8]) {
+  // ---- primal
+  double vl[3], Bl[3];
+  lower(m.g, v, vl);
+  lower(m.g, B, Bl);
+  const double W = 1.0 / sqrt(1.0 - (v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2]));
+  const double B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const double Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
+  const double ia = 1.0 / m.alp;
+  const double iW = 1.0 / W;
+  const double b2 = B2 * iW * iW + Bv * Bv;
+  const double rhoh = rho + gfac * press;
+  const double e = rhoh + b2;
+  double u[4], bb[4];
+  u[0] = W * ia;
+  bb[0] = W * Bv * ia;
+  for (int q = 0; q < 3; q++) {
+    u[1 + q] = W * (v[q] - m.beta[q] * ia);
+    bb[1 + q] = (B[q] + m.alp * bb[0] * u[1 + q]) * iW;
+  }
+  const double ia2 = ia * ia;
+  // ---- weights of T^00, T^0i, T^ij in sum_q mu_q src_q
+  double K[6], dalp[3];
+  for (int q = 0; q < 6; q++) K[q] = cg[(CG_K + q) * V + c];
+  for (int q = 0; q < 3; q++) dalp[q] = cg[(CG_DALP + q) * V + c];
+  double betal[3];
+  lower(m.g, m.beta, betal);
+  const double asg = m.alp * m.sqg;
+  double Kb[3];
+  for (int q = 0; q < 3; q++) Kb[q] = K[sym(q, 0)] * m.beta[0] + K[sym(q, 1)] * m.beta[1] + K[sym(q, 2)] * m.beta[2];
+  const double w4 = mu[4] * asg;
+  double bT00 = w4 * (m.beta[0] * Kb[0] + m.beta[1] * Kb[1] + m.beta[2] * Kb[2]);
+  double bT0[3], bTij[6];
+  for (int q = 0; q < 3; q++) {
+    bT00 -= w4 * m.beta[q] * dalp[q];
+    bT0[q] = w4 * (2.0 * Kb[q] - dalp[q]);
+  }
+  for (int q = 0; q < 6; q++) bTij[q] = ((q == 0 || q == 3 || q == 5) ? 1.0 : 2.0) * w4 * K[q];
+  double bT0l[3] = {0.0, 0.0, 0.0}, bM[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = 0; i < 3; i++) {
+    const double wi = mu[1 + i] * asg;
+    bT00 -= wi * m.alp * dalp[i];
+    for (int q = 0; q < 3; q++) bT0l[q] += wi * cg[(CG_DBETA + i * 3 + q) * V + c];
+    const double* dg = cg + (CG_DG + i * 6) * V + c;
+    bM[0] += 0.5 * wi * dg[0];
+    bM[3] += 0.5 * wi * dg[3 * V];
+    bM[5] += 0.5 * wi * dg[5 * V];
+    bM[1] += wi * dg[V];
+    bM[2] += wi * dg[2 * V];
+    bM[4] += wi * dg[4 * V];
+  }
+  for (int q = 0; q < 3; q++) {
+    bT00 += bT0l[q] * betal[q];
+    for (int r = 0; r < 3; r++) bT0[r] += bT0l[q] * m.g[sym(q, r)];
+  }
+  for (int q = 0; q < 3; q++)
+    for (int r = q; r < 3; r++) {
+      const double bm = bM[sym(q, r)];
+      bT00 += bm * m.beta[q] * m.beta[r];
+      bT0[q] += bm * m.beta[r];
+      bT0[r] += bm * m.beta[q];
+      bTij[sym(q, r)] += bm;
+    }
+  // ---- T^{mu nu} = e u u + p_t g^{mu nu} - b b, back to (e, p_t, u, b)
+  double be = bT00 * u[0] * u[0], bpt = -bT00 * ia2;
+  double bu[4] = {2.0 * e * u[0] * bT00, 0.0, 0.0, 0.0};
+  double bbb[4] = {-2.0 * bb[0] * bT00, 0.0, 0.0, 0.0};
+  for (int q = 0; q < 3; q++) {
+    be += bT0[q] * u[0] * u[1 + q];
+    bpt += bT0[q] * m.beta[q] * ia2;
+    bu[0] += bT0[q] * e * u[1 + q];
+    bu[1 + q] += bT0[q] * e * u[0];
+    bbb[0] -= bT0[q] * bb[1 + q];
+    bbb[1 + q] -= bT0[q] * bb[0];
+  }
+  for (int q = 0; q < 3; q++)
+    for (int r = q; r < 3; r++) {
+      const double bt = bTij[sym(q, r)];
+      be += bt * u[1 + q] * u[1 + r];
+      bpt += bt * (m.gu[sym(q, r)] - m.beta[q] * m.beta[r] * ia2);
+      bu[1 + q] += bt * e * u[1 + r];
+      bu[1 + r] += bt * e * u[1 + q];
+      bbb[1 + q] -= bt * bb[1 + r];
+      bbb[1 + r] -= bt * bb[1 + q];
+    }
+  // b^i = (B^i + alpha b^0 u^i) / W, b^0 = W Bv / alpha, u^i = W (v^i - beta^i / alpha), u^0 = W / alpha
+  double bB[3], bv[3], biW = 0.0, bW = 0.0, bBv = 0.0;
+  for (int q = 0; q < 3; q++) {
+    bB[q] = bbb[1 + q] * iW;
+    bbb[0] += bbb[1 + q] * m.alp * u[1 + q] * iW;
+    bu[1 + q] += bbb[1 + q] * m.alp * bb[0] * iW;
+    biW += bbb[1 + q] * (B[q] + m.alp * bb[0] * u[1 + q]);
+  }
+  bW += bbb[0] * Bv * ia + bu[0] * ia;
+  bBv += bbb[0] * W * ia;
+  for (int q = 0; q < 3; q++) {
+    bW += bu[1 + q] * (v[q] - m.beta[q] * ia);
+    bv[q] = bu[1 + q] * W;
+  }
+  // e = rho h + b^2, p_t = p + b^2 / 2, b^2 = B^2 / W^2 + Bv^2, rho h = rho + gfac p
+  const double bb2 = be + 0.5 * bpt;
+  const double brhoh = be;
+  double bB2 = bb2 * iW * iW;
+  biW += bb2 * B2 * 2.0 * iW;
+  bBv += bb2 * 2.0 * Bv;
+  g[0] = brhoh;
+  g[1] = bpt + gfac * brhoh;
+  // W = (1 - v.g.v)^(-1/2), iW = 1 / W
+  bW -= biW * iW * iW;
+  const double bvv = bW * 0.5 * W * W * W;
+  // Bv = B . g v, B^2 = B . g B
+  for (int q = 0; q < 3; q++) {
+    bv[q] += 2.0 * bvv * vl[q];
+    bB[q] += bBv * vl[q] + 2.0 * bB2 * Bl[q];
+  }
+  double tmp[3];
+  const double bvlB[3] = {bBv * B[0], bBv * B[1], bBv * B[2]};
+  lower(m.g, bvlB, tmp);
+  for (int q = 0; q < 3; q++) {
+    g[2 + q] = bv[q] + tmp[q];
+    g[5 + q] = bB[q];
+  }
+}
+
 // ----------------------------------------------------------------------------------------------------------
 // Primitive recovery (Sec. 3.5) for one cell.  Inputs undensitised: D, S_i, tau, centre B^i.
 
@@ -395,7 +697,7 @@ struct C2PResult {
   int iters;
 };
 
-__device__ __forceinline__ void c2p_velocity(const Geo& m, const double S[3], const double B[3], double z,
+__host__ __device__ __forceinline__ void c2p_velocity(const Geo& m, const double S[3], const double B[3], double z,
                                              double B2, double BS, double v[3]) {
   // Eq. (Noble2D v)
   const double izB = 1.0 / (z + B2);
@@ -405,11 +707,11 @@ __device__ __forceinline__ void c2p_velocity(const Geo& m, const double S[3], co
   v[2] = (m.gu[2] * S[0] + m.gu[4] * S[1] + m.gu[5] * S[2]) * izB + f * B[2];
 }
 
-__device__ __forceinline__ bool not_physical(double x) { return !(x >= 0.0) || isinf(x); }
+__host__ __device__ __forceinline__ bool not_physical(double x) { return !(x >= 0.0) || isinf(x); }
 
 // Noble et al. 2D Newton on (z, v^2): residuals Eqs. (Noble2D momentum) and (Noble2D energy) with the ideal-gas
 // p(z, v^2) = (G-1)/G (z (1 - v^2) - D sqrt(1 - v^2)); a step that would make z <= 0 halves z instead.
-__device__ inline bool c2p_noble(const Geo& m, double D, const double S[3], double tau, const double B[3], double S2,
+__host__ __device__ inline bool c2p_noble(const Geo& m, double D, const double S[3], double tau, const double B[3], double S2,
                           double B2, double BS, double z, double v2, const C2PParams& P, C2PResult& r) {
   const double gf = (P.gamma - 1.0) / P.gamma;
   const double v2max = 1.0 - 1.0 / (P.W_max * P.W_max);
@@ -459,7 +761,7 @@ __device__ inline bool c2p_noble(const Geo& m, double D, const double S[3], doub
 // Palenzuela et al. 1D function f(x) = x - h^(x) W^(x), x = hW (Eq. Palenzuela Brent and the steps below it).
 struct PalFn {
   double q, r, s, t, D, gamma, v2max;
-  __device__ __forceinline__ double operator()(double x, double* W_, double* rho_, double* eps_) const {
+  __host__ __device__ __forceinline__ double operator()(double x, double* W_, double* rho_, double* eps_) const {
     double v2 = (r * x * x + t * t * (2.0 * x + s)) / (x * x * (x + s) * (x + s));
     v2 = fmin(fmax(v2, 0.0), v2max);
     const double W = 1.0 / sqrt(1.0 - v2);
@@ -476,7 +778,7 @@ struct PalFn {
 
 // Bracketed root by Brent's method (Brent 1973): inverse quadratic / secant steps kept inside the bracket,
 // bisection otherwise.  Returns false without a sign change or after maxiter.
-__device__ inline bool brent(const PalFn& f, double lo, double hi, double xtol, int maxiter, double* root) {
+__host__ __device__ inline bool brent(const PalFn& f, double lo, double hi, double xtol, int maxiter, double* root) {
   double W_, r_, e_;
   double a = lo, b = hi, fa = f(a, &W_, &r_, &e_), fb = f(b, &W_, &r_, &e_);
   if (!isfinite(fa) || !isfinite(fb) || (fa > 0.0 && fb > 0.0) || (fa < 0.0 && fb < 0.0)) return false;
@@ -531,7 +833,7 @@ __device__ inline bool brent(const PalFn& f, double lo, double hi, double xtol, 
   return false;
 }
 
-__device__ inline bool c2p_palenzuela(const Geo& m, double D, const double S[3], double tau, const double B[3], double S2,
+__host__ __device__ inline bool c2p_palenzuela(const Geo& m, double D, const double S[3], double tau, const double B[3], double S2,
                                double B2, double BS, const C2PParams& P, C2PResult& r) {
   PalFn f;
   f.q = tau / D;

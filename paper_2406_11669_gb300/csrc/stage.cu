@@ -898,6 +898,19 @@ cudaError_t launch_recon_dir(const StageArgs& a, const F5& P, int D, cudaStream_
   return cudaGetLastError();
 }
 
+cudaError_t launch_face_data(const StageArgs& a, const F5& P, double* const rec[3], cudaStream_t s) {
+  Single t = single_of(a.b, a.w);
+  t.r.P = P;
+  const StageConsts k = consts_of(a, -1, 0.0, nullptr);
+  launch<UVel>(t, k, KIND_CELLS_ALL, s);
+  Single td[3] = {t, t, t};
+  for (int d = 0; d < 3; d++) td[d].r.w.rec = rec[d];
+  seq_dir<0>(td[0], k, a.recon, s);
+  seq_dir<1>(td[1], k, a.recon, s);
+  seq_dir<2>(td[2], k, a.recon, s);
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------------------------------------------------
 // Batched stage: every block of the table in one launch per kernel.
 
