@@ -182,6 +182,17 @@ asterx_status asterx_rhs_adjoint(const asterx_params *p, const asterx_block *blk
                                  asterx_state *lam, void *ws, size_t ws_bytes, void *aws, size_t aws_bytes,
                                  asterx_stream stream);
 
+/* Adjoint of one RK stage as asterx_rk_stage forms it (k = L(Us); Unext = Un + c dt k, Uacc' = Uacc + b dt k for
+ * stages 0..2; Unext = Un + Uacc + dt/6 k for stage 3): given the adjoints lam_next of Unext and lam_acc of
+ * Uacc' (ignored, may be NULL, for stage 3), writes lam_s = (dL/dUs)^T kbar with kbar = c dt lam_next + b dt
+ * lam_acc (dt/6 lam_next for stage 3).  The linear parts (Un receives lam_next, Uacc receives lam_acc, or
+ * lam_next at stage 3) are the caller's to add.  Us is the stage's input state (a checkpoint; unchanged), P a
+ * primitive guess (overwritten by the recovery at Us). */
+asterx_status asterx_rk_stage_adjoint(const asterx_params *p, const asterx_block *blk, int stage, double dt,
+                                      const asterx_state *Us, asterx_prims *P, const asterx_state *lam_next,
+                                      const asterx_state *lam_acc, asterx_state *lam_s, void *ws, size_t ws_bytes,
+                                      void *aws, size_t aws_bytes, asterx_stream stream);
+
 /* Adjoint of one classical RK4 step U_{n+1} = Phi(U_n): on entry lam holds dJ/dU_{n+1}, on exit dJ/dU_n.
  * Un is the checkpoint of the step's input state (unchanged); P is a primitive guess (overwritten). */
 asterx_status asterx_rk4_step_adjoint(const asterx_params *p, const asterx_block *blk, double dt,

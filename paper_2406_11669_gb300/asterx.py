@@ -98,9 +98,11 @@ def lib():
         L.asterx_rhs_adjoint.argtypes = [P, B, ctypes.c_double, S, Pr, S, S, vp, sz, vp, sz, st]
         L.asterx_rk4_step_adjoint.argtypes = [P, B, ctypes.c_double, S, Pr, S, vp, sz, vp, sz, st]
         L.asterx_prim2con_adjoint.argtypes = [P, B, S, Pr, S, Pr, vp, sz, vp, sz, st]
+        L.asterx_rk_stage_adjoint.argtypes = [P, B, ctypes.c_int, ctypes.c_double, S, Pr, S, S, S, vp, sz, vp, sz,
+                                              st]
         L.asterx_rk4_steps_checkpointed.argtypes = [P, B, ctypes.c_double, ctypes.c_int, S, Pr, S, vp, vp, sz, st]
         L.asterx_rk4_adjoint_steps.argtypes = [P, B, ctypes.c_double, ctypes.c_int, S, Pr, S, vp, sz, vp, sz, st]
-        for name in ("asterx_rhs_adjoint", "asterx_rk4_step_adjoint", "asterx_prim2con_adjoint",
+        for name in ("asterx_rhs_adjoint", "asterx_rk4_step_adjoint", "asterx_prim2con_adjoint", "asterx_rk_stage_adjoint",
                      "asterx_rk4_steps_checkpointed", "asterx_rk4_adjoint_steps"):
             getattr(L, name).restype = ctypes.c_int
         L.asterx_con2prim_noalloc.argtypes = [P, B, M, S, Pr, vp, vp, st]
@@ -287,6 +289,15 @@ class Solver:
         _check(lib().asterx_rhs_adjoint(*self._args(), float(dt), ctypes.byref(u), ctypes.byref(p), ctypes.byref(m),
                                         ctypes.byref(l), self.ws_ptr, self.ws_bytes, ap, ab, _stream(stream)),
                "asterx_rhs_adjoint")
+
+    def rk_stage_adjoint(self, stage, dt, Us, P, lam_next, lam_acc, lam_s, stream=None):
+        """lam_s = (dL/dUs)^T (c dt lam_next + b dt lam_acc) for stage 0..2, (dL/dUs)^T (dt/6 lam_next) for stage 3."""
+        ap, ab = self._adjoint_ws()
+        la = ctypes.byref(state_struct(lam_acc)) if lam_acc is not None else None
+        _check(lib().asterx_rk_stage_adjoint(*self._args(), int(stage), float(dt), ctypes.byref(state_struct(Us)),
+                                             ctypes.byref(prims_struct(P)), ctypes.byref(state_struct(lam_next)),
+                                             la, ctypes.byref(state_struct(lam_s)), self.ws_ptr, self.ws_bytes, ap,
+                                             ab, _stream(stream)), "asterx_rk_stage_adjoint")
 
     def rk4_step_adjoint(self, Un, P, lam, dt, stream=None):
         """In place: lam = dJ/dU_{n+1} on entry, dJ/dU_n on exit, for the RK4 step taken from state Un."""

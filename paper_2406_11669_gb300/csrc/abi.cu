@@ -588,6 +588,37 @@ asterx_status asterx_rhs_adjoint(const asterx_params* p, const asterx_block* blk
   return cuda_status(e);
 }
 
+asterx_status asterx_rk_stage_adjoint(const asterx_params* p, const asterx_block* blk, int stage, double dt,
+                                      const asterx_state* Us, asterx_prims* P, const asterx_state* lam_next,
+                                      const asterx_state* lam_acc, asterx_state* lam_s, void* ws, size_t ws_bytes,
+                                      void* aws, size_t aws_bytes, asterx_stream stream) {
+  asterx_status st = adj_checks(p, blk, dt, ws, ws_bytes, aws, aws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (stage < 0 || stage > 3) return ASTERX_EINVAL;
+  if (!set_ok<asterx_state, 9>(Us) || !set_ok<asterx_prims, 5>(P) || !set_ok<asterx_state, 9>(lam_next) ||
+      !set_ok<asterx_state, 9>(lam_s) || (stage < 3 && !set_ok<asterx_state, 9>(lam_acc)))
+    return ASTERX_EINVAL;
+  StageArgs sa = make_args(p, blk, ws);
+  const Blk& b = sa.b;
+  AdjLayout L = make_adj(blk, aws);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // kbar = c dt lam_next + b dt lam_acc (stages 0..2), dt/6 lam_next (stage 3)
+  const double c[3] = {0.5, 0.5, 1.0}, w[3] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0};
+  cudaError_t e = copy9(L.kbar, f9(lam_next), b.V, s);
+  if (e == cudaSuccess && stage < 3) {
+    e = copy9(L.lam, f9(lam_acc), b.V, s);
+    if (e == cudaSuccess) e = launch_axpby9(b, w[stage] * dt, L.lam, c[stage] * dt, L.kbar, s);
+  } else if (e == cudaSuccess) {
+    e = launch_axpby9(b, 0.0, L.kbar, dt / 6.0, L.kbar, s);
+  }
+  if (e == cudaSuccess) e = launch_mask_owned9(b, L.kbar, s);
+  if (e == cudaSuccess) e = copy9(L.ycopy, f9(Us), b.V, s);
+  AdjWs a = adj_ws(L, b, L.ycopy, f5(P), L.kbar);
+  if (e == cudaSuccess) e = launch_rhs_adjoint(sa, a, dt, s);
+  if (e == cudaSuccess) e = copy9(f9(lam_s), f9_from(a.lY, b.V), b.V, s);
+  return cuda_status(e);
+}
+
 asterx_status asterx_rk4_step_adjoint(const asterx_params* p, const asterx_block* blk, double dt,
                                       const asterx_state* Un, asterx_prims* P, asterx_state* lam, void* ws,
                                       size_t ws_bytes, void* aws, size_t aws_bytes, asterx_stream stream) {

@@ -262,3 +262,84 @@ def test_loss_gradient_through_steps_and_initial_data():
                                                             loss(P0, perturbed(base, v, idx, -h * scale))) /
                            (2.0 * h * scale))
             assert ok, (v, idx, gU[(v,) + idx], fd)
+
+
+def test_stage_adjoints_compose_to_the_step_adjoint():
+    """Four asterx_rk_stage_adjoint calls with the linear RK4 bookkeeping reproduce asterx_rk4_step_adjoint."""
+    need_gpu()
+    w = W.smooth_general(n=(10, 9, 8), seed=108, **CASES["minmod_copy_lorenz"])
+    prob = Problem(w, seed=2205)
+    case = GpuCase(w)
+    s = case.solver
+    dt = w.dt
+    # forward stages (the checkpoints Y0..Y3)
+    Y = [case.dev(prob.U)]
+    acc = s.zeros_state()
+    P = case.dev(prob.P)
+    for st in range(3):
+        nxt = Y[-1].clone()
+        s.rk_stage(st, dt, Y[0], Y[st], nxt, acc, P)
+        Y.append(nxt)
+    lam = case.dev(np.where(prob.mask, prob.r_mu, 0.0))
+    # reverse: k-bar weights through the stages, U_n collects every stage input's adjoint plus lam
+    total = lam.clone()
+    lam_s = s.zeros_state()
+    s.rk_stage_adjoint(3, dt, Y[3], P, lam, None, lam_s)
+    total += lam_s
+    lam_acc = lam.clone()
+    lam_next = lam_s
+    for st in (2, 1, 0):
+        out = s.zeros_state()
+        s.rk_stage_adjoint(st, dt, Y[st], P, lam_next, lam_acc, out)
+        total += out
+        lam_next = out
+    ref = case.dev(np.where(prob.mask, prob.r_mu, 0.0))
+    s.rk4_step_adjoint(case.dev(prob.U), case.dev(prob.P), ref, dt)
+    a, r = case.host(total), case.host(ref)
+    for v in range(9):
+        scale = np.abs(r[v]).max()
+        assert np.abs(a[v] - r[v]).max() <= 1e-12 * scale, v
+
+
+def test_autograd_functions_match_the_direct_calls():
+    """The loss gradient through torch.autograd (InitialData, RK4Step) equals the direct adjoint calls."""
+    need_gpu()
+    from paper_2406_11669_gb300.autograd import InitialData, RK4Step
+    w = W.smooth_general(n=(9, 8, 10), seed=109, **CASES["ppm_periodic_lorenz"])
+    case = GpuCase(w)
+    s = case.solver
+    g, n = w.g, w.n
+    inter = (slice(g, g + n[2]), slice(g, g + n[1]), slice(g, g + n[0]))
+    P0 = case.dev(O.prims_array(w))
+    pot0 = s.zeros_state()
+    pot0[5], pot0[6], pot0[7], pot0[8] = (case.dev(w.A["Ax"]), case.dev(w.A["Ay"]), case.dev(w.A["Az"]),
+                                          case.dev(w.Psi))
+    T = torch.ones_like(pot0[0])
+    # autograd
+    Pr = P0.clone().requires_grad_(True)
+    pot = pot0.clone().requires_grad_(True)
+    Pbuf = P0.clone()
+    U = InitialData.apply(Pr, pot, s)
+    for _ in range(2):
+        U = RK4Step.apply(U, s, Pbuf, w.dt)
+    loss = 0.5 * ((U[0][inter] - T[inter]) ** 2).sum()
+    loss.backward()
+    # direct calls
+    U = pot0.clone()
+    U[:5].zero_()
+    s.fill_ghosts(U)
+    Pd = P0.clone()
+    s.prim2con(U, Pd)
+    U0 = U.clone()
+    ckpt = [s.zeros_state() for _ in range(2)]
+    s.rk4_steps_checkpointed(U, Pd, w.dt, ckpt)
+    lam = torch.zeros_like(U)
+    lam[(0,) + inter] = U[(0,) + inter] - T[inter]
+    s.rk4_adjoint_steps(ckpt, Pd, lam, w.dt)
+    lamP = s.zeros_prims()
+    s.prim2con_adjoint(U0, P0, lam, lamP)
+    for a, r in ((Pr.grad, lamP), (pot.grad, lam)):
+        a, r = case.host(a), case.host(r)
+        for v in range(r.shape[0]):
+            scale = np.abs(r[v]).max()
+            assert np.abs(a[v] - r[v]).max() <= 1e-12 * max(scale, 1e-300), v
