@@ -145,7 +145,7 @@ def read_face_flops():
 
 
 def read_traffic():
-    path = os.path.join(ROOT, "profiles", "k_faces_config2_128_ncu.txt")
+    path = os.path.join(ROOT, "profiles", "faces_config2_128_traffic.txt")
     if not os.path.exists(path):
         return None
     with open(path) as f:
@@ -456,7 +456,7 @@ def run_ours(args):
     faces_per_launch = (args.n + 1) * (args.n + 6) ** 2
     flops_per_face = read_face_flops()
     face_avg_ms = face_ms / max(nface, 1)
-    roofline = {"bound": "alu", "kernel": "k_faces (face solve: prim->cons, fluxes, quartic speeds, HLLE)",
+    roofline = {"bound": "alu", "kernel": "k_single<Faces<D>> (face solve: prim->cons, fluxes, quartic speeds, HLLE)",
                 "unit": "TFLOP/s", "peak": FP64_NOMINAL_TFLOPS,
                 "peak_kind": "nominal FP64 (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)",
                 "peak_measured_dfma": dfma_tflops, "launch_ms": face_avg_ms, "launches": nface,

@@ -31,7 +31,7 @@ def main():
     mean = sum(r[2] for r in rows) / 3.0
     out = os.path.join(ROOT, "profiles", "face_flops_config2_128.txt")
     with open(out, "w") as f:
-        f.write("# Algorithmic FP64 flops per face of the face solve (k_faces), counted with the oracle's\n")
+        f.write("# Algorithmic FP64 flops per face of the face solve (k_single<Faces<D>>), counted with the oracle's\n")
         f.write("# flop-counting scalar on the central 128x16x16 slab of the 128^3 WENO-Z Schwarzschild workload\n")
         f.write("# (every 3rd face of each direction).  + - * / sqrt count one flop each; metric interpolation\n")
         f.write("# is excluded (frozen metric, precomputed once).  Command: python oracle/count_face_flops.py\n")

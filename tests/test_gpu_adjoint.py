@@ -338,8 +338,9 @@ def test_autograd_functions_match_the_direct_calls():
     s.rk4_adjoint_steps(ckpt, Pd, lam, w.dt)
     lamP = s.zeros_prims()
     s.prim2con_adjoint(U0, P0, lam, lamP)
+    # per tensor scale: the Psi gradient is zero up to rounding (see the loss-gradient test)
     for a, r in ((Pr.grad, lamP), (pot.grad, lam)):
         a, r = case.host(a), case.host(r)
+        scale = np.abs(r).max()
         for v in range(r.shape[0]):
-            scale = np.abs(r[v]).max()
-            assert np.abs(a[v] - r[v]).max() <= 1e-12 * max(scale, 1e-300), v
+            assert np.abs(a[v] - r[v]).max() <= 1e-12 * scale, v
