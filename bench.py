@@ -52,9 +52,10 @@ def parse():
     ap.add_argument("--batch-blocks", type=int, default=512)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward measurement")
     ap.add_argument("--adjoint-n", type=int, default=64, help="cells per axis of the adjoint workload")
-    ap.add_argument("--profile-region", choices=("none", "forward", "adjoint"), default="none",
-                    help="bracket one extra forward RK4 step (main workload) or one adjoint step with "
-                         "cudaProfilerStart/Stop, for a profiler run with --profile-from-start off")
+    ap.add_argument("--profile-region", choices=("none", "forward", "adjoint", "batched"), default="none",
+                    help="bracket one extra forward RK4 step (main workload), one adjoint step, or one batched "
+                         "step and one step of the equal-volume block with cudaProfilerStart/Stop, for a "
+                         "profiler run with --profile-from-start off")
     return ap.parse_args()
 
 
@@ -230,6 +231,11 @@ def run_batched(args, dev, stream):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms_b = e0.elapsed_time(e1) / steps
+    if args.profile_region == "batched":
+        torch.cuda.profiler.start()
+        batch.step(dt, nsteps=1)
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.stop()
     pool_bytes = batch.ws_bytes
     del batch, entries
     torch.cuda.empty_cache()
@@ -250,6 +256,11 @@ def run_batched(args, dev, stream):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms_s = e0.elapsed_time(e1) / steps
+    if args.profile_region == "batched":
+        torch.cuda.profiler.start()
+        s.rk4_step(U, P, w.dt)
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.stop()
     single_cells = w.interior_cells
     del s, M, U, P
     torch.cuda.empty_cache()
