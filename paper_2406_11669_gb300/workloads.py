@@ -327,6 +327,79 @@ def smooth_general(n=(12, 10, 11), seed=106, recon=RECON_PPM, bc=BC_PERIODIC, ga
                     A, psi, metric)
 
 
+def loop_advection(n=24, seed=0) -> Workload:
+    """Magnetic loop advection (Sec. 4, loop-advection test): periodic [-1/2, 1/2]^2 (one cell in z), rho = 1,
+    p = 3, v = (1/12, 1/24, 1/24), A_z = max(0, A_loop (R_loop - r)) with A_loop = 1e-3, R_loop = 0.3, Gamma = 5/3,
+    minmod, dt = dx/4.  (The seed is unused: the set-up is deterministic.)"""
+    g = 3
+    nn = (n, n, 1)
+    dx = (1.0 / n, 1.0 / n, 1.0 / n)
+    x0 = (-0.5, -0.5, 0.0)
+    N = [m + 2 * g for m in nn]
+    shape = (N[2] + 1, N[1] + 1, N[0] + 1)
+    rho = _full(shape, 1.0)
+    press = _full(shape, 3.0)
+    v = [_full(shape, 1.0 / 12.0), _full(shape, 1.0 / 24.0), _full(shape, 1.0 / 24.0)]
+    X, Y, _ = positions(nn, g, x0, dx, ZEDGE)
+    r = np.sqrt(X ** 2 + Y ** 2)
+    Az = np.broadcast_to(np.maximum(0.0, 1e-3 * (0.3 - r)), shape).copy()
+    A = dict(Ax=_full(shape, 0.0), Ay=_full(shape, 0.0), Az=Az)
+    params = default_params(gamma=5.0 / 3.0, gamma_atm=5.0 / 3.0, rho_atm=1e-7, K_atm=1.0, recon=RECON_MINMOD)
+    prims = dict(rho=rho, press=press, velx=v[0], vely=v[1], velz=v[2])
+    return Workload("loop_advection_2d", nn, g, x0, dx, (BC_PERIODIC,) * 3, params, 0.25 * dx[0], prims, A,
+                    _full(shape, 0.0), flat_metric(shape))
+
+
+def smooth_periodic_1d(n, seed=110, recon=RECON_PPM) -> Workload:
+    """Smooth periodic data on [0,1] along x (one cell in y and z, every field a function of x only), shaped like
+    the adjoint workload: rho = 1 + 0.05 * 3 modes, p = 1 + 0.05 * 2 modes, all three velocity components from
+    4 modes (|v| <= 0.2), transverse B ~ 0.2 from A_y(x), A_z(x), lapse 1 - 0.01 sin 2 pi x; Gamma = 4/3,
+    dt = dx/4.  The modes do not depend on n, so blocks of several n sample the same continuum data (a
+    self-convergence study)."""
+    g = 3
+    nn = (n, 1, 1)
+    dx = (1.0 / n, 1.0 / n, 1.0 / n)
+    x0 = (0.0, 0.0, 0.0)
+    N = [m + 2 * g for m in nn]
+    shape = (N[2] + 1, N[1] + 1, N[0] + 1)
+    rng = Rng(seed)
+
+    def modes(count):
+        out = []
+        for _ in range(count):
+            k = float(rng.choice(np.arange(1, 3), 1)[0])
+            a = rng.uniform(3, -1.0, 1.0)
+            phi = float(rng.uniform(1, 0.0, 2.0 * math.pi)[0])
+            out.append((k, a, phi))
+        return out
+
+    def field(md, X, amp, comp=0, fn=np.sin):
+        acc = np.zeros(shape)
+        for k, a, phi in md:
+            acc = acc + amp * a[comp] * fn(2.0 * math.pi * k * X + phi)
+        return np.broadcast_to(acc, shape).copy()
+
+    Xc, _, _ = positions(nn, g, x0, dx, CELL)
+    rho = 1.0 + field(modes(3), Xc, 0.05)
+    press = 1.0 + field(modes(2), Xc, 0.05)
+    vm = modes(4)
+    v = [field(vm, Xc, 1.0, d) for d in range(3)]
+    vmag = max(np.sqrt(v[0] ** 2 + v[1] ** 2 + v[2] ** 2).max(), 1e-300)
+    v = [c * (0.2 / vmag) for c in v]
+    am = modes(4)
+    Xy, _, _ = positions(nn, g, x0, dx, YEDGE)
+    Xz, _, _ = positions(nn, g, x0, dx, ZEDGE)
+    A = dict(Ax=_full(shape, 0.0), Ay=field(am, Xy, 0.2 / (2.0 * math.pi), 1, np.cos),
+             Az=field(am, Xz, 0.2 / (2.0 * math.pi), 2, np.cos))
+    metric = flat_metric(shape)
+    Xv, _, _ = positions(nn, g, x0, dx, VERTEX)
+    metric["alp"] = np.broadcast_to(1.0 - 0.01 * np.sin(2.0 * math.pi * Xv), shape).copy()
+    params = default_params(gamma=4.0 / 3.0, gamma_atm=4.0 / 3.0, rho_atm=1e-7, K_atm=1.0, recon=recon)
+    prims = dict(rho=rho, press=press, velx=v[0], vely=v[1], velz=v[2])
+    return Workload(f"smooth_periodic_1d_{n}", nn, g, x0, dx, (BC_PERIODIC,) * 3, params, 0.25 * dx[0], prims, A,
+                    _full(shape, 0.0), metric)
+
+
 def config2(n=(128, 128, 128), seed=102) -> Workload:
     """128^3 on [-1/2,1/2]^3, copy BCs, Gamma = 5/3, WENO-Z.  Table 1 test-1 states split at x = 0:
     left rho=1, p=1, right rho=0.125, p=0.1, v=0; densitised field B~x = 0.5, B~y = +1 (left) / -1 (right)

@@ -237,3 +237,36 @@ def test_balsara1_robustness_smoke():
     U1, st = O.rk4_step(w, M, U, P)
     assert st["n_failed"] == 0 and st["n_atm"] == 0
     assert np.all(np.isfinite(U1[:, w.g:w.g + 6, w.g:w.g + 6, w.g:w.g + 24]))
+
+
+def test_loop_advection_moves_with_the_flow():
+    """Magnetic loop advection (Sec. 4) on a coarse 16^2 grid for t = 0.75: the loop's magnetic energy
+    centroid moves by v t = (1, 1/2) cells (periodic centroid), and minmod keeps most of its energy.  An
+    induction update of the wrong sign would carry the loop the other way."""
+    n, T = 16, 0.75
+    w = W.loop_advection(n)
+    M = O.metric_array(w)
+    U, P = O.initial_state(w)
+    O.ghost_fill_state(w, U)
+    g = w.g
+
+    def energy(U):
+        Bf = O.face_B(w, U)
+        bx = 0.5 * (Bf[0][g, g:g + n, g:g + n] + Bf[0][g, g:g + n, g + 1:g + n + 1])
+        by = 0.5 * (Bf[1][g, g:g + n, g:g + n] + Bf[1][g, g + 1:g + n + 1, g:g + n])
+        return bx ** 2 + by ** 2
+
+    def centroid(e):
+        ys, xs = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+        cx = np.angle((e * np.exp(2j * np.pi * (xs + 0.5) / n)).sum()) / (2 * np.pi) * n
+        cy = np.angle((e * np.exp(2j * np.pi * (ys + 0.5) / n)).sum()) / (2 * np.pi) * n
+        return np.array([cx, cy])
+
+    e0 = energy(U)
+    for _ in range(int(round(T / w.dt))):
+        U, _ = O.rk4_step(w, M, U, P)
+    e1 = energy(U)
+    shift = centroid(e1) - centroid(e0)
+    shift = (shift + n / 2) % n - n / 2
+    assert np.allclose(shift, [T / 12 * n, T / 24 * n], atol=0.1), shift
+    assert 0.6 < e1.sum() / e0.sum() <= 1.0
