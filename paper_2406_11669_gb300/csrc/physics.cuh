@@ -429,9 +429,30 @@ __host__ __device__ __forceinline__ void ppm_limit(T ai, T& l, T& r) {
   }
 }
 
+// PPM values on both sides of the interface between positions 2 and 3 of f[0..5] (the upper value of cell 2 and
+// the lower value of cell 3, each as recon5<1> gives it): the slopes of cells 1..4 and the interface value
+// between cells 2 and 3 are formed once for the two cells.
+template <class T>
+__host__ __device__ __forceinline__ void ppm_pair(const T f[6], T& L, T& R) {
+  const T d1 = ppm_dq(f[0], f[1], f[2]);
+  const T d2 = ppm_dq(f[1], f[2], f[3]);
+  const T d3 = ppm_dq(f[2], f[3], f[4]);
+  const T d4 = ppm_dq(f[3], f[4], f[5]);
+  T l2 = f[1] + 0.5 * (f[2] - f[1]) - (d2 - d1) * (1.0 / 6.0);
+  T r2 = f[2] + 0.5 * (f[3] - f[2]) - (d3 - d2) * (1.0 / 6.0);
+  T r3 = f[3] + 0.5 * (f[4] - f[3]) - (d4 - d3) * (1.0 / 6.0);
+  T l3 = r2;
+  ppm_limit(f[2], l2, r2);
+  ppm_limit(f[3], l3, r3);
+  L = r2;
+  R = l3;
+}
+
 // WENO-Z values at both faces of the middle cell of s[0..4].  The lower face uses the mirrored stencil, whose
-// smoothness indicators are those of the upper face in reverse order, so the three indicators and the three
-// ratios tau5 / (beta_k + eps) are shared; the three reciprocals come from one division.
+// smoothness indicators are those of the upper face in reverse order, so the indicators are shared.  With
+// e_k = beta_k + eps and p = 2 the nonlinear weights alpha_k = d_k (1 + (tau5 / e_k)^2) are proportional to
+// d_k (e_k^2 + tau5^2) prod_{j != k} e_j^2, which needs no division before the normalisation (e_k >= eps keeps the
+// products above the smallest normal double; out-of-range products take the form with the quotients).
 template <class T>
 __host__ __device__ __forceinline__ void wenoz_both(const T s[5], T& lo, T& hi) {
   const T t0a = s[0] - 2.0 * s[1] + s[2], t0b = s[0] - 4.0 * s[1] + 3.0 * s[2];
@@ -441,25 +462,21 @@ __host__ __device__ __forceinline__ void wenoz_both(const T s[5], T& lo, T& hi) 
   const T e1 = (13.0 / 12.0) * t1a * t1a + 0.25 * t1b * t1b + 1e-40;
   const T e2 = (13.0 / 12.0) * t2a * t2a + 0.25 * t2b * t2b + 1e-40;
   const T tau5 = fabs(e0 - e2);
-  const T e01 = e0 * e1;
-  const T inv = 1.0 / (e01 * e2);
-  T r0, r1, r2;
-  if (isfinite(val(inv)) && val(inv) > 0.0) {
-    r0 = tau5 * (inv * (e1 * e2));
-    r1 = tau5 * (inv * (e0 * e2));
-    r2 = tau5 * (inv * e01);
-  } else {  // product out of range: three divisions
-    r0 = tau5 / e0;
-    r1 = tau5 / e1;
-    r2 = tau5 / e2;
+  const T tt = tau5 * tau5;
+  const T E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
+  T a0 = (E0 + tt) * (E1 * E2), a1 = (E1 + tt) * (E0 * E2), a2 = (E2 + tt) * (E0 * E1);
+  if (!(isfinite(val(a0 + a1 + a2)) && val(a0 + a1 + a2) > 0.0)) {  // products out of range
+    const T r0 = tau5 / e0, r1 = tau5 / e1, r2 = tau5 / e2;
+    a0 = 1.0 + r0 * r0;
+    a1 = 1.0 + r1 * r1;
+    a2 = 1.0 + r2 * r2;
   }
-  const T z0 = 1.0 + r0 * r0, z1 = 1.0 + r1 * r1, z2 = 1.0 + r2 * r2;
   // upper face: linear weights (1/10, 6/10, 3/10) on the sub-stencils ending at, centred on, starting at i
   {
     const T q0 = (2.0 * s[0] - 7.0 * s[1] + 11.0 * s[2]) * (1.0 / 6.0);
     const T q1 = (-s[1] + 5.0 * s[2] + 2.0 * s[3]) * (1.0 / 6.0);
     const T q2 = (2.0 * s[2] + 5.0 * s[3] - s[4]) * (1.0 / 6.0);
-    const T w0 = 0.1 * z0, w1 = 0.6 * z1, w2 = 0.3 * z2;
+    const T w0 = 0.1 * a0, w1 = 0.6 * a1, w2 = 0.3 * a2;
     hi = (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
   }
   // lower face: mirrored stencil, indicator k of the mirror is indicator 2-k here
@@ -467,7 +484,7 @@ __host__ __device__ __forceinline__ void wenoz_both(const T s[5], T& lo, T& hi) 
     const T q0 = (2.0 * s[4] - 7.0 * s[3] + 11.0 * s[2]) * (1.0 / 6.0);
     const T q1 = (-s[3] + 5.0 * s[2] + 2.0 * s[1]) * (1.0 / 6.0);
     const T q2 = (2.0 * s[2] + 5.0 * s[1] - s[0]) * (1.0 / 6.0);
-    const T w0 = 0.1 * z2, w1 = 0.6 * z1, w2 = 0.3 * z0;
+    const T w0 = 0.1 * a2, w1 = 0.6 * a1, w2 = 0.3 * a0;
     lo = (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
   }
 }

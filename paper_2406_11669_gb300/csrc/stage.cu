@@ -561,14 +561,8 @@ struct Vertex {
   }
 };
 
-// PPM value at the interface between stencil positions 2 and 3 of f[0..5]
-__device__ __forceinline__ void ppm_interface(const double f[6], double& L, double& R) {
-  double l, h;
-  recon5<1>(f, l, h);
-  L = h;
-  recon5<1>(f + 1, l, h);
-  R = l;
-}
+// PPM values on both sides of the interface between stencil positions 2 and 3 of f[0..5]
+__device__ __forceinline__ void ppm_interface(const double f[6], double& L, double& R) { ppm_pair(f, L, R); }
 
 // Edges along E (owned range): UCT electric field (Sec. 3.4, Eqs. uct1, uct2, eq3.20) with (E, d1, d2) cyclic,
 //   E_E = -HLL_d1(v~^d1 B~^d2) + HLL_d2(v~^d2 B~^d1),
