@@ -107,6 +107,7 @@ Ws make_ws(const asterx_block* in, void* base) {
   w.uacc = take(9);
   w.ustage = take(18);
   w.counters = reinterpret_cast<unsigned long long*>(p);
+  w.roots = nullptr;
   return w;
 }
 
@@ -467,17 +468,18 @@ asterx_status asterx_batched_step(const asterx_params* p, const asterx_batch_blo
 // ----------------------------------------------------------------------------------------------------------
 // Adjoint.  Adjoint workspace: RK4 stage states Y0..Y3 (36 fields), forward accumulator (9), running adjoint
 // lambda (9), stage adjoint kbar (9), sum (9), the right-hand-side adjoint accumulators (ADJ_ACC_FIELDS),
-// reconstructed-value adjoints (2 NREC), the reconstructed values of the three directions (6 NREC), a state
-// copy (9), recovery flags.
+// reconstructed-value adjoints (2 NREC), the reconstructed values of the three directions (6 NREC), the face
+// solves' roots of the three directions (12), a state copy (9), recovery flags.
 
 namespace {
-constexpr int ADJ_FIELDS = 36 + 9 + 9 + 9 + 9 + ADJ_ACC_FIELDS + 2 * NREC + 6 * NREC + 9;
+constexpr int ADJ_FIELDS = 36 + 9 + 9 + 9 + 9 + ADJ_ACC_FIELDS + 2 * NREC + 6 * NREC + 12 + 9;
 
 struct AdjLayout {
   F9 Ys[4], acc, lam, kbar, sum, ycopy;
   double* accum;
   double* lrec;
   double* rec3[3];
+  double* roots;
   signed char* flags;
 };
 
@@ -511,6 +513,8 @@ AdjLayout make_adj(const asterx_block* in, void* base) {
     L.rec3[d] = p;
     p += 2L * NREC * fs;
   }
+  L.roots = p;
+  p += 12L * fs;
   L.ycopy = take9();
   L.flags = reinterpret_cast<signed char*>(p);
   return L;
@@ -522,6 +526,7 @@ AdjWs adj_ws(const AdjLayout& L, const Blk& b, const F9& Y, const F5& P, const F
   a.P = P;
   a.mu = mu;
   for (int d = 0; d < 3; d++) a.rec3[d] = L.rec3[d];
+  a.roots = L.roots;
   a.flags = L.flags;
   double* q = L.accum;
   a.lY_base = q;

@@ -6,10 +6,12 @@
 //   cells (flux divergence, sources) -> scalar potential -> edges (UCT, grad G_A) -> vertex potentials ->
 //   face solves and reconstruction (per direction) -> u = W v -> primitive ghost fill -> recovery ->
 //   centre field -> curl -> state ghost fill.
-// Linear maps are transposed by hand.  Nonlinear pointwise maps take their local Jacobian from the same
-// templated device code as the forward path run with forward-mode dual numbers; the wave speeds and the
-// recovery are differentiated by the implicit-function theorem at the converged root (one Newton step in dual
-// arithmetic from the root for the speeds; the prim->cons Jacobian inverted at the root for the recovery).
+// Linear maps are transposed by hand.  The heavy nonlinear maps are reversed by hand (reverse mode): the face
+// solve (face_side_vjp, the wave speeds by the implicit-function theorem at the converged roots), the source
+// terms (sources_vjp), minmod and PPM (recon5_vjp).  The others take their local Jacobian from the same
+// templated device code as the forward path run with forward-mode dual numbers: u = W v, WENO-Z, and
+// prim->cons, whose Jacobian inverted at the recovered primitives differentiates the recovery (implicit-function
+// theorem).
 // Limiters, max/min and branch choices take the derivative of the branch taken.  Atmosphere cells (constant
 // primitives) pass no derivative through the recovery.
 //
@@ -154,8 +156,8 @@ __global__ void ka_grad_ga(Blk b, AdjWs a, F9 mu) {
   }
 }
 
-// UCT: E_E = -HLL_d1(v~^d1 B~^d2) + HLL_d2(v~^d2 B~^d1); lambda_E = -mu_A.  Each term's local Jacobian: PPM
-// interfaces by dual numbers (6 inputs), the HLL formula by hand, a_+- = max over the two faces (branch taken).
+// UCT: E_E = -HLL_d1(v~^d1 B~^d2) + HLL_d2(v~^d2 B~^d1); lambda_E = -mu_A.  Each term reversed by hand: the HLL
+// formula, the PPM interface values (reverse-mode recon5), a_+- = max over the two faces (branch taken).
 template <int E>
 __global__ void ka_edges(Blk b, Ws w, AdjWs a, F9 mu) {
   constexpr int D1 = (E + 1) % 3, D2 = (E + 2) % 3;
@@ -177,22 +179,16 @@ __global__ void ka_edges(Blk b, Ws w, AdjWs a, F9 mu) {
       const int slot = (((df + 1) % 3) == dr) ? FD_VB1 : FD_VB2;
       const long vb_off = ((long)df * NFD + slot) * b.V;
       const long bn_off = (long)df * b.V;
-      typedef Dual<6> D6;
-      D6 vs[6], bs[6];
+      double vs[6], bs[6];
       for (int s = 0; s < 6; s++) {
         const long q = c + (s - 3) * sr;
-        vs[s] = D6::seed(w.face[vb_off + q], s);
-        bs[s] = D6::seed(w.bf[bn_off + q], s);
+        vs[s] = w.face[vb_off + q];
+        bs[s] = w.bf[bn_off + q];
       }
-      D6 l, h, vL, vR, BL, BR;
-      recon5<1>(vs, l, h);
-      vL = h;
-      recon5<1>(vs + 1, l, h);
-      vR = l;
-      recon5<1>(bs, l, h);
-      BL = h;
-      recon5<1>(bs + 1, l, h);
-      BR = l;
+      PpmPair pv, pb;
+      pv.values(vs);
+      pb.values(bs);
+      const double vL = pv.L, vR = pv.R, BL = pb.L, BR = pb.R;
       const long fdr = (long)dr * NFD * b.V;
       const long c0 = c - sf;
       const double apa = w.face[fdr + FD_CMAX * b.V + c0], apb = w.face[fdr + FD_CMAX * b.V + c];
@@ -202,25 +198,27 @@ __global__ void ka_edges(Blk b, Ws w, AdjWs a, F9 mu) {
       const double lt = sgn * lE;  // adjoint of this term
       double gvL, gvR, gBL, gBR, gap = 0.0, gam = 0.0;
       if (den > 0.0) {
-        const double term = (ap * vL.v * BL.v + am * vR.v * BR.v - ap * am * (BR.v - BL.v)) / den;
-        gvL = ap * BL.v / den;
-        gBL = (ap * vL.v + ap * am) / den;
-        gvR = am * BR.v / den;
-        gBR = (am * vR.v - ap * am) / den;
-        gap = (vL.v * BL.v - am * (BR.v - BL.v) - term) / den;
-        gam = (vR.v * BR.v - ap * (BR.v - BL.v) - term) / den;
+        const double term = (ap * vL * BL + am * vR * BR - ap * am * (BR - BL)) / den;
+        gvL = ap * BL / den;
+        gBL = (ap * vL + ap * am) / den;
+        gvR = am * BR / den;
+        gBR = (am * vR - ap * am) / den;
+        gap = (vL * BL - am * (BR - BL) - term) / den;
+        gam = (vR * BR - ap * (BR - BL) - term) / den;
       } else {
-        gvL = 0.5 * BL.v;
-        gBL = 0.5 * vL.v;
-        gvR = 0.5 * BR.v;
-        gBR = 0.5 * vR.v;
+        gvL = 0.5 * BL;
+        gBL = 0.5 * vL;
+        gvR = 0.5 * BR;
+        gBR = 0.5 * vR;
       }
+      // the PPM interface values by reverse mode: the upper value of stencil cell 2, the lower of cell 3
+      double gv[6], gb[6];
+      pv.vjp(gvL * lt, gvR * lt, gv);
+      pb.vjp(gBL * lt, gBR * lt, gb);
       for (int s = 0; s < 6; s++) {
         const long q = c + (s - 3) * sr;
-        const double dv = (gvL * vL.d[s] + gvR * vR.d[s]) * lt;
-        const double db = (gBL * BL.d[s] + gBR * BR.d[s]) * lt;
-        if (dv != 0.0) atomicAdd(&a.lface[vb_off + q], dv);
-        if (db != 0.0) atomicAdd(&a.lBf[bn_off + q], db);
+        if (gv[s] != 0.0) atomicAdd(&a.lface[vb_off + q], gv[s]);
+        if (gb[s] != 0.0) atomicAdd(&a.lBf[bn_off + q], gb[s]);
       }
       if (gap != 0.0) atomicAdd(&a.lface[fdr + FD_CMAX * b.V + (apb > apa ? c : c0)], gap * lt);
       if (gam != 0.0) atomicAdd(&a.lface[fdr + FD_CMIN * b.V + (amb > ama ? c : c0)], gam * lt);
@@ -321,7 +319,9 @@ __global__ void ka_faces(Blk b, Ws w, AdjWs a, double gamma, double gfac) {
       B[side][D] = w.bf[D * b.V + c] * isqg;
       B[side][T1] = rr[5 * b.V];
       B[side][T2] = rr[6 * b.V];
-      face_side(m, ia, width, D, rho[side], press[side], u[side], B[side], gamma, gfac, s[side]);
+      // the roots the recompute's face solve found (no Newton iteration here)
+      const double rt[2] = {a.roots[((long)D * 4 + 2 * side) * b.V + c], a.roots[((long)D * 4 + 2 * side + 1) * b.V + c]};
+      face_side(m, ia, width, D, rho[side], press[side], u[side], B[side], gamma, gfac, s[side], rt);
     }
     const double* lf = a.lface + (long)D * NFD * b.V + c;
     double lF[5], lvb[2];
@@ -414,15 +414,21 @@ __global__ void ka_recon(Blk b, Ws w, AdjWs a) {
     for (int v = 0; v < NREC; v++) {
       const double glo = a.lrec[v * b.V + c], ghi = a.lrec[(NREC + v) * b.V + c];
       if (glo == 0.0 && ghi == 0.0) continue;
-      typedef Dual<5> D5;
-      D5 s5[5];
-      for (int s = 0; s < 5; s++) s5[s] = D5::seed(src[v][c + (s - 2) * st], s);
-      D5 l, h;
-      recon5<SCHEME>(s5, l, h);
-      for (int s = 0; s < 5; s++) {
-        const double g = l.d[s] * glo + h.d[s] * ghi;
-        if (g != 0.0) atomicAdd(&dst[v][c + (s - 2) * st], g);
+      double g[5];
+      if constexpr (SCHEME < 2) {  // minmod, PPM: reverse mode
+        double a5[5];
+        for (int s = 0; s < 5; s++) a5[s] = src[v][c + (s - 2) * st];
+        recon5_vjp<SCHEME>(a5, glo, ghi, g);
+      } else {  // WENO-Z: dual numbers through the forward code
+        typedef Dual<5> D5;
+        D5 s5[5];
+        for (int s = 0; s < 5; s++) s5[s] = D5::seed(src[v][c + (s - 2) * st], s);
+        D5 l, h;
+        recon5<SCHEME>(s5, l, h);
+        for (int s = 0; s < 5; s++) g[s] = l.d[s] * glo + h.d[s] * ghi;
       }
+      for (int s = 0; s < 5; s++)
+        if (g[s] != 0.0) atomicAdd(&dst[v][c + (s - 2) * st], g[s]);
     }
   }
 }
@@ -522,7 +528,7 @@ __global__ void ka_c2p(Blk b, Ws w, AdjWs a, double gamma, double gfac) {
     const D8 W = 1.0 / sqrt(1.0 - contract_sym(m.g, v, v));
     const D8 u[3] = {W * v[0], W * v[1], W * v[2]};
     SideOutT<D8> o;
-    face_side(m, 1.0 / m.alp, m.alp * sqrt(m.gu[0]), 0, rho, press, u, B, gamma, gfac, o);
+    face_side<D8, false>(m, 1.0 / m.alp, m.alp * sqrt(m.gu[0]), 0, rho, press, u, B, gamma, gfac, o);
     // solve Jp^T x = lambda_P (5x5, partial pivoting); Jp[row q][col r] = dU_q / dP_r
     double M[5][6];
     for (int r = 0; r < 5; r++) {
@@ -696,7 +702,7 @@ __global__ void ka_prim2con(Blk b, Ws w, AdjWs a, F9 lamU, F5 lamP, double gamma
     const D8 W = 1.0 / sqrt(1.0 - contract_sym(m.g, v, v));
     const D8 u[3] = {W * v[0], W * v[1], W * v[2]};
     SideOutT<D8> o;
-    face_side(m, 1.0 / m.alp, m.alp * sqrt(m.gu[0]), 0, rho, press, u, B, gamma, gfac, o);
+    face_side<D8, false>(m, 1.0 / m.alp, m.alp * sqrt(m.gu[0]), 0, rho, press, u, B, gamma, gfac, o);
     double g8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int q = 0; q < 5; q++) {
       const double l = lamU.f[q][c];
@@ -772,7 +778,7 @@ cudaError_t launch_rhs_adjoint(const StageArgs& sa, const AdjWs& a, double dt, c
   if (e == cudaSuccess) e = launch_bfield(b, sa.w, a.Y, s);
   if (e == cudaSuccess) e = launch_c2p(sa, a.Y, a.P, a.flags, nullptr, s);
   if (e == cudaSuccess) e = launch_ghost_prims(b, a.P, s);
-  if (e == cudaSuccess) e = launch_face_data(sa, a.P, a.rec3, s);
+  if (e == cudaSuccess) e = launch_face_data(sa, a.P, a.rec3, a.roots, s);
   if (e != cudaSuccess) return e;
   // adjoint accumulators
   cudaMemsetAsync(a.lY_base, 0, (size_t)ADJ_ACC_FIELDS * b.V * sizeof(double), s);

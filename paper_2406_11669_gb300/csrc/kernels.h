@@ -54,6 +54,7 @@ struct AdjWs {
   F5 P;            // primitives recovered from Y (caller's buffers; the entry values are the guess)
   F9 mu;           // adjoint of dU/dt (owned ranges read)
   double* rec3[3];  // reconstructed values of each direction (2 NREC fields each), kept from the recompute
+  double* roots;    // 12 fields: the face solves' roots (lambda_+, lambda_- of left and right) per direction
   signed char* flags;
   double* lY_base;  // start of the ADJ_ACC_FIELDS accumulators
   double* lY;       // 9: result, adjoint of Y
@@ -77,8 +78,8 @@ struct AdjGhost {
 // forward reconstruction of one direction into the workspace
 cudaError_t launch_recon_dir(const StageArgs& a, const F5& P, int D, cudaStream_t s);
 // u = W v, then per direction D the reconstruction into rec[D] (2 NREC fields) and the face solve (face data of
-// direction D in the workspace); no right-hand side is formed
-cudaError_t launch_face_data(const StageArgs& a, const F5& P, double* const rec[3], cudaStream_t s);
+// direction D in the workspace, its roots into `roots`, 12 fields); no right-hand side is formed
+cudaError_t launch_face_data(const StageArgs& a, const F5& P, double* const rec[3], double* roots, cudaStream_t s);
 // lambda = (dL/dY)^T mu at the state a.Y (recomputes the forward intermediates)
 cudaError_t launch_rhs_adjoint(const StageArgs& sa, const AdjWs& a, double dt, cudaStream_t s);
 // adjoint of the initial data U = (prim2con(P, B(A)), A, Psi) at the state a.Y (copy; ghost-filled here):

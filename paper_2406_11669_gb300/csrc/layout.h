@@ -56,6 +56,8 @@ struct Ws {
   double* face;    // 3 * NFD fields
   double* ga;      // 1 field: G_A at vertices
   double* fpsi;    // 3 fields: F_Psi^j at vertices
+  double* roots;   // null, or 12 fields: the face solves' (lambda_+, lambda_-) of the left and right states per
+                   // direction, written by the face solve for the adjoint's reverse sweep
   double* uacc;    // 9 fields: RK4 accumulator of asterx_rk4_step
   double* ustage;  // 2 * 9 fields: RK4 stage buffers of asterx_rk4_step
   unsigned long long* counters;  // 8 counters (internal statistics when the caller passes none)

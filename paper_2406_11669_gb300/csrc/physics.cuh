@@ -131,11 +131,13 @@ struct QuarticT {
   }
 };
 
-// gfac = Gamma / (Gamma - 1), ia = 1 / alpha, width = alpha sqrt(gamma^dd) (hoisted by the caller)
-template <class T>
+// gfac = Gamma / (Gamma - 1), ia = 1 / alpha, width = alpha sqrt(gamma^dd) (hoisted by the caller).  kSpeeds =
+// false skips the magnetosonic speeds (o.lm, o.lp unset: prim->cons and fluxes only); `roots`, when given, holds
+// the two speeds (lambda_+, lambda_-) already found for these inputs, and replaces the Newton iteration.
+template <class T, bool kSpeeds = true>
 __host__ __device__ __forceinline__ void face_side(const Geo& m, double ia, double width, int d, T rho, T press,
                                           const T u[3], const T B[3], double gamma, double gfac,
-                                          SideOutT<T>& o) {
+                                          SideOutT<T>& o, const double* roots = nullptr) {
   const T uu = contract_sym(m.g, u, u);
   const T W = sqrt(1.0 + uu);
   const T iW = 1.0 / W;
@@ -167,6 +169,7 @@ __host__ __device__ __forceinline__ void face_side(const Geo& m, double ia, doub
   o.F[1 + d] += asg * pt;
   o.F[4] = o.U[4] * vt + asg * (pt * v[d] - Bv * Bd);
 
+  if constexpr (!kSpeeds) return;
   // magnetosonic speeds
   const T u0 = W * ia;
   const T ud = W * (v[d] - m.beta[d] * ia);
@@ -187,23 +190,29 @@ __host__ __device__ __forceinline__ void face_side(const Geo& m, double ia, doub
   Q.betad = m.beta[d];
   Q.ia2 = ia * ia;
   Q.gdd = m.gu[sym(d, d)];
-  // Starting points: the lab-frame speeds of an isotropic wave with the perpendicular fast speed
-  // c^2 = cs^2 + cA^2 - cs^2 cA^2 (cA^2 = b^2 / (rho h + b^2)), which bounds the fast magnetosonic speed in
-  // every direction, so both starts lie outside the extreme roots and Newton converges monotonically from
-  // there (as from the light cone, but from much closer).  Clamped to the light cone.
-  const double c2 = Q.cs2 + val(ca2) - Q.cs2 * val(ca2);
-  const double v2 = 1.0 - val(iW2);
-  const double den = 1.0 - v2 * c2;
-  const double vd = val(v[d]);
-  const double disc = fmax((1.0 - v2) * (Q.gdd * den - vd * vd * (1.0 - c2)), 0.0);
-  const double spread = sqrt(c2 * disc);
-  const double idn = m.alp / den;
-  const double mid = vd * (1.0 - c2);
-  const double lc = -m.beta[d];
-  const double lp0 = fmin((mid + spread) * idn - m.beta[d] + 1e-12 * width, lc + width);
-  const double lm0 = fmax((mid - spread) * idn - m.beta[d] - 1e-12 * width, lc - width);
-  const double lp = Q.newton(lp0, width);
-  const double lm = Q.newton(lm0, width);
+  double lp, lm;
+  if (roots) {
+    lp = roots[0];
+    lm = roots[1];
+  } else {
+    // Starting points: the lab-frame speeds of an isotropic wave with the perpendicular fast speed
+    // c^2 = cs^2 + cA^2 - cs^2 cA^2 (cA^2 = b^2 / (rho h + b^2)), which bounds the fast magnetosonic speed in
+    // every direction, so both starts lie outside the extreme roots and Newton converges monotonically from
+    // there (as from the light cone, but from much closer).  Clamped to the light cone.
+    const double c2 = Q.cs2 + val(ca2) - Q.cs2 * val(ca2);
+    const double v2 = 1.0 - val(iW2);
+    const double den = 1.0 - v2 * c2;
+    const double vd = val(v[d]);
+    const double disc = fmax((1.0 - v2) * (Q.gdd * den - vd * vd * (1.0 - c2)), 0.0);
+    const double spread = sqrt(c2 * disc);
+    const double idn = m.alp / den;
+    const double mid = vd * (1.0 - c2);
+    const double lc = -m.beta[d];
+    const double lp0 = fmin((mid + spread) * idn - m.beta[d] + 1e-12 * width, lc + width);
+    const double lm0 = fmax((mid - spread) * idn - m.beta[d] - 1e-12 * width, lc - width);
+    lp = Q.newton(lp0, width);
+    lm = Q.newton(lm0, width);
+  }
   if constexpr (sizeof(T) == sizeof(double)) {
     o.lp = lp;
     o.lm = lm;
@@ -506,6 +515,122 @@ __host__ __device__ __forceinline__ void recon5(const T a[5], T& lo, T& hi) {
     hi = r;
   } else {
     wenoz_both(a, lo, hi);
+  }
+}
+
+// Reverse mode of recon5 for minmod and PPM: weights (glo, ghi) on the cell's (lower, upper) values give the
+// gradient g[0..4] with respect to a[0..4], along the branches the forward code takes (ties as there: minmod
+// keeps x when |x| = |y|, fmin keeps its first argument).
+__host__ __device__ __forceinline__ void ppm_dq_vjp(double am, double a0, double ap, double gd, double& gm,
+                                                    double& g0, double& gp) {
+  if (gd == 0.0 || (ap - a0) * (a0 - am) <= 0.0) return;
+  const double c = 0.5 * (ap - am);
+  const double x = 2.0 * fabs(a0 - am), y = 2.0 * fabs(ap - a0);
+  const bool inner_y = y < x;  // fmin(x, y) keeps x on ties
+  const double inner = inner_y ? y : x;
+  if (!(inner < fabs(c))) {  // |c| is the minimum: the slope is c
+    gp += 0.5 * gd;
+    gm -= 0.5 * gd;
+  } else if (inner_y) {  // 2 |ap - a0| with the sign of c, which is the sign of ap - a0 here
+    gp += 2.0 * gd;
+    g0 -= 2.0 * gd;
+  } else {  // 2 |a0 - am|
+    g0 += 2.0 * gd;
+    gm -= 2.0 * gd;
+  }
+}
+
+// Reverse of ppm_limit along the branch the forward takes: weights (glo, ghi) on the limited (l, r) give the
+// weight on the cell value ai (added) and on the raw interface values (gl, gr).
+__host__ __device__ __forceinline__ void ppm_limit_vjp(double ai, double l, double r, double glo, double ghi,
+                                                       double& gai, double& gl, double& gr) {
+  gl = gr = 0.0;
+  if ((r - ai) * (ai - l) <= 0.0) {
+    gai += glo + ghi;
+    return;
+  }
+  const double dlr = r - l;
+  const double mid = ai - 0.5 * (l + r);
+  const double d6 = dlr * dlr * (1.0 / 6.0);
+  if (dlr * mid > d6) {  // lo = 3 ai - 2 r
+    gai += 3.0 * glo;
+    gr = ghi - 2.0 * glo;
+  } else if (-d6 > dlr * mid) {  // hi = 3 ai - 2 l
+    gai += 3.0 * ghi;
+    gl = glo - 2.0 * ghi;
+  } else {
+    gl = glo;
+    gr = ghi;
+  }
+}
+
+// ppm_pair with its primal kept for the reverse sweep: values() as ppm_pair gives them, then vjp() turns the
+// weights on (L, R) into the gradient with respect to f[0..5], without recomputing the primal.
+struct PpmPair {
+  double f[6], d[4], am, ac, ap, L, R;
+  __host__ __device__ __forceinline__ void values(const double in[6]) {
+    for (int i = 0; i < 6; i++) f[i] = in[i];
+    for (int i = 0; i < 4; i++) d[i] = ppm_dq(f[i], f[i + 1], f[i + 2]);
+    am = f[1] + 0.5 * (f[2] - f[1]) - (d[1] - d[0]) * (1.0 / 6.0);
+    ac = f[2] + 0.5 * (f[3] - f[2]) - (d[2] - d[1]) * (1.0 / 6.0);
+    ap = f[3] + 0.5 * (f[4] - f[3]) - (d[3] - d[2]) * (1.0 / 6.0);
+    double l2 = am, r2 = ac, l3 = ac, r3 = ap;
+    ppm_limit(f[2], l2, r2);
+    ppm_limit(f[3], l3, r3);
+    L = r2;
+    R = l3;
+  }
+  __host__ __device__ __forceinline__ void vjp(double gL, double gR, double g[6]) const {
+    for (int i = 0; i < 6; i++) g[i] = 0.0;
+    double gl2, gr2, gl3, gr3;
+    ppm_limit_vjp(f[2], am, ac, 0.0, gL, g[2], gl2, gr2);
+    ppm_limit_vjp(f[3], ac, ap, gR, 0.0, g[3], gl3, gr3);
+    const double gam = gl2, gac = gr2 + gl3, gap = gr3;
+    double gd[4];
+    g[1] += 0.5 * gam;
+    g[2] += 0.5 * gam + 0.5 * gac;
+    g[3] += 0.5 * gac + 0.5 * gap;
+    g[4] += 0.5 * gap;
+    gd[0] = gam * (1.0 / 6.0);
+    gd[1] = (gac - gam) * (1.0 / 6.0);
+    gd[2] = (gap - gac) * (1.0 / 6.0);
+    gd[3] = -gap * (1.0 / 6.0);
+    for (int i = 0; i < 4; i++) ppm_dq_vjp(f[i], f[i + 1], f[i + 2], gd[i], g[i], g[i + 1], g[i + 2]);
+  }
+};
+
+template <int SCHEME>
+__host__ __device__ __forceinline__ void recon5_vjp(const double a[5], double glo, double ghi, double g[5]) {
+  for (int i = 0; i < 5; i++) g[i] = 0.0;
+  if (SCHEME == 0) {
+    const double x = a[2] - a[1], y = a[3] - a[2];
+    const double gs = 0.5 * (ghi - glo);
+    g[2] += glo + ghi;
+    if (x * y > 0.0) {
+      if (fabs(x) <= fabs(y)) {
+        g[2] += gs;
+        g[1] -= gs;
+      } else {
+        g[3] += gs;
+        g[2] -= gs;
+      }
+    }
+  } else {
+    const double dm = ppm_dq(a[0], a[1], a[2]);
+    const double d0 = ppm_dq(a[1], a[2], a[3]);
+    const double dp = ppm_dq(a[2], a[3], a[4]);
+    const double l = a[1] + 0.5 * (a[2] - a[1]) - (d0 - dm) * (1.0 / 6.0);
+    const double r = a[2] + 0.5 * (a[3] - a[2]) - (dp - d0) * (1.0 / 6.0);
+    double gl, gr;
+    ppm_limit_vjp(a[2], l, r, glo, ghi, g[2], gl, gr);
+    // l = (a1 + a2) / 2 - (d0 - dm) / 6, r = (a2 + a3) / 2 - (dp - d0) / 6
+    g[1] += 0.5 * gl;
+    g[2] += 0.5 * gl + 0.5 * gr;
+    g[3] += 0.5 * gr;
+    const double gdm = gl * (1.0 / 6.0), gd0 = (gr - gl) * (1.0 / 6.0), gdp = -gr * (1.0 / 6.0);
+    ppm_dq_vjp(a[0], a[1], a[2], gdm, g[0], g[1], g[2]);
+    ppm_dq_vjp(a[1], a[2], a[3], gd0, g[1], g[2], g[3]);
+    ppm_dq_vjp(a[2], a[3], a[4], gdp, g[2], g[3], g[4]);
   }
 }
 

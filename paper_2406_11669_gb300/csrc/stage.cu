@@ -254,7 +254,8 @@ struct Prim2Con {
     const double u[3] = {W * v[0], W * v[1], W * v[2]};
     const double B[3] = {r.w.bc[c], r.w.bc[b.V + c], r.w.bc[2 * b.V + c]};
     SideOut o;
-    face_side(m, 1.0 / m.alp, m.alp * sqrt(m.gu[0]), 0, r.P.f[0][c], r.P.f[1][c], u, B, k.gamma, k.gfac, o);
+    face_side<double, false>(m, 1.0 / m.alp, m.alp * sqrt(m.gu[0]), 0, r.P.f[0][c], r.P.f[1][c], u, B, k.gamma,
+                             k.gfac, o);
     for (int a = 0; a < 5; a++) r.Us.f[a][c] = o.U[a];
   }
 };
@@ -509,6 +510,13 @@ struct Faces {
     }
     fd[FD_CMAX * b.V + c] = cmax;
     fd[FD_CMIN * b.V + c] = cmin;
+    if (r.w.roots) {  // kept for the adjoint
+      double* rt = r.w.roots + (long)D * 4 * b.V + c;
+      rt[0] = s[0].lp;
+      rt[b.V] = s[0].lm;
+      rt[2 * b.V] = s[1].lp;
+      rt[3 * b.V] = s[1].lm;
+    }
   }
 };
 
@@ -892,9 +900,10 @@ cudaError_t launch_recon_dir(const StageArgs& a, const F5& P, int D, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t launch_face_data(const StageArgs& a, const F5& P, double* const rec[3], cudaStream_t s) {
+cudaError_t launch_face_data(const StageArgs& a, const F5& P, double* const rec[3], double* roots, cudaStream_t s) {
   Single t = single_of(a.b, a.w);
   t.r.P = P;
+  t.r.w.roots = roots;
   const StageConsts k = consts_of(a, -1, 0.0, nullptr);
   launch<UVel>(t, k, KIND_CELLS_ALL, s);
   Single td[3] = {t, t, t};
