@@ -1,7 +1,7 @@
 """Pins of the oracle's primitive recovery (Sec. 3.5) against the prim->cons map it must invert.
 
 prim -> cons (Eq. cons) is a closed form; recovery must return the primitives it started from.  States cover
-the ranges of the survey's plan: rho in [1e-10, 1], p/rho in [1e-4, 10], W in [1, 10], b^2/rho in [0, 100],
+ranges from dilute to strongly magnetised, relativistic states: rho in [1e-10, 1], p/rho in [1e-4, 10], W in [1, 10], b^2/rho in [0, 100],
 random field and velocity directions, flat and curved (alpha, beta, non-diagonal gamma) metrics.
 
 Accuracy bound: p enters Eq. (Noble2D energy) beside terms of size tau + D and B^2, so the pressure can only
