@@ -1,8 +1,9 @@
 """Pins of the oracle's primitive recovery (Sec. 3.5) against the prim->cons map it must invert.
 
-prim -> cons (Eq. cons) is a closed form; recovery must return the primitives it started from.  States cover
-ranges from dilute to strongly magnetised, relativistic states: rho in [1e-10, 1], p/rho in [1e-4, 10], W in [1, 10], b^2/rho in [0, 100],
-random field and velocity directions, flat and curved (alpha, beta, non-diagonal gamma) metrics.
+prim -> cons (Eq. cons) is a closed form; recovery must return the primitives it started from.  States range
+from dilute to strongly magnetised and relativistic: rho in [1e-10, 1], p/rho in [1e-4, 10], W in [1, 10],
+b^2/rho in [0, 100], random field and velocity directions, flat and curved (alpha, beta, non-diagonal gamma)
+metrics.
 
 Accuracy bound: p enters Eq. (Noble2D energy) beside terms of size tau + D and B^2, so the pressure can only
 be recovered to ~eps (tau + D + B^2) in absolute terms, times the amplification of the 2x2 Newton system
