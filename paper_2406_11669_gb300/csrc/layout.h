@@ -86,6 +86,8 @@ struct BlockRec {
   signed char* flags;
 };
 
+constexpr int RCHUNK = 8;  // cells per work item of the chunked (sliding-stencil) PPM reconstruction
+
 // Item spaces of the kernels (per block).  The batched launches concatenate the blocks' item spaces in
 // table order; off[kind][blk] is the first item of block blk.
 enum Kind {
@@ -98,6 +100,7 @@ enum Kind {
   KIND_VERTEX,       // (n+3)^3: G_A, F_Psi
   KIND_EDGES_X, KIND_EDGES_Y, KIND_EDGES_Z,
   KIND_PSI,          // (n+1)^3
+  KIND_RCHUNK_X, KIND_RCHUNK_Y, KIND_RCHUNK_Z,  // PPM reconstruction by chunks of RCHUNK cells along the axis
   NKIND
 };
 
@@ -123,6 +126,9 @@ __host__ __device__ inline long kind_count(int kind, const Blk& b) {
     case KIND_EDGES_Y: return (n0 + 1) * n1 * (n2 + 1);
     case KIND_EDGES_Z: return (n0 + 1) * (n1 + 1) * n2;
     case KIND_PSI: return (n0 + 1) * (n1 + 1) * (n2 + 1);
+    case KIND_RCHUNK_X: return ((n0 + 2 + RCHUNK - 1) / RCHUNK) * N1 * N2;
+    case KIND_RCHUNK_Y: return N0 * ((n1 + 2 + RCHUNK - 1) / RCHUNK) * N2;
+    case KIND_RCHUNK_Z: return N0 * N1 * ((n2 + 2 + RCHUNK - 1) / RCHUNK);
   }
   return 0;
 }

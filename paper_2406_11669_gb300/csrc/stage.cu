@@ -453,6 +453,56 @@ struct Recon {
   }
 };
 
+// PPM reconstruction along D by chunks: one work item is a run of RCHUNK cells along D (cells g-1 .. g+n, all
+// transverse indices) that slides its 5-cell stencil, so each cell forms one new van Leer slope and one new
+// interface value (the others carry over from the previous cell) and then applies the CW84 constraints; the
+// results are those of Recon<D, 1>.  The transverse axis of smaller stride varies fastest across threads.
+template <int D>
+struct ReconPPM {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts&, long t) {
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    constexpr int TA = (D == 0) ? 1 : 0, TB = (D == 2) ? 1 : 2;
+    const Blk& b = r.b;
+    const int lenD = b.n[D] + 2;
+    int p[3];
+    p[TA] = (int)(t % b.N[TA]);
+    const long q = t / b.N[TA];
+    p[TB] = (int)(q % b.N[TB]);
+    const int ch = (int)(q / b.N[TB]);
+    const int i0 = b.g - 1 + ch * RCHUNK;
+    const int i1 = min(b.g - 1 + lenD, i0 + RCHUNK);
+    p[D] = i0;
+    const long st = stride(b, D);
+    const long c0 = lin(b, p[0], p[1], p[2]);
+    const double* src[NREC] = {r.P.f[0], r.P.f[1], r.w.uvel, r.w.uvel + b.V, r.w.uvel + 2 * b.V,
+                               r.w.bc + T1 * b.V, r.w.bc + T2 * b.V};
+    for (int v = 0; v < NREC; v++) {
+      const double* __restrict__ a = src[v];
+      long c = c0;
+      double fm2 = a[c - 2 * st], fm1 = a[c - st], f0 = a[c], fp1 = a[c + st], fp2 = a[c + 2 * st];
+      double dm = ppm_dq(fm2, fm1, f0), d0 = ppm_dq(fm1, f0, fp1), dp = ppm_dq(f0, fp1, fp2);
+      double alo = fm1 + 0.5 * (f0 - fm1) - (d0 - dm) * (1.0 / 6.0);
+      for (int i = i0; i < i1; i++) {
+        const double ahi = f0 + 0.5 * (fp1 - f0) - (dp - d0) * (1.0 / 6.0);
+        double l = alo, h = ahi;
+        ppm_limit(f0, l, h);
+        r.w.rec[v * b.V + c] = l;
+        r.w.rec[(NREC + v) * b.V + c] = h;
+        if (i + 1 < i1) {
+          fm1 = f0;
+          f0 = fp1;
+          fp1 = fp2;
+          fp2 = a[c + 3 * st];
+          d0 = dp;
+          dp = ppm_dq(f0, fp1, fp2);
+          alo = ahi;
+          c += st;
+        }
+      }
+    }
+  }
+};
+
 // Face solve along D for faces g..g+n along D and all transverse indices: left state = upper value of cell
 // f-1, right state = lower value of cell f; HLLE (Eq. HLLEfluxes) and the upwind velocities of Eq. uct1.
 template <int D>
@@ -776,7 +826,7 @@ static void seq_bfield(const T& t, const StageConsts& k, cudaStream_t s) {
 template <int D, class T>
 static void seq_dir(const T& t, const StageConsts& k, int recon, cudaStream_t s) {
   if (recon == 0) launch<Recon<D, 0>>(t, k, KIND_RECON_X + D, s);
-  else if (recon == 1) launch<Recon<D, 1>>(t, k, KIND_RECON_X + D, s);
+  else if (recon == 1) launch<ReconPPM<D>>(t, k, KIND_RCHUNK_X + D, s);
   else launch<Recon<D, 2>>(t, k, KIND_RECON_X + D, s);
   const bool mark = g_prof.on && g_prof.n < g_prof.cap && !capturing(s);
   if (mark) cudaEventRecord(g_prof.ev[2 * g_prof.n], s);
@@ -886,15 +936,15 @@ cudaError_t launch_recon_dir(const StageArgs& a, const F5& P, int D, cudaStream_
   const StageConsts k = zero_consts();
   if (D == 0) {
     if (a.recon == 0) launch<Recon<0, 0>>(t, k, KIND_RECON_X, s);
-    else if (a.recon == 1) launch<Recon<0, 1>>(t, k, KIND_RECON_X, s);
+    else if (a.recon == 1) launch<ReconPPM<0>>(t, k, KIND_RCHUNK_X, s);
     else launch<Recon<0, 2>>(t, k, KIND_RECON_X, s);
   } else if (D == 1) {
     if (a.recon == 0) launch<Recon<1, 0>>(t, k, KIND_RECON_Y, s);
-    else if (a.recon == 1) launch<Recon<1, 1>>(t, k, KIND_RECON_Y, s);
+    else if (a.recon == 1) launch<ReconPPM<1>>(t, k, KIND_RCHUNK_Y, s);
     else launch<Recon<1, 2>>(t, k, KIND_RECON_Y, s);
   } else {
     if (a.recon == 0) launch<Recon<2, 0>>(t, k, KIND_RECON_Z, s);
-    else if (a.recon == 1) launch<Recon<2, 1>>(t, k, KIND_RECON_Z, s);
+    else if (a.recon == 1) launch<ReconPPM<2>>(t, k, KIND_RCHUNK_Z, s);
     else launch<Recon<2, 2>>(t, k, KIND_RECON_Z, s);
   }
   return cudaGetLastError();
