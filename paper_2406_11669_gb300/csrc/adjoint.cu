@@ -64,7 +64,7 @@ __global__ void ka_flux_div(Blk b, AdjWs a, F9 mu, int D) {
       const double ml = left_in ? mu.f[v][c - st] : 0.0;
       const double mr = right_in ? mu.f[v][c] : 0.0;
       // F(c) enters dU(c) with +1/dx and dU(c - e_D) with -1/dx
-      a.lface[((long)D * NFD + FD_F + v) * b.V + c] = (mr - ml) / b.dx[D];
+      a.lface[((long)D * NFD + FD_F + v) * b.V + c] = (mr - ml) * b.idx[D];
     }
   }
 }
@@ -120,7 +120,7 @@ __global__ void ka_psi(Blk b, Ws w, AdjWs a, F9 mu, double xi) {
       const double mm = owned(qm) ? mu.f[8][c - astr(b, d)] : 0.0;
       const double mp = owned(qp) ? mu.f[8][c + astr(b, d)] : 0.0;
       // F^d(c) enters dPsi(c + e_d) with +1/(2dx) and dPsi(c - e_d) with -1/(2dx)
-      a.lFpsi[d * b.V + c] = (mp - mm) / (2.0 * b.dx[d]);
+      a.lFpsi[d * b.V + c] = (mp - mm) * (0.5 * b.idx[d]);
     }
     if (owned(p)) a.lY[8 * b.V + c] += -xi * w.vg[VG_ALP * b.V + c] * mu.f[8][c];
   }
@@ -150,7 +150,7 @@ __global__ void ka_grad_ga(Blk b, AdjWs a, F9 mu) {
       qm[E] -= 1;
       const double m_here = owned(p) ? mu.f[5 + E][c] : 0.0;               // edge at c: +G(c)/dx
       const double m_below = owned(qm) ? mu.f[5 + E][c - astr(b, E)] : 0.0;  // edge at c-e: -G(c)/dx
-      acc += (m_here - m_below) / b.dx[E];
+      acc += (m_here - m_below) * b.idx[E];
     }
     a.lGA[c] = acc;
   }

@@ -667,7 +667,7 @@ struct Edges {
       term[tt] = (den > 0.0) ? (ap * vL * BL + am * vR * BR - ap * am * (BR - BL)) / den : 0.5 * (vL * BL + vR * BR);
     }
     const double Ee = -term[0] + term[1];
-    const double dG = (w.ga[c + stride(b, E)] - w.ga[c]) / b.dx[E];
+    const double dG = (w.ga[c + stride(b, E)] - w.ga[c]) * b.idx[E];
     combine(k.stage, k.dt, c, 5 + E, -Ee - dG, r);
   }
 };
@@ -683,9 +683,9 @@ struct Psi {
     const long c = lin(b, i, j, kk);
     double rr = 0.0;
     if (k.lorenz) {
-      const double div = (w.fpsi[c + 1] - w.fpsi[c - 1]) / (2.0 * b.dx[0]) +
-                         (w.fpsi[b.V + c + b.sy] - w.fpsi[b.V + c - b.sy]) / (2.0 * b.dx[1]) +
-                         (w.fpsi[2 * b.V + c + b.sz] - w.fpsi[2 * b.V + c - b.sz]) / (2.0 * b.dx[2]);
+      const double div = (w.fpsi[c + 1] - w.fpsi[c - 1]) * (0.5 * b.idx[0]) +
+                         (w.fpsi[b.V + c + b.sy] - w.fpsi[b.V + c - b.sy]) * (0.5 * b.idx[1]) +
+                         (w.fpsi[2 * b.V + c + b.sz] - w.fpsi[2 * b.V + c - b.sz]) * (0.5 * b.idx[2]);
       rr = -div - k.xi * w.vg[VG_ALP * b.V + c] * r.Us.f[8][c];
     }
     combine(k.stage, k.dt, c, 8, rr, r);
@@ -707,7 +707,7 @@ struct Cells {
       const double* __restrict__ fd = w.face + (long)d * NFD * b.V;
       const long c1 = c + stride(b, d);
 #pragma unroll
-      for (int v = 0; v < 5; v++) rr[v] -= (fd[(FD_F + v) * b.V + c1] - fd[(FD_F + v) * b.V + c]) / b.dx[d];
+      for (int v = 0; v < 5; v++) rr[v] -= (fd[(FD_F + v) * b.V + c1] - fd[(FD_F + v) * b.V + c]) * b.idx[d];
     }
     Geo m;
     load_geo_centre(b, w.cg, c, m);
