@@ -91,7 +91,8 @@ def lib():
         L.asterx_batch_prepare.argtypes = [P, BB, ctypes.c_int, vp, sz, st]
         L.asterx_batch_prim2con.argtypes = [P, BB, ctypes.c_int, vp, sz, st]
         L.asterx_batched_step.argtypes = [P, BB, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, vp, sz, st]
-        for name in ("asterx_batch_prepare", "asterx_batch_prim2con", "asterx_batched_step"):
+        L.asterx_batch_release.argtypes = [vp]
+        for name in ("asterx_batch_prepare", "asterx_batch_prim2con", "asterx_batched_step", "asterx_batch_release"):
             getattr(L, name).restype = ctypes.c_int
         L.asterx_adjoint_workspace_size.restype = ctypes.c_size_t
         L.asterx_adjoint_workspace_size.argtypes = [B]
@@ -407,3 +408,14 @@ class Batch:
         sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
         _check(lib().asterx_batched_step(ctypes.byref(self.p), self.arr, self.nb, float(dt), int(nsteps), sp,
                                          self.ws_ptr, self.ws_bytes, _stream(stream)), "asterx_batched_step")
+
+    def release(self):
+        """Drops the step graphs the library cached for this batch's workspace (also done on deletion)."""
+        if getattr(self, "ws_ptr", None) is not None:
+            lib().asterx_batch_release(self.ws_ptr)
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass

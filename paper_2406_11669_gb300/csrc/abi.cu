@@ -1,8 +1,10 @@
 // Host runtime of the C ABI declared in include/asterx.h: argument validation (before any launch), workspace
 // layout, and the order of launches of one RK stage (Sec. 3.9 workflow of arXiv:2406.11669).
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/asterx.h"
@@ -151,6 +153,78 @@ asterx_status common_checks(const asterx_params* p, const asterx_block* blk, voi
 
 asterx_status cuda_status(cudaError_t e) { return e == cudaSuccess ? ASTERX_OK : ASTERX_ECUDA; }
 
+}  // namespace
+
+// One RK4 step of a batch captured as a CUDA graph (88 launches), replayed by later calls.  The graph bakes in the
+// launch parameters (tables, per-kind totals, dt, counters, physics parameters), so an entry is reused only
+// when all of them match; asterx_batch_prepare and asterx_batch_release drop the entries of their workspace.
+namespace {
+struct StepGraph {
+  int device;
+  void* ws;
+  int nb;
+  double dt;
+  void* stats;
+  asterx_params p;
+  std::vector<long> totals;
+  cudaGraphExec_t exec;
+};
+std::mutex g_graph_mu;
+std::vector<StepGraph> g_graphs;
+
+void drop_graphs(void* ws) {
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  for (size_t i = 0; i < g_graphs.size();) {
+    if (g_graphs[i].ws == ws) {
+      cudaGraphExecDestroy(g_graphs[i].exec);
+      g_graphs.erase(g_graphs.begin() + i);
+    } else {
+      i++;
+    }
+  }
+}
+
+// the cached step graph for these launch parameters, captured on a private stream if there is none (null if
+// capture is not possible, e.g. inside the caller's own capture)
+cudaGraphExec_t step_graph(const StageArgs& a, const asterx_params* p, void* ws, const BlockRec* tab, const long* off,
+                           const long* totals, int nb, double dt, unsigned long long* stats) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  for (const StepGraph& g : g_graphs)
+    if (g.device == dev && g.ws == ws && g.nb == nb && g.dt == dt && g.stats == stats &&
+        std::memcmp(&g.p, p, sizeof(*p)) == 0 && std::equal(g.totals.begin(), g.totals.end(), totals))
+      return g.exec;
+  cudaStream_t ps = nullptr;
+  if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(ps, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int stage = 0; stage < 4 && e == cudaSuccess; stage++)
+      e = launch_batch_stage(a, tab + (size_t)stage * nb, off, totals, nb, stage, dt, stats, ps);
+    const cudaError_t e2 = cudaStreamEndCapture(ps, &graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(ps);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  StepGraph g;
+  g.device = dev;
+  g.ws = ws;
+  g.nb = nb;
+  g.dt = dt;
+  g.stats = stats;
+  g.p = *p;
+  g.totals.assign(totals, totals + NKIND);
+  g.exec = exec;
+  g_graphs.push_back(g);
+  return exec;
+}
 }  // namespace
 
 extern "C" {
@@ -383,6 +457,7 @@ asterx_status asterx_batch_prepare(const asterx_params* p, const asterx_batch_bl
                                    void* ws, size_t ws_bytes, asterx_stream stream) {
   asterx_status st = batch_checks(p, blocks, nblocks, ws, ws_bytes);
   if (st != ASTERX_OK) return st;
+  drop_graphs(ws);  // new tables: cached step graphs of this workspace no longer apply
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int nb = nblocks;
   std::vector<BlockRec> tabs(4 * (size_t)nb);
@@ -441,6 +516,13 @@ asterx_status asterx_batch_prim2con(const asterx_params* p, const asterx_batch_b
   return ASTERX_OK;
 }
 
+
+asterx_status asterx_batch_release(void* ws) {
+  if (!ws) return ASTERX_EINVAL;
+  drop_graphs(ws);
+  return ASTERX_OK;
+}
+
 asterx_status asterx_batched_step(const asterx_params* p, const asterx_batch_block* blocks, int nblocks, double dt,
                                   int nsteps, asterx_c2p_stats* stats, void* ws, size_t ws_bytes,
                                   asterx_stream stream) {
@@ -456,10 +538,19 @@ asterx_status asterx_batched_step(const asterx_params* p, const asterx_batch_blo
   const BlockRec* tab = reinterpret_cast<const BlockRec*>(ws);
   const long* off = reinterpret_cast<const long*>(static_cast<char*>(ws) + 4 * (size_t)nb * sizeof(BlockRec));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(stats);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (nsteps > 0 && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+    cudaGraphExec_t exec = step_graph(a, p, ws, tab, off, totals, nb, dt, cnt);
+    if (exec) {
+      for (int step = 0; step < nsteps; step++)
+        if (cudaGraphLaunch(exec, s) != cudaSuccess) return ASTERX_ECUDA;
+      return ASTERX_OK;
+    }
+  }
   for (int step = 0; step < nsteps; step++)
     for (int stage = 0; stage < 4; stage++) {
-      cudaError_t e = launch_batch_stage(a, tab + (size_t)stage * nb, off, totals, nb, stage, dt,
-                                         reinterpret_cast<unsigned long long*>(stats), s);
+      cudaError_t e = launch_batch_stage(a, tab + (size_t)stage * nb, off, totals, nb, stage, dt, cnt, s);
       if (e != cudaSuccess) return ASTERX_ECUDA;
     }
   return ASTERX_OK;

@@ -100,3 +100,39 @@ def test_batched_block_matches_oracle():
         for v in range(9):
             err, _ = rel_field_err(Ub, U1, w, v, abs_allow=allow if v < 5 else 0.0)
             assert err <= 1e-12, (w.n, v, err)
+
+
+def test_batched_step_graph_replay_matches_direct_launches():
+    """Repeated asterx_batched_step calls replay the step graph the first call cached; inside the caller's own
+    stream capture the step launches its kernels directly (and the captured graph replays them).  Both end
+    bit-identical after three steps."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_11669_gb300 import asterx as A
+    ws = _blocks(nb=4, seed=404)
+    params, dt = ws[0].params, ws[0].dt
+
+    def make():
+        entries = []
+        for w in ws:
+            M, U, P = _inputs(w)
+            entries.append((w.n, w.g, w.x0, w.dx, w.bc, _dev(M), _dev(U), _dev(P)))
+        b = A.Batch(params, entries)
+        b.prepare()
+        b.prim2con()
+        return b, entries
+
+    b1, e1 = make()
+    for _ in range(3):
+        b1.step(dt, nsteps=1)
+    b2, e2 = make()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b2.step(dt, nsteps=3)
+    g.replay()
+    torch.cuda.synchronize()
+    for x, y in zip(e1, e2):
+        assert torch.equal(x[6], y[6]) and torch.equal(x[7], y[7])
+    b1.release()
+    b2.release()
