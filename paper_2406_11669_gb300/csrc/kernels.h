@@ -76,7 +76,6 @@ struct AdjGhost {
 };
 
 // forward reconstruction of one direction into the workspace
-cudaError_t launch_recon_dir(const StageArgs& a, const F5& P, int D, cudaStream_t s);
 // u = W v, then per direction D the reconstruction into rec[D] (2 NREC fields) and the face solve (face data of
 // direction D in the workspace, its roots into `roots`, 12 fields); no right-hand side is formed
 cudaError_t launch_face_data(const StageArgs& a, const F5& P, double* const rec[3], double* roots, cudaStream_t s);

@@ -930,26 +930,6 @@ cudaError_t launch_rhs(const StageArgs& a, const F9& Us, const F5& P, int stage,
   return cudaGetLastError();
 }
 
-cudaError_t launch_recon_dir(const StageArgs& a, const F5& P, int D, cudaStream_t s) {
-  Single t = single_of(a.b, a.w);
-  t.r.P = P;
-  const StageConsts k = zero_consts();
-  if (D == 0) {
-    if (a.recon == 0) launch<Recon<0, 0>>(t, k, KIND_RECON_X, s);
-    else if (a.recon == 1) launch<ReconPPM<0>>(t, k, KIND_RCHUNK_X, s);
-    else launch<Recon<0, 2>>(t, k, KIND_RECON_X, s);
-  } else if (D == 1) {
-    if (a.recon == 0) launch<Recon<1, 0>>(t, k, KIND_RECON_Y, s);
-    else if (a.recon == 1) launch<ReconPPM<1>>(t, k, KIND_RCHUNK_Y, s);
-    else launch<Recon<1, 2>>(t, k, KIND_RECON_Y, s);
-  } else {
-    if (a.recon == 0) launch<Recon<2, 0>>(t, k, KIND_RECON_Z, s);
-    else if (a.recon == 1) launch<ReconPPM<2>>(t, k, KIND_RCHUNK_Z, s);
-    else launch<Recon<2, 2>>(t, k, KIND_RECON_Z, s);
-  }
-  return cudaGetLastError();
-}
-
 cudaError_t launch_face_data(const StageArgs& a, const F5& P, double* const rec[3], double* roots, cudaStream_t s) {
   Single t = single_of(a.b, a.w);
   t.r.P = P;
