@@ -559,35 +559,45 @@ asterx_status asterx_batched_step(const asterx_params* p, const asterx_batch_blo
 // ----------------------------------------------------------------------------------------------------------
 // Adjoint.  Adjoint workspace: RK4 stage states Y0..Y3 (36 fields), forward accumulator (9), running adjoint
 // lambda (9), stage adjoint kbar (9), sum (9), the right-hand-side adjoint accumulators (ADJ_ACC_FIELDS),
-// reconstructed-value adjoints (2 NREC), the reconstructed values of the three directions (6 NREC), the face
-// solves' roots of the three directions (12), a state copy (9), recovery flags.
+// reconstructed-value adjoints (2 NREC), a state copy (9), and the kept forward intermediates of the four stages
+// (4 KEEP_FIELDS: recovered primitives and flags, B~ and B, u, face data, reconstruction, roots).
 
 namespace {
-constexpr int ADJ_FIELDS = 36 + 9 + 9 + 9 + 9 + ADJ_ACC_FIELDS + 2 * NREC + 6 * NREC + 12 + 9;
+constexpr int ADJ_BASE_FIELDS = 36 + 9 + 9 + 9 + 9 + ADJ_ACC_FIELDS + 2 * NREC + 9;
+constexpr int ADJ_FIELDS = ADJ_BASE_FIELDS + 4 * KEEP_FIELDS;
+
+struct Keep {
+  F5 P;
+  signed char* flags;
+  double *bf, *bc, *uvel, *face, *rec3[3], *roots;
+};
 
 struct AdjLayout {
   F9 Ys[4], acc, lam, kbar, sum, ycopy;
   double* accum;
   double* lrec;
-  double* rec3[3];
-  double* roots;
-  signed char* flags;
+  Keep keep[4];
 };
 
 size_t adj_bytes_for(const asterx_block* b) {
   const long V = padded_V(b);
   const long fs = field_stride(V);
-  return (size_t)ADJ_FIELDS * fs * sizeof(double) + (size_t)fs * sizeof(double) + kAlign;
+  return (size_t)ADJ_FIELDS * fs * sizeof(double) + kAlign;
 }
 
 AdjLayout make_adj(const asterx_block* in, void* base) {
   const long V = padded_V(in);
   const long fs = field_stride(V);
   double* p = reinterpret_cast<double*>(base);
+  auto take = [&](int nf) {
+    double* q = p;
+    p += (long)nf * fs;
+    return q;
+  };
   auto take9 = [&]() {
     F9 f;
-    for (int v = 0; v < 9; v++) f.f[v] = p + v * V;
-    p += 9 * fs;
+    double* q = take(9);
+    for (int v = 0; v < 9; v++) f.f[v] = q + v * V;
     return f;
   };
   AdjLayout L;
@@ -596,29 +606,38 @@ AdjLayout make_adj(const asterx_block* in, void* base) {
   L.lam = take9();
   L.kbar = take9();
   L.sum = take9();
-  L.accum = p;
-  p += (long)ADJ_ACC_FIELDS * fs;
-  L.lrec = p;
-  p += 2L * NREC * fs;
-  for (int d = 0; d < 3; d++) {
-    L.rec3[d] = p;
-    p += 2L * NREC * fs;
-  }
-  L.roots = p;
-  p += 12L * fs;
+  L.accum = take(ADJ_ACC_FIELDS);
+  L.lrec = take(2 * NREC);
   L.ycopy = take9();
-  L.flags = reinterpret_cast<signed char*>(p);
+  for (int s = 0; s < 4; s++) {
+    Keep& k = L.keep[s];
+    double* q = take(5);
+    for (int v = 0; v < 5; v++) k.P.f[v] = q + v * V;
+    k.bf = take(3);
+    k.bc = take(3);
+    k.uvel = take(3);
+    k.face = take(3 * NFD);
+    for (int d = 0; d < 3; d++) k.rec3[d] = take(2 * NREC);
+    k.roots = take(12);
+    k.flags = reinterpret_cast<signed char*>(take(1));
+  }
   return L;
 }
 
-AdjWs adj_ws(const AdjLayout& L, const Blk& b, const F9& Y, const F5& P, const F9& mu) {
+// the adjoint arguments of one stage: state Y, weights mu, the kept intermediates of stage `ks`
+AdjWs adj_ws(const AdjLayout& L, const Blk& b, const F9& Y, int ks, const F9& mu) {
   AdjWs a;
+  const Keep& k = L.keep[ks];
   a.Y = Y;
-  a.P = P;
   a.mu = mu;
-  for (int d = 0; d < 3; d++) a.rec3[d] = L.rec3[d];
-  a.roots = L.roots;
-  a.flags = L.flags;
+  a.P = k.P;
+  a.flags = k.flags;
+  a.kbf = k.bf;
+  a.kbc = k.bc;
+  a.kuvel = k.uvel;
+  a.kface = k.face;
+  for (int d = 0; d < 3; d++) a.rec3[d] = k.rec3[d];
+  a.roots = k.roots;
   double* q = L.accum;
   a.lY_base = q;
   a.lY = q; q += 9 * b.V;
@@ -642,6 +661,14 @@ F9 f9_from(double* base, long V) {
 
 cudaError_t copy9(const F9& dst, const F9& src, long V, cudaStream_t s) {
   for (int v = 0; v < 9; v++) {
+    cudaError_t e = cudaMemcpyAsync(dst.f[v], src.f[v], V * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t copy5(const F5& dst, const F5& src, long V, cudaStream_t s) {
+  for (int v = 0; v < 5; v++) {
     cudaError_t e = cudaMemcpyAsync(dst.f[v], src.f[v], V * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
   }
@@ -675,12 +702,15 @@ asterx_status asterx_rhs_adjoint(const asterx_params* p, const asterx_block* blk
   StageArgs sa = make_args(p, blk, ws);
   AdjLayout L = make_adj(blk, aws);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = copy9(L.ycopy, f9(U), sa.b.V, s);
-  if (e == cudaSuccess) e = copy9(L.kbar, f9(mu), sa.b.V, s);
+  const long V = sa.b.V;
+  cudaError_t e = copy9(L.ycopy, f9(U), V, s);
+  if (e == cudaSuccess) e = copy9(L.kbar, f9(mu), V, s);
   if (e == cudaSuccess) e = launch_mask_owned9(sa.b, L.kbar, s);
-  AdjWs a = adj_ws(L, sa.b, L.ycopy, f5(P), L.kbar);
+  if (e == cudaSuccess) e = copy5(L.keep[0].P, f5(P), V, s);  // the recovery's guess
+  AdjWs a = adj_ws(L, sa.b, L.ycopy, 0, L.kbar);
   if (e == cudaSuccess) e = launch_rhs_adjoint(sa, a, dt, s);
-  if (e == cudaSuccess) e = copy9(f9(lam), f9_from(a.lY, sa.b.V), sa.b.V, s);
+  if (e == cudaSuccess) e = copy9(f9(lam), f9_from(a.lY, V), V, s);
+  if (e == cudaSuccess) e = copy5(f5(P), L.keep[0].P, V, s);
   return cuda_status(e);
 }
 
@@ -709,9 +739,11 @@ asterx_status asterx_rk_stage_adjoint(const asterx_params* p, const asterx_block
   }
   if (e == cudaSuccess) e = launch_mask_owned9(b, L.kbar, s);
   if (e == cudaSuccess) e = copy9(L.ycopy, f9(Us), b.V, s);
-  AdjWs a = adj_ws(L, b, L.ycopy, f5(P), L.kbar);
+  if (e == cudaSuccess) e = copy5(L.keep[0].P, f5(P), b.V, s);
+  AdjWs a = adj_ws(L, b, L.ycopy, 0, L.kbar);
   if (e == cudaSuccess) e = launch_rhs_adjoint(sa, a, dt, s);
   if (e == cudaSuccess) e = copy9(f9(lam_s), f9_from(a.lY, b.V), b.V, s);
+  if (e == cudaSuccess) e = copy5(f5(P), L.keep[0].P, b.V, s);
   return cuda_status(e);
 }
 
@@ -726,12 +758,16 @@ asterx_status asterx_rk4_step_adjoint(const asterx_params* p, const asterx_block
   const Blk& b = sa.b;
   AdjLayout L = make_adj(blk, aws);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // forward recompute of the stage states Y0..Y3 from the checkpoint
+  // forward pass from the checkpoint, keeping each stage's intermediates: the stage states Y0..Y3 and, per
+  // stage, the recovery, face data and reconstruction (the recovery's guess carries from stage to stage)
   cudaError_t e = copy9(L.Ys[0], f9(Un), b.V, s);
-  for (int stage = 0; stage < 3 && e == cudaSuccess; stage++) {
-    const asterx_status r = stage_impl(sa, stage, dt, L.Ys[0], L.Ys[stage], L.Ys[stage + 1], L.acc, f5(P), nullptr,
-                                       nullptr, s);
-    if (r != ASTERX_OK) return r;
+  if (e == cudaSuccess) e = copy5(L.keep[0].P, f5(P), b.V, s);
+  for (int stage = 0; stage < 4 && e == cudaSuccess; stage++) {
+    AdjWs a = adj_ws(L, b, L.Ys[stage], stage, L.kbar);
+    if (stage > 0) e = copy5(L.keep[stage].P, L.keep[stage - 1].P, b.V, s);
+    if (e == cudaSuccess) e = launch_adjoint_forward(sa, a, s);
+    if (stage < 3 && e == cudaSuccess)
+      e = launch_rhs_from_kept(sa, a, stage, dt, L.Ys[0], L.Ys[stage + 1], L.acc, L.Ys[stage + 1], s);
   }
   // reverse sweep: kbar_3 = dt/6 lam, Ybar_s = J_s^T kbar_s, kbar_{s-1} = b_{s-1} dt lam + c_s dt Ybar_s
   if (e == cudaSuccess) e = copy9(L.lam, f9(lam), b.V, s);
@@ -742,8 +778,8 @@ asterx_status asterx_rk4_step_adjoint(const asterx_params* p, const asterx_block
   const double blam[3] = {dt / 6.0, dt / 3.0, dt / 3.0};  // weight of lam in kbar_{s}, s = 0, 1, 2
   const double cy[3] = {0.5 * dt, 0.5 * dt, dt};          // weight of Ybar_{s+1} in kbar_{s}
   for (int stage = 3; stage >= 0 && e == cudaSuccess; stage--) {
-    AdjWs a = adj_ws(L, b, L.Ys[stage], f5(P), L.kbar);
-    e = launch_rhs_adjoint(sa, a, dt, s);
+    AdjWs a = adj_ws(L, b, L.Ys[stage], stage, L.kbar);
+    e = launch_adjoint_reverse(sa, a, dt, s);
     const F9 ybar = f9_from(a.lY, b.V);
     if (e == cudaSuccess) e = launch_axpby9(b, 1.0, ybar, 1.0, L.sum, s);
     if (stage > 0 && e == cudaSuccess) {
@@ -753,6 +789,7 @@ asterx_status asterx_rk4_step_adjoint(const asterx_params* p, const asterx_block
     }
   }
   if (e == cudaSuccess) e = copy9(f9(lam), L.sum, b.V, s);
+  if (e == cudaSuccess) e = copy5(f5(P), L.keep[0].P, b.V, s);
   return cuda_status(e);
 }
 
@@ -770,7 +807,8 @@ asterx_status asterx_prim2con_adjoint(const asterx_params* p, const asterx_block
   cudaError_t e = copy9(L.ycopy, f9(U), sa.b.V, s);
   if (e == cudaSuccess) e = copy9(L.kbar, f9(lam), sa.b.V, s);
   if (e == cudaSuccess) e = launch_mask_owned9(sa.b, L.kbar, s);
-  AdjWs a = adj_ws(L, sa.b, L.ycopy, f5(const_cast<asterx_prims*>(P)), L.kbar);
+  if (e == cudaSuccess) e = copy5(L.keep[0].P, f5(P), sa.b.V, s);
+  AdjWs a = adj_ws(L, sa.b, L.ycopy, 0, L.kbar);
   if (e == cudaSuccess) e = launch_prim2con_adjoint(sa, a, L.kbar, f5(lamP), s);
   if (e == cudaSuccess) e = copy9(f9(lam), f9_from(a.lY, sa.b.V), sa.b.V, s);
   return cuda_status(e);

@@ -720,17 +720,28 @@ __global__ void ka_zero5(Blk b, F5 x) {
   }
 }
 
+// the workspace as the kept intermediates of one stage see it
+static Ws kept_ws(const StageArgs& sa, const AdjWs& a) {
+  Ws w = sa.w;
+  w.bf = a.kbf;
+  w.bc = a.kbc;
+  w.uvel = a.kuvel;
+  w.face = a.kface;
+  return w;
+}
+
 cudaError_t launch_prim2con_adjoint(const StageArgs& sa, const AdjWs& a, const F9& lamU, const F5& lamP,
                                     cudaStream_t s) {
   const Blk& b = sa.b;
   const int T = 128;
+  const Ws w = kept_ws(sa, a);
   cudaError_t e = launch_ghost_state(b, a.Y, s);
-  if (e == cudaSuccess) e = launch_bfield(b, sa.w, a.Y, s);
+  if (e == cudaSuccess) e = launch_bfield(b, w, a.Y, s);
   if (e != cudaSuccess) return e;
   cudaMemsetAsync(a.lY_base, 0, (size_t)ADJ_ACC_FIELDS * b.V * sizeof(double), s);
   ka_zero5<<<agrid(5 * b.V, 256), 256, 0, s>>>(b, lamP);
-  ka_prim2con<<<agrid((long)b.n[0] * b.n[1] * b.n[2], T), T, 0, s>>>(b, sa.w, a, lamU, lamP, sa.gamma, sa.gfac);
-  ka_bcentre<<<agrid(b.V, T), T, 0, s>>>(b, sa.w, a);
+  ka_prim2con<<<agrid((long)b.n[0] * b.n[1] * b.n[2], T), T, 0, s>>>(b, w, a, lamU, lamP, sa.gamma, sa.gfac);
+  ka_bcentre<<<agrid(b.V, T), T, 0, s>>>(b, w, a);
   ka_curl<<<agrid(b.V, T), T, 0, s>>>(b, a);
   F9 ly;
   for (int v = 0; v < 9; v++) ly.f[v] = a.lY + v * b.V;
@@ -769,17 +780,23 @@ static void adjoint_dir(const StageArgs& sa, const AdjWs& a, cudaStream_t s) {
   else ka_recon<D, 2><<<agrid(rc, T), T, 0, s>>>(b, w, a);
 }
 
-cudaError_t launch_rhs_adjoint(const StageArgs& sa, const AdjWs& a, double dt, cudaStream_t s) {
+cudaError_t launch_adjoint_forward(const StageArgs& sa, const AdjWs& a, cudaStream_t s) {
+  StageArgs k = sa;
+  k.w = kept_ws(sa, a);
+  const Blk& b = sa.b;
+  cudaError_t e = launch_ghost_state(b, a.Y, s);
+  if (e == cudaSuccess) e = launch_bfield(b, k.w, a.Y, s);
+  if (e == cudaSuccess) e = launch_c2p(k, a.Y, a.P, a.flags, nullptr, s);
+  if (e == cudaSuccess) e = launch_ghost_prims(b, a.P, s);
+  if (e == cudaSuccess) e = launch_face_data(k, a.P, a.rec3, a.roots, s);
+  return e;
+}
+
+cudaError_t launch_adjoint_reverse(const StageArgs& sa0, const AdjWs& a, double dt, cudaStream_t s) {
+  StageArgs sa = sa0;
+  sa.w = kept_ws(sa0, a);
   const Blk& b = sa.b;
   const int T = 128;
-  // forward recompute: ghost fill of Y, face/centre field, recovery (flags), primitive ghost fill, u and the
-  // reconstruction and face data of every direction (what the reverse kernels read; no right-hand side)
-  cudaError_t e = launch_ghost_state(b, a.Y, s);
-  if (e == cudaSuccess) e = launch_bfield(b, sa.w, a.Y, s);
-  if (e == cudaSuccess) e = launch_c2p(sa, a.Y, a.P, a.flags, nullptr, s);
-  if (e == cudaSuccess) e = launch_ghost_prims(b, a.P, s);
-  if (e == cudaSuccess) e = launch_face_data(sa, a.P, a.rec3, a.roots, s);
-  if (e != cudaSuccess) return e;
   // adjoint accumulators
   cudaMemsetAsync(a.lY_base, 0, (size_t)ADJ_ACC_FIELDS * b.V * sizeof(double), s);
   const int lorenz = (sa.gauge == 0);
@@ -826,6 +843,12 @@ cudaError_t launch_rhs_adjoint(const StageArgs& sa, const AdjWs& a, double dt, c
     launch_ghost_adjoint(b, g, 9, s);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_adjoint(const StageArgs& sa, const AdjWs& a, double dt, cudaStream_t s) {
+  cudaError_t e = launch_adjoint_forward(sa, a, s);
+  if (e == cudaSuccess) e = launch_adjoint_reverse(sa, a, dt, s);
+  return e;
 }
 
 }  // namespace asterx

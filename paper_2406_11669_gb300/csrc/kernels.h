@@ -49,13 +49,20 @@ cudaError_t launch_batch_stage(const StageArgs& a, const BlockRec* tab, const lo
 // accumulators cleared together at the start of each right-hand-side adjoint (contiguous, in this order)
 constexpr int ADJ_ACC_FIELDS = 9 + 5 + 3 + 3 + 3 + 3 * NFD + 1 + 3 + 3;
 
+// One stage's forward intermediates, kept from its forward pass for its reverse sweep: the primitives recovered
+// at the stage state and their flags, the face and centre field, u = W v, the face data and reconstruction of
+// every direction, and the face solves' roots.  KEEP_FIELDS fields (the flags take one).
+constexpr int KEEP_FIELDS = 5 + 3 + 3 + 3 + 3 * NFD + 6 * NREC + 12 + 1;
+
 struct AdjWs {
   F9 Y;            // the state the right-hand side is linearised at (a copy; ghost-filled, atmosphere-reset)
-  F5 P;            // primitives recovered from Y (caller's buffers; the entry values are the guess)
   F9 mu;           // adjoint of dU/dt (owned ranges read)
-  double* rec3[3];  // reconstructed values of each direction (2 NREC fields each), kept from the recompute
-  double* roots;    // 12 fields: the face solves' roots (lambda_+, lambda_- of left and right) per direction
+  // the stage's kept forward intermediates
+  F5 P;             // primitives recovered from Y (the entry values are the guess)
   signed char* flags;
+  double *kbf, *kbc, *kuvel, *kface;  // face B~ (3), centre B (3), u (3), face data (3 NFD)
+  double* rec3[3];  // reconstructed values of each direction (2 NREC fields each)
+  double* roots;    // 12 fields: the face solves' roots (lambda_+, lambda_- of left and right) per direction
   double* lY_base;  // start of the ADJ_ACC_FIELDS accumulators
   double* lY;       // 9: result, adjoint of Y
   double* lP;       // 5: primitives
@@ -75,11 +82,19 @@ struct AdjGhost {
   int lin[9];
 };
 
-// forward reconstruction of one direction into the workspace
 // u = W v, then per direction D the reconstruction into rec[D] (2 NREC fields) and the face solve (face data of
 // direction D in the workspace, its roots into `roots`, 12 fields); no right-hand side is formed
 cudaError_t launch_face_data(const StageArgs& a, const F5& P, double* const rec[3], double* roots, cudaStream_t s);
-// lambda = (dL/dY)^T mu at the state a.Y (recomputes the forward intermediates)
+// the forward pass of one stage at a.Y into the kept intermediates of a (ghost fill of a.Y, B~ and B, recovery
+// into a.P with a.flags, primitive ghost fill, u and the face data of every direction); no right-hand side
+cudaError_t launch_adjoint_forward(const StageArgs& sa, const AdjWs& a, cudaStream_t s);
+// the right-hand side's remaining steps (vertex potentials, UCT edges, Psi, cells with the RK combine) from the
+// kept intermediates of a: forms dU (stage < 0) or the stage's RK4 update, as launch_rhs does
+cudaError_t launch_rhs_from_kept(const StageArgs& sa, const AdjWs& a, int stage, double dt, const F9& Un,
+                                 const F9& Unext, const F9& Uacc, const F9& dU, cudaStream_t s);
+// lambda = (dL/dY)^T mu from the kept intermediates (the reverse sweep alone)
+cudaError_t launch_adjoint_reverse(const StageArgs& sa, const AdjWs& a, double dt, cudaStream_t s);
+// forward pass, then reverse sweep
 cudaError_t launch_rhs_adjoint(const StageArgs& sa, const AdjWs& a, double dt, cudaStream_t s);
 // adjoint of the initial data U = (prim2con(P, B(A)), A, Psi) at the state a.Y (copy; ghost-filled here):
 // lamP (interior cells) and a.lY (A, Psi entries; independent ranges) from lamU

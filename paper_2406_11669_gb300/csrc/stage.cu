@@ -835,6 +835,16 @@ static void seq_dir(const T& t, const StageConsts& k, int recon, cudaStream_t s)
 }
 
 template <class T>
+static void seq_rhs_tail(const T& t, const StageConsts& k, cudaStream_t s) {
+  launch<Vertex>(t, k, KIND_VERTEX, s);
+  launch<Edges<0>>(t, k, KIND_EDGES_X, s);
+  launch<Edges<1>>(t, k, KIND_EDGES_Y, s);
+  launch<Edges<2>>(t, k, KIND_EDGES_Z, s);
+  launch<Psi>(t, k, KIND_PSI, s);
+  launch<Cells>(t, k, KIND_INTERIOR, s);
+}
+
+template <class T>
 static void seq_rhs(const T& t, const StageConsts& k, int recon, cudaStream_t s) {
   launch<UVel>(t, k, KIND_CELLS_ALL, s);
   seq_dir<0>(t, k, recon, s);
@@ -927,6 +937,24 @@ cudaError_t launch_rhs(const StageArgs& a, const F9& Us, const F5& P, int stage,
   t.r.Uacc = Uacc;
   t.r.dU = dU;
   seq_rhs(t, consts_of(a, stage, dt, nullptr), a.recon, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_from_kept(const StageArgs& sa, const AdjWs& a, int stage, double dt, const F9& Un,
+                                 const F9& Unext, const F9& Uacc, const F9& dU, cudaStream_t s) {
+  Ws w = sa.w;
+  w.bf = a.kbf;
+  w.bc = a.kbc;
+  w.uvel = a.kuvel;
+  w.face = a.kface;
+  Single t = single_of(sa.b, w);
+  t.r.Us = a.Y;
+  t.r.P = a.P;
+  t.r.Un = Un;
+  t.r.Unext = Unext;
+  t.r.Uacc = Uacc;
+  t.r.dU = dU;
+  seq_rhs_tail(t, consts_of(sa, stage, dt, nullptr), s);
   return cudaGetLastError();
 }
 
