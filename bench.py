@@ -35,7 +35,7 @@ WORKLOAD = ("128^3 block + 3 ghosts, FP64, ideal gas Gamma=5/3, WENO-Z + HLLE + 
             "0.5 outside the box, copy BCs, one RK4 step = 4 stages")
 # kernels the library launches per RK stage: 3 + 3 ghost sweeps, 2 field kernels, recovery, velocity, 3 x
 # (reconstruction + face solve), vertex potentials, 3 edge kernels, scalar potential, cells
-LAUNCHES_PER_STAGE = 22
+LAUNCHES_PER_STAGE = 28
 # nominal FP64 peak: 152 SMs x 2 DFMA/clock/SM x 2 flops x 2.07 GHz (unit counts and clock of the GB300 recipe)
 FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 

@@ -248,7 +248,7 @@ asterx_status asterx_batch_prim2con(const asterx_params *p, const asterx_batch_b
 
 /* `nsteps` classical RK4 steps of every block (the same `blocks` array as asterx_batch_prepare); `stats`
  * (device, may be NULL) accumulates the recovery counters of all blocks and stages.  The first call captures
- * one RK4 step (4 stages x 22 launches) as a CUDA graph on a private stream and caches it (host memory, guarded
+ * one RK4 step (4 stages x 28 launches) as a CUDA graph on a private stream and caches it (host memory, guarded
  * by a mutex) for the workspace and launch parameters (dt, stats, params); this and later calls with the same
  * parameters replay it.  Inside the caller's own stream capture the launches are issued directly. */
 asterx_status asterx_batched_step(const asterx_params *p, const asterx_batch_block *blocks, int nblocks,

@@ -108,6 +108,7 @@ Ws make_ws(const asterx_block* in, void* base) {
   w.fpsi = take(3);
   w.uacc = take(9);
   w.ustage = take(18);
+  w.erec = take(24);
   w.counters = reinterpret_cast<unsigned long long*>(p);
   w.roots = nullptr;
   return w;
@@ -155,7 +156,7 @@ asterx_status cuda_status(cudaError_t e) { return e == cudaSuccess ? ASTERX_OK :
 
 }  // namespace
 
-// One RK4 step of a batch captured as a CUDA graph (88 launches), replayed by later calls.  The graph bakes in the
+// One RK4 step of a batch captured as a CUDA graph (112 launches), replayed by later calls.  The graph bakes in the
 // launch parameters (tables, per-kind totals, dt, counters, physics parameters), so an entry is reused only
 // when all of them match; asterx_batch_prepare and asterx_batch_release drop the entries of their workspace.
 namespace {

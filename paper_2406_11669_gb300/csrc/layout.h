@@ -58,12 +58,14 @@ struct Ws {
   double* fpsi;    // 3 fields: F_Psi^j at vertices
   double* roots;   // null, or 12 fields: the face solves' (lambda_+, lambda_-) of the left and right states per
                    // direction, written by the face solve for the adjoint's reverse sweep
+  double* erec;    // 24 fields: per face normal df and transverse direction dr (2 per df), the PPM lower and
+                   // upper values along dr of the upwind velocity v~bar^dr and of B~^df (UCT's edge inputs)
   double* uacc;    // 9 fields: RK4 accumulator of asterx_rk4_step
   double* ustage;  // 2 * 9 fields: RK4 stage buffers of asterx_rk4_step
   unsigned long long* counters;  // 8 counters (internal statistics when the caller passes none)
 };
 
-constexpr int WS_FIELDS = NCG + 3 * NFG + NVG + 3 + 3 + 3 + 2 * NREC + 3 * NFD + 1 + 3 + 9 + 18;
+constexpr int WS_FIELDS = NCG + 3 * NFG + NVG + 3 + 3 + 3 + 2 * NREC + 3 * NFD + 1 + 3 + 9 + 18 + 24;
 
 struct F9 {
   double* f[9];
@@ -101,7 +103,8 @@ enum Kind {
   KIND_EDGES_X, KIND_EDGES_Y, KIND_EDGES_Z,
   KIND_PSI,          // (n+1)^3
   KIND_RCHUNK_X, KIND_RCHUNK_Y, KIND_RCHUNK_Z,  // PPM reconstruction by chunks of RCHUNK cells along the axis
-  NKIND
+  KIND_EREC,  // 6 kinds KIND_EREC + 2 df + k: face data of faces normal to df along dr = (df + 1 + k) % 3, by chunks
+  NKIND = KIND_EREC + 6
 };
 
 __host__ __device__ inline long kind_count(int kind, const Blk& b) {
@@ -129,6 +132,13 @@ __host__ __device__ inline long kind_count(int kind, const Blk& b) {
     case KIND_RCHUNK_X: return ((n0 + 2 + RCHUNK - 1) / RCHUNK) * N1 * N2;
     case KIND_RCHUNK_Y: return N0 * ((n1 + 2 + RCHUNK - 1) / RCHUNK) * N2;
     case KIND_RCHUNK_Z: return N0 * N1 * ((n2 + 2 + RCHUNK - 1) / RCHUNK);
+    default:
+      if (kind >= KIND_EREC && kind < KIND_EREC + 6) {
+        const int df = (kind - KIND_EREC) / 2, dr = (df + 1 + (kind - KIND_EREC) % 2) % 3, de = 3 - df - dr;
+        const long n[3] = {n0, n1, n2};
+        // faces g-1..g+n along dr (chunks), g..g+n along df, g..g+n-1 along de
+        return ((n[dr] + 2 + RCHUNK - 1) / RCHUNK) * (n[df] + 1) * n[de];
+      }
   }
   return 0;
 }

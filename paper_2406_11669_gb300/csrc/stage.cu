@@ -619,8 +619,60 @@ struct Vertex {
   }
 };
 
-// PPM values on both sides of the interface between stencil positions 2 and 3 of f[0..5]
-__device__ __forceinline__ void ppm_interface(const double f[6], double& L, double& R) { ppm_pair(f, L, R); }
+
+// UCT edge inputs: for the faces normal to DF, the PPM lower and upper values along DR (chunked, sliding
+// stencil as in ReconPPM) of the upwind velocity v~bar^DR and of the face field B~^DF, over the faces the edges
+// use (g-1..g+n along DR, g..g+n along DF, g..g+n-1 along the third axis).  The edge between faces f-1 and f
+// along DR takes the upper value of f-1 and the lower value of f: the values ppm_pair forms from f-3..f+2.
+template <int DF, int K>
+struct EdgeRecon {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts&, long t) {
+    constexpr int DR = (DF + 1 + K) % 3, DE = 3 - DF - DR;
+    constexpr int TA = (DF < DE) ? DF : DE, TB = (DF < DE) ? DE : DF;  // transverse axes, smaller stride first
+    const Blk& b = r.b;
+    const int ea = (TA == DF) ? b.n[DF] + 1 : b.n[DE];
+    const int eb = (TB == DF) ? b.n[DF] + 1 : b.n[DE];
+    int p[3];
+    p[TA] = b.g + (int)(t % ea);
+    const long q = t / ea;
+    p[TB] = b.g + (int)(q % eb);
+    const int ch = (int)(q / eb);
+    const int i0 = b.g - 1 + ch * RCHUNK;
+    const int i1 = min(b.g + b.n[DR] + 1, i0 + RCHUNK);
+    p[DR] = i0;
+    const long st = stride(b, DR);
+    const long c0 = lin(b, p[0], p[1], p[2]);
+    const int slot = (((DF + 1) % 3) == DR) ? FD_VB1 : FD_VB2;
+    const double* srcs[2] = {r.w.face + ((long)DF * NFD + slot) * b.V, r.w.bf + (long)DF * b.V};
+    double* out = r.w.erec + (long)(DF * 2 + K) * 4 * b.V;
+    for (int qn = 0; qn < 2; qn++) {
+      const double* __restrict__ a = srcs[qn];
+      double* __restrict__ lo = out + (2 * qn) * b.V;
+      double* __restrict__ hi = out + (2 * qn + 1) * b.V;
+      long c = c0;
+      double fm2 = a[c - 2 * st], fm1 = a[c - st], f0 = a[c], fp1 = a[c + st], fp2 = a[c + 2 * st];
+      double dm = ppm_dq(fm2, fm1, f0), d0 = ppm_dq(fm1, f0, fp1), dp = ppm_dq(f0, fp1, fp2);
+      double alo = fm1 + 0.5 * (f0 - fm1) - (d0 - dm) * (1.0 / 6.0);
+      for (int i = i0; i < i1; i++) {
+        const double ahi = f0 + 0.5 * (fp1 - f0) - (dp - d0) * (1.0 / 6.0);
+        double l = alo, h = ahi;
+        ppm_limit(f0, l, h);
+        lo[c] = l;
+        hi[c] = h;
+        if (i + 1 < i1) {
+          fm1 = f0;
+          f0 = fp1;
+          fp1 = fp2;
+          fp2 = a[c + 3 * st];
+          d0 = dp;
+          dp = ppm_dq(f0, fp1, fp2);
+          alo = ahi;
+          c += st;
+        }
+      }
+    }
+  }
+};
 
 // Edges along E (owned range): UCT electric field (Sec. 3.4, Eqs. uct1, uct2, eq3.20) with (E, d1, d2) cyclic,
 //   E_E = -HLL_d1(v~^d1 B~^d2) + HLL_d2(v~^d2 B~^d1),
@@ -646,19 +698,10 @@ struct Edges {
       const long sr = stride(b, dr);
       const long sf = stride(b, df);
       // component dr on df-faces: slot VB1 holds component (df+1)%3, VB2 holds (df+2)%3
-      const int slot = (((df + 1) % 3) == dr) ? FD_VB1 : FD_VB2;
-      const double* __restrict__ vb = w.face + ((long)df * NFD + slot) * b.V;
-      const double* __restrict__ bn = w.bf + (long)df * b.V;
-      double vs[6], bs[6];
-#pragma unroll
-      for (int s = 0; s < 6; s++) {
-        const long q = c + (s - 3) * sr;
-        vs[s] = vb[q];
-        bs[s] = bn[q];
-      }
-      double vL, vR, BL, BR;
-      ppm_interface(vs, vL, vR);
-      ppm_interface(bs, BL, BR);
+      // the PPM values on both sides of the edge, from the UCT edge inputs of the faces normal to df
+      const int kk = (((df + 1) % 3) == dr) ? 0 : 1;
+      const double* __restrict__ er = w.erec + (long)(df * 2 + kk) * 4 * b.V;
+      const double vL = er[b.V + c - sr], vR = er[c], BL = er[3 * b.V + c - sr], BR = er[2 * b.V + c];
       const double* __restrict__ fdr = w.face + (long)dr * NFD * b.V;
       const long c0 = c - sf;
       const double ap = fmax(fdr[FD_CMAX * b.V + c0], fdr[FD_CMAX * b.V + c]);
@@ -835,7 +878,18 @@ static void seq_dir(const T& t, const StageConsts& k, int recon, cudaStream_t s)
 }
 
 template <class T>
+static void seq_erec(const T& t, const StageConsts& k, cudaStream_t s) {
+  launch<EdgeRecon<0, 0>>(t, k, KIND_EREC + 0, s);
+  launch<EdgeRecon<0, 1>>(t, k, KIND_EREC + 1, s);
+  launch<EdgeRecon<1, 0>>(t, k, KIND_EREC + 2, s);
+  launch<EdgeRecon<1, 1>>(t, k, KIND_EREC + 3, s);
+  launch<EdgeRecon<2, 0>>(t, k, KIND_EREC + 4, s);
+  launch<EdgeRecon<2, 1>>(t, k, KIND_EREC + 5, s);
+}
+
+template <class T>
 static void seq_rhs_tail(const T& t, const StageConsts& k, cudaStream_t s) {
+  seq_erec(t, k, s);
   launch<Vertex>(t, k, KIND_VERTEX, s);
   launch<Edges<0>>(t, k, KIND_EDGES_X, s);
   launch<Edges<1>>(t, k, KIND_EDGES_Y, s);
@@ -850,6 +904,7 @@ static void seq_rhs(const T& t, const StageConsts& k, int recon, cudaStream_t s)
   seq_dir<0>(t, k, recon, s);
   seq_dir<1>(t, k, recon, s);
   seq_dir<2>(t, k, recon, s);
+  seq_erec(t, k, s);
   launch<Vertex>(t, k, KIND_VERTEX, s);
   launch<Edges<0>>(t, k, KIND_EDGES_X, s);
   launch<Edges<1>>(t, k, KIND_EDGES_Y, s);
