@@ -438,25 +438,6 @@ __host__ __device__ __forceinline__ void ppm_limit(T ai, T& l, T& r) {
   }
 }
 
-// PPM values on both sides of the interface between positions 2 and 3 of f[0..5] (the upper value of cell 2 and
-// the lower value of cell 3, each as recon5<1> gives it): the slopes of cells 1..4 and the interface value
-// between cells 2 and 3 are formed once for the two cells.
-template <class T>
-__host__ __device__ __forceinline__ void ppm_pair(const T f[6], T& L, T& R) {
-  const T d1 = ppm_dq(f[0], f[1], f[2]);
-  const T d2 = ppm_dq(f[1], f[2], f[3]);
-  const T d3 = ppm_dq(f[2], f[3], f[4]);
-  const T d4 = ppm_dq(f[3], f[4], f[5]);
-  T l2 = f[1] + 0.5 * (f[2] - f[1]) - (d2 - d1) * (1.0 / 6.0);
-  T r2 = f[2] + 0.5 * (f[3] - f[2]) - (d3 - d2) * (1.0 / 6.0);
-  T r3 = f[3] + 0.5 * (f[4] - f[3]) - (d4 - d3) * (1.0 / 6.0);
-  T l3 = r2;
-  ppm_limit(f[2], l2, r2);
-  ppm_limit(f[3], l3, r3);
-  L = r2;
-  R = l3;
-}
-
 // WENO-Z values at both faces of the middle cell of s[0..4].  The lower face uses the mirrored stencil, whose
 // smoothness indicators are those of the upper face in reverse order, so the indicators are shared.  With
 // e_k = beta_k + eps and p = 2 the nonlinear weights alpha_k = d_k (1 + (tau5 / e_k)^2) are proportional to
@@ -564,8 +545,10 @@ __host__ __device__ __forceinline__ void ppm_limit_vjp(double ai, double l, doub
   }
 }
 
-// ppm_pair with its primal kept for the reverse sweep: values() as ppm_pair gives them, then vjp() turns the
-// weights on (L, R) into the gradient with respect to f[0..5], without recomputing the primal.
+// PPM values on both sides of the interface between positions 2 and 3 of f[0..5] (the upper value of cell 2 and
+// the lower value of cell 3, each as recon5<1> gives it), with the primal kept for the reverse sweep: values()
+// forms the slopes of cells 1..4 and the three interface values once, then vjp() turns the weights on (L, R)
+// into the gradient with respect to f[0..5] without recomputing the primal.
 struct PpmPair {
   double f[6], d[4], am, ac, ap, L, R;
   __host__ __device__ __forceinline__ void values(const double in[6]) {

@@ -423,7 +423,8 @@ struct UVel {
 
 // ----------------------------------------------------------------------------------------------------------
 // Reconstruction along D of each cell once (cells g-1 .. g+n along D, all transverse cells): the values at the
-// cell's lower and upper D-faces of rho, p, u^x, u^y, u^z and the two transverse centre B components.
+// cell's lower and upper D-faces of rho, p, u^x, u^y, u^z and the two transverse centre B components.  Minmod
+// and WENO-Z per cell; PPM runs as ReconPPM below (chunks with a sliding stencil).
 
 template <int D, int SCHEME>
 struct Recon {
