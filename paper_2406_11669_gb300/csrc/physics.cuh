@@ -444,13 +444,7 @@ __host__ __device__ __forceinline__ void ppm_limit(T ai, T& l, T& r) {
 // d_k (e_k^2 + tau5^2) prod_{j != k} e_j^2, which needs no division before the normalisation (e_k >= eps keeps the
 // products above the smallest normal double; out-of-range products take the form with the quotients).
 template <class T>
-__host__ __device__ __forceinline__ void wenoz_both(const T s[5], T& lo, T& hi) {
-  const T t0a = s[0] - 2.0 * s[1] + s[2], t0b = s[0] - 4.0 * s[1] + 3.0 * s[2];
-  const T t1a = s[1] - 2.0 * s[2] + s[3], t1b = s[1] - s[3];
-  const T t2a = s[2] - 2.0 * s[3] + s[4], t2b = 3.0 * s[2] - 4.0 * s[3] + s[4];
-  const T e0 = (13.0 / 12.0) * t0a * t0a + 0.25 * t0b * t0b + 1e-40;
-  const T e1 = (13.0 / 12.0) * t1a * t1a + 0.25 * t1b * t1b + 1e-40;
-  const T e2 = (13.0 / 12.0) * t2a * t2a + 0.25 * t2b * t2b + 1e-40;
+__host__ __device__ __forceinline__ void wenoz_from_indicators(const T s[5], T e0, T e1, T e2, T& lo, T& hi) {
   const T tau5 = fabs(e0 - e2);
   const T tt = tau5 * tau5;
   const T E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
@@ -477,6 +471,22 @@ __host__ __device__ __forceinline__ void wenoz_both(const T s[5], T& lo, T& hi) 
     const T w0 = 0.1 * a2, w1 = 0.6 * a1, w2 = 0.3 * a0;
     lo = (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
   }
+}
+
+// the (13/12) (second difference)^2 part of a Jiang-Shu indicator, for the three-point sub-stencil centred at b
+template <class T>
+__host__ __device__ __forceinline__ T wenoz_curv(T a, T b, T c) {
+  const T t = a - 2.0 * b + c;
+  return (13.0 / 12.0) * t * t;
+}
+
+template <class T>
+__host__ __device__ __forceinline__ void wenoz_both(const T s[5], T& lo, T& hi) {
+  const T t0b = s[0] - 4.0 * s[1] + 3.0 * s[2], t1b = s[1] - s[3], t2b = 3.0 * s[2] - 4.0 * s[3] + s[4];
+  const T e0 = wenoz_curv(s[0], s[1], s[2]) + 0.25 * t0b * t0b + 1e-40;
+  const T e1 = wenoz_curv(s[1], s[2], s[3]) + 0.25 * t1b * t1b + 1e-40;
+  const T e2 = wenoz_curv(s[2], s[3], s[4]) + 0.25 * t2b * t2b + 1e-40;
+  wenoz_from_indicators(s, e0, e1, e2, lo, hi);
 }
 
 template <int SCHEME, class T>

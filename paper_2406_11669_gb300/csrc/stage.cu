@@ -424,7 +424,7 @@ struct UVel {
 // ----------------------------------------------------------------------------------------------------------
 // Reconstruction along D of each cell once (cells g-1 .. g+n along D, all transverse cells): the values at the
 // cell's lower and upper D-faces of rho, p, u^x, u^y, u^z and the two transverse centre B components.  Minmod
-// and WENO-Z per cell; PPM runs as ReconPPM below (chunks with a sliding stencil).
+// runs per cell; PPM and WENO-Z run as ReconPPM and ReconWENO below (chunks with a sliding stencil).
 
 template <int D, int SCHEME>
 struct Recon {
@@ -620,6 +620,58 @@ struct Vertex {
   }
 };
 
+
+// WENO-Z reconstruction along D by chunks: as ReconPPM, a run of RCHUNK cells along D slides its 5-cell stencil;
+// the curvature part (13/12) (second difference)^2 of the Jiang-Shu indicators is shared by three consecutive
+// cells, so each cell forms one new curvature term and the rest of its indicators and weights (wenoz_both).
+template <int D>
+struct ReconWENO {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts&, long t) {
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    constexpr int TA = (D == 0) ? 1 : 0, TB = (D == 2) ? 1 : 2;
+    const Blk& b = r.b;
+    const int lenD = b.n[D] + 2;
+    int p[3];
+    p[TA] = (int)(t % b.N[TA]);
+    const long q = t / b.N[TA];
+    p[TB] = (int)(q % b.N[TB]);
+    const int ch = (int)(q / b.N[TB]);
+    const int i0 = b.g - 1 + ch * RCHUNK;
+    const int i1 = min(b.g - 1 + lenD, i0 + RCHUNK);
+    p[D] = i0;
+    const long st = stride(b, D);
+    const long c0 = lin(b, p[0], p[1], p[2]);
+    const double* src[NREC] = {r.P.f[0], r.P.f[1], r.w.uvel, r.w.uvel + b.V, r.w.uvel + 2 * b.V,
+                               r.w.bc + T1 * b.V, r.w.bc + T2 * b.V};
+    for (int v = 0; v < NREC; v++) {
+      const double* __restrict__ a = src[v];
+      long c = c0;
+      double s[5] = {a[c - 2 * st], a[c - st], a[c], a[c + st], a[c + 2 * st]};
+      double k0 = wenoz_curv(s[0], s[1], s[2]), k1 = wenoz_curv(s[1], s[2], s[3]), k2 = wenoz_curv(s[2], s[3], s[4]);
+      for (int i = i0; i < i1; i++) {
+        const double t0b = s[0] - 4.0 * s[1] + 3.0 * s[2], t1b = s[1] - s[3], t2b = 3.0 * s[2] - 4.0 * s[3] + s[4];
+        const double e0 = k0 + 0.25 * t0b * t0b + 1e-40;
+        const double e1 = k1 + 0.25 * t1b * t1b + 1e-40;
+        const double e2 = k2 + 0.25 * t2b * t2b + 1e-40;
+        double l, h;
+        wenoz_from_indicators(s, e0, e1, e2, l, h);
+        r.w.rec[v * b.V + c] = l;
+        r.w.rec[(NREC + v) * b.V + c] = h;
+        if (i + 1 < i1) {
+          s[0] = s[1];
+          s[1] = s[2];
+          s[2] = s[3];
+          s[3] = s[4];
+          s[4] = a[c + 3 * st];
+          k0 = k1;
+          k1 = k2;
+          k2 = wenoz_curv(s[2], s[3], s[4]);
+          c += st;
+        }
+      }
+    }
+  }
+};
 
 // UCT edge inputs: for the faces normal to DF, the PPM lower and upper values along DR (chunked, sliding
 // stencil as in ReconPPM) of the upwind velocity v~bar^DR and of the face field B~^DF, over the faces the edges
@@ -871,7 +923,7 @@ template <int D, class T>
 static void seq_dir(const T& t, const StageConsts& k, int recon, cudaStream_t s) {
   if (recon == 0) launch<Recon<D, 0>>(t, k, KIND_RECON_X + D, s);
   else if (recon == 1) launch<ReconPPM<D>>(t, k, KIND_RCHUNK_X + D, s);
-  else launch<Recon<D, 2>>(t, k, KIND_RECON_X + D, s);
+  else launch<ReconWENO<D>>(t, k, KIND_RCHUNK_X + D, s);
   const bool mark = g_prof.on && g_prof.n < g_prof.cap && !capturing(s);
   if (mark) cudaEventRecord(g_prof.ev[2 * g_prof.n], s);
   launch<Faces<D>>(t, k, KIND_FACES_X + D, s);
