@@ -86,6 +86,10 @@ def lib():
         L.oracle_recon_flops.argtypes = [ctypes.c_int, _P, _P]
         L.oracle_point_sources.argtypes = [ctypes.POINTER(OParams), _P, _P, _P, _P, _P, _P, _P]
         L.oracle_grid_sources.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP]
+        L.oracle_stage_jvp.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP, _PP,
+                                       _PP, ctypes.c_double]
+        L.oracle_rk4_jvp.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP, _PP, _PP,
+                                     ctypes.c_double]
     return _lib
 
 
@@ -205,6 +209,29 @@ def rk4_step(w, M, U, P, dt=None, params=None):
         tot = st if tot is None else {k: tot[k] + st[k] for k in tot}
         Us = Unext
     return Us, tot
+
+
+def stage_jvp(w, M, U, dU, P, dt=None, params=None):
+    """(L, J dU): the stage operator L(U) = RHS(ghost fill U, recovery, ghost fill P) and its derivative in
+    the direction dU, by forward-mode dual numbers (the recovery differentiated at its root).  U and dU are
+    read only (ghost filled on copies); P holds the recovery's guess and receives the primitives."""
+    L = np.zeros((9,) + w.shape)
+    JL = np.zeros((9,) + w.shape)
+    lib().oracle_stage_jvp(ctypes.byref(params_struct(params or w.params)), ctypes.byref(block_struct(w)),
+                           _ptrs(M), _ptrs(np.ascontiguousarray(U)), _ptrs(np.ascontiguousarray(dU)), _ptrs(P),
+                           _ptrs(L), _ptrs(JL), float(dt if dt is not None else w.dt))
+    return L, JL
+
+
+def rk4_jvp(w, M, U, dU, P, dt=None, params=None):
+    """(U_next, J dU): one RK4 step as rk4_step forms it and its derivative in the direction dU (owned
+    ranges); U and dU are read only, P holds the guess and receives the last stage's primitives."""
+    U1 = np.zeros((9,) + w.shape)
+    JU1 = np.zeros((9,) + w.shape)
+    lib().oracle_rk4_jvp(ctypes.byref(params_struct(params or w.params)), ctypes.byref(block_struct(w)),
+                         _ptrs(M), _ptrs(np.ascontiguousarray(U)), _ptrs(np.ascontiguousarray(dU)), _ptrs(P),
+                         _ptrs(U1), _ptrs(JU1), float(dt if dt is not None else w.dt))
+    return U1, JU1
 
 
 def point_prim2con(params, m16, prim5, B3):

@@ -6,8 +6,9 @@
 // never calls it.
 //
 // Style: every step is written out literally in the order the paper states it, per cell / per face /
-// per edge, with temporaries in full-size arrays and no fusion, hoisting or blocking.  Pointwise physics is
-// templated on the scalar type R so that a flop-counting type can be substituted (R = double for results).
+// per edge, with temporaries in full-size arrays and no fusion, hoisting or blocking.  The physics and the
+// stage's grid steps are templated on the scalar type R: R = double for results, a flop-counting type for the
+// algorithmic counts, and a one-direction dual number for Jacobian-vector products of the stage operator.
 // Citations name the paper's sections and equation labels.
 //
 // Readings of the paper that this file takes (all listed in the repository's design notes):
@@ -69,6 +70,39 @@ inline double val(Fc a) { return a.v; }
 inline double val(double a) { return a; }
 inline bool finite(double a) { return std::isfinite(a); }
 inline bool finite(Fc a) { return std::isfinite(a.v); }
+
+// Forward-mode dual number with one direction: value v and directional derivative d.  Comparisons act on the
+// value, so a branch contributes the derivative of the branch taken.
+struct Dual1 {
+  double v, d;
+  Dual1() : v(0.0), d(0.0) {}
+  Dual1(double x) : v(x), d(0.0) {}
+  Dual1(double x, double dx) : v(x), d(dx) {}
+};
+inline Dual1 operator+(Dual1 a, Dual1 b) { return Dual1(a.v + b.v, a.d + b.d); }
+inline Dual1 operator-(Dual1 a, Dual1 b) { return Dual1(a.v - b.v, a.d - b.d); }
+inline Dual1 operator*(Dual1 a, Dual1 b) { return Dual1(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual1 operator/(Dual1 a, Dual1 b) {
+  const double q = a.v / b.v;
+  return Dual1(q, (a.d - q * b.d) / b.v);
+}
+inline Dual1 operator-(Dual1 a) { return Dual1(-a.v, -a.d); }
+inline Dual1& operator+=(Dual1& a, Dual1 b) { a = a + b; return a; }
+inline Dual1& operator-=(Dual1& a, Dual1 b) { a = a - b; return a; }
+inline Dual1& operator*=(Dual1& a, Dual1 b) { a = a * b; return a; }
+inline bool operator<(Dual1 a, Dual1 b) { return a.v < b.v; }
+inline bool operator>(Dual1 a, Dual1 b) { return a.v > b.v; }
+inline bool operator<=(Dual1 a, Dual1 b) { return a.v <= b.v; }
+inline bool operator>=(Dual1 a, Dual1 b) { return a.v >= b.v; }
+inline bool operator==(Dual1 a, Dual1 b) { return a.v == b.v; }
+inline bool operator!=(Dual1 a, Dual1 b) { return a.v != b.v; }
+inline Dual1 sqrt(Dual1 a) {
+  const double r = std::sqrt(a.v);
+  return Dual1(r, a.d / (2.0 * r));
+}
+inline Dual1 fabs(Dual1 a) { return (a.v < 0.0) ? -a : a; }
+inline double val(Dual1 a) { return a.v; }
+inline bool finite(Dual1 a) { return std::isfinite(a.v); }
 using std::fabs;
 using std::sqrt;
 
@@ -260,6 +294,22 @@ static Metric3<double> metric_at_vertex(const Grid& G, const VertexMetric& vm, i
   const int p[3] = {i, j, k};
   const int half[3] = {0, 0, 0};
   return metric_at(G, vm, p, half);
+}
+
+// The frozen metric (and, below, its derivatives) as scalars R: they carry no derivative.
+template <class R> Metric3<R> lift(const Metric3<double>& m) {
+  Metric3<R> r;
+  r.alp = R(m.alp);
+  r.sqrtg = R(m.sqrtg);
+  for (int a = 0; a < 3; a++) {
+    r.beta[a] = R(m.beta[a]);
+    for (int b = 0; b < 3; b++) {
+      r.g[a][b] = R(m.g[a][b]);
+      r.K[a][b] = R(m.K[a][b]);
+      r.gu[a][b] = R(m.gu[a][b]);
+    }
+  }
+  return r;
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -483,10 +533,11 @@ template <class R> void hlle(const R FL[5], const R FR[5], const R UL[5], const 
 // Face solve: from the reconstructed left/right states and the face metric, the HLLE flux of the 5 hydro
 // variables and the data that upwind constrained transport needs at this face (Eq. uct1, uct2).
 
-struct FaceInput {
-  double rho[2], press[2], u[2][3], Bt[2][3];  // side 0 = left, 1 = right; u = W v; Bt: transverse B only
-  double Bn;                                    // densitised normal field at the face (staggered)
+template <class R> struct FaceInputT {
+  R rho[2], press[2], u[2][3], Bt[2][3];  // side 0 = left, 1 = right; u = W v; Bt: transverse B only
+  R Bn;                                    // densitised normal field at the face (staggered)
 };
+typedef FaceInputT<double> FaceInput;
 
 template <class R> struct FaceOut {
   R F[5];
@@ -495,7 +546,7 @@ template <class R> struct FaceOut {
   int iters;
 };
 
-template <class R> FaceOut<R> face_solve(const Metric3<R>& m, const FaceInput& in, double gamma, int d) {
+template <class R, class In> FaceOut<R> face_solve(const Metric3<R>& m, const In& in, double gamma, int d) {
   FaceOut<R> out;
   R U[2][5], F[2][5], lp[2], lm[2], vt[2][3];
   out.iters = 0;
@@ -791,7 +842,7 @@ static C2POut c2p_cell(const Metric3<double>& m, const C2PIn& in, const OParams&
 // Ghost zones (Sec. 3.8): periodic wrap, or copy of the nearest owned value (linear extrapolation for A).
 
 // stagger: 1 if the quantity is cell-like along `axis`, 0 if vertex-like.
-static void fill_axis(const Grid& G, double* f, int axis, int cell_like, bool linear) {
+template <class R> static void fill_axis(const Grid& G, R* f, int axis, int cell_like, bool linear) {
   const int n = G.n[axis], g = G.g, Nn = G.N[axis];
   const int lo = g;
   const int hi = (cell_like || G.bc[axis] == BC_PERIODIC) ? g + n - 1 : g + n;  // owned index range [lo, hi]
@@ -804,7 +855,7 @@ static void fill_axis(const Grid& G, double* f, int axis, int cell_like, bool li
         p[axis] = i;
         p[a1] = q1;
         p[a2] = q2;
-        double v;
+        R v;
         if (G.bc[axis] == BC_PERIODIC) {
           int src = lo + (((i - lo) % n) + n) % n;  // periodic image inside the owned range
           int q[3] = {p[0], p[1], p[2]};
@@ -817,8 +868,8 @@ static void fill_axis(const Grid& G, double* f, int axis, int cell_like, bool li
           q0[axis] = e0;
           q1v[axis] = e1;
           if (linear && hi > lo) {  // linear extrapolation needs two owned layers; one layer copies
-            const double f0 = f[G.at(q0)], f1 = f[G.at(q1v)];
-            v = f0 + (double)(i < lo ? lo - i : i - hi) * (f0 - f1);
+            const R f0 = f[G.at(q0)], f1 = f[G.at(q1v)];
+            v = f0 + R((double)(i < lo ? lo - i : i - hi)) * (f0 - f1);
           } else {
             v = f[G.at(q0)];
           }
@@ -831,12 +882,12 @@ static void fill_axis(const Grid& G, double* f, int axis, int cell_like, bool li
 static const int STATE_CELL_LIKE[9][3] = {{1, 1, 1}, {1, 1, 1}, {1, 1, 1}, {1, 1, 1}, {1, 1, 1},
                                           {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 0, 0}};
 
-static void ghost_fill_state(const Grid& G, double* const U[9]) {
+template <class R> static void ghost_fill_state(const Grid& G, R* const U[9]) {
   for (int axis = 0; axis < 3; axis++)
     for (int v = 0; v < 9; v++) fill_axis(G, U[v], axis, STATE_CELL_LIKE[v][axis], v >= 5 && v <= 7);
 }
 
-static void ghost_fill_prims(const Grid& G, double* const P[5]) {
+template <class R> static void ghost_fill_prims(const Grid& G, R* const P[5]) {
   for (int axis = 0; axis < 3; axis++)
     for (int v = 0; v < 5; v++) fill_axis(G, P[v], axis, 1, false);
 }
@@ -845,24 +896,26 @@ static void ghost_fill_prims(const Grid& G, double* const P[5]) {
 // Magnetic field from the vector potential (Sec. 3.4, Eq. BEulerian): B~^i = [ijk] d_j A_k on faces, by
 // second-order differences of the edge values.  Cell-centre B^i = (B~^i_- + B~^i_+) / (2 sqrt(gamma_c)).
 
-static void face_B(const Grid& G, const double* Ax, const double* Ay, const double* Az, Field Bf[3]) {
-  for (int d = 0; d < 3; d++) Bf[d].assign(G.size(), 0.0);
+template <class R>
+static void face_B(const Grid& G, const R* Ax, const R* Ay, const R* Az, std::vector<R> Bf[3]) {
+  for (int d = 0; d < 3; d++) Bf[d].assign(G.size(), R(0.0));
   const double ix = 1.0 / G.dx[0], iy = 1.0 / G.dx[1], iz = 1.0 / G.dx[2];
   for (int k = 0; k <= G.N[2]; k++)
     for (int j = 0; j <= G.N[1]; j++)
       for (int i = 0; i <= G.N[0]; i++) {
         const long c = G.at(i, j, k);
         if (j < G.N[1] && k < G.N[2])  // x-face (i, j+1/2, k+1/2)
-          Bf[0][c] = (Az[G.at(i, j + 1, k)] - Az[c]) * iy - (Ay[G.at(i, j, k + 1)] - Ay[c]) * iz;
+          Bf[0][c] = (Az[G.at(i, j + 1, k)] - Az[c]) * R(iy) - (Ay[G.at(i, j, k + 1)] - Ay[c]) * R(iz);
         if (i < G.N[0] && k < G.N[2])  // y-face (i+1/2, j, k+1/2)
-          Bf[1][c] = (Ax[G.at(i, j, k + 1)] - Ax[c]) * iz - (Az[G.at(i + 1, j, k)] - Az[c]) * ix;
+          Bf[1][c] = (Ax[G.at(i, j, k + 1)] - Ax[c]) * R(iz) - (Az[G.at(i + 1, j, k)] - Az[c]) * R(ix);
         if (i < G.N[0] && j < G.N[1])  // z-face (i+1/2, j+1/2, k)
-          Bf[2][c] = (Ay[G.at(i + 1, j, k)] - Ay[c]) * ix - (Ax[G.at(i, j + 1, k)] - Ax[c]) * iy;
+          Bf[2][c] = (Ay[G.at(i + 1, j, k)] - Ay[c]) * R(ix) - (Ax[G.at(i, j + 1, k)] - Ax[c]) * R(iy);
       }
 }
 
-static void centre_B(const Grid& G, const VertexMetric& vm, const Field Bf[3], Field Bc[3]) {
-  for (int d = 0; d < 3; d++) Bc[d].assign(G.size(), 0.0);
+template <class R>
+static void centre_B(const Grid& G, const VertexMetric& vm, const std::vector<R> Bf[3], std::vector<R> Bc[3]) {
+  for (int d = 0; d < 3; d++) Bc[d].assign(G.size(), R(0.0));
   for (int k = 0; k < G.N[2]; k++)
     for (int j = 0; j < G.N[1]; j++)
       for (int i = 0; i < G.N[0]; i++) {
@@ -870,7 +923,7 @@ static void centre_B(const Grid& G, const VertexMetric& vm, const Field Bf[3], F
         const long c = G.at(i, j, k);
         for (int d = 0; d < 3; d++) {
           const long c1 = c + G.s[d];
-          Bc[d][c] = 0.5 * (Bf[d][c] + Bf[d][c1]) / m.sqrtg;
+          Bc[d][c] = R(0.5) * (Bf[d][c] + Bf[d][c1]) / R(m.sqrtg);
         }
       }
 }
@@ -954,6 +1007,18 @@ static MetricDeriv<double> metric_deriv_at_centre(const Grid& G, const VertexMet
   return dm;
 }
 
+template <class R> MetricDeriv<R> lift_deriv(const MetricDeriv<double>& d) {
+  MetricDeriv<R> r;
+  for (int a = 0; a < 3; a++) {
+    r.dalp[a] = R(d.dalp[a]);
+    for (int b = 0; b < 3; b++) {
+      r.dbeta[a][b] = R(d.dbeta[a][b]);
+      for (int c = 0; c < 3; c++) r.dg[a][b][c] = R(d.dg[a][b][c]);
+    }
+  }
+  return r;
+}
+
 // ------------------------------------------------------------------------------------------------------
 // The right-hand side of one stage (Sec. 3.9 workflow: reconstruct, Riemann solve, sources; Sec. 3.4 for
 // the potentials).  Inputs: state with ghosts filled and primitives with ghosts filled.
@@ -962,28 +1027,30 @@ struct RhsStats {
   unsigned long long speed_iters, faces;
 };
 
-struct FaceData {
-  Field F[5], vbar[3], cmax, cmin;
+template <class R> struct FaceDataT {
+  std::vector<R> F[5], vbar[3], cmax, cmin;
 };
 
-static void compute_faces(const Grid& G, const VertexMetric& vm, const OParams& P, double* const prim[5],
-                          const Field Bf[3], const Field Bc[3], int d, FaceData& fd, RhsStats* st) {
-  for (int v = 0; v < 5; v++) fd.F[v].assign(G.size(), 0.0);
-  for (int v = 0; v < 3; v++) fd.vbar[v].assign(G.size(), 0.0);
-  fd.cmax.assign(G.size(), 0.0);
-  fd.cmin.assign(G.size(), 0.0);
+template <class R>
+static void compute_faces(const Grid& G, const VertexMetric& vm, const OParams& P, R* const prim[5],
+                          const std::vector<R> Bf[3], const std::vector<R> Bc[3], int d, FaceDataT<R>& fd,
+                          RhsStats* st) {
+  for (int v = 0; v < 5; v++) fd.F[v].assign(G.size(), R(0.0));
+  for (int v = 0; v < 3; v++) fd.vbar[v].assign(G.size(), R(0.0));
+  fd.cmax.assign(G.size(), R(0.0));
+  fd.cmin.assign(G.size(), R(0.0));
   // reconstructed variables at every cell: rho, p, u^x, u^y, u^z (u = W v) and the centre B
-  Field cellvar[8];
-  for (int v = 0; v < 8; v++) cellvar[v].assign(G.size(), 0.0);
+  std::vector<R> cellvar[8];
+  for (int v = 0; v < 8; v++) cellvar[v].assign(G.size(), R(0.0));
   for (int k = 0; k < G.N[2]; k++)
     for (int j = 0; j < G.N[1]; j++)
       for (int i = 0; i < G.N[0]; i++) {
         const long c = G.at(i, j, k);
         const Metric3<double> m = metric_at_centre(G, vm, i, j, k);
-        double v2 = 0.0;
+        R v2 = R(0.0);
         for (int a = 0; a < 3; a++)
-          for (int b = 0; b < 3; b++) v2 += m.g[a][b] * prim[2 + a][c] * prim[2 + b][c];
-        const double W = 1.0 / std::sqrt(1.0 - v2);
+          for (int b = 0; b < 3; b++) v2 += R(m.g[a][b]) * prim[2 + a][c] * prim[2 + b][c];
+        const R W = R(1.0) / sqrt(R(1.0) - v2);
         cellvar[0][c] = prim[0][c];
         cellvar[1][c] = prim[1][c];
         for (int a = 0; a < 3; a++) cellvar[2 + a][c] = W * prim[2 + a][c];
@@ -998,25 +1065,25 @@ static void compute_faces(const Grid& G, const VertexMetric& vm, const OParams& 
         p[a1] = q1;
         p[a2] = q2;
         const long fc = G.at(p);
-        FaceInput in;
+        FaceInputT<R> in;
         for (int s = 0; s < 2; s++) {
           // left state: upper face value of cell f-1; right state: lower face value of cell f
           const int cell = f - 1 + s;
-          double stencil[8][5];
+          R stencil[8][5];
           for (int t = 0; t < 5; t++) {
             int q[3] = {p[0], p[1], p[2]};
             q[d] = cell - 2 + t;
             const long cc = G.at(q);
             for (int v = 0; v < 8; v++) stencil[v][t] = cellvar[v][cc];
           }
-          double rec[8];
+          R rec[8];
           for (int v = 0; v < 8; v++) {
             if (v >= 5 && v - 5 == d) {
-              rec[v] = 0.0;  // normal B is the staggered face value, not reconstructed
+              rec[v] = R(0.0);  // normal B is the staggered face value, not reconstructed
               continue;
             }
-            double aL, aR;
-            recon_cell<double>(P.recon, stencil[v], &aL, &aR);
+            R aL, aR;
+            recon_cell<R>(P.recon, stencil[v], &aL, &aR);
             rec[v] = (s == 0) ? aR : aL;
           }
           in.rho[s] = rec[0];
@@ -1025,8 +1092,8 @@ static void compute_faces(const Grid& G, const VertexMetric& vm, const OParams& 
           for (int a = 0; a < 3; a++) in.Bt[s][a] = rec[5 + a];
         }
         in.Bn = Bf[d][fc];
-        const Metric3<double> m = metric_at_face(G, vm, d, p[0], p[1], p[2]);
-        FaceOut<double> o = face_solve<double>(m, in, P.gamma, d);
+        const Metric3<R> m = lift<R>(metric_at_face(G, vm, d, p[0], p[1], p[2]));
+        FaceOut<R> o = face_solve<R>(m, in, P.gamma, d);
         for (int v = 0; v < 5; v++) fd.F[v][fc] = o.F[v];
         for (int a = 0; a < 3; a++) fd.vbar[a][fc] = o.vbar[a];
         fd.cmax[fc] = o.cmax;
@@ -1040,31 +1107,32 @@ static void compute_faces(const Grid& G, const VertexMetric& vm, const OParams& 
 
 // PPM value at the interface between stencil positions 2 and 3 of f[0..5]: left = upper value of cell 2
 // (stencil 0..4), right = lower value of cell 3 (stencil 1..5).
-static void ppm_interface(const double f[6], double* L, double* R) {
-  double aL, aR;
-  recon_ppm<double>(f, &aL, &aR);
+template <class T> static void ppm_interface(const T f[6], T* L, T* R) {
+  T aL, aR;
+  recon_ppm<T>(f, &aL, &aR);
   *L = aR;
-  recon_ppm<double>(f + 1, &aL, &aR);
+  recon_ppm<T>(f + 1, &aL, &aR);
   *R = aL;
 }
 
-static double hll_edge(double ap, double am, double vL, double BL, double vR, double BR) {
-  const double den = ap + am;
-  if (den > 0.0) return (ap * vL * BL + am * vR * BR - ap * am * (BR - BL)) / den;
-  return 0.5 * (vL * BL + vR * BR);
+template <class T> static T hll_edge(T ap, T am, T vL, T BL, T vR, T BR) {
+  const T den = ap + am;
+  if (den > T(0.0)) return (ap * vL * BL + am * vR * BR - ap * am * (BR - BL)) / den;
+  return T(0.5) * (vL * BL + vR * BR);
 }
 
 // Upwind constrained transport (Sec. 3.4, Eqs. uct1, uct2, eq3.20) for the edge along e at vertex-index
 // position p, with (e, d1, d2) cyclic:  E_e = -HLL_d1(v^d1 B~^d2) + HLL_d2(v^d2 B~^d1), the products
 // reconstructed (PPM) to the edge from the faces normal to d2 (resp. d1), and a^d_+- at the edge the maximum
 // over the two d-faces sharing the edge.
-static double uct_E(const Grid& G, const FaceData fd[3], const Field Bf[3], int e, const int p[3]) {
+template <class R>
+static R uct_E(const Grid& G, const FaceDataT<R> fd[3], const std::vector<R> Bf[3], int e, const int p[3]) {
   const int d1 = (e + 1) % 3, d2 = (e + 2) % 3;
-  double term[2];
+  R term[2];
   for (int t = 0; t < 2; t++) {
     const int dr = (t == 0) ? d1 : d2;    // direction of reconstruction / upwinding
     const int df = (t == 0) ? d2 : d1;    // normal of the faces that carry the data
-    double vs[6], bs[6];
+    R vs[6], bs[6];
     for (int s = 0; s < 6; s++) {
       int q[3] = {p[0], p[1], p[2]};
       q[dr] = p[dr] - 3 + s;
@@ -1072,15 +1140,15 @@ static double uct_E(const Grid& G, const FaceData fd[3], const Field Bf[3], int 
       vs[s] = fd[df].vbar[dr][c];
       bs[s] = Bf[df][c];
     }
-    double vL, vR, BL, BR;
+    R vL, vR, BL, BR;
     ppm_interface(vs, &vL, &vR);
     ppm_interface(bs, &BL, &BR);
     // speeds along dr: the two dr-faces sharing the edge are at p - e_df and p
     int q0[3] = {p[0], p[1], p[2]};
     q0[df] -= 1;
     const long c0 = G.at(q0), c1 = G.at(p);
-    const double ap = std::fmax(fd[dr].cmax[c0], fd[dr].cmax[c1]);
-    const double am = std::fmax(fd[dr].cmin[c0], fd[dr].cmin[c1]);
+    const R ap = rmax(fd[dr].cmax[c0], fd[dr].cmax[c1]);
+    const R am = rmax(fd[dr].cmin[c0], fd[dr].cmin[c1]);
     term[t] = hll_edge(ap, am, vL, BL, vR, BR);
   }
   return -term[0] + term[1];
@@ -1090,12 +1158,13 @@ struct RhsOut {
   double* const* dU;  // 9 fields (D, Sx, Sy, Sz, tau at cells; Ax, Ay, Az at edges; Psi at vertices)
 };
 
-static void rhs(const Grid& G, const VertexMetric& vm, const OParams& P, double dt, double* const U[9],
-                double* const prim[5], double* const dU[9], RhsStats* st) {
-  Field Bf[3], Bc[3];
+template <class R>
+static void rhs(const Grid& G, const VertexMetric& vm, const OParams& P, double dt, R* const U[9],
+                R* const prim[5], R* const dU[9], RhsStats* st) {
+  std::vector<R> Bf[3], Bc[3];
   face_B(G, U[5], U[6], U[7], Bf);
   centre_B(G, vm, Bf, Bc);
-  FaceData fd[3];
+  FaceDataT<R> fd[3];
   for (int d = 0; d < 3; d++) compute_faces(G, vm, P, prim, Bf, Bc, d, fd[d], st);
   const int g = G.g;
   // hydro: flux divergence plus sources at interior cells
@@ -1103,42 +1172,42 @@ static void rhs(const Grid& G, const VertexMetric& vm, const OParams& P, double 
     for (int j = g; j < g + G.n[1]; j++)
       for (int i = g; i < g + G.n[0]; i++) {
         const long c = G.at(i, j, k);
-        double r[5] = {0, 0, 0, 0, 0};
+        R r[5] = {R(0.0), R(0.0), R(0.0), R(0.0), R(0.0)};
         for (int d = 0; d < 3; d++) {
           const long c1 = c + G.s[d];
-          for (int v = 0; v < 5; v++) r[v] -= (fd[d].F[v][c1] - fd[d].F[v][c]) / G.dx[d];
+          for (int v = 0; v < 5; v++) r[v] -= (fd[d].F[v][c1] - fd[d].F[v][c]) / R(G.dx[d]);
         }
-        const Metric3<double> m = metric_at_centre(G, vm, i, j, k);
-        const MetricDeriv<double> dm = metric_deriv_at_centre(G, vm, i, j, k);
-        Prim<double> pr;
+        const Metric3<R> m = lift<R>(metric_at_centre(G, vm, i, j, k));
+        const MetricDeriv<R> dm = lift_deriv<R>(metric_deriv_at_centre(G, vm, i, j, k));
+        Prim<R> pr;
         pr.rho = prim[0][c];
         pr.press = prim[1][c];
-        pr.eps = pr.press / ((P.gamma - 1.0) * pr.rho);
+        pr.eps = pr.press / (R(P.gamma - 1.0) * pr.rho);
         for (int a = 0; a < 3; a++) {
           pr.vel[a] = prim[2 + a][c];
           pr.B[a] = Bc[a][c];
         }
-        double src[5];
-        source_terms<double>(m, dm, pr, src);
+        R src[5];
+        source_terms<R>(m, dm, pr, src);
         for (int v = 0; v < 5; v++) dU[v][c] = r[v] + src[v];
       }
   // potentials: G_A and F_Psi at vertices, from the vertex average of the edge A_j (Sec. 3.4)
-  Field GA(G.size(), 0.0), FPsi[3];
-  for (int d = 0; d < 3; d++) FPsi[d].assign(G.size(), 0.0);
+  std::vector<R> GA(G.size(), R(0.0)), FPsi[3];
+  for (int d = 0; d < 3; d++) FPsi[d].assign(G.size(), R(0.0));
   const bool lorenz = (P.gauge == GAUGE_LORENZ);
   for (int k = 1; k <= G.N[2]; k++)
     for (int j = 1; j <= G.N[1]; j++)
       for (int i = 1; i <= G.N[0]; i++) {
         const long c = G.at(i, j, k);
-        const Metric3<double> m = metric_at_vertex(G, vm, i, j, k);
-        double Av[3];
-        for (int a = 0; a < 3; a++) Av[a] = 0.5 * (U[5 + a][c - G.s[a]] + U[5 + a][c]);
-        const double psi = U[8][c];
-        double bA = 0.0;
+        const Metric3<R> m = lift<R>(metric_at_vertex(G, vm, i, j, k));
+        R Av[3];
+        for (int a = 0; a < 3; a++) Av[a] = R(0.5) * (U[5 + a][c - G.s[a]] + U[5 + a][c]);
+        const R psi = U[8][c];
+        R bA = R(0.0);
         for (int a = 0; a < 3; a++) bA += m.beta[a] * Av[a];
-        GA[c] = lorenz ? (m.alp * psi / m.sqrtg - bA) : 0.0;
+        GA[c] = lorenz ? (m.alp * psi / m.sqrtg - bA) : R(0.0);
         for (int a = 0; a < 3; a++) {
-          double Aup = m.gu[a][0] * Av[0] + m.gu[a][1] * Av[1] + m.gu[a][2] * Av[2];
+          R Aup = m.gu[a][0] * Av[0] + m.gu[a][1] * Av[1] + m.gu[a][2] * Av[2];
           FPsi[a][c] = m.alp * m.sqrtg * Aup - m.beta[a] * psi;
         }
       }
@@ -1154,8 +1223,8 @@ static void rhs(const Grid& G, const VertexMetric& vm, const OParams& P, double 
         for (int i = lo[0]; i <= hi[0]; i++) {
           const int p[3] = {i, j, k};
           const long c = G.at(p);
-          const double E = uct_E(G, fd, Bf, e, p);
-          const double dG = (GA[c + G.s[e]] - GA[c]) / G.dx[e];
+          const R E = uct_E(G, fd, Bf, e, p);
+          const R dG = (GA[c + G.s[e]] - GA[c]) / R(G.dx[e]);
           dU[5 + e][c] = -E - dG;
         }
   }
@@ -1166,12 +1235,12 @@ static void rhs(const Grid& G, const VertexMetric& vm, const OParams& P, double 
       for (int i = g; i <= g + G.n[0]; i++) {
         const long c = G.at(i, j, k);
         if (!lorenz) {
-          dU[8][c] = 0.0;
+          dU[8][c] = R(0.0);
           continue;
         }
-        double div = 0.0;
-        for (int a = 0; a < 3; a++) div += (FPsi[a][c + G.s[a]] - FPsi[a][c - G.s[a]]) / (2.0 * G.dx[a]);
-        dU[8][c] = -div - xi * vm.f[0][c] * U[8][c];
+        R div = R(0.0);
+        for (int a = 0; a < 3; a++) div += (FPsi[a][c + G.s[a]] - FPsi[a][c - G.s[a]]) / R(2.0 * G.dx[a]);
+        dU[8][c] = -div - R(xi * vm.f[0][c]) * U[8][c];
       }
 }
 
@@ -1301,6 +1370,116 @@ static void rk_stage(const Grid& G, const VertexMetric& vm, const OParams& P, in
   }
 }
 
+// ------------------------------------------------------------------------------------------------------
+// Jacobian-vector products of the stage operator L(U) = RHS(ghost fill, recovery, primitive ghost fill) and
+// of one RK4 step, in the direction dU, by the one-direction dual number.  The recovery keeps its values from
+// c2p_cell (the recovery above, as it stands) and takes its derivative from the implicit-function theorem:
+// one Noble Newton step in dual arithmetic from the converged root (z, v^2), whose value change is ~0 and
+// whose derivative is -J^{-1} (df / dinputs) (the Palenzuela root satisfies the same two equations).  Cells
+// set to the atmosphere keep constant primitives; their conserved variables are reset as con2prim does.
+
+static void con2prim_jvp(const Grid& G, const VertexMetric& vm, const OParams& P, Dual1* const U[9],
+                         Dual1* const prim[5], signed char* flags) {
+  std::vector<Dual1> Bf[3], Bc[3];
+  face_B(G, U[5], U[6], U[7], Bf);
+  centre_B(G, vm, Bf, Bc);
+  const int g = G.g;
+  for (int k = g; k < g + G.n[2]; k++)
+    for (int j = g; j < g + G.n[1]; j++)
+      for (int i = g; i < g + G.n[0]; i++) {
+        const long c = G.at(i, j, k);
+        const Metric3<double> m = metric_at_centre(G, vm, i, j, k);
+        C2PIn in;
+        in.Dtilde = U[0][c].v;
+        in.D = U[0][c].v / m.sqrtg;
+        for (int a = 0; a < 3; a++) in.S[a] = U[1 + a][c].v / m.sqrtg;
+        in.tau = U[4][c].v / m.sqrtg;
+        for (int a = 0; a < 3; a++) in.B[a] = Bc[a][c].v;
+        in.guess_rho = prim[0][c].v;
+        in.guess_press = prim[1][c].v;
+        for (int a = 0; a < 3; a++) in.guess_vel[a] = prim[2 + a][c].v;
+        const C2POut o = c2p_cell(m, in, P);
+        if (flags) flags[c] = (signed char)o.flag;
+        double dr = 0.0, dp = 0.0, dv[3] = {0.0, 0.0, 0.0};
+        if (o.flag == 0 || o.flag == 1) {
+          const Dual1 sg(m.sqrtg);
+          const Dual1 D = U[0][c] / sg, tau = U[4][c] / sg;
+          Dual1 S[3], B[3];
+          for (int a = 0; a < 3; a++) {
+            S[a] = U[1 + a][c] / sg;
+            B[a] = Bc[a][c];
+          }
+          Dual1 S2(0.0), B2(0.0), BS(0.0);
+          for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) {
+              S2 += Dual1(m.gu[a][b]) * S[a] * S[b];
+              B2 += Dual1(m.g[a][b]) * B[a] * B[b];
+            }
+          for (int a = 0; a < 3; a++) BS += B[a] * S[a];
+          // the root from the recovered primitives: z = rho h W^2, v^2
+          double v2 = 0.0;
+          for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) v2 += m.g[a][b] * o.vel[a] * o.vel[b];
+          const double W = 1.0 / std::sqrt(1.0 - v2);
+          const double eps = o.press / ((P.gamma - 1.0) * o.rho);
+          const double z = o.rho * (1.0 + eps + o.press / o.rho) * W * W;
+          Dual1 f[2], J[2][2];
+          noble_residual<Dual1>(Dual1(z), Dual1(v2), D, tau, S2, B2, BS, P.gamma, f, J);
+          const Dual1 det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+          const Dual1 zd = Dual1(z) + (-f[0] * J[1][1] + J[0][1] * f[1]) / det;
+          const Dual1 v2d = Dual1(v2) + (-J[0][0] * f[1] + J[1][0] * f[0]) / det;
+          const Dual1 Wd = Dual1(1.0) / sqrt(Dual1(1.0) - v2d);
+          const Dual1 rhod = D / Wd;
+          const Dual1 epsd = (zd / (rhod * Wd * Wd) - Dual1(1.0)) / Dual1(P.gamma);
+          const Dual1 pd = Dual1(P.gamma - 1.0) * rhod * epsd;
+          dr = rhod.d;
+          dp = pd.d;
+          for (int a = 0; a < 3; a++) {  // Eq. (Noble2D v)
+            Dual1 Su(0.0);
+            for (int b = 0; b < 3; b++) Su += Dual1(m.gu[a][b]) * S[b];
+            dv[a] = (Su / (zd + B2) + BS * B[a] / (zd * (zd + B2))).d;
+          }
+        }
+        prim[0][c] = Dual1(o.rho, dr);
+        prim[1][c] = Dual1(o.press, dp);
+        for (int a = 0; a < 3; a++) prim[2 + a][c] = Dual1(o.vel[a], dv[a]);
+        if (o.reset) {  // as con2prim: conserved variables from the atmosphere primitives, B kept (Sec. 3.6)
+          Prim<Dual1> pr;
+          pr.rho = Dual1(o.rho);
+          pr.press = Dual1(o.press);
+          pr.eps = Dual1(o.press / ((P.gamma_atm - 1.0) * o.rho));
+          for (int a = 0; a < 3; a++) {
+            pr.vel[a] = Dual1(0.0);
+            pr.B[a] = Bc[a][c];
+          }
+          const Metric3<Dual1> md = lift<Dual1>(m);
+          const Cons<Dual1> uc = prim2con(md, pr, comoving(md, pr));
+          U[0][c] = uc.D;
+          for (int a = 0; a < 3; a++) U[1 + a][c] = uc.S[a];
+          U[4][c] = uc.tau;
+        }
+      }
+}
+
+typedef std::vector<std::vector<Dual1>> DualFields;
+
+static DualFields dual_fields(int n, long size) { return DualFields(n, std::vector<Dual1>(size)); }
+
+template <int N> static void ptrs_of(DualFields& f, Dual1* out[N]) {
+  for (int v = 0; v < N; v++) out[v] = f[v].data();
+}
+
+// k = L(Y) with its derivative (Y: 9 dual fields, ghosts filled here; prim: 5 dual fields, guess in, out)
+static void stage_rhs_jvp(const Grid& G, const VertexMetric& vm, const OParams& P, double dt, Dual1* const Y[9],
+                          Dual1* const prim[5], Dual1* const k[9]) {
+  ghost_fill_state(G, Y);
+  con2prim_jvp(G, vm, P, Y, prim, nullptr);
+  ghost_fill_prims(G, prim);
+  for (int v = 0; v < 9; v++)
+    for (long c = 0; c < G.size(); c++) k[v][c] = Dual1(0.0);
+  rhs(G, vm, P, dt, Y, prim, k, (RhsStats*)nullptr);
+}
+
 }  // namespace asterx_oracle
 
 // ------------------------------------------------------------------------------------------------------
@@ -1363,6 +1542,86 @@ void oracle_rk_stage(const OParams* p, const OBlock* b, const double* const* met
                      double* const* prim, signed char* flags, OStats* stats) {
   Grid G(*b);
   rk_stage(G, vmetric(metric), *p, stage, dt, Un, Us, Unext, Uacc, prim, flags, stats);
+}
+
+// L(U) and its derivative in direction dir (9 fields each; U's ghosts are filled on a copy).  prim: the
+// recovery's guess in, the recovered primitives out.
+void oracle_stage_jvp(const OParams* p, const OBlock* b, const double* const* metric, const double* const* U,
+                      const double* const* dir, double* const* prim, double* const* L, double* const* JL,
+                      double dt) {
+  Grid G(*b);
+  VertexMetric vm = vmetric(metric);
+  DualFields Y = dual_fields(9, G.size()), Pd = dual_fields(5, G.size()), k = dual_fields(9, G.size());
+  for (int v = 0; v < 9; v++)
+    for (long c = 0; c < G.size(); c++) Y[v][c] = Dual1(U[v][c], dir[v][c]);
+  for (int v = 0; v < 5; v++)
+    for (long c = 0; c < G.size(); c++) Pd[v][c] = Dual1(prim[v][c]);
+  Dual1 *Yp[9], *Pp[5], *kp[9];
+  ptrs_of<9>(Y, Yp);
+  ptrs_of<5>(Pd, Pp);
+  ptrs_of<9>(k, kp);
+  stage_rhs_jvp(G, vm, *p, dt, Yp, Pp, kp);
+  for (int v = 0; v < 9; v++)
+    for (long c = 0; c < G.size(); c++) {
+      L[v][c] = k[v][c].v;
+      JL[v][c] = k[v][c].d;
+    }
+  for (int v = 0; v < 5; v++)
+    for (long c = 0; c < G.size(); c++) prim[v][c] = Pd[v][c].v;
+}
+
+// One classical RK4 step of U (9 fields, ghosts filled) and its derivative in direction dir: U1, JU1 on the
+// owned ranges (the stages as oracle_rk_stage forms them).  prim: guess in, last recovery out.
+void oracle_rk4_jvp(const OParams* p, const OBlock* b, const double* const* metric, const double* const* U,
+                    const double* const* dir, double* const* prim, double* const* U1, double* const* JU1,
+                    double dt) {
+  Grid G(*b);
+  VertexMetric vm = vmetric(metric);
+  DualFields Un = dual_fields(9, G.size()), Ys = dual_fields(9, G.size()), acc = dual_fields(9, G.size());
+  DualFields k = dual_fields(9, G.size()), Pd = dual_fields(5, G.size());
+  for (int v = 0; v < 9; v++)
+    for (long c = 0; c < G.size(); c++) Un[v][c] = Dual1(U[v][c], dir[v][c]);
+  for (int v = 0; v < 5; v++)
+    for (long c = 0; c < G.size(); c++) Pd[v][c] = Dual1(prim[v][c]);
+  Ys = Un;
+  Dual1 *Ysp[9], *Pp[5], *kp[9];
+  ptrs_of<5>(Pd, Pp);
+  ptrs_of<9>(k, kp);
+  static const double cnext[3] = {0.5, 0.5, 1.0};
+  static const double bw[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  for (int stage = 0; stage < 4; stage++) {
+    DualFields next = Ys;  // entries outside the owned ranges keep the stage state's values
+    ptrs_of<9>(Ys, Ysp);
+    stage_rhs_jvp(G, vm, *p, dt, Ysp, Pp, kp);
+    if (stage == 0) Un = Ys;  // the first stage fills U_n's ghosts (and U_s = U_n)
+    for (int v = 0; v < 9; v++) {
+      int lo[3], hi[3];
+      owned_range(G, v, lo, hi);
+      for (int kk = lo[2]; kk <= hi[2]; kk++)
+        for (int j = lo[1]; j <= hi[1]; j++)
+          for (int i = lo[0]; i <= hi[0]; i++) {
+            const long c = G.at(i, j, kk);
+            const Dual1 kv = k[v][c];
+            if (stage == 0) {
+              acc[v][c] = Dual1(bw[0] * dt) * kv;
+              next[v][c] = Un[v][c] + Dual1(cnext[0] * dt) * kv;
+            } else if (stage < 3) {
+              acc[v][c] = acc[v][c] + Dual1(bw[stage] * dt) * kv;
+              next[v][c] = Un[v][c] + Dual1(cnext[stage] * dt) * kv;
+            } else {
+              next[v][c] = Un[v][c] + acc[v][c] + Dual1(bw[3] * dt) * kv;
+            }
+          }
+    }
+    Ys = next;
+  }
+  for (int v = 0; v < 9; v++)
+    for (long c = 0; c < G.size(); c++) {
+      U1[v][c] = Ys[v][c].v;
+      JU1[v][c] = Ys[v][c].d;
+    }
+  for (int v = 0; v < 5; v++)
+    for (long c = 0; c < G.size(); c++) prim[v][c] = Pd[v][c].v;
 }
 
 // Algorithmic flop count of the face solve (Sec. 3.3: prim->cons, fluxes, magnetosonic speeds, HLLE and the

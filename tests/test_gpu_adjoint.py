@@ -157,6 +157,65 @@ def test_rk4_step_adjoint_matches_central_differences(name):
     check_vjp(prob, prob.rk4, lam, full_entries=False)
 
 
+def check_against_jvp(prob, mu, lam, jvp, entries_full=True, rtol=1e-10):
+    """<lam, d> against <mu, J d> with J d from the oracle's dual-number derivative (no truncation error: the two
+    agree to rounding and the recovery's root tolerance): one random direction over every independent entry, one
+    per input group, then unit directions at the sampled entries of every field (lam_i = <mu, J e_i>)."""
+    w, U = prob.w, prob.U
+    dirs = [np.where(prob.mask, prob.r_v, 0.0) * prob.uscale[:, None, None, None]]
+    for grp in IN_GROUPS:
+        d = np.zeros_like(U)
+        for v in grp:
+            d[v] = dirs[0][v]
+        dirs.append(d)
+    worst = 0.0
+    for d in dirs:
+        Jd = jvp(d)
+        ad, ref = float(np.sum(lam * d)), float(np.sum(mu * Jd))
+        scale = max(float(np.sum(np.abs(lam * d))), float(np.sum(np.abs(mu * Jd))))
+        worst = max(worst, abs(ad - ref) / scale)
+        assert abs(ad - ref) <= rtol * scale, (ad, ref, scale)
+    for v in range(9):
+        for idx in sample_entries(w, v, entries_full):
+            d = np.zeros_like(U)
+            d[(v,) + idx] = 1.0
+            Jd = jvp(d)
+            ad, ref = float(lam[(v,) + idx]), float(np.sum(mu * Jd))
+            scale = max(float(np.sum(np.abs(mu * Jd))), 1e-300)
+            worst = max(worst, abs(ad - ref) / scale)
+            assert abs(ad - ref) <= rtol * scale, (v, idx, ad, ref, scale)
+    return worst
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_adjoint_equals_the_oracle_jvp(name):
+    need_gpu()
+    w = W.smooth_general(**CASES[name])
+    prob = Problem(w, seed=2206)
+    mu = prob.mu_for(prob.stage_rhs(prob.U))
+    case = GpuCase(w)
+    lam_d = case.solver.zeros_state()
+    case.solver.rhs_adjoint(case.dev(prob.U), case.dev(prob.P), case.dev(mu), lam_d, w.dt)
+    lam = case.host(lam_d)
+    worst = check_against_jvp(prob, mu, lam, lambda d: O.stage_jvp(w, prob.M, prob.U, d, prob.P.copy())[1])
+    print(f"{name}: largest relative difference {worst:.2e}")
+
+
+@pytest.mark.parametrize("name", ["wenoz_periodic_algebraic", "minmod_copy_lorenz"])
+def test_rk4_step_adjoint_equals_the_oracle_jvp(name):
+    need_gpu()
+    w = W.smooth_general(n=(10, 9, 8), **CASES[name])
+    prob = Problem(w, seed=2207)
+    mu = prob.mu_for(prob.rk4(prob.U))
+    case = GpuCase(w)
+    lam_d = case.dev(mu)
+    case.solver.rk4_step_adjoint(case.dev(prob.U), case.dev(prob.P), lam_d, w.dt)
+    lam = case.host(lam_d)
+    worst = check_against_jvp(prob, mu, lam, lambda d: O.rk4_jvp(w, prob.M, prob.U, d, prob.P.copy())[1],
+                              entries_full=False)
+    print(f"{name}: largest relative difference {worst:.2e}")
+
+
 def test_rhs_adjoint_is_linear_in_the_weights():
     """J^T (2 mu1 - 3 mu2) = 2 J^T mu1 - 3 J^T mu2 up to the summation order of the atomic accumulations."""
     need_gpu()
