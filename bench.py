@@ -52,10 +52,12 @@ def parse():
     ap.add_argument("--batch-blocks", type=int, default=512)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward measurement")
     ap.add_argument("--adjoint-n", type=int, default=64, help="cells per axis of the adjoint workload")
-    ap.add_argument("--profile-region", choices=("none", "forward", "adjoint", "batched"), default="none",
-                    help="bracket one extra forward RK4 step (main workload), one adjoint step, or one batched "
-                         "step and one step of the equal-volume block with cudaProfilerStart/Stop, for a "
-                         "profiler run with --profile-from-start off")
+    ap.add_argument("--no-coupling", action="store_true",
+                    help="skip the stress-energy tensor and time-dependent-metric step measurements")
+    ap.add_argument("--profile-region", choices=("none", "forward", "adjoint", "batched", "coupling"), default="none",
+                    help="bracket one extra forward RK4 step (main workload), one adjoint step, one batched "
+                         "step and one step of the equal-volume block, or one stress-energy tensor call with "
+                         "cudaProfilerStart/Stop, for a profiler run with --profile-from-start off")
     return ap.parse_args()
 
 
@@ -360,6 +362,55 @@ def run_adjoint(args, dev, stream):
                                   "max_abs_dJ_drho": grad_norm}}
 
 
+def run_coupling(args, s, U, P, M, w, dev, stream):
+    """Coupling to a spacetime solver on the benchmark block: T_{mu nu} at the (n+1)^3 owned vertices (asterx_tmunu:
+    face and centre field, u = W v, then the vertex kernel), and one RK4 step whose four stages each re-derive the
+    geometry from a stage metric (asterx_rk4_step_metrics) against the frozen-metric step."""
+    import torch
+
+    T = torch.zeros((10,) + tuple(U.shape[1:]), dtype=torch.float64, device=dev)
+    reps = max(3, min(args.steps * 4, 20))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.tmunu(U, P, T)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        s.tmunu(U, P, T)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_t = e0.elapsed_time(e1) / reps
+    if args.profile_region == "coupling":
+        torch.cuda.profiler.start()
+        s.tmunu(U, P, T)
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.stop()
+    finite = bool(torch.isfinite(T).all())
+    del T
+    metrics = [M, M, M, M]
+    s.rk4_step_metrics(U, P, w.dt, metrics)
+    torch.cuda.synchronize(dev)
+    steps = max(1, min(args.steps, 3))
+    e0.record(stream)
+    for _ in range(steps):
+        s.rk4_step_metrics(U, P, w.dt, metrics)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_dyn = e0.elapsed_time(e1) / steps
+    e0.record(stream)
+    for _ in range(steps):
+        s.rk4_step(U, P, w.dt)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_frozen = e0.elapsed_time(e1) / steps
+    nv = 1
+    for d in range(3):
+        nv *= w.n[d] + 1
+    return {"tmunu": {"vertices": nv, "ms": ms_t, "vertices_per_s": nv / (ms_t / 1e3), "finite": finite,
+                      "launches": 4},
+            "metric_step": {"ms_per_step": ms_dyn, "frozen_ms_per_step": ms_frozen,
+                            "overhead": ms_dyn / ms_frozen - 1.0, "steps": steps}}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -500,6 +551,8 @@ def run_ours(args):
                       "d2h_bytes_per_step": io_bytes},
               "gpu_launches": LAUNCHES_PER_STAGE * 4 * args.steps,
               "clocks": clk, "roofline": roofline, "c2p_counters_timed": c2p, "state_finite": finite}
+    if not args.no_coupling:
+        result["coupling"] = run_coupling(args, s, U, P, M, w, dev, stream)
     if not args.no_batched:
         result["batched"] = run_batched(args, dev, stream)
     if not args.no_adjoint:

@@ -161,6 +161,30 @@ asterx_status asterx_rk4_step_host(const asterx_params *p, const asterx_block *b
                                    double *const *h_U9, double *const *h_P5, asterx_state *dU, asterx_prims *dP,
                                    asterx_c2p_stats *stats, void *ws, size_t ws_bytes, asterx_stream stream);
 
+/* ---- coupling to a spacetime solver ----
+ *
+ * Stress-energy tensor T_{mu nu} (Eq. tmunu with both indices lowered by the 4-metric; T lives at vertices,
+ * Sec. 3.1), the matter input of a spacetime solver.  At every vertex g..g+n of each axis, the rest-mass
+ * density, pressure, u^i = W v^i (W from the cell's metric) and centre field B^i of the eight cells around the
+ * vertex are averaged to it and combined with the vertex metric of `metric` (alpha, beta^i, gamma_ij).  `ws`
+ * must be prepared from the same metric.  U's A and P must have their ghosts filled, as asterx_rk_stage leaves
+ * its stage state U_s and P.  Writes the 10 fields of T at those vertices and nowhere else. */
+typedef struct { double *tt, *tx, *ty, *tz, *xx, *xy, *xz, *yy, *yz, *zz; } asterx_tmunu_fields;
+asterx_status asterx_tmunu(const asterx_params *p, const asterx_block *blk, const asterx_metric *metric,
+                           const asterx_state *U, const asterx_prims *P, asterx_tmunu_fields *T, void *ws,
+                           size_t ws_bytes, asterx_stream stream);
+
+/* One RK4 step over a time-dependent metric: stage s = 0..3 runs on metric[s], the spacetime of that stage
+ * (t_n, t_n + dt/2, t_n + dt/2, t_n + dt for a prescribed metric; the spacetime solver's stage states when the
+ * two are integrated together), with the geometry re-derived as asterx_prepare does before each stage.  Each
+ * metric's K_ij must be the extrinsic curvature of its slicing (consistent with d gamma_ij / dt), which the
+ * source terms use.  Otherwise as asterx_rk4_step; the workspace ends prepared from metric[3].  `metric` is a
+ * HOST array of 4 pointers to metric sets (an entry may repeat). */
+asterx_status asterx_rk4_step_metrics(const asterx_params *p, const asterx_block *blk, double dt,
+                                      const asterx_metric *const *metric, asterx_state *U, asterx_prims *P,
+                                      signed char *flags, asterx_c2p_stats *stats, void *ws, size_t ws_bytes,
+                                      asterx_stream stream);
+
 /* ---- adjoint (vector-Jacobian products) ----
  *
  * Reverse-mode derivatives of the stage operator and of one RK4 step, for gradients of a scalar loss with

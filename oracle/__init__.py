@@ -86,6 +86,9 @@ def lib():
         L.oracle_recon_flops.argtypes = [ctypes.c_int, _P, _P]
         L.oracle_point_sources.argtypes = [ctypes.POINTER(OParams), _P, _P, _P, _P, _P, _P, _P]
         L.oracle_grid_sources.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP]
+        L.oracle_centre_metric.argtypes = [ctypes.POINTER(OBlock), _PP, _PP]
+        L.oracle_face_metric.argtypes = [ctypes.POINTER(OBlock), _PP, ctypes.c_int, _PP]
+        L.oracle_tmunu.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP]
         L.oracle_stage_jvp.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP, _PP,
                                        _PP, ctypes.c_double]
         L.oracle_rk4_jvp.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP, _PP, _PP,
@@ -211,6 +214,32 @@ def rk4_step(w, M, U, P, dt=None, params=None):
     return Us, tot
 
 
+def centre_metric(w, M):
+    """(53, ...) interpolated metric at every cell centre: alpha, beta^i, gamma_ij (6), gamma^ij (6), sqrt(gamma),
+    K_ij (6), d_i alpha (3), d_i beta^j (9), d_i gamma_jk (18)."""
+    out = np.zeros((53,) + w.shape)
+    lib().oracle_centre_metric(ctypes.byref(block_struct(w)), _ptrs(M), _ptrs(out))
+    return out
+
+
+def face_metric(w, M, d):
+    """(17, ...) interpolated metric at the faces normal to d: alpha, beta^i, gamma_ij, gamma^ij, sqrt(gamma)."""
+    out = np.zeros((17,) + w.shape)
+    lib().oracle_face_metric(ctypes.byref(block_struct(w)), _ptrs(M), int(d), _ptrs(out))
+    return out
+
+
+TMUNU_NAMES = ("tt", "tx", "ty", "tz", "xx", "xy", "xz", "yy", "yz", "zz")
+
+
+def tmunu(w, M, U, P, params=None):
+    """T_{mu nu} (10, ...) at the vertices g..g+n of every axis (zero elsewhere); U's A and P ghost-filled."""
+    T = np.zeros((10,) + w.shape)
+    lib().oracle_tmunu(ctypes.byref(params_struct(params or w.params)), ctypes.byref(block_struct(w)), _ptrs(M),
+                       _ptrs(U), _ptrs(P), _ptrs(T))
+    return T
+
+
 def stage_jvp(w, M, U, dU, P, dt=None, params=None):
     """(L, J dU): the stage operator L(U) = RHS(ghost fill U, recovery, ghost fill P) and its derivative in
     the direction dU, by forward-mode dual numbers (the recovery differentiated at its root).  U and dU are
@@ -232,6 +261,21 @@ def rk4_jvp(w, M, U, dU, P, dt=None, params=None):
                          _ptrs(M), _ptrs(np.ascontiguousarray(U)), _ptrs(np.ascontiguousarray(dU)), _ptrs(P),
                          _ptrs(U1), _ptrs(JU1), float(dt if dt is not None else w.dt))
     return U1, JU1
+
+
+def rk4_step_metrics(w, Ms, U, P, dt=None, params=None):
+    """One RK4 step whose stage s runs on the metric Ms[s] (a time-dependent spacetime sampled at the stage
+    times); otherwise as rk4_step."""
+    dt = float(dt if dt is not None else w.dt)
+    Uacc = np.zeros_like(U)
+    Us = U
+    tot = None
+    for s in range(4):
+        Unext = Us.copy()
+        _, st = rk_stage(w, Ms[s], s, dt, U, Us, Unext, Uacc, P, params)
+        tot = st if tot is None else {k: tot[k] + st[k] for k in tot}
+        Us = Unext
+    return Us, tot
 
 
 def point_prim2con(params, m16, prim5, B3):

@@ -1371,6 +1371,97 @@ static void rk_stage(const Grid& G, const VertexMetric& vm, const OParams& P, in
 }
 
 // ------------------------------------------------------------------------------------------------------
+// Stress-energy tensor at vertices (Eq. tmunu; T_{mu nu} is stored at vertices, Sec. 3.1).  The cell-centred
+// rest-mass density, pressure, u^i = W v^i (W from the cell's metric) and centre field B^i of the eight cells
+// around a vertex are averaged to it; W, v^i and the comoving field follow from the vertex metric, T^{mu nu}
+// is formed as in the source terms, and both indices are lowered with the 4-metric,
+// T_{mu nu} = g_{mu a} g_{nu b} T^{ab}.  Components in the order tt, tx, ty, tz, xx, xy, xz, yy, yz, zz.
+
+static void tmunu_vertices(const Grid& G, const VertexMetric& vm, const OParams& P, double* const U[9],
+                           double* const prim[5], double* const Tout[10]) {
+  std::vector<double> Bf[3], Bc[3];
+  face_B(G, U[5], U[6], U[7], Bf);
+  centre_B(G, vm, Bf, Bc);
+  const int g = G.g;
+  for (int k = g; k <= g + G.n[2]; k++)
+    for (int j = g; j <= g + G.n[1]; j++)
+      for (int i = g; i <= g + G.n[0]; i++) {
+        double rho = 0.0, press = 0.0, u[3] = {0.0, 0.0, 0.0}, B[3] = {0.0, 0.0, 0.0};
+        for (int ck = k - 1; ck <= k; ck++)
+          for (int cj = j - 1; cj <= j; cj++)
+            for (int ci = i - 1; ci <= i; ci++) {
+              const long c = G.at(ci, cj, ck);
+              const Metric3<double> mc = metric_at_centre(G, vm, ci, cj, ck);
+              double v2 = 0.0;
+              for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) v2 += mc.g[a][b] * prim[2 + a][c] * prim[2 + b][c];
+              const double Wc = 1.0 / std::sqrt(1.0 - v2);
+              rho += prim[0][c];
+              press += prim[1][c];
+              for (int a = 0; a < 3; a++) {
+                u[a] += Wc * prim[2 + a][c];
+                B[a] += Bc[a][c];
+              }
+            }
+        rho /= 8.0;
+        press /= 8.0;
+        for (int a = 0; a < 3; a++) {
+          u[a] /= 8.0;
+          B[a] /= 8.0;
+        }
+        const Metric3<double> m = metric_at_vertex(G, vm, i, j, k);
+        double u2 = 0.0;
+        for (int a = 0; a < 3; a++)
+          for (int b = 0; b < 3; b++) u2 += m.g[a][b] * u[a] * u[b];
+        const double W = std::sqrt(1.0 + u2);
+        Prim<double> pr;
+        pr.rho = rho;
+        pr.press = press;
+        pr.eps = press / ((P.gamma - 1.0) * rho);
+        for (int a = 0; a < 3; a++) {
+          pr.vel[a] = u[a] / W;
+          pr.B[a] = B[a];
+        }
+        const Comoving<double> cm = comoving(m, pr);
+        double u4[4], b4[4];
+        u4[0] = cm.u0;
+        b4[0] = cm.b0;
+        for (int a = 0; a < 3; a++) {
+          u4[a + 1] = cm.uup[a];
+          b4[a + 1] = cm.bup[a];
+        }
+        const double a2 = m.alp * m.alp;
+        double guu[4][4], gdd[4][4];  // inverse and covariant 4-metric
+        guu[0][0] = -1.0 / a2;
+        double betalow[3];
+        for (int a = 0; a < 3; a++) betalow[a] = m.g[a][0] * m.beta[0] + m.g[a][1] * m.beta[1] + m.g[a][2] * m.beta[2];
+        gdd[0][0] = -a2 + betalow[0] * m.beta[0] + betalow[1] * m.beta[1] + betalow[2] * m.beta[2];
+        for (int a = 0; a < 3; a++) {
+          guu[0][a + 1] = guu[a + 1][0] = m.beta[a] / a2;
+          gdd[0][a + 1] = gdd[a + 1][0] = betalow[a];
+          for (int b = 0; b < 3; b++) {
+            guu[a + 1][b + 1] = m.gu[a][b] - m.beta[a] * m.beta[b] / a2;
+            gdd[a + 1][b + 1] = m.g[a][b];
+          }
+        }
+        const double rhohb = pr.rho * cm.h + cm.b2;
+        const double ptot = pr.press + 0.5 * cm.b2;
+        double Tup[4][4];
+        for (int mu = 0; mu < 4; mu++)
+          for (int nu = 0; nu < 4; nu++) Tup[mu][nu] = rhohb * u4[mu] * u4[nu] + ptot * guu[mu][nu] - b4[mu] * b4[nu];
+        static const int IDX[10][2] = {{0, 0}, {0, 1}, {0, 2}, {0, 3}, {1, 1}, {1, 2}, {1, 3}, {2, 2}, {2, 3}, {3, 3}};
+        const long v = G.at(i, j, k);
+        for (int q = 0; q < 10; q++) {
+          const int mu = IDX[q][0], nu = IDX[q][1];
+          double t = 0.0;
+          for (int a = 0; a < 4; a++)
+            for (int b = 0; b < 4; b++) t += gdd[mu][a] * gdd[nu][b] * Tup[a][b];
+          Tout[q][v] = t;
+        }
+      }
+}
+
+// ------------------------------------------------------------------------------------------------------
 // Jacobian-vector products of the stage operator L(U) = RHS(ghost fill, recovery, primitive ghost fill) and
 // of one RK4 step, in the direction dU, by the one-direction dual number.  The recovery keeps its values from
 // c2p_cell (the recovery above, as it stands) and takes its derivative from the implicit-function theorem:
@@ -1542,6 +1633,67 @@ void oracle_rk_stage(const OParams* p, const OBlock* b, const double* const* met
                      double* const* prim, signed char* flags, OStats* stats) {
   Grid G(*b);
   rk_stage(G, vmetric(metric), *p, stage, dt, Un, Us, Unext, Uacc, prim, flags, stats);
+}
+
+// The interpolated metric (Sec. 3.2) at every cell centre of the padded block, for checks of precomputed
+// geometry elsewhere: 53 fields, alpha, beta^i (3), gamma_ij (6: xx, xy, xz, yy, yz, zz), gamma^ij (6),
+// sqrt(gamma), K_ij (6), d_i alpha (3), d_i beta^j (9, index 3 i + j), d_i gamma_jk (18, index 6 i + jk).
+void oracle_centre_metric(const OBlock* b, const double* const* metric, double* const* out) {
+  Grid G(*b);
+  VertexMetric vm = vmetric(metric);
+  for (int k = 0; k < G.N[2]; k++)
+    for (int j = 0; j < G.N[1]; j++)
+      for (int i = 0; i < G.N[0]; i++) {
+        const long c = G.at(i, j, k);
+        const Metric3<double> m = metric_at_centre(G, vm, i, j, k);
+        const MetricDeriv<double> dm = metric_deriv_at_centre(G, vm, i, j, k);
+        int q = 0;
+        out[q++][c] = m.alp;
+        for (int a = 0; a < 3; a++) out[q++][c] = m.beta[a];
+        for (int a = 0; a < 3; a++)
+          for (int e = a; e < 3; e++) out[q++][c] = m.g[a][e];
+        for (int a = 0; a < 3; a++)
+          for (int e = a; e < 3; e++) out[q++][c] = m.gu[a][e];
+        out[q++][c] = m.sqrtg;
+        for (int a = 0; a < 3; a++)
+          for (int e = a; e < 3; e++) out[q++][c] = m.K[a][e];
+        for (int d = 0; d < 3; d++) out[q++][c] = dm.dalp[d];
+        for (int d = 0; d < 3; d++)
+          for (int a = 0; a < 3; a++) out[q++][c] = dm.dbeta[d][a];
+        for (int d = 0; d < 3; d++)
+          for (int a = 0; a < 3; a++)
+            for (int e = a; e < 3; e++) out[q++][c] = dm.dg[d][a][e];
+      }
+}
+
+// The interpolated metric at the faces normal to d (index 0..N along d, cells across): 17 fields, alpha,
+// beta^i (3), gamma_ij (6), gamma^ij (6), sqrt(gamma).
+void oracle_face_metric(const OBlock* b, const double* const* metric, int d, double* const* out) {
+  Grid G(*b);
+  VertexMetric vm = vmetric(metric);
+  int hi[3] = {G.N[0] - 1, G.N[1] - 1, G.N[2] - 1};
+  hi[d] = G.N[d];
+  for (int k = 0; k <= hi[2]; k++)
+    for (int j = 0; j <= hi[1]; j++)
+      for (int i = 0; i <= hi[0]; i++) {
+        const long c = G.at(i, j, k);
+        const Metric3<double> m = metric_at_face(G, vm, d, i, j, k);
+        int q = 0;
+        out[q++][c] = m.alp;
+        for (int a = 0; a < 3; a++) out[q++][c] = m.beta[a];
+        for (int a = 0; a < 3; a++)
+          for (int e = a; e < 3; e++) out[q++][c] = m.g[a][e];
+        for (int a = 0; a < 3; a++)
+          for (int e = a; e < 3; e++) out[q++][c] = m.gu[a][e];
+        out[q++][c] = m.sqrtg;
+      }
+}
+
+// T_{mu nu} at the vertices g..g+n of every axis (U's A and the primitives ghost-filled); 10 output fields.
+void oracle_tmunu(const OParams* p, const OBlock* b, const double* const* metric, double* const* U,
+                  double* const* prim, double* const* T) {
+  Grid G(*b);
+  tmunu_vertices(G, vmetric(metric), *p, U, prim, T);
 }
 
 // L(U) and its derivative in direction dir (9 fields each; U's ghosts are filled on a copy).  prim: the

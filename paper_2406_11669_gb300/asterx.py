@@ -50,6 +50,10 @@ class Metric(ctypes.Structure):
                                                 "gyz", "gzz", "kxx", "kxy", "kxz", "kyy", "kyz", "kzz")]
 
 
+class TmunuFields(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("tt", "tx", "ty", "tz", "xx", "xy", "xz", "yy", "yz", "zz")]
+
+
 class BatchBlock(ctypes.Structure):
     _fields_ = [("blk", Block), ("metric", Metric), ("U", State), ("P", Prims)]
 
@@ -85,6 +89,8 @@ def lib():
         L.asterx_rk4_step.argtypes = [P, B, ctypes.c_double, S, Pr, vp, vp, vp, sz, st]
         L.asterx_rk4_step_host.argtypes = [P, B, ctypes.c_double, ctypes.POINTER(ctypes.c_void_p),
                                            ctypes.POINTER(ctypes.c_void_p), S, Pr, vp, vp, sz, st]
+        L.asterx_tmunu.argtypes = [P, B, M, S, Pr, ctypes.POINTER(TmunuFields), vp, sz, st]
+        L.asterx_rk4_step_metrics.argtypes = [P, B, ctypes.c_double, ctypes.POINTER(M), S, Pr, vp, vp, vp, sz, st]
         BB = ctypes.POINTER(BatchBlock)
         L.asterx_batch_workspace_size.restype = ctypes.c_size_t
         L.asterx_batch_workspace_size.argtypes = [BB, ctypes.c_int]
@@ -113,7 +119,8 @@ def lib():
         L.asterx_profile_disable.restype = None
         L.asterx_dfma_probe.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_long, st]
         for name in ("asterx_prepare", "asterx_prim2con", "asterx_con2prim", "asterx_fill_ghosts", "asterx_rhs",
-                     "asterx_rk_stage", "asterx_rk4_step", "asterx_rk4_step_host", "asterx_profile_enable",
+                     "asterx_rk_stage", "asterx_rk4_step", "asterx_rk4_step_host", "asterx_tmunu",
+                     "asterx_rk4_step_metrics", "asterx_profile_enable",
                      "asterx_profile_read", "asterx_dfma_probe"):
             getattr(L, name).restype = ctypes.c_int
         if L.asterx_abi_version() != ABI_VERSION:
@@ -273,6 +280,28 @@ class Solver:
         sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
         _check(lib().asterx_rk4_step_host(*self._args(), float(dt), hu, hp, ctypes.byref(u), ctypes.byref(p), sp,
                                           self.ws_ptr, self.ws_bytes, _stream(stream)), "asterx_rk4_step_host")
+
+    def tmunu(self, U, P, T, stream=None):
+        """T (10, ...): T_{mu nu} (tt, tx, ty, tz, xx, xy, xz, yy, yz, zz) at the owned vertices from U's A and P
+        (ghosts filled) with the metric this solver was prepared from."""
+        m, u, p = metric_struct(self._metric), state_struct(U), prims_struct(P)
+        t = TmunuFields(*_field_ptrs(T, 10))
+        _check(lib().asterx_tmunu(*self._args(), ctypes.byref(m), ctypes.byref(u), ctypes.byref(p), ctypes.byref(t),
+                                  self.ws_ptr, self.ws_bytes, _stream(stream)), "asterx_tmunu")
+
+    def rk4_step_metrics(self, U, P, dt, metrics, flags=None, stats=None, stream=None):
+        """One RK4 step whose stage s runs on metrics[s] (four (16, ...) tensors); the solver ends prepared from
+        metrics[3]."""
+        assert len(metrics) == 4
+        ms = [metric_struct(M) for M in metrics]
+        arr = (ctypes.POINTER(Metric) * 4)(*[ctypes.pointer(m) for m in ms])
+        u, p = state_struct(U), prims_struct(P)
+        fl = ctypes.c_void_p(flags.data_ptr()) if flags is not None else None
+        sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
+        _check(lib().asterx_rk4_step_metrics(*self._args(), float(dt), arr, ctypes.byref(u), ctypes.byref(p), fl, sp,
+                                             self.ws_ptr, self.ws_bytes, _stream(stream)),
+               "asterx_rk4_step_metrics")
+        self._metric = metrics[3]
 
     def _adjoint_ws(self):
         import torch

@@ -370,6 +370,59 @@ asterx_status asterx_rk4_step(const asterx_params* p, const asterx_block* blk, d
   return ASTERX_OK;
 }
 
+asterx_status asterx_tmunu(const asterx_params* p, const asterx_block* blk, const asterx_metric* metric,
+                           const asterx_state* U, const asterx_prims* P, asterx_tmunu_fields* T, void* ws,
+                           size_t ws_bytes, asterx_stream stream) {
+  asterx_status st = common_checks(p, blk, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!set_ok<asterx_metric, 16>(metric) || !set_ok<asterx_state, 9>(U) || !set_ok<asterx_prims, 5>(P) ||
+      !set_ok<asterx_tmunu_fields, 10>(T))
+    return ASTERX_EINVAL;
+  StageArgs a = make_args(p, blk, ws);
+  CF16 m;
+  std::memcpy(m.f, metric, sizeof(m.f));
+  double* t[10];
+  std::memcpy(t, T, sizeof(t));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_bfield(a.b, a.w, f9(U), s);
+  if (e == cudaSuccess) e = launch_uvel(a.b, a.w, f5(P), s);
+  if (e == cudaSuccess) e = launch_tmunu(a.b, a.w, a.gamma, m, f5(P), t, s);
+  return cuda_status(e);
+}
+
+asterx_status asterx_rk4_step_metrics(const asterx_params* p, const asterx_block* blk, double dt,
+                                      const asterx_metric* const* metric, asterx_state* U, asterx_prims* P,
+                                      signed char* flags, asterx_c2p_stats* stats, void* ws, size_t ws_bytes,
+                                      asterx_stream stream) {
+  asterx_status st = common_checks(p, blk, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!finite_pos(dt) || !set_ok<asterx_state, 9>(U) || !set_ok<asterx_prims, 5>(P) || !metric)
+    return ASTERX_EINVAL;
+  for (int q = 0; q < 4; q++)
+    if (!set_ok<asterx_metric, 16>(metric[q])) return ASTERX_EINVAL;
+  if (stats && ((uintptr_t)stats % 8) != 0) return ASTERX_EINVAL;
+  StageArgs a = make_args(p, blk, ws);
+  const long V = a.b.V;
+  F9 un = f9(U), acc, sb[2];
+  for (int v = 0; v < 9; v++) {
+    acc.f[v] = a.w.uacc + v * V;
+    sb[0].f[v] = a.w.ustage + v * V;
+    sb[1].f[v] = a.w.ustage + (9 + v) * V;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(stats);
+  for (int stage = 0; stage < 4; stage++) {
+    CF16 m;
+    std::memcpy(m.f, metric[stage], sizeof(m.f));
+    if (launch_prepare(a.b, m, a.w, s) != cudaSuccess) return ASTERX_ECUDA;
+    const F9& us = stage == 0 ? un : sb[(stage - 1) % 2];
+    const F9& unext = stage == 3 ? un : sb[stage % 2];
+    st = stage_impl(a, stage, dt, un, us, unext, acc, f5(P), flags, cnt, s);
+    if (st != ASTERX_OK) return st;
+  }
+  return ASTERX_OK;
+}
+
 asterx_status asterx_rk4_step_host(const asterx_params* p, const asterx_block* blk, double dt,
                                    double* const* h_U9, double* const* h_P5, asterx_state* dU, asterx_prims* dP,
                                    asterx_c2p_stats* stats, void* ws, size_t ws_bytes, asterx_stream stream) {

@@ -8,8 +8,14 @@
 //
 // All sums here use rounded multiply and add without contraction, in a fixed order (x innermost, then y, then
 // z), so the records are exactly reproducible by any implementation that sums in that order: the recovery's
-// atmosphere test D~ < sqrt(gamma) rho_atm then decides identically given identical inputs.  These kernels run
-// once per workspace, so the cost of the unfused operations does not matter.
+// atmosphere test D~ < sqrt(gamma) rho_atm then decides identically given identical inputs.
+//
+// The tensor-product stencils are evaluated separably (launch_prepare), which keeps that order: one pass along
+// x writes the x-contracted values (and x-derivatives) of every field at (cell x, vertex y, vertex z) into
+// workspace scratch; a column kernel then contracts along y and, sliding along z, along z, so each partial sum
+// is formed once and shared by every cell and face that uses it.  With a time-dependent metric the geometry
+// is re-derived every stage, and the separable form needs 48 (not 256) multiply-adds per cell and metric field
+// with derivatives.  k_geom_centre below keeps the direct 4x4x4 form for callers without a workspace.
 #include "kernels.h"
 #include "physics.cuh"
 
@@ -54,8 +60,8 @@ __device__ void metric_inverse_exact(const double g[6], double gu[6], double* sq
   *sqg = __dsqrt_rn(det);
 }
 
-// Centre record for every cell of the padded block.  One thread per cell; the 4x4x4 vertex values of each
-// field are contracted along x, then y, then z.
+// Centre record for every cell of the padded block, directly: one thread per cell contracts the 4x4x4 vertex
+// values of each field along x, then y, then z (launch_prepare_centre, for callers without scratch space).
 __global__ void k_geom_centre(Blk b, CF16 m, double* __restrict__ cg) {
   const long ncell = (long)b.N[0] * b.N[1] * b.N[2];
   const double der4[4] = {1.0 / 24.0, -27.0 / 24.0, 27.0 / 24.0, -1.0 / 24.0};
@@ -124,58 +130,219 @@ __global__ void k_geom_centre(Blk b, CF16 m, double* __restrict__ cg) {
   }
 }
 
-// Face record for the faces normal to D: index along D from 0..N_D, transverse 0..N-1.  The lower-index
-// transverse axis is contracted first.
-template <int D>
-__global__ void k_geom_face(Blk b, CF16 m, double* __restrict__ fg) {
-  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-  constexpr int A = (T1 < T2) ? T1 : T2;
-  constexpr int Bx = (T1 < T2) ? T2 : T1;
-  const long n0 = (D == 0) ? b.N[0] + 1 : b.N[0];
-  const long n1 = (D == 1) ? b.N[1] + 1 : b.N[1];
-  const long n2 = (D == 2) ? b.N[2] + 1 : b.N[2];
-  const long count = n0 * n1 * n2;
+// ---- separable passes (launch_prepare) ----
+// Scratch layout (pitch V): SX: 16 fields, x-contracted values at (i cell, j' vertex, k' vertex);
+// SDX: 10 fields, x-derivatives there; SFY: 10 fields, y-contracted values at (i' vertex, j cell, k' vertex).
+constexpr int SX = 0, SDX = 16, SFY = 26, NSCRATCH = 36;
+
+__device__ __forceinline__ void der_weights(const Blk& b, int d, double dw[4]) {
+  const double der4[4] = {1.0 / 24.0, -27.0 / 24.0, 27.0 / 24.0, -1.0 / 24.0};
+  for (int a = 0; a < 4; a++) dw[a] = __ddiv_rn(der4[a], b.dx[d]);
+}
+
+// x pass: field f = blockIdx.y (16 fields; the x-derivative and the y pass for the x-faces for f < 10)
+__global__ void k_geom_xpass(Blk b, CF16 m, double* __restrict__ sc) {
+  const int f = blockIdx.y;
+  const double* __restrict__ src = m.f[f];
+  const long n0 = b.N[0], n1 = b.N[1] + 1;
+  const long count = (long)(b.N[0] + 1) * (b.N[1] + 1) * (b.N[2] + 1);
+  double dw[4];
+  der_weights(b, 0, dw);
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x) {
-    int p[3];
-    p[0] = (int)(t % n0);
-    p[1] = (int)((t / n0) % n1);
-    p[2] = (int)(t / (n0 * n1));
-    double wa[4], wb[4];
-    const int sa = lagrange_mid(p[A], b.N[A], wa);
-    const int sb = lagrange_mid(p[Bx], b.N[Bx], wb);
-    const long sta = (A == 0) ? 1 : (A == 1 ? b.sy : b.sz);
-    const long stb = (Bx == 0) ? 1 : (Bx == 1 ? b.sy : b.sz);
-    int q[3] = {p[0], p[1], p[2]};
-    q[A] = sa;
-    q[Bx] = sb;
-    const long base = q[0] + b.sy * q[1] + b.sz * q[2];
-    const long c = p[0] + b.sy * p[1] + b.sz * p[2];
-    double val[10];
-    for (int f = 0; f < 10; f++) {
-      const double* __restrict__ src = m.f[f] + base;
-      double acc = 0.0;
+    // t runs over the vertex box; entry (i, j, k) serves both the (cell i, vertex j, vertex k) x-contraction
+    // and the (vertex i, cell j, vertex k) y-contraction
+    const int i = (int)(t % (n0 + 1));
+    const int j = (int)((t / (n0 + 1)) % n1);
+    const int k = (int)(t / ((n0 + 1) * n1));
+    const long c = i + b.sy * j + b.sz * k;
+    if (i < b.N[0]) {
+      double wx[4];
+      const int sx = lagrange_mid(i, b.N[0], wx);
+      const double* p = src + sx + b.sy * j + b.sz * k;
+      double vx = 0.0, dx_ = 0.0;
 #pragma unroll
-      for (int cb = 0; cb < 4; cb++) {
-        double s_ = 0.0;
-#pragma unroll
-        for (int ca = 0; ca < 4; ca++) s_ = madd(s_, wa[ca], src[ca * sta + cb * stb]);
-        acc = madd(acc, wb[cb], s_);
+      for (int a = 0; a < 4; a++) {
+        vx = madd(vx, wx[a], p[a]);
+        dx_ = madd(dx_, dw[a], p[a]);
       }
-      val[f] = acc;
+      sc[(SX + f) * b.V + c] = vx;
+      if (f < 10) sc[(SDX + f) * b.V + c] = dx_;
     }
-    double gu[6], sqg;
-    metric_inverse_exact(val + 4, gu, &sqg);
-    double* out = fg + (long)D * NFG * b.V;
-    out[FG_ALP * b.V + c] = val[0];
-    for (int a = 0; a < 3; a++) out[(FG_BETA + a) * b.V + c] = val[1 + a];
-    for (int a = 0; a < 6; a++) {
-      out[(FG_G + a) * b.V + c] = val[4 + a];
-      out[(FG_GU + a) * b.V + c] = gu[a];
+    if (f < 10 && j < b.N[1]) {
+      double wy[4];
+      const int sy = lagrange_mid(j, b.N[1], wy);
+      const double* p = src + i + b.sy * sy + b.sz * k;
+      double vy = 0.0;
+#pragma unroll
+      for (int a = 0; a < 4; a++) vy = madd(vy, wy[a], p[a * b.sy]);
+      sc[(SFY + f) * b.V + c] = vy;
     }
-    out[FG_SQG * b.V + c] = sqg;
-    out[FG_IALP * b.V + c] = 1.0 / val[0];
-    out[FG_ISQG * b.V + c] = 1.0 / sqg;
-    out[FG_WIDTH * b.V + c] = val[0] * sqrt(gu[sym(D, D)]);
+  }
+}
+
+__device__ __forceinline__ long deriv_slot(int f, int d) {
+  if (f == 0) return CG_DALP + d;
+  if (f < 4) return CG_DBETA + d * 3 + (f - 1);
+  return CG_DG + d * 6 + (f - 4);
+}
+
+__device__ __forceinline__ long centre_slot(int f) {
+  if (f == 0) return CG_ALP;
+  if (f < 4) return CG_BETA + (f - 1);
+  if (f < 10) return CG_G + (f - 4);
+  return CG_K + (f - 10);
+}
+
+// y contraction and, sliding along z, z contraction of the x-pass values: per (cell i, cell j) column and
+// field f = blockIdx.y, the centre values and derivatives of every cell and (f < 10) the z-face values
+template <bool DERIV>
+__device__ __forceinline__ void column(const Blk& b, const double* __restrict__ sc, double* __restrict__ cg,
+                                       double* __restrict__ fgz, int f, int i, int j) {
+  double wy[4], dwy[4], dwz[4];
+  const int sy = lagrange_mid(j, b.N[1], wy);
+  der_weights(b, 1, dwy);
+  der_weights(b, 2, dwz);
+  const double* __restrict__ X = sc + (long)(SX + f) * b.V + i + b.sy * sy;
+  const double* __restrict__ DX = sc + (long)(SDX + (DERIV ? f : 0)) * b.V + i + b.sy * sy;
+  const bool inner_ij = i >= b.g && i < b.g + b.n[0] && j >= b.g && j < b.g + b.n[1];
+  // window over vertex nodes s..s+3 along z: Y = y-contracted X, DXY = y-contracted DX, XDY = y-derivative of X
+  double Y[4], DXY[4], XDY[4];
+  int have = 0;  // nodes 0 .. have-1 computed
+  int s = 0;
+  auto node = [&](int kz, double& y, double& dxy, double& xdy) {
+    const long o = b.sz * kz;
+    y = 0.0;
+    dxy = 0.0;
+    xdy = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+      const double xv = X[o + a * b.sy];
+      y = madd(y, wy[a], xv);
+      if (DERIV) {
+        dxy = madd(dxy, wy[a], DX[o + a * b.sy]);
+        xdy = madd(xdy, dwy[a], xv);
+      }
+    }
+    if (fgz) fgz[i + b.sy * j + b.sz * kz] = y;
+  };
+  for (int a = 0; a < 4; a++) node(a, Y[a], DXY[a], XDY[a]);
+  have = 4;
+  const long cbase = i + b.sy * j;
+  for (int k = 0; k < b.N[2]; k++) {
+    double wz[4];
+    const int sk = lagrange_mid(k, b.N[2], wz);
+    while (s < sk) {  // slide the window up by one node
+      for (int a = 0; a < 3; a++) {
+        Y[a] = Y[a + 1];
+        DXY[a] = DXY[a + 1];
+        XDY[a] = XDY[a + 1];
+      }
+      node(have, Y[3], DXY[3], XDY[3]);
+      have++;
+      s++;
+    }
+    double v = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+      v = madd(v, wz[a], Y[a]);
+      if (DERIV) {
+        ax = madd(ax, wz[a], DXY[a]);
+        ay = madd(ay, wz[a], XDY[a]);
+        az = madd(az, dwz[a], Y[a]);
+      }
+    }
+    const long c = cbase + b.sz * k;
+    cg[centre_slot(f) * b.V + c] = v;
+    if (DERIV) {
+      const bool inner = inner_ij && k >= b.g && k < b.g + b.n[2];
+      cg[deriv_slot(f, 0) * b.V + c] = inner ? ax : 0.0;
+      cg[deriv_slot(f, 1) * b.V + c] = inner ? ay : 0.0;
+      cg[deriv_slot(f, 2) * b.V + c] = inner ? az : 0.0;
+    }
+  }
+  // the z-faces of the column's last nodes (k' up to N2)
+  while (have <= b.N[2]) {
+    double y, dxy, xdy;
+    node(have, y, dxy, xdy);
+    have++;
+  }
+}
+
+__global__ void k_geom_columns(Blk b, const double* __restrict__ sc, double* __restrict__ cg, double* __restrict__ fg) {
+  const int f = blockIdx.y;
+  const long count = (long)b.N[0] * b.N[1];
+  double* fgz = f < 10 ? fg + (long)(2 * NFG + (f == 0 ? FG_ALP : (f < 4 ? FG_BETA + f - 1 : FG_G + f - 4))) * b.V
+                       : nullptr;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % b.N[0]);
+    const int j = (int)(t / b.N[0]);
+    if (f < 10) column<true>(b, sc, cg, fgz, f, i, j);
+    else column<false>(b, sc, cg, nullptr, f, i, j);
+  }
+}
+
+__device__ __forceinline__ long face_slot(int f) {
+  return f == 0 ? FG_ALP : (f < 4 ? FG_BETA + f - 1 : FG_G + f - 4);
+}
+
+// z contraction for the x-faces (of the y pass) and the y-faces (of the x pass); field f = blockIdx.y < 10
+__global__ void k_geom_xyfaces(Blk b, const double* __restrict__ sc, double* __restrict__ fg) {
+  const int f = blockIdx.y;
+  const long n0 = b.N[0] + 1, n1 = b.N[1] + 1;
+  const long count = n0 * n1 * b.N[2];
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n0);
+    const int j = (int)((t / n0) % n1);
+    const int k = (int)(t / (n0 * n1));
+    double wz[4];
+    const int sz = lagrange_mid(k, b.N[2], wz);
+    const long c = i + b.sy * j + b.sz * k;
+    const long base = i + b.sy * j + b.sz * sz;
+    if (j < b.N[1]) {  // x-face (vertex i, cell j, cell k)
+      const double* p = sc + (long)(SFY + f) * b.V + base;
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a < 4; a++) v = madd(v, wz[a], p[a * b.sz]);
+      fg[(0 * NFG + face_slot(f)) * b.V + c] = v;
+    }
+    if (i < b.N[0]) {  // y-face (cell i, vertex j, cell k)
+      const double* p = sc + (long)(SX + f) * b.V + base;
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a < 4; a++) v = madd(v, wz[a], p[a * b.sz]);
+      fg[(1 * NFG + face_slot(f)) * b.V + c] = v;
+    }
+  }
+}
+
+// the derived parts of the records: inverse metric and sqrt(gamma) at centres; at faces also 1/alpha,
+// 1/sqrt(gamma) and the light-cone half-width alpha sqrt(gamma^DD)
+__global__ void k_geom_complete(Blk b, double* __restrict__ cg, double* __restrict__ fg) {
+  const long count = b.V;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < count; c += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % b.sy);
+    const int j = (int)((c / b.sy) % (b.N[1] + 1));
+    const int k = (int)(c / b.sz);
+    double g6[6], gu[6], sqg;
+    if (i < b.N[0] && j < b.N[1] && k < b.N[2]) {
+      for (int a = 0; a < 6; a++) g6[a] = cg[(CG_G + a) * b.V + c];
+      metric_inverse_exact(g6, gu, &sqg);
+      for (int a = 0; a < 6; a++) cg[(CG_GU + a) * b.V + c] = gu[a];
+      cg[CG_SQG * b.V + c] = sqg;
+    }
+    for (int D = 0; D < 3; D++) {
+      const bool on = (D == 0 ? j < b.N[1] && k < b.N[2] : (D == 1 ? i < b.N[0] && k < b.N[2] : i < b.N[0] && j < b.N[1]));
+      if (!on) continue;
+      double* out = fg + (long)D * NFG * b.V;
+      for (int a = 0; a < 6; a++) g6[a] = out[(FG_G + a) * b.V + c];
+      metric_inverse_exact(g6, gu, &sqg);
+      for (int a = 0; a < 6; a++) out[(FG_GU + a) * b.V + c] = gu[a];
+      const double alp = out[FG_ALP * b.V + c];
+      out[FG_SQG * b.V + c] = sqg;
+      out[FG_IALP * b.V + c] = 1.0 / alp;
+      out[FG_ISQG * b.V + c] = 1.0 / sqg;
+      out[FG_WIDTH * b.V + c] = alp * sqrt(gu[sym(D, D)]);
+    }
   }
 }
 
@@ -204,13 +371,18 @@ cudaError_t launch_prepare_centre(const Blk& b, const CF16& m, double* cg, cudaS
 }
 
 cudaError_t launch_prepare(const Blk& b, const CF16& m, const Ws& w, cudaStream_t s) {
+  // scratch: the stage-local fields of the workspace from bf on (bf, bc, uvel, rec, face, ga, fpsi: 54 fields,
+  // contiguous), none of which carries data across asterx calls or RK stages
+  static_assert(NSCRATCH <= 3 + 3 + 3 + 2 * NREC + 3 * NFD + 1 + 3, "geometry scratch exceeds the stage fields");
+  double* sc = w.bf;
   const int T = 128;
-  k_geom_centre<<<grid_for((long)b.N[0] * b.N[1] * b.N[2], T), T, 0, s>>>(b, m, w.cg);
-  const long fc = (long)(b.N[0] + 1) * b.N[1] * b.N[2];
-  k_geom_face<0><<<grid_for(fc, T), T, 0, s>>>(b, m, w.fg);
-  k_geom_face<1><<<grid_for(fc, T), T, 0, s>>>(b, m, w.fg);
-  k_geom_face<2><<<grid_for(fc, T), T, 0, s>>>(b, m, w.fg);
-  k_geom_vertex<<<grid_for(b.V, 256), 256, 0, s>>>(b, m, w.vg);
+  const long V = b.V;
+  k_geom_xpass<<<dim3(grid_for(V, T) / 16 + 1, 16), T, 0, s>>>(b, m, sc);
+  const long cols = (long)b.N[0] * b.N[1];
+  k_geom_columns<<<dim3((unsigned)((cols + 63) / 64), 16), 64, 0, s>>>(b, sc, w.cg, w.fg);
+  k_geom_xyfaces<<<dim3(grid_for(V, T) / 10 + 1, 10), T, 0, s>>>(b, sc, w.fg);
+  k_geom_complete<<<grid_for(V, T), T, 0, s>>>(b, w.cg, w.fg);
+  k_geom_vertex<<<grid_for(V, 256), 256, 0, s>>>(b, m, w.vg);
   return cudaGetLastError();
 }
 

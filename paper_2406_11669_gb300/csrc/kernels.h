@@ -28,6 +28,14 @@ cudaError_t launch_ghost_prims(const Blk& b, const F5& P, cudaStream_t s);
 // B~ = curl A on faces, then the undensitised centre field of every cell
 cudaError_t launch_bfield(const Blk& b, const Ws& w, const F9& U, cudaStream_t s);
 
+// u^i = W v^i at every cell into w.uvel (primitives with ghosts)
+cudaError_t launch_uvel(const Blk& b, const Ws& w, const F5& P, cudaStream_t s);
+
+// T_{mu nu} at the owned vertices (g..g+n per axis) into T (10 fields: tt, tx, ty, tz, xx, xy, xz, yy, yz, zz)
+// from the primitives, w.uvel and w.bc (launch_bfield and launch_uvel first) and the vertex metric m
+cudaError_t launch_tmunu(const Blk& b, const Ws& w, double gamma, const CF16& m, const F5& P, double* const T[10],
+                         cudaStream_t s);
+
 // conserved variables of every cell from primitives (needs launch_bfield first)
 cudaError_t launch_prim2con(const StageArgs& a, const F9& U, const F5& P, cudaStream_t s);
 

@@ -1017,6 +1017,13 @@ cudaError_t launch_bfield(const Blk& b, const Ws& w, const F9& U, cudaStream_t s
   return cudaGetLastError();
 }
 
+cudaError_t launch_uvel(const Blk& b, const Ws& w, const F5& P, cudaStream_t s) {
+  Single t = single_of(b, w);
+  t.r.P = P;
+  launch<UVel>(t, zero_consts(), KIND_CELLS_ALL, s);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prim2con(const StageArgs& a, const F9& U, const F5& P, cudaStream_t s) {
   Single t = single_of(a.b, a.w);
   t.r.Us = U;

@@ -135,3 +135,32 @@ def test_adjoint_workspace_size_and_validation():
                                    ctypes.byref(pr), ctypes.byref(st), ctypes.c_void_p(256), need,
                                    ctypes.c_void_p(512), size, None)
     assert rc == A.ASTERX_EINVAL  # dt <= 0
+
+
+def test_tmunu_and_metric_step_validation():
+    L = A.lib()
+    p = _params()
+    b = A.block_struct((8, 8, 8), 3, (0, 0, 0), (0.1,) * 3, (0, 0, 0))
+    need = A.workspace_size(b)
+    st = A.State(*([8] * 9))
+    pr = A.Prims(*([8] * 5))
+    m = A.Metric(*([8] * 16))
+    T = A.TmunuFields(*([8] * 10))
+    ws = ctypes.c_void_p(256)
+    rc = L.asterx_tmunu(ctypes.byref(p), ctypes.byref(b), ctypes.byref(m), ctypes.byref(st), ctypes.byref(pr),
+                        ctypes.byref(A.TmunuFields(*([8] * 9 + [0]))), ws, need, None)
+    assert rc == A.ASTERX_EINVAL  # null output field
+    rc = L.asterx_tmunu(ctypes.byref(p), ctypes.byref(b), ctypes.byref(A.Metric(*([8] * 15 + [12]))),
+                        ctypes.byref(st), ctypes.byref(pr), ctypes.byref(T), ws, need, None)
+    assert rc == A.ASTERX_EINVAL  # misaligned metric field
+    rc = L.asterx_tmunu(ctypes.byref(p), ctypes.byref(b), ctypes.byref(m), ctypes.byref(st), ctypes.byref(pr),
+                        ctypes.byref(T), ws, need - 8, None)
+    assert rc == A.ASTERX_ENOMEM
+    ms = (ctypes.POINTER(A.Metric) * 4)(*[ctypes.pointer(m)] * 3 + [ctypes.POINTER(A.Metric)()])
+    rc = L.asterx_rk4_step_metrics(ctypes.byref(p), ctypes.byref(b), ctypes.c_double(0.01), ms, ctypes.byref(st),
+                                   ctypes.byref(pr), None, None, ws, need, None)
+    assert rc == A.ASTERX_EINVAL  # missing stage metric
+    ms = (ctypes.POINTER(A.Metric) * 4)(*[ctypes.pointer(m)] * 4)
+    rc = L.asterx_rk4_step_metrics(ctypes.byref(p), ctypes.byref(b), ctypes.c_double(0.0), ms, ctypes.byref(st),
+                                   ctypes.byref(pr), None, None, ws, need, None)
+    assert rc == A.ASTERX_EINVAL  # dt <= 0

@@ -157,7 +157,7 @@ def test_rk4_step_adjoint_matches_central_differences(name):
     check_vjp(prob, prob.rk4, lam, full_entries=False)
 
 
-def check_against_jvp(prob, mu, lam, jvp, entries_full=True, rtol=1e-10):
+def check_against_jvp(prob, mu, lam, jvp, entries_full=True, rtol=1e-11):
     """<lam, d> against <mu, J d> with J d from the oracle's dual-number derivative (no truncation error: the two
     agree to rounding and the recovery's root tolerance): one random direction over every independent entry, one
     per input group, then unit directions at the sampled entries of every field (lam_i = <mu, J e_i>)."""
@@ -172,7 +172,7 @@ def check_against_jvp(prob, mu, lam, jvp, entries_full=True, rtol=1e-10):
     for d in dirs:
         Jd = jvp(d)
         ad, ref = float(np.sum(lam * d)), float(np.sum(mu * Jd))
-        scale = max(float(np.sum(np.abs(lam * d))), float(np.sum(np.abs(mu * Jd))))
+        scale = max(float(np.sum(np.abs(lam * d))), float(np.sum(np.abs(mu * Jd))), 1e-300)
         worst = max(worst, abs(ad - ref) / scale)
         assert abs(ad - ref) <= rtol * scale, (ad, ref, scale)
     for v in range(9):
@@ -201,7 +201,7 @@ def test_rhs_adjoint_equals_the_oracle_jvp(name):
     print(f"{name}: largest relative difference {worst:.2e}")
 
 
-@pytest.mark.parametrize("name", ["wenoz_periodic_algebraic", "minmod_copy_lorenz"])
+@pytest.mark.parametrize("name", list(CASES))
 def test_rk4_step_adjoint_equals_the_oracle_jvp(name):
     need_gpu()
     w = W.smooth_general(n=(10, 9, 8), **CASES[name])
