@@ -56,8 +56,9 @@ def parse():
                     help="skip the stress-energy tensor and time-dependent-metric step measurements")
     ap.add_argument("--profile-region", choices=("none", "forward", "adjoint", "batched", "coupling"), default="none",
                     help="bracket one extra forward RK4 step (main workload), one adjoint step, one batched "
-                         "step and one step of the equal-volume block, or one stress-energy tensor call with "
-                         "cudaProfilerStart/Stop, for a profiler run with --profile-from-start off")
+                         "step and one step of the equal-volume block, or one geometry derivation and one "
+                         "stress-energy tensor call with cudaProfilerStart/Stop, for a profiler run with "
+                         "--profile-from-start off")
     return ap.parse_args()
 
 
@@ -381,11 +382,20 @@ def run_coupling(args, s, U, P, M, w, dev, stream):
     ms_t = e0.elapsed_time(e1) / reps
     if args.profile_region == "coupling":
         torch.cuda.profiler.start()
+        s.prepare(M)
         s.tmunu(U, P, T)
         torch.cuda.synchronize(dev)
         torch.cuda.profiler.stop()
     finite = bool(torch.isfinite(T).all())
     del T
+    s.prepare(M)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        s.prepare(M)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_prep = e0.elapsed_time(e1) / reps
     metrics = [M, M, M, M]
     s.rk4_step_metrics(U, P, w.dt, metrics)
     torch.cuda.synchronize(dev)
@@ -407,6 +417,7 @@ def run_coupling(args, s, U, P, M, w, dev, stream):
         nv *= w.n[d] + 1
     return {"tmunu": {"vertices": nv, "ms": ms_t, "vertices_per_s": nv / (ms_t / 1e3), "finite": finite,
                       "launches": 4},
+            "prepare_ms": ms_prep,
             "metric_step": {"ms_per_step": ms_dyn, "frozen_ms_per_step": ms_frozen,
                             "overhead": ms_dyn / ms_frozen - 1.0, "steps": steps}}
 

@@ -232,7 +232,8 @@ static const double DER4[4] = {1.0 / 24.0, -27.0 / 24.0, 27.0 / 24.0, -1.0 / 24.
 
 // Interpolate the vertex metric to a point that is at vertex index along axes where half[d] == 0 and at the
 // midpoint p+1/2 along axes where half[d] == 1.  If dflag >= 0, the axis dflag (which must be a half axis)
-// takes the staggered derivative stencil instead, and the result is d/dx^dflag of the field.
+// takes the staggered derivative stencil instead, and the result is d/dx^dflag of the field.  The sums run
+// x innermost, then y, then z, each term a fused multiply-add (one rounding).
 static double vertex_interp(const Grid& G, const double* f, const int p[3], const int half[3], int dflag) {
   int st[3];
   double w[3][4];
@@ -256,10 +257,10 @@ static double vertex_interp(const Grid& G, const double* f, const int p[3], cons
     double accy = 0.0;
     for (int b = 0; b < cnt[1]; b++) {
       double accx = 0.0;
-      for (int a = 0; a < cnt[0]; a++) accx += w[0][a] * f[G.at(st[0] + a, st[1] + b, st[2] + c)];
-      accy += w[1][b] * accx;
+      for (int a = 0; a < cnt[0]; a++) accx = std::fma(w[0][a], f[G.at(st[0] + a, st[1] + b, st[2] + c)], accx);
+      accy = std::fma(w[1][b], accx, accy);
     }
-    acc += w[2][c] * accy;
+    acc = std::fma(w[2][c], accy, acc);
   }
   return acc;
 }

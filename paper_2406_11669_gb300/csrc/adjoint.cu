@@ -300,10 +300,8 @@ __global__ void ka_faces(Blk b, Ws w, AdjWs a, double gamma, double gfac) {
     Geo m;
     m.alp = fg[FG_ALP * b.V + c];
     for (int q = 0; q < 3; q++) m.beta[q] = fg[(FG_BETA + q) * b.V + c];
-    for (int q = 0; q < 6; q++) {
-      m.g[q] = fg[(FG_G + q) * b.V + c];
-      m.gu[q] = fg[(FG_GU + q) * b.V + c];
-    }
+    for (int q = 0; q < 6; q++) m.g[q] = fg[(FG_G + q) * b.V + c];
+    m.gu[sym(D, D)] = fg[FG_GUDD * b.V + c];  // the only inverse-metric component the face solve reads
     m.sqg = fg[FG_SQG * b.V + c];
     const double ia = fg[FG_IALP * b.V + c];
     const double width = fg[FG_WIDTH * b.V + c];

@@ -6,16 +6,17 @@
 // here and read by every stage.  Near the end of the padded array the 4-point stencil is shifted inward so
 // that it stays 4th order; centre derivatives use (f_{-3/2} - 27 f_{-1/2} + 27 f_{1/2} - f_{3/2}) / (24 h).
 //
-// All sums here use rounded multiply and add without contraction, in a fixed order (x innermost, then y, then
-// z), so the records are exactly reproducible by any implementation that sums in that order: the recovery's
-// atmosphere test D~ < sqrt(gamma) rho_atm then decides identically given identical inputs.
+// All stencil sums here accumulate one fused multiply-add per term, in a fixed order (x innermost, then y, then
+// z), and the inverse metric uses rounded operations without contraction, so the records are exactly
+// reproducible by any implementation that does the same: the recovery's atmosphere test D~ < sqrt(gamma)
+// rho_atm then decides identically given identical inputs.
 //
 // The tensor-product stencils are evaluated separably (launch_prepare), which keeps that order: one pass along
 // x writes the x-contracted values (and x-derivatives) of every field at (cell x, vertex y, vertex z) into
 // workspace scratch; a column kernel then contracts along y and, sliding along z, along z, so each partial sum
 // is formed once and shared by every cell and face that uses it.  With a time-dependent metric the geometry
-// is re-derived every stage, and the separable form needs 48 (not 256) multiply-adds per cell and metric field
-// with derivatives.  k_geom_centre below keeps the direct 4x4x4 form for callers without a workspace.
+// is re-derived every stage, and the separable form needs 48 (not 256) fused multiply-adds per cell and metric
+// field with derivatives.  k_geom_centre below keeps the direct 4x4x4 form for callers without a workspace.
 #include "kernels.h"
 #include "physics.cuh"
 
@@ -37,7 +38,8 @@ __device__ __forceinline__ int lagrange_mid(int p, int Nv, double w[4]) {
   return s;
 }
 
-__device__ __forceinline__ double madd(double acc, double w, double v) { return __dadd_rn(acc, __dmul_rn(w, v)); }
+// one term of a stencil sum: a fused multiply-add, rounded once (the oracle's interpolation rounds the same way)
+__device__ __forceinline__ double madd(double acc, double w, double v) { return __fma_rn(w, v, acc); }
 __device__ __forceinline__ double dmsub(double a, double b, double c, double d) {
   return __dsub_rn(__dmul_rn(a, b), __dmul_rn(c, d));
 }
@@ -58,6 +60,16 @@ __device__ void metric_inverse_exact(const double g[6], double gu[6], double* sq
   gu[4] = __ddiv_rn(c12, det);
   gu[5] = __ddiv_rn(c22, det);
   *sqg = __dsqrt_rn(det);
+}
+
+// determinant and the diagonal inverse component gamma^DD = cofactor_DD / det, rounded as metric_inverse_exact
+__device__ void metric_det_exact(const double g[6], int D, double* det, double* gdd) {
+  const double c00 = dmsub(g[3], g[5], g[4], g[4]);
+  const double c01 = dmsub(g[4], g[2], g[1], g[5]);
+  const double c02 = dmsub(g[1], g[4], g[3], g[2]);
+  *det = __dadd_rn(__dadd_rn(__dmul_rn(g[0], c00), __dmul_rn(g[1], c01)), __dmul_rn(g[2], c02));
+  const double cdd = D == 0 ? c00 : (D == 1 ? dmsub(g[0], g[5], g[2], g[2]) : dmsub(g[0], g[3], g[1], g[1]));
+  *gdd = __ddiv_rn(cdd, *det);
 }
 
 // Centre record for every cell of the padded block, directly: one thread per cell contracts the 4x4x4 vertex
@@ -335,13 +347,15 @@ __global__ void k_geom_complete(Blk b, double* __restrict__ cg, double* __restri
       if (!on) continue;
       double* out = fg + (long)D * NFG * b.V;
       for (int a = 0; a < 6; a++) g6[a] = out[(FG_G + a) * b.V + c];
-      metric_inverse_exact(g6, gu, &sqg);
-      for (int a = 0; a < 6; a++) out[(FG_GU + a) * b.V + c] = gu[a];
+      double det, gdd;
+      metric_det_exact(g6, D, &det, &gdd);
+      sqg = __dsqrt_rn(det);
       const double alp = out[FG_ALP * b.V + c];
+      out[FG_GUDD * b.V + c] = gdd;
       out[FG_SQG * b.V + c] = sqg;
       out[FG_IALP * b.V + c] = 1.0 / alp;
       out[FG_ISQG * b.V + c] = 1.0 / sqg;
-      out[FG_WIDTH * b.V + c] = alp * sqrt(gu[sym(D, D)]);
+      out[FG_WIDTH * b.V + c] = alp * sqrt(gdd);
     }
   }
 }

@@ -21,8 +21,9 @@ enum {
 };
 
 // Face geometry record (per face, one set per direction): metric interpolated in the two transverse directions.
-enum { FG_ALP = 0, FG_BETA = 1, FG_G = 4, FG_GU = 10, FG_SQG = 16, FG_IALP = 17, FG_ISQG = 18, FG_WIDTH = 19,
-       NFG = 20 };  // FG_WIDTH: light-cone half-width alpha sqrt(gamma^dd) along the face normal
+// Of the inverse metric the face solve needs gamma^dd alone (the normal component of faces normal to d).
+enum { FG_ALP = 0, FG_BETA = 1, FG_G = 4, FG_GUDD = 10, FG_SQG = 11, FG_IALP = 12, FG_ISQG = 13, FG_WIDTH = 14,
+       NFG = 15 };  // FG_WIDTH: light-cone half-width alpha sqrt(gamma^dd) along the face normal
 
 // Vertex geometry record: lapse, shift, sqrt(det gamma), inverse metric.
 enum { VG_ALP = 0, VG_BETA = 1, VG_SQG = 4, VG_GU = 5, NVG = 11 };

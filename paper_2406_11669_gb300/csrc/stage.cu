@@ -524,10 +524,8 @@ struct Faces {
     Geo m;
     m.alp = fg[FG_ALP * b.V + c];
     for (int a = 0; a < 3; a++) m.beta[a] = fg[(FG_BETA + a) * b.V + c];
-    for (int a = 0; a < 6; a++) {
-      m.g[a] = fg[(FG_G + a) * b.V + c];
-      m.gu[a] = fg[(FG_GU + a) * b.V + c];
-    }
+    for (int a = 0; a < 6; a++) m.g[a] = fg[(FG_G + a) * b.V + c];
+    m.gu[sym(D, D)] = fg[FG_GUDD * b.V + c];  // the only inverse-metric component the face solve reads
     m.sqg = fg[FG_SQG * b.V + c];
     const double ia = fg[FG_IALP * b.V + c];
     const double width = fg[FG_WIDTH * b.V + c];

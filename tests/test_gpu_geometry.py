@@ -5,7 +5,7 @@ scratch, then y and z contractions per column), with rounded multiply and add in
 per-point sums (x innermost, then y, then z).  The records must therefore equal the oracle's values exactly:
 the recovery's atmosphere test compares D~ with sqrt(gamma) rho_atm, and identical inputs must decide
 identically on both sides.  White-box: the test reads the records from the workspace in the layout of
-csrc/layout.h (centre record of 53 fields at the workspace start, then three face records of 20 fields, each
+csrc/layout.h (centre record of 53 fields at the workspace start, then three face records of 15 fields, each
 group at pitch V and 256-byte aligned field stride).
 """
 import numpy as np
@@ -18,9 +18,9 @@ from paper_2406_11669_gb300 import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-NCG, NFG = 53, 20
+NCG, NFG = 53, 15
 CG_DALP = 23
-FG_IALP, FG_ISQG, FG_WIDTH = 17, 18, 19
+FG_GUDD, FG_SQG, FG_IALP, FG_ISQG, FG_WIDTH = 10, 11, 12, 13, 14
 SYM = [[0, 1, 2], [1, 3, 4], [2, 4, 5]]
 
 
@@ -74,8 +74,10 @@ def check_exact(case, M):
     for d in range(3):
         fr = O.face_metric(w, M, d)
         fsl = faces(w, d)
-        for q in range(17):
+        for q in range(10):
             assert np.array_equal(fg[d][q][fsl], fr[q][fsl]), ("face", d, q)
+        assert np.array_equal(fg[d][FG_GUDD][fsl], fr[10 + SYM[d][d]][fsl])
+        assert np.array_equal(fg[d][FG_SQG][fsl], fr[16][fsl])
         assert np.array_equal(fg[d][FG_IALP][fsl], 1.0 / fr[0][fsl])
         assert np.array_equal(fg[d][FG_ISQG][fsl], 1.0 / fr[16][fsl])
         assert np.array_equal(fg[d][FG_WIDTH][fsl], fr[0][fsl] * np.sqrt(fr[10 + SYM[d][d]][fsl]))
