@@ -34,7 +34,8 @@ class OParams(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("rho_atm", ctypes.c_double), ("K_atm", ctypes.c_double),
                 ("gamma_atm", ctypes.c_double), ("c2p_tol", ctypes.c_double), ("c2p_maxiter", ctypes.c_int),
                 ("brent_maxiter", ctypes.c_int), ("W_max", ctypes.c_double), ("recon", ctypes.c_int),
-                ("gauge", ctypes.c_int), ("xi_lorenz", ctypes.c_double), ("use_fallback", ctypes.c_int)]
+                ("gauge", ctypes.c_int), ("xi_lorenz", ctypes.c_double), ("use_fallback", ctypes.c_int),
+                ("flux", ctypes.c_int), ("efield", ctypes.c_int)]
 
 
 class OBlock(ctypes.Structure):
@@ -86,6 +87,7 @@ def lib():
         L.oracle_recon_flops.argtypes = [ctypes.c_int, _P, _P]
         L.oracle_point_sources.argtypes = [ctypes.POINTER(OParams), _P, _P, _P, _P, _P, _P, _P]
         L.oracle_grid_sources.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP]
+        L.oracle_point_face.argtypes = [ctypes.POINTER(OParams), _P, _P, _P, ctypes.c_double, ctypes.c_int, _P]
         L.oracle_centre_metric.argtypes = [ctypes.POINTER(OBlock), _PP, _PP]
         L.oracle_face_metric.argtypes = [ctypes.POINTER(OBlock), _PP, ctypes.c_int, _PP]
         L.oracle_tmunu.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP]
@@ -102,7 +104,7 @@ def lib():
 def params_struct(p: dict) -> OParams:
     return OParams(p["gamma"], p["rho_atm"], p["K_atm"], p["gamma_atm"], p["c2p_tol"], int(p["c2p_maxiter"]),
                    int(p["brent_maxiter"]), p["W_max"], int(p["recon"]), int(p["gauge"]), p["xi_lorenz"],
-                   int(p["use_fallback"]))
+                   int(p["use_fallback"]), int(p.get("flux", 0)), int(p.get("efield", 0)))
 
 
 def block_struct(w) -> OBlock:
@@ -263,6 +265,17 @@ def rk4_jvp(w, M, U, dU, P, dt=None, params=None):
     return U1, JU1
 
 
+def rk2_step(w, M, U, P, dt=None, params=None):
+    """One RK2 step (explicit midpoint: U_1 = U_n + dt/2 L(U_n), U_{n+1} = U_n + dt L(U_1)); as rk4_step."""
+    dt = float(dt if dt is not None else w.dt)
+    Uacc = np.zeros_like(U)
+    U1 = U.copy()
+    _, s0 = rk_stage(w, M, 4, dt, U, U, U1, Uacc, P, params)
+    U2 = U1.copy()
+    _, s1 = rk_stage(w, M, 5, dt, U, U1, U2, Uacc, P, params)
+    return U2, {k: s0[k] + s1[k] for k in s0}
+
+
 def rk4_step_metrics(w, Ms, U, P, dt=None, params=None):
     """One RK4 step whose stage s runs on the metric Ms[s] (a time-dependent spacetime sampled at the stage
     times); otherwise as rk4_step."""
@@ -276,6 +289,16 @@ def rk4_step_metrics(w, Ms, U, P, dt=None, params=None):
         tot = st if tot is None else {k: tot[k] + st[k] for k in tot}
         Us = Unext
     return Us, tot
+
+
+def point_face(params, m16, L8, R8, Bn, d):
+    """One face solve: dict with F (5), Fb (3: induction fluxes along d of B~^x,y,z), cmax, cmin, vbar (3).
+    L8, R8: rho, p, u^x, u^y, u^z (u = W v), B^x, B^y, B^z (undensitised; the normal entry unused)."""
+    out = np.zeros(13)
+    lib().oracle_point_face(ctypes.byref(params_struct(params)), _p(np.ascontiguousarray(m16, float)),
+                            _p(np.ascontiguousarray(L8, float)), _p(np.ascontiguousarray(R8, float)), float(Bn),
+                            int(d), _p(out))
+    return dict(F=out[:5], Fb=out[5:8], cmax=out[8], cmin=out[9], vbar=out[10:13])
 
 
 def point_prim2con(params, m16, prim5, B3):

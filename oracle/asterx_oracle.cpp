@@ -125,6 +125,8 @@ struct OParams {
   int gauge;          // 0 generalised Lorenz, 1 algebraic
   double xi_lorenz;   // Lorenz damping; 0 => 1.5/dt
   int use_fallback;   // Palenzuela fallback on/off
+  int flux;           // 0 HLLE (Eq. HLLEfluxes), 1 Lax-Friedrichs (Eq. LxFfluxes)
+  int efield;         // 0 upwind constrained transport (Eq. eq3.20), 1 flux constrained transport
 };
 
 struct OBlock {
@@ -140,6 +142,8 @@ struct OStats {
 };
 
 enum { RECON_MINMOD = 0, RECON_PPM = 1, RECON_WENOZ = 2 };
+enum { FLUX_HLLE = 0, FLUX_LXF = 1 };
+enum { EFIELD_UCT = 0, EFIELD_FCT = 1 };
 enum { BC_PERIODIC = 0, BC_COPY = 1 };
 enum { GAUGE_LORENZ = 0, GAUGE_ALGEBRAIC = 1 };
 
@@ -530,9 +534,18 @@ template <class R> void hlle(const R FL[5], const R FR[5], const R UL[5], const 
   }
 }
 
+// Lax-Friedrichs (Eq. LxFfluxes): the average of the two fluxes minus c_wave / 2 times the jump of the conserved
+// variables, c_wave = max(c_max, c_min).
+template <class R> void lxf(const R FL[5], const R FR[5], const R UL[5], const R UR[5], R cmax, R cmin, R out[5]) {
+  const R cw = rmax(cmax, cmin);
+  for (int v = 0; v < 5; v++) out[v] = R(0.5) * (FR[v] + FL[v] - cw * (UR[v] - UL[v]));
+}
+
 // ------------------------------------------------------------------------------------------------------
-// Face solve: from the reconstructed left/right states and the face metric, the HLLE flux of the 5 hydro
-// variables and the data that upwind constrained transport needs at this face (Eq. uct1, uct2).
+// Face solve: from the reconstructed left/right states and the face metric, the HLLE (or Lax-Friedrichs) flux of
+// the 5 hydro variables, the data that upwind constrained transport needs at this face (Eq. uct1, uct2), and
+// for flux constrained transport the same solver's fluxes of the induction equation (Eq. inductioneq):
+// along d the flux of B~^a (a != d) is v~^d B~^a - v~^a B~^d.
 
 template <class R> struct FaceInputT {
   R rho[2], press[2], u[2][3], Bt[2][3];  // side 0 = left, 1 = right; u = W v; Bt: transverse B only
@@ -543,13 +556,16 @@ typedef FaceInputT<double> FaceInput;
 template <class R> struct FaceOut {
   R F[5];
   R vbar[3];  // upwind v~ components (the normal one unused)
+  R Fb[3];    // induction fluxes along d of the densitised B~^a, a != d (the normal one unused)
   R cmax, cmin;
   int iters;
 };
 
-template <class R, class In> FaceOut<R> face_solve(const Metric3<R>& m, const In& in, double gamma, int d) {
+template <class R, class In>
+FaceOut<R> face_solve(const Metric3<R>& m, const In& in, double gamma, int d, int solver = FLUX_HLLE,
+                      bool induction = false) {
   FaceOut<R> out;
-  R U[2][5], F[2][5], lp[2], lm[2], vt[2][3];
+  R U[2][5], F[2][5], lp[2], lm[2], vt[2][3], Bt[2][3];
   out.iters = 0;
   for (int s = 0; s < 2; s++) {
     Prim<R> P;
@@ -575,10 +591,28 @@ template <class R, class In> FaceOut<R> face_solve(const Metric3<R>& m, const In
     wave_speeds(m, P, c, gamma, d, &lm[s], &lp[s], &it);
     out.iters += it;
     for (int a = 0; a < 3; a++) vt[s][a] = m.alp * P.vel[a] - m.beta[a];
+    for (int a = 0; a < 3; a++) Bt[s][a] = (a == d) ? R(in.Bn) : m.sqrtg * P.B[a];
   }
   out.cmax = rmax(R(0.0), rmax(lp[0], lp[1]));
   out.cmin = -rmin(R(0.0), rmin(lm[0], lm[1]));
-  hlle(F[0], F[1], U[0], U[1], out.cmax, out.cmin, out.F);
+  if (solver == FLUX_LXF) lxf(F[0], F[1], U[0], U[1], out.cmax, out.cmin, out.F);
+  else hlle(F[0], F[1], U[0], U[1], out.cmax, out.cmin, out.F);
+  // induction fluxes of the transverse B~ with the same solver (one-component forms of the above), when the
+  // electric field is formed from them
+  for (int a = 0; a < 3; a++) {
+    if (a == d || !induction) {
+      out.Fb[a] = R(0.0);
+      continue;
+    }
+    R fl[5] = {vt[0][d] * Bt[0][a] - vt[0][a] * Bt[0][d], R(0.0), R(0.0), R(0.0), R(0.0)};
+    R fr[5] = {vt[1][d] * Bt[1][a] - vt[1][a] * Bt[1][d], R(0.0), R(0.0), R(0.0), R(0.0)};
+    R ul[5] = {Bt[0][a], R(0.0), R(0.0), R(0.0), R(0.0)};
+    R ur[5] = {Bt[1][a], R(0.0), R(0.0), R(0.0), R(0.0)};
+    R o5[5];
+    if (solver == FLUX_LXF) lxf(fl, fr, ul, ur, out.cmax, out.cmin, o5);
+    else hlle(fl, fr, ul, ur, out.cmax, out.cmin, o5);
+    out.Fb[a] = o5[0];
+  }
   const R den = out.cmax + out.cmin;
   for (int a = 0; a < 3; a++) {
     if (a == d) {
@@ -1029,7 +1063,7 @@ struct RhsStats {
 };
 
 template <class R> struct FaceDataT {
-  std::vector<R> F[5], vbar[3], cmax, cmin;
+  std::vector<R> F[5], vbar[3], Fb[3], cmax, cmin;
 };
 
 template <class R>
@@ -1038,6 +1072,7 @@ static void compute_faces(const Grid& G, const VertexMetric& vm, const OParams& 
                           RhsStats* st) {
   for (int v = 0; v < 5; v++) fd.F[v].assign(G.size(), R(0.0));
   for (int v = 0; v < 3; v++) fd.vbar[v].assign(G.size(), R(0.0));
+  for (int v = 0; v < 3; v++) fd.Fb[v].assign(G.size(), R(0.0));
   fd.cmax.assign(G.size(), R(0.0));
   fd.cmin.assign(G.size(), R(0.0));
   // reconstructed variables at every cell: rho, p, u^x, u^y, u^z (u = W v) and the centre B
@@ -1094,9 +1129,10 @@ static void compute_faces(const Grid& G, const VertexMetric& vm, const OParams& 
         }
         in.Bn = Bf[d][fc];
         const Metric3<R> m = lift<R>(metric_at_face(G, vm, d, p[0], p[1], p[2]));
-        FaceOut<R> o = face_solve<R>(m, in, P.gamma, d);
+        FaceOut<R> o = face_solve<R>(m, in, P.gamma, d, P.flux, P.efield == EFIELD_FCT);
         for (int v = 0; v < 5; v++) fd.F[v][fc] = o.F[v];
         for (int a = 0; a < 3; a++) fd.vbar[a][fc] = o.vbar[a];
+        for (int a = 0; a < 3; a++) fd.Fb[a][fc] = o.Fb[a];
         fd.cmax[fc] = o.cmax;
         fd.cmin[fc] = o.cmin;
         if (st) {
@@ -1153,6 +1189,21 @@ static R uct_E(const Grid& G, const FaceDataT<R> fd[3], const std::vector<R> Bf[
     term[t] = hll_edge(ap, am, vL, BL, vR, BR);
   }
   return -term[0] + term[1];
+}
+
+// Flux constrained transport (Sec. 3.4; Balsara & Spicer 1999): the electric field on the edge along e at
+// vertex-index position p is the average of the induction fluxes on the four faces that share the edge.  With
+// (e, d1, d2) cyclic and E = -v~ x B~, the flux along d1 of B~^d2 is -E_e and the flux along d2 of B~^d1 is +E_e;
+// the d1-faces sharing the edge sit at p and p - e_d2, the d2-faces at p and p - e_d1.
+template <class R> static R fct_E(const Grid& G, const FaceDataT<R> fd[3], int e, const int p[3]) {
+  const int d1 = (e + 1) % 3, d2 = (e + 2) % 3;
+  int q1[3] = {p[0], p[1], p[2]};
+  q1[d2] -= 1;
+  int q2[3] = {p[0], p[1], p[2]};
+  q2[d1] -= 1;
+  const R f1 = fd[d1].Fb[d2][G.at(p)] + fd[d1].Fb[d2][G.at(q1)];
+  const R f2 = fd[d2].Fb[d1][G.at(p)] + fd[d2].Fb[d1][G.at(q2)];
+  return R(0.25) * (f2 - f1);
 }
 
 struct RhsOut {
@@ -1224,7 +1275,7 @@ static void rhs(const Grid& G, const VertexMetric& vm, const OParams& P, double 
         for (int i = lo[0]; i <= hi[0]; i++) {
           const int p[3] = {i, j, k};
           const long c = G.at(p);
-          const R E = uct_E(G, fd, Bf, e, p);
+          const R E = (P.efield == EFIELD_FCT) ? fct_E(G, fd, e, p) : uct_E(G, fd, Bf, e, p);
           const R dG = (GA[c + G.s[e]] - GA[c]) / R(G.dx[e]);
           dU[5 + e][c] = -E - dG;
         }
@@ -1329,6 +1380,8 @@ static void prim2con_grid(const Grid& G, const VertexMetric& vm, const OParams& 
 // ------------------------------------------------------------------------------------------------------
 // Classical RK4 stage (method of lines): k_s = L(U_s); U_{s+1} = U_n + c_{s+1} dt k_s, c = (1/2, 1/2, 1);
 // U_acc accumulates b_s dt k_s, b = (1/6, 1/3, 1/3, 1/6); the last stage writes U_n + U_acc + dt/6 k_3.
+// Stages 4 and 5 are the two stages of RK2, the explicit midpoint method: U_1 = U_n + dt/2 k(U_n), then
+// U_{n+1} = U_n + dt k(U_1) (U_acc unused).
 // Stage order (Sec. 3.9): ghost fill U_s, con2prim on the interior, ghost fill primitives, RHS, combine.
 
 static void owned_range(const Grid& G, int v, int lo[3], int hi[3]) {
@@ -1364,8 +1417,12 @@ static void rk_stage(const Grid& G, const VertexMetric& vm, const OParams& P, in
           } else if (stage < 3) {
             Uacc[v][c] = Uacc[v][c] + bw[stage] * dt * kv;
             Unext[v][c] = Un[v][c] + cnext[stage] * dt * kv;
-          } else {
+          } else if (stage == 3) {
             Unext[v][c] = Un[v][c] + Uacc[v][c] + bw[3] * dt * kv;
+          } else if (stage == 4) {  // RK2 (explicit midpoint), first stage
+            Unext[v][c] = Un[v][c] + 0.5 * dt * kv;
+          } else {  // RK2, second stage: the slope at the midpoint state
+            Unext[v][c] = Un[v][c] + dt * kv;
           }
         }
   }
@@ -1990,6 +2047,40 @@ void oracle_batch_prim2con(const OParams* p, long n, const double* m16, const do
                            double* cons5) {
   for (long q = 0; q < n; q++) oracle_point_prim2con(p, m16 + 16 * q, prim5 + 5 * q, B3 + 3 * q, cons5 + 5 * q,
                                                      nullptr);
+}
+
+// One face solve from explicit states (for pins): L8 and R8 hold rho, p, u^x, u^y, u^z (u = W v) and the
+// undensitised B^x, B^y, B^z of the left and right sides (the normal entry unused), Bn the densitised normal
+// field, m16 the face metric.  out (13): the hydro flux (5), the induction fluxes along d of B~^x,y,z (3, the
+// normal one 0; computed when p->efield selects flux constrained transport), c_max, c_min, the upwind v~ (3).
+void oracle_point_face(const OParams* p, const double* m16, const double* L8, const double* R8, double Bn, int d,
+                       double* out) {
+  Metric3<double> m;
+  m.alp = m16[0];
+  for (int a = 0; a < 3; a++) m.beta[a] = m16[1 + a];
+  for (int a = 0; a < 3; a++)
+    for (int c = 0; c < 3; c++) {
+      m.g[a][c] = m16[4 + SYM[a][c]];
+      m.K[a][c] = m16[10 + SYM[a][c]];
+    }
+  metric_complete(m);
+  FaceInput in;
+  const double* side[2] = {L8, R8};
+  for (int s = 0; s < 2; s++) {
+    in.rho[s] = side[s][0];
+    in.press[s] = side[s][1];
+    for (int a = 0; a < 3; a++) {
+      in.u[s][a] = side[s][2 + a];
+      in.Bt[s][a] = side[s][5 + a];
+    }
+  }
+  in.Bn = Bn;
+  const FaceOut<double> o = face_solve<double>(m, in, p->gamma, d, p->flux, p->efield == EFIELD_FCT);
+  for (int v = 0; v < 5; v++) out[v] = o.F[v];
+  for (int a = 0; a < 3; a++) out[5 + a] = o.Fb[a];
+  out[8] = o.cmax;
+  out[9] = o.cmin;
+  for (int a = 0; a < 3; a++) out[10 + a] = o.vbar[a];
 }
 
 // Reconstruction of one cell from five values: returns the lower and upper face values.

@@ -31,6 +31,8 @@ import numpy as np
 RECON_MINMOD, RECON_PPM, RECON_WENOZ = 0, 1, 2
 BC_PERIODIC, BC_COPY = 0, 1
 GAUGE_LORENZ, GAUGE_ALGEBRAIC = 0, 1
+FLUX_HLLE, FLUX_LXF = 0, 1          # Riemann solver (Eq. HLLEfluxes, Eq. LxFfluxes)
+EFIELD_UCT, EFIELD_FCT = 0, 1       # edge electric field (upwind or flux constrained transport)
 
 PRIM_NAMES = ("rho", "press", "velx", "vely", "velz")
 CONS_NAMES = ("D", "Sx", "Sy", "Sz", "tau")
@@ -104,7 +106,8 @@ class Workload:
 
 def default_params(**kw) -> dict:
     p = dict(gamma=5.0 / 3.0, rho_atm=1e-7, K_atm=1.0, gamma_atm=5.0 / 3.0, c2p_tol=1e-13, c2p_maxiter=100,
-             brent_maxiter=300, W_max=50.0, recon=RECON_PPM, gauge=GAUGE_LORENZ, xi_lorenz=0.0, use_fallback=1)
+             brent_maxiter=300, W_max=50.0, recon=RECON_PPM, gauge=GAUGE_LORENZ, xi_lorenz=0.0, use_fallback=1,
+             flux=FLUX_HLLE, efield=EFIELD_UCT)
     p.update(kw)
     return p
 
