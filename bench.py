@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--batch-blocks", type=int, default=512)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward measurement")
     ap.add_argument("--adjoint-n", type=int, default=64, help="cells per axis of the adjoint workload")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the Lax-Friedrichs / flux-CT / RK2 step measurements")
     ap.add_argument("--no-coupling", action="store_true",
                     help="skip the stress-energy tensor and time-dependent-metric step measurements")
     ap.add_argument("--profile-region", choices=("none", "forward", "adjoint", "batched", "coupling"), default="none",
@@ -422,6 +424,36 @@ def run_coupling(args, s, U, P, M, w, dev, stream):
                             "overhead": ms_dyn / ms_frozen - 1.0, "steps": steps}}
 
 
+def run_variants(args, s, U, P, w, dev, stream):
+    """The paper's alternative schemes on the benchmark block: one RK4 step with the Lax-Friedrichs flux, with flux
+    constrained transport, with both, and one RK2 step of the default scheme (rates per RK stage)."""
+    import torch
+
+    from paper_2406_11669_gb300 import asterx as A
+
+    base = s.p
+    out = {}
+    steps = max(1, min(args.steps, 3))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, flux, efield, rk2 in (("lxf", 1, 0, False), ("fct", 0, 1, False), ("lxf_fct", 1, 1, False),
+                                    ("rk2", 0, 0, True)):
+        s.p = A.params_struct(dict(s.params, flux=flux, efield=efield))
+        step = s.rk2_step if rk2 else s.rk4_step
+        step(U, P, w.dt)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            step(U, P, w.dt)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        stages = 2 if rk2 else 4
+        out[name] = {"ms_per_step": ms, "value": w.interior_cells * stages / (ms / 1e3), "unit": UNIT,
+                     "stages_per_step": stages}
+    s.p = base
+    return out
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -564,6 +596,8 @@ def run_ours(args):
               "clocks": clk, "roofline": roofline, "c2p_counters_timed": c2p, "state_finite": finite}
     if not args.no_coupling:
         result["coupling"] = run_coupling(args, s, U, P, M, w, dev, stream)
+    if not args.no_variants:
+        result["variants"] = run_variants(args, s, U, P, w, dev, stream)
     if not args.no_batched:
         result["batched"] = run_batched(args, dev, stream)
     if not args.no_adjoint:

@@ -55,6 +55,8 @@ typedef enum {
 typedef enum { ASTERX_RECON_MINMOD = 0, ASTERX_RECON_PPM = 1, ASTERX_RECON_WENOZ = 2 } asterx_recon;
 typedef enum { ASTERX_BC_PERIODIC = 0, ASTERX_BC_COPY = 1 } asterx_bc;
 typedef enum { ASTERX_GAUGE_LORENZ = 0, ASTERX_GAUGE_ALGEBRAIC = 1 } asterx_gauge;
+typedef enum { ASTERX_FLUX_HLLE = 0, ASTERX_FLUX_LXF = 1 } asterx_flux;
+typedef enum { ASTERX_EFIELD_UCT = 0, ASTERX_EFIELD_FCT = 1 } asterx_efield;
 
 /* Physics parameters (HOST struct, read during the call). */
 typedef struct {
@@ -70,6 +72,11 @@ typedef struct {
   int gauge;           /* asterx_gauge; the generalised Lorenz gauge is the paper's default (Sec. 3.4) */
   double xi_lorenz;    /* Lorenz damping xi; 0 => 1.5 / dt (Sec. 3.4) */
   int use_fallback;    /* 1: Palenzuela fallback after a Noble failure */
+  int flux;            /* asterx_flux: HLLE (Eq. HLLEfluxes, the default) or Lax-Friedrichs (Eq. LxFfluxes,
+                          c_wave = max(c_max, c_min)) for the hydro fluxes */
+  int efield;          /* asterx_efield: upwind constrained transport (Sec. 3.4 (i)-(iii), Eq. eq3.20, the
+                          default) or flux constrained transport (Sec. 3.4: the average of the induction-equation
+                          fluxes, from the same Riemann solver, on the four faces sharing an edge) */
 } asterx_params;
 
 /* Geometry of one block (HOST struct). */
@@ -161,6 +168,13 @@ asterx_status asterx_rk4_step_host(const asterx_params *p, const asterx_block *b
                                    double *const *h_U9, double *const *h_P5, asterx_state *dU, asterx_prims *dP,
                                    asterx_c2p_stats *stats, void *ws, size_t ws_bytes, asterx_stream stream);
 
+/* One RK2 step in place (Sec. 5 compares RK2 with RK4; read as the explicit midpoint method):
+ * U_1 = U_n + dt/2 L(U_n), U_{n+1} = U_n + dt L(U_1), each stage with ghost fill and recovery as in
+ * asterx_rk_stage.  Otherwise as asterx_rk4_step. */
+asterx_status asterx_rk2_step(const asterx_params *p, const asterx_block *blk, double dt, asterx_state *U,
+                              asterx_prims *P, signed char *flags, asterx_c2p_stats *stats, void *ws,
+                              size_t ws_bytes, asterx_stream stream);
+
 /* ---- coupling to a spacetime solver ----
  *
  * Stress-energy tensor T_{mu nu} (Eq. tmunu with both indices lowered by the 4-metric; T lives at vertices,
@@ -196,7 +210,9 @@ asterx_status asterx_rk4_step_metrics(const asterx_params *p, const asterx_block
  * only: g..g+n-1 along cell-like axes and along periodic axes (there the vertex index g+n is the periodic image
  * of g), g..g+n along vertex-like axes with copy BCs.  Adjoint inputs are read there only; outputs are zero
  * everywhere else.  `aws` is a second, caller-owned
- * workspace of asterx_adjoint_workspace_size() bytes (256-byte aligned); `ws` is the prepared forward one. */
+ * workspace of asterx_adjoint_workspace_size() bytes (256-byte aligned); `ws` is the prepared forward one.
+ * The stage adjoints differentiate the default scheme (flux HLLE, efield UCT); other switches return
+ * ASTERX_EINVAL. */
 size_t asterx_adjoint_workspace_size(const asterx_block *blk);
 
 /* lam = (dL/dU)^T mu for the right-hand side L of asterx_rhs at state U (U unchanged; P: guess in, the

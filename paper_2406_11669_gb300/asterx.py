@@ -16,7 +16,7 @@ import os
 from . import build as _build
 
 ASTERX_OK, ASTERX_EINVAL, ASTERX_ECUDA, ASTERX_ENOMEM, ASTERX_EC2P, ASTERX_ETIMEOUT = range(6)
-ABI_VERSION = 1
+ABI_VERSION = 2
 
 
 class AsterxError(RuntimeError):
@@ -29,7 +29,8 @@ class Params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("rho_atm", ctypes.c_double), ("K_atm", ctypes.c_double),
                 ("gamma_atm", ctypes.c_double), ("c2p_tol", ctypes.c_double), ("c2p_maxiter", ctypes.c_int),
                 ("brent_maxiter", ctypes.c_int), ("W_max", ctypes.c_double), ("recon", ctypes.c_int),
-                ("gauge", ctypes.c_int), ("xi_lorenz", ctypes.c_double), ("use_fallback", ctypes.c_int)]
+                ("gauge", ctypes.c_int), ("xi_lorenz", ctypes.c_double), ("use_fallback", ctypes.c_int),
+                ("flux", ctypes.c_int), ("efield", ctypes.c_int)]
 
 
 class Block(ctypes.Structure):
@@ -87,6 +88,7 @@ def lib():
         L.asterx_rhs.argtypes = [P, B, S, Pr, S, ctypes.c_double, vp, sz, st]
         L.asterx_rk_stage.argtypes = [P, B, ctypes.c_int, ctypes.c_double, S, S, S, S, Pr, vp, vp, vp, sz, st]
         L.asterx_rk4_step.argtypes = [P, B, ctypes.c_double, S, Pr, vp, vp, vp, sz, st]
+        L.asterx_rk2_step.argtypes = [P, B, ctypes.c_double, S, Pr, vp, vp, vp, sz, st]
         L.asterx_rk4_step_host.argtypes = [P, B, ctypes.c_double, ctypes.POINTER(ctypes.c_void_p),
                                            ctypes.POINTER(ctypes.c_void_p), S, Pr, vp, vp, sz, st]
         L.asterx_tmunu.argtypes = [P, B, M, S, Pr, ctypes.POINTER(TmunuFields), vp, sz, st]
@@ -119,7 +121,7 @@ def lib():
         L.asterx_profile_disable.restype = None
         L.asterx_dfma_probe.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_long, st]
         for name in ("asterx_prepare", "asterx_prim2con", "asterx_con2prim", "asterx_fill_ghosts", "asterx_rhs",
-                     "asterx_rk_stage", "asterx_rk4_step", "asterx_rk4_step_host", "asterx_tmunu",
+                     "asterx_rk_stage", "asterx_rk4_step", "asterx_rk2_step", "asterx_rk4_step_host", "asterx_tmunu",
                      "asterx_rk4_step_metrics", "asterx_profile_enable",
                      "asterx_profile_read", "asterx_dfma_probe"):
             getattr(L, name).restype = ctypes.c_int
@@ -147,7 +149,7 @@ def _check(status: int, what: str):
 def params_struct(p: dict) -> Params:
     return Params(p["gamma"], p["rho_atm"], p["K_atm"], p["gamma_atm"], p["c2p_tol"], int(p["c2p_maxiter"]),
                   int(p["brent_maxiter"]), p["W_max"], int(p["recon"]), int(p["gauge"]), p["xi_lorenz"],
-                  int(p["use_fallback"]))
+                  int(p["use_fallback"]), int(p.get("flux", 0)), int(p.get("efield", 0)))
 
 
 def block_struct(n, g, x0, dx, bc) -> Block:
@@ -271,6 +273,13 @@ class Solver:
         sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
         _check(lib().asterx_rk4_step(*self._args(), float(dt), ctypes.byref(u), ctypes.byref(p), fl, sp,
                                      self.ws_ptr, self.ws_bytes, _stream(stream)), "asterx_rk4_step")
+
+    def rk2_step(self, U, P, dt, flags=None, stats=None, stream=None):
+        u, p = state_struct(U), prims_struct(P)
+        fl = ctypes.c_void_p(flags.data_ptr()) if flags is not None else None
+        sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
+        _check(lib().asterx_rk2_step(*self._args(), float(dt), ctypes.byref(u), ctypes.byref(p), fl, sp,
+                                     self.ws_ptr, self.ws_bytes, _stream(stream)), "asterx_rk2_step")
 
     def rk4_step_host(self, hU, hP, dU, dP, dt, stats=None, stream=None):
         """hU (9, ...) and hP (5, ...) are pinned host tensors; dU, dP device tensors of the same shapes."""

@@ -14,7 +14,7 @@ using namespace asterx;
 
 namespace {
 
-constexpr int kAbiVersion = 1;
+constexpr int kAbiVersion = 2;
 constexpr size_t kAlign = 256;
 
 long padded_V(const asterx_block* b) {
@@ -50,6 +50,8 @@ bool params_ok(const asterx_params* p) {
   if (p->recon < ASTERX_RECON_MINMOD || p->recon > ASTERX_RECON_WENOZ) return false;
   if (p->gauge != ASTERX_GAUGE_LORENZ && p->gauge != ASTERX_GAUGE_ALGEBRAIC) return false;
   if (!(std::isfinite(p->xi_lorenz) && p->xi_lorenz >= 0.0)) return false;
+  if (p->flux != ASTERX_FLUX_HLLE && p->flux != ASTERX_FLUX_LXF) return false;
+  if (p->efield != ASTERX_EFIELD_UCT && p->efield != ASTERX_EFIELD_FCT) return false;
   return p->use_fallback == 0 || p->use_fallback == 1;
 }
 
@@ -131,6 +133,8 @@ StageArgs make_args(const asterx_params* p, const asterx_block* blk, void* ws) {
   a.c2p_maxiter = p->c2p_maxiter;
   a.brent_maxiter = p->brent_maxiter;
   a.use_fallback = p->use_fallback;
+  a.flux = p->flux;
+  a.efield = p->efield;
   return a;
 }
 
@@ -368,6 +372,27 @@ asterx_status asterx_rk4_step(const asterx_params* p, const asterx_block* blk, d
     if (st != ASTERX_OK) return st;
   }
   return ASTERX_OK;
+}
+
+asterx_status asterx_rk2_step(const asterx_params* p, const asterx_block* blk, double dt, asterx_state* U,
+                              asterx_prims* P, signed char* flags, asterx_c2p_stats* stats, void* ws,
+                              size_t ws_bytes, asterx_stream stream) {
+  asterx_status st = common_checks(p, blk, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!finite_pos(dt) || !set_ok<asterx_state, 9>(U) || !set_ok<asterx_prims, 5>(P)) return ASTERX_EINVAL;
+  if (stats && ((uintptr_t)stats % 8) != 0) return ASTERX_EINVAL;
+  StageArgs a = make_args(p, blk, ws);
+  const long V = a.b.V;
+  F9 un = f9(U), acc, mid;
+  for (int v = 0; v < 9; v++) {
+    acc.f[v] = a.w.uacc + v * V;  // unused by the RK2 combine
+    mid.f[v] = a.w.ustage + v * V;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(stats);
+  st = stage_impl(a, 4, dt, un, un, mid, acc, f5(P), flags, cnt, s);  // U_1 = U_n + dt/2 L(U_n)
+  if (st != ASTERX_OK) return st;
+  return stage_impl(a, 5, dt, un, mid, un, acc, f5(P), flags, cnt, s);  // U_{n+1} = U_n + dt L(U_1)
 }
 
 asterx_status asterx_tmunu(const asterx_params* p, const asterx_block* blk, const asterx_metric* metric,
@@ -745,10 +770,16 @@ static asterx_status adj_checks(const asterx_params* p, const asterx_block* blk,
   return ASTERX_OK;
 }
 
+// the stage adjoints differentiate the default scheme (HLLE fluxes, upwind constrained transport) only
+static asterx_status adj_scheme_checks(const asterx_params* p) {
+  return (p->flux == ASTERX_FLUX_HLLE && p->efield == ASTERX_EFIELD_UCT) ? ASTERX_OK : ASTERX_EINVAL;
+}
+
 asterx_status asterx_rhs_adjoint(const asterx_params* p, const asterx_block* blk, double dt, const asterx_state* U,
                                  asterx_prims* P, const asterx_state* mu, asterx_state* lam, void* ws,
                                  size_t ws_bytes, void* aws, size_t aws_bytes, asterx_stream stream) {
   asterx_status st = adj_checks(p, blk, dt, ws, ws_bytes, aws, aws_bytes);
+  if (st == ASTERX_OK) st = adj_scheme_checks(p);
   if (st != ASTERX_OK) return st;
   if (!set_ok<asterx_state, 9>(U) || !set_ok<asterx_prims, 5>(P) || !set_ok<asterx_state, 9>(mu) ||
       !set_ok<asterx_state, 9>(lam))
@@ -773,6 +804,7 @@ asterx_status asterx_rk_stage_adjoint(const asterx_params* p, const asterx_block
                                       const asterx_state* lam_acc, asterx_state* lam_s, void* ws, size_t ws_bytes,
                                       void* aws, size_t aws_bytes, asterx_stream stream) {
   asterx_status st = adj_checks(p, blk, dt, ws, ws_bytes, aws, aws_bytes);
+  if (st == ASTERX_OK) st = adj_scheme_checks(p);
   if (st != ASTERX_OK) return st;
   if (stage < 0 || stage > 3) return ASTERX_EINVAL;
   if (!set_ok<asterx_state, 9>(Us) || !set_ok<asterx_prims, 5>(P) || !set_ok<asterx_state, 9>(lam_next) ||
@@ -805,6 +837,7 @@ asterx_status asterx_rk4_step_adjoint(const asterx_params* p, const asterx_block
                                       const asterx_state* Un, asterx_prims* P, asterx_state* lam, void* ws,
                                       size_t ws_bytes, void* aws, size_t aws_bytes, asterx_stream stream) {
   asterx_status st = adj_checks(p, blk, dt, ws, ws_bytes, aws, aws_bytes);
+  if (st == ASTERX_OK) st = adj_scheme_checks(p);
   if (st != ASTERX_OK) return st;
   if (!set_ok<asterx_state, 9>(Un) || !set_ok<asterx_prims, 5>(P) || !set_ok<asterx_state, 9>(lam))
     return ASTERX_EINVAL;
@@ -892,6 +925,7 @@ asterx_status asterx_rk4_adjoint_steps(const asterx_params* p, const asterx_bloc
                                        const asterx_state* ckpt, asterx_prims* P, asterx_state* lam, void* ws,
                                        size_t ws_bytes, void* aws, size_t aws_bytes, asterx_stream stream) {
   asterx_status st = adj_checks(p, blk, dt, ws, ws_bytes, aws, aws_bytes);
+  if (st == ASTERX_OK) st = adj_scheme_checks(p);
   if (st != ASTERX_OK) return st;
   if (nsteps < 1 || !ckpt) return ASTERX_EINVAL;
   for (int k = 0; k < nsteps; k++)

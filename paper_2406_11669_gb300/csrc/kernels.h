@@ -12,6 +12,8 @@ struct StageArgs {
   Ws w;
   int recon;
   int gauge;
+  int flux;    // 0 HLLE, 1 Lax-Friedrichs
+  int efield;  // 0 upwind constrained transport, 1 flux constrained transport
   double gamma, rho_atm, K_atm, gamma_atm, c2p_tol, W_max, xi;
   double gfac;  // Gamma / (Gamma - 1)
   int c2p_maxiter, brent_maxiter, use_fallback;

@@ -28,9 +28,10 @@ enum { FG_ALP = 0, FG_BETA = 1, FG_G = 4, FG_GUDD = 10, FG_SQG = 11, FG_IALP = 1
 // Vertex geometry record: lapse, shift, sqrt(det gamma), inverse metric.
 enum { VG_ALP = 0, VG_BETA = 1, VG_SQG = 4, VG_GU = 5, NVG = 11 };
 
-// Face data written by the face kernel (per face, one set per direction): HLLE flux of the 5 hydro variables,
-// the upwind transverse velocities of Eq. uct1 (components (d+1)%3 and (d+2)%3), c_max and c_min.
-enum { FD_F = 0, FD_VB1 = 5, FD_VB2 = 6, FD_CMAX = 7, FD_CMIN = 8, NFD = 9 };
+// Face data written by the face kernel (per face, one set per direction): HLLE (or Lax-Friedrichs) flux of the
+// 5 hydro variables, the upwind transverse velocities of Eq. uct1 (components (d+1)%3 and (d+2)%3), c_max and
+// c_min, and with flux constrained transport the induction fluxes along d of B~^((d+1)%3) and B~^((d+2)%3).
+enum { FD_F = 0, FD_VB1 = 5, FD_VB2 = 6, FD_CMAX = 7, FD_CMIN = 8, FD_EB1 = 9, FD_EB2 = 10, NFD = 11 };
 
 // Reconstructed variables per cell and direction: rho, p, u^x, u^y, u^z (u = W v), the two transverse B.
 enum { NREC = 7 };

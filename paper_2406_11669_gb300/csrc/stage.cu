@@ -56,6 +56,7 @@ __device__ __forceinline__ long stride(const Blk& b, int d) { return d == 0 ? 1 
 struct StageConsts {
   double gamma, gfac, dt, xi;
   int stage, lorenz;
+  int lxf, fct;  // Lax-Friedrichs fluxes; flux constrained transport
   C2PParams cp;
   unsigned long long* stats;
 };
@@ -506,8 +507,10 @@ struct ReconPPM {
 
 // Face solve along D for faces g..g+n along D and all transverse indices: left state = upper value of cell
 // f-1, right state = lower value of cell f; HLLE (Eq. HLLEfluxes) and the upwind velocities of Eq. uct1.
-template <int D>
-struct Faces {
+// ALT: the alternative schemes (Lax-Friedrichs fluxes, flux constrained transport), a separate instantiation
+// (FacesAlt) so that the default kernel (Faces) keeps its register budget.
+template <int D, bool ALT>
+struct FaceSolve {
   static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts& k, long t) {
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     const Blk& b = r.b;
@@ -531,6 +534,7 @@ struct Faces {
     const double width = fg[FG_WIDTH * b.V + c];
     const double Bn = r.w.bf[D * b.V + c] * fg[FG_ISQG * b.V + c];
     SideOut s[2];
+    double Bt[2][2];  // transverse B^T1, B^T2 (undensitised) of each side
 #pragma unroll
     for (int side = 0; side < 2; side++) {
       const long cc = side == 0 ? c - st : c;
@@ -538,8 +542,8 @@ struct Faces {
       const double u[3] = {rr[2 * b.V], rr[3 * b.V], rr[4 * b.V]};
       double B[3];
       B[D] = Bn;
-      B[T1] = rr[5 * b.V];
-      B[T2] = rr[6 * b.V];
+      B[T1] = Bt[side][0] = rr[5 * b.V];
+      B[T2] = Bt[side][1] = rr[6 * b.V];
       face_side(m, ia, width, D, rr[0], rr[b.V], u, B, k.gamma, k.gfac, s[side]);
     }
     const double cmax = fmax(0.0, fmax(s[0].lp, s[1].lp));
@@ -547,15 +551,38 @@ struct Faces {
     const double den = cmax + cmin;
     if (den > 0.0) {
       const double iden = 1.0 / den;
-      for (int v = 0; v < 5; v++)
-        fd[(FD_F + v) * b.V + c] =
-            (cmin * s[1].F[v] + cmax * s[0].F[v] - cmax * cmin * (s[1].U[v] - s[0].U[v])) * iden;
+      if (ALT && k.lxf) {  // Eq. LxFfluxes: c_wave = max(c_max, c_min)
+        const double cw = fmax(cmax, cmin);
+        for (int v = 0; v < 5; v++)
+          fd[(FD_F + v) * b.V + c] = 0.5 * (s[1].F[v] + s[0].F[v] - cw * (s[1].U[v] - s[0].U[v]));
+      } else {
+        for (int v = 0; v < 5; v++)
+          fd[(FD_F + v) * b.V + c] =
+              (cmin * s[1].F[v] + cmax * s[0].F[v] - cmax * cmin * (s[1].U[v] - s[0].U[v])) * iden;
+      }
       fd[FD_VB1 * b.V + c] = (cmax * s[0].vt[T1] + cmin * s[1].vt[T1]) * iden;
       fd[FD_VB2 * b.V + c] = (cmax * s[0].vt[T2] + cmin * s[1].vt[T2]) * iden;
     } else {
       for (int v = 0; v < 5; v++) fd[(FD_F + v) * b.V + c] = 0.5 * (s[0].F[v] + s[1].F[v]);
       fd[FD_VB1 * b.V + c] = 0.5 * (s[0].vt[T1] + s[1].vt[T1]);
       fd[FD_VB2 * b.V + c] = 0.5 * (s[0].vt[T2] + s[1].vt[T2]);
+    }
+    if (ALT && k.fct) {
+      // induction fluxes along D of B~^T1 and B~^T2 (v~^D B~^a - v~^a B~^D) with the same Riemann solver
+      const double Bnt = r.w.bf[D * b.V + c];
+      const double sqg = m.sqg;
+#pragma unroll
+      for (int q = 0; q < 2; q++) {
+        const int a = q == 0 ? T1 : T2;
+        const double BL = sqg * Bt[0][q], BR = sqg * Bt[1][q];
+        const double FL = s[0].vt[D] * BL - s[0].vt[a] * Bnt;
+        const double FR = s[1].vt[D] * BR - s[1].vt[a] * Bnt;
+        double Fh;
+        if (den > 0.0 && k.lxf) Fh = 0.5 * (FR + FL - fmax(cmax, cmin) * (BR - BL));
+        else if (den > 0.0) Fh = (cmin * FR + cmax * FL - cmax * cmin * (BR - BL)) / den;
+        else Fh = 0.5 * (FL + FR);
+        fd[(FD_EB1 + q) * b.V + c] = Fh;
+      }
     }
     fd[FD_CMAX * b.V + c] = cmax;
     fd[FD_CMIN * b.V + c] = cmin;
@@ -568,9 +595,14 @@ struct Faces {
     }
   }
 };
+template <int D>
+struct Faces : FaceSolve<D, false> {};
+template <int D>
+struct FacesAlt : FaceSolve<D, true> {};
 
 // ----------------------------------------------------------------------------------------------------------
-// RK4 combine (classical): stage < 0 writes dU/dt.
+// Stage combine: classical RK4 (stages 0..3) or RK2, the explicit midpoint method (stages 4 and 5); stage < 0
+// writes dU/dt.
 
 __device__ __forceinline__ void combine(int stage, double dt, long c, int v, double k, const BlockRec& r) {
   if (stage < 0) {
@@ -584,8 +616,12 @@ __device__ __forceinline__ void combine(int stage, double dt, long c, int v, dou
   } else if (stage == 2) {
     r.Uacc.f[v][c] = r.Uacc.f[v][c] + (1.0 / 3.0) * dt * k;
     r.Unext.f[v][c] = r.Un.f[v][c] + 1.0 * dt * k;
-  } else {
+  } else if (stage == 3) {
     r.Unext.f[v][c] = r.Un.f[v][c] + r.Uacc.f[v][c] + (1.0 / 6.0) * dt * k;
+  } else if (stage == 4) {  // RK2 (explicit midpoint), first stage
+    r.Unext.f[v][c] = r.Un.f[v][c] + 0.5 * dt * k;
+  } else {  // RK2, second stage
+    r.Unext.f[v][c] = r.Un.f[v][c] + dt * k;
   }
 }
 
@@ -741,6 +777,17 @@ struct Edges {
     int i, j, kk;
     box.at(t, i, j, kk);
     const long c = lin(b, i, j, kk);
+    if (k.fct) {
+      // flux constrained transport: the average of the induction fluxes on the four faces sharing the edge; the
+      // flux along D1 of B~^D2 (slot EB1 of the D1-faces at c and c - e_D2) is -E, the flux along D2 of B~^D1
+      // (slot EB2 of the D2-faces at c and c - e_D1) is +E
+      const double* __restrict__ f1 = w.face + ((long)D1 * NFD + FD_EB1) * b.V;
+      const double* __restrict__ f2 = w.face + ((long)D2 * NFD + FD_EB2) * b.V;
+      const double Ee = 0.25 * ((f2[c] + f2[c - stride(b, D1)]) - (f1[c] + f1[c - stride(b, D2)]));
+      const double dG = (w.ga[c + stride(b, E)] - w.ga[c]) * b.idx[E];
+      combine(k.stage, k.dt, c, 5 + E, -Ee - dG, r);
+      return;
+    }
     double term[2];
 #pragma unroll
     for (int tt = 0; tt < 2; tt++) {
@@ -884,6 +931,8 @@ static StageConsts consts_of(const StageArgs& a, int stage, double dt, unsigned 
   k.xi = a.xi > 0.0 ? a.xi : (dt > 0.0 ? 1.5 / dt : 0.0);
   k.stage = stage;
   k.lorenz = (a.gauge == 0);
+  k.lxf = (a.flux == 1);
+  k.fct = (a.efield == 1);
   k.cp.gamma = a.gamma;
   k.cp.rho_atm = a.rho_atm;
   k.cp.K_atm = a.K_atm;
@@ -924,7 +973,8 @@ static void seq_dir(const T& t, const StageConsts& k, int recon, cudaStream_t s)
   else launch<ReconWENO<D>>(t, k, KIND_RCHUNK_X + D, s);
   const bool mark = g_prof.on && g_prof.n < g_prof.cap && !capturing(s);
   if (mark) cudaEventRecord(g_prof.ev[2 * g_prof.n], s);
-  launch<Faces<D>>(t, k, KIND_FACES_X + D, s);
+  if (k.lxf || k.fct) launch<FacesAlt<D>>(t, k, KIND_FACES_X + D, s);
+  else launch<Faces<D>>(t, k, KIND_FACES_X + D, s);
   if (mark) cudaEventRecord(g_prof.ev[2 * g_prof.n++ + 1], s);
 }
 
@@ -940,7 +990,7 @@ static void seq_erec(const T& t, const StageConsts& k, cudaStream_t s) {
 
 template <class T>
 static void seq_rhs_tail(const T& t, const StageConsts& k, cudaStream_t s) {
-  seq_erec(t, k, s);
+  if (!k.fct) seq_erec(t, k, s);  // UCT's edge reconstruction (flux constrained transport needs none)
   launch<Vertex>(t, k, KIND_VERTEX, s);
   launch<Edges<0>>(t, k, KIND_EDGES_X, s);
   launch<Edges<1>>(t, k, KIND_EDGES_Y, s);
@@ -955,7 +1005,7 @@ static void seq_rhs(const T& t, const StageConsts& k, int recon, cudaStream_t s)
   seq_dir<0>(t, k, recon, s);
   seq_dir<1>(t, k, recon, s);
   seq_dir<2>(t, k, recon, s);
-  seq_erec(t, k, s);
+  if (!k.fct) seq_erec(t, k, s);
   launch<Vertex>(t, k, KIND_VERTEX, s);
   launch<Edges<0>>(t, k, KIND_EDGES_X, s);
   launch<Edges<1>>(t, k, KIND_EDGES_Y, s);
