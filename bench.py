@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--batch-blocks", type=int, default=512)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward measurement")
     ap.add_argument("--adjoint-n", type=int, default=64, help="cells per axis of the adjoint workload")
+    ap.add_argument("--no-tiled", action="store_true",
+                    help="skip the tiled-domain (ghost exchange between blocks) measurement")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the Lax-Friedrichs / flux-CT / RK2 step measurements")
     ap.add_argument("--no-coupling", action="store_true",
@@ -283,6 +285,53 @@ def run_batched(args, dev, stream):
             "steps": steps, "pool_bytes": int(pool_bytes),
             "single_equal_volume": {"n": side, "interior_cells": single_cells, "value": rate_s, "ms_per_step": ms_s},
             "batched_vs_single": rate_b / rate_s}
+
+
+def run_tiled(args, dev, stream, single_ms):
+    """The benchmark's 128^3 domain cut into 2x2x2 blocks of 64^3 and 4x4x4 blocks of 32^3, advanced by the batched
+    launch with same-level ghost exchange between the blocks, against the single 128^3 block (single_ms)."""
+    import numpy as np
+    import torch
+
+    from paper_2406_11669_gb300 import asterx as A
+    from paper_2406_11669_gb300 import workloads as W
+
+    w = W.config2(n=(args.n,) * 3)
+    M, U, P = _upload_block(w, dev)
+    out = {}
+    for k in (2, 4):
+        m = args.n // k
+        cuts = [list(range(0, args.n + 1, m))] * 3
+        entries = []
+        for bz in range(k):
+            for by in range(k):
+                for bx in range(k):
+                    lo = (bx * m, by * m, bz * m)
+                    sl = (slice(None),) + tuple(slice(lo[d], lo[d] + m + 2 * w.g + 1) for d in (2, 1, 0))
+                    x0 = tuple(w.x0[d] + lo[d] * w.dx[d] for d in range(3))
+                    entries.append(((m, m, m), w.g, x0, w.dx, w.bc, M[sl].contiguous(), U[sl].contiguous(),
+                                    P[sl].contiguous()))
+        batch = A.Batch(w.params, entries, device=dev, tiling=((k, k, k), cuts))
+        batch.prepare()
+        batch.prim2con()
+        steps = max(1, min(args.steps, 3))
+        batch.step(w.dt, nsteps=1)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.step(w.dt, nsteps=steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        finite = all(bool(torch.isfinite(e[6]).all()) for e in entries)
+        batch.release()
+        del batch, entries
+        torch.cuda.empty_cache()
+        out[f"{k}x{k}x{k}"] = {"block_n": m, "ms_per_step": ms, "value": w.interior_cells * 4 / (ms / 1e3),
+                               "unit": UNIT, "tiled_vs_single": single_ms / ms, "finite": finite}
+    del M, U, P
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_adjoint(args, dev, stream):
@@ -600,6 +649,8 @@ def run_ours(args):
         result["variants"] = run_variants(args, s, U, P, w, dev, stream)
     if not args.no_batched:
         result["batched"] = run_batched(args, dev, stream)
+    if not args.no_tiled:
+        result["tiled"] = run_tiled(args, dev, stream, ms_max / args.steps)
     if not args.no_adjoint:
         result["adjoint"] = run_adjoint(args, dev, stream)
     if not args.no_cpu_baseline:

@@ -299,6 +299,23 @@ asterx_status asterx_batched_step(const asterx_params *p, const asterx_batch_blo
  * for the workspace it prepares).  EINVAL for a null pointer. */
 asterx_status asterx_batch_release(void *ws);
 
+/* A batch whose blocks tile one rectangular domain on a common grid: nblk[0] x nblk[1] x nblk[2] blocks listed x
+ * fastest (block bx + nblk[0] (by + nblk[1] bz)); along axis d block b covers the interior cells
+ * cuts[d][b] .. cuts[d][b+1]-1 of the domain (cuts[d][0] = 0, every block at least 3 cells wide), all blocks
+ * share dx and the domain's boundary conditions, and each block's x0 is the first block's plus cuts * dx.
+ * asterx_batch_prepare_tiled replaces asterx_batch_prepare for such a batch: every later asterx_batch_prim2con
+ * and asterx_batched_step on this workspace fills the ghost layers a block shares with its neighbours (and
+ * across periodic boundaries) from the neighbours' owned values before the boundary-condition sweeps, so the
+ * tiled domain evolves as one block covering it would (same-level ghost exchange; no refinement levels).
+ * `cuts` are HOST arrays.  Returns ASTERX_EINVAL if the blocks do not tile the domain as described. */
+typedef struct {
+  int nblk[3];
+  const int *cuts[3];
+} asterx_tiling;
+asterx_status asterx_batch_prepare_tiled(const asterx_params *p, const asterx_batch_block *blocks, int nblocks,
+                                         const asterx_tiling *tiling, void *ws, size_t ws_bytes,
+                                         asterx_stream stream);
+
 /* ---- recovery for callers that cannot allocate device memory (the paper has no counterpart) ----
  *
  * Some callers cannot call cudaMalloc: a plugin inside a host application that owns all device memory and

@@ -59,6 +59,10 @@ class BatchBlock(ctypes.Structure):
     _fields_ = [("blk", Block), ("metric", Metric), ("U", State), ("P", Prims)]
 
 
+class Tiling(ctypes.Structure):
+    _fields_ = [("nblk", ctypes.c_int * 3), ("cuts", ctypes.POINTER(ctypes.c_int) * 3)]
+
+
 class C2PStats(ctypes.Structure):
     _fields_ = [("n_noble", ctypes.c_ulonglong), ("n_fallback", ctypes.c_ulonglong),
                 ("n_atm", ctypes.c_ulonglong), ("n_failed", ctypes.c_ulonglong), ("iters", ctypes.c_ulonglong)]
@@ -100,7 +104,9 @@ def lib():
         L.asterx_batch_prim2con.argtypes = [P, BB, ctypes.c_int, vp, sz, st]
         L.asterx_batched_step.argtypes = [P, BB, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, vp, sz, st]
         L.asterx_batch_release.argtypes = [vp]
-        for name in ("asterx_batch_prepare", "asterx_batch_prim2con", "asterx_batched_step", "asterx_batch_release"):
+        L.asterx_batch_prepare_tiled.argtypes = [P, BB, ctypes.c_int, ctypes.POINTER(Tiling), vp, sz, st]
+        for name in ("asterx_batch_prepare", "asterx_batch_prim2con", "asterx_batched_step", "asterx_batch_release",
+                     "asterx_batch_prepare_tiled"):
             getattr(L, name).restype = ctypes.c_int
         L.asterx_adjoint_workspace_size.restype = ctypes.c_size_t
         L.asterx_adjoint_workspace_size.argtypes = [B]
@@ -412,10 +418,21 @@ def con2prim_noalloc(params: dict, n, g, x0, dx, bc, metric, U, P, flags=None, s
 
 class Batch:
     """Many blocks advanced together by asterx_batched_step.  `blocks` is a list of (n, g, x0, dx, bc, metric,
-    U, P) with device tensors; all share `params`.  The pooled workspace is one torch allocation."""
+    U, P) with device tensors; all share `params`.  The pooled workspace is one torch allocation.  With
+    `tiling` = (nblk, cuts) — blocks per axis and per axis the nblk + 1 cell offsets of the block boundaries,
+    blocks listed x fastest — the blocks tile one domain and exchange their shared ghost layers."""
 
-    def __init__(self, params: dict, blocks, device="cuda"):
+    def __init__(self, params: dict, blocks, device="cuda", tiling=None):
         import torch
+        self.tiling = None
+        if tiling is not None:
+            nblk, cuts = tiling
+            self._cuts = [(ctypes.c_int * len(c))(*[int(x) for x in c]) for c in cuts]
+            t = Tiling()
+            for d in range(3):
+                t.nblk[d] = int(nblk[d])
+                t.cuts[d] = ctypes.cast(self._cuts[d], ctypes.POINTER(ctypes.c_int))
+            self.tiling = t
         self.params = dict(params)
         self.p = params_struct(self.params)
         self.keep = blocks  # tensors stay alive while the tables refer to them
@@ -435,8 +452,13 @@ class Batch:
         self.ws_ptr = ctypes.c_void_p(self.ws.data_ptr() + off)
 
     def prepare(self, stream=None):
-        _check(lib().asterx_batch_prepare(ctypes.byref(self.p), self.arr, self.nb, self.ws_ptr, self.ws_bytes,
-                                          _stream(stream)), "asterx_batch_prepare")
+        if self.tiling is not None:
+            _check(lib().asterx_batch_prepare_tiled(ctypes.byref(self.p), self.arr, self.nb, ctypes.byref(self.tiling),
+                                                    self.ws_ptr, self.ws_bytes, _stream(stream)),
+                   "asterx_batch_prepare_tiled")
+        else:
+            _check(lib().asterx_batch_prepare(ctypes.byref(self.p), self.arr, self.nb, self.ws_ptr, self.ws_bytes,
+                                              _stream(stream)), "asterx_batch_prepare")
 
     def prim2con(self, stream=None):
         _check(lib().asterx_batch_prim2con(ctypes.byref(self.p), self.arr, self.nb, self.ws_ptr, self.ws_bytes,

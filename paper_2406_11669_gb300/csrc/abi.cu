@@ -73,6 +73,7 @@ size_t ws_bytes_for(const asterx_block* b) {
 
 Blk make_blk(const asterx_block* in) {
   Blk b;
+  std::memset(&b, 0, sizeof(b));
   b.g = in->g;
   for (int d = 0; d < 3; d++) {
     b.n[d] = in->n[d];
@@ -176,6 +177,18 @@ struct StepGraph {
 };
 std::mutex g_graph_mu;
 std::vector<StepGraph> g_graphs;
+std::vector<void*> g_tiled;  // batch workspaces prepared as a tiled domain (guarded by g_graph_mu)
+
+void set_tiled(void* ws, bool tiled) {
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  g_tiled.erase(std::remove(g_tiled.begin(), g_tiled.end(), ws), g_tiled.end());
+  if (tiled) g_tiled.push_back(ws);
+}
+
+bool is_tiled(void* ws) {
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  return std::find(g_tiled.begin(), g_tiled.end(), ws) != g_tiled.end();
+}
 
 void drop_graphs(void* ws) {
   std::lock_guard<std::mutex> lock(g_graph_mu);
@@ -192,7 +205,7 @@ void drop_graphs(void* ws) {
 // the cached step graph for these launch parameters, captured on a private stream if there is none (null if
 // capture is not possible, e.g. inside the caller's own capture)
 cudaGraphExec_t step_graph(const StageArgs& a, const asterx_params* p, void* ws, const BlockRec* tab, const long* off,
-                           const long* totals, int nb, double dt, unsigned long long* stats) {
+                           const long* totals, int nb, double dt, unsigned long long* stats, const Tiling* til) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
   std::lock_guard<std::mutex> lock(g_graph_mu);
@@ -207,7 +220,7 @@ cudaGraphExec_t step_graph(const StageArgs& a, const asterx_params* p, void* ws,
   cudaError_t e = cudaStreamBeginCapture(ps, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     for (int stage = 0; stage < 4 && e == cudaSuccess; stage++)
-      e = launch_batch_stage(a, tab + (size_t)stage * nb, off, totals, nb, stage, dt, stats, ps);
+      e = launch_batch_stage(a, tab + (size_t)stage * nb, off, totals, nb, stage, dt, stats, ps, til);
     const cudaError_t e2 = cudaStreamEndCapture(ps, &graph);
     if (e == cudaSuccess) e = e2;
   }
@@ -481,8 +494,13 @@ asterx_status asterx_rk4_step_host(const asterx_params* p, const asterx_block* b
 
 static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// header: 4 stage tables, the item offsets, then room for a tiling (struct and up to 3 (nb + 1) cut offsets)
+static size_t batch_tiling_offset(int nb) {
+  return round_up(4 * (size_t)nb * sizeof(BlockRec) + (size_t)NKIND * (nb + 1) * sizeof(long), 16);
+}
+
 static size_t batch_header_bytes(int nb) {
-  return round_up(4 * (size_t)nb * sizeof(BlockRec) + (size_t)NKIND * (nb + 1) * sizeof(long), kAlign);
+  return round_up(batch_tiling_offset(nb) + sizeof(Tiling) + 3 * (size_t)(nb + 1) * sizeof(int), kAlign);
 }
 
 static bool batch_blocks_ok(const asterx_batch_block* blocks, int nb) {
@@ -532,11 +550,10 @@ size_t asterx_batch_workspace_size(const asterx_batch_block* blocks, int nblocks
   return batch_bytes(blocks, nblocks);
 }
 
-asterx_status asterx_batch_prepare(const asterx_params* p, const asterx_batch_block* blocks, int nblocks,
-                                   void* ws, size_t ws_bytes, asterx_stream stream) {
-  asterx_status st = batch_checks(p, blocks, nblocks, ws, ws_bytes);
-  if (st != ASTERX_OK) return st;
+static asterx_status batch_prepare_impl(const asterx_params* p, const asterx_batch_block* blocks, int nblocks,
+                                        const asterx_tiling* tl, void* ws, asterx_stream stream) {
   drop_graphs(ws);  // new tables: cached step graphs of this workspace no longer apply
+  set_tiled(ws, tl != nullptr);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int nb = nblocks;
   std::vector<BlockRec> tabs(4 * (size_t)nb);
@@ -555,6 +572,15 @@ asterx_status asterx_batch_prepare(const asterx_params* p, const asterx_batch_bl
       acc.f[v] = a.w.uacc + v * a.b.V;
       sb[0].f[v] = a.w.ustage + v * a.b.V;
       sb[1].f[v] = a.w.ustage + (9 + v) * a.b.V;
+    }
+    if (tl) {  // position in the block grid; sides with a neighbour (or a periodic wrap) take exchanged ghosts
+      const int c3[3] = {i % tl->nblk[0], (i / tl->nblk[0]) % tl->nblk[1], i / (tl->nblk[0] * tl->nblk[1])};
+      for (int d = 0; d < 3; d++) {
+        a.b.coord[d] = c3[d];
+        a.b.off[d] = tl->cuts[d][c3[d]];
+        if (c3[d] > 0 || a.b.bc[d] == ASTERX_BC_PERIODIC) a.b.halo |= 1 << (2 * d);
+        if (c3[d] < tl->nblk[d] - 1 || a.b.bc[d] == ASTERX_BC_PERIODIC) a.b.halo |= 1 << (2 * d + 1);
+      }
     }
     for (int stage = 0; stage < 4; stage++) {
       BlockRec& r = tabs[(size_t)stage * nb + i];
@@ -575,8 +601,67 @@ asterx_status asterx_batch_prepare(const asterx_params* p, const asterx_batch_bl
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(hdr + 4 * (size_t)nb * sizeof(BlockRec), offsets.data(), offsets.size() * sizeof(long),
                         cudaMemcpyHostToDevice, s);
+  std::vector<char> tbuf;
+  if (tl && e == cudaSuccess) {
+    Tiling t;
+    int at = 0;
+    for (int d = 0; d < 3; d++) {
+      t.nblk[d] = tl->nblk[d];
+      t.ntot[d] = tl->cuts[d][tl->nblk[d]];
+      t.bc[d] = blocks[0].blk.bc[d];
+      t.cut_at[d] = at;
+      at += tl->nblk[d] + 1;
+    }
+    tbuf.resize(sizeof(Tiling) + (size_t)at * sizeof(int));
+    std::memcpy(tbuf.data(), &t, sizeof(t));
+    int* cuts = reinterpret_cast<int*>(tbuf.data() + sizeof(Tiling));
+    for (int d = 0; d < 3; d++)
+      for (int q = 0; q <= tl->nblk[d]; q++) cuts[t.cut_at[d] + q] = tl->cuts[d][q];
+    e = cudaMemcpyAsync(hdr + batch_tiling_offset(nb), tbuf.data(), tbuf.size(), cudaMemcpyHostToDevice, s);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host tables go out of scope
   return cuda_status(e);
+}
+
+asterx_status asterx_batch_prepare(const asterx_params* p, const asterx_batch_block* blocks, int nblocks,
+                                   void* ws, size_t ws_bytes, asterx_stream stream) {
+  asterx_status st = batch_checks(p, blocks, nblocks, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  return batch_prepare_impl(p, blocks, nblocks, nullptr, ws, stream);
+}
+
+// the blocks tile one domain: nblk[0] nblk[1] nblk[2] blocks listed x fastest, each block's interior the cells
+// between consecutive cuts, common spacing and boundary conditions, origins consistent with the cuts
+static bool tiling_ok(const asterx_batch_block* blocks, int nb, const asterx_tiling* t) {
+  if (!t) return false;
+  long count = 1;
+  for (int d = 0; d < 3; d++) {
+    if (t->nblk[d] < 1 || !t->cuts[d] || t->cuts[d][0] != 0) return false;
+    for (int q = 0; q < t->nblk[d]; q++)
+      if (t->cuts[d][q + 1] - t->cuts[d][q] < blocks[0].blk.g) return false;  // at least g cells per block
+    count *= t->nblk[d];
+  }
+  if (count != nb) return false;
+  for (int i = 0; i < nb; i++) {
+    const asterx_block& b = blocks[i].blk;
+    const int c3[3] = {i % t->nblk[0], (i / t->nblk[0]) % t->nblk[1], i / (t->nblk[0] * t->nblk[1])};
+    for (int d = 0; d < 3; d++) {
+      if (b.n[d] != t->cuts[d][c3[d] + 1] - t->cuts[d][c3[d]]) return false;
+      if (b.dx[d] != blocks[0].blk.dx[d] || b.bc[d] != blocks[0].blk.bc[d]) return false;
+      const double x0 = blocks[0].blk.x0[d] + t->cuts[d][c3[d]] * b.dx[d];
+      if (std::fabs(b.x0[d] - x0) > 1e-9 * b.dx[d]) return false;
+    }
+  }
+  return true;
+}
+
+asterx_status asterx_batch_prepare_tiled(const asterx_params* p, const asterx_batch_block* blocks, int nblocks,
+                                         const asterx_tiling* tiling, void* ws, size_t ws_bytes,
+                                         asterx_stream stream) {
+  asterx_status st = batch_checks(p, blocks, nblocks, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!tiling_ok(blocks, nblocks, tiling)) return ASTERX_EINVAL;
+  return batch_prepare_impl(p, blocks, nblocks, tiling, ws, stream);
 }
 
 asterx_status asterx_batch_prim2con(const asterx_params* p, const asterx_batch_block* blocks, int nblocks,
@@ -584,10 +669,20 @@ asterx_status asterx_batch_prim2con(const asterx_params* p, const asterx_batch_b
   asterx_status st = batch_checks(p, blocks, nblocks, ws, ws_bytes);
   if (st != ASTERX_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool tiled = is_tiled(ws);
+  if (tiled) {  // the potentials' ghosts from the neighbouring blocks (stage-0 records: U_s = U)
+    long totals[NKIND];
+    batch_totals(blocks, nblocks, totals, nullptr);
+    const BlockRec* tab = reinterpret_cast<const BlockRec*>(ws);
+    const long* off =
+        reinterpret_cast<const long*>(static_cast<char*>(ws) + 4 * (size_t)nblocks * sizeof(BlockRec));
+    const Tiling* til = reinterpret_cast<const Tiling*>(static_cast<char*>(ws) + batch_tiling_offset(nblocks));
+    if (launch_batch_ghosts(tab, off, totals, nblocks, til, s) != cudaSuccess) return ASTERX_ECUDA;
+  }
   for (int i = 0; i < nblocks; i++) {
     StageArgs a = make_args(p, &blocks[i].blk, block_ws(blocks, nblocks, ws, i));
     F9 u = f9(&blocks[i].U);
-    cudaError_t e = launch_ghost_state(a.b, u, s);
+    cudaError_t e = tiled ? cudaSuccess : launch_ghost_state(a.b, u, s);
     if (e == cudaSuccess) e = launch_bfield(a.b, a.w, u, s);
     if (e == cudaSuccess) e = launch_prim2con(a, u, f5(&blocks[i].P), s);
     if (e != cudaSuccess) return ASTERX_ECUDA;
@@ -599,6 +694,7 @@ asterx_status asterx_batch_prim2con(const asterx_params* p, const asterx_batch_b
 asterx_status asterx_batch_release(void* ws) {
   if (!ws) return ASTERX_EINVAL;
   drop_graphs(ws);
+  set_tiled(ws, false);
   return ASTERX_OK;
 }
 
@@ -616,11 +712,13 @@ asterx_status asterx_batched_step(const asterx_params* p, const asterx_batch_blo
   StageArgs a = make_args(p, &blocks[0].blk, block_ws(blocks, nb, ws, 0));
   const BlockRec* tab = reinterpret_cast<const BlockRec*>(ws);
   const long* off = reinterpret_cast<const long*>(static_cast<char*>(ws) + 4 * (size_t)nb * sizeof(BlockRec));
+  const Tiling* til =
+      is_tiled(ws) ? reinterpret_cast<const Tiling*>(static_cast<char*>(ws) + batch_tiling_offset(nb)) : nullptr;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(stats);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (nsteps > 0 && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
-    cudaGraphExec_t exec = step_graph(a, p, ws, tab, off, totals, nb, dt, cnt);
+    cudaGraphExec_t exec = step_graph(a, p, ws, tab, off, totals, nb, dt, cnt, til);
     if (exec) {
       for (int step = 0; step < nsteps; step++)
         if (cudaGraphLaunch(exec, s) != cudaSuccess) return ASTERX_ECUDA;
@@ -629,7 +727,7 @@ asterx_status asterx_batched_step(const asterx_params* p, const asterx_batch_blo
   }
   for (int step = 0; step < nsteps; step++)
     for (int stage = 0; stage < 4; stage++) {
-      cudaError_t e = launch_batch_stage(a, tab + (size_t)stage * nb, off, totals, nb, stage, dt, cnt, s);
+      cudaError_t e = launch_batch_stage(a, tab + (size_t)stage * nb, off, totals, nb, stage, dt, cnt, s, til);
       if (e != cudaSuccess) return ASTERX_ECUDA;
     }
   return ASTERX_OK;

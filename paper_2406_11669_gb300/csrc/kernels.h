@@ -30,6 +30,11 @@ cudaError_t launch_ghost_prims(const Blk& b, const F5& P, cudaStream_t s);
 // B~ = curl A on faces, then the undensitised centre field of every cell
 cudaError_t launch_bfield(const Blk& b, const Ws& w, const F9& U, cudaStream_t s);
 
+// ghost layers of the state (record field Us) of every block of a table: exchange between the blocks of a
+// tiling (device, may be null), then the boundary-condition sweeps
+cudaError_t launch_batch_ghosts(const BlockRec* tab, const long* off, const long* host_total, int nb,
+                                const Tiling* tiling, cudaStream_t s);
+
 // u^i = W v^i at every cell into w.uvel (primitives with ghosts)
 cudaError_t launch_uvel(const Blk& b, const Ws& w, const F5& P, cudaStream_t s);
 
@@ -51,9 +56,11 @@ cudaError_t launch_rhs(const StageArgs& a, const F9& Us, const F5& P, int stage,
                        const F9& Unext, const F9& Uacc, const F9& dU, cudaStream_t s);
 
 // one RK4 stage of every block of a device table (one launch per kernel); tab holds nb records of this stage,
-// off the NKIND * (nb + 1) item offsets (device), host_total the NKIND totals (host)
+// off the NKIND * (nb + 1) item offsets (device), host_total the NKIND totals (host); with a (device) tiling the
+// ghost layers between blocks are filled from the neighbours before the boundary-condition sweeps
 cudaError_t launch_batch_stage(const StageArgs& a, const BlockRec* tab, const long* off, const long* host_total,
-                               int nb, int stage, double dt, unsigned long long* stats, cudaStream_t s);
+                               int nb, int stage, double dt, unsigned long long* stats, cudaStream_t s,
+                               const Tiling* tiling = nullptr);
 
 // ---- adjoint ----
 // accumulators cleared together at the start of each right-hand-side adjoint (contiguous, in this order)

@@ -45,6 +45,23 @@ struct Blk {
   long V;       // entries per field
   double dx[3];
   double idx[3];
+  // blocks of a tiled domain: bit 2 a + s set = the lower (s = 0) or upper (s = 1) ghost layers along axis a are
+  // filled from the neighbouring blocks (the boundary-condition sweeps skip them); the block's position in the
+  // block grid and the domain index of its first interior cell per axis.  Zero for a lone block.
+  int halo;
+  int coord[3];
+  int off[3];
+};
+
+// A domain tiled by a grid of blocks (same spacing; block (bx, by, bz) covers the interior cells
+// cuts_d[b_d] .. cuts_d[b_d + 1] - 1 along each axis d; the batch lists the blocks x fastest).  Stored in the
+// batch workspace; the cut offsets follow the struct (axis d's nblk[d] + 1 values from index cut_at[d]).
+struct Tiling {
+  int nblk[3];
+  int ntot[3];   // interior cells of the domain per axis
+  int bc[3];     // the domain's boundary condition per axis
+  int cut_at[3];
+  __host__ __device__ const int* cuts(int d) const { return reinterpret_cast<const int*>(this + 1) + cut_at[d]; }
 };
 
 struct Ws {

@@ -59,6 +59,8 @@ struct StageConsts {
   int lxf, fct;  // Lax-Friedrichs fluxes; flux constrained transport
   C2PParams cp;
   unsigned long long* stats;
+  const BlockRec* tab;  // tiled batch: this stage's block records (device), else null
+  const Tiling* til;    // tiled batch: the tiling (device), else null
 };
 
 // ----------------------------------------------------------------------------------------------------------
@@ -144,6 +146,7 @@ __device__ __forceinline__ void ghost_point(const Blk& b, long t, double* const*
     const int lo = g;
     const int hi = (cl || b.bc[AX] == 0) ? g + n - 1 : g + n;
     if (i >= lo && i <= hi) continue;
+    if ((b.halo >> (2 * AX + (i < lo ? 0 : 1))) & 1) continue;  // filled from the neighbouring block
     double* __restrict__ a = f[fi] + base;
     double v;
     if (b.bc[AX] == 0) {
@@ -182,6 +185,66 @@ struct GhostPrims {  // the 5 primitives (record field P)
     ghost_point<AX, 5>(r.b, t, r.P.f, cl, lin_);
   }
 };
+
+// ----------------------------------------------------------------------------------------------------------
+// Ghost exchange between the blocks of a tiled domain: a point outside the block's owned range whose domain
+// position lies inside the domain (after the periodic wrap) takes the value of the block that owns that
+// position, read at the owner's own index; points outside the domain along a copy-BC axis are left to the
+// boundary-condition sweeps that follow (which then read exchanged values where a neighbour exists, exactly
+// as the sweeps of one block covering the whole domain would).  Owned ranges as in the ghost fill.
+
+template <int NF, bool STATE>
+struct Exchange {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts& k, long t) {
+    const Blk& b = r.b;
+    const Tiling& T = *k.til;
+    Box box = make_box(0, b.N[0], 0, b.N[1], 0, b.N[2]);
+    int p[3];
+    box.at(t, p[0], p[1], p[2]);
+    const long c = lin(b, p[0], p[1], p[2]);
+    const int clm[9] = {7, 7, 7, 7, 7, 1, 2, 4, 0};  // bit a: cell-like along axis a
+#pragma unroll 1
+    for (int fi = 0; fi < NF; fi++) {
+      const int cl_bits = STATE ? clm[fi] : 7;
+      bool owned = true, outside = false;
+      int own[3], loc[3];
+      for (int a = 0; a < 3; a++) {
+        const bool cl = (cl_bits >> a) & 1;
+        const int hi = (cl || b.bc[a] == 0) ? b.g + b.n[a] - 1 : b.g + b.n[a];
+        if (p[a] >= b.g && p[a] <= hi) {
+          own[a] = b.coord[a];
+          loc[a] = p[a];
+          continue;
+        }
+        owned = false;
+        const int Nt = T.ntot[a];
+        int G = b.off[a] + p[a] - b.g;  // domain index along a
+        if (T.bc[a] == 0) {
+          G = ((G % Nt) + Nt) % Nt;
+        } else if (G < 0 || G > (cl ? Nt - 1 : Nt)) {
+          outside = true;
+          break;
+        }
+        const int* cuts = T.cuts(a);
+        int lo = 0, hi2 = T.nblk[a];  // largest lo with cuts[lo] <= G (the last block for G == Nt)
+        while (hi2 - lo > 1) {
+          const int mid = (lo + hi2) >> 1;
+          if (cuts[mid] <= G) lo = mid;
+          else hi2 = mid;
+        }
+        own[a] = lo;
+        loc[a] = G - cuts[lo] + b.g;
+      }
+      if (owned || outside) continue;
+      const BlockRec& o = k.tab[own[0] + T.nblk[0] * (own[1] + T.nblk[1] * own[2])];
+      const long oc = lin(o.b, loc[0], loc[1], loc[2]);
+      if (STATE) r.Us.f[fi][c] = o.Us.f[fi][oc];
+      else r.P.f[fi][c] = o.P.f[fi][oc];
+    }
+  }
+};
+using ExchangeState = Exchange<9, true>;
+using ExchangePrims = Exchange<5, false>;
 
 // ----------------------------------------------------------------------------------------------------------
 // B~^i = [ijk] d_j A_k on faces (Eq. BEulerian, second-order differences of the edge values), then the
@@ -943,6 +1006,8 @@ static StageConsts consts_of(const StageArgs& a, int stage, double dt, unsigned 
   k.cp.brent_maxiter = a.brent_maxiter;
   k.cp.use_fallback = a.use_fallback;
   k.stats = stats;
+  k.tab = nullptr;
+  k.til = nullptr;
   return k;
 }
 
@@ -1016,9 +1081,11 @@ static void seq_rhs(const T& t, const StageConsts& k, int recon, cudaStream_t s)
 
 template <class T>
 static void seq_stage(const T& t, const StageConsts& k, int recon, cudaStream_t s) {
+  if (k.til) launch<ExchangeState>(t, k, KIND_VERTS_ALL, s);
   seq_ghost_state(t, k, s);
   seq_bfield(t, k, s);
   launch_c2p_kind(t, k, s);
+  if (k.til) launch<ExchangePrims>(t, k, KIND_VERTS_ALL, s);
   seq_ghost_prims(t, k, s);
   seq_rhs(t, k, recon, s);
 }
@@ -1138,14 +1205,35 @@ cudaError_t launch_face_data(const StageArgs& a, const F5& P, double* const rec[
 // ----------------------------------------------------------------------------------------------------------
 // Batched stage: every block of the table in one launch per kernel.
 
-cudaError_t launch_batch_stage(const StageArgs& a, const BlockRec* tab, const long* off, const long* host_total,
-                               int nb, int stage, double dt, unsigned long long* stats, cudaStream_t s) {
+cudaError_t launch_batch_ghosts(const BlockRec* tab, const long* off, const long* host_total, int nb,
+                                const Tiling* tiling, cudaStream_t s) {
   Batch t;
   t.tab = tab;
   t.off = off;
   t.host_total = host_total;
   t.nb = nb;
-  seq_stage(t, consts_of(a, stage, dt, stats), a.recon, s);
+  StageConsts k = zero_consts();
+  k.tab = tab;
+  k.til = tiling;
+  if (tiling) launch<ExchangeState>(t, k, KIND_VERTS_ALL, s);
+  seq_ghost_state(t, k, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_stage(const StageArgs& a, const BlockRec* tab, const long* off, const long* host_total,
+                               int nb, int stage, double dt, unsigned long long* stats, cudaStream_t s,
+                               const Tiling* tiling) {
+  Batch t;
+  t.tab = tab;
+  t.off = off;
+  t.host_total = host_total;
+  t.nb = nb;
+  StageConsts k = consts_of(a, stage, dt, stats);
+  if (tiling) {
+    k.tab = tab;
+    k.til = tiling;
+  }
+  seq_stage(t, k, a.recon, s);
   return cudaGetLastError();
 }
 

@@ -181,3 +181,45 @@ def test_adjoint_rejects_the_alternative_schemes():
                                        ctypes.byref(pr), ctypes.byref(st), ctypes.c_void_p(256), need,
                                        ctypes.c_void_p(512), size, None)
         assert rc == A.ASTERX_EINVAL, change
+
+
+def test_tiled_batch_validation():
+    """asterx_batch_prepare_tiled rejects blocks that do not tile the domain as the cuts describe."""
+    L = A.lib()
+    p = _params()
+    cuts = ([0, 8, 20], [0, 12], [0, 6])
+    nblk = (2, 1, 1)
+
+    def arr_for(ns, x0s, dxs=None):
+        arr = (A.BatchBlock * len(ns))()
+        for i, (n, x0) in enumerate(zip(ns, x0s)):
+            arr[i].blk = A.block_struct(n, 3, x0, dxs[i] if dxs else (0.1,) * 3, (1, 1, 1))
+            arr[i].metric = A.Metric(*([8] * 16))
+            arr[i].U = A.State(*([8] * 9))
+            arr[i].P = A.Prims(*([8] * 5))
+        return arr
+
+    def tiling(nb=nblk, cc=cuts):
+        t = A.Tiling()
+        keep = [(ctypes.c_int * len(c))(*c) for c in cc]
+        for d in range(3):
+            t.nblk[d] = nb[d]
+            t.cuts[d] = ctypes.cast(keep[d], ctypes.POINTER(ctypes.c_int))
+        return t, keep
+
+    good = arr_for([(8, 12, 6), (12, 12, 6)], [(0.0, 0.0, 0.0), (0.8, 0.0, 0.0)])
+    size = L.asterx_batch_workspace_size(good, 2)
+    assert size > 0
+    cases = [
+        (arr_for([(8, 12, 6), (11, 12, 6)], [(0.0, 0.0, 0.0), (0.8, 0.0, 0.0)]), tiling()),  # n off the cuts
+        (arr_for([(8, 12, 6), (12, 12, 6)], [(0.0, 0.0, 0.0), (0.9, 0.0, 0.0)]), tiling()),  # origin off
+        (arr_for([(8, 12, 6), (12, 12, 6)], [(0.0, 0.0, 0.0), (0.8, 0.0, 0.0)],
+                 [(0.1,) * 3, (0.1, 0.1, 0.2)]), tiling()),                                  # spacing differs
+        (good, tiling(nb=(1, 1, 1), cc=([0, 20], [0, 12], [0, 6]))),                          # block count
+        (arr_for([(2, 12, 6), (18, 12, 6)], [(0.0, 0.0, 0.0), (0.2, 0.0, 0.0)]),
+         tiling(cc=([0, 2, 20], [0, 12], [0, 6]))),                                           # a block under 3 cells
+    ]
+    for arr, (t, keep) in cases:
+        sz = max(L.asterx_batch_workspace_size(arr, 2), size)
+        rc = L.asterx_batch_prepare_tiled(ctypes.byref(p), arr, 2, ctypes.byref(t), ctypes.c_void_p(256), sz, None)
+        assert rc == A.ASTERX_EINVAL
