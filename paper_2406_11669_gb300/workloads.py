@@ -601,6 +601,31 @@ def config5(n=(256, 256, 256), seed=105) -> Workload:
                     0.25 * min(dx), prims, A, _full(shape, 0.0), metric)
 
 
+def weak_field_wave(nx, recon=RECON_PPM, amp=1e-3, cfl=0.25) -> Workload:
+    """A smooth small-amplitude wave on the config-4 weak-field lapse alpha = 1 - 0.01 sin 2 pi x (gamma = I,
+    beta = K = 0), periodic on [0, 1] along x, one cell across y and z: rho = 1 + amp sin 2 pi x,
+    p = 1 + amp cos 2 pi x, v^x = amp sin 2 pi x, B = 0, Gamma = 4/3; dt = cfl dx (for self-convergence)."""
+    n = (int(nx), 1, 1)
+    g = 3
+    x0 = (0.0, 0.0, 0.0)
+    h = 1.0 / nx
+    dx = (h, h, h)
+    N = [m + 2 * g for m in n]
+    shape = (N[2] + 1, N[1] + 1, N[0] + 1)
+    Xc, _, _ = positions(n, g, x0, dx, CELL)
+    Xv, _, _ = positions(n, g, x0, dx, VERTEX)
+    s = np.broadcast_to(np.sin(2.0 * math.pi * Xc), shape)
+    c = np.broadcast_to(np.cos(2.0 * math.pi * Xc), shape)
+    prims = dict(rho=1.0 + amp * s, press=1.0 + amp * c, velx=amp * s, vely=_full(shape, 0.0),
+                 velz=_full(shape, 0.0))
+    metric = flat_metric(shape)
+    metric["alp"][...] = np.broadcast_to(1.0 - 0.01 * np.sin(2.0 * math.pi * Xv), shape)
+    zero = _full(shape, 0.0)
+    params = default_params(gamma=4.0 / 3.0, gamma_atm=4.0 / 3.0, rho_atm=1e-7, K_atm=1.0, recon=recon)
+    return Workload(f"weak_field_wave_{nx}", n, g, x0, dx, (BC_PERIODIC,) * 3, params, cfl * h, prims,
+                    dict(Ax=zero, Ay=zero.copy(), Az=zero.copy()), zero.copy(), metric)
+
+
 def alfven_wave(nx, recon=RECON_MINMOD, ny=1, nz=1, cfl=0.2):
     """Circularly polarised Alfven wave of Sec. 4.2: rho = 1, p = 0.5, A0 = 1, v_A = 0.5, B^x = 1,
     v^y = -v_A A0 cos kx, v^z = -v_A A0 sin kx, B^y = A0 B^x cos kx, B^z = A0 B^x sin kx, Gamma = 5/3, on
