@@ -58,11 +58,11 @@ def parse():
                     help="skip the Lax-Friedrichs / flux-CT / RK2 step measurements")
     ap.add_argument("--no-coupling", action="store_true",
                     help="skip the stress-energy tensor and time-dependent-metric step measurements")
-    ap.add_argument("--profile-region", choices=("none", "forward", "adjoint", "batched", "coupling"), default="none",
+    ap.add_argument("--profile-region", choices=("none", "forward", "adjoint", "batched", "coupling", "tiled"), default="none",
                     help="bracket one extra forward RK4 step (main workload), one adjoint step, one batched "
-                         "step and one step of the equal-volume block, or one geometry derivation and one "
-                         "stress-energy tensor call with cudaProfilerStart/Stop, for a profiler run with "
-                         "--profile-from-start off")
+                         "step and one step of the equal-volume block, one geometry derivation and one "
+                         "stress-energy tensor call, or one step of the 4x4x4-tiled domain with "
+                         "cudaProfilerStart/Stop, for a profiler run with --profile-from-start off")
     return ap.parse_args()
 
 
@@ -323,6 +323,11 @@ def run_tiled(args, dev, stream, single_ms):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / steps
+        if args.profile_region == "tiled" and k == 4:
+            torch.cuda.profiler.start()
+            batch.step(w.dt, nsteps=1)
+            torch.cuda.synchronize(dev)
+            torch.cuda.profiler.stop()
         finite = all(bool(torch.isfinite(e[6]).all()) for e in entries)
         batch.release()
         del batch, entries
