@@ -480,7 +480,8 @@ def run_coupling(args, s, U, P, M, w, dev, stream):
 
 def run_variants(args, s, U, P, w, dev, stream):
     """The paper's alternative schemes on the benchmark block: one RK4 step with the Lax-Friedrichs flux, with flux
-    constrained transport, with both, and one RK2 step of the default scheme (rates per RK stage)."""
+    constrained transport, with both, with the algebraic gauge, and one RK2 step of the default scheme (rates per
+    RK stage)."""
     import torch
 
     from paper_2406_11669_gb300 import asterx as A
@@ -489,9 +490,10 @@ def run_variants(args, s, U, P, w, dev, stream):
     out = {}
     steps = max(1, min(args.steps, 3))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for name, flux, efield, rk2 in (("lxf", 1, 0, False), ("fct", 0, 1, False), ("lxf_fct", 1, 1, False),
-                                    ("rk2", 0, 0, True)):
-        s.p = A.params_struct(dict(s.params, flux=flux, efield=efield))
+    for name, flux, efield, rk2, gauge in (("lxf", 1, 0, False, 0), ("fct", 0, 1, False, 0),
+                                           ("lxf_fct", 1, 1, False, 0), ("rk2", 0, 0, True, 0),
+                                           ("algebraic_gauge", 0, 0, False, 1)):
+        s.p = A.params_struct(dict(s.params, flux=flux, efield=efield, gauge=gauge))
         step = s.rk2_step if rk2 else s.rk4_step
         step(U, P, w.dt)
         torch.cuda.synchronize(dev)
