@@ -211,8 +211,8 @@ asterx_status asterx_rk4_step_metrics(const asterx_params *p, const asterx_block
  * of g), g..g+n along vertex-like axes with copy BCs.  Adjoint inputs are read there only; outputs are zero
  * everywhere else.  `aws` is a second, caller-owned
  * workspace of asterx_adjoint_workspace_size() bytes (256-byte aligned); `ws` is the prepared forward one.
- * The stage adjoints differentiate the default scheme (flux HLLE, efield UCT); other switches return
- * ASTERX_EINVAL. */
+ * Every flux (HLLE, Lax-Friedrichs) and electric-field (UCT, FCT) switch is differentiated; c_wave's max takes
+ * c_max's branch on ties. */
 size_t asterx_adjoint_workspace_size(const asterx_block *blk);
 
 /* lam = (dL/dU)^T mu for the right-hand side L of asterx_rhs at state U (U unchanged; P: guess in, the

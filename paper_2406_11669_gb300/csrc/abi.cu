@@ -868,16 +868,11 @@ static asterx_status adj_checks(const asterx_params* p, const asterx_block* blk,
   return ASTERX_OK;
 }
 
-// the stage adjoints differentiate the default scheme (HLLE fluxes, upwind constrained transport) only
-static asterx_status adj_scheme_checks(const asterx_params* p) {
-  return (p->flux == ASTERX_FLUX_HLLE && p->efield == ASTERX_EFIELD_UCT) ? ASTERX_OK : ASTERX_EINVAL;
-}
 
 asterx_status asterx_rhs_adjoint(const asterx_params* p, const asterx_block* blk, double dt, const asterx_state* U,
                                  asterx_prims* P, const asterx_state* mu, asterx_state* lam, void* ws,
                                  size_t ws_bytes, void* aws, size_t aws_bytes, asterx_stream stream) {
   asterx_status st = adj_checks(p, blk, dt, ws, ws_bytes, aws, aws_bytes);
-  if (st == ASTERX_OK) st = adj_scheme_checks(p);
   if (st != ASTERX_OK) return st;
   if (!set_ok<asterx_state, 9>(U) || !set_ok<asterx_prims, 5>(P) || !set_ok<asterx_state, 9>(mu) ||
       !set_ok<asterx_state, 9>(lam))
@@ -902,7 +897,6 @@ asterx_status asterx_rk_stage_adjoint(const asterx_params* p, const asterx_block
                                       const asterx_state* lam_acc, asterx_state* lam_s, void* ws, size_t ws_bytes,
                                       void* aws, size_t aws_bytes, asterx_stream stream) {
   asterx_status st = adj_checks(p, blk, dt, ws, ws_bytes, aws, aws_bytes);
-  if (st == ASTERX_OK) st = adj_scheme_checks(p);
   if (st != ASTERX_OK) return st;
   if (stage < 0 || stage > 3) return ASTERX_EINVAL;
   if (!set_ok<asterx_state, 9>(Us) || !set_ok<asterx_prims, 5>(P) || !set_ok<asterx_state, 9>(lam_next) ||
@@ -935,7 +929,6 @@ asterx_status asterx_rk4_step_adjoint(const asterx_params* p, const asterx_block
                                       const asterx_state* Un, asterx_prims* P, asterx_state* lam, void* ws,
                                       size_t ws_bytes, void* aws, size_t aws_bytes, asterx_stream stream) {
   asterx_status st = adj_checks(p, blk, dt, ws, ws_bytes, aws, aws_bytes);
-  if (st == ASTERX_OK) st = adj_scheme_checks(p);
   if (st != ASTERX_OK) return st;
   if (!set_ok<asterx_state, 9>(Un) || !set_ok<asterx_prims, 5>(P) || !set_ok<asterx_state, 9>(lam))
     return ASTERX_EINVAL;
@@ -1023,7 +1016,6 @@ asterx_status asterx_rk4_adjoint_steps(const asterx_params* p, const asterx_bloc
                                        const asterx_state* ckpt, asterx_prims* P, asterx_state* lam, void* ws,
                                        size_t ws_bytes, void* aws, size_t aws_bytes, asterx_stream stream) {
   asterx_status st = adj_checks(p, blk, dt, ws, ws_bytes, aws, aws_bytes);
-  if (st == ASTERX_OK) st = adj_scheme_checks(p);
   if (st != ASTERX_OK) return st;
   if (nsteps < 1 || !ckpt) return ASTERX_EINVAL;
   for (int k = 0; k < nsteps; k++)

@@ -159,7 +159,7 @@ __global__ void ka_grad_ga(Blk b, AdjWs a, F9 mu) {
 // UCT: E_E = -HLL_d1(v~^d1 B~^d2) + HLL_d2(v~^d2 B~^d1); lambda_E = -mu_A.  Each term reversed by hand: the HLL
 // formula, the PPM interface values (reverse-mode recon5), a_+- = max over the two faces (branch taken).
 template <int E>
-__global__ void ka_edges(Blk b, Ws w, AdjWs a, F9 mu) {
+__global__ void ka_edges(Blk b, Ws w, AdjWs a, F9 mu, int fct) {
   constexpr int D1 = (E + 1) % 3, D2 = (E + 2) % 3;
   int lo[3] = {b.g, b.g, b.g}, ex[3] = {b.n[0] + 1, b.n[1] + 1, b.n[2] + 1};
   ex[E] = b.n[E];
@@ -169,6 +169,15 @@ __global__ void ka_edges(Blk b, Ws w, AdjWs a, F9 mu) {
     decode(t, lo[0], ex[0], lo[1], ex[1], lo[2], p[0], p[1], p[2]);
     const long c = alin(b, p[0], p[1], p[2]);
     const double lE = -mu.f[5 + E][c];
+    if (fct) {  // E = (F_D2(B~^D1) at c and c - e_D1  -  F_D1(B~^D2) at c and c - e_D2) / 4
+      const double q = 0.25 * lE;
+      const long f2 = ((long)D2 * NFD + FD_EB2) * b.V, f1 = ((long)D1 * NFD + FD_EB1) * b.V;
+      atomicAdd(&a.lface[f2 + c], q);
+      atomicAdd(&a.lface[f2 + c - astr(b, D1)], q);
+      atomicAdd(&a.lface[f1 + c], -q);
+      atomicAdd(&a.lface[f1 + c - astr(b, D2)], -q);
+      continue;
+    }
 #pragma unroll
     for (int tt = 0; tt < 2; tt++) {
       const double sgn = tt == 0 ? -1.0 : 1.0;  // E = -term0 + term1
@@ -284,8 +293,11 @@ __global__ void ka_vertex_to_edges(Blk b, AdjWs a) {
 // Face solve along D (faces g..g+n along D, all transverse): adjoints of (F^, v~bar, c_max, c_min) -> adjoints
 // of the reconstructed left/right states and of the face field B~.  The primal side solves run first (their
 // speeds set the HLLE weights), then HLLE is reversed by hand and each side by its reverse-mode VJP.
-template <int D>
-__global__ void ka_faces(Blk b, Ws w, AdjWs a, double gamma, double gfac) {
+// ALT: with the alternative schemes (Lax-Friedrichs, flux constrained transport) a separate instantiation, so
+// that the default one keeps its register budget.
+template <int D, bool ALT>
+__global__ void ka_faces(Blk b, Ws w, AdjWs a, double gamma, double gfac, int lxf_, int fct_) {
+  const bool lxf = ALT && lxf_, fct = ALT && fct_;
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   int lo[3] = {0, 0, 0}, ex[3] = {b.N[0], b.N[1], b.N[2]};
   lo[D] = b.g;
@@ -334,26 +346,85 @@ __global__ void ka_faces(Blk b, Ws w, AdjWs a, double gamma, double gfac) {
     SideBar wb[2];
     for (int side = 0; side < 2; side++) {
       wb[side].lp = wb[side].lm = 0.0;
-      wb[side].vt[D] = 0.0;
+      for (int q = 0; q < 3; q++) wb[side].vt[q] = 0.0;
+    }
+    // Lax-Friedrichs: c_wave = max(c_max, c_min), its derivative to c_max on ties
+    const bool cw_max = cmax >= cmin;
+    const double cw = cw_max ? cmax : cmin;
+    double extraB[2][2] = {{0.0, 0.0}, {0.0, 0.0}};  // adjoints of the sides' transverse B (induction fluxes)
+    double gBnt = 0.0;                               // adjoint of the densitised face field (induction fluxes)
+    if (fct) {
+      // the induction fluxes along D of B~^T1, B~^T2 (v~^D B~^a - v~^a B~^D), reversed: the solver, then the
+      // products of the sides' v~ and densitised B~
+      const double Bnt = w.bf[D * b.V + c];
+      for (int q = 0; q < 2; q++) {
+        const int ax = q == 0 ? T1 : T2;
+        const double lFb = lf[(FD_EB1 + q) * b.V];
+        if (lFb == 0.0) continue;
+        const double BL = m.sqg * B[0][ax], BR = m.sqg * B[1][ax];
+        const double FL = s[0].vt[D] * BL - s[0].vt[ax] * Bnt, FR = s[1].vt[D] * BR - s[1].vt[ax] * Bnt;
+        double gFL, gFR, gBL, gBR;
+        if (den > 0.0 && lxf) {
+          gFL = gFR = 0.5;
+          gBL = 0.5 * cw;
+          gBR = -0.5 * cw;
+          if (cw_max) lcmax += -0.5 * (BR - BL) * lFb;
+          else lcmin += -0.5 * (BR - BL) * lFb;
+        } else if (den > 0.0) {
+          const double id = 1.0 / den;
+          const double Fh = (cmin * FR + cmax * FL - cmax * cmin * (BR - BL)) * id;
+          gFL = cmax * id;
+          gFR = cmin * id;
+          gBL = cmax * cmin * id;
+          gBR = -cmax * cmin * id;
+          lcmax += (FL - cmin * (BR - BL) - Fh) * id * lFb;
+          lcmin += (FR - cmax * (BR - BL) - Fh) * id * lFb;
+        } else {
+          gFL = gFR = 0.5;
+          gBL = gBR = 0.0;
+        }
+        const double wFL = gFL * lFb, wFR = gFR * lFb;
+        wb[0].vt[D] += wFL * BL;
+        wb[0].vt[ax] -= wFL * Bnt;
+        wb[1].vt[D] += wFR * BR;
+        wb[1].vt[ax] -= wFR * Bnt;
+        extraB[0][q] += m.sqg * (wFL * s[0].vt[D] + gBL * lFb);
+        extraB[1][q] += m.sqg * (wFR * s[1].vt[D] + gBR * lFb);
+        gBnt -= wFL * s[0].vt[ax] + wFR * s[1].vt[ax];
+      }
     }
     if (den > 0.0) {
       const double id = 1.0 / den;
-      for (int v = 0; v < 5; v++) {
-        const double dU = s[1].U[v] - s[0].U[v];
-        const double Fh = (cmin * s[1].F[v] + cmax * s[0].F[v] - cmax * cmin * dU) * id;
-        wb[0].F[v] = cmax * id * lF[v];
-        wb[1].F[v] = cmin * id * lF[v];
-        wb[0].U[v] = cmax * cmin * id * lF[v];
-        wb[1].U[v] = -cmax * cmin * id * lF[v];
-        lcmax += (s[0].F[v] - cmin * dU - Fh) * id * lF[v];
-        lcmin += (s[1].F[v] - cmax * dU - Fh) * id * lF[v];
+      if (lxf) {
+        double lcw = 0.0;
+        for (int v = 0; v < 5; v++) {
+          const double dU = s[1].U[v] - s[0].U[v];
+          wb[0].F[v] = 0.5 * lF[v];
+          wb[1].F[v] = 0.5 * lF[v];
+          wb[0].U[v] = 0.5 * cw * lF[v];
+          wb[1].U[v] = -0.5 * cw * lF[v];
+          lcw -= 0.5 * dU * lF[v];
+        }
+        if (cw_max) lcmax += lcw;
+        else lcmin += lcw;
+      } else {
+        for (int v = 0; v < 5; v++) {
+          const double dU = s[1].U[v] - s[0].U[v];
+          const double Fh = (cmin * s[1].F[v] + cmax * s[0].F[v] - cmax * cmin * dU) * id;
+          wb[0].F[v] = cmax * id * lF[v];
+          wb[1].F[v] = cmin * id * lF[v];
+          wb[0].U[v] = cmax * cmin * id * lF[v];
+          wb[1].U[v] = -cmax * cmin * id * lF[v];
+          lcmax += (s[0].F[v] - cmin * dU - Fh) * id * lF[v];
+          lcmin += (s[1].F[v] - cmax * dU - Fh) * id * lF[v];
+        }
       }
       const int tq[2] = {T1, T2};
       for (int q = 0; q < 2; q++) {
         const double vtL = s[0].vt[tq[q]], vtR = s[1].vt[tq[q]];
         const double vb = (cmax * vtL + cmin * vtR) * id;
-        wb[0].vt[tq[q]] = cmax * id * lvb[q];
-        wb[1].vt[tq[q]] = cmin * id * lvb[q];
+        wb[0].vt[tq[q]] += cmax * id * lvb[q];
+        wb[1].vt[tq[q]] += cmin * id * lvb[q];
         lcmax += (vtL - vb) * id * lvb[q];
         lcmin += (vtR - vb) * id * lvb[q];
       }
@@ -362,8 +433,10 @@ __global__ void ka_faces(Blk b, Ws w, AdjWs a, double gamma, double gfac) {
         wb[0].F[v] = wb[1].F[v] = 0.5 * lF[v];
         wb[0].U[v] = wb[1].U[v] = 0.0;
       }
-      wb[0].vt[T1] = wb[1].vt[T1] = 0.5 * lvb[0];
-      wb[0].vt[T2] = wb[1].vt[T2] = 0.5 * lvb[1];
+      for (int side = 0; side < 2; side++) {
+        wb[side].vt[T1] += 0.5 * lvb[0];
+        wb[side].vt[T2] += 0.5 * lvb[1];
+      }
     }
     // c_max = max(0, lp_L, lp_R), c_min = -min(0, lm_L, lm_R): the branch taken carries the derivative
     if (cmax > 0.0) {
@@ -384,11 +457,11 @@ __global__ void ka_faces(Blk b, Ws w, AdjWs a, double gamma, double gfac) {
       lr[0] = gr;
       lr[b.V] = gp;
       for (int q = 0; q < 3; q++) lr[(2 + q) * b.V] = gu[q];
-      lr[5 * b.V] = gB[T1];
-      lr[6 * b.V] = gB[T2];
+      lr[5 * b.V] = gB[T1] + extraB[side][0];
+      lr[6 * b.V] = gB[T2] + extraB[side][1];
       gBn += gB[D];
     }
-    a.lBf[D * b.V + c] += gBn * isqg;
+    a.lBf[D * b.V + c] += gBn * isqg + gBnt;
   }
 }
 
@@ -771,7 +844,10 @@ static void adjoint_dir(const StageArgs& sa, const AdjWs& a, cudaStream_t s) {
   w.rec = a.rec3[D];  // this direction's reconstruction, kept from the recompute
   const long fc = (long)b.N[0] * b.N[1] * b.N[2] / b.N[D] * (b.n[D] + 1);
   cudaMemsetAsync(a.lrec, 0, 2 * NREC * b.V * sizeof(double), s);
-  ka_faces<D><<<agrid(fc, T), T, 0, s>>>(b, w, a, sa.gamma, sa.gfac);
+  if (sa.flux == 1 || sa.efield == 1)
+    ka_faces<D, true><<<agrid(fc, T), T, 0, s>>>(b, w, a, sa.gamma, sa.gfac, sa.flux == 1, sa.efield == 1);
+  else
+    ka_faces<D, false><<<agrid(fc, T), T, 0, s>>>(b, w, a, sa.gamma, sa.gfac, 0, 0);
   const long rc = (long)b.N[0] * b.N[1] * b.N[2] / b.N[D] * (b.n[D] + 2);
   if (sa.recon == 0) ka_recon<D, 0><<<agrid(rc, T), T, 0, s>>>(b, w, a);
   else if (sa.recon == 1) ka_recon<D, 1><<<agrid(rc, T), T, 0, s>>>(b, w, a);
@@ -808,9 +884,9 @@ cudaError_t launch_adjoint_reverse(const StageArgs& sa0, const AdjWs& a, double 
   if (lorenz) ka_psi<<<agrid(vc, T), T, 0, s>>>(b, sa.w, a, a.mu, xi);
   ka_grad_ga<<<agrid(vc, T), T, 0, s>>>(b, a, a.mu);
   const long ec = (long)(b.n[0] + 1) * (b.n[1] + 1) * (b.n[2] + 1);
-  ka_edges<0><<<agrid(ec, T), T, 0, s>>>(b, sa.w, a, a.mu);
-  ka_edges<1><<<agrid(ec, T), T, 0, s>>>(b, sa.w, a, a.mu);
-  ka_edges<2><<<agrid(ec, T), T, 0, s>>>(b, sa.w, a, a.mu);
+  ka_edges<0><<<agrid(ec, T), T, 0, s>>>(b, sa.w, a, a.mu, sa.efield == 1);
+  ka_edges<1><<<agrid(ec, T), T, 0, s>>>(b, sa.w, a, a.mu, sa.efield == 1);
+  ka_edges<2><<<agrid(ec, T), T, 0, s>>>(b, sa.w, a, a.mu, sa.efield == 1);
   ka_vertex<<<agrid(vc, T), T, 0, s>>>(b, sa.w, a, lorenz);
   ka_vertex_to_edges<<<agrid((long)(b.n[0] + 4) * (b.n[1] + 4) * (b.n[2] + 4), T), T, 0, s>>>(b, a);
   adjoint_dir<0>(sa, a, s);

@@ -167,22 +167,6 @@ def test_tmunu_and_metric_step_validation():
     assert rc == A.ASTERX_EINVAL  # dt <= 0
 
 
-def test_adjoint_rejects_the_alternative_schemes():
-    """The stage adjoints differentiate HLLE with upwind constrained transport only."""
-    L = A.lib()
-    b = A.block_struct((8, 8, 8), 3, (0, 0, 0), (0.1,) * 3, (0, 0, 0))
-    st = A.State(*([8] * 9))
-    pr = A.Prims(*([8] * 5))
-    need = A.workspace_size(b)
-    size = L.asterx_adjoint_workspace_size(ctypes.byref(b))
-    for change in (dict(flux=W.FLUX_LXF), dict(efield=W.EFIELD_FCT)):
-        p = _params(**change)
-        rc = L.asterx_rk4_step_adjoint(ctypes.byref(p), ctypes.byref(b), ctypes.c_double(0.01), ctypes.byref(st),
-                                       ctypes.byref(pr), ctypes.byref(st), ctypes.c_void_p(256), need,
-                                       ctypes.c_void_p(512), size, None)
-        assert rc == A.ASTERX_EINVAL, change
-
-
 def test_tiled_batch_validation():
     """asterx_batch_prepare_tiled rejects blocks that do not tile the domain as the cuts describe."""
     L = A.lib()

@@ -216,6 +216,43 @@ def test_rk4_step_adjoint_equals_the_oracle_jvp(name):
     print(f"{name}: largest relative difference {worst:.2e}")
 
 
+SWITCHES = {"lxf": dict(flux=W.FLUX_LXF), "fct": dict(efield=W.EFIELD_FCT),
+            "lxf_fct": dict(flux=W.FLUX_LXF, efield=W.EFIELD_FCT)}
+
+
+@pytest.mark.parametrize("sw", list(SWITCHES))
+@pytest.mark.parametrize("name", ["ppm_periodic_lorenz", "minmod_copy_lorenz"])
+def test_rhs_adjoint_of_the_scheme_switches_equals_the_oracle_jvp(name, sw):
+    """The Lax-Friedrichs and flux-CT switches differentiated: the oracle's dual-number derivative follows the
+    switches through the same face solve and electric field code."""
+    need_gpu()
+    w = W.smooth_general(**CASES[name])
+    w.params = dict(w.params, **SWITCHES[sw])
+    prob = Problem(w, seed=2208)
+    mu = prob.mu_for(prob.stage_rhs(prob.U))
+    case = GpuCase(w)
+    lam_d = case.solver.zeros_state()
+    case.solver.rhs_adjoint(case.dev(prob.U), case.dev(prob.P), case.dev(mu), lam_d, w.dt)
+    lam = case.host(lam_d)
+    worst = check_against_jvp(prob, mu, lam, lambda d: O.stage_jvp(w, prob.M, prob.U, d, prob.P.copy())[1])
+    print(f"{name} {sw}: largest relative difference {worst:.2e}")
+
+
+def test_rk4_step_adjoint_of_the_scheme_switches_equals_the_oracle_jvp():
+    need_gpu()
+    w = W.smooth_general(n=(10, 9, 8), **CASES["wenoz_periodic_algebraic"])
+    w.params = dict(w.params, flux=W.FLUX_LXF, efield=W.EFIELD_FCT)
+    prob = Problem(w, seed=2209)
+    mu = prob.mu_for(prob.rk4(prob.U))
+    case = GpuCase(w)
+    lam_d = case.dev(mu)
+    case.solver.rk4_step_adjoint(case.dev(prob.U), case.dev(prob.P), lam_d, w.dt)
+    lam = case.host(lam_d)
+    worst = check_against_jvp(prob, mu, lam, lambda d: O.rk4_jvp(w, prob.M, prob.U, d, prob.P.copy())[1],
+                              entries_full=False)
+    print(f"lxf_fct rk4: largest relative difference {worst:.2e}")
+
+
 def test_rhs_adjoint_is_linear_in_the_weights():
     """J^T (2 mu1 - 3 mu2) = 2 J^T mu1 - 3 J^T mu2 up to the summation order of the atomic accumulations."""
     need_gpu()
