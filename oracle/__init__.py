@@ -87,6 +87,13 @@ def lib():
         L.oracle_recon_flops.argtypes = [ctypes.c_int, _P, _P]
         L.oracle_point_sources.argtypes = [ctypes.POINTER(OParams), _P, _P, _P, _P, _P, _P, _P]
         L.oracle_grid_sources.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP]
+        L.oracle_rk_stage_given_ghosts.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, ctypes.c_int,
+                                                   ctypes.c_double, _PP, _PP, _PP, _PP, _PP, ctypes.c_void_p,
+                                                   ctypes.POINTER(OStats)]
+        IP = ctypes.POINTER(ctypes.c_int)
+        L.oracle_prolong.argtypes = [ctypes.POINTER(OBlock), ctypes.POINTER(OBlock), IP, _PP, _PP, _PP, _PP,
+                                     ctypes.c_int]
+        L.oracle_restrict.argtypes = [ctypes.POINTER(OBlock), ctypes.POINTER(OBlock), IP, _PP, _PP]
         L.oracle_point_face.argtypes = [ctypes.POINTER(OParams), _P, _P, _P, ctypes.c_double, ctypes.c_int, _P]
         L.oracle_centre_metric.argtypes = [ctypes.POINTER(OBlock), _PP, _PP]
         L.oracle_face_metric.argtypes = [ctypes.POINTER(OBlock), _PP, ctypes.c_int, _PP]
@@ -263,6 +270,50 @@ def rk4_jvp(w, M, U, dU, P, dt=None, params=None):
                          _ptrs(M), _ptrs(np.ascontiguousarray(U)), _ptrs(np.ascontiguousarray(dU)), _ptrs(P),
                          _ptrs(U1), _ptrs(JU1), float(dt if dt is not None else w.dt))
     return U1, JU1
+
+
+def _ivec(L):
+    return (ctypes.c_int * 3)(*[int(x) for x in L])
+
+
+def prolong(wc, wf, L, Uc, Pc, Uf, Pf, all_points=False):
+    """Fills the fine block's ghost points (every point with all_points) of Uf (9) and Pf (5) from the coarse
+    level; the fine interior covers the coarse interior cells L .. L + n_fine / 2 - 1."""
+    lib().oracle_prolong(ctypes.byref(block_struct(wc)), ctypes.byref(block_struct(wf)), _ivec(L), _ptrs(Uc),
+                         _ptrs(Pc), _ptrs(Uf), _ptrs(Pf), int(bool(all_points)))
+
+
+def restrict(wc, wf, L, Uc, Uf):
+    """The coarse points under the fine interior from the fine state (9 fields)."""
+    lib().oracle_restrict(ctypes.byref(block_struct(wc)), ctypes.byref(block_struct(wf)), _ivec(L), _ptrs(Uc),
+                          _ptrs(Uf))
+
+
+def rk_stage_given_ghosts(w, M, stage, dt, Un, Us, Unext, Uacc, P, params=None):
+    pp = params_struct(params or w.params)
+    flags = np.zeros(w.shape, dtype=np.int8)
+    st = OStats()
+    lib().oracle_rk_stage_given_ghosts(ctypes.byref(pp), ctypes.byref(block_struct(w)), _ptrs(M), int(stage),
+                                       float(dt), _ptrs(Un), _ptrs(Us), _ptrs(Unext), _ptrs(Uacc), _ptrs(P),
+                                       flags.ctypes.data, ctypes.byref(st))
+    return flags, st.asdict()
+
+
+def refined_rk4_step(wc, Mc, Uc, Pc, wf, Mf, Uf, Pf, L, dt, params=None):
+    """One RK4 step of two refinement levels with one time step (no subcycling): each stage runs the coarse
+    stage, prolongs the coarse stage state and primitives to the fine ghost points, and runs the fine stage on
+    them; then the coarse points under the fine interior are restricted.  Returns (Uc_next, Uf_next)."""
+    Ua_c, Ua_f = np.zeros_like(Uc), np.zeros_like(Uf)
+    Us_c, Us_f = Uc, Uf
+    for s in range(4):
+        Un_c = Us_c.copy()
+        rk_stage(wc, Mc, s, dt, Uc, Us_c, Un_c, Ua_c, Pc, params)
+        prolong(wc, wf, L, Us_c, Pc, Us_f, Pf)
+        Un_f = Us_f.copy()
+        rk_stage_given_ghosts(wf, Mf, s, dt, Uf, Us_f, Un_f, Ua_f, Pf, params)
+        Us_c, Us_f = Un_c, Un_f
+    restrict(wc, wf, L, Us_c, Us_f)
+    return Us_c, Us_f
 
 
 def rk2_step(w, M, U, P, dt=None, params=None):

@@ -1393,10 +1393,10 @@ static void owned_range(const Grid& G, int v, int lo[3], int hi[3]) {
 
 static void rk_stage(const Grid& G, const VertexMetric& vm, const OParams& P, int stage, double dt,
                      double* const Un[9], double* const Us[9], double* const Unext[9], double* const Uacc[9],
-                     double* const prim[5], signed char* flags, OStats* stats) {
-  ghost_fill_state(G, Us);
+                     double* const prim[5], signed char* flags, OStats* stats, bool fill_ghosts = true) {
+  if (fill_ghosts) ghost_fill_state(G, Us);
   con2prim(G, vm, P, Us, prim, flags, stats);
-  ghost_fill_prims(G, prim);
+  if (fill_ghosts) ghost_fill_prims(G, prim);
   std::vector<Field> k(9, Field(G.size(), 0.0));
   double* kp[9];
   for (int v = 0; v < 9; v++) kp[v] = k[v].data();
@@ -1517,6 +1517,109 @@ static void tmunu_vertices(const Grid& G, const VertexMetric& vm, const OParams&
           Tout[q][v] = t;
         }
       }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Two refinement levels (the BoxInBox fixed refinement of Sec. 3; prolongation at the inner refinement boundary
+// as the magnetic-rotor AMR test describes it): a fine block of half the spacing whose interior covers the
+// coarse cells L .. L+m-1 along each axis (m = n_fine / 2).  The fine ghost layers are prolonged from the coarse
+// level; after a step the coarse points under the fine interior are restricted from it.
+//
+// Prolongation, axis by axis in the order x, y, z: where the variable is cell-centred along the axis, third-order
+// conservative: the parabola through three coarse cell averages averaged over the fine half,
+// u_I -/+ (u_{I+1} - u_{I-1}) / 8, with the linear fallback u_I -/+ minmod(u_I - u_{I-1}, u_{I+1} - u_I) / 4
+// for both halves where either parabola value would leave the range of the three averages (a discontinuity or
+// an extremum; deciding per coarse cell keeps the halves' mean at u_I); where it is
+// vertex-centred, a fine point on a coarse point copies it and a midpoint takes the cubic through four coarse
+// points, (-u_{J-1} + 9 u_J + 9 u_{J+1} - u_{J+2}) / 16.  Restriction: the mean of the fine points covering a
+// coarse point (two halves along a cell-centred axis, the coincident point along a vertex-centred one).
+
+static int floor_div2(int f) { return (f >= 0) ? f / 2 : -((-f + 1) / 2); }
+
+template <class Get> static double prolong_1d(bool cell, int f, const Get& get) {
+  if (cell) {
+    const int I = floor_div2(f);
+    const bool right = (f - 2 * I) == 1;
+    const double um = get(I - 1), u0 = get(I), up = get(I + 1);
+    const double d = (up - um) / 8.0;
+    const double lo = std::min(um, std::min(u0, up)), hi = std::max(um, std::max(u0, up));
+    // the decision is the coarse cell's, for both halves, so that their mean stays u0
+    if (u0 - d < lo || u0 - d > hi || u0 + d < lo || u0 + d > hi) {
+      const double a = u0 - um, b = up - u0;
+      const double s = (a * b <= 0.0) ? 0.0 : (std::fabs(a) <= std::fabs(b) ? a : b);
+      return right ? u0 + 0.25 * s : u0 - 0.25 * s;
+    }
+    return right ? u0 + d : u0 - d;
+  }
+  if ((f & 1) == 0) return get(f / 2);
+  const int J = floor_div2(f - 1);
+  return (-get(J - 1) + 9.0 * get(J) + 9.0 * get(J + 1) - get(J + 2)) / 16.0;
+}
+
+// value at the fine point of interior-relative index fr (fine units) of a field with staggering cl from the
+// coarse array uc (coarse interior-relative index of the box corner L)
+static double prolong_point(const Grid& C, const double* uc, const int L[3], const int cl[3], const int fr[3]) {
+  auto coarse = [&](int qx, int qy, int qz) { return uc[C.at(C.g + L[0] + qx, C.g + L[1] + qy, C.g + L[2] + qz)]; };
+  auto along_z = [&](int qz) {
+    auto along_y = [&](int qy) {
+      auto along_x = [&](int qx) { return coarse(qx, qy, qz); };
+      return prolong_1d(cl[0], fr[0], along_x);
+    };
+    return prolong_1d(cl[1], fr[1], along_y);
+  };
+  return prolong_1d(cl[2], fr[2], along_z);
+}
+
+static const int PRIM_CELL_LIKE[3] = {1, 1, 1};
+
+// fills the fine block's ghost points (outside the owned ranges, copy-BC convention) of the 9 state fields and
+// the 5 primitives; with all != 0 every point of the fine padded array
+static void prolong_grid(const Grid& C, const Grid& F, const int L[3], double* const Uc[9], double* const Pc[5],
+                         double* const Uf[9], double* const Pf[5], bool all) {
+  for (int k = 0; k <= F.N[2]; k++)
+    for (int j = 0; j <= F.N[1]; j++)
+      for (int i = 0; i <= F.N[0]; i++) {
+        const int p[3] = {i, j, k};
+        const int fr[3] = {i - F.g, j - F.g, k - F.g};
+        const long c = F.at(p);
+        for (int v = 0; v < 14; v++) {
+          const int* cl = v < 9 ? STATE_CELL_LIKE[v] : PRIM_CELL_LIKE;
+          bool owned = true, inside = true;
+          for (int a = 0; a < 3; a++) {
+            const int hi = cl[a] ? F.g + F.n[a] - 1 : F.g + F.n[a];
+            owned = owned && p[a] >= F.g && p[a] <= hi;
+            inside = inside && p[a] < F.N[a] + (cl[a] ? 0 : 1);  // cell-like axes end at N-1
+          }
+          if ((owned && !all) || !inside) continue;
+          const double* src = v < 9 ? Uc[v] : Pc[v - 9];
+          double* dst = v < 9 ? Uf[v] : Pf[v - 9];
+          dst[c] = prolong_point(C, src, L, cl, fr);
+        }
+      }
+}
+
+// coarse points covered by the fine interior, from the fine state (9 fields)
+static void restrict_grid(const Grid& C, const Grid& F, const int L[3], double* const Uc[9], double* const Uf[9]) {
+  const int m[3] = {F.n[0] / 2, F.n[1] / 2, F.n[2] / 2};
+  for (int v = 0; v < 9; v++) {
+    const int* cl = STATE_CELL_LIKE[v];
+    int hi[3];
+    for (int a = 0; a < 3; a++) hi[a] = cl[a] ? m[a] - 1 : m[a];
+    for (int qz = 0; qz <= hi[2]; qz++)
+      for (int qy = 0; qy <= hi[1]; qy++)
+        for (int qx = 0; qx <= hi[0]; qx++) {
+          const int q[3] = {qx, qy, qz};
+          double sum = 0.0;
+          int cnt = 0;
+          for (int dz = 0; dz <= cl[2]; dz++)
+            for (int dy = 0; dy <= cl[1]; dy++)
+              for (int dx = 0; dx <= cl[0]; dx++) {
+                sum += Uf[v][F.at(F.g + 2 * q[0] + dx, F.g + 2 * q[1] + dy, F.g + 2 * q[2] + dz)];
+                cnt++;
+              }
+          Uc[v][C.at(C.g + L[0] + q[0], C.g + L[1] + q[1], C.g + L[2] + q[2])] = sum / cnt;
+        }
+  }
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -1691,6 +1794,30 @@ void oracle_rk_stage(const OParams* p, const OBlock* b, const double* const* met
                      double* const* prim, signed char* flags, OStats* stats) {
   Grid G(*b);
   rk_stage(G, vmetric(metric), *p, stage, dt, Un, Us, Unext, Uacc, prim, flags, stats);
+}
+
+// As oracle_rk_stage, with the ghost layers of U_s and of the primitives taken as given (a refined block whose
+// ghosts were prolonged from the coarse level).
+void oracle_rk_stage_given_ghosts(const OParams* p, const OBlock* b, const double* const* metric, int stage,
+                                  double dt, double* const* Un, double* const* Us, double* const* Unext,
+                                  double* const* Uacc, double* const* prim, signed char* flags, OStats* stats) {
+  Grid G(*b);
+  rk_stage(G, vmetric(metric), *p, stage, dt, Un, Us, Unext, Uacc, prim, flags, stats, false);
+}
+
+// Prolongation from a coarse block to the ghost points (all != 0: every point) of a nested fine block whose
+// interior starts at coarse interior cell L (state 9 fields, primitives 5 fields on each level).
+void oracle_prolong(const OBlock* coarse, const OBlock* fine, const int* L, double* const* Uc, double* const* Pc,
+                    double* const* Uf, double* const* Pf, int all) {
+  Grid C(*coarse), F(*fine);
+  prolong_grid(C, F, L, Uc, Pc, Uf, Pf, all != 0);
+}
+
+// Restriction of the fine interior's state to the coarse points it covers.
+void oracle_restrict(const OBlock* coarse, const OBlock* fine, const int* L, double* const* Uc,
+                     double* const* Uf) {
+  Grid C(*coarse), F(*fine);
+  restrict_grid(C, F, L, Uc, Uf);
 }
 
 // The interpolated metric (Sec. 3.2) at every cell centre of the padded block, for checks of precomputed
