@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--batch-blocks", type=int, default=512)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward measurement")
     ap.add_argument("--adjoint-n", type=int, default=64, help="cells per axis of the adjoint workload")
+    ap.add_argument("--no-refined", action="store_true",
+                    help="skip the two-level (refined box) measurement")
     ap.add_argument("--no-tiled", action="store_true",
                     help="skip the tiled-domain (ghost exchange between blocks) measurement")
     ap.add_argument("--no-variants", action="store_true",
@@ -337,6 +339,56 @@ def run_tiled(args, dev, stream, single_ms):
     del M, U, P
     torch.cuda.empty_cache()
     return out
+
+
+def run_refined(args, dev, stream, single_ms):
+    """Two refinement levels on the benchmark workload: the 128^3 block plus a fine block of half the spacing over
+    its central 64^3 coarse cells (128^3 fine cells; fine data prolonged from the coarse level, the Schwarzschild
+    metric evaluated at the fine vertices), stepped together with the fine time step (prolongation of each coarse
+    stage state to the fine ghosts, restriction after the step).  Compared with two plain steps of 128^3 blocks."""
+    import numpy as np
+    import torch
+
+    from paper_2406_11669_gb300 import asterx as A
+    from paper_2406_11669_gb300 import workloads as W
+
+    w = W.config2(n=(args.n,) * 3)
+    M, U, P = _upload_block(w, dev)
+    sc = A.Solver.for_workload(w, device=dev)
+    sc.prepare(M)
+    sc.fill_ghosts(U)
+    sc.prim2con(U, P)
+    Lc, m = args.n // 4, args.n // 2
+    nf = (2 * m,) * 3
+    x0f = tuple(w.x0[d] + Lc * w.dx[d] for d in range(3))
+    dxf = tuple(h / 2 for h in w.dx)
+    Nf = [v + 2 * w.g for v in nf]
+    shape_f = (Nf[2] + 1, Nf[1] + 1, Nf[0] + 1)
+    Xv, Yv, Zv = W.positions(nf, w.g, x0f, dxf, W.VERTEX)
+    metf = W.schwarzschild_isotropic(Xv, Yv, Zv, 0.1, (-1.0, 0.0, 0.0), shape_f)
+    Mf = torch.from_numpy(np.ascontiguousarray(np.stack([metf[k] for k in W.METRIC_NAMES]))).to(dev)
+    sf = A.Solver(w.params, nf, w.g, x0f, dxf, w.bc, device=dev)
+    sf.prepare(Mf)
+    Uf, Pf = sf.zeros_state(), sf.zeros_prims()
+    A.prolong(sc, sf, U, P, Uf, Pf, all_points=True)
+    dt = 0.5 * w.dt
+    A.rk4_step_refined(sc, sf, U, P, Uf, Pf, dt)
+    torch.cuda.synchronize(dev)
+    steps = max(1, min(args.steps, 3))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        A.rk4_step_refined(sc, sf, U, P, Uf, Pf, dt)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    finite = bool(torch.isfinite(U).all()) and bool(torch.isfinite(Uf).all())
+    cells = w.interior_cells + int(np.prod(nf))
+    del sc, sf, M, U, P, Mf, Uf, Pf
+    torch.cuda.empty_cache()
+    return {"coarse_n": args.n, "fine_box_coarse_cells": m, "fine_n": nf[0], "ms_per_step": ms,
+            "value": cells * 4 / (ms / 1e3), "unit": UNIT, "vs_two_single_steps": 2.0 * single_ms / ms,
+            "finite": finite}
 
 
 def run_adjoint(args, dev, stream):
@@ -658,6 +710,8 @@ def run_ours(args):
         result["batched"] = run_batched(args, dev, stream)
     if not args.no_tiled:
         result["tiled"] = run_tiled(args, dev, stream, ms_max / args.steps)
+    if not args.no_refined:
+        result["refined"] = run_refined(args, dev, stream, ms_max / args.steps)
     if not args.no_adjoint:
         result["adjoint"] = run_adjoint(args, dev, stream)
     if not args.no_cpu_baseline:

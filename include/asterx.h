@@ -175,6 +175,31 @@ asterx_status asterx_rk2_step(const asterx_params *p, const asterx_block *blk, d
                               asterx_prims *P, signed char *flags, asterx_c2p_stats *stats, void *ws,
                               size_t ws_bytes, asterx_stream stream);
 
+/* ---- two refinement levels (fixed box-in-box refinement, one time step for both levels) ----
+ *
+ * A fine block of half the coarse spacing (dx_fine = dx_coarse / 2 exactly, n_fine even along every axis) whose
+ * interior covers the coarse interior cells L .. L + n_fine/2 - 1, with L = (x0_fine - x0_coarse) / dx_coarse
+ * integer, L >= 0 and L + n_fine/2 <= n_coarse.  Prolongation (the paper's AMR test, Sec. 4): third-order
+ * conservative along cell-centred directions with a minmod-limited linear fallback for both halves of a coarse
+ * cell where either would leave its three coarse averages' range; cubic interpolation along vertex-centred
+ * directions.  Restriction: the mean of the fine points covering a coarse point.
+ *
+ * asterx_prolong fills the fine block's ghost points (all != 0: every point, e.g. for initial data) of the 9
+ * state fields and 5 primitives from the coarse arrays (their ghosts filled where the stencil reaches them). */
+asterx_status asterx_prolong(const asterx_block *coarse, const asterx_block *fine, const asterx_state *Uc,
+                             const asterx_prims *Pc, asterx_state *Uf, asterx_prims *Pf, int all,
+                             asterx_stream stream);
+
+/* One RK4 step of both levels with the fine time step dt: per stage, the coarse stage (asterx_rk_stage), the
+ * prolongation of the coarse stage state and recovered primitives to the fine ghost points, and the fine stage
+ * on them (no ghost fill of its own); after the step the coarse points under the fine interior are restricted.
+ * ws_c / ws_f: the two blocks' prepared workspaces.  flags are not written; stats (may be NULL) accumulates both
+ * levels. */
+asterx_status asterx_rk4_step_refined(const asterx_params *p, const asterx_block *coarse, const asterx_block *fine,
+                                      double dt, asterx_state *Uc, asterx_prims *Pc, asterx_state *Uf,
+                                      asterx_prims *Pf, asterx_c2p_stats *stats, void *ws_c, size_t ws_c_bytes,
+                                      void *ws_f, size_t ws_f_bytes, asterx_stream stream);
+
 /* ---- coupling to a spacetime solver ----
  *
  * Stress-energy tensor T_{mu nu} (Eq. tmunu with both indices lowered by the 4-metric; T lives at vertices,

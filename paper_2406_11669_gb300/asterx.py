@@ -97,6 +97,8 @@ def lib():
                                            ctypes.POINTER(ctypes.c_void_p), S, Pr, vp, vp, sz, st]
         L.asterx_tmunu.argtypes = [P, B, M, S, Pr, ctypes.POINTER(TmunuFields), vp, sz, st]
         L.asterx_rk4_step_metrics.argtypes = [P, B, ctypes.c_double, ctypes.POINTER(M), S, Pr, vp, vp, vp, sz, st]
+        L.asterx_prolong.argtypes = [B, B, S, Pr, S, Pr, ctypes.c_int, st]
+        L.asterx_rk4_step_refined.argtypes = [P, B, B, ctypes.c_double, S, Pr, S, Pr, vp, vp, sz, vp, sz, st]
         BB = ctypes.POINTER(BatchBlock)
         L.asterx_batch_workspace_size.restype = ctypes.c_size_t
         L.asterx_batch_workspace_size.argtypes = [BB, ctypes.c_int]
@@ -128,7 +130,8 @@ def lib():
         L.asterx_dfma_probe.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_long, st]
         for name in ("asterx_prepare", "asterx_prim2con", "asterx_con2prim", "asterx_fill_ghosts", "asterx_rhs",
                      "asterx_rk_stage", "asterx_rk4_step", "asterx_rk2_step", "asterx_rk4_step_host", "asterx_tmunu",
-                     "asterx_rk4_step_metrics", "asterx_profile_enable",
+                     "asterx_rk4_step_metrics", "asterx_prolong", "asterx_rk4_step_refined",
+                     "asterx_profile_enable",
                      "asterx_profile_read", "asterx_dfma_probe"):
             getattr(L, name).restype = ctypes.c_int
         if L.asterx_abi_version() != ABI_VERSION:
@@ -414,6 +417,24 @@ def con2prim_noalloc(params: dict, n, g, x0, dx, bc, metric, U, P, flags=None, s
     sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
     return lib().asterx_con2prim_noalloc(ctypes.byref(p), ctypes.byref(b), ctypes.byref(m), ctypes.byref(u),
                                          ctypes.byref(pr), fl, sp, _stream(stream))
+
+
+def prolong(coarse, fine, Uc, Pc, Uf, Pf, all_points=False, stream=None):
+    """Fine ghost points (every point with all_points) of Uf, Pf from the coarse level (two Solvers)."""
+    _check(lib().asterx_prolong(ctypes.byref(coarse.b), ctypes.byref(fine.b), ctypes.byref(state_struct(Uc)),
+                                ctypes.byref(prims_struct(Pc)), ctypes.byref(state_struct(Uf)),
+                                ctypes.byref(prims_struct(Pf)), int(bool(all_points)), _stream(stream)),
+           "asterx_prolong")
+
+
+def rk4_step_refined(coarse, fine, Uc, Pc, Uf, Pf, dt, stats=None, stream=None):
+    """One RK4 step of two refinement levels (coarse and fine Solvers, both prepared) with time step dt."""
+    sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
+    _check(lib().asterx_rk4_step_refined(ctypes.byref(coarse.p), ctypes.byref(coarse.b), ctypes.byref(fine.b),
+                                         float(dt), ctypes.byref(state_struct(Uc)), ctypes.byref(prims_struct(Pc)),
+                                         ctypes.byref(state_struct(Uf)), ctypes.byref(prims_struct(Pf)), sp,
+                                         coarse.ws_ptr, coarse.ws_bytes, fine.ws_ptr, fine.ws_bytes,
+                                         _stream(stream)), "asterx_rk4_step_refined")
 
 
 class Batch:

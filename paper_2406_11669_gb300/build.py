@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libasterx.so")
-SOURCES = ["geometry.cu", "stage.cu", "abi.cu", "probe.cu", "noalloc.cu", "adjoint.cu", "tmunu.cu"]
+SOURCES = ["geometry.cu", "stage.cu", "abi.cu", "probe.cu", "noalloc.cu", "adjoint.cu", "tmunu.cu", "refine.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include")]

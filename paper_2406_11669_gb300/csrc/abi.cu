@@ -387,6 +387,80 @@ asterx_status asterx_rk4_step(const asterx_params* p, const asterx_block* blk, d
   return ASTERX_OK;
 }
 
+// the fine block nested in the coarse one as asterx_prolong requires; L = the coarse cell of the fine corner
+static bool nesting_ok(const asterx_block* c, const asterx_block* f, int L[3]) {
+  if (!block_ok(c) || !block_ok(f)) return false;
+  for (int d = 0; d < 3; d++) {
+    if (f->dx[d] * 2.0 != c->dx[d] || (f->n[d] % 2) != 0) return false;
+    const double q = (f->x0[d] - c->x0[d]) / c->dx[d];
+    L[d] = (int)std::lround(q);
+    if (std::fabs(q - L[d]) > 1e-9 || L[d] < 0 || L[d] + f->n[d] / 2 > c->n[d]) return false;
+  }
+  return true;
+}
+
+asterx_status asterx_prolong(const asterx_block* coarse, const asterx_block* fine, const asterx_state* Uc,
+                             const asterx_prims* Pc, asterx_state* Uf, asterx_prims* Pf, int all,
+                             asterx_stream stream) {
+  int L[3];
+  if (!nesting_ok(coarse, fine, L)) return ASTERX_EINVAL;
+  if (!set_ok<asterx_state, 9>(Uc) || !set_ok<asterx_prims, 5>(Pc) || !set_ok<asterx_state, 9>(Uf) ||
+      !set_ok<asterx_prims, 5>(Pf))
+    return ASTERX_EINVAL;
+  return cuda_status(launch_prolong(make_blk(coarse), make_blk(fine), L, f9(Uc), f5(Pc), f9(Uf), f5(Pf), all != 0,
+                                    reinterpret_cast<cudaStream_t>(stream)));
+}
+
+// a stage whose ghost layers (state and primitives) are given: the fine level's, prolonged from the coarse one
+static asterx_status stage_given_ghosts(const StageArgs& a, int stage, double dt, const F9& un, const F9& us,
+                                        const F9& unext, const F9& uacc, const F5& pr, unsigned long long* stats,
+                                        cudaStream_t s) {
+  cudaError_t e = launch_bfield(a.b, a.w, us, s);
+  if (e == cudaSuccess) e = launch_c2p(a, us, pr, nullptr, stats, s);
+  if (e == cudaSuccess) e = launch_rhs(a, us, pr, stage, dt, un, unext, uacc, unext, s);
+  return cuda_status(e);
+}
+
+asterx_status asterx_rk4_step_refined(const asterx_params* p, const asterx_block* coarse, const asterx_block* fine,
+                                      double dt, asterx_state* Uc, asterx_prims* Pc, asterx_state* Uf,
+                                      asterx_prims* Pf, asterx_c2p_stats* stats, void* ws_c, size_t ws_c_bytes,
+                                      void* ws_f, size_t ws_f_bytes, asterx_stream stream) {
+  asterx_status st = common_checks(p, coarse, ws_c, ws_c_bytes);
+  if (st == ASTERX_OK) st = common_checks(p, fine, ws_f, ws_f_bytes);
+  if (st != ASTERX_OK) return st;
+  int L[3];
+  if (!nesting_ok(coarse, fine, L) || !finite_pos(dt)) return ASTERX_EINVAL;
+  if (!set_ok<asterx_state, 9>(Uc) || !set_ok<asterx_prims, 5>(Pc) || !set_ok<asterx_state, 9>(Uf) ||
+      !set_ok<asterx_prims, 5>(Pf))
+    return ASTERX_EINVAL;
+  if (stats && ((uintptr_t)stats % 8) != 0) return ASTERX_EINVAL;
+  StageArgs ac = make_args(p, coarse, ws_c), af = make_args(p, fine, ws_f);
+  F9 unc = f9(Uc), unf = f9(Uf), accc, accf, sbc[2], sbf[2];
+  for (int v = 0; v < 9; v++) {
+    accc.f[v] = ac.w.uacc + v * ac.b.V;
+    accf.f[v] = af.w.uacc + v * af.b.V;
+    for (int q = 0; q < 2; q++) {
+      sbc[q].f[v] = ac.w.ustage + (9 * q + v) * ac.b.V;
+      sbf[q].f[v] = af.w.ustage + (9 * q + v) * af.b.V;
+    }
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(stats);
+  const F5 pc = f5(Pc), pf = f5(Pf);
+  for (int stage = 0; stage < 4; stage++) {
+    const F9& usc = stage == 0 ? unc : sbc[(stage - 1) % 2];
+    const F9& unxc = stage == 3 ? unc : sbc[stage % 2];
+    const F9& usf = stage == 0 ? unf : sbf[(stage - 1) % 2];
+    const F9& unxf = stage == 3 ? unf : sbf[stage % 2];
+    st = stage_impl(ac, stage, dt, unc, usc, unxc, accc, pc, nullptr, cnt, s);
+    if (st != ASTERX_OK) return st;
+    if (launch_prolong(ac.b, af.b, L, usc, pc, usf, pf, false, s) != cudaSuccess) return ASTERX_ECUDA;
+    st = stage_given_ghosts(af, stage, dt, unf, usf, unxf, accf, pf, cnt, s);
+    if (st != ASTERX_OK) return st;
+  }
+  return cuda_status(launch_restrict(ac.b, af.b, L, unc, unf, s));
+}
+
 asterx_status asterx_rk2_step(const asterx_params* p, const asterx_block* blk, double dt, asterx_state* U,
                               asterx_prims* P, signed char* flags, asterx_c2p_stats* stats, void* ws,
                               size_t ws_bytes, asterx_stream stream) {

@@ -122,6 +122,13 @@ void launch_ghost_adjoint(const Blk& b, const AdjGhost& g, int nf, cudaStream_t 
 cudaError_t launch_axpby9(const Blk& b, double alpha, const F9& x, double beta, const F9& y, cudaStream_t s);
 cudaError_t launch_mask_owned9(const Blk& b, const F9& x, cudaStream_t s);
 
+// two refinement levels: a fine block (spacing / 2) whose interior covers the coarse interior cells L .. L + n_f/2
+// - 1; prolongation of the 9 state fields and 5 primitives to the fine ghost points (every point if all), and
+// restriction of the 9 state fields to the coarse points under the fine interior
+cudaError_t launch_prolong(const Blk& C, const Blk& F, const int L[3], const F9& Uc, const F5& Pc, const F9& Uf,
+                           const F5& Pf, bool all, cudaStream_t s);
+cudaError_t launch_restrict(const Blk& C, const Blk& F, const int L[3], const F9& Uc, const F9& Uf, cudaStream_t s);
+
 // face-kernel launch timing (measurement hook of the benchmark)
 cudaError_t profile_enable(int cap);
 void profile_disable();

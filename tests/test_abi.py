@@ -207,3 +207,23 @@ def test_tiled_batch_validation():
         sz = max(L.asterx_batch_workspace_size(arr, 2), size)
         rc = L.asterx_batch_prepare_tiled(ctypes.byref(p), arr, 2, ctypes.byref(t), ctypes.c_void_p(256), sz, None)
         assert rc == A.ASTERX_EINVAL
+
+
+def test_refinement_nesting_validation():
+    """asterx_prolong checks the nesting on the host: half the spacing, even fine extents, a fine corner on a
+    coarse vertex, the box inside the coarse interior."""
+    L = A.lib()
+    st = A.State(*([8] * 9))
+    pr = A.Prims(*([8] * 5))
+    c = A.block_struct((16, 16, 16), 3, (0.0, 0.0, 0.0), (0.1,) * 3, (1, 1, 1))
+    bad = [
+        A.block_struct((8, 8, 8), 3, (0.3, 0.3, 0.3), (0.06, 0.05, 0.05), (1, 1, 1)),  # not half the spacing
+        A.block_struct((7, 8, 8), 3, (0.3, 0.3, 0.3), (0.05,) * 3, (1, 1, 1)),         # odd fine extent
+        A.block_struct((8, 8, 8), 3, (0.35, 0.3, 0.3), (0.05,) * 3, (1, 1, 1)),        # corner between coarse vertices
+        A.block_struct((8, 8, 8), 3, (1.3, 0.3, 0.3), (0.05,) * 3, (1, 1, 1)),         # beyond the coarse interior
+        A.block_struct((8, 8, 8), 3, (-0.1, 0.3, 0.3), (0.05,) * 3, (1, 1, 1)),        # before it
+    ]
+    for f in bad:
+        rc = L.asterx_prolong(ctypes.byref(c), ctypes.byref(f), ctypes.byref(st), ctypes.byref(pr),
+                              ctypes.byref(st), ctypes.byref(pr), 0, None)
+        assert rc == A.ASTERX_EINVAL
