@@ -60,11 +60,11 @@ def parse():
                     help="skip the Lax-Friedrichs / flux-CT / RK2 step measurements")
     ap.add_argument("--no-coupling", action="store_true",
                     help="skip the stress-energy tensor and time-dependent-metric step measurements")
-    ap.add_argument("--profile-region", choices=("none", "forward", "adjoint", "batched", "coupling", "tiled"), default="none",
+    ap.add_argument("--profile-region", choices=("none", "forward", "adjoint", "batched", "coupling", "tiled", "refined"), default="none",
                     help="bracket one extra forward RK4 step (main workload), one adjoint step, one batched "
                          "step and one step of the equal-volume block, one geometry derivation and one "
-                         "stress-energy tensor call, or one step of the 4x4x4-tiled domain with "
-                         "cudaProfilerStart/Stop, for a profiler run with --profile-from-start off")
+                         "stress-energy tensor call, one step of the 4x4x4-tiled domain, or one two-level step "
+                         "with cudaProfilerStart/Stop, for a profiler run with --profile-from-start off")
     return ap.parse_args()
 
 
@@ -382,6 +382,11 @@ def run_refined(args, dev, stream, single_ms):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / steps
+    if args.profile_region == "refined":
+        torch.cuda.profiler.start()
+        A.rk4_step_refined(sc, sf, U, P, Uf, Pf, dt)
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.stop()
     finite = bool(torch.isfinite(U).all()) and bool(torch.isfinite(Uf).all())
     cells = w.interior_cells + int(np.prod(nf))
     del sc, sf, M, U, P, Mf, Uf, Pf

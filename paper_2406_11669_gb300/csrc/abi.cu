@@ -549,16 +549,23 @@ asterx_status asterx_rk4_step_host(const asterx_params* p, const asterx_block* b
   const size_t bytes = (size_t)padded_V(blk) * sizeof(double);
   F9 u = f9(dU);
   F5 pr = f5(dP);
-  for (int v = 0; v < 9; v++)
-    if (cudaMemcpyAsync(u.f[v], h_U9[v], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return ASTERX_ECUDA;
-  for (int v = 0; v < 5; v++)
-    if (cudaMemcpyAsync(pr.f[v], h_P5[v], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return ASTERX_ECUDA;
+  // one copy per run of fields that are consecutive on both sides (a stacked array is one copy)
+  auto copy_fields = [&](double* const* dst, double* const* src, int nf, cudaMemcpyKind kind) {
+    for (int v = 0; v < nf;) {
+      int e = v + 1;
+      while (e < nf && dst[e] == dst[e - 1] + bytes / sizeof(double) && src[e] == src[e - 1] + bytes / sizeof(double))
+        e++;
+      if (cudaMemcpyAsync(dst[v], src[v], (size_t)(e - v) * bytes, kind, s) != cudaSuccess) return false;
+      v = e;
+    }
+    return true;
+  };
+  if (!copy_fields(u.f, h_U9, 9, cudaMemcpyHostToDevice) || !copy_fields(pr.f, h_P5, 5, cudaMemcpyHostToDevice))
+    return ASTERX_ECUDA;
   st = asterx_rk4_step(p, blk, dt, dU, dP, nullptr, stats, ws, ws_bytes, stream);
   if (st != ASTERX_OK) return st;
-  for (int v = 0; v < 9; v++)
-    if (cudaMemcpyAsync(h_U9[v], u.f[v], bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return ASTERX_ECUDA;
-  for (int v = 0; v < 5; v++)
-    if (cudaMemcpyAsync(h_P5[v], pr.f[v], bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return ASTERX_ECUDA;
+  if (!copy_fields(h_U9, u.f, 9, cudaMemcpyDeviceToHost) || !copy_fields(h_P5, pr.f, 5, cudaMemcpyDeviceToHost))
+    return ASTERX_ECUDA;
   return cuda_status(cudaStreamSynchronize(s));
 }
 

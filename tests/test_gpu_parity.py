@@ -213,3 +213,28 @@ def test_rk4_step_graph_capture_replays_identically():
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(Ua, Ub) and torch.equal(Pa, Pb)
+
+
+@pytest.mark.parametrize("stacked", [True, False])
+def test_rk4_step_host_buffers_equal_the_device_step(stacked):
+    """asterx_rk4_step_host (pinned host buffers in, the step, host buffers out) ends bit-identical to
+    asterx_rk4_step on device arrays; stacked host arrays travel as one copy per array, separate ones per field."""
+    need_gpu()
+    w = WORKLOADS["config3"]
+    case = GpuCase(w)
+    U, P = O.initial_state(w)
+    O.ghost_fill_state(w, U)
+    Ud, Pd = case.dev(U), case.dev(P)
+    case.solver.rk4_step(Ud, Pd, w.dt)
+    if stacked:
+        hU = torch.from_numpy(U.copy()).pin_memory()
+        hP = torch.from_numpy(P.copy()).pin_memory()
+    else:  # each field its own allocation: a list of pinned tensors viewed through a stacked wrapper
+        hU = [torch.from_numpy(U[v].copy()).pin_memory() for v in range(9)]
+        hP = [torch.from_numpy(P[v].copy()).pin_memory() for v in range(5)]
+    dU2, dP2 = torch.empty_like(Ud), torch.empty_like(Pd)
+    case.solver.rk4_step_host(hU, hP, dU2, dP2, w.dt)
+    gotU = np.stack([np.asarray(hU[v]) for v in range(9)])
+    gotP = np.stack([np.asarray(hP[v]) for v in range(5)])
+    assert np.array_equal(gotU, case.host(Ud))
+    assert np.array_equal(gotP, case.host(Pd))
