@@ -51,15 +51,57 @@ struct RefineArgs {
 
 __device__ __forceinline__ long clin(const Blk& b, int i, int j, int k) { return i + b.sy * j + b.sz * k; }
 
+// the points of the fine padded array outside its cell interior [g, g+n) along some axis (every ghost point of
+// every field lies there): the planes before and after the interior along z, then along y within the interior
+// z range, then along x within the interior y and z ranges
+__host__ __device__ inline long shell_count(const Blk& F) {
+  return F.V - (long)F.n[0] * F.n[1] * F.n[2];
+}
+
+__device__ __forceinline__ void shell_point(const Blk& F, long t, int& i, int& j, int& k) {
+  const long e0 = F.N[0] + 1, e1 = F.N[1] + 1;
+  const long zA = (long)(F.N[2] + 1 - F.n[2]) * e1 * e0;
+  if (t < zA) {
+    const long pl = t / (e1 * e0), r = t % (e1 * e0);
+    k = (int)(pl < F.g ? pl : pl + F.n[2]);
+    j = (int)(r / e0);
+    i = (int)(r % e0);
+    return;
+  }
+  t -= zA;
+  const long yw = (long)(F.N[1] + 1 - F.n[1]) * e0;
+  const long zB = (long)F.n[2] * yw;
+  if (t < zB) {
+    k = F.g + (int)(t / yw);
+    const long r = t % yw, q = r / e0;
+    j = (int)(q < F.g ? q : q + F.n[1]);
+    i = (int)(r % e0);
+    return;
+  }
+  t -= zB;
+  const long xw = F.N[0] + 1 - F.n[0];
+  k = F.g + (int)(t / ((long)F.n[1] * xw));
+  const long r = t % ((long)F.n[1] * xw);
+  j = F.g + (int)(r / xw);
+  const long q = r % xw;
+  i = (int)(q < F.g ? q : q + F.n[0]);
+}
+
 __global__ void __launch_bounds__(128) k_prolong(RefineArgs a) {
   const Blk& F = a.F;
   const Blk& C = a.C;
-  const long count = F.V;
+  const long count = a.all ? F.V : shell_count(F);
   const int clm[14] = {7, 7, 7, 7, 7, 1, 2, 4, 0, 7, 7, 7, 7, 7};  // bit a: cell-centred along axis a
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % F.sy);
-    const int j = (int)((t / F.sy) % (F.N[1] + 1));
-    const int k = (int)(t / F.sz);
+    int i, j, k;
+    if (a.all) {
+      i = (int)(t % F.sy);
+      j = (int)((t / F.sy) % (F.N[1] + 1));
+      k = (int)(t / F.sz);
+    } else {
+      shell_point(F, t, i, j, k);
+    }
+    const long c = clin(F, i, j, k);
     const int p[3] = {i, j, k};
     const int fr[3] = {i - F.g, j - F.g, k - F.g};
 #pragma unroll 1
@@ -84,8 +126,8 @@ __global__ void __launch_bounds__(128) k_prolong(RefineArgs a) {
         return prolong_1d(cl[1], fr[1], along_y);
       };
       const double val = prolong_1d(cl[2], fr[2], along_z);
-      if (v < 9) a.Uf.f[v][t] = val;
-      else a.Pf.f[v - 9][t] = val;
+      if (v < 9) a.Uf.f[v][c] = val;
+      else a.Pf.f[v - 9][c] = val;
     }
   }
 }
@@ -140,7 +182,7 @@ cudaError_t launch_prolong(const Blk& C, const Blk& F, const int L[3], const F9&
   a.Uf = Uf;
   a.Pf = Pf;
   a.all = all;
-  k_prolong<<<refine_grid(F.V), 128, 0, s>>>(a);
+  k_prolong<<<refine_grid(all ? F.V : shell_count(F)), 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 
