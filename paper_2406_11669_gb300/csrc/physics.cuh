@@ -456,22 +456,23 @@ __host__ __device__ __forceinline__ void wenoz_from_indicators(const T s[5], T e
     a2 = 1.0 + r2 * r2;
   }
   // upper face: linear weights (1/10, 6/10, 3/10) on the sub-stencils ending at, centred on, starting at i, with the
-  // candidates' common factor 1/6 and the weights' 1/10 taken out of numerator and denominator
+  // candidates' common factor 1/6 and the weights' 1/10 taken out of numerator and denominator; lower face: the
+  // mirrored stencil, whose indicator k is indicator 2-k here
   const T w1 = 6.0 * a1;
-  {
-    const T q0 = 2.0 * s[0] - 7.0 * s[1] + 11.0 * s[2];
-    const T q1 = -s[1] + 5.0 * s[2] + 2.0 * s[3];
-    const T q2 = 2.0 * s[2] + 5.0 * s[3] - s[4];
-    const T w2 = 3.0 * a2;
-    hi = (a0 * q0 + w1 * q1 + w2 * q2) / (6.0 * (a0 + w1 + w2));
-  }
-  // lower face: mirrored stencil, indicator k of the mirror is indicator 2-k here
-  {
-    const T q0 = 2.0 * s[4] - 7.0 * s[3] + 11.0 * s[2];
-    const T q1 = -s[3] + 5.0 * s[2] + 2.0 * s[1];
-    const T q2 = 2.0 * s[2] + 5.0 * s[1] - s[0];
-    const T w2 = 3.0 * a0;
-    lo = (a2 * q0 + w1 * q1 + w2 * q2) / (6.0 * (a2 + w1 + w2));
+  const T Nh = a0 * (2.0 * s[0] - 7.0 * s[1] + 11.0 * s[2]) + w1 * (-s[1] + 5.0 * s[2] + 2.0 * s[3]) +
+               (3.0 * a2) * (2.0 * s[2] + 5.0 * s[3] - s[4]);
+  const T Nl = a2 * (2.0 * s[4] - 7.0 * s[3] + 11.0 * s[2]) + w1 * (-s[3] + 5.0 * s[2] + 2.0 * s[1]) +
+               (3.0 * a0) * (2.0 * s[2] + 5.0 * s[1] - s[0]);
+  const T Dh = a0 + w1 + 3.0 * a2, Dl = a2 + w1 + 3.0 * a0;
+  // both normalisations from one division where the product of the two sums is in range
+  const T DD = Dh * Dl;
+  if (val(DD) > 1e-290 && val(DD) < 1e290) {
+    const T r = 1.0 / (6.0 * DD);
+    hi = Nh * Dl * r;
+    lo = Nl * Dh * r;
+  } else {
+    hi = Nh / (6.0 * Dh);
+    lo = Nl / (6.0 * Dl);
   }
 }
 
