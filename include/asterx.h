@@ -383,6 +383,12 @@ void asterx_profile_disable(void);
  * blocks*threads doubles) so the work cannot be elided. */
 asterx_status asterx_dfma_probe(double *out, int blocks, int threads, long iters, asterx_stream stream);
 
+/* The reciprocal the magnetosonic-speed Newton iteration (Sec. 3.3) uses for its corrections: out[i] ~ 1/d[i]
+ * for n device doubles (a hardware estimate refined by one Newton-Raphson step; relative error far below the
+ * iteration's stopping threshold for 1e-290 < |d| < 1e290, the range it is used in).  Lets tests bound its
+ * error; not part of the method's interface.  d and out: device, n doubles each, caller-owned. */
+asterx_status asterx_newton_rcp(const double *d, double *out, long n, asterx_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -128,11 +128,12 @@ def lib():
         L.asterx_profile_read.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
         L.asterx_profile_disable.restype = None
         L.asterx_dfma_probe.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_long, st]
+        L.asterx_newton_rcp.argtypes = [vp, vp, ctypes.c_long, st]
         for name in ("asterx_prepare", "asterx_prim2con", "asterx_con2prim", "asterx_fill_ghosts", "asterx_rhs",
                      "asterx_rk_stage", "asterx_rk4_step", "asterx_rk2_step", "asterx_rk4_step_host", "asterx_tmunu",
                      "asterx_rk4_step_metrics", "asterx_prolong", "asterx_rk4_step_refined",
                      "asterx_profile_enable",
-                     "asterx_profile_read", "asterx_dfma_probe"):
+                     "asterx_profile_read", "asterx_dfma_probe", "asterx_newton_rcp"):
             getattr(L, name).restype = ctypes.c_int
         if L.asterx_abi_version() != ABI_VERSION:
             raise ImportError(f"libasterx ABI {L.asterx_abi_version()} != binding ABI {ABI_VERSION}")
@@ -403,6 +404,12 @@ def profile_disable():
 def dfma_probe(out, blocks, threads, iters, stream=None):
     _check(lib().asterx_dfma_probe(ctypes.c_void_p(out.data_ptr()), int(blocks), int(threads), int(iters),
                                    _stream(stream)), "asterx_dfma_probe")
+
+
+def newton_rcp(d, out, stream=None):
+    """The speed solver's Newton-correction reciprocal of the device doubles d, written to out."""
+    _check(lib().asterx_newton_rcp(ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(out.data_ptr()), int(d.numel()),
+                                   _stream(stream)), "asterx_newton_rcp")
 
 
 NOALLOC_MAX_ENTRIES = 65536

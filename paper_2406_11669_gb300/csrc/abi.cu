@@ -1126,4 +1126,10 @@ asterx_status asterx_dfma_probe(double* out, int blocks, int threads, long iters
   return cuda_status(launch_dfma_probe(out, blocks, threads, iters, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+asterx_status asterx_newton_rcp(const double* d, double* out, long n, asterx_stream stream) {
+  if (n < 0 || (n > 0 && (!ptr_ok(d) || !ptr_ok(out)))) return ASTERX_EINVAL;
+  if (n == 0) return ASTERX_OK;
+  return cuda_status(launch_newton_rcp(d, out, n, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 }  // extern "C"

@@ -136,5 +136,7 @@ cudaError_t profile_read(int* launches, double* total_ms);
 
 // FP64 fused multiply-add throughput probe (measurement helper)
 cudaError_t launch_dfma_probe(double* out, int blocks, int threads, long iters, cudaStream_t s);
+// the quartic solver's Newton-correction reciprocal on n values (measurement helper)
+cudaError_t launch_newton_rcp(const double* d, double* out, long n, cudaStream_t s);
 
 }  // namespace asterx

@@ -75,6 +75,20 @@ struct SideOutT {
 };
 using SideOut = SideOutT<double>;
 
+// Reciprocal for Newton corrections, where a relative error far below the correction's own accuracy is enough:
+// the PTX reciprocal estimate (rcp.approx.ftz.f64) refined by one Newton-Raphson step r <- r + r (1 - d r), the
+// textbook iteration for 1/d (Flynn 1970), which squares the estimate's relative error.  Meant for
+// 1e-290 < |d| < 1e290 (the caller divides outside that range); the host build divides.
+__host__ __device__ __forceinline__ double newton_rcp(double d) {
+#ifdef __CUDA_ARCH__
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  return fma(r, fma(-d, r, 1.0), r);
+#else
+  return 1.0 / d;
+#endif
+}
+
 // Extreme roots of the magnetosonic quartic (Sec. 3.3): with phi = (-lambda, e_d),
 //   a = u^mu phi_mu = ud - lambda u0,  Bc = b^mu phi_mu = bd - lambda b0,
 //   G = g^{mu nu} phi_mu phi_nu = gamma^dd - (lambda + beta^d)^2 / alpha^2,
@@ -101,8 +115,14 @@ struct Quartic {
       const double r = cs2 * bc * bc - C2 * a2;
       const double q = A4 * a2 * a2 + r * G;
       const double dq = k4 * a2 * a + (ka * a + kb * bc) * G + r * (kg * lb);
-      if (dq == 0.0) break;
-      const double step = q / dq;
+      const double adq = fabs(dq);
+      double step;
+      if (adq > 1e-290 && adq < 1e290) {
+        step = q * newton_rcp(dq);
+      } else {
+        if (adq == 0.0) break;
+        step = q / dq;
+      }
       lam -= step;
       if (fabs(step) <= thr) break;
     }

@@ -1,6 +1,7 @@
 // FP64 fused multiply-add throughput probe: the ALU roofline of an FP64-bound kernel is the rate at which
 // the SMs retire DFMA.  Eight independent chains per thread keep the FP64 pipe busy regardless of latency.
 #include "kernels.h"
+#include "physics.cuh"
 
 namespace asterx {
 
@@ -22,6 +23,19 @@ __global__ void k_dfma_probe(double* out, long iters) {
 
 cudaError_t launch_dfma_probe(double* out, int blocks, int threads, long iters, cudaStream_t s) {
   k_dfma_probe<<<blocks, threads, 0, s>>>(out, iters);
+  return cudaGetLastError();
+}
+
+// the Newton-correction reciprocal of the quartic solver applied to n values (its error bound is tested)
+__global__ void k_newton_rcp(const double* __restrict__ d, double* __restrict__ out, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = newton_rcp(d[i]);
+}
+
+cudaError_t launch_newton_rcp(const double* d, double* out, long n, cudaStream_t s) {
+  long blocks = (n + 255) / 256;
+  if (blocks > 152L * 16) blocks = 152L * 16;
+  k_newton_rcp<<<(int)blocks, 256, 0, s>>>(d, out, n);
   return cudaGetLastError();
 }
 

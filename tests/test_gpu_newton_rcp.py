@@ -1,0 +1,36 @@
+"""Error bound of the reciprocal the magnetosonic-speed Newton iteration (Sec. 3.3) uses for its corrections: a
+hardware reciprocal estimate refined by one Newton-Raphson step, which squares the estimate's relative error.
+
+A Newton correction stops the iteration once it falls below 3e-9 of the speed scale, so a relative error of the
+correction far below 1e-6 leaves the converged root unchanged to rounding; the bound asserted here, 1e-11 over
+the whole range the solver uses it in (1e-290 < |d| < 1e290, both signs, including powers of two and their
+neighbours), is far inside that.  The reference values are numpy's correctly rounded 1/d.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def test_newton_reciprocal_relative_error():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_11669_gb300 import asterx as A
+    rng = np.random.default_rng(2406)
+    mags = 10.0 ** rng.uniform(-289.5, 289.5, 1 << 20)
+    d = mags * rng.choice([-1.0, 1.0], mags.size)
+    p2 = 2.0 ** np.arange(-960, 961, 7, dtype=np.float64)
+    special = np.concatenate([p2, np.nextafter(p2, 0), np.nextafter(p2, np.inf), -p2, 1.0 + 2.0 ** -np.arange(1, 53),
+                              [1.0, -1.0, 3.0, 1.0 / 3.0, 0.1, 7.0e-289, 6.0e289]])
+    d = np.concatenate([d, special])
+    dd = torch.from_numpy(d).cuda()
+    out = torch.empty_like(dd)
+    A.newton_rcp(dd, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    ref = 1.0 / d
+    rel = np.abs(got - ref) / np.abs(ref)
+    print(f"largest relative error {rel.max():.3e} over {d.size} values")
+    assert np.all(np.isfinite(got))
+    assert rel.max() <= 1e-11
