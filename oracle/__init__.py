@@ -316,6 +316,81 @@ def refined_rk4_step(wc, Mc, Uc, Pc, wf, Mf, Uf, Pf, L, dt, params=None):
     return Us_c, Us_f
 
 
+def rk4_dense_weights(theta):
+    """The continuous extension of classical RK4: u(t_n + theta h) ~ u_n + h sum_i b_i(theta) k_i with
+    b_1 = theta - 3 theta^2 / 2 + 2 theta^3 / 3, b_2 = b_3 = theta^2 - 2 theta^3 / 3, b_4 = -theta^2 / 2 +
+    2 theta^3 / 3 (b(1) = the RK4 weights).  Returns the four b_i and their first three theta-derivatives as a
+    (4, 4) array [derivative order, i]."""
+    t = float(theta)
+    return np.array([
+        [t - 1.5 * t * t + 2.0 * t ** 3 / 3.0, t * t - 2.0 * t ** 3 / 3.0, t * t - 2.0 * t ** 3 / 3.0,
+         -0.5 * t * t + 2.0 * t ** 3 / 3.0],
+        [1.0 - 3.0 * t + 2.0 * t * t, 2.0 * t - 2.0 * t * t, 2.0 * t - 2.0 * t * t, -t + 2.0 * t * t],
+        [-3.0 + 4.0 * t, 2.0 - 4.0 * t, 2.0 - 4.0 * t, -1.0 + 4.0 * t],
+        [4.0, -4.0, -4.0, 4.0]])
+
+
+def subcycle_stage_weights(m):
+    """Weights beta[s, i] of the coarse slopes h k_i in the fine ghost values of stage s of fine substep m (0 or
+    1; each of half the coarse step h, starting at theta0 = m / 2).  The fine RK4 stage states of a linear
+    problem are Taylor sums about the substep start: u, u + (h_f/2) u', u + (h_f/2) u' + (h_f^2/4) u'', and
+    u + h_f u' + (h_f^2/2) u'' + (h_f^3/4) u'''; u and its time derivatives come from the coarse step's dense
+    output (the time interpolation that replaces buffer zones in the paper's subcycling, Sec. 2.5; the
+    stage-consistent form of Mongwane 2015).  With h_f = h / 2 the powers of h_f become 1/4, 1/16, 1/2, 1/8 and
+    1/32 times the dense output's theta-derivatives."""
+    B = rk4_dense_weights(0.5 * m)
+    return np.array([B[0],
+                     B[0] + 0.25 * B[1],
+                     B[0] + 0.25 * B[1] + (1.0 / 16.0) * B[2],
+                     B[0] + 0.5 * B[1] + 0.125 * B[2] + (1.0 / 32.0) * B[3]])
+
+
+def subcycle_ghost_state(Un, Y1, Y2, Y3, U1, m, s):
+    """The coarse state that feeds the fine ghost points at stage s of fine substep m: U_n + sum_i beta[s, i]
+    h k_i, the slopes taken from the coarse step's base U_n, stage states Y_1..Y_3 and result U_1 = U_{n+1}."""
+    g0 = 2.0 * (Y1 - Un)
+    g1 = 2.0 * (Y2 - Un)
+    g2 = Y3 - Un
+    g3 = 6.0 * (U1 - Un) - g0 - 2.0 * g1 - 2.0 * g2
+    beta = subcycle_stage_weights(m)
+    return Un + (beta[s, 0] * g0 + beta[s, 1] * g1 + beta[s, 2] * g2 + beta[s, 3] * g3)
+
+
+def subcycled_rk4_step(wc, Mc, Uc, Pc, wf, Mf, Uf, Pf, L, dt, params=None):
+    """One coarse RK4 step of size dt with the fine level subcycled (two RK4 steps of dt / 2).  The coarse step
+    runs first and keeps its stage states Y_1..Y_3 and its base U_n (as the first stage's recovery leaves it);
+    its slopes h k_i follow from them (h k_1 = 2 (Y_1 - U_n), h k_2 = 2 (Y_2 - U_n), h k_3 = Y_3 - U_n,
+    h k_4 = 6 (U_{n+1} - U_n) - h k_1 - 2 h k_2 - 2 h k_3).  Before each fine stage the coarse state
+    U_n + sum_i beta[s, i] h k_i (subcycle_stage_weights) is ghost-filled, recovered (seeded by the previous
+    recovery, starting from the primitives the coarse step leaves) and prolonged to the fine ghost points.  After
+    both substeps the coarse points under the fine interior are restricted.  Returns (Uc_next, Uf_next)."""
+    h = float(dt)
+    Ua = np.zeros_like(Uc)
+    Y = [Uc, np.array(Uc), np.array(Uc), np.array(Uc)]
+    Un = None
+    for s in range(4):
+        nxt = Y[s + 1] if s < 3 else Uc
+        rk_stage(wc, Mc, s, h, Uc, Y[s], nxt, Ua, Pc, params)
+        if s == 0:
+            Un = Uc.copy()
+    Pt = Pc.copy()
+    for m in range(2):
+        Ua_f = np.zeros_like(Uf)
+        Us_f = Uf
+        for s in range(4):
+            Yt = subcycle_ghost_state(Un, Y[1], Y[2], Y[3], Uc, m, s)
+            ghost_fill_state(wc, Yt)
+            con2prim(wc, Mc, Yt, Pt, params)
+            ghost_fill_prims(wc, Pt)
+            prolong(wc, wf, L, Yt, Pt, Us_f, Pf)
+            Un_f = Us_f.copy()
+            rk_stage_given_ghosts(wf, Mf, s, 0.5 * h, Uf, Us_f, Un_f, Ua_f, Pf, params)
+            Us_f = Un_f
+        Uf = Us_f
+    restrict(wc, wf, L, Uc, Uf)
+    return Uc, Uf
+
+
 def rk2_step(w, M, U, P, dt=None, params=None):
     """One RK2 step (explicit midpoint: U_1 = U_n + dt/2 L(U_n), U_{n+1} = U_n + dt L(U_1)); as rk4_step."""
     dt = float(dt if dt is not None else w.dt)
