@@ -60,11 +60,13 @@ def parse():
                     help="skip the Lax-Friedrichs / flux-CT / RK2 step measurements")
     ap.add_argument("--no-coupling", action="store_true",
                     help="skip the stress-energy tensor and time-dependent-metric step measurements")
-    ap.add_argument("--profile-region", choices=("none", "forward", "adjoint", "batched", "coupling", "tiled", "refined"), default="none",
+    ap.add_argument("--profile-region", choices=("none", "forward", "adjoint", "batched", "coupling", "tiled", "refined",
+                                                  "subcycled"), default="none",
                     help="bracket one extra forward RK4 step (main workload), one adjoint step, one batched "
                          "step and one step of the equal-volume block, one geometry derivation and one "
-                         "stress-energy tensor call, one step of the 4x4x4-tiled domain, or one two-level step "
-                         "with cudaProfilerStart/Stop, for a profiler run with --profile-from-start off")
+                         "stress-energy tensor call, one step of the 4x4x4-tiled domain, one two-level step or "
+                         "one subcycled two-level step with cudaProfilerStart/Stop, for a profiler run with "
+                         "--profile-from-start off")
     return ap.parse_args()
 
 
@@ -345,7 +347,9 @@ def run_refined(args, dev, stream, single_ms):
     """Two refinement levels on the benchmark workload: the 128^3 block plus a fine block of half the spacing over
     its central 64^3 coarse cells (128^3 fine cells; fine data prolonged from the coarse level, the Schwarzschild
     metric evaluated at the fine vertices), stepped together with the fine time step (prolongation of each coarse
-    stage state to the fine ghosts, restriction after the step).  Compared with two plain steps of 128^3 blocks."""
+    stage state to the fine ghosts, restriction after the step).  Compared with two plain steps of 128^3 blocks.
+    Then the same levels subcycled: one coarse step of twice the size, two fine steps, against two of the steps
+    with the fine step on both levels (the same time covered)."""
     import numpy as np
     import torch
 
@@ -387,13 +391,31 @@ def run_refined(args, dev, stream, single_ms):
         A.rk4_step_refined(sc, sf, U, P, Uf, Pf, dt)
         torch.cuda.synchronize(dev)
         torch.cuda.profiler.stop()
+    # subcycled: one coarse step of twice the fine step, two fine steps (the same time covered as two of the
+    # steps above)
+    A.rk4_step_subcycled(sc, sf, U, P, Uf, Pf, 2.0 * dt)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        A.rk4_step_subcycled(sc, sf, U, P, Uf, Pf, 2.0 * dt)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_sub = e0.elapsed_time(e1) / steps
+    if args.profile_region == "subcycled":
+        torch.cuda.profiler.start()
+        A.rk4_step_subcycled(sc, sf, U, P, Uf, Pf, 2.0 * dt)
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.stop()
     finite = bool(torch.isfinite(U).all()) and bool(torch.isfinite(Uf).all())
     cells = w.interior_cells + int(np.prod(nf))
+    updates_sub = 4 * w.interior_cells + 8 * int(np.prod(nf))  # zone-stage updates per coarse step
     del sc, sf, M, U, P, Mf, Uf, Pf
     torch.cuda.empty_cache()
     return {"coarse_n": args.n, "fine_box_coarse_cells": m, "fine_n": nf[0], "ms_per_step": ms,
             "value": cells * 4 / (ms / 1e3), "unit": UNIT, "vs_two_single_steps": 2.0 * single_ms / ms,
-            "finite": finite}
+            "finite": finite,
+            "subcycled": {"ms_per_coarse_step": ms_sub, "value": updates_sub / (ms_sub / 1e3), "unit": UNIT,
+                          "speedup_vs_same_step": 2.0 * ms / ms_sub}}
 
 
 def run_adjoint(args, dev, stream):

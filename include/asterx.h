@@ -200,6 +200,25 @@ asterx_status asterx_rk4_step_refined(const asterx_params *p, const asterx_block
                                       asterx_prims *Pf, asterx_c2p_stats *stats, void *ws_c, size_t ws_c_bytes,
                                       void *ws_f, size_t ws_f_bytes, asterx_stream stream);
 
+/* Subcycling in time (Sec. 3.10; the paper defers its method, so this follows the published stage-consistent
+ * form of Mongwane 2015): one RK4 step of size dt on the coarse level and two of dt/2 on the fine one, with no
+ * buffer zones.  The coarse step runs first and keeps its base U_n, stage states Y_1..Y_3 and result; before
+ * each fine stage the coarse state U_n + sum_i beta_i h k_i is formed from them (the coarse step's dense
+ * output and its time derivatives at the substep start, combined as the fine stage states of a linear problem:
+ * fourth-order accurate ghost data), ghost-filled, recovered (seeded by the previous such recovery, starting
+ * from the primitives the coarse step leaves; only on the coarse cells the prolongation reads, or on whole
+ * axes where those reach the boundary) and prolonged to the fine ghost points as asterx_prolong does.
+ * After both fine steps the coarse points under the fine interior are restricted.  ws_c / ws_f: the two
+ * blocks' prepared workspaces; ws_t: scratch of asterx_subcycle_workspace_size(coarse) bytes (256-byte
+ * aligned).  The Lorenz damping (xi_lorenz = 0) is 1.5 / dt on the coarse level and 3 / dt on the fine one.
+ * flags are not written; stats (may be NULL) accumulates the stage recoveries of both levels. */
+size_t asterx_subcycle_workspace_size(const asterx_block *coarse);
+asterx_status asterx_rk4_step_subcycled(const asterx_params *p, const asterx_block *coarse,
+                                        const asterx_block *fine, double dt, asterx_state *Uc, asterx_prims *Pc,
+                                        asterx_state *Uf, asterx_prims *Pf, asterx_c2p_stats *stats, void *ws_c,
+                                        size_t ws_c_bytes, void *ws_f, size_t ws_f_bytes, void *ws_t,
+                                        size_t ws_t_bytes, asterx_stream stream);
+
 /* ---- coupling to a spacetime solver ----
  *
  * Stress-energy tensor T_{mu nu} (Eq. tmunu with both indices lowered by the 4-metric; T lives at vertices,

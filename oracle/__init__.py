@@ -335,7 +335,7 @@ def subcycle_stage_weights(m):
     1; each of half the coarse step h, starting at theta0 = m / 2).  The fine RK4 stage states of a linear
     problem are Taylor sums about the substep start: u, u + (h_f/2) u', u + (h_f/2) u' + (h_f^2/4) u'', and
     u + h_f u' + (h_f^2/2) u'' + (h_f^3/4) u'''; u and its time derivatives come from the coarse step's dense
-    output (the time interpolation that replaces buffer zones in the paper's subcycling, Sec. 2.5; the
+    output (the time interpolation that replaces buffer zones in the paper's subcycling, Sec. 3.10; the
     stage-consistent form of Mongwane 2015).  With h_f = h / 2 the powers of h_f become 1/4, 1/16, 1/2, 1/8 and
     1/32 times the dense output's theta-derivatives."""
     B = rk4_dense_weights(0.5 * m)

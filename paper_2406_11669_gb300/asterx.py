@@ -99,6 +99,10 @@ def lib():
         L.asterx_rk4_step_metrics.argtypes = [P, B, ctypes.c_double, ctypes.POINTER(M), S, Pr, vp, vp, vp, sz, st]
         L.asterx_prolong.argtypes = [B, B, S, Pr, S, Pr, ctypes.c_int, st]
         L.asterx_rk4_step_refined.argtypes = [P, B, B, ctypes.c_double, S, Pr, S, Pr, vp, vp, sz, vp, sz, st]
+        L.asterx_subcycle_workspace_size.restype = ctypes.c_size_t
+        L.asterx_subcycle_workspace_size.argtypes = [B]
+        L.asterx_rk4_step_subcycled.argtypes = [P, B, B, ctypes.c_double, S, Pr, S, Pr, vp, vp, sz, vp, sz, vp, sz,
+                                                st]
         BB = ctypes.POINTER(BatchBlock)
         L.asterx_batch_workspace_size.restype = ctypes.c_size_t
         L.asterx_batch_workspace_size.argtypes = [BB, ctypes.c_int]
@@ -131,7 +135,7 @@ def lib():
         L.asterx_newton_rcp.argtypes = [vp, vp, ctypes.c_long, st]
         for name in ("asterx_prepare", "asterx_prim2con", "asterx_con2prim", "asterx_fill_ghosts", "asterx_rhs",
                      "asterx_rk_stage", "asterx_rk4_step", "asterx_rk2_step", "asterx_rk4_step_host", "asterx_tmunu",
-                     "asterx_rk4_step_metrics", "asterx_prolong", "asterx_rk4_step_refined",
+                     "asterx_rk4_step_metrics", "asterx_prolong", "asterx_rk4_step_refined", "asterx_rk4_step_subcycled",
                      "asterx_profile_enable",
                      "asterx_profile_read", "asterx_dfma_probe", "asterx_newton_rcp"):
             getattr(L, name).restype = ctypes.c_int
@@ -442,6 +446,26 @@ def rk4_step_refined(coarse, fine, Uc, Pc, Uf, Pf, dt, stats=None, stream=None):
                                          ctypes.byref(state_struct(Uf)), ctypes.byref(prims_struct(Pf)), sp,
                                          coarse.ws_ptr, coarse.ws_bytes, fine.ws_ptr, fine.ws_bytes,
                                          _stream(stream)), "asterx_rk4_step_refined")
+
+
+def rk4_step_subcycled(coarse, fine, Uc, Pc, Uf, Pf, dt, stats=None, stream=None):
+    """One coarse RK4 step of size dt with the fine level subcycled (two steps of dt / 2; coarse and fine
+    Solvers, both prepared).  The scratch space is a torch allocation kept on the coarse Solver."""
+    import torch
+    need = int(lib().asterx_subcycle_workspace_size(ctypes.byref(coarse.b)))
+    if need == 0:
+        raise AsterxError("asterx_subcycle_workspace_size: invalid coarse block")
+    buf = getattr(coarse, "_subcycle_ws", None)
+    if buf is None or buf.numel() < need + 256:
+        buf = torch.empty(need + 256, dtype=torch.uint8, device=coarse.ws.device)
+        coarse._subcycle_ws = buf
+    ptr = ctypes.c_void_p(buf.data_ptr() + (-buf.data_ptr()) % 256)
+    sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
+    _check(lib().asterx_rk4_step_subcycled(ctypes.byref(coarse.p), ctypes.byref(coarse.b), ctypes.byref(fine.b),
+                                           float(dt), ctypes.byref(state_struct(Uc)), ctypes.byref(prims_struct(Pc)),
+                                           ctypes.byref(state_struct(Uf)), ctypes.byref(prims_struct(Pf)), sp,
+                                           coarse.ws_ptr, coarse.ws_bytes, fine.ws_ptr, fine.ws_bytes, ptr, need,
+                                           _stream(stream)), "asterx_rk4_step_subcycled")
 
 
 class Batch:

@@ -461,6 +461,115 @@ asterx_status asterx_rk4_step_refined(const asterx_params* p, const asterx_block
   return cuda_status(launch_restrict(ac.b, af.b, L, unc, unf, s));
 }
 
+// Subcycling (Sec. 3.10): the weights of the coarse slopes h k_i in the fine ghost data at stage s of fine
+// substep m.  The coarse step's continuous extension u(t_n + theta h) = u_n + h sum_i b_i(theta) k_i, with
+// b_1 = theta - 3/2 theta^2 + 2/3 theta^3, b_2 = b_3 = theta^2 - 2/3 theta^3, b_4 = -1/2 theta^2 + 2/3 theta^3,
+// gives u and its first three time derivatives at the substep start theta = m / 2.  The fine stage states of a
+// linear problem are u, u + (h_f/2) u', u + (h_f/2) u' + (h_f^2/4) u'' and u + h_f u' + (h_f^2/2) u'' +
+// (h_f^3/4) u'''; with h_f = h / 2 they weight the theta-derivatives by 1/4, 1/16 (stages 1, 2) and by
+// 1/2, 1/8, 1/32 (stage 3).
+static void subcycle_weights(int m, int s, double beta[4]) {
+  const double t = 0.5 * m;
+  const double b0[4] = {t - 1.5 * t * t + 2.0 * (t * t * t) / 3.0, t * t - 2.0 * (t * t * t) / 3.0,
+                        t * t - 2.0 * (t * t * t) / 3.0, -0.5 * t * t + 2.0 * (t * t * t) / 3.0};
+  const double b1[4] = {1.0 - 3.0 * t + 2.0 * t * t, 2.0 * t - 2.0 * t * t, 2.0 * t - 2.0 * t * t, -t + 2.0 * t * t};
+  const double b2[4] = {-3.0 + 4.0 * t, 2.0 - 4.0 * t, 2.0 - 4.0 * t, -1.0 + 4.0 * t};
+  const double b3[4] = {4.0, -4.0, -4.0, 4.0};
+  static const double w1[4] = {0.0, 0.25, 0.25, 0.5}, w2[4] = {0.0, 0.0, 1.0 / 16.0, 0.125},
+                      w3[4] = {0.0, 0.0, 0.0, 1.0 / 32.0};
+  for (int i = 0; i < 4; i++) beta[i] = b0[i] + w1[s] * b1[i] + w2[s] * b2[i] + w3[s] * b3[i];
+}
+
+static size_t subcycle_bytes_for(const asterx_block* coarse) {
+  const size_t fields = 5 * 9 + 5;  // U_n, Y_1, Y_2, Y_3, the interpolated state; its primitives
+  return (fields * (size_t)padded_V(coarse) * sizeof(double) + kAlign - 1) / kAlign * kAlign;
+}
+
+size_t asterx_subcycle_workspace_size(const asterx_block* coarse) {
+  if (!block_ok(coarse)) return 0;
+  return subcycle_bytes_for(coarse);
+}
+
+asterx_status asterx_rk4_step_subcycled(const asterx_params* p, const asterx_block* coarse,
+                                        const asterx_block* fine, double dt, asterx_state* Uc, asterx_prims* Pc,
+                                        asterx_state* Uf, asterx_prims* Pf, asterx_c2p_stats* stats, void* ws_c,
+                                        size_t ws_c_bytes, void* ws_f, size_t ws_f_bytes, void* ws_t,
+                                        size_t ws_t_bytes, asterx_stream stream) {
+  asterx_status st = common_checks(p, coarse, ws_c, ws_c_bytes);
+  if (st == ASTERX_OK) st = common_checks(p, fine, ws_f, ws_f_bytes);
+  if (st != ASTERX_OK) return st;
+  int L[3];
+  if (!nesting_ok(coarse, fine, L) || !finite_pos(dt)) return ASTERX_EINVAL;
+  if (!set_ok<asterx_state, 9>(Uc) || !set_ok<asterx_prims, 5>(Pc) || !set_ok<asterx_state, 9>(Uf) ||
+      !set_ok<asterx_prims, 5>(Pf))
+    return ASTERX_EINVAL;
+  if (stats && ((uintptr_t)stats % 8) != 0) return ASTERX_EINVAL;
+  if (!ws_t || ((uintptr_t)ws_t % kAlign) != 0) return ASTERX_EINVAL;
+  if (ws_t_bytes < subcycle_bytes_for(coarse)) return ASTERX_ENOMEM;
+  StageArgs ac = make_args(p, coarse, ws_c), af = make_args(p, fine, ws_f);
+  const long Vc = ac.b.V;
+  double* t = static_cast<double*>(ws_t);
+  F9 unc = f9(Uc), unf = f9(Uf), accc, accf, sbf[2], un, y[3], yt;
+  F5 pt;
+  for (int v = 0; v < 9; v++) {
+    accc.f[v] = ac.w.uacc + v * Vc;
+    accf.f[v] = af.w.uacc + v * af.b.V;
+    for (int q = 0; q < 2; q++) sbf[q].f[v] = af.w.ustage + (9 * q + v) * af.b.V;
+    un.f[v] = t + v * Vc;
+    for (int q = 0; q < 3; q++) y[q].f[v] = t + (9 * (q + 1) + v) * Vc;
+    yt.f[v] = t + (36 + v) * Vc;
+  }
+  for (int v = 0; v < 5; v++) pt.f[v] = t + (45 + v) * Vc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(stats);
+  const F5 pc = f5(Pc), pf = f5(Pf);
+  // the coarse step, keeping its stage states and its base (as the first stage's recovery leaves it)
+  for (int stage = 0; stage < 4; stage++) {
+    const F9& us = stage == 0 ? unc : y[stage - 1];
+    const F9& unext = stage == 3 ? unc : y[stage];
+    st = stage_impl(ac, stage, dt, unc, us, unext, accc, pc, nullptr, cnt, s);
+    if (st != ASTERX_OK) return st;
+    if (stage == 0)
+      for (int v = 0; v < 9; v++)
+        if (cudaMemcpyAsync(un.f[v], unc.f[v], Vc * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+          return ASTERX_ECUDA;
+  }
+  for (int v = 0; v < 5; v++)
+    if (cudaMemcpyAsync(pt.f[v], pc.f[v], Vc * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return ASTERX_ECUDA;
+  // the coarse cells whose primitives the prolongation reads (cells L - 3 .. L + n_fine/2 + 2 of the interior,
+  // one more on each side kept as margin); an axis where that range would leave the interior is recovered
+  // whole, so that the ghost fill (periodic wrap included) reads recovered cells only
+  int rlo[3], rhi[3];
+  for (int d = 0; d < 3; d++) {
+    rlo[d] = ac.b.g + L[d] - 4;
+    rhi[d] = ac.b.g + L[d] + fine->n[d] / 2 + 3;
+    if (rlo[d] < ac.b.g || rhi[d] > ac.b.g + ac.b.n[d] - 1) {
+      rlo[d] = ac.b.g;
+      rhi[d] = ac.b.g + ac.b.n[d] - 1;
+    }
+  }
+  // two fine steps of dt / 2, their ghost data from the coarse step by time interpolation
+  for (int m = 0; m < 2; m++) {
+    for (int stage = 0; stage < 4; stage++) {
+      double beta[4];
+      subcycle_weights(m, stage, beta);
+      cudaError_t e = launch_subcycle_combine(ac.b, un, y[0], y[1], y[2], unc, yt, beta, s);
+      if (e == cudaSuccess) e = launch_ghost_state(ac.b, yt, s);
+      if (e == cudaSuccess) e = launch_bfield(ac.b, ac.w, yt, s);
+      if (e == cudaSuccess) e = launch_c2p_range(ac, yt, pt, rlo, rhi, s);
+      if (e == cudaSuccess) e = launch_ghost_prims(ac.b, pt, s);
+      const F9& usf = stage == 0 ? unf : sbf[(stage - 1) % 2];
+      const F9& unxf = stage == 3 ? unf : sbf[stage % 2];
+      if (e == cudaSuccess) e = launch_prolong(ac.b, af.b, L, yt, pt, usf, pf, false, s);
+      if (e != cudaSuccess) return ASTERX_ECUDA;
+      st = stage_given_ghosts(af, stage, 0.5 * dt, unf, usf, unxf, accf, pf, cnt, s);
+      if (st != ASTERX_OK) return st;
+    }
+  }
+  return cuda_status(launch_restrict(ac.b, af.b, L, unc, unf, s));
+}
+
 asterx_status asterx_rk2_step(const asterx_params* p, const asterx_block* blk, double dt, asterx_state* U,
                               asterx_prims* P, signed char* flags, asterx_c2p_stats* stats, void* ws,
                               size_t ws_bytes, asterx_stream stream) {

@@ -49,6 +49,9 @@ cudaError_t launch_prim2con(const StageArgs& a, const F9& U, const F5& P, cudaSt
 // recovery on interior cells (needs launch_bfield first); flags/stats may be null
 cudaError_t launch_c2p(const StageArgs& a, const F9& U, const F5& P, signed char* flags,
                        unsigned long long* stats, cudaStream_t s);
+// the recovery on the interior cells lo..hi (inclusive) only, without flags or counters
+cudaError_t launch_c2p_range(const StageArgs& a, const F9& U, const F5& P, const int lo[3], const int hi[3],
+                             cudaStream_t s);
 
 // right-hand side (stage < 0) or RK4 stage combine (stage 0..3): faces, edges, vertices and cells.
 // Needs launch_bfield on U_s and primitives with ghosts.
@@ -127,6 +130,10 @@ cudaError_t launch_mask_owned9(const Blk& b, const F9& x, cudaStream_t s);
 // restriction of the 9 state fields to the coarse points under the fine interior
 cudaError_t launch_prolong(const Blk& C, const Blk& F, const int L[3], const F9& Uc, const F5& Pc, const F9& Uf,
                            const F5& Pf, bool all, cudaStream_t s);
+// subcycling: out = U_n + sum_i beta_i h k_i with the coarse slopes recovered from U_n, Y_1..Y_3 and U_1 (every
+// point of the padded block, 9 fields)
+cudaError_t launch_subcycle_combine(const Blk& b, const F9& un, const F9& y1, const F9& y2, const F9& y3,
+                                    const F9& u1, const F9& out, const double beta[4], cudaStream_t s);
 cudaError_t launch_restrict(const Blk& C, const Blk& F, const int L[3], const F9& Uc, const F9& Uf, cudaStream_t s);
 
 // face-kernel launch timing (measurement hook of the benchmark)

@@ -1,5 +1,6 @@
-// Two refinement levels (the fixed BoxInBox refinement of Sec. 3, with the prolongation the AMR magnetic-rotor
-// test of arXiv:2406.11669 describes): a fine block of half the spacing whose interior covers the coarse interior
+// Two refinement levels (the fixed BoxInBox refinement of Sec. 3.9, with the prolongation the AMR
+// magnetic-rotor test of arXiv:2406.11669, Sec. 4.4, describes; the time interpolation of subcycling, Sec. 3.10,
+// at the end): a fine block of half the spacing whose interior covers the coarse interior
 // cells L .. L + n_fine/2 - 1 along each axis.
 //
 // Prolongation to the fine block's ghost points (or to all its points), axis by axis in the order x, y, z: along
@@ -163,6 +164,35 @@ __global__ void __launch_bounds__(128) k_restrict(RefineArgs a) {
   }
 }
 
+// Subcycling (Sec. 3.10): the coarse state that feeds the fine ghost points at one fine stage, U_n + sum_i beta_i
+// h k_i over every point of the padded coarse block, with the coarse RK4 slopes recovered from the step's base
+// U_n, stage states Y_1..Y_3 and result U_1 (h k_1 = 2 (Y_1 - U_n), h k_2 = 2 (Y_2 - U_n), h k_3 = Y_3 - U_n,
+// h k_4 = 6 (U_1 - U_n) - h k_1 - 2 h k_2 - 2 h k_3); individually rounded operations in a fixed order.
+struct CombineArgs {
+  long V;
+  F9 un, y1, y2, y3, u1, out;
+  double beta[4];
+};
+
+__global__ void __launch_bounds__(256) k_subcycle_combine(CombineArgs a) {
+  const long total = 9 * a.V;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int v = (int)(t / a.V);
+    const long c = t - (long)v * a.V;
+    const double un = a.un.f[v][c];
+    const double g0 = __dmul_rn(2.0, __dsub_rn(a.y1.f[v][c], un));
+    const double g1 = __dmul_rn(2.0, __dsub_rn(a.y2.f[v][c], un));
+    const double g2 = __dsub_rn(a.y3.f[v][c], un);
+    const double g3 = __dsub_rn(__dsub_rn(__dsub_rn(__dmul_rn(6.0, __dsub_rn(a.u1.f[v][c], un)), g0),
+                                          __dmul_rn(2.0, g1)),
+                                __dmul_rn(2.0, g2));
+    const double sum = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(a.beta[0], g0), __dmul_rn(a.beta[1], g1)),
+                                           __dmul_rn(a.beta[2], g2)),
+                                 __dmul_rn(a.beta[3], g3));
+    a.out.f[v][c] = __dadd_rn(un, sum);
+  }
+}
+
 int refine_grid(long count) {
   long blocks = (count + 127) / 128;
   if (blocks > 152L * 64) blocks = 152L * 64;
@@ -183,6 +213,23 @@ cudaError_t launch_prolong(const Blk& C, const Blk& F, const int L[3], const F9&
   a.Pf = Pf;
   a.all = all;
   k_prolong<<<refine_grid(all ? F.V : shell_count(F)), 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_subcycle_combine(const Blk& b, const F9& un, const F9& y1, const F9& y2, const F9& y3,
+                                    const F9& u1, const F9& out, const double beta[4], cudaStream_t s) {
+  CombineArgs a;
+  a.V = b.V;
+  a.un = un;
+  a.y1 = y1;
+  a.y2 = y2;
+  a.y3 = y3;
+  a.u1 = u1;
+  a.out = out;
+  for (int i = 0; i < 4; i++) a.beta[i] = beta[i];
+  long blocks = (9 * b.V + 255) / 256;
+  if (blocks > 152L * 32) blocks = 152L * 32;
+  k_subcycle_combine<<<(int)blocks, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

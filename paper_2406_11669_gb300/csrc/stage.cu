@@ -333,12 +333,8 @@ struct C2PCount {
   unsigned long long noble, fb, atm, fail, it;
 };
 
-__device__ __forceinline__ C2PCount c2p_cell(const BlockRec& r, const C2PParams& cp, long t) {
+__device__ __forceinline__ C2PCount c2p_at(const BlockRec& r, const C2PParams& cp, long c) {
   const Blk& b = r.b;
-  Box box = make_box(b.g, b.g + b.n[0] - 1, b.g, b.g + b.n[1] - 1, b.g, b.g + b.n[2] - 1);
-  int i, j, k;
-  box.at(t, i, j, k);
-  const long c = lin(b, i, j, k);
   Geo m;
   load_geo_centre(b, r.w.cg, c, m);
   const F9& U = r.Us;
@@ -409,6 +405,14 @@ __device__ __forceinline__ C2PCount c2p_cell(const BlockRec& r, const C2PParams&
   return out;
 }
 
+__device__ __forceinline__ C2PCount c2p_cell(const BlockRec& r, const C2PParams& cp, long t) {
+  const Blk& b = r.b;
+  Box box = make_box(b.g, b.g + b.n[0] - 1, b.g, b.g + b.n[1] - 1, b.g, b.g + b.n[2] - 1);
+  int i, j, k;
+  box.at(t, i, j, k);
+  return c2p_at(r, cp, lin(b, i, j, k));
+}
+
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
@@ -437,6 +441,20 @@ __global__ void __launch_bounds__(128) k_c2p_single(BlockRec r, StageConsts k, l
     C2PCount c = {0, 0, 0, 0, 0};
     if (t < count) c = c2p_cell(r, k.cp, t);
     if (k.stats) add_counts(c, k.stats);
+  }
+}
+
+// the recovery on the cells lo..hi (inclusive, inside the interior) of one block, without counters
+struct CellRange {
+  int lo[3], hi[3];
+};
+
+__global__ void __launch_bounds__(128) k_c2p_range(BlockRec r, StageConsts k, CellRange q, long count) {
+  const Box box = make_box(q.lo[0], q.hi[0], q.lo[1], q.hi[1], q.lo[2], q.hi[2]);
+  GRID_LOOP(t, count) {
+    int i, j, kk;
+    box.at(t, i, j, kk);
+    c2p_at(r, k.cp, lin(r.b, i, j, kk));
   }
 }
 
@@ -1154,6 +1172,23 @@ cudaError_t launch_c2p(const StageArgs& a, const F9& U, const F5& P, signed char
   t.r.P = P;
   t.r.flags = flags;
   launch_c2p_kind(t, consts_of(a, -1, 0.0, stats), s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c2p_range(const StageArgs& a, const F9& U, const F5& P, const int lo[3], const int hi[3],
+                             cudaStream_t s) {
+  Single t = single_of(a.b, a.w);
+  t.r.Us = U;
+  t.r.P = P;
+  CellRange q;
+  long count = 1;
+  for (int d = 0; d < 3; d++) {
+    if (lo[d] < a.b.g || hi[d] > a.b.g + a.b.n[d] - 1 || hi[d] < lo[d]) return cudaErrorInvalidValue;
+    q.lo[d] = lo[d];
+    q.hi[d] = hi[d];
+    count *= hi[d] - lo[d] + 1;
+  }
+  k_c2p_range<<<grid_for(count, 128), 128, 0, s>>>(t.r, consts_of(a, -1, 0.0, nullptr), q, count);
   return cudaGetLastError();
 }
 

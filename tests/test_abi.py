@@ -227,3 +227,32 @@ def test_refinement_nesting_validation():
         rc = L.asterx_prolong(ctypes.byref(c), ctypes.byref(f), ctypes.byref(st), ctypes.byref(pr),
                               ctypes.byref(st), ctypes.byref(pr), 0, None)
         assert rc == A.ASTERX_EINVAL
+
+
+def test_subcycled_step_workspace_and_validation():
+    """asterx_rk4_step_subcycled: its scratch holds 50 coarse padded fields (U_n, Y_1..Y_3, the interpolated
+    state, its primitives); a short, missing or misaligned scratch, a bad nesting or dt <= 0 are refused on the
+    host before any launch."""
+    L = A.lib()
+    p = _params()
+    st = A.State(*([8] * 9))
+    pr = A.Prims(*([8] * 5))
+    c = A.block_struct((16, 16, 16), 3, (0.0, 0.0, 0.0), (0.1,) * 3, (1, 1, 1))
+    f = A.block_struct((8, 8, 8), 3, (0.3, 0.3, 0.3), (0.05,) * 3, (1, 1, 1))
+    need = L.asterx_subcycle_workspace_size(ctypes.byref(c))
+    assert need == (50 * 23 ** 3 * 8 + 255) // 256 * 256
+    bad_blk = A.block_struct((16, 16, 16), 3, (0, 0, 0), (0.0, 0.1, 0.1), (1, 1, 1))
+    assert L.asterx_subcycle_workspace_size(ctypes.byref(bad_blk)) == 0
+    wc, wf = A.workspace_size(c), A.workspace_size(f)
+
+    def call(fine=f, dt=0.01, wt=256, wt_bytes=need):
+        return L.asterx_rk4_step_subcycled(ctypes.byref(p), ctypes.byref(c), ctypes.byref(fine), ctypes.c_double(dt),
+                                           ctypes.byref(st), ctypes.byref(pr), ctypes.byref(st), ctypes.byref(pr),
+                                           None, ctypes.c_void_p(256), wc, ctypes.c_void_p(256), wf,
+                                           ctypes.c_void_p(wt) if wt is not None else None, wt_bytes, None)
+
+    assert call(wt_bytes=need - 8) == A.ASTERX_ENOMEM
+    assert call(wt=None) == A.ASTERX_EINVAL
+    assert call(wt=128) == A.ASTERX_EINVAL
+    assert call(dt=0.0) == A.ASTERX_EINVAL
+    assert call(fine=A.block_struct((8, 8, 8), 3, (0.35, 0.3, 0.3), (0.05,) * 3, (1, 1, 1))) == A.ASTERX_EINVAL

@@ -1,7 +1,9 @@
 """Two refinement levels on the CUDA path against the oracle: prolongation (to the ghost points and to every point
-of a nested fine block) and the two-level RK4 step (coarse stage, prolongation of its stage state to the fine
-ghosts, fine stage, restriction after the step).  Prolongation within 1e-13 of each field's magnitude (the
-same arithmetic, rounding aside); the two-level step within 1e-12 of each field group's magnitude."""
+of a nested fine block), the two-level RK4 step (coarse stage, prolongation of its stage state to the fine
+ghosts, fine stage, restriction after the step) and the subcycled two-level step (one coarse step, two fine
+steps of half its size with ghost data interpolated in time from the coarse step).  Prolongation within 1e-13
+of each field's magnitude (the same arithmetic, rounding aside); the two-level steps within 1e-12 of each field
+group's magnitude."""
 import numpy as np
 import pytest
 
@@ -87,3 +89,33 @@ def test_two_level_step_matches_oracle(recon):
     kids = gf[0][g:g + 2 * M[2], g:g + 2 * M[1], g:g + 2 * M[0]].reshape(M[2], 2, M[1], 2, M[0], 2).mean(axis=(1, 3, 5))
     par = gc[0][wc.g + L[2]:wc.g + L[2] + M[2], wc.g + L[1]:wc.g + L[1] + M[1], wc.g + L[0]:wc.g + L[0] + M[0]]
     assert np.abs(kids - par).max() <= 1e-14 * np.abs(par).max()
+
+
+@pytest.mark.parametrize("recon", [W.RECON_PPM, W.RECON_WENOZ])
+def test_subcycled_step_matches_oracle(recon):
+    """Two coarse steps of the subcycled two-level step (each: one coarse RK4 step, two fine ones of half the
+    size with time-interpolated ghost data) against the oracle, within the parity tolerance on both levels."""
+    need_gpu()
+    from paper_2406_11669_gb300 import asterx as A
+    wc, wf = levels(recon=recon)
+    Uc, Pc = O.initial_state(wc)
+    O.ghost_fill_state(wc, Uc)
+    Uf, Pf = O.initial_state(wf)
+    Mc, Mf = O.metric_array(wc), O.metric_array(wf)
+    dt = 2.0 * wf.dt
+    cc, cf = GpuCase(wc), GpuCase(wf)
+    Ucd, Pcd, Ufd, Pfd = cc.dev(Uc), cc.dev(Pc), cf.dev(Uf), cf.dev(Pf)
+    stats = cc.stats()
+    for _ in range(2):
+        A.rk4_step_subcycled(cc.solver, cf.solver, Ucd, Pcd, Ufd, Pfd, dt, stats=stats)
+    rc, rf = Uc.copy(), Uf.copy()
+    pc, pf = Pc.copy(), Pf.copy()
+    for _ in range(2):
+        rc, rf = O.subcycled_rk4_step(wc, Mc, rc, pc, wf, Mf, rf, pf, L, dt)
+    gc, gf = cc.host(Ucd), cf.host(Ufd)
+    for v in range(9):
+        e, s = rel_field_err(gc, rc, wc, v)
+        assert s == 0.0 or e <= 1e-12, ("coarse", v, e)
+        e, s = rel_field_err(gf, rf, wf, v)
+        assert s == 0.0 or e <= 1e-12, ("fine", v, e)
+    assert int(stats[3]) == 0

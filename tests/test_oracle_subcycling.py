@@ -1,6 +1,6 @@
 """Pins of the oracle's subcycled two-level step (the fine level takes two RK4 steps of half the coarse step; its
 ghost values at every fine stage come from the coarse step by time interpolation, with no buffer zones: the
-subcycling of Sec. 2.5, here in the stage-consistent form of Mongwane 2015).
+subcycling of Sec. 3.10, here in the stage-consistent form of Mongwane 2015).
 
 Closed forms: the continuous extension of RK4 reproduces u(0) = u_n and u(h) = u_{n+1}, integrates quadratic
 right-hand sides u' = f(t) exactly at every theta, and its derivative rows are the derivatives of its weights.
