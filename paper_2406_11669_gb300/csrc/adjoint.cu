@@ -37,10 +37,10 @@ __device__ __forceinline__ long alin(const Blk& b, int i, int j, int k) { return
 __device__ __forceinline__ long astr(const Blk& b, int d) { return d == 0 ? 1 : (d == 1 ? b.sy : b.sz); }
 
 __device__ __forceinline__ void decode(long t, int lo0, int e0, int lo1, int e1, int lo2, int& i, int& j, int& k) {
-  i = lo0 + (int)(t % e0);
-  const long r = t / e0;
-  j = lo1 + (int)(r % e1);
-  k = lo2 + (int)(r / e1);
+  unflatten3(t, (unsigned)e0, (unsigned)e1, i, j, k);
+  i += lo0;
+  j += lo1;
+  k += lo2;
 }
 
 // ----------------------------------------------------------------------------------------------------------
@@ -537,10 +537,8 @@ __device__ __forceinline__ void ka_ghost(Blk b, double* const* f, const int* cel
   const long st = astr(b, AX);
   const long count = slots * m1 * m2;
   ALOOP(t, count) {
-    const int q = (int)(t % slots);
-    const long r = t / slots;
-    const int q1 = (int)(r % m1);
-    const int q2 = (int)(r / m1);
+    int q, q1, q2;
+    unflatten3(t, (unsigned)slots, (unsigned)m1, q, q1, q2);
     const int i = (q < g) ? q : Nn - 2 * g + q;
     int pp[3];
     pp[AX] = 0;

@@ -78,9 +78,8 @@ __global__ void k_geom_centre(Blk b, CF16 m, double* __restrict__ cg) {
   const long ncell = (long)b.N[0] * b.N[1] * b.N[2];
   const double der4[4] = {1.0 / 24.0, -27.0 / 24.0, 27.0 / 24.0, -1.0 / 24.0};
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < ncell; t += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % b.N[0]);
-    const int j = (int)((t / b.N[0]) % b.N[1]);
-    const int k = (int)(t / ((long)b.N[0] * b.N[1]));
+    int i, j, k;
+    unflatten3(t, (unsigned)b.N[0], (unsigned)b.N[1], i, j, k);
     double wx[4], wy[4], wz[4];
     const int sx = lagrange_mid(i, b.N[0], wx);
     const int sy = lagrange_mid(j, b.N[1], wy);
@@ -163,9 +162,8 @@ __global__ void k_geom_xpass(Blk b, CF16 m, double* __restrict__ sc) {
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x) {
     // t runs over the vertex box; entry (i, j, k) serves both the (cell i, vertex j, vertex k) x-contraction
     // and the (vertex i, cell j, vertex k) y-contraction
-    const int i = (int)(t % (n0 + 1));
-    const int j = (int)((t / (n0 + 1)) % n1);
-    const int k = (int)(t / ((n0 + 1) * n1));
+    int i, j, k;
+    unflatten3(t, (unsigned)(n0 + 1), (unsigned)n1, i, j, k);
     const long c = i + b.sy * j + b.sz * k;
     if (i < b.N[0]) {
       double wx[4];
@@ -286,8 +284,8 @@ __global__ void k_geom_columns(Blk b, const double* __restrict__ sc, double* __r
   double* fgz = f < 10 ? fg + (long)(2 * NFG + (f == 0 ? FG_ALP : (f < 4 ? FG_BETA + f - 1 : FG_G + f - 4))) * b.V
                        : nullptr;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % b.N[0]);
-    const int j = (int)(t / b.N[0]);
+    int i, j;
+    unflatten2(t, (unsigned)b.N[0], i, j);
     if (f < 10) column<true>(b, sc, cg, fgz, f, i, j);
     else column<false>(b, sc, cg, nullptr, f, i, j);
   }
@@ -303,9 +301,8 @@ __global__ void k_geom_xyfaces(Blk b, const double* __restrict__ sc, double* __r
   const long n0 = b.N[0] + 1, n1 = b.N[1] + 1;
   const long count = n0 * n1 * b.N[2];
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % n0);
-    const int j = (int)((t / n0) % n1);
-    const int k = (int)(t / (n0 * n1));
+    int i, j, k;
+    unflatten3(t, (unsigned)n0, (unsigned)n1, i, j, k);
     double wz[4];
     const int sz = lagrange_mid(k, b.N[2], wz);
     const long c = i + b.sy * j + b.sz * k;
@@ -332,9 +329,8 @@ __global__ void k_geom_xyfaces(Blk b, const double* __restrict__ sc, double* __r
 __global__ void k_geom_complete(Blk b, double* __restrict__ cg, double* __restrict__ fg) {
   const long count = b.V;
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < count; c += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(c % b.sy);
-    const int j = (int)((c / b.sy) % (b.N[1] + 1));
-    const int k = (int)(c / b.sz);
+    int i, j, k;
+    unflatten3(c, (unsigned)b.sy, (unsigned)(b.N[1] + 1), i, j, k);
     double g6[6], gu[6], sqg;
     if (i < b.N[0] && j < b.N[1] && k < b.N[2]) {
       for (int a = 0; a < 6; a++) g6[a] = cg[(CG_G + a) * b.V + c];

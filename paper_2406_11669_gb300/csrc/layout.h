@@ -107,6 +107,25 @@ struct BlockRec {
   signed char* flags;
 };
 
+// Item indices of one block's kernels are below its padded volume, which block validation keeps under 4e9 <
+// 2^32, so they are split into coordinates with 32-bit unsigned division: the 64-bit form costs several times
+// more instructions per item, a large share of the light kernels.  t = i + e0 (j + e1 k).
+__host__ __device__ __forceinline__ void unflatten3(long t, unsigned e0, unsigned e1, int& i, int& j, int& k) {
+  const unsigned u = (unsigned)t;
+  const unsigned r = u / e0;
+  i = (int)(u - r * e0);
+  const unsigned q = r / e1;
+  j = (int)(r - q * e1);
+  k = (int)q;
+}
+// t = i + e0 j
+__host__ __device__ __forceinline__ void unflatten2(long t, unsigned e0, int& i, int& j) {
+  const unsigned u = (unsigned)t;
+  const unsigned r = u / e0;
+  i = (int)(u - r * e0);
+  j = (int)r;
+}
+
 constexpr int RCHUNK = 8;  // cells per work item of the chunked (sliding-stencil) PPM reconstruction
 
 // Item spaces of the kernels (per block).  The batched launches concatenate the blocks' item spaces in

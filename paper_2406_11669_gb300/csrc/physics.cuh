@@ -661,11 +661,11 @@ __host__ __device__ __forceinline__ void sources(const Geo& m, const double* __r
   T vl[3], Bl[3];
   lower(m.g, v, vl);
   lower(m.g, B, Bl);
-  const T W = 1.0 / sqrt(1.0 - (v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2]));
+  const T iW = sqrt(1.0 - (v[0] * vl[0] + v[1] * vl[1] + v[2] * vl[2]));  // 1 / W
+  const T W = 1.0 / iW;
   const T B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
   const T Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
   const double ia = 1.0 / m.alp;
-  const T iW = 1.0 / W;
   const T b2 = B2 * iW * iW + Bv * Bv;
   const T rhoh = rho + gfac * press;
   const T e = rhoh + b2;

@@ -144,9 +144,7 @@ __device__ __forceinline__ void parent_at(const ParentGrid& q, bool all, long t,
   int i, j, k;
   const long e0 = q.E[0], e1 = q.E[1];
   if (all) {
-    i = (int)(t % e0);
-    j = (int)((t / e0) % e1);
-    k = (int)(t / (e0 * e1));
+    unflatten3(t, (unsigned)e0, (unsigned)e1, i, j, k);
   } else {
     const int nz = q.ih[2] - q.il[2] + 1, ny = q.ih[1] - q.il[1] + 1, nx = q.ih[0] - q.il[0] + 1;
     const long zA = (long)(q.E[2] - nz) * e1 * e0;
@@ -207,7 +205,8 @@ __global__ void __launch_bounds__(128) k_restrict(RefineArgs a) {
   const long count = e0 * e1 * (m[2] + 1);
   const int clm[9] = {7, 7, 7, 7, 7, 1, 2, 4, 0};
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x) {
-    const int q[3] = {(int)(t % e0), (int)((t / e0) % e1), (int)(t / (e0 * e1))};
+    int q[3];
+    unflatten3(t, (unsigned)e0, (unsigned)e1, q[0], q[1], q[2]);
 #pragma unroll 1
     for (int v = 0; v < 9; v++) {
       int cl[3];

@@ -35,10 +35,10 @@ struct Box {
   int e[3];
   __host__ __device__ long count() const { return (long)e[0] * e[1] * e[2]; }
   __device__ __forceinline__ void at(long t, int& i, int& j, int& k) const {
-    i = lo[0] + (int)(t % e[0]);
-    const long r = t / e[0];
-    j = lo[1] + (int)(r % e[1]);
-    k = lo[2] + (int)(r / e[1]);
+    unflatten3(t, (unsigned)e[0], (unsigned)e[1], i, j, k);
+    i += lo[0];
+    j += lo[1];
+    k += lo[2];
   }
 };
 
@@ -130,10 +130,8 @@ __device__ __forceinline__ void ghost_point(const Blk& b, long t, double* const*
   const long m1 = b.N[A1] + 1;
   const int slots = 2 * g + 1;
   const long st = stride(b, AX);
-  const int q = (int)(t % slots);
-  const long r = t / slots;
-  const int q1 = (int)(r % m1);
-  const int q2 = (int)(r / m1);
+  int q, q1, q2;
+  unflatten3(t, (unsigned)slots, (unsigned)m1, q, q1, q2);
   const int i = (q < g) ? q : Nn - 2 * g + q;
   int p[3];
   p[AX] = 0;
@@ -285,6 +283,8 @@ struct BCentre {
     box.at(t, i, j, k);
     const long c = lin(b, i, j, k);
     const double sqg = r.w.cg[CG_SQG * b.V + c];
+    // divided, not multiplied by a reciprocal: the same rounding as the oracle's, so that the centre field (and
+    // the reconstruction of its transverse components) matches bit for bit given the same face field
     bc[c] = 0.5 * (bf[c] + bf[c + 1]) / sqg;
     bc[b.V + c] = 0.5 * (bf[b.V + c] + bf[b.V + c + b.sy]) / sqg;
     bc[2 * b.V + c] = 0.5 * (bf[2 * b.V + c] + bf[2 * b.V + c + b.sz]) / sqg;
@@ -347,6 +347,8 @@ __device__ __forceinline__ C2PCount c2p_at(const BlockRec& r, const C2PParams& c
   bool atm = !(Dt >= m.sqg * cp.rho_atm);
   int flag = 2;
   if (!atm) {
+    // divided, as the oracle does: on the rim of the torus workload the stage's right-hand side amplifies
+    // one-ulp differences of the recovered primitives to about 1e-12 of its magnitude
     const double D = Dt / m.sqg;
     const double S[3] = {U.f[1][c] / m.sqg, U.f[2][c] / m.sqg, U.f[3][c] / m.sqg};
     const double tau = U.f[4][c] / m.sqg;
@@ -548,10 +550,8 @@ struct ReconPPM {
     const Blk& b = r.b;
     const int lenD = b.n[D] + 2;
     int p[3];
-    p[TA] = (int)(t % b.N[TA]);
-    const long q = t / b.N[TA];
-    p[TB] = (int)(q % b.N[TB]);
-    const int ch = (int)(q / b.N[TB]);
+    int ch;
+    unflatten3(t, (unsigned)b.N[TA], (unsigned)b.N[TB], p[TA], p[TB], ch);
     const int i0 = b.g - 1 + ch * RCHUNK;
     const int i1 = min(b.g - 1 + lenD, i0 + RCHUNK);
     p[D] = i0;
@@ -747,10 +747,8 @@ struct ReconWENO {
     const Blk& b = r.b;
     const int lenD = b.n[D] + 2;
     int p[3];
-    p[TA] = (int)(t % b.N[TA]);
-    const long q = t / b.N[TA];
-    p[TB] = (int)(q % b.N[TB]);
-    const int ch = (int)(q / b.N[TB]);
+    int ch;
+    unflatten3(t, (unsigned)b.N[TA], (unsigned)b.N[TB], p[TA], p[TB], ch);
     const int i0 = b.g - 1 + ch * RCHUNK;
     const int i1 = min(b.g - 1 + lenD, i0 + RCHUNK);
     p[D] = i0;
@@ -801,10 +799,10 @@ struct EdgeRecon {
     const int ea = (TA == DF) ? b.n[DF] + 1 : b.n[DE];
     const int eb = (TB == DF) ? b.n[DF] + 1 : b.n[DE];
     int p[3];
-    p[TA] = b.g + (int)(t % ea);
-    const long q = t / ea;
-    p[TB] = b.g + (int)(q % eb);
-    const int ch = (int)(q / eb);
+    int ch;
+    unflatten3(t, (unsigned)ea, (unsigned)eb, p[TA], p[TB], ch);
+    p[TA] += b.g;
+    p[TB] += b.g;
     const int i0 = b.g - 1 + ch * RCHUNK;
     const int i1 = min(b.g + b.n[DR] + 1, i0 + RCHUNK);
     p[DR] = i0;

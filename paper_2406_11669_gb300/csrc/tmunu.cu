@@ -33,10 +33,11 @@ __global__ void __launch_bounds__(128) k_tmunu(TmunuArgs a) {
   const int e0 = b.n[0] + 1, e1 = b.n[1] + 1;
   const long count = (long)e0 * e1 * (b.n[2] + 1);
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x) {
-    const int i = b.g + (int)(t % e0);
-    const long r = t / e0;
-    const int j = b.g + (int)(r % e1);
-    const int k = b.g + (int)(r / e1);
+    int i, j, k;
+    unflatten3(t, (unsigned)e0, (unsigned)e1, i, j, k);
+    i += b.g;
+    j += b.g;
+    k += b.g;
     const long v = i + b.sy * j + b.sz * k;
     const long c0 = v - 1 - b.sy - b.sz;  // cell (i-1, j-1, k-1)
     const long off[8] = {0, 1, b.sy, b.sy + 1, b.sz, b.sz + 1, b.sz + b.sy, b.sz + b.sy + 1};
