@@ -540,13 +540,20 @@ asterx_status asterx_rk4_step_subcycled(const asterx_params* p, const asterx_blo
   // the coarse cells whose primitives the prolongation reads (cells L - 3 .. L + n_fine/2 + 2 of the interior,
   // one more on each side kept as margin); an axis where that range would leave the interior is recovered
   // whole, so that the ghost fill (periodic wrap included) reads recovered cells only
-  int rlo[3], rhi[3];
+  // the interpolated state itself is formed on those cells and two more points on each side (the face and
+  // centre field of the recovery reach one point beyond them, the prolongation of the potentials one more), or
+  // along the whole padded axis where the recovery covers the whole axis
+  int rlo[3], rhi[3], clo[3], chi[3];
   for (int d = 0; d < 3; d++) {
     rlo[d] = ac.b.g + L[d] - 4;
     rhi[d] = ac.b.g + L[d] + fine->n[d] / 2 + 3;
+    clo[d] = rlo[d] - 2;
+    chi[d] = rhi[d] + 2;
     if (rlo[d] < ac.b.g || rhi[d] > ac.b.g + ac.b.n[d] - 1) {
       rlo[d] = ac.b.g;
       rhi[d] = ac.b.g + ac.b.n[d] - 1;
+      clo[d] = 0;
+      chi[d] = ac.b.N[d];
     }
   }
   // two fine steps of dt / 2, their ghost data from the coarse step by time interpolation
@@ -554,7 +561,7 @@ asterx_status asterx_rk4_step_subcycled(const asterx_params* p, const asterx_blo
     for (int stage = 0; stage < 4; stage++) {
       double beta[4];
       subcycle_weights(m, stage, beta);
-      cudaError_t e = launch_subcycle_combine(ac.b, un, y[0], y[1], y[2], unc, yt, beta, s);
+      cudaError_t e = launch_subcycle_combine(ac.b, clo, chi, un, y[0], y[1], y[2], unc, yt, beta, s);
       if (e == cudaSuccess) e = launch_ghost_state(ac.b, yt, s);
       if (e == cudaSuccess) e = launch_bfield(ac.b, ac.w, yt, s);
       if (e == cudaSuccess) e = launch_c2p_range(ac, yt, pt, rlo, rhi, s);

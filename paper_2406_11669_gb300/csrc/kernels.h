@@ -130,10 +130,11 @@ cudaError_t launch_mask_owned9(const Blk& b, const F9& x, cudaStream_t s);
 // restriction of the 9 state fields to the coarse points under the fine interior
 cudaError_t launch_prolong(const Blk& C, const Blk& F, const int L[3], const F9& Uc, const F5& Pc, const F9& Uf,
                            const F5& Pf, bool all, cudaStream_t s);
-// subcycling: out = U_n + sum_i beta_i h k_i with the coarse slopes recovered from U_n, Y_1..Y_3 and U_1 (every
-// point of the padded block, 9 fields)
-cudaError_t launch_subcycle_combine(const Blk& b, const F9& un, const F9& y1, const F9& y2, const F9& y3,
-                                    const F9& u1, const F9& out, const double beta[4], cudaStream_t s);
+// subcycling: out = U_n + sum_i beta_i h k_i with the coarse slopes recovered from U_n, Y_1..Y_3 and U_1 (the
+// points lo..hi, inclusive, of the padded block, 9 fields)
+cudaError_t launch_subcycle_combine(const Blk& b, const int lo[3], const int hi[3], const F9& un, const F9& y1,
+                                    const F9& y2, const F9& y3, const F9& u1, const F9& out, const double beta[4],
+                                    cudaStream_t s);
 cudaError_t launch_restrict(const Blk& C, const Blk& F, const int L[3], const F9& Uc, const F9& Uf, cudaStream_t s);
 
 // face-kernel launch timing (measurement hook of the benchmark)

@@ -230,11 +230,12 @@ __global__ void __launch_bounds__(128) k_restrict(RefineArgs a) {
 }
 
 // Subcycling (Sec. 3.10): the coarse state that feeds the fine ghost points at one fine stage, U_n + sum_i beta_i
-// h k_i over every point of the padded coarse block, with the coarse RK4 slopes recovered from the step's base
+// h k_i over a box of points of the padded coarse block, with the coarse RK4 slopes recovered from the step's base
 // U_n, stage states Y_1..Y_3 and result U_1 (h k_1 = 2 (Y_1 - U_n), h k_2 = 2 (Y_2 - U_n), h k_3 = Y_3 - U_n,
 // h k_4 = 6 (U_1 - U_n) - h k_1 - 2 h k_2 - 2 h k_3); individually rounded operations in a fixed order.
 struct CombineArgs {
-  long V;
+  Blk b;
+  int lo[3], e[3];  // the points lo .. lo + e - 1 of the padded block
   F9 un, y1, y2, y3, u1, out;
   double beta[4];
 };
@@ -248,7 +249,11 @@ __global__ void __launch_bounds__(256) k_subcycle_combine(CombineArgs a) {
   const double* __restrict__ p3 = a.y3.f[v];
   const double* __restrict__ pu = a.u1.f[v];
   double* __restrict__ po = a.out.f[v];
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < a.V; c += (long)gridDim.x * blockDim.x) {
+  const long count = (long)a.e[0] * a.e[1] * a.e[2];
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count; t += (long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    unflatten3(t, (unsigned)a.e[0], (unsigned)a.e[1], i, j, k);
+    const long c = clin(a.b, a.lo[0] + i, a.lo[1] + j, a.lo[2] + k);
     const double un = pn[c];
     const double g0 = __dmul_rn(2.0, __dsub_rn(p1[c], un));
     const double g1 = __dmul_rn(2.0, __dsub_rn(p2[c], un));
@@ -287,10 +292,18 @@ cudaError_t launch_prolong(const Blk& C, const Blk& F, const int L[3], const F9&
   return cudaGetLastError();
 }
 
-cudaError_t launch_subcycle_combine(const Blk& b, const F9& un, const F9& y1, const F9& y2, const F9& y3,
-                                    const F9& u1, const F9& out, const double beta[4], cudaStream_t s) {
+cudaError_t launch_subcycle_combine(const Blk& b, const int lo[3], const int hi[3], const F9& un, const F9& y1,
+                                    const F9& y2, const F9& y3, const F9& u1, const F9& out, const double beta[4],
+                                    cudaStream_t s) {
   CombineArgs a;
-  a.V = b.V;
+  a.b = b;
+  long count = 1;
+  for (int d = 0; d < 3; d++) {
+    if (lo[d] < 0 || hi[d] > b.N[d] || hi[d] < lo[d]) return cudaErrorInvalidValue;
+    a.lo[d] = lo[d];
+    a.e[d] = hi[d] - lo[d] + 1;
+    count *= a.e[d];
+  }
   a.un = un;
   a.y1 = y1;
   a.y2 = y2;
@@ -298,7 +311,7 @@ cudaError_t launch_subcycle_combine(const Blk& b, const F9& un, const F9& y1, co
   a.u1 = u1;
   a.out = out;
   for (int i = 0; i < 4; i++) a.beta[i] = beta[i];
-  long blocks = (b.V + 255) / 256;
+  long blocks = (count + 255) / 256;
   if (blocks > 152L * 8) blocks = 152L * 8;
   k_subcycle_combine<<<dim3((unsigned)blocks, 9), 256, 0, s>>>(a);
   return cudaGetLastError();
