@@ -206,8 +206,9 @@ asterx_status asterx_rk4_step_refined(const asterx_params *p, const asterx_block
  * each fine stage the coarse state U_n + sum_i beta_i h k_i is formed from them (the coarse step's dense
  * output and its time derivatives at the substep start, combined as the fine stage states of a linear problem:
  * fourth-order accurate ghost data), ghost-filled, recovered (seeded by the previous such recovery, starting
- * from the primitives the coarse step leaves; only on the coarse cells the prolongation reads, or on whole
- * axes where those reach the boundary) and prolonged to the fine ghost points as asterx_prolong does.
+ * from the primitives the coarse step leaves) and prolonged to the fine ghost points as asterx_prolong does;
+ * it is formed and recovered only on the coarse cells the prolongation reads (with the margin the field
+ * needs), or along whole axes where those reach the boundary.
  * After both fine steps the coarse points under the fine interior are restricted.  ws_c / ws_f: the two
  * blocks' prepared workspaces; ws_t: scratch of asterx_subcycle_workspace_size(coarse) bytes (256-byte
  * aligned).  The Lorenz damping (xi_lorenz = 0) is 1.5 / dt on the coarse level and 3 / dt on the fine one.
