@@ -717,40 +717,48 @@ void launch_ghost_adjoint(const Blk& b, const AdjGhost& ag, int nf, cudaStream_t
   ka_ghost_k<0><<<agrid((long)slots * (b.N[1] + 1) * (b.N[2] + 1), T), T, 0, s>>>(b, g, nf);
 }
 
-// elementwise helpers of the RK4 adjoint
+// field q of a pointer set, chosen with constant indices (a runtime index into a kernel parameter struct makes
+// the compiler copy the whole struct to local memory in every thread)
+template <class FS, int NF>
+__device__ __forceinline__ double* field_at(const FS& x, int q) {
+  double* p = x.f[0];
+#pragma unroll
+  for (int r = 1; r < NF; r++)
+    if (q == r) p = x.f[r];
+  return p;
+}
+
+// elementwise helpers of the RK4 adjoint (grid y = the field)
 __global__ void ka_axpby9(Blk b, double alpha, F9 x, double beta, F9 y) {
-  ALOOP(t, 9 * b.V) {
-    const int f = (int)(t / b.V);
-    const long c = t - (long)f * b.V;
-    y.f[f][c] = alpha * x.f[f][c] + beta * y.f[f][c];
-  }
+  const double* __restrict__ xf = field_at<F9, 9>(x, blockIdx.y);
+  double* __restrict__ yf = field_at<F9, 9>(y, blockIdx.y);
+  ALOOP(c, b.V) yf[c] = alpha * xf[c] + beta * yf[c];
 }
 
 // Keeps the independent entries: g..g+n-1 along cell-like axes and along periodic axes (where the vertex index
 // g+n is the periodic image of g), g..g+n along vertex-like axes with copy BCs.
 __global__ void ka_mask_owned9(Blk b, F9 x) {
-  const int cl[9] = {7, 7, 7, 7, 7, 1, 2, 4, 0};
-  ALOOP(t, 9 * b.V) {
-    const int f = (int)(t / b.V);
-    const long c = t - (long)f * b.V;
+  const int f = blockIdx.y;
+  const int clf = f < 5 ? 7 : (f == 5 ? 1 : (f == 6 ? 2 : (f == 7 ? 4 : 0)));  // bit d: cell-like along d
+  int hi[3];
+  for (int d = 0; d < 3; d++) hi[d] = (((clf >> d) & 1) || b.bc[d] == 0) ? b.g + b.n[d] - 1 : b.g + b.n[d];
+  double* __restrict__ xf = field_at<F9, 9>(x, f);
+  ALOOP(c, b.V) {
     int p[3];
     decode(c, 0, b.N[0] + 1, 0, b.N[1] + 1, 0, p[0], p[1], p[2]);
     bool own = true;
-    for (int d = 0; d < 3; d++) {
-      const int hi = (((cl[f] >> d) & 1) || b.bc[d] == 0) ? b.g + b.n[d] - 1 : b.g + b.n[d];
-      own = own && p[d] >= b.g && p[d] <= hi;
-    }
-    if (!own) x.f[f][c] = 0.0;
+    for (int d = 0; d < 3; d++) own = own && p[d] >= b.g && p[d] <= hi[d];
+    if (!own) xf[c] = 0.0;
   }
 }
 
 cudaError_t launch_axpby9(const Blk& b, double alpha, const F9& x, double beta, const F9& y, cudaStream_t s) {
-  ka_axpby9<<<agrid(9 * b.V, 256), 256, 0, s>>>(b, alpha, x, beta, y);
+  ka_axpby9<<<dim3(agrid(b.V, 256), 9), 256, 0, s>>>(b, alpha, x, beta, y);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mask_owned9(const Blk& b, const F9& x, cudaStream_t s) {
-  ka_mask_owned9<<<agrid(9 * b.V, 256), 256, 0, s>>>(b, x);
+  ka_mask_owned9<<<dim3(agrid(b.V, 256), 9), 256, 0, s>>>(b, x);
   return cudaGetLastError();
 }
 
@@ -782,11 +790,9 @@ __global__ void ka_prim2con(Blk b, Ws w, AdjWs a, F9 lamU, F5 lamP, double gamma
   }
 }
 
-__global__ void ka_zero5(Blk b, F5 x) {
-  ALOOP(t, 5 * b.V) {
-    const int f = (int)(t / b.V);
-    x.f[f][t - (long)f * b.V] = 0.0;
-  }
+__global__ void ka_zero5(Blk b, F5 x) {  // grid y = the field
+  double* __restrict__ xf = field_at<F5, 5>(x, blockIdx.y);
+  ALOOP(c, b.V) xf[c] = 0.0;
 }
 
 // the workspace as the kept intermediates of one stage see it
@@ -808,7 +814,7 @@ cudaError_t launch_prim2con_adjoint(const StageArgs& sa, const AdjWs& a, const F
   if (e == cudaSuccess) e = launch_bfield(b, w, a.Y, s);
   if (e != cudaSuccess) return e;
   cudaMemsetAsync(a.lY_base, 0, (size_t)ADJ_ACC_FIELDS * b.V * sizeof(double), s);
-  ka_zero5<<<agrid(5 * b.V, 256), 256, 0, s>>>(b, lamP);
+  ka_zero5<<<dim3(agrid(b.V, 256), 5), 256, 0, s>>>(b, lamP);
   ka_prim2con<<<agrid((long)b.n[0] * b.n[1] * b.n[2], T), T, 0, s>>>(b, w, a, lamU, lamP, sa.gamma, sa.gfac);
   ka_bcentre<<<agrid(b.V, T), T, 0, s>>>(b, w, a);
   ka_curl<<<agrid(b.V, T), T, 0, s>>>(b, a);
