@@ -20,8 +20,6 @@ namespace asterx {
 
 namespace {
 
-__device__ __forceinline__ int floor_div2(int f) { return (f >= 0) ? f / 2 : -((-f + 1) / 2); }
-
 struct RefineArgs {
   Blk C, F;
   int L[3];
