@@ -149,8 +149,8 @@ class ClockSampler:
 
 def read_face_flops():
     """Algorithmic FP64 flops per face of the face-solve kernel, counted by the oracle's flop-counting scalar on
-    this workload (profiles/face_flops_config2_128.txt, written by oracle/count_face_flops.py)."""
-    path = os.path.join(ROOT, "profiles", "face_flops_config2_128.txt")
+    this workload (profiles/face_flops_balsara_schwarzschild_128.txt, written by oracle/count_face_flops.py)."""
+    path = os.path.join(ROOT, "profiles", "face_flops_balsara_schwarzschild_128.txt")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -163,7 +163,7 @@ def read_face_flops():
 
 
 def read_traffic():
-    path = os.path.join(ROOT, "profiles", "faces_config2_128_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "faces_balsara_schwarzschild_128_traffic.txt")
     if not os.path.exists(path):
         return None
     with open(path) as f:
@@ -227,11 +227,11 @@ def run_batched(args, dev, stream):
     from paper_2406_11669_gb300 import asterx as A
     from paper_2406_11669_gb300 import workloads as W
 
-    lay = W.config3_layout(nblocks=args.batch_blocks)
+    lay = W.star_layout(nblocks=args.batch_blocks)
     entries = []
     cells = 0
     for n, o in lay:
-        w = W.config3_block(n, o)
+        w = W.star_block(n, o)
         M, U, P = _upload_block(w, dev)
         entries.append((w.n, w.g, w.x0, w.dx, w.bc, M, U, P))
         cells += w.interior_cells
@@ -259,7 +259,7 @@ def run_batched(args, dev, stream):
     # one block of the same total interior volume, centred on the star
     side = int(round(cells ** (1.0 / 3.0)))
     h = 1.0 / 256.0
-    w = W.config3_block((side, side, side), (-0.5 * side * h,) * 3)
+    w = W.star_block((side, side, side), (-0.5 * side * h,) * 3)
     M, U, P = _upload_block(w, dev)
     s = A.Solver.for_workload(w, device=dev)
     s.prepare(M)
@@ -300,7 +300,7 @@ def run_tiled(args, dev, stream, single_ms):
     from paper_2406_11669_gb300 import asterx as A
     from paper_2406_11669_gb300 import workloads as W
 
-    w = W.config2(n=(args.n,) * 3)
+    w = W.balsara_schwarzschild(n=(args.n,) * 3)
     M, U, P = _upload_block(w, dev)
     out = {}
     for k in (2, 4):
@@ -356,7 +356,7 @@ def run_refined(args, dev, stream, single_ms):
     from paper_2406_11669_gb300 import asterx as A
     from paper_2406_11669_gb300 import workloads as W
 
-    w = W.config2(n=(args.n,) * 3)
+    w = W.balsara_schwarzschild(n=(args.n,) * 3)
     M, U, P = _upload_block(w, dev)
     sc = A.Solver.for_workload(w, device=dev)
     sc.prepare(M)
@@ -430,7 +430,7 @@ def run_adjoint(args, dev, stream):
     from paper_2406_11669_gb300 import asterx as A
     from paper_2406_11669_gb300 import workloads as W
 
-    w = W.config4(n=(args.adjoint_n,) * 3)
+    w = W.weak_field_modes(n=(args.adjoint_n,) * 3)
     M, U, P = _upload_block(w, dev)
     s = A.Solver.for_workload(w, device=dev)
     s.prepare(M)
@@ -466,7 +466,7 @@ def run_adjoint(args, dev, stream):
         torch.cuda.profiler.stop()
     # whole 10-step gradient
     nsteps = 10
-    T = torch.from_numpy(W.config4_target(w)).to(dev)
+    T = torch.from_numpy(W.weak_field_target(w)).to(dev)
     ckpt = [torch.empty_like(U) for _ in range(nsteps)]
     lamP = torch.zeros_like(P)
 
@@ -594,7 +594,7 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2406_11669_gb300 import workloads as W
-    w_full = W.config2(n=(args.n,) * 3)
+    w_full = W.balsara_schwarzschild(n=(args.n,) * 3)
     w = slab_workload(w_full, 8, 8)
     sec_w = cpu_oracle_steps(w, max(args.warmup, 0)) if args.warmup > 0 else 0.0
     del sec_w
@@ -626,7 +626,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w = W.config2(n=(args.n,) * 3)
+    w = W.balsara_schwarzschild(n=(args.n,) * 3)
     s = A.Solver.for_workload(w, device=dev)
     M = torch.from_numpy(np.ascontiguousarray(np.stack([w.metric[k] for k in W.METRIC_NAMES]))).to(dev)
     P0 = np.ascontiguousarray(np.stack([w.prims[k] for k in W.PRIM_NAMES]))

@@ -1,4 +1,4 @@
-"""Writes profiles/face_flops_config2_128.txt: the algorithmic FP64 flops per face of the face solve for the
+"""Writes profiles/face_flops_balsara_schwarzschild_128.txt: the algorithmic FP64 flops per face of the face solve for the
 benchmark workload (128^3 WENO-Z block of Balsara-1 data in the Schwarzschild slice), counted by the oracle's
 flop-counting scalar (+, -, *, /, sqrt each one flop) on the central 128x16x16 slab of the same data (the data
 are uniform in y and z, so the slab has the block's per-face mix).  Calls only the oracle.
@@ -16,7 +16,7 @@ from paper_2406_11669_gb300 import workloads as W  # noqa: E402
 
 
 def main():
-    full = W.config2(n=(128, 128, 128))
+    full = W.balsara_schwarzschild(n=(128, 128, 128))
     w = W.sub_block(full, (0, 56, 56), (128, 16, 16), name="slab")
     U, P = O.initial_state(w)
     M = O.metric_array(w)
@@ -29,7 +29,7 @@ def main():
         tot = c["add"] + c["mul"] + c["div"] + c["sqrt"]
         rows.append((d, c, tot / c["faces"]))
     mean = sum(r[2] for r in rows) / 3.0
-    out = os.path.join(ROOT, "profiles", "face_flops_config2_128.txt")
+    out = os.path.join(ROOT, "profiles", "face_flops_balsara_schwarzschild_128.txt")
     with open(out, "w") as f:
         f.write("# Algorithmic FP64 flops per face of the face solve (k_single<Faces<D>>), counted with the oracle's\n")
         f.write("# flop-counting scalar on the central 128x16x16 slab of the 128^3 WENO-Z Schwarzschild workload\n")

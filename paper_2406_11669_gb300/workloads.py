@@ -14,11 +14,12 @@ cell centre (i+1/2, j+1/2, k+1/2), x-face (i, j+1/2, k+1/2), x-edge (i+1/2, j, k
 Vertex i sits at x0 + (i - g) dx.
 
 The five workloads follow the paper's tests and benchmarks (Sec. 4, Table 1, Sec. 5 "Setup A"):
-  config1  32^3 periodic, flat metric, minmod, smooth Fourier-mode data
-  config2  128^3, Schwarzschild (isotropic), WENO-Z, Balsara-1 states split along x (Table 1)
-  config3  512 uneven blocks, Schwarzschild M=0.2, PPM, magnetised-star profile (Eq. magtovAvec with n_s=1)
-  config4  64^3 periodic, weak-field lapse, PPM, smooth data (adjoint workload, seeded target)
-  config5  256^3, Schwarzschild, WENO-Z, rotating torus plus an axial jet with W up to 7
+  flat_modes             32^3 periodic, flat metric, minmod, smooth Fourier-mode data
+  balsara_schwarzschild  128^3, Schwarzschild (isotropic), WENO-Z, Balsara-1 states split along x (Table 1)
+  star_layout/star_block 512 uneven blocks, Schwarzschild M=0.2, PPM, magnetised-star profile (Eq. magtovAvec,
+                         n_s = 1)
+  weak_field_modes       64^3 periodic, weak-field lapse, PPM, smooth data (adjoint workload, seeded target)
+  torus_jet              256^3, Schwarzschild, WENO-Z, rotating torus plus an axial jet with W up to 7
 Constants the paper leaves open are fixed here and listed in the design notes of the repository.
 """
 from __future__ import annotations
@@ -249,21 +250,21 @@ def _smooth_periodic(name, n, seed, gamma, recon, alp_amp, vmax, Bmax, rho_amp, 
                     _full(shape, 0.0), metric)
 
 
-def config1(n=(32, 32, 32), seed=101) -> Workload:
+def flat_modes(n=(32, 32, 32), seed=101) -> Workload:
     """32^3 periodic on [0,1]^3, flat metric, Gamma=4/3, minmod; rho = 1 + 0.1 sin 2 pi x, p = 1;
     |v| <= 0.1 from 4 transverse Fourier modes, |B| ~ 0.1 from 4 potential modes; dt = dx/4."""
-    return _smooth_periodic("config1_32cube_periodic_flat_minmod", n, seed, 4.0 / 3.0, RECON_MINMOD,
+    return _smooth_periodic("flat_modes_32cube_periodic_minmod", n, seed, 4.0 / 3.0, RECON_MINMOD,
                             0.0, 0.1, 0.1, 0.1, 0)
 
 
-def config4(n=(64, 64, 64), seed=104) -> Workload:
+def weak_field_modes(n=(64, 64, 64), seed=104) -> Workload:
     """64^3 periodic, lapse 1 - 0.01 sin 2 pi x, gamma = I, Gamma = 4/3, PPM; rho = 1 + 0.05 * 3 modes, p = 1,
     |v| <= 0.2, |B| ~ 0.2; dt = dx/4 (the adjoint workload: 10 RK4 steps)."""
-    return _smooth_periodic("config4_64cube_periodic_weakfield_ppm", n, seed, 4.0 / 3.0, RECON_PPM,
+    return _smooth_periodic("weak_field_modes_64cube_periodic_ppm", n, seed, 4.0 / 3.0, RECON_PPM,
                             0.01, 0.2, 0.2, 0.05, 3)
 
 
-def config4_target(w: Workload, seed=1104) -> np.ndarray:
+def weak_field_target(w: Workload, seed=1104) -> np.ndarray:
     """Seeded target density field T = 1 + 0.05 * 3 modes at cell centres for the adjoint loss."""
     rng = Rng(seed)
     Xc, Yc, Zc = positions(w.n, w.g, w.x0, w.dx, CELL)
@@ -403,7 +404,7 @@ def smooth_periodic_1d(n, seed=110, recon=RECON_PPM) -> Workload:
                     _full(shape, 0.0), metric)
 
 
-def config2(n=(128, 128, 128), seed=102) -> Workload:
+def balsara_schwarzschild(n=(128, 128, 128), seed=102) -> Workload:
     """128^3 on [-1/2,1/2]^3, copy BCs, Gamma = 5/3, WENO-Z.  Table 1 test-1 states split at x = 0:
     left rho=1, p=1, right rho=0.125, p=0.1, v=0; densitised field B~x = 0.5, B~y = +1 (left) / -1 (right)
     from A_z = |x| + y/2.  Frozen isotropic Schwarzschild metric, M = 0.1, centred at (-1, 0, 0)."""
@@ -425,7 +426,7 @@ def config2(n=(128, 128, 128), seed=102) -> Workload:
     params = default_params(gamma=5.0 / 3.0, gamma_atm=5.0 / 3.0, rho_atm=1e-7, K_atm=1.0, recon=RECON_WENOZ)
     prims = dict(rho=rho, press=press, velx=zero.copy(), vely=zero.copy(), velz=zero.copy())
     A = dict(Ax=zero.copy(), Ay=zero.copy(), Az=Az)
-    return Workload("config2_128cube_schwarzschild_wenoz_riemann", tuple(n), g, x0, dx, (BC_COPY,) * 3, params,
+    return Workload("balsara_schwarzschild_128cube_wenoz", tuple(n), g, x0, dx, (BC_COPY,) * 3, params,
                     0.25 * min(dx), prims, A, zero.copy(), metric)
 
 
@@ -473,7 +474,7 @@ def _star(R=0.4, rho_c=1e-3, rho_floor=1e-10, K=100.0):
     return rho, press, grad_press
 
 
-def config3_block(n, origin, dx=1.0 / 256.0, name="config3_block") -> Workload:
+def star_block(n, origin, dx=1.0 / 256.0, name="star_block") -> Workload:
     """One block of the uneven batch: magnetised star rho = max(1e-3 (1 - r^2/0.4^2), 1e-10), p = 100 rho^2,
     v = 0, poloidal A_phi with p_cut = 0.04 p_max and max b^2/2p ~ 1e-2; Schwarzschild M = 0.2 at (-1,0,0);
     Gamma = 2, atmosphere K = 100, Gamma_atm = 2, rho_atm = 1e-10; copy BCs, PPM."""
@@ -488,7 +489,7 @@ def config3_block(n, origin, dx=1.0 / 256.0, name="config3_block") -> Workload:
     press = np.broadcast_to(press_fn(Xc, Yc, Zc), shape).copy()
     p_max = 100.0 * 1e-3 ** 2
     # A_b must not depend on the block: it is fixed once on a reference grid through the star's centre.
-    A, _ = _poloidal_potential_fixed(n, g, x0, dxs, shape, press_fn, 0.04 * p_max, _config3_Ab())
+    A, _ = _poloidal_potential_fixed(n, g, x0, dxs, shape, press_fn, 0.04 * p_max, _star_Ab())
     Xv, Yv, Zv = positions(n, g, x0, dxs, VERTEX)
     metric = schwarzschild_isotropic(Xv, Yv, Zv, 0.2, (-1.0, 0.0, 0.0), shape)
     zero = _full(shape, 0.0)
@@ -501,7 +502,7 @@ def config3_block(n, origin, dx=1.0 / 256.0, name="config3_block") -> Workload:
 _AB_CACHE = {}
 
 
-def _config3_Ab():
+def _star_Ab():
     if "c3" not in _AB_CACHE:
         n = (64, 64, 64)
         g = 3
@@ -528,7 +529,7 @@ def _poloidal_potential_fixed(n, g, x0, dx, shape, press_fn, p_cut, Ab):
     return A, Ab
 
 
-def config3_layout(nblocks=512, seed=103, sizes=(16, 24, 32, 48, 64), dx=1.0 / 256.0):
+def star_layout(nblocks=512, seed=103, sizes=(16, 24, 32, 48, 64), dx=1.0 / 256.0):
     """Seeded block table of the uneven batch: per axis n from `sizes`, origins uniform on the dx lattice such
     that each block lies inside [-1/2, 1/2]^3.  Returns a list of (n, origin)."""
     rng = Rng(seed)
@@ -544,7 +545,7 @@ def config3_layout(nblocks=512, seed=103, sizes=(16, 24, 32, 48, 64), dx=1.0 / 2
     return out
 
 
-def config5(n=(256, 256, 256), seed=105) -> Workload:
+def torus_jet(n=(256, 256, 256), seed=105) -> Workload:
     """256^3 on [-1/2,1/2]^3, copy BCs, Gamma = 4/3, WENO-Z.  Torus rho = max(1e-2 exp(-(varpi-0.3)^2/0.01
     - z^2/0.01), 1e-10), p = 0.1 rho^(4/3), rigid rotation Omega = 0.5, plus an axial jet (varpi < 0.1) whose
     Lorentz factor W = 1 + 6 exp(-(varpi/0.04)^2)(0.75 + 0.25 cos(2 pi z + phi_seed)) reaches 7.  Poloidal
@@ -597,13 +598,13 @@ def config5(n=(256, 256, 256), seed=105) -> Workload:
     metric = schwarzschild_isotropic(Xv, Yv, Zv, M, centre, shape)
     params = default_params(gamma=4.0 / 3.0, gamma_atm=4.0 / 3.0, rho_atm=1e-10, K_atm=0.1, recon=RECON_WENOZ)
     prims = dict(rho=rho, press=press, velx=velx, vely=vely, velz=velz)
-    return Workload("config5_256cube_schwarzschild_wenoz_torus_jet", tuple(n), g, x0, dx, (BC_COPY,) * 3, params,
+    return Workload("torus_jet_256cube_schwarzschild_wenoz", tuple(n), g, x0, dx, (BC_COPY,) * 3, params,
                     0.25 * min(dx), prims, A, _full(shape, 0.0), metric)
 
 
 def weak_field_wave(nx, recon=RECON_PPM, amp=1e-3, cfl=0.25) -> Workload:
-    """A smooth small-amplitude wave on the config-4 weak-field lapse alpha = 1 - 0.01 sin 2 pi x (gamma = I,
-    beta = K = 0), periodic on [0, 1] along x, one cell across y and z: rho = 1 + amp sin 2 pi x,
+    """A smooth small-amplitude wave on the adjoint workload's weak-field lapse alpha = 1 - 0.01 sin 2 pi x
+    (gamma = I, beta = K = 0), periodic on [0, 1] along x, one cell across y and z: rho = 1 + amp sin 2 pi x,
     p = 1 + amp cos 2 pi x, v^x = amp sin 2 pi x, B = 0, Gamma = 4/3; dt = cfl dx (for self-convergence)."""
     n = (int(nx), 1, 1)
     g = 3

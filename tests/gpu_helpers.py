@@ -87,13 +87,13 @@ def stats_dict(t):
 
 def small_workloads():
     """Small blocks of every workload kind, with ragged extents (not multiples of 8, 16 or 32)."""
-    c3 = W.config3_block((16, 20, 12), (0.3515625, -0.0390625, -0.0234375), name="config3_block_surface")
+    c3 = W.star_block((16, 20, 12), (0.3515625, -0.0390625, -0.0234375), name="star_block_surface")
     return {
-        "config1": W.config1(n=(20, 13, 9)),
-        "config2": W.config2(n=(26, 10, 9)),
-        "config3": c3,
-        "config4": W.config4(n=(12, 10, 11)),
-        "config5": W.config5(n=(22, 21, 18)),
+        "flat_modes": W.flat_modes(n=(20, 13, 9)),
+        "balsara_schwarzschild": W.balsara_schwarzschild(n=(26, 10, 9)),
+        "star": c3,
+        "weak_field_modes": W.weak_field_modes(n=(12, 10, 11)),
+        "torus_jet": W.torus_jet(n=(22, 21, 18)),
         "alfven1d": W.alfven_wave(16, recon=W.RECON_PPM),
     }
 

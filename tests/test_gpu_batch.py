@@ -18,8 +18,8 @@ SIZES = (8, 12, 16, 20)
 
 
 def _blocks(nb=7, seed=303):
-    lay = W.config3_layout(nblocks=nb, seed=seed, sizes=SIZES, dx=1.0 / 64.0)
-    return [W.config3_block(n, o, dx=1.0 / 64.0) for n, o in lay]
+    lay = W.star_layout(nblocks=nb, seed=seed, sizes=SIZES, dx=1.0 / 64.0)
+    return [W.star_block(n, o, dx=1.0 / 64.0) for n, o in lay]
 
 
 def _dev(x):

@@ -24,7 +24,7 @@ def need_gpu():
 
 def _uniform_with_ripple(bx, bc, n=(10, 9, 8), ripple=1e-3):
     """rho = 1, p = 1 (Gamma = 4/3), B = (bx, 0, 0) from A_z = bx y, a small velocity ripple; flat metric."""
-    w = W.config1(n=n)
+    w = W.flat_modes(n=n)
     w.bc = (bc,) * 3
     X, Y, Z = W.positions(w.n, w.g, w.x0, w.dx, W.CELL)
     shape = w.shape

@@ -74,9 +74,9 @@ def check_fields(gpu_full, ref_subs, w, samples, n, margin, tol, fields=range(9)
 
 SAMPLES = {
     # the 128^3 benchmark block: corner, across the Riemann interface at x = 0, an upper corner
-    "config2": (W.config2, [(0, 0, 0), (58, 40, 70), (116, 116, 0), (60, 116, 116)]),
+    "balsara_schwarzschild": (W.balsara_schwarzschild, [(0, 0, 0), (58, 40, 70), (116, 116, 0), (60, 116, 116)]),
     # the 256^3 torus with its jet: atmosphere corner, jet axis, torus ring, mixed
-    "config5": (W.config5, [(0, 0, 0), (122, 122, 60), (200, 122, 122), (170, 60, 200)]),
+    "torus_jet": (W.torus_jet, [(0, 0, 0), (122, 122, 60), (200, 122, 122), (170, 60, 200)]),
 }
 
 
@@ -157,7 +157,7 @@ def test_rk_stage_full_size():
     """One RK stage (stage 0: ghost fill, recovery, right-hand side, combine) over the whole 128^3 block against
     the oracle's stage on 22^3 sub-blocks (inner 8^3: influence reaches at most 6 cells per stage)."""
     need_gpu()
-    make, samples = SAMPLES["config2"]
+    make, samples = SAMPLES["balsara_schwarzschild"]
     w = make()
     U, P, M = potentials_and_prims(w)
     case = GpuCase(w)
@@ -190,10 +190,10 @@ def test_batched_step_full_size():
     may differ by a few sqrt(gamma) rho_atm (the allowance of the small-block RK4 test)."""
     need_gpu()
     from paper_2406_11669_gb300 import asterx as A
-    lay = W.config3_layout(nblocks=512)
+    lay = W.star_layout(nblocks=512)
     entries = []
     for nn, o in lay:
-        w = W.config3_block(nn, o)
+        w = W.star_block(nn, o)
         U, P, M = potentials_and_prims(w)
         Ud, Pd, Md = (torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (U, P, M))
         entries.append((w.n, w.g, w.x0, w.dx, w.bc, Md, Ud, Pd))
@@ -206,7 +206,7 @@ def test_batched_step_full_size():
     sizes = [int(np.prod(nn)) for nn, _ in lay]
     picks = [int(np.argmin(sizes)), len(lay) // 2, len(lay) - 1]
     for i in picks:
-        w = W.config3_block(*lay[i])
+        w = W.star_block(*lay[i])
         Mo = O.metric_array(w)
         Uo, Po = O.initial_state(w)
         O.ghost_fill_state(w, Uo)

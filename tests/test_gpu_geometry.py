@@ -83,12 +83,12 @@ def check_exact(case, M):
         assert np.array_equal(fg[d][FG_WIDTH][fsl], fr[0][fsl] * np.sqrt(fr[10 + SYM[d][d]][fsl]))
 
 
-@pytest.mark.parametrize("name", ["smooth_general", "config3", "config2"])
+@pytest.mark.parametrize("name", ["smooth_general", "star", "balsara_schwarzschild"])
 def test_prepared_geometry_equals_the_oracle_exactly(name):
     need_gpu()
     w = {"smooth_general": W.smooth_general(n=(9, 7, 11)),
-         "config3": W.config3_block((16, 20, 12), (0.3515625, -0.0390625, -0.0234375), name="config3_block"),
-         "config2": W.config2(n=(26, 10, 9))}[name]
+         "star": W.star_block((16, 20, 12), (0.3515625, -0.0390625, -0.0234375), name="star_block"),
+         "balsara_schwarzschild": W.balsara_schwarzschild(n=(26, 10, 9))}[name]
     case = GpuCase(w)
     check_exact(case, case.M)
 

@@ -175,7 +175,7 @@ def test_rk4_step_parity(case):
 
 def test_algebraic_gauge_parity():
     need_gpu()
-    w = WORKLOADS["config1"]
+    w = WORKLOADS["flat_modes"]
     params = dict(w.params, gauge=1)
     case = GpuCase(w, params)
     U, P = O.initial_state(w)
@@ -194,7 +194,7 @@ def test_rk4_step_graph_capture_replays_identically():
     """asterx_rk4_step only enqueues kernels (no synchronisation, no allocation), so a caller can capture it in
     a CUDA graph; replaying the graph gives the same result as the direct call."""
     need_gpu()
-    w = WORKLOADS["config1"]
+    w = WORKLOADS["flat_modes"]
     case = GpuCase(w)
     U, P = O.initial_state(w)
     O.ghost_fill_state(w, U)
@@ -220,7 +220,7 @@ def test_rk4_step_host_buffers_equal_the_device_step(stacked):
     """asterx_rk4_step_host (pinned host buffers in, the step, host buffers out) ends bit-identical to
     asterx_rk4_step on device arrays; stacked host arrays travel as one copy per array, separate ones per field."""
     need_gpu()
-    w = WORKLOADS["config3"]
+    w = WORKLOADS["star"]
     case = GpuCase(w)
     U, P = O.initial_state(w)
     O.ghost_fill_state(w, U)

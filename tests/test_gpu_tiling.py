@@ -35,10 +35,10 @@ def owned(w, v):
 def domain(kind):
     n = tuple(c[-1] for c in CUTS)
     if kind == "periodic_flat":
-        return W.config1(n=n)
+        return W.flat_modes(n=n)
     if kind == "copy_curved":  # every field and the whole metric vary smoothly
         return W.smooth_general(n=n, recon=W.RECON_WENOZ, bc=W.BC_COPY)
-    w = W.config2(n=n)
+    w = W.balsara_schwarzschild(n=n)
     w.metric = W.flat_metric(w.shape)
     return w
 

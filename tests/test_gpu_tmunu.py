@@ -63,7 +63,7 @@ def test_tmunu_of_a_stage_state():
     """After asterx_rk_stage the stage state U_s and the primitives have their ghosts filled, so T_{mu nu} of the
     stage state follows directly (the coupling order of a spacetime solver's right-hand side)."""
     need_gpu()
-    w = W.config3_block((14, 12, 16), (0.3515625, -0.0390625, -0.0234375), name="config3_block_surface")
+    w = W.star_block((14, 12, 16), (0.3515625, -0.0390625, -0.0234375), name="star_block_surface")
     U, P = O.initial_state(w)
     O.ghost_fill_state(w, U)
     M = O.metric_array(w)
@@ -83,7 +83,7 @@ def test_tmunu_full_size():
     from the same arrays: T at a vertex reads cells within one cell and the metric within two, so the sub-block's
     vertices one layer in from its cut agree."""
     need_gpu()
-    w = W.config2()
+    w = W.balsara_schwarzschild()
     U = np.zeros((9,) + w.shape)
     U[5], U[6], U[7], U[8] = w.A["Ax"], w.A["Ay"], w.A["Az"], w.Psi
     P, M = O.prims_array(w), O.metric_array(w)
@@ -122,7 +122,7 @@ def stage_metrics(w):
     return out
 
 
-@pytest.mark.parametrize("name", ["config3", "smooth_general", "config2"])
+@pytest.mark.parametrize("name", ["star", "smooth_general", "balsara_schwarzschild"])
 def test_rk4_step_metrics_matches_oracle(name):
     need_gpu()
     w = CASES[name]
@@ -145,7 +145,7 @@ def test_rk4_step_metrics_matches_oracle(name):
 
 def test_rk4_step_metrics_with_one_metric_is_the_frozen_step():
     need_gpu()
-    w = CASES["config4"]
+    w = CASES["weak_field_modes"]
     U, P = O.initial_state(w)
     O.ghost_fill_state(w, U)
     case = GpuCase(w)

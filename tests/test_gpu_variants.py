@@ -18,7 +18,7 @@ SWITCHES = {"lxf_uct": (W.FLUX_LXF, W.EFIELD_UCT), "hlle_fct": (W.FLUX_HLLE, W.E
             "lxf_fct": (W.FLUX_LXF, W.EFIELD_FCT)}
 WORKLOADS = dict(small_workloads())
 WORKLOADS["smooth_general"] = W.smooth_general(n=(9, 8, 7))
-NAMES = ["config1", "config2", "config3", "config5", "smooth_general"]
+NAMES = ["flat_modes", "balsara_schwarzschild", "star", "torus_jet", "smooth_general"]
 
 
 def need_gpu():
@@ -58,7 +58,7 @@ def allowance(w, M, st):
 
 
 @pytest.mark.parametrize("sw", list(SWITCHES))
-@pytest.mark.parametrize("name", ["config1", "config3", "smooth_general"])
+@pytest.mark.parametrize("name", ["flat_modes", "star", "smooth_general"])
 def test_rk4_step_parity(name, sw):
     need_gpu()
     w = WORKLOADS[name]
@@ -79,7 +79,7 @@ def test_rk4_step_parity(name, sw):
 
 
 @pytest.mark.parametrize("sw", [None, "lxf_fct"])
-@pytest.mark.parametrize("name", ["config1", "config3", "config4"])
+@pytest.mark.parametrize("name", ["flat_modes", "star", "weak_field_modes"])
 def test_rk2_step_parity(name, sw):
     need_gpu()
     w = WORKLOADS[name]
@@ -106,7 +106,7 @@ def test_batched_step_with_switches_matches_single_blocks():
     single-block step with the same switches."""
     need_gpu()
     from paper_2406_11669_gb300 import asterx as A
-    blocks = [W.config3_block(n, o) for n, o in (((12, 16, 10), (0.3515625, -0.0390625, -0.0234375)),
+    blocks = [W.star_block(n, o) for n, o in (((12, 16, 10), (0.3515625, -0.0390625, -0.0234375)),
                                                    ((16, 12, 14), (-0.1, 0.05, 0.02)))]
     params = dict(blocks[0].params, flux=W.FLUX_LXF, efield=W.EFIELD_FCT)
     entries, singles = [], []

@@ -31,8 +31,8 @@ def div_B(w, U):
             (Bf[2][k1, j, i] - Bf[2][k, j, i]) / dx[2]), np.abs(Bf).max()
 
 
-@pytest.mark.parametrize("maker", [lambda: W.config1(n=(12, 10, 8)), lambda: W.config2(n=(12, 8, 8)),
-                                   lambda: W.config5(n=(12, 12, 10))])
+@pytest.mark.parametrize("maker", [lambda: W.flat_modes(n=(12, 10, 8)), lambda: W.balsara_schwarzschild(n=(12, 8, 8)),
+                                   lambda: W.torus_jet(n=(12, 12, 10))])
 def test_divB_zero_after_step(maker):
     w = maker()
     U, P = O.initial_state(w)
@@ -45,7 +45,7 @@ def test_divB_zero_after_step(maker):
 
 
 def test_conservation_periodic_flat():
-    w = W.config1(n=(12, 10, 8))
+    w = W.flat_modes(n=(12, 10, 8))
     U, P = O.initial_state(w)
     M = O.metric_array(w)
     O.ghost_fill_state(w, U)
@@ -60,8 +60,8 @@ def test_conservation_periodic_flat():
 
 
 def test_conservation_of_D_curved_periodic():
-    """Weak-field lapse (config 4 metric): only D~ is conserved (the others have sources)."""
-    w = W.config4(n=(10, 8, 8))
+    """Weak-field lapse (the adjoint workload's metric): only D~ is conserved (the others have sources)."""
+    w = W.weak_field_modes(n=(10, 8, 8))
     U, P = O.initial_state(w)
     M = O.metric_array(w)
     O.ghost_fill_state(w, U)
@@ -210,14 +210,14 @@ def test_alfven_wave_convergence_and_speed():
 
 
 def test_ghost_fill_periodic_and_copy():
-    w = W.config1(n=(6, 5, 4))
+    w = W.flat_modes(n=(6, 5, 4))
     U, _ = O.initial_state(w)
     O.ghost_fill_state(w, U)
     g, n = w.g, w.n
     # periodic: index i and i + n are the same object for every staggering
     assert np.array_equal(U[:, :, :, 0:g], U[:, :, :, n[0]:n[0] + g])
     assert np.array_equal(U[:, :, 0:g, :], U[:, :, n[1]:n[1] + g, :])
-    w2 = W.config2(n=(6, 5, 4))
+    w2 = W.balsara_schwarzschild(n=(6, 5, 4))
     U2, _ = O.initial_state(w2)
     O.ghost_fill_state(w2, U2)
     # copy: hydro ghosts equal the nearest owned cell; A_z (vertex-like along x) extrapolates linearly
@@ -229,8 +229,9 @@ def test_ghost_fill_periodic_and_copy():
 
 
 def test_balsara1_robustness_smoke():
-    """Table 1 test 1 states (config 2 data) in the Schwarzschild slice: one step, no recovery failure."""
-    w = W.config2(n=(24, 6, 6))
+    """Table 1 test 1 states (the bench workload's data) in the Schwarzschild slice: one step, no recovery
+    failure."""
+    w = W.balsara_schwarzschild(n=(24, 6, 6))
     U, P = O.initial_state(w)
     M = O.metric_array(w)
     O.ghost_fill_state(w, U)

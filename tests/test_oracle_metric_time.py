@@ -27,7 +27,7 @@ def owned(w, v):
 
 
 def test_stage_lapses_scale_the_stage_slopes():
-    w = W.config1(n=(7, 6, 8))
+    w = W.flat_modes(n=(7, 6, 8))
     w.params = dict(w.params, recon=W.RECON_PPM, xi_lorenz=10.0)
     M1 = O.metric_array(w)
     U0, P0 = O.initial_state(w)

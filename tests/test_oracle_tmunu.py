@@ -19,7 +19,7 @@ IDX = [(0, 0), (0, 1), (0, 2), (0, 3), (1, 1), (1, 2), (1, 3), (2, 2), (2, 3), (
 
 
 def block(n=(5, 4, 6), gamma=5.0 / 3.0):
-    w = W.config1(n=n)
+    w = W.flat_modes(n=n)
     w.params = dict(w.params, gamma=gamma)
     return w
 

@@ -111,7 +111,7 @@ SWITCHES = [(W.FLUX_LXF, W.EFIELD_UCT), (W.FLUX_HLLE, W.EFIELD_FCT), (W.FLUX_LXF
 @pytest.mark.parametrize("flux,efield", SWITCHES)
 def test_switches_keep_divB_conservation_and_steady_states(flux, efield):
     from test_oracle_grid import _uniform_workload, div_B, interior
-    w = variant(W.config1(n=(10, 8, 6)), flux, efield)
+    w = variant(W.flat_modes(n=(10, 8, 6)), flux, efield)
     U, P = O.initial_state(w)
     M = O.metric_array(w)
     O.ghost_fill_state(w, U)
@@ -209,7 +209,7 @@ def gauge_wave(n=(4, 4, 1), eps=1e-3):
     """Uniform fluid at rest in flat space with a pure-gauge potential A = grad chi (discrete gradient of a vertex
     chi, so the discrete curl B~ is zero) and Psi = 0: the Lorenz-gauge potentials then obey the linear damped
     wave system dA/dt = -grad Psi, dPsi/dt = -div A - xi Psi while the fluid stays put."""
-    w = W.config1(n=n)
+    w = W.flat_modes(n=n)
     w.params = dict(w.params, recon=W.RECON_PPM, xi_lorenz=2.0)
     g, N = w.g, w.N
     x = [w.x0[a] + (np.arange(N[a] + 2) - g) * w.dx[a] for a in range(3)]

@@ -53,7 +53,7 @@ def test_noalloc_matches_workspace_entry_point_twice():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     # two different blocks in a row: the second call must not see the first call's scratch
-    blocks = [W.config5(n=(20, 18, 16)), W.config2(n=(24, 11, 9))]
+    blocks = [W.torus_jet(n=(20, 18, 16)), W.balsara_schwarzschild(n=(24, 11, 9))]
     for w in blocks:
         assert np.prod([m + 7 for m in w.n]) <= 65536
         M = O.metric_array(w)
@@ -75,7 +75,7 @@ def test_noalloc_rejects_blocks_beyond_the_scratch_array():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2406_11669_gb300 import asterx as A
-    w = W.config1(n=(40, 40, 40))  # 47^3 = 103823 padded entries > 65536: rejected before any launch
+    w = W.flat_modes(n=(40, 40, 40))  # 47^3 = 103823 padded entries > 65536: rejected before any launch
     M = torch.zeros((16,) + w.shape, dtype=torch.float64, device="cuda")
     U = torch.zeros((9,) + w.shape, dtype=torch.float64, device="cuda")
     P = torch.zeros((5,) + w.shape, dtype=torch.float64, device="cuda")
