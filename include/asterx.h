@@ -137,7 +137,7 @@ asterx_status asterx_con2prim(const asterx_params *p, const asterx_block *blk, a
 asterx_status asterx_fill_ghosts(const asterx_params *p, const asterx_block *blk, asterx_state *U, void *ws,
                                  size_t ws_bytes, asterx_stream stream);
 
-/* Right-hand side dU/dt of the 9 state fields (Sec. 3.9 workflow, Sec. 3.4): U and P must have their ghosts
+/* Right-hand side dU/dt of the 9 state fields (Sec. 3.12 workflow, Sec. 3.4): U and P must have their ghosts
  * filled (P after recovery).  Writes dUdt at the interior cells, at the edges/vertices of the owned range
  * (indices g..g+n along vertex-like axes, g..g+n-1 along cell-like axes), and nowhere else.  `dt` only sets
  * the Lorenz damping when xi_lorenz == 0. */

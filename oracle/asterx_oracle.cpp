@@ -1055,7 +1055,7 @@ template <class R> MetricDeriv<R> lift_deriv(const MetricDeriv<double>& d) {
 }
 
 // ------------------------------------------------------------------------------------------------------
-// The right-hand side of one stage (Sec. 3.9 workflow: reconstruct, Riemann solve, sources; Sec. 3.4 for
+// The right-hand side of one stage (Sec. 3.12 workflow: reconstruct, Riemann solve, sources; Sec. 3.4 for
 // the potentials).  Inputs: state with ghosts filled and primitives with ghosts filled.
 
 struct RhsStats {
@@ -1350,7 +1350,7 @@ static void con2prim(const Grid& G, const VertexMetric& vm, const OParams& P, do
       }
 }
 
-// Conserved variables at all cells from primitives (initial data, Sec. 3.9 and Eq. cons).
+// Conserved variables at all cells from primitives (initial data, Sec. 3.12 and Eq. cons).
 static void prim2con_grid(const Grid& G, const VertexMetric& vm, const OParams& P, double* const U[9],
                           double* const prim[5]) {
   Field Bf[3], Bc[3];
@@ -1382,7 +1382,7 @@ static void prim2con_grid(const Grid& G, const VertexMetric& vm, const OParams& 
 // U_acc accumulates b_s dt k_s, b = (1/6, 1/3, 1/3, 1/6); the last stage writes U_n + U_acc + dt/6 k_3.
 // Stages 4 and 5 are the two stages of RK2, the explicit midpoint method: U_1 = U_n + dt/2 k(U_n), then
 // U_{n+1} = U_n + dt k(U_1) (U_acc unused).
-// Stage order (Sec. 3.9): ghost fill U_s, con2prim on the interior, ghost fill primitives, RHS, combine.
+// Stage order (Sec. 3.12): ghost fill U_s, con2prim on the interior, ghost fill primitives, RHS, combine.
 
 static void owned_range(const Grid& G, int v, int lo[3], int hi[3]) {
   for (int a = 0; a < 3; a++) {

@@ -1,5 +1,5 @@
 // Host runtime of the C ABI declared in include/asterx.h: argument validation (before any launch), workspace
-// layout, and the order of launches of one RK stage (Sec. 3.9 workflow of arXiv:2406.11669).
+// layout, and the order of launches of one RK stage (Sec. 3.12 workflow of arXiv:2406.11669).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>

@@ -1,6 +1,6 @@
 // Kernels of one RK stage of the Valencia GRMHD right-hand side (AsterX, arXiv:2406.11669).
 //
-// Stage order (Sec. 3.9 workflow): ghost fill of U_s, B~ = curl A, recovery on the interior (Sec. 3.5),
+// Stage order (Sec. 3.12 workflow): ghost fill of U_s, B~ = curl A, recovery on the interior (Sec. 3.5),
 // ghost fill of the primitives, then per direction: reconstruction of each cell once (Sec. 3.3) and the face
 // solve (prim->cons, fluxes, magnetosonic speeds, HLLE, upwind transverse velocities of Eq. uct1); vertex
 // potentials G_A and F_Psi (Sec. 3.4); edges: UCT electric field (Eq. eq3.20) and dA/dt = -E - grad G_A;

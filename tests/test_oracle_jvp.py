@@ -1,5 +1,5 @@
 """Pins of the oracle's forward-mode derivative: the Jacobian-vector product J dU of the stage operator
-L(U) = RHS(ghost fill U, recovery, ghost fill P) and of one classical RK4 step (Sec. 3.9), evaluated with
+L(U) = RHS(ghost fill U, recovery, ghost fill P) and of one classical RK4 step (Sec. 3.12), evaluated with
 one-direction dual numbers and, for the recovery, the implicit-function theorem at its root.
 
 The dual evaluation repeats the plain oracle's arithmetic in its value part, so L and the stepped state must
