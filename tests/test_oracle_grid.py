@@ -1,12 +1,12 @@
 """Grid-level pins of the oracle's RK stage: structure the discretisation must have whatever the data.
 
-P2  div B~ = 0 to round-off after a stage (B~ = curl A on faces, Sec. 3.4, Eq. divB2).
-P3  volume integrals of D~, S~_i, tau~ conserved on a periodic flat box (flux form, Eq. fluxconseqs).
-P4  a uniform state in a uniform (non-flat) metric has a zero hydro right-hand side, and curl(dA/dt) = 0.
-P1  A_z advected by a uniform flow moves toward +x (fixes the sign of E = -v~ x B~, Eq. eq3.20 vs the
-    induction equation) with second-order error.
-P9  the circularly polarised Alfven wave of Sec. 4.2 travels at v_A = 0.5 and converges at ~2nd order.
-Ghost fill: periodic copies are exact images; copy BCs copy hydro and extrapolate A linearly.
+* div B~ = 0 to round-off after a stage (B~ = curl A on faces, Sec. 3.4, Eq. divB2).
+* volume integrals of D~, S~_i, tau~ conserved on a periodic flat box (flux form, Eq. fluxconseqs).
+* a uniform state in a uniform (non-flat) metric has a zero hydro right-hand side, and curl(dA/dt) = 0.
+* A_z advected by a uniform flow moves toward +x (fixes the sign of E = -v~ x B~, Eq. eq3.20 vs the
+  induction equation) with second-order error.
+* the circularly polarised Alfven wave of Sec. 4.2 travels at v_A = 0.5 and converges at ~2nd order.
+* ghost fill: periodic copies are exact images; copy BCs copy hydro and extrapolate A linearly.
 """
 import math
 
