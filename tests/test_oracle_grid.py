@@ -97,8 +97,6 @@ def _uniform_workload(recon, metric_kind):
     for name, st, comp in (("Ax", W.XEDGE, 0), ("Ay", W.YEDGE, 1), ("Az", W.ZEDGE, 2)):
         X, Y, Z = W.positions(n, g, x0, dx, st)
         r = [np.broadcast_to(X, shape), np.broadcast_to(Y, shape), np.broadcast_to(Z, shape)]
-        c = np.cross(Bt, np.array([0, 0, 0]))  # placeholder to keep shapes explicit
-        del c
         a1, a2 = (comp + 1) % 3, (comp + 2) % 3
         A[name] = 0.5 * (Bt[a1] * r[a2] - Bt[a2] * r[a1])
     prims = dict(rho=full(0.7), press=full(0.4), velx=full(0.2), vely=full(-0.1), velz=full(0.15))

@@ -82,10 +82,10 @@ def test_ghost_states_are_fourth_order(lam):
             assert e1[m, s] / e2[m, s] >= 13.0, (m, s, e1[m, s], e2[m, s])
 
 
-def test_subcycled_step_keeps_a_uniform_state():
+@pytest.mark.parametrize("Lr", [(2, 2, 1), (0, 4, 2)])  # inside; touching the coarse boundary at low x, high y, z
+def test_subcycled_step_keeps_a_uniform_state(Lr):
     from test_oracle_grid import _uniform_workload
     wc = _uniform_workload(W.RECON_PPM, "flat")
-    Lr = (2, 2, 1)
     wf = W.Workload("fine", (8, 6, 8), wc.g, tuple(wc.x0[d] + Lr[d] * wc.dx[d] for d in range(3)),
                     tuple(h / 2 for h in wc.dx), wc.bc, wc.params, wc.dt / 2, {}, {}, None, {})
     Uc, Pc = O.initial_state(wc)
