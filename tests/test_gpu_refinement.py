@@ -119,3 +119,32 @@ def test_subcycled_step_matches_oracle(recon):
         e, s = rel_field_err(gf, rf, wf, v)
         assert s == 0.0 or e <= 1e-12, ("fine", v, e)
     assert int(stats[3]) == 0
+
+
+@pytest.mark.parametrize("bc", [W.BC_COPY, W.BC_PERIODIC])
+def test_subcycled_step_with_the_box_on_the_boundary_matches_oracle(bc):
+    """The fine box touching the coarse block's boundary (low x, high y, high z): the interpolated coarse state
+    is then formed and recovered along whole axes there, and its ghost fill (copy or periodic) feeds the
+    prolongation.  One subcycled step against the oracle, both levels within 1e-12."""
+    need_gpu()
+    from paper_2406_11669_gb300 import asterx as A
+    Lb = (0, 9, 7)  # with M = (4, 3, 5) coarse cells under the box: L + M = (4, 12, 12)
+    n = (12, 12, 12)
+    wc = W.smooth_general(n=n, bc=bc, recon=W.RECON_WENOZ)
+    wfd = W.smooth_general(n=tuple(2 * v for v in n), bc=bc, recon=W.RECON_WENOZ)
+    wf = W.sub_block(wfd, tuple(2 * v for v in Lb), tuple(2 * v for v in M))
+    Uc, Pc = O.initial_state(wc)
+    O.ghost_fill_state(wc, Uc)
+    Uf, Pf = O.initial_state(wf)
+    Mc, Mf = O.metric_array(wc), O.metric_array(wf)
+    dt = 2.0 * wf.dt
+    cc, cf = GpuCase(wc), GpuCase(wf)
+    Ucd, Pcd, Ufd, Pfd = cc.dev(Uc), cc.dev(Pc), cf.dev(Uf), cf.dev(Pf)
+    A.rk4_step_subcycled(cc.solver, cf.solver, Ucd, Pcd, Ufd, Pfd, dt)
+    rc, rf = O.subcycled_rk4_step(wc, Mc, Uc.copy(), Pc.copy(), wf, Mf, Uf.copy(), Pf.copy(), Lb, dt)
+    gc, gf = cc.host(Ucd), cf.host(Ufd)
+    for v in range(9):
+        e, s = rel_field_err(gc, rc, wc, v)
+        assert s == 0.0 or e <= 1e-12, ("coarse", v, e)
+        e, s = rel_field_err(gf, rf, wf, v)
+        assert s == 0.0 or e <= 1e-12, ("fine", v, e)
