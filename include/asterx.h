@@ -365,8 +365,11 @@ asterx_status asterx_batch_prepare_tiled(const asterx_params *p, const asterx_ba
  *
  * Some callers cannot call cudaMalloc: a plugin inside a host application that owns all device memory and
  * hands out only the buffers it manages, or a time-critical loop that must not allocate because cudaMalloc
- * can synchronise the device and can fail in the middle of a run.  For them this entry point runs the same
- * recovery as asterx_con2prim (same kernels, same results) without a caller workspace: the scratch it needs
+ * can synchronise the device and can fail in the middle of a run.  For them this entry point runs the
+ * recovery of asterx_con2prim (the same face-field, centre-field and recovery kernels) without a caller
+ * workspace.  Its centre metric record comes from a direct 4x4x4 contraction of the vertex metric instead of
+ * asterx_prepare's separable passes; the two agree to rounding, so the recovered primitives agree with
+ * asterx_con2prim's to rounding (not bit for bit) and the flags and counters match.  The scratch it needs
  * (the frozen-metric centre record, the face field B~ and the centre field B) lives in one fixed-size array
  * in the library's own device memory, which every GPU that loads the library holds until the process exits
  * ((53 + 6) * ASTERX_NOALLOC_MAX_ENTRIES doubles, about 31 MB).  The caller still passes the inputs and
@@ -375,13 +378,17 @@ asterx_status asterx_batch_prepare_tiled(const asterx_params *p, const asterx_ba
  * It allocates nothing and calls no allocating routine.
  *
  * Limits and rules:
- *  - the padded block (n[0]+7)(n[1]+7)(n[2]+7) may hold at most ASTERX_NOALLOC_MAX_ENTRIES entries per field
- *    (for example 33^3 interior cells); larger blocks return ASTERX_EINVAL before anything is launched;
+ *  - the block must pass the checks of the workspace entry points (parameters, 3 ghosts, 1..2^20 cells per
+ *    axis, finite origin and spacing), and the padded block (n[0]+7)(n[1]+7)(n[2]+7) may hold at most
+ *    ASTERX_NOALLOC_MAX_ENTRIES entries per field (for example 33^3 interior cells); other blocks return
+ *    ASTERX_EINVAL before anything is launched;
  *  - every call shares the one array, which keeps the last call's contents; calls that overlap on the GPU
  *    (different streams, or different host threads without ordering) race on it and must be serialised by
  *    the caller;
  *  - the first call on each device looks up the array's device address (cudaGetSymbolAddress) with that
- *    device current; make that first call before any stream capture. */
+ *    device current, and looks it up again when that device's context has changed (after a device reset by
+ *    the host application); make the first call, and the first call after a reset, before any stream
+ *    capture. */
 #define ASTERX_NOALLOC_MAX_ENTRIES 65536L
 asterx_status asterx_con2prim_noalloc(const asterx_params *p, const asterx_block *blk,
                                       const asterx_metric *metric, asterx_state *U, asterx_prims *P,

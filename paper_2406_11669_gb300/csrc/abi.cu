@@ -9,6 +9,7 @@
 
 #include "../../include/asterx.h"
 #include "kernels.h"
+#include "validate.h"
 
 using namespace asterx;
 
@@ -17,54 +18,16 @@ namespace {
 constexpr int kAbiVersion = 2;
 constexpr size_t kAlign = 256;
 
-long padded_V(const asterx_block* b) {
-  long V = 1;
-  for (int d = 0; d < 3; d++) V *= (long)(b->n[d] + 2 * b->g + 1);
-  return V;
-}
+long padded_V(const asterx_block* b) { return check::padded_volume(b); }
 
 // each field starts on a 256-byte boundary
 long field_stride(long V) { return (V + 31) / 32 * 32; }
 
-bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
-
-bool block_ok(const asterx_block* b) {
-  if (!b) return false;
-  if (b->g != 3) return false;
-  for (int d = 0; d < 3; d++) {
-    if (b->n[d] < 1 || b->n[d] > (1 << 20)) return false;
-    if (!finite_pos(b->dx[d]) || !std::isfinite(b->x0[d])) return false;
-    if (b->bc[d] != ASTERX_BC_PERIODIC && b->bc[d] != ASTERX_BC_COPY) return false;
-  }
-  const double V = (double)(b->n[0] + 7) * (b->n[1] + 7) * (b->n[2] + 7);
-  return V < 4.0e9;
-}
-
-bool params_ok(const asterx_params* p) {
-  if (!p) return false;
-  if (!(std::isfinite(p->gamma) && p->gamma > 1.0)) return false;
-  if (!finite_pos(p->rho_atm) || !(std::isfinite(p->K_atm) && p->K_atm >= 0.0)) return false;
-  if (!(std::isfinite(p->gamma_atm) && p->gamma_atm > 1.0)) return false;
-  if (!finite_pos(p->c2p_tol) || p->c2p_maxiter < 1 || p->brent_maxiter < 1) return false;
-  if (!(std::isfinite(p->W_max) && p->W_max > 1.0)) return false;
-  if (p->recon < ASTERX_RECON_MINMOD || p->recon > ASTERX_RECON_WENOZ) return false;
-  if (p->gauge != ASTERX_GAUGE_LORENZ && p->gauge != ASTERX_GAUGE_ALGEBRAIC) return false;
-  if (!(std::isfinite(p->xi_lorenz) && p->xi_lorenz >= 0.0)) return false;
-  if (p->flux != ASTERX_FLUX_HLLE && p->flux != ASTERX_FLUX_LXF) return false;
-  if (p->efield != ASTERX_EFIELD_UCT && p->efield != ASTERX_EFIELD_FCT) return false;
-  return p->use_fallback == 0 || p->use_fallback == 1;
-}
-
-bool ptr_ok(const void* q) { return q && ((uintptr_t)q % 8 == 0); }
-
-template <class S, int N>
-bool set_ok(const S* s) {
-  if (!s) return false;
-  const double* const* f = reinterpret_cast<const double* const*>(s);
-  for (int i = 0; i < N; i++)
-    if (!ptr_ok(f[i])) return false;
-  return true;
-}
+using check::block_ok;
+using check::finite_pos;
+using check::params_ok;
+using check::ptr_ok;
+using check::set_ok;
 
 size_t ws_bytes_for(const asterx_block* b) {
   const long fs = field_stride(padded_V(b));

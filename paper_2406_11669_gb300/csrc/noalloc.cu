@@ -1,6 +1,8 @@
 // Primitive recovery without any device allocation by the caller or the library: the scratch memory the
 // recovery needs (centre geometry, face field, centre field) lives in one fixed-size array in the library's
 // own device memory.  See asterx_con2prim_noalloc in include/asterx.h for who needs this and its limits.
+#include <cuda.h>
+
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -8,6 +10,7 @@
 
 #include "../../include/asterx.h"
 #include "kernels.h"
+#include "validate.h"
 
 using namespace asterx;
 
@@ -22,27 +25,59 @@ __device__ __align__(256) double g_noalloc_scratch[(long)kFields * kMaxEntries];
 
 std::mutex g_mutex;
 constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+  unsigned long long ctx_id;  // the CUDA context the address belongs to (0: not looked up yet)
+  double* ptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once per device.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique id of the current context, through the driver entry points the runtime hands out (the library
+// links no driver library).  A device reset ends the context; the next one has a new id.
+cudaError_t current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f = nullptr;
+    void* g = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1);
+    if (e != cudaSuccess || q1 != cudaDriverEntryPointSuccess || !f) return e != cudaSuccess ? e : cudaErrorUnknown;
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess || q2 != cudaDriverEntryPointSuccess || !g) return e != cudaSuccess ? e : cudaErrorUnknown;
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    get_id = reinterpret_cast<CtxGetIdFn>(g);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+  return get_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+// Device address of the scratch array on the current device.  It is looked up (cudaGetSymbolAddress, which
+// also creates the device's context if the process has none yet) on the first call on each device and again
+// whenever the device's context has changed since, e.g. after the host application reset the device.  If the
+// context cannot be identified, the address is looked up on every call.
 cudaError_t scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[dev]) {
+  unsigned long long id = 0;
+  const bool known = g_scratch_addr[dev].ctx_id != 0 && current_context_id(&id) == cudaSuccess &&
+                     id == g_scratch_addr[dev].ctx_id;
+  if (!known) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double*>(p);
+    g_scratch_addr[dev].ctx_id = (current_context_id(&id) == cudaSuccess) ? id : 0;
+    g_scratch_addr[dev].ptr = static_cast<double*>(p);
   }
-  *out = g_scratch_addr[dev];
+  *out = g_scratch_addr[dev].ptr;
   return cudaSuccess;
 }
-
-bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
-bool aligned8(const void* q) { return q && ((uintptr_t)q % 8 == 0); }
 
 }  // namespace
 
@@ -50,28 +85,13 @@ extern "C" asterx_status asterx_con2prim_noalloc(const asterx_params* p, const a
                                                  const asterx_metric* metric, asterx_state* U, asterx_prims* P,
                                                  signed char* flags, asterx_c2p_stats* stats,
                                                  asterx_stream stream) {
-  // argument checks (the same rules as the workspace entry points)
-  if (!p || !blk || !metric || !U || !P) return ASTERX_EINVAL;
-  if (!(std::isfinite(p->gamma) && p->gamma > 1.0) || !finite_pos(p->rho_atm) || !(p->K_atm >= 0.0) ||
-      !(p->gamma_atm > 1.0) || !finite_pos(p->c2p_tol) || p->c2p_maxiter < 1 || p->brent_maxiter < 1 ||
-      !(p->W_max > 1.0) || (p->use_fallback != 0 && p->use_fallback != 1))
-    return ASTERX_EINVAL;
-  if (blk->g != 3) return ASTERX_EINVAL;
-  long V = 1;
-  for (int d = 0; d < 3; d++) {
-    if (blk->n[d] < 1 || !finite_pos(blk->dx[d]) || (blk->bc[d] != 0 && blk->bc[d] != 1)) return ASTERX_EINVAL;
-    V *= (long)(blk->n[d] + 2 * blk->g + 1);
-  }
+  // argument checks: the same rules as the workspace entry points, then the size of the fixed array
+  if (!check::params_ok(p) || !check::block_ok(blk)) return ASTERX_EINVAL;
+  const long V = check::padded_volume(blk);  // bounded factors: each n + 7 <= 2^20 + 7, product < 4e9
   if (V > kMaxEntries) return ASTERX_EINVAL;  // the block does not fit the fixed scratch array
-  const double* const* mf = reinterpret_cast<const double* const*>(metric);
-  for (int f = 0; f < 16; f++)
-    if (!aligned8(mf[f])) return ASTERX_EINVAL;
-  double* const* uf = reinterpret_cast<double* const*>(U);
-  for (int f = 0; f < 9; f++)
-    if (!aligned8(uf[f])) return ASTERX_EINVAL;
-  double* const* pf = reinterpret_cast<double* const*>(P);
-  for (int f = 0; f < 5; f++)
-    if (!aligned8(pf[f])) return ASTERX_EINVAL;
+  if (!metric || !check::set_ok<asterx_metric, 16>(metric) || !check::set_ok<asterx_state, 9>(U) ||
+      !check::set_ok<asterx_prims, 5>(P))
+    return ASTERX_EINVAL;
   if (stats && ((uintptr_t)stats % 8) != 0) return ASTERX_EINVAL;
 
   double* base = nullptr;

@@ -256,3 +256,38 @@ def test_subcycled_step_workspace_and_validation():
     assert call(wt=128) == A.ASTERX_EINVAL
     assert call(dt=0.0) == A.ASTERX_EINVAL
     assert call(fine=A.block_struct((8, 8, 8), 3, (0.35, 0.3, 0.3), (0.05,) * 3, (1, 1, 1))) == A.ASTERX_EINVAL
+
+
+@pytest.mark.parametrize("n", [(1, 1, 2 ** 31 - 7), (2 ** 21 - 7,) * 3, (2 ** 20 + 1, 1, 1), (40, 40, 40),
+                               (0, 8, 8), (-5, 8, 8)])
+def test_noalloc_rejects_blocks_it_cannot_hold_on_host(n):
+    """The allocation-free recovery rejects, before any CUDA call, blocks whose padded volume exceeds its fixed
+    scratch array, including sizes whose padded volume overflows a 32- or 64-bit product."""
+    L = A.lib()
+    p = _params()
+    b = A.block_struct(n, 3, (0, 0, 0), (0.1,) * 3, (0, 0, 0))
+    m = A.Metric(*([8] * 16))
+    st = A.State(*([8] * 9))
+    pr = A.Prims(*([8] * 5))
+    rc = L.asterx_con2prim_noalloc(ctypes.byref(p), ctypes.byref(b), ctypes.byref(m), ctypes.byref(st),
+                                   ctypes.byref(pr), None, None, None)
+    assert rc == A.ASTERX_EINVAL
+
+
+@pytest.mark.parametrize("change", [dict(K_atm=float("inf")), dict(gamma_atm=float("inf")),
+                                    dict(W_max=float("inf")), dict(recon=7), dict(gauge=3), dict(flux=2),
+                                    dict(efield=-1), dict(xi_lorenz=-1.0)])
+def test_noalloc_applies_the_workspace_entry_points_parameter_rules(change):
+    L = A.lib()
+    p = _params(**change)
+    b = A.block_struct((8, 8, 8), 3, (0, 0, 0), (0.1,) * 3, (0, 0, 0))
+    m = A.Metric(*([8] * 16))
+    st = A.State(*([8] * 9))
+    pr = A.Prims(*([8] * 5))
+    rc = L.asterx_con2prim_noalloc(ctypes.byref(p), ctypes.byref(b), ctypes.byref(m), ctypes.byref(st),
+                                   ctypes.byref(pr), None, None, None)
+    assert rc == A.ASTERX_EINVAL
+    b.x0[0] = float("nan")
+    rc = L.asterx_con2prim_noalloc(ctypes.byref(_params()), ctypes.byref(b), ctypes.byref(m), ctypes.byref(st),
+                                   ctypes.byref(pr), None, None, None)
+    assert rc == A.ASTERX_EINVAL
