@@ -20,12 +20,12 @@ _LIB = os.path.join(_LIBDIR, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
-    """Compiles the oracle with g++ (-O2, no floating-point contraction, portable flags)."""
+    """Compiles the oracle with g++ (-O2, no floating-point contraction, OpenMP, portable flags)."""
     os.makedirs(_LIBDIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp,
-                               _SRC])
+        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                               "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -62,6 +62,10 @@ def lib():
         _lib = ctypes.CDLL(build())
         L = _lib
         L.oracle_abi_version.restype = ctypes.c_int
+        L.oracle_set_threads.restype = ctypes.c_int
+        L.oracle_set_threads.argtypes = [ctypes.c_int]
+        # one thread unless asked otherwise: the test suite runs in parallel processes
+        L.oracle_set_threads(int(os.environ.get("ORACLE_THREADS", "1")))
         for name in ("oracle_ghost_fill_state", "oracle_ghost_fill_prims"):
             getattr(L, name).argtypes = [ctypes.POINTER(OBlock), _PP]
         L.oracle_prim2con.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP]
@@ -85,6 +89,8 @@ def lib():
         L.oracle_face_flops.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, ctypes.c_int,
                                         ctypes.c_int, _P]
         L.oracle_recon_flops.argtypes = [ctypes.c_int, _P, _P]
+        L.oracle_stage_flops.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, ctypes.c_int,
+                                         ctypes.c_double, _P]
         L.oracle_point_sources.argtypes = [ctypes.POINTER(OParams), _P, _P, _P, _P, _P, _P, _P]
         L.oracle_grid_sources.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP]
         L.oracle_rk_stage_given_ghosts.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, ctypes.c_int,
@@ -106,6 +112,11 @@ def lib():
 
 
 # ------------------------------------------------------------------------------------------------------------
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's grid loops; returns the count in effect."""
+    return int(lib().oracle_set_threads(int(n)))
 
 
 def params_struct(p: dict) -> OParams:
@@ -511,3 +522,27 @@ def recon_flops(scheme, a5):
     out = np.zeros(4)
     lib().oracle_recon_flops(int(scheme), _p(np.ascontiguousarray(a5, float)), _p(out))
     return dict(zip(("add", "mul", "div", "sqrt"), out.tolist()))
+
+
+STAGE_FLOP_PARTS = ("ghost_state", "recovery", "ghost_prims", "faces", "hydro_cells", "potentials", "edges", "psi",
+                    "combine")
+
+
+def stage_flops(w, M, U, P, stage=1, dt=None, params=None):
+    """Algorithmic flop counts of one RK stage on state U (ghosts filled on a copy) with the recovery's guess P,
+    part by part (each a dict add, mul, div, sqrt), plus the interior cell count (n_cells), the speed iterations and faces of the
+    face solves, the flops spent inside the speed Newton loops, the Noble iterations and the recovery's branch
+    counts.  The right-hand side's recomputation of the face and centre field is reported apart ('rhs_field')."""
+    out = np.zeros(60)
+    lib().oracle_stage_flops(ctypes.byref(params_struct(params or w.params)), ctypes.byref(block_struct(w)),
+                             _ptrs(M), _ptrs(np.ascontiguousarray(U)), _ptrs(np.ascontiguousarray(P)), int(stage),
+                             float(dt if dt is not None else w.dt), _p(out))
+    keys = ("add", "mul", "div", "sqrt")
+    res = {"n_cells": out[0]}
+    for q, name in enumerate(STAGE_FLOP_PARTS):
+        res[name] = dict(zip(keys, out[1 + 4 * q:5 + 4 * q].tolist()))
+    res["rhs_field"] = dict(zip(keys, out[45:49].tolist()))
+    res.update(speed_iters=out[37], faces_solved=out[38], speed_loop_flops=out[39], noble_iters=out[40],
+               n_noble=out[41], n_fallback=out[42], n_atm=out[43], n_failed=out[44], cellvar_flops=out[49],
+               recon_flops=out[50], facesolve_flops=out[51], edge_ppm_flops=out[52], recovery_field_flops=out[53])
+    return res

@@ -33,7 +33,11 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace asterx_oracle {
 
@@ -44,6 +48,17 @@ struct Flops {
   unsigned long long add = 0, mul = 0, div = 0, sqrt = 0;
 };
 static Flops g_flops;
+static unsigned long long flops_total(const Flops& f) { return f.add + f.mul + f.div + f.sqrt; }
+// Flops spent inside the wave-speed Newton loops (flop-counting scalar only), and the phase boundaries of the
+// right-hand side (set by the flop-count entry; null otherwise).
+static unsigned long long g_speed_loop_flops = 0;
+static Flops* g_rhs_marks = nullptr;
+// Flops of steps that this literal oracle repeats where an implementation does them once (flop-counting scalar
+// only): u = W v per cell (formed for each of the three directions), the per-cell reconstruction (formed for
+// both faces of every cell), the PPM interfaces of the edge fields (formed for both edges that share a face
+// value); and the face solves themselves.
+static unsigned long long g_cellvar_flops = 0, g_recon_flops = 0, g_facesolve_flops = 0, g_edge_ppm_flops = 0;
+
 
 struct Fc {
   double v;
@@ -70,6 +85,16 @@ inline double val(Fc a) { return a.v; }
 inline double val(double a) { return a; }
 inline bool finite(double a) { return std::isfinite(a); }
 inline bool finite(Fc a) { return std::isfinite(a.v); }
+
+// Adds the flops counted while it lives to *acc (flop-counting scalar only; a no-op for other scalars).
+template <class R> struct FlopScope {
+  unsigned long long* acc;
+  unsigned long long t0;
+  explicit FlopScope(unsigned long long* a) : acc(a), t0(std::is_same<R, Fc>::value ? flops_total(g_flops) : 0) {}
+  ~FlopScope() {
+    if (std::is_same<R, Fc>::value) *acc += flops_total(g_flops) - t0;
+  }
+};
 
 // Forward-mode dual number with one direction: value v and directional derivative d.  Comparisons act on the
 // value, so a branch contributes the derivative of the branch taken.
@@ -105,6 +130,15 @@ inline double val(Dual1 a) { return a.v; }
 inline bool finite(Dual1 a) { return std::isfinite(a.v); }
 using std::fabs;
 using std::sqrt;
+
+// The per-cell, per-face and per-edge loops of the grid steps run on OpenMP threads over (k, j) pencils (every
+// iteration writes its own entries; counters are reduced).  The flop-counting scalar keeps one global tally, so
+// loops instantiated with it stay on one thread.  oracle_set_threads() sets the thread count.
+template <class R> constexpr bool parallel_ok() { return !std::is_same<R, Fc>::value; }
+#define ORACLE_PRAGMA(x) _Pragma(#x)
+#define ORACLE_PAR(R) ORACLE_PRAGMA(omp parallel for collapse(2) schedule(static) if (parallel_ok<R>()))
+#define ORACLE_PAR_REDUCE(R, red) \
+  ORACLE_PRAGMA(omp parallel for collapse(2) schedule(static) if (parallel_ok<R>()) red)
 
 template <class R> inline R rmax(R a, R b) { return (a < b) ? b : a; }
 template <class R> inline R rmin(R a, R b) { return (b < a) ? b : a; }
@@ -424,6 +458,7 @@ template <class R> void wave_speeds(const Metric3<R>& m, const Prim<R>& P, const
   Q.gdd = m.gu[d][d];
   const R width = m.alp * sqrt(m.gu[d][d]);
   int it_total = 0;
+  const Flops loop0 = g_flops;
   for (int side = 0; side < 2; side++) {
     const R sgn = (side == 0) ? R(1.0) : R(-1.0);
     R lam = -m.beta[d] + sgn * width;  // light-cone speed on this side
@@ -439,6 +474,7 @@ template <class R> void wave_speeds(const Metric3<R>& m, const Prim<R>& P, const
     if (side == 0) *lam_plus = lam;
     else *lam_minus = lam;
   }
+  if (std::is_same<R, Fc>::value) g_speed_loop_flops += flops_total(g_flops) - flops_total(loop0);
   if (iters) *iters = it_total;
 }
 
@@ -661,82 +697,94 @@ template <class R> void noble_residual(R z, R v2, R D, R tau, R S2, R B2, R BS, 
 }
 
 // velocity from Eq. (Noble2D v): v^i = gamma^ij S_j / (z + B^2) + (B^j S_j) B^i / (z (z + B^2))
-static void noble_velocity(const Metric3<double>& m, const C2PIn& in, double z, double B2, double BS, double v[3]) {
+template <class R>
+static void noble_velocity(const Metric3<R>& m, const C2PIn& in, R z, R B2, R BS, R v[3]) {
   for (int a = 0; a < 3; a++) {
-    double Su = m.gu[a][0] * in.S[0] + m.gu[a][1] * in.S[1] + m.gu[a][2] * in.S[2];
-    v[a] = Su / (z + B2) + BS * in.B[a] / (z * (z + B2));
+    R Su = m.gu[a][0] * R(in.S[0]) + m.gu[a][1] * R(in.S[1]) + m.gu[a][2] * R(in.S[2]);
+    v[a] = Su / (z + B2) + BS * R(in.B[a]) / (z * (z + B2));
   }
 }
 
-static bool bad(double x) { return !std::isfinite(x) || x < 0.0; }
+template <class R> static bool bad(R x) { return !finite(x) || x < R(0.0); }
 
-static bool c2p_noble(const Metric3<double>& m, const C2PIn& in, const OParams& P, double S2, double B2, double BS,
-                      C2POut* out) {
+// x^(3/2); the flop-counting scalar counts it as one product and one square root
+static double pow15(double x) { return std::pow(x, 1.5); }
+static Fc pow15(Fc x) {
+  g_flops.mul++;
+  g_flops.sqrt++;
+  return Fc(std::pow(x.v, 1.5));
+}
+
+// The recovery is templated on the scalar for the algorithmic flop count; the inputs (C2PIn) and results
+// (C2POut) are plain doubles, and every branch is decided on values.
+template <class R>
+static bool c2p_noble(const Metric3<R>& m, const C2PIn& in, const OParams& P, R S2, R B2, R BS, C2POut* out) {
   const double gamma = P.gamma;
   const double v2max = 1.0 - 1.0 / (P.W_max * P.W_max);
   // initial guess from the previous primitives
-  double gv2 = 0.0;
+  R gv2 = R(0.0);
   for (int a = 0; a < 3; a++)
-    for (int b = 0; b < 3; b++) gv2 += m.g[a][b] * in.guess_vel[a] * in.guess_vel[b];
-  if (!(gv2 >= 0.0)) gv2 = 0.0;
-  if (gv2 > v2max) gv2 = v2max;
-  const double gW = 1.0 / std::sqrt(1.0 - gv2);
-  const double geps = in.guess_press / ((gamma - 1.0) * in.guess_rho);
-  const double gh = 1.0 + geps + in.guess_press / in.guess_rho;
-  double z = in.guess_rho * gh * gW * gW;
-  double v2 = gv2;
-  if (!(z > 0.0) || !std::isfinite(z)) return false;
+    for (int b = 0; b < 3; b++) gv2 += m.g[a][b] * R(in.guess_vel[a]) * R(in.guess_vel[b]);
+  if (!(gv2 >= R(0.0))) gv2 = R(0.0);
+  if (gv2 > R(v2max)) gv2 = R(v2max);
+  const R gW = R(1.0) / sqrt(R(1.0) - gv2);
+  const R geps = R(in.guess_press) / (R(gamma - 1.0) * R(in.guess_rho));
+  const R gh = R(1.0) + geps + R(in.guess_press) / R(in.guess_rho);
+  R z = R(in.guess_rho) * gh * gW * gW;
+  R v2 = gv2;
+  if (!(z > R(0.0)) || !finite(z)) return false;
   bool conv = false;
   int it;
   for (it = 1; it <= P.c2p_maxiter; it++) {
-    double f[2], J[2][2];
-    noble_residual<double>(z, v2, in.D, in.tau, S2, B2, BS, gamma, f, J);
-    const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-    const double dz = (-f[0] * J[1][1] + J[0][1] * f[1]) / det;
-    const double dv2 = (-J[0][0] * f[1] + J[1][0] * f[0]) / det;
+    R f[2], J[2][2];
+    noble_residual<R>(z, v2, R(in.D), R(in.tau), S2, B2, BS, gamma, f, J);
+    const R det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const R dz = (-f[0] * J[1][1] + J[0][1] * f[1]) / det;
+    const R dv2 = (-J[0][0] * f[1] + J[1][0] * f[0]) / det;
     // damped step: a step that would make z non-positive halves z instead (z = rho h W^2 > 0)
-    const bool damped = !(z + dz > 0.0);
-    z = damped ? 0.5 * z : z + dz;
+    const bool damped = !(z + dz > R(0.0));
+    z = damped ? R(0.5) * z : z + dz;
     v2 += dv2;
-    if (v2 < 0.0) v2 = 0.0;
-    if (v2 > v2max) v2 = v2max;
-    if (!std::isfinite(z) || !std::isfinite(v2)) break;
-    if (!damped && std::fabs(dz) <= P.c2p_tol * std::fabs(z) && std::fabs(dv2) <= P.c2p_tol) {
+    if (v2 < R(0.0)) v2 = R(0.0);
+    if (v2 > R(v2max)) v2 = R(v2max);
+    if (!finite(z) || !finite(v2)) break;
+    if (!damped && fabs(dz) <= R(P.c2p_tol) * fabs(z) && fabs(dv2) <= R(P.c2p_tol)) {
       conv = true;
       break;
     }
   }
   out->iters = (it > P.c2p_maxiter) ? P.c2p_maxiter : it;
-  if (!conv || !(z > 0.0) || !(v2 >= 0.0) || !(v2 < 1.0)) return false;
-  const double W = 1.0 / std::sqrt(1.0 - v2);
-  const double rho = in.D / W;
-  double v[3];
-  noble_velocity(m, in, z, B2, BS, v);
-  const double eps = (z / (rho * W * W) - 1.0) / gamma;  // Eq. (Noble2D epsilon) with the adiabatic index
-  const double press = (gamma - 1.0) * rho * eps;
+  if (!conv || !(z > R(0.0)) || !(v2 >= R(0.0)) || !(v2 < R(1.0))) return false;
+  const R W = R(1.0) / sqrt(R(1.0) - v2);
+  const R rho = R(in.D) / W;
+  R v[3];
+  noble_velocity<R>(m, in, z, B2, BS, v);
+  const R eps = (z / (rho * W * W) - R(1.0)) / R(gamma);  // Eq. (Noble2D epsilon) with the adiabatic index
+  const R press = R(gamma - 1.0) * rho * eps;
   if (bad(rho) || bad(eps) || bad(press)) return false;
   for (int a = 0; a < 3; a++)
-    if (!std::isfinite(v[a])) return false;
-  out->rho = rho;
-  out->press = press;
-  for (int a = 0; a < 3; a++) out->vel[a] = v[a];
+    if (!finite(v[a])) return false;
+  out->rho = val(rho);
+  out->press = val(press);
+  for (int a = 0; a < 3; a++) out->vel[a] = val(v[a]);
   return true;
 }
 
 // Palenzuela et al. 2015 function f(x) = x - h^ W^ (Eq. Palenzuela Brent), with W^, rho^, eps^ from x.
-struct PalenzuelaFn {
-  double q, r, s, t, D, gamma, v2max;
-  double W, rho, eps, press;
-  double operator()(double x) {
-    double v2 = (r * x * x + t * t * (2.0 * x + s)) / (x * x * (x + s) * (x + s));
-    if (v2 > v2max) v2 = v2max;
-    if (v2 < 0.0) v2 = 0.0;
-    W = 1.0 / std::sqrt(1.0 - v2);
+template <class R> struct PalenzuelaFn {
+  R q, r, s, t, D;
+  double gamma, v2max;
+  R W, rho, eps, press;
+  R operator()(R x) {
+    R v2 = (r * x * x + t * t * (R(2.0) * x + s)) / (x * x * (x + s) * (x + s));
+    if (v2 > R(v2max)) v2 = R(v2max);
+    if (v2 < R(0.0)) v2 = R(0.0);
+    W = R(1.0) / sqrt(R(1.0) - v2);
     rho = D / W;
-    eps = -1.0 + (x / W) * (1.0 - W * W) + W * (1.0 + q - s + 0.5 * (t * t / (x * x) + s / (W * W)));
-    if (eps < 0.0) eps = 0.0;
-    press = (gamma - 1.0) * rho * eps;
-    const double h = 1.0 + eps + press / rho;
+    eps = R(-1.0) + (x / W) * (R(1.0) - W * W) + W * (R(1.0) + q - s + R(0.5) * (t * t / (x * x) + s / (W * W)));
+    if (eps < R(0.0)) eps = R(0.0);
+    press = R(gamma - 1.0) * rho * eps;
+    const R h = R(1.0) + eps + press / rho;
     return x - h * W;
   }
 };
@@ -745,46 +793,46 @@ struct PalenzuelaFn {
 // [b, c] with a sign change, b the best iterate; try inverse quadratic interpolation (or the secant when only
 // two points are distinct) and fall back to bisection whenever the interpolated step is not safely inside
 // the bracket or does not shrink fast enough.
-template <class F> static bool brent_root(F& f, double lo, double hi, double xtol, int maxiter, double* root) {
-  double a = lo, b = hi;
-  double fa = f(a), fb = f(b);
-  if (!std::isfinite(fa) || !std::isfinite(fb)) return false;
-  if ((fa > 0.0 && fb > 0.0) || (fa < 0.0 && fb < 0.0)) return false;
-  double c = a, fc = fa;
-  double step = b - a, prev_step = step;
+template <class R, class F> static bool brent_root(F& f, R lo, R hi, R xtol, int maxiter, R* root) {
+  R a = lo, b = hi;
+  R fa = f(a), fb = f(b);
+  if (!finite(fa) || !finite(fb)) return false;
+  if ((fa > R(0.0) && fb > R(0.0)) || (fa < R(0.0) && fb < R(0.0))) return false;
+  R c = a, fc = fa;
+  R step = b - a, prev_step = step;
   for (int it = 0; it < maxiter; it++) {
-    if ((fb > 0.0 && fc > 0.0) || (fb < 0.0 && fc < 0.0)) {
+    if ((fb > R(0.0) && fc > R(0.0)) || (fb < R(0.0) && fc < R(0.0))) {
       c = a;  // re-establish the bracket [b, c]
       fc = fa;
       step = prev_step = b - a;
     }
-    if (std::fabs(fc) < std::fabs(fb)) {  // make b the better end
+    if (fabs(fc) < fabs(fb)) {  // make b the better end
       a = b; b = c; c = a;
       fa = fb; fb = fc; fc = fa;
     }
-    const double tol = 2.0 * 2.220446049250313e-16 * std::fabs(b) + 0.5 * xtol;
-    const double half = 0.5 * (c - b);
-    if (std::fabs(half) <= tol || fb == 0.0) {
+    const R tol = R(2.0 * 2.220446049250313e-16) * fabs(b) + R(0.5) * xtol;
+    const R half = R(0.5) * (c - b);
+    if (fabs(half) <= tol || fb == R(0.0)) {
       *root = b;
       return true;
     }
     bool bisect = true;
-    if (std::fabs(prev_step) >= tol && std::fabs(fa) > std::fabs(fb)) {
-      double num, den;
-      const double sb = fb / fa;
+    if (fabs(prev_step) >= tol && fabs(fa) > fabs(fb)) {
+      R num, den;
+      const R sb = fb / fa;
       if (a == c) {  // secant through a, b
-        num = 2.0 * half * sb;
-        den = 1.0 - sb;
+        num = R(2.0) * half * sb;
+        den = R(1.0) - sb;
       } else {       // inverse quadratic interpolation through a, b, c
-        const double qa = fa / fc, rb = fb / fc;
-        num = sb * (2.0 * half * qa * (qa - rb) - (b - a) * (rb - 1.0));
-        den = (qa - 1.0) * (rb - 1.0) * (sb - 1.0);
+        const R qa = fa / fc, rb = fb / fc;
+        num = sb * (R(2.0) * half * qa * (qa - rb) - (b - a) * (rb - R(1.0)));
+        den = (qa - R(1.0)) * (rb - R(1.0)) * (sb - R(1.0));
       }
-      if (num > 0.0) den = -den;
+      if (num > R(0.0)) den = -den;
       else num = -num;
-      const double lim1 = 3.0 * half * den - std::fabs(tol * den);
-      const double lim2 = std::fabs(prev_step * den);
-      if (2.0 * num < (lim1 < lim2 ? lim1 : lim2)) {
+      const R lim1 = R(3.0) * half * den - fabs(tol * den);
+      const R lim2 = fabs(prev_step * den);
+      if (R(2.0) * num < (lim1 < lim2 ? lim1 : lim2)) {
         prev_step = step;
         step = num / den;
         bisect = false;
@@ -796,40 +844,42 @@ template <class F> static bool brent_root(F& f, double lo, double hi, double xto
     }
     a = b;
     fa = fb;
-    if (std::fabs(step) > tol) b += step;
-    else b += (half > 0.0 ? tol : -tol);
+    if (fabs(step) > tol) b += step;
+    else b += (half > R(0.0) ? tol : -tol);
     fb = f(b);
-    if (!std::isfinite(fb)) return false;
+    if (!finite(fb)) return false;
   }
   return false;
 }
 
-static bool c2p_palenzuela(const Metric3<double>& m, const C2PIn& in, const OParams& P, double S2, double B2,
-                           double BS, C2POut* out) {
-  PalenzuelaFn f;
-  f.q = in.tau / in.D;
-  f.r = S2 / (in.D * in.D);
-  f.s = B2 / in.D;
-  f.t = BS / std::pow(in.D, 1.5);
-  f.D = in.D;
+template <class R>
+static bool c2p_palenzuela(const Metric3<R>& m, const C2PIn& in, const OParams& P, R S2, R B2, R BS,
+                           C2POut* out) {
+  PalenzuelaFn<R> f;
+  const R D = R(in.D);
+  f.q = R(in.tau) / D;
+  f.r = S2 / (D * D);
+  f.s = B2 / D;
+  f.t = BS / pow15(D);
+  f.D = D;
   f.gamma = P.gamma;
   f.v2max = 1.0 - 1.0 / (P.W_max * P.W_max);
-  double lo = 1.0 + f.q - f.s;
-  if (lo < 1.0) lo = 1.0;
-  const double hi = 2.0 + 2.0 * f.q - f.s;
+  R lo = R(1.0) + f.q - f.s;
+  if (lo < R(1.0)) lo = R(1.0);
+  const R hi = R(2.0) + R(2.0) * f.q - f.s;
   if (!(hi > lo)) return false;
-  double x;
-  if (!brent_root(f, lo, hi, 1e-15 * hi, P.brent_maxiter, &x)) return false;
+  R x;
+  if (!brent_root<R>(f, lo, hi, R(1e-15) * hi, P.brent_maxiter, &x)) return false;
   f(x);  // primitives at the root
-  const double z = in.D * x;  // z = rho W x (Eq. Noble2D z with x = hW)
-  double v[3];
-  noble_velocity(m, in, z, B2, BS, v);
+  const R z = D * x;  // z = rho W x (Eq. Noble2D z with x = hW)
+  R v[3];
+  noble_velocity<R>(m, in, z, B2, BS, v);
   if (bad(f.rho) || bad(f.eps) || bad(f.press)) return false;
   for (int a = 0; a < 3; a++)
-    if (!std::isfinite(v[a])) return false;
-  out->rho = f.rho;
-  out->press = f.press;
-  for (int a = 0; a < 3; a++) out->vel[a] = v[a];
+    if (!finite(v[a])) return false;
+  out->rho = val(f.rho);
+  out->press = val(f.press);
+  for (int a = 0; a < 3; a++) out->vel[a] = val(v[a]);
   return true;
 }
 
@@ -841,29 +891,29 @@ static void atmosphere(const OParams& P, C2POut* out) {
   out->reset = true;
 }
 
-static C2POut c2p_cell(const Metric3<double>& m, const C2PIn& in, const OParams& P) {
+template <class R> static C2POut c2p_cell(const Metric3<R>& m, const C2PIn& in, const OParams& P) {
   C2POut out;
   out.flag = 0;
   out.iters = 0;
   out.reset = false;
   // atmosphere test on the densitised density before the recovery: D~ < sqrt(gamma) rho_atm
-  if (!(in.Dtilde >= m.sqrtg * P.rho_atm)) {
+  if (!(R(in.Dtilde) >= m.sqrtg * R(P.rho_atm))) {
     atmosphere(P, &out);
     out.flag = 2;
     return out;
   }
-  double S2 = 0.0, B2 = 0.0, BS = 0.0;
+  R S2 = R(0.0), B2 = R(0.0), BS = R(0.0);
   for (int a = 0; a < 3; a++)
     for (int b = 0; b < 3; b++) {
-      S2 += m.gu[a][b] * in.S[a] * in.S[b];
-      B2 += m.g[a][b] * in.B[a] * in.B[b];
+      S2 += m.gu[a][b] * R(in.S[a]) * R(in.S[b]);
+      B2 += m.g[a][b] * R(in.B[a]) * R(in.B[b]);
     }
-  for (int a = 0; a < 3; a++) BS += in.B[a] * in.S[a];
-  bool ok = c2p_noble(m, in, P, S2, B2, BS, &out);
+  for (int a = 0; a < 3; a++) BS += R(in.B[a]) * R(in.S[a]);
+  bool ok = c2p_noble<R>(m, in, P, S2, B2, BS, &out);
   if (ok) {
     out.flag = 0;
   } else if (P.use_fallback) {
-    ok = c2p_palenzuela(m, in, P, S2, B2, BS, &out);
+    ok = c2p_palenzuela<R>(m, in, P, S2, B2, BS, &out);
     if (ok) out.flag = 1;
   }
   if (!ok) {
@@ -935,6 +985,7 @@ template <class R>
 static void face_B(const Grid& G, const R* Ax, const R* Ay, const R* Az, std::vector<R> Bf[3]) {
   for (int d = 0; d < 3; d++) Bf[d].assign(G.size(), R(0.0));
   const double ix = 1.0 / G.dx[0], iy = 1.0 / G.dx[1], iz = 1.0 / G.dx[2];
+  ORACLE_PAR(R)
   for (int k = 0; k <= G.N[2]; k++)
     for (int j = 0; j <= G.N[1]; j++)
       for (int i = 0; i <= G.N[0]; i++) {
@@ -951,6 +1002,7 @@ static void face_B(const Grid& G, const R* Ax, const R* Ay, const R* Az, std::ve
 template <class R>
 static void centre_B(const Grid& G, const VertexMetric& vm, const std::vector<R> Bf[3], std::vector<R> Bc[3]) {
   for (int d = 0; d < 3; d++) Bc[d].assign(G.size(), R(0.0));
+  ORACLE_PAR(R)
   for (int k = 0; k < G.N[2]; k++)
     for (int j = 0; j < G.N[1]; j++)
       for (int i = 0; i < G.N[0]; i++) {
@@ -1078,6 +1130,9 @@ static void compute_faces(const Grid& G, const VertexMetric& vm, const OParams& 
   // reconstructed variables at every cell: rho, p, u^x, u^y, u^z (u = W v) and the centre B
   std::vector<R> cellvar[8];
   for (int v = 0; v < 8; v++) cellvar[v].assign(G.size(), R(0.0));
+  {
+  FlopScope<R> scope(&g_cellvar_flops);
+  ORACLE_PAR(R)
   for (int k = 0; k < G.N[2]; k++)
     for (int j = 0; j < G.N[1]; j++)
       for (int i = 0; i < G.N[0]; i++) {
@@ -1092,7 +1147,10 @@ static void compute_faces(const Grid& G, const VertexMetric& vm, const OParams& 
         for (int a = 0; a < 3; a++) cellvar[2 + a][c] = W * prim[2 + a][c];
         for (int a = 0; a < 3; a++) cellvar[5 + a][c] = Bc[a][c];
       }
+  }
   const int a1 = (d + 1) % 3, a2 = (d + 2) % 3;
+  unsigned long long n_iters = 0, n_faces = 0;
+  ORACLE_PAR_REDUCE(R, reduction(+ : n_iters, n_faces))
   for (int q2 = 0; q2 < G.N[a2]; q2++)
     for (int q1 = 0; q1 < G.N[a1]; q1++)
       for (int f = G.g; f <= G.g + G.n[d]; f++) {
@@ -1102,6 +1160,8 @@ static void compute_faces(const Grid& G, const VertexMetric& vm, const OParams& 
         p[a2] = q2;
         const long fc = G.at(p);
         FaceInputT<R> in;
+        {
+        FlopScope<R> recon_scope(&g_recon_flops);
         for (int s = 0; s < 2; s++) {
           // left state: upper face value of cell f-1; right state: lower face value of cell f
           const int cell = f - 1 + s;
@@ -1127,19 +1187,26 @@ static void compute_faces(const Grid& G, const VertexMetric& vm, const OParams& 
           for (int a = 0; a < 3; a++) in.u[s][a] = rec[2 + a];
           for (int a = 0; a < 3; a++) in.Bt[s][a] = rec[5 + a];
         }
+        }
         in.Bn = Bf[d][fc];
         const Metric3<R> m = lift<R>(metric_at_face(G, vm, d, p[0], p[1], p[2]));
-        FaceOut<R> o = face_solve<R>(m, in, P.gamma, d, P.flux, P.efield == EFIELD_FCT);
+        FaceOut<R> o;
+        {
+          FlopScope<R> solve_scope(&g_facesolve_flops);
+          o = face_solve<R>(m, in, P.gamma, d, P.flux, P.efield == EFIELD_FCT);
+        }
         for (int v = 0; v < 5; v++) fd.F[v][fc] = o.F[v];
         for (int a = 0; a < 3; a++) fd.vbar[a][fc] = o.vbar[a];
         for (int a = 0; a < 3; a++) fd.Fb[a][fc] = o.Fb[a];
         fd.cmax[fc] = o.cmax;
         fd.cmin[fc] = o.cmin;
-        if (st) {
-          st->speed_iters += o.iters;
-          st->faces++;
-        }
+        n_iters += o.iters;
+        n_faces++;
       }
+  if (st) {
+    st->speed_iters += n_iters;
+    st->faces += n_faces;
+  }
 }
 
 // PPM value at the interface between stencil positions 2 and 3 of f[0..5]: left = upper value of cell 2
@@ -1178,8 +1245,11 @@ static R uct_E(const Grid& G, const FaceDataT<R> fd[3], const std::vector<R> Bf[
       bs[s] = Bf[df][c];
     }
     R vL, vR, BL, BR;
-    ppm_interface(vs, &vL, &vR);
-    ppm_interface(bs, &BL, &BR);
+    {
+      FlopScope<R> scope(&g_edge_ppm_flops);
+      ppm_interface(vs, &vL, &vR);
+      ppm_interface(bs, &BL, &BR);
+    }
     // speeds along dr: the two dr-faces sharing the edge are at p - e_df and p
     int q0[3] = {p[0], p[1], p[2]};
     q0[df] -= 1;
@@ -1217,9 +1287,13 @@ static void rhs(const Grid& G, const VertexMetric& vm, const OParams& P, double 
   face_B(G, U[5], U[6], U[7], Bf);
   centre_B(G, vm, Bf, Bc);
   FaceDataT<R> fd[3];
+  const bool marks = std::is_same<R, Fc>::value && g_rhs_marks;
+  if (marks) g_rhs_marks[0] = g_flops;
   for (int d = 0; d < 3; d++) compute_faces(G, vm, P, prim, Bf, Bc, d, fd[d], st);
+  if (marks) g_rhs_marks[1] = g_flops;
   const int g = G.g;
   // hydro: flux divergence plus sources at interior cells
+  ORACLE_PAR(R)
   for (int k = g; k < g + G.n[2]; k++)
     for (int j = g; j < g + G.n[1]; j++)
       for (int i = g; i < g + G.n[0]; i++) {
@@ -1243,10 +1317,12 @@ static void rhs(const Grid& G, const VertexMetric& vm, const OParams& P, double 
         source_terms<R>(m, dm, pr, src);
         for (int v = 0; v < 5; v++) dU[v][c] = r[v] + src[v];
       }
+  if (marks) g_rhs_marks[2] = g_flops;
   // potentials: G_A and F_Psi at vertices, from the vertex average of the edge A_j (Sec. 3.4)
   std::vector<R> GA(G.size(), R(0.0)), FPsi[3];
   for (int d = 0; d < 3; d++) FPsi[d].assign(G.size(), R(0.0));
   const bool lorenz = (P.gauge == GAUGE_LORENZ);
+  ORACLE_PAR(R)
   for (int k = 1; k <= G.N[2]; k++)
     for (int j = 1; j <= G.N[1]; j++)
       for (int i = 1; i <= G.N[0]; i++) {
@@ -1263,6 +1339,7 @@ static void rhs(const Grid& G, const VertexMetric& vm, const OParams& P, double 
           FPsi[a][c] = m.alp * m.sqrtg * Aup - m.beta[a] * psi;
         }
       }
+  if (marks) g_rhs_marks[3] = g_flops;
   // dA_e/dt = -E_e - d_e G_A on edges
   for (int e = 0; e < 3; e++) {
     int lo[3], hi[3];
@@ -1270,6 +1347,7 @@ static void rhs(const Grid& G, const VertexMetric& vm, const OParams& P, double 
       lo[a] = g;
       hi[a] = (a == e) ? g + G.n[a] - 1 : g + G.n[a];
     }
+    ORACLE_PAR(R)
     for (int k = lo[2]; k <= hi[2]; k++)
       for (int j = lo[1]; j <= hi[1]; j++)
         for (int i = lo[0]; i <= hi[0]; i++) {
@@ -1280,8 +1358,10 @@ static void rhs(const Grid& G, const VertexMetric& vm, const OParams& P, double 
           dU[5 + e][c] = -E - dG;
         }
   }
+  if (marks) g_rhs_marks[4] = g_flops;
   // dPsi/dt = -d_j F_Psi^j - xi alpha Psi at vertices (Eq. recastedScalarPot)
   const double xi = (P.xi_lorenz > 0.0) ? P.xi_lorenz : 1.5 / dt;
+  ORACLE_PAR(R)
   for (int k = g; k <= g + G.n[2]; k++)
     for (int j = g; j <= g + G.n[1]; j++)
       for (int i = g; i <= g + G.n[0]; i++) {
@@ -1305,6 +1385,8 @@ static void con2prim(const Grid& G, const VertexMetric& vm, const OParams& P, do
   face_B(G, U[5], U[6], U[7], Bf);
   centre_B(G, vm, Bf, Bc);
   const int g = G.g;
+  unsigned long long s_iters = 0, s_noble = 0, s_fb = 0, s_atm = 0, s_failed = 0;
+  ORACLE_PAR_REDUCE(double, reduction(+ : s_iters, s_noble, s_fb, s_atm, s_failed))
   for (int k = g; k < g + G.n[2]; k++)
     for (int j = g; j < g + G.n[1]; j++)
       for (int i = g; i < g + G.n[0]; i++) {
@@ -1324,13 +1406,11 @@ static void con2prim(const Grid& G, const VertexMetric& vm, const OParams& P, do
         prim[1][c] = o.press;
         for (int a = 0; a < 3; a++) prim[2 + a][c] = o.vel[a];
         if (flags) flags[c] = (signed char)o.flag;
-        if (stats) {
-          stats->iters += o.iters;
-          if (o.flag == 0) stats->n_noble++;
-          else if (o.flag == 1) stats->n_fallback++;
-          else if (o.flag == 2) stats->n_atm++;
-          else stats->n_failed++;
-        }
+        s_iters += o.iters;
+        if (o.flag == 0) s_noble++;
+        else if (o.flag == 1) s_fb++;
+        else if (o.flag == 2) s_atm++;
+        else s_failed++;
         if (o.reset) {
           // conserved variables reset from the atmosphere primitives with B kept (Sec. 3.6)
           Prim<double> pr;
@@ -1348,6 +1428,13 @@ static void con2prim(const Grid& G, const VertexMetric& vm, const OParams& P, do
           U[4][c] = uc.tau;
         }
       }
+  if (stats) {
+    stats->iters += s_iters;
+    stats->n_noble += s_noble;
+    stats->n_fallback += s_fb;
+    stats->n_atm += s_atm;
+    stats->n_failed += s_failed;
+  }
 }
 
 // Conserved variables at all cells from primitives (initial data, Sec. 3.12 and Eq. cons).
@@ -1356,6 +1443,7 @@ static void prim2con_grid(const Grid& G, const VertexMetric& vm, const OParams& 
   Field Bf[3], Bc[3];
   face_B(G, U[5], U[6], U[7], Bf);
   centre_B(G, vm, Bf, Bc);
+  ORACLE_PAR(double)
   for (int k = 0; k < G.N[2]; k++)
     for (int j = 0; j < G.N[1]; j++)
       for (int i = 0; i < G.N[0]; i++) {
@@ -1406,6 +1494,7 @@ static void rk_stage(const Grid& G, const VertexMetric& vm, const OParams& P, in
   for (int v = 0; v < 9; v++) {
     int lo[3], hi[3];
     owned_range(G, v, lo, hi);
+    ORACLE_PAR(double)
     for (int kk = lo[2]; kk <= hi[2]; kk++)
       for (int j = lo[1]; j <= hi[1]; j++)
         for (int i = lo[0]; i <= hi[0]; i++) {
@@ -1749,6 +1838,17 @@ extern "C" {
 
 int oracle_abi_version(void) { return 1; }
 
+// Threads of the OpenMP loops (1 = serial); returns the count in effect.
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 void oracle_ghost_fill_state(const OBlock* b, double* const* U) {
   Grid G(*b);
   ghost_fill_state(G, U);
@@ -2057,6 +2157,151 @@ void oracle_recon_flops(int scheme, const double* a5, double* out) {
   out[1] = (double)(g_flops.mul - before.mul);
   out[2] = (double)(g_flops.div - before.div);
   out[3] = (double)(g_flops.sqrt - before.sqrt);
+}
+
+// Algorithmic flop count of one RK stage (Sec. 3.12 workflow) with the flop-counting scalar, part by part:
+// ghost fill of the state (linear extrapolation of A), recovery over the interior cells (face and centre field,
+// undensitisation, Noble / Palenzuela / atmosphere reset), ghost fill of the primitives, the right-hand side
+// (faces: u = W v, reconstruction and face solve of the three directions; cells: flux divergence and sources;
+// potentials at vertices; edge fields and dA/dt; dPsi/dt) and the RK4 combine of stage `stage` (0..3) over the
+// owned entries.  Interpolation of the frozen metric is not counted (an input of every step).  U is the stage
+// state (its ghosts are filled here, on a copy), prim the recovery's guess.  out (60 values): [0] interior
+// cells; then (add, mul, div, sqrt) of: [1] state ghost fill, [5] recovery, [9] primitive ghost fill, [13]
+// faces, [17] cells, [21] potentials, [25] edges, [29] Psi, [33] combine, [45] the right-hand side's own
+// recomputation of the face and centre field (the recovery's are reused by an implementation, so it is
+// reported apart); [37] speed iterations, [38] faces solved, [39] flops inside the speed Newton loops, [40]
+// Noble iterations, [41..44] cells recovered by Noble / Palenzuela / atmosphere / both failed; flops (all
+// kinds) of [49] u = W v as the faces part forms it (once per direction), [50] the reconstruction as the faces
+// part forms it (twice per cell), [51] the face solves, [52] the edge fields' PPM interfaces (twice per face
+// value), [53] the recovery's face and centre field; [54..59] unused.
+void oracle_stage_flops(const OParams* p, const OBlock* b, const double* const* metric, double* const* U,
+                        double* const* prim, int stage, double dt, double* out) {
+  Grid G(*b);
+  VertexMetric vm = vmetric(metric);
+  for (int q = 0; q < 60; q++) out[q] = 0.0;
+  g_cellvar_flops = g_recon_flops = g_facesolve_flops = g_edge_ppm_flops = 0;
+  std::vector<Fc> Uv[9], Pv[5], kv[9];
+  Fc *Up[9], *Pp[5], *kp[9];
+  for (int v = 0; v < 9; v++) {
+    Uv[v].resize(G.size());
+    kv[v].assign(G.size(), Fc(0.0));
+    for (long c = 0; c < G.size(); c++) Uv[v][c] = Fc(U[v][c]);
+    Up[v] = Uv[v].data();
+    kp[v] = kv[v].data();
+  }
+  for (int v = 0; v < 5; v++) {
+    Pv[v].resize(G.size());
+    for (long c = 0; c < G.size(); c++) Pv[v][c] = Fc(prim[v][c]);
+    Pp[v] = Pv[v].data();
+  }
+  auto put = [&](int at, const Flops& a, const Flops& z) {
+    out[at] = (double)(z.add - a.add);
+    out[at + 1] = (double)(z.mul - a.mul);
+    out[at + 2] = (double)(z.div - a.div);
+    out[at + 3] = (double)(z.sqrt - a.sqrt);
+  };
+  Flops f0 = g_flops;
+  ghost_fill_state<Fc>(G, Up);
+  Flops f1 = g_flops;
+  put(1, f0, f1);
+  // recovery, as con2prim does it, in the counting scalar
+  std::vector<Fc> Bf[3], Bc[3];
+  face_B<Fc>(G, Up[5], Up[6], Up[7], Bf);
+  centre_B<Fc>(G, vm, Bf, Bc);
+  out[53] = (double)(flops_total(g_flops) - flops_total(f1));
+  const int g = G.g;
+  double iters = 0, nflag[4] = {0, 0, 0, 0};
+  for (int k = g; k < g + G.n[2]; k++)
+    for (int j = g; j < g + G.n[1]; j++)
+      for (int i = g; i < g + G.n[0]; i++) {
+        const long c = G.at(i, j, k);
+        const Metric3<Fc> m = lift<Fc>(metric_at_centre(G, vm, i, j, k));
+        C2PIn in;
+        in.Dtilde = Up[0][c].v;
+        in.D = (Up[0][c] / m.sqrtg).v;
+        for (int a = 0; a < 3; a++) in.S[a] = (Up[1 + a][c] / m.sqrtg).v;
+        in.tau = (Up[4][c] / m.sqrtg).v;
+        for (int a = 0; a < 3; a++) in.B[a] = Bc[a][c].v;
+        in.guess_rho = Pp[0][c].v;
+        in.guess_press = Pp[1][c].v;
+        for (int a = 0; a < 3; a++) in.guess_vel[a] = Pp[2 + a][c].v;
+        C2POut o = c2p_cell<Fc>(m, in, *p);
+        iters += o.iters;
+        nflag[o.flag == 0 ? 0 : o.flag == 1 ? 1 : o.flag == 2 ? 2 : 3] += 1;
+        Pp[0][c] = Fc(o.rho);
+        Pp[1][c] = Fc(o.press);
+        for (int a = 0; a < 3; a++) Pp[2 + a][c] = Fc(o.vel[a]);
+        if (o.reset) {
+          Prim<Fc> pr;
+          pr.rho = Fc(o.rho);
+          pr.press = Fc(o.press);
+          pr.eps = pr.press / (Fc(p->gamma_atm - 1.0) * pr.rho);
+          for (int a = 0; a < 3; a++) {
+            pr.vel[a] = Fc(0.0);
+            pr.B[a] = Bc[a][c];
+          }
+          Comoving<Fc> cm = comoving(m, pr);
+          Cons<Fc> uc = prim2con(m, pr, cm);
+          Up[0][c] = uc.D;
+          for (int a = 0; a < 3; a++) Up[1 + a][c] = uc.S[a];
+          Up[4][c] = uc.tau;
+        }
+      }
+  Flops f2 = g_flops;
+  put(5, f1, f2);
+  ghost_fill_prims<Fc>(G, Pp);
+  Flops f3 = g_flops;
+  put(9, f2, f3);
+  // right-hand side, phase by phase
+  Flops marks[5];
+  g_rhs_marks = marks;
+  const unsigned long long loop0 = g_speed_loop_flops;
+  RhsStats st = {0, 0};
+  rhs<Fc>(G, vm, *p, dt, Up, Pp, kp, &st);
+  g_rhs_marks = nullptr;
+  Flops f4 = g_flops;
+  put(45, f3, marks[0]);
+  put(13, marks[0], marks[1]);
+  put(17, marks[1], marks[2]);
+  put(21, marks[2], marks[3]);
+  put(25, marks[3], marks[4]);
+  put(29, marks[4], f4);
+  // RK4 combine of this stage over the owned entries (as rk_stage forms it)
+  static const double cnext[3] = {0.5, 0.5, 1.0};
+  static const double bw[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  for (int v = 0; v < 9; v++) {
+    int lo[3], hi[3];
+    owned_range(G, v, lo, hi);
+    for (int kk = lo[2]; kk <= hi[2]; kk++)
+      for (int j = lo[1]; j <= hi[1]; j++)
+        for (int i = lo[0]; i <= hi[0]; i++) {
+          const long c = G.at(i, j, kk);
+          const Fc k1 = kp[v][c], un = Up[v][c];
+          Fc acc = Fc(0.0), next;
+          if (stage == 0) {
+            acc = Fc(bw[0]) * Fc(dt) * k1;
+            next = un + Fc(cnext[0]) * Fc(dt) * k1;
+          } else if (stage < 3) {
+            acc = acc + Fc(bw[stage]) * Fc(dt) * k1;
+            next = un + Fc(cnext[stage]) * Fc(dt) * k1;
+          } else {
+            next = un + acc + Fc(bw[3]) * Fc(dt) * k1;
+          }
+          (void)next;
+        }
+  }
+  Flops f5 = g_flops;
+  put(33, f4, f5);
+  out[0] = (double)G.n[0] * G.n[1] * G.n[2];
+  out[37] = (double)st.speed_iters;
+  out[38] = (double)st.faces;
+  out[39] = (double)(g_speed_loop_flops - loop0);
+  out[40] = iters;
+  for (int q = 0; q < 4; q++) out[41 + q] = nflag[q];
+  out[49] = (double)g_cellvar_flops;
+  out[50] = (double)g_recon_flops;
+  out[51] = (double)g_facesolve_flops;
+  out[52] = (double)g_edge_ppm_flops;
 }
 
 // Pointwise helpers for the pins of the test suite.
