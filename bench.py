@@ -1,17 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 GRMHD RK stage: FP64 zone-updates per second per RK stage.
 
-Workload: the 128^3 block of WENO-Z + HLLE over the frozen isotropic Schwarzschild slice (M = 0.1, centre at
-(-1, 0, 0)) with Balsara test-1 states split along x and copy BCs; one step = one classical RK4 step (4 stages:
-ghost fill, recovery, reconstruction, face solve, UCT, potentials, sources, combine).  Inputs are seeded and
-synthetic; the frozen-metric geometry is derived once before timing (asterx_prepare).  The state lives in HBM
-(about 0.2 GB per state copy and 3.9 GB of workspace, far above the 129 MB L2), so no L2 flush is needed.
+Workload: the 256^3 block of the rotating magnetised torus with an axial jet (Lorentz factor up to 7) in the
+frozen isotropic Schwarzschild slice (M = 0.1, centre at (-1, 0, 0)), WENO-Z + HLLE + UCT, ideal gas Gamma = 4/3,
+copy BCs, atmosphere floor 1e-10; one step = one classical RK4 step (4 stages: ghost fill, recovery,
+reconstruction, face solve, UCT, potentials, sources, combine).  Inputs are seeded and synthetic; the
+frozen-metric geometry is derived once before timing (asterx_prepare).  The state lives in HBM (about 1.3 GB per
+state copy and 32 GB of workspace, far above the 129 MB L2), so no L2 flush is needed.  The 128^3 block of
+Balsara test-1 states in the same slice (WENO-Z, Gamma = 5/3) is timed beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 With N > 1 it is launched by torch.distributed.run; every rank runs an independent replica of the block
 (no data exchange: the path has none) and rank 0 prints one JSON line.  --impl reference times the CPU oracle
-(the reference implementation of this tier) on a bounded slab of the same workload.
+(the reference implementation of this tier) on all host cores on a bounded slab of the same workload.
 """
 from __future__ import annotations
 
@@ -19,6 +21,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -30,14 +33,17 @@ if ROOT not in sys.path:
 
 METRIC = "FP64 GRMHD zone-updates/s per RK stage; batched-vs-single and adjoint/forward time"
 UNIT = "zone-updates/s"
-WORKLOAD = ("128^3 block + 3 ghosts, FP64, ideal gas Gamma=5/3, WENO-Z + HLLE + UCT, Noble2D/Palenzuela c2p, "
-            "Balsara-1 Riemann data split at x=0 (Bx=0.5, By=+-1), frozen isotropic Schwarzschild M=0.1 centred "
-            "0.5 outside the box, copy BCs, one RK4 step = 4 stages")
+WORKLOAD = ("256^3 block + 3 ghosts, FP64, ideal gas Gamma=4/3, WENO-Z + HLLE + UCT, Noble2D/Palenzuela c2p, "
+            "rotating magnetised torus rho=max(1e-2 exp(-(R-0.3)^2/0.01-z^2/0.01),1e-10), p=0.1 rho^(4/3), "
+            "Omega=0.5, axial jet W<=7 (seed 105), frozen isotropic Schwarzschild M=0.1 centred 0.5 outside the "
+            "box, copy BCs, one RK4 step = 4 stages")
+WORKLOAD_128 = ("128^3 block + 3 ghosts, FP64, Gamma=5/3, WENO-Z + HLLE + UCT, Balsara-1 Riemann data split at x=0 "
+                "(Bx=0.5, By=+-1), frozen isotropic Schwarzschild M=0.1 (seed 102)")
 # kernels the library launches per RK stage: 3 + 3 ghost sweeps, 2 field kernels, recovery, velocity, 3 x
 # (reconstruction + face solve), vertex potentials, 3 edge kernels, scalar potential, cells
 LAUNCHES_PER_STAGE = 28
-# nominal FP64 peak: 152 SMs x 2 DFMA/clock/SM x 2 flops x 2.07 GHz (unit counts and clock of the GB300 recipe)
-FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 units: 2 DFMA per clock per SM (GB300), 2 flops each
+DFMA_PER_CLOCK_PER_SM = 2
 
 
 def parse():
@@ -46,7 +52,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--n", type=int, default=128, help="cells per axis of the block (default: the 128^3 workload)")
+    ap.add_argument("--n", type=int, default=256, help="cells per axis of the torus block (default: the 256^3 workload)")
+    ap.add_argument("--balsara-n", type=int, default=128,
+                    help="cells per axis of the Balsara block (timed beside the torus; also the tiled and "
+                         "two-level measurements)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch measurement")
     ap.add_argument("--batch-blocks", type=int, default=512)
@@ -147,10 +156,9 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(power) if power else None}
 
 
-def read_face_flops():
-    """Algorithmic FP64 flops per face of the face-solve kernel, counted by the oracle's flop-counting scalar on
-    this workload (profiles/face_flops_balsara_schwarzschild_128.txt, written by oracle/count_face_flops.py)."""
-    path = os.path.join(ROOT, "profiles", "face_flops_balsara_schwarzschild_128.txt")
+def read_kv(name):
+    """key = value lines of a committed profile summary (None if the file is absent)."""
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     vals = {}
@@ -159,18 +167,40 @@ def read_face_flops():
             if "=" in line and not line.startswith("#"):
                 k, v = line.split("=", 1)
                 vals[k.strip()] = float(v.split()[0])
-    return vals.get("flops_per_face")
+    return vals
 
 
-def read_traffic():
-    path = os.path.join(ROOT, "profiles", "faces_balsara_schwarzschild_128_traffic.txt")
-    if not os.path.exists(path):
-        return None
-    with open(path) as f:
-        for line in f:
-            if line.startswith("dram_bytes_per_launch") and "=" in line:
-                return float(line.split("=", 1)[1].split()[0])
-    return None
+def read_stage_flops(n):
+    """Algorithmic FP64 flops per zone-stage and per kernel unit on the n^3 torus-and-jet workload, counted by the
+    oracle's flop-counting scalar (written by oracle/count_stage_flops.py)."""
+    return read_kv(f"stage_flops_torus_jet_{n}.txt")
+
+
+def read_traffic(n):
+    """DRAM bytes of one face-solve launch on the n^3 torus workload (from an ncu capture, scaled by faces)."""
+    v = read_kv(f"faces_torus_jet_{n}_traffic.txt")
+    return v.get("dram_bytes_per_launch") if v else None
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                    name = line.split(":", 1)[1].strip()
+                    if name:
+                        return name
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def slab_workload(w_full, ny, nz):
@@ -180,9 +210,11 @@ def slab_workload(w_full, ny, nz):
     return W.sub_block(w_full, lo, (n[0], ny, nz), name="slab")
 
 
-def cpu_oracle_steps(w, steps):
-    """Times `steps` oracle RK4 steps on workload w; returns seconds per step (single host thread)."""
+def cpu_oracle_steps(w, steps, threads):
+    """Times `steps` oracle RK4 steps on workload w with `threads` OpenMP threads; returns (seconds per step,
+    threads in effect)."""
     import oracle as O
+    used = O.set_threads(threads)
     U, P = O.initial_state(w)
     M = O.metric_array(w)
     O.ghost_fill_state(w, U)
@@ -190,17 +222,27 @@ def cpu_oracle_steps(w, steps):
     for _ in range(steps):
         U, _ = O.rk4_step(w, M, U, P)
         O.ghost_fill_state(w, U)
-    return (time.perf_counter() - t0) / steps
+    return (time.perf_counter() - t0) / steps, used
 
 
 def cpu_baseline(w_full):
-    ny = nz = 16
-    w = slab_workload(w_full, ny, nz)
-    sec = cpu_oracle_steps(w, 1)
-    cells = w.interior_cells
-    return {"value": cells * 4 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one RK4 step of the {w.n[0]}x{ny}x{nz} central slab of the same workload "
-                      f"({cells} cells, {sec:.1f} s, single host thread, g++ -O2)"}
+    """The oracle as it stands on the host: one RK4 step of a central x-slab of the workload on one core, and of a
+    wider slab on every core (OpenMP over (k, j) pencils)."""
+    model, cores = cpu_model(), host_cores()
+    out = {"kind": "oracle", "unit": UNIT, "cpu_model": model, "nproc": cores}
+    runs = []
+    for threads, ny in ((1, 8), (cores, 24)):
+        w = slab_workload(w_full, ny, ny)
+        sec, used = cpu_oracle_steps(w, 1, threads)
+        cells = w.interior_cells
+        runs.append({"cores": used, "value": cells * 4 / sec, "seconds": sec,
+                     "sample": f"one RK4 step of the central {w.n[0]}x{ny}x{ny} x-slab of the workload ({cells} "
+                               f"cells) on {used} thread(s), g++ -O2 -fopenmp"})
+    out["one_core"], out["all_cores"] = runs
+    out["value"] = runs[1]["value"]
+    out["cores"] = runs[1]["cores"]
+    out["sample"] = runs[1]["sample"] + f"; one core: {runs[0]['value']:.4g} {UNIT}"
+    return out
 
 
 def _upload_block(w, dev):
@@ -292,7 +334,7 @@ def run_batched(args, dev, stream):
 
 
 def run_tiled(args, dev, stream, single_ms):
-    """The benchmark's 128^3 domain cut into 2x2x2 blocks of 64^3 and 4x4x4 blocks of 32^3, advanced by the batched
+    """The 128^3 Balsara domain cut into 2x2x2 blocks of 64^3 and 4x4x4 blocks of 32^3, advanced by the batched
     launch with same-level ghost exchange between the blocks, against the single 128^3 block (single_ms)."""
     import numpy as np
     import torch
@@ -300,12 +342,12 @@ def run_tiled(args, dev, stream, single_ms):
     from paper_2406_11669_gb300 import asterx as A
     from paper_2406_11669_gb300 import workloads as W
 
-    w = W.balsara_schwarzschild(n=(args.n,) * 3)
+    w = W.balsara_schwarzschild(n=(args.balsara_n,) * 3)
     M, U, P = _upload_block(w, dev)
     out = {}
     for k in (2, 4):
-        m = args.n // k
-        cuts = [list(range(0, args.n + 1, m))] * 3
+        m = args.balsara_n // k
+        cuts = [list(range(0, args.balsara_n + 1, m))] * 3
         entries = []
         for bz in range(k):
             for by in range(k):
@@ -344,7 +386,7 @@ def run_tiled(args, dev, stream, single_ms):
 
 
 def run_refined(args, dev, stream, single_ms):
-    """Two refinement levels on the benchmark workload: the 128^3 block plus a fine block of half the spacing over
+    """Two refinement levels on the 128^3 Balsara workload: the 128^3 block plus a fine block of half the spacing over
     its central 64^3 coarse cells (128^3 fine cells; fine data prolonged from the coarse level, the Schwarzschild
     metric evaluated at the fine vertices), stepped together with the fine time step (prolongation of each coarse
     stage state to the fine ghosts, restriction after the step).  Compared with two plain steps of 128^3 blocks.
@@ -356,13 +398,13 @@ def run_refined(args, dev, stream, single_ms):
     from paper_2406_11669_gb300 import asterx as A
     from paper_2406_11669_gb300 import workloads as W
 
-    w = W.balsara_schwarzschild(n=(args.n,) * 3)
+    w = W.balsara_schwarzschild(n=(args.balsara_n,) * 3)
     M, U, P = _upload_block(w, dev)
     sc = A.Solver.for_workload(w, device=dev)
     sc.prepare(M)
     sc.fill_ghosts(U)
     sc.prim2con(U, P)
-    Lc, m = args.n // 4, args.n // 2
+    Lc, m = args.balsara_n // 4, args.balsara_n // 2
     nf = (2 * m,) * 3
     x0f = tuple(w.x0[d] + Lc * w.dx[d] for d in range(3))
     dxf = tuple(h / 2 for h in w.dx)
@@ -411,7 +453,7 @@ def run_refined(args, dev, stream, single_ms):
     updates_sub = 4 * w.interior_cells + 8 * int(np.prod(nf))  # zone-stage updates per coarse step
     del sc, sf, M, U, P, Mf, Uf, Pf
     torch.cuda.empty_cache()
-    return {"coarse_n": args.n, "fine_box_coarse_cells": m, "fine_n": nf[0], "ms_per_step": ms,
+    return {"coarse_n": args.balsara_n, "fine_box_coarse_cells": m, "fine_n": nf[0], "ms_per_step": ms,
             "value": cells * 4 / (ms / 1e3), "unit": UNIT, "vs_two_single_steps": 2.0 * single_ms / ms,
             "finite": finite,
             "subcycled": {"ms_per_coarse_step": ms_sub, "value": updates_sub / (ms_sub / 1e3), "unit": UNIT,
@@ -590,26 +632,72 @@ def run_variants(args, s, U, P, w, dev, stream):
 
 
 def run_reference(args):
+    """The oracle as it stands, on every host core, each step one RK4 step of the central n x 16 x 16 x-slab of
+    the workload (the slab crosses the jet and both sides of the torus)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     from paper_2406_11669_gb300 import workloads as W
-    w_full = W.balsara_schwarzschild(n=(args.n,) * 3)
-    w = slab_workload(w_full, 8, 8)
-    sec_w = cpu_oracle_steps(w, max(args.warmup, 0)) if args.warmup > 0 else 0.0
-    del sec_w
-    sec = cpu_oracle_steps(w, args.steps)
+    w_full = W.torus_jet(n=(args.n,) * 3)
+    w = slab_workload(w_full, 16, 16)
+    del w_full
+    cores = host_cores()
+    if args.warmup > 0:
+        cpu_oracle_steps(w, args.warmup, cores)
+    sec, used = cpu_oracle_steps(w, args.steps, cores)
     cells = w.interior_cells
     value = cells * 4 / sec
-    sample = (f"each step: one oracle RK4 step of the {w.n[0]}x8x8 central slab of the workload ({cells} cells), "
-              f"single host thread")
+    sample = (f"each step: one oracle RK4 step of the central {w.n[0]}x16x16 x-slab of the workload ({cells} "
+              f"cells) on {used} host threads ({cpu_model()})")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "sample_cells": cells},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+                            "cpu_model": cpu_model(), "nproc": cores},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def time_steps(s, U, P, dt, steps, stream, dev, stats=None):
+    """CUDA-event time (ms) of `steps` RK4 steps of solver s on the launching stream."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        s.rk4_step(U, P, dt, stats=stats)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1)
+
+
+def run_balsara(args, dev, stream):
+    """The 128^3 Balsara block in the same slice (WENO-Z): rate per RK stage and its face-kernel launch time."""
+    import torch
+
+    from paper_2406_11669_gb300 import asterx as A
+    from paper_2406_11669_gb300 import workloads as W
+
+    w = W.balsara_schwarzschild(n=(args.balsara_n,) * 3)
+    M, U, P = _upload_block(w, dev)
+    s = A.Solver.for_workload(w, device=dev)
+    s.prepare(M)
+    s.fill_ghosts(U)
+    s.prim2con(U, P)
+    for _ in range(max(args.warmup, 1)):
+        s.rk4_step(U, P, w.dt)
+    torch.cuda.synchronize(dev)
+    steps = max(3, args.steps)
+    A.profile_enable(steps * 4 * 3)
+    ms = time_steps(s, U, P, w.dt, steps, stream, dev)
+    nface, face_ms = A.profile_read()
+    A.profile_disable()
+    del s, M, U, P
+    torch.cuda.empty_cache()
+    return {"workload": WORKLOAD_128, "ms_per_step": ms / steps, "steps": steps,
+            "value": w.interior_cells * 4 * steps / (ms / 1e3), "unit": UNIT,
+            "face_launch_ms": face_ms / max(nface, 1), "faces_per_launch": (w.n[0] + 1) * (w.n[0] + 6) ** 2}
 
 
 def run_ours(args):
@@ -625,8 +713,10 @@ def run_ours(args):
         dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
 
-    w = W.balsara_schwarzschild(n=(args.n,) * 3)
+    w = W.torus_jet(n=(args.n,) * 3)
     s = A.Solver.for_workload(w, device=dev)
     M = torch.from_numpy(np.ascontiguousarray(np.stack([w.metric[k] for k in W.METRIC_NAMES]))).to(dev)
     P0 = np.ascontiguousarray(np.stack([w.prims[k] for k in W.PRIM_NAMES]))
@@ -636,6 +726,7 @@ def run_ours(args):
     U[6] = torch.from_numpy(w.A["Ay"]).to(dev)
     U[7] = torch.from_numpy(w.A["Az"]).to(dev)
     P = torch.from_numpy(P0).to(dev)
+    del P0
     s.fill_ghosts(U)
     s.prim2con(U, P)
     stats = torch.zeros(5, dtype=torch.int64, device=dev)
@@ -651,16 +742,9 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        s.rk4_step(U, P, w.dt, stats=stats)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
+    ms = time_steps(s, U, P, w.dt, args.steps, stream, dev, stats=stats)
     clk = clocks.stop()
     barrier(world)
-    ms = e0.elapsed_time(e1)
     nface, face_ms = A.profile_read()
     A.profile_disable()
     ms_max = max_over_ranks(ms, world)
@@ -689,9 +773,11 @@ def run_ours(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e_value = world * cells * 4 * args.steps / e2e_s
     io_bytes = (9 + 5) * U[0].numel() * 8
+    del hU, hP, dU2, dP2
+    torch.cuda.empty_cache()
 
-    # FP64 FMA throughput measured on this GPU (context for the nominal peak)
-    blocks, threads, iters = 152 * 8, 256, 4096
+    # FP64 FMA throughput measured on this GPU: the peak of the roofline
+    blocks, threads, iters = sms * 8, 256, 4096
     out = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
     A.dfma_probe(out, blocks, threads, 64)
     torch.cuda.synchronize(dev)
@@ -702,43 +788,67 @@ def run_ours(args):
     p1.record(stream)
     torch.cuda.synchronize(dev)
     dfma_tflops = blocks * threads * iters * 8 * 8 * 2 / (p0.elapsed_time(p1) / 1e3) / 1e12
+    del out
+    max_mhz = clk.get("sm_max_mhz") or 2070.0
+    nominal_tflops = sms * DFMA_PER_CLOCK_PER_SM * 2 * max_mhz * 1e6 / 1e12
 
     if rank != 0:
         return
     faces_per_launch = (args.n + 1) * (args.n + 6) ** 2
-    flops_per_face = read_face_flops()
+    sf = read_stage_flops(args.n) or {}
+    flops_per_face = sf.get("face_solve_flops_per_face")
     face_avg_ms = face_ms / max(nface, 1)
     roofline = {"bound": "alu", "kernel": "k_single<Faces<D>> (face solve: prim->cons, fluxes, quartic speeds, HLLE)",
-                "unit": "TFLOP/s", "peak": FP64_NOMINAL_TFLOPS,
-                "peak_kind": "nominal FP64 (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)",
-                "peak_measured_dfma": dfma_tflops, "launch_ms": face_avg_ms, "launches": nface,
-                "faces_per_launch": faces_per_launch, "flops_per_face": flops_per_face,
-                "achieved": None, "frac": None, "traffic": read_traffic(),
-                "face_share_of_step": face_ms / (ms * 1.0) if ms > 0 else None}
+                "unit": "TFLOP/s", "peak": dfma_tflops,
+                "peak_kind": "measured: FP64 FMA probe on this GPU (MEASURED_PEAKS.json has no FP64 entry)",
+                "peak_nominal": nominal_tflops,
+                "peak_nominal_kind": f"{sms} SMs (device) x {DFMA_PER_CLOCK_PER_SM} DFMA/clk x 2 flop x {max_mhz:.0f} MHz",
+                "launch_ms": face_avg_ms, "launches": nface, "faces_per_launch": faces_per_launch,
+                "flops_per_face": flops_per_face,
+                "flops_per_face_literal": sf.get("face_solve_flops_per_face_literal"),
+                "achieved": None, "frac": None, "traffic": read_traffic(args.n),
+                "face_share_of_step": face_ms / ms if ms > 0 else None}
     if flops_per_face:
         achieved = flops_per_face * faces_per_launch / (face_avg_ms / 1e3) / 1e12
         roofline["achieved"] = achieved
-        roofline["frac"] = achieved / FP64_NOMINAL_TFLOPS
+        roofline["frac"] = achieved / dfma_tflops
+    step_roofline = None
+    if sf.get("flops_per_zone_stage"):
+        fz = sf["flops_per_zone_stage"]
+        ach = fz * value / world / 1e12
+        step_roofline = {"bound": "alu", "unit": "TFLOP/s", "flops_per_zone_stage": fz,
+                         "flops_per_zone_stage_literal_speed_iterations":
+                             sf.get("flops_per_zone_stage_literal_speed_iterations"),
+                         "achieved": ach, "peak": dfma_tflops, "frac": ach / dfma_tflops,
+                         "bytes_per_zone_stage": 568, "hbm_gbs": 568 * value / world / 1e9}
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
               "config": {"workload": WORKLOAD, "interior_cells": cells, "stages_per_step": 4,
                          "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush)",
-                         "resident_bytes": int(s.ws_bytes + 2 * U.numel() * 8 + P.numel() * 8 + M.numel() * 8)},
+                         "resident_bytes": int(s.ws_bytes + 2 * U.numel() * 8 + P.numel() * 8 + M.numel() * 8),
+                         "sm_count": sms},
               "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
                       "d2h_bytes_per_step": io_bytes},
               "gpu_launches": LAUNCHES_PER_STAGE * 4 * args.steps,
-              "clocks": clk, "roofline": roofline, "c2p_counters_timed": c2p, "state_finite": finite}
+              "clocks": clk, "roofline": roofline, "step_roofline": step_roofline,
+              "c2p_counters_timed": {"n_noble": c2p[0], "n_fallback": c2p[1], "n_atm": c2p[2], "n_failed": c2p[3],
+                                     "noble_iters": c2p[4]},
+              "state_finite": finite}
     if not args.no_coupling:
         result["coupling"] = run_coupling(args, s, U, P, M, w, dev, stream)
     if not args.no_variants:
         result["variants"] = run_variants(args, s, U, P, w, dev, stream)
+    del s, U, P, M
+    torch.cuda.empty_cache()
+    b128 = run_balsara(args, dev, stream)
+    result["balsara_128"] = b128
     if not args.no_batched:
         result["batched"] = run_batched(args, dev, stream)
     if not args.no_tiled:
-        result["tiled"] = run_tiled(args, dev, stream, ms_max / args.steps)
+        result["tiled"] = run_tiled(args, dev, stream, b128["ms_per_step"])
     if not args.no_refined:
-        result["refined"] = run_refined(args, dev, stream, ms_max / args.steps)
+        result["refined"] = run_refined(args, dev, stream, b128["ms_per_step"])
     if not args.no_adjoint:
         result["adjoint"] = run_adjoint(args, dev, stream)
     if not args.no_cpu_baseline:

@@ -370,7 +370,7 @@ __global__ void k_geom_vertex(Blk b, CF16 m, double* __restrict__ vg) {
 
 static int grid_for(long count, int threads) {
   long blocks = (count + threads - 1) / threads;
-  const long cap = 152L * 32;
+  const long cap = 32L * device_sm_count();
   return (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
 }
 

@@ -142,6 +142,10 @@ cudaError_t profile_enable(int cap);
 void profile_disable();
 cudaError_t profile_read(int* launches, double* total_ms);
 
+// streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, read once per device);
+// grid caps of grid-stride kernels are multiples of it
+int device_sm_count();
+
 // FP64 fused multiply-add throughput probe (measurement helper)
 cudaError_t launch_dfma_probe(double* out, int blocks, int threads, long iters, cudaStream_t s);
 // the quartic solver's Newton-correction reciprocal on n values (measurement helper)

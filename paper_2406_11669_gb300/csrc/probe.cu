@@ -1,9 +1,25 @@
 // FP64 fused multiply-add throughput probe: the ALU roofline of an FP64-bound kernel is the rate at which
 // the SMs retire DFMA.  Eight independent chains per thread keep the FP64 pipe busy regardless of latency.
+#include <mutex>
+
 #include "kernels.h"
 #include "physics.cuh"
 
 namespace asterx {
+
+int device_sm_count() {
+  static std::mutex mu;
+  static int count[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  std::lock_guard<std::mutex> lock(mu);
+  if (count[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+    count[dev] = n;
+  }
+  return count[dev];
+}
 
 __global__ void k_dfma_probe(double* out, long iters) {
   const double s = 1.0 + 1e-12 * (threadIdx.x + 1);
@@ -34,7 +50,8 @@ __global__ void k_newton_rcp(const double* __restrict__ d, double* __restrict__ 
 
 cudaError_t launch_newton_rcp(const double* d, double* out, long n, cudaStream_t s) {
   long blocks = (n + 255) / 256;
-  if (blocks > 152L * 16) blocks = 152L * 16;
+  const long cap = 16L * device_sm_count();
+  if (blocks > cap) blocks = cap;
   k_newton_rcp<<<(int)blocks, 256, 0, s>>>(d, out, n);
   return cudaGetLastError();
 }

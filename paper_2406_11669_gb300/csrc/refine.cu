@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(256) k_subcycle_combine(CombineArgs a) {
 
 int refine_grid(long count) {
   long blocks = (count + 127) / 128;
-  if (blocks > 152L * 64) blocks = 152L * 64;
+  if (blocks > 64L * device_sm_count()) blocks = 64L * device_sm_count();
   return (int)(blocks < 1 ? 1 : blocks);
 }
 
@@ -310,7 +310,7 @@ cudaError_t launch_subcycle_combine(const Blk& b, const int lo[3], const int hi[
   a.out = out;
   for (int i = 0; i < 4; i++) a.beta[i] = beta[i];
   long blocks = (count + 255) / 256;
-  if (blocks > 152L * 8) blocks = 152L * 8;
+  if (blocks > 8L * device_sm_count()) blocks = 8L * device_sm_count();
   k_subcycle_combine<<<dim3((unsigned)blocks, 9), 256, 0, s>>>(a);
   return cudaGetLastError();
 }

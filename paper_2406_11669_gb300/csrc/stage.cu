@@ -23,7 +23,7 @@ namespace asterx {
 
 static __host__ int grid_for(long count, int threads) {
   long blocks = (count + threads - 1) / threads;
-  const long cap = 152L * 64;
+  const long cap = 64L * device_sm_count();
   return (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
 }
 

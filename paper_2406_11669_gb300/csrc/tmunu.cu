@@ -118,7 +118,7 @@ cudaError_t launch_tmunu(const Blk& b, const Ws& w, double gamma, const CF16& m,
   a.gfac = gamma / (gamma - 1.0);
   const long count = (long)(b.n[0] + 1) * (b.n[1] + 1) * (b.n[2] + 1);
   long blocks = (count + 127) / 128;
-  if (blocks > 152L * 64) blocks = 152L * 64;
+  if (blocks > 64L * device_sm_count()) blocks = 64L * device_sm_count();
   k_tmunu<<<(int)blocks, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
