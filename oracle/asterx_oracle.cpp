@@ -155,7 +155,7 @@ struct OParams {
   int c2p_maxiter;
   int brent_maxiter;
   double W_max;       // Lorentz-factor cap used on failure paths of the recovery
-  int recon;          // 0 minmod, 1 PPM, 2 WENO-Z
+  int recon;          // 0 minmod, 1 PPM, 2 WENO-Z, 3 MP5
   int gauge;          // 0 generalised Lorenz, 1 algebraic
   double xi_lorenz;   // Lorenz damping; 0 => 1.5/dt
   int use_fallback;   // Palenzuela fallback on/off
@@ -175,7 +175,7 @@ struct OStats {
   unsigned long long n_noble, n_fallback, n_atm, n_failed, iters;
 };
 
-enum { RECON_MINMOD = 0, RECON_PPM = 1, RECON_WENOZ = 2 };
+enum { RECON_MINMOD = 0, RECON_PPM = 1, RECON_WENOZ = 2, RECON_MP5 = 3 };
 enum { FLUX_HLLE = 0, FLUX_LXF = 1 };
 enum { EFIELD_UCT = 0, EFIELD_FCT = 1 };
 enum { BC_PERIODIC = 0, BC_COPY = 1 };
@@ -551,9 +551,52 @@ template <class R> void recon_wenoz(const R a[5], R* aL, R* aR) {
   *aL = wenoz_upper(a[4], a[3], a[2], a[1], a[0]);
 }
 
+// MP5 (Suresh & Huynh 1997, the monotonicity-preserving fifth-order scheme; Sec. 3.3 lists it among the
+// reconstruction methods): the fifth-order interface value from the five averages, kept where it lies between
+// the cell value and the monotonicity-preserving bound a_i + minmod(a_{i+1} - a_i, alpha (a_i - a_{i-1}))
+// (alpha = 4); elsewhere moved to the nearer end of the interval the curvature-based bounds allow (the
+// median of the value and the interval's ends).  Value at the upper face of the middle cell of s[0..4]; the
+// lower face is the same formula on the mirrored stencil.
+template <class R> R minmod4(R w, R x, R y, R z) {
+  const R zero = R(0.0);
+  if (w > zero && x > zero && y > zero && z > zero) return rmin(rmin(w, x), rmin(y, z));
+  if (w < zero && x < zero && y < zero && z < zero) return rmax(rmax(w, x), rmax(y, z));
+  return zero;
+}
+
+template <class R> R median3(R x, R lo, R hi) {  // the median of x, lo, hi for lo <= hi: x clipped to [lo, hi]
+  return x + minmod(lo - x, hi - x);
+}
+
+template <class R> R mp5_upper(R s0, R s1, R s2, R s3, R s4) {
+  const R alpha = R(4.0);
+  const R v_or = (R(2.0) * s0 - R(13.0) * s1 + R(47.0) * s2 + R(27.0) * s3 - R(3.0) * s4) / R(60.0);
+  const R v_mp = s2 + minmod(s3 - s2, alpha * (s2 - s1));
+  if ((v_or - s2) * (v_or - v_mp) <= R(0.0)) return v_or;
+  // second differences at cells i-1, i, i+1 and the limited curvatures at the faces i-1/2, i+1/2
+  const R dm = s0 - R(2.0) * s1 + s2;
+  const R d0 = s1 - R(2.0) * s2 + s3;
+  const R dp = s2 - R(2.0) * s3 + s4;
+  const R dM4p = minmod4(R(4.0) * d0 - dp, R(4.0) * dp - d0, d0, dp);
+  const R dM4m = minmod4(R(4.0) * dm - d0, R(4.0) * d0 - dm, dm, d0);
+  const R v_ul = s2 + alpha * (s2 - s1);
+  const R v_av = R(0.5) * (s2 + s3);
+  const R v_md = v_av - R(0.5) * dM4p;
+  const R v_lc = s2 + R(0.5) * (s2 - s1) + R(4.0 / 3.0) * dM4m;
+  const R v_min = rmax(rmin(rmin(s2, s3), v_md), rmin(rmin(s2, v_ul), v_lc));
+  const R v_max = rmin(rmax(rmax(s2, s3), v_md), rmax(rmax(s2, v_ul), v_lc));
+  return median3(v_or, v_min, v_max);
+}
+
+template <class R> void recon_mp5(const R a[5], R* aL, R* aR) {
+  *aR = mp5_upper(a[0], a[1], a[2], a[3], a[4]);
+  *aL = mp5_upper(a[4], a[3], a[2], a[1], a[0]);
+}
+
 template <class R> void recon_cell(int scheme, const R a[5], R* aL, R* aR) {
   if (scheme == RECON_MINMOD) recon_minmod(a, aL, aR);
   else if (scheme == RECON_PPM) recon_ppm(a, aL, aR);
+  else if (scheme == RECON_MP5) recon_mp5(a, aL, aR);
   else recon_wenoz(a, aL, aR);
 }
 

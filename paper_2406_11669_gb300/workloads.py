@@ -29,7 +29,7 @@ import math
 
 import numpy as np
 
-RECON_MINMOD, RECON_PPM, RECON_WENOZ = 0, 1, 2
+RECON_MINMOD, RECON_PPM, RECON_WENOZ, RECON_MP5 = 0, 1, 2, 3
 BC_PERIODIC, BC_COPY = 0, 1
 GAUGE_LORENZ, GAUGE_ALGEBRAIC = 0, 1
 FLUX_HLLE, FLUX_LXF = 0, 1          # Riemann solver (Eq. HLLEfluxes, Eq. LxFfluxes)
@@ -325,7 +325,7 @@ def smooth_general(n=(12, 10, 11), seed=106, recon=RECON_PPM, bc=BC_PERIODIC, ga
         metric[name] = _smooth_scalar(rng, 2, Xv, Yv, Zv, shape, 0.02)
     params = default_params(gamma=4.0 / 3.0, gamma_atm=4.0 / 3.0, rho_atm=1e-7, K_atm=1.0, recon=recon, gauge=gauge)
     prims = dict(rho=rho, press=press, velx=v[0], vely=v[1], velz=v[2])
-    rname = {RECON_MINMOD: "minmod", RECON_PPM: "ppm", RECON_WENOZ: "wenoz"}[recon]
+    rname = {RECON_MINMOD: "minmod", RECON_PPM: "ppm", RECON_WENOZ: "wenoz", RECON_MP5: "mp5"}[recon]
     bname = "periodic" if bc == BC_PERIODIC else "copy"
     return Workload(f"smooth_general_{rname}_{bname}", tuple(n), g, x0, dx, (bc,) * 3, params, 0.25 * min(dx), prims,
                     A, psi, metric)
@@ -600,6 +600,41 @@ def torus_jet(n=(256, 256, 256), seed=105) -> Workload:
     prims = dict(rho=rho, press=press, velx=velx, vely=vely, velz=velz)
     return Workload("torus_jet_256cube_schwarzschild_wenoz", tuple(n), g, x0, dx, (BC_COPY,) * 3, params,
                     0.25 * min(dx), prims, A, _full(shape, 0.0), metric)
+
+
+def recovery_states(n=(48, 48, 48), seed=107, Bmax=0.03) -> Workload:
+    """A block whose cells hold independent seeded states for the primitive recovery, over the ranges of the
+    recovery's round-trip check: rho log-uniform in [1e-10, 1], p / rho log-uniform in [1e-4, 10], Lorentz factor
+    uniform in [1, 10] in a random direction; the field comes from a smooth seeded potential (|B| up to about
+    Bmax), so b^2 / rho spans many decades across the cells.  Isotropic Schwarzschild M = 0.1 at (-1, 0, 0) on
+    [-1/2, 1/2]^3; Gamma = 4/3, atmosphere floor 1e-12 (below every drawn density)."""
+    g = 3
+    x0 = (-0.5, -0.5, -0.5)
+    dx = tuple(1.0 / m for m in n)
+    N = [m + 2 * g for m in n]
+    shape = (N[2] + 1, N[1] + 1, N[0] + 1)
+    size = shape[0] * shape[1] * shape[2]
+    rng = Rng(seed)
+    rho = 10.0 ** rng.uniform(size, -10.0, 0.0).reshape(shape)
+    press = rho * 10.0 ** rng.uniform(size, -4.0, 1.0).reshape(shape)
+    Wl = rng.uniform(size, 1.0, 10.0).reshape(shape)
+    # random directions: normalised Gaussian-free draw (uniform in a cube, rejected outside the unit ball)
+    dirs = rng.uniform(3 * size, -1.0, 1.0).reshape((3,) + shape)
+    norm = np.sqrt(dirs[0] ** 2 + dirs[1] ** 2 + dirs[2] ** 2)
+    norm = np.where(norm > 1e-3, norm, 1.0)
+    M, centre = 0.1, (-1.0, 0.0, 0.0)
+    Xc, Yc, Zc = positions(n, g, x0, dx, CELL)
+    rr = np.sqrt((Xc - centre[0]) ** 2 + (Yc - centre[1]) ** 2 + (Zc - centre[2]) ** 2)
+    psi2 = (1.0 + M / (2.0 * rr)) ** 2
+    speed = np.sqrt(1.0 - 1.0 / Wl ** 2) / psi2  # gamma_ij v^i v^j = psi^4 |v|^2 = 1 - 1/W^2
+    vel = [dirs[d] / norm * speed for d in range(3)]
+    A = _fourier_potential(rng, 4, n, g, x0, dx, shape, Bmax)
+    Xv, Yv, Zv = positions(n, g, x0, dx, VERTEX)
+    metric = schwarzschild_isotropic(Xv, Yv, Zv, M, centre, shape)
+    params = default_params(gamma=4.0 / 3.0, gamma_atm=4.0 / 3.0, rho_atm=1e-12, K_atm=0.1, recon=RECON_PPM)
+    prims = dict(rho=rho, press=press, velx=vel[0], vely=vel[1], velz=vel[2])
+    return Workload("recovery_states", tuple(n), g, x0, dx, (BC_COPY,) * 3, params, 0.25 * min(dx), prims, A,
+                    _full(shape, 0.0), metric)
 
 
 def weak_field_wave(nx, recon=RECON_PPM, amp=1e-3, cfl=0.25) -> Workload:

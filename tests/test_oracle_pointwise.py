@@ -228,7 +228,7 @@ def test_speeds_causal_and_ordered():
 # ------------------------------------------------------------------------------------------- reconstruction
 
 
-@pytest.mark.parametrize("scheme", [W.RECON_MINMOD, W.RECON_PPM, W.RECON_WENOZ])
+@pytest.mark.parametrize("scheme", [W.RECON_MINMOD, W.RECON_PPM, W.RECON_WENOZ, W.RECON_MP5])
 def test_recon_exact_on_linear_and_constant(scheme):
     for a0, s in ((1.3, 0.0), (-2.0, 0.25), (5.0, -1.5)):
         a = a0 + s * np.arange(-2, 3)
@@ -237,7 +237,8 @@ def test_recon_exact_on_linear_and_constant(scheme):
         assert hi == pytest.approx(a0 + 0.5 * s, abs=1e-14)
 
 
-@pytest.mark.parametrize("scheme,order", [(W.RECON_MINMOD, 1.9), (W.RECON_PPM, 2.9), (W.RECON_WENOZ, 4.5)])
+@pytest.mark.parametrize("scheme,order", [(W.RECON_MINMOD, 1.9), (W.RECON_PPM, 2.9), (W.RECON_WENOZ, 4.5),
+                                          (W.RECON_MP5, 4.8)])
 def test_recon_design_order_on_smooth_averages(scheme, order):
     def err(n):
         h = 1.0 / n
@@ -252,17 +253,56 @@ def test_recon_design_order_on_smooth_averages(scheme, order):
     assert math.log2(e1 / e2) >= order
 
 
-@pytest.mark.parametrize("scheme", [W.RECON_MINMOD, W.RECON_PPM, W.RECON_WENOZ])
+@pytest.mark.parametrize("scheme", [W.RECON_MINMOD, W.RECON_PPM, W.RECON_WENOZ, W.RECON_MP5])
 def test_recon_no_new_extrema_at_jump(scheme):
     data = np.array([1.0] * 6 + [0.125] * 6)
     for i in range(2, 10):
         lo, hi = O.point_recon(scheme, data[i - 2:i + 3])
         window = data[i - 1:i + 2]
-        if scheme != W.RECON_WENOZ:  # TVD schemes: within the neighbouring values
+        if scheme != W.RECON_WENOZ:  # TVD and monotonicity-preserving schemes: within the neighbouring values
             assert window.min() - 1e-15 <= lo <= window.max() + 1e-15
             assert window.min() - 1e-15 <= hi <= window.max() + 1e-15
         else:  # WENO-Z is essentially non-oscillatory: overshoot tiny against the jump
             assert 0.125 - 1e-3 <= lo <= 1.0 + 1e-3 and 0.125 - 1e-3 <= hi <= 1.0 + 1e-3
+
+
+def test_mp5_keeps_fifth_order_through_smooth_extrema():
+    """MP5's curvature bounds leave smooth extrema unclipped (Suresh & Huynh 1997): on averages of sin 2 pi x,
+    whose extrema the cells resolve, the maximum face error over all cells still falls at fifth order, and on
+    averages of a monotone quartic the face values are the exact point values (the fifth-order interface
+    formula is exact for polynomials of degree four)."""
+    def err(n):
+        h = 1.0 / n
+        xc = (np.arange(-2, n + 2) + 0.5) * h
+        avg = (np.cos(2 * math.pi * (xc - h / 2)) - np.cos(2 * math.pi * (xc + h / 2))) / (2 * math.pi * h)
+        e = 0.0
+        for i in range(2, n + 2):
+            lo, hi = O.point_recon(W.RECON_MP5, avg[i - 2:i + 3])
+            e = max(e, abs(hi - math.sin(2 * math.pi * (xc[i] + h / 2))),
+                    abs(lo - math.sin(2 * math.pi * (xc[i] - h / 2))))
+        return e
+    e1, e2 = err(32), err(64)
+    assert math.log2(e1 / e2) >= 4.8
+    h = 0.05
+    f = lambda x: 1.0 + x + 0.3 * x ** 2 + 0.2 * x ** 3 + 0.1 * x ** 4
+    F = lambda x: x + x ** 2 / 2 + 0.1 * x ** 3 + 0.05 * x ** 4 + 0.02 * x ** 5
+    xc = (np.arange(5) + 0.5) * h + 0.5
+    avg = (F(xc + h / 2) - F(xc - h / 2)) / h
+    lo, hi = O.point_recon(W.RECON_MP5, avg)
+    assert hi == pytest.approx(f(xc[2] + h / 2), rel=1e-14)
+    assert lo == pytest.approx(f(xc[2] - h / 2), rel=1e-14)
+
+
+def test_mp5_adds_no_ramp_at_an_isolated_jump():
+    """Next to an isolated jump in otherwise flat data the monotonicity-preserving bounds collapse onto the
+    cell's own value (the fifth-order value, 0.4 of the jump into the flat cell, lies outside the interval
+    [a_i, a_i + minmod(a_i+1 - a_i, 4 (a_i - a_i-1))] = [a_i, a_i]), so every face value is its cell's value."""
+    for lo_v, hi_v in ((1.0, 0.125), (0.0, 1.0), (-3.0, 2.5)):
+        data = np.array([lo_v] * 6 + [hi_v] * 6)
+        for i in range(2, 10):
+            lo, hi = O.point_recon(W.RECON_MP5, data[i - 2:i + 3])
+            assert abs(lo - data[i]) <= 1e-15 * abs(data[i]) + 1e-300
+            assert abs(hi - data[i]) <= 1e-15 * abs(data[i]) + 1e-300
 
 
 def test_ppm_recovers_parabola_interface_values():
