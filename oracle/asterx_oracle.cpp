@@ -43,6 +43,9 @@ namespace asterx_oracle {
 
 // ------------------------------------------------------------------------------------------------------
 // Flop-counting scalar.  + - * / sqrt each count one flop; divisions and square roots are also counted apart.
+// A value is either data (derived from the evolved state) or a constant (a literal, a parameter, or derived from
+// the frozen metric alone): operations whose operands are all constants are not counted, because a frozen
+// metric's arithmetic is done once, not every stage.  Fc(x) makes a constant; fc_data(x) a data value.
 
 struct Flops {
   unsigned long long add = 0, mul = 0, div = 0, sqrt = 0;
@@ -59,17 +62,19 @@ static Flops* g_rhs_marks = nullptr;
 // value); and the face solves themselves.
 static unsigned long long g_cellvar_flops = 0, g_recon_flops = 0, g_facesolve_flops = 0, g_edge_ppm_flops = 0;
 
-
 struct Fc {
   double v;
-  Fc() : v(0.0) {}
-  Fc(double x) : v(x) {}
+  bool k;  // constant
+  Fc() : v(0.0), k(true) {}
+  Fc(double x) : v(x), k(true) {}
+  Fc(double x, bool constant) : v(x), k(constant) {}
 };
-inline Fc operator+(Fc a, Fc b) { g_flops.add++; return Fc(a.v + b.v); }
-inline Fc operator-(Fc a, Fc b) { g_flops.add++; return Fc(a.v - b.v); }
-inline Fc operator*(Fc a, Fc b) { g_flops.mul++; return Fc(a.v * b.v); }
-inline Fc operator/(Fc a, Fc b) { g_flops.div++; return Fc(a.v / b.v); }
-inline Fc operator-(Fc a) { return Fc(-a.v); }
+inline Fc fc_data(double x) { return Fc(x, false); }
+inline Fc operator+(Fc a, Fc b) { if (!(a.k && b.k)) g_flops.add++; return Fc(a.v + b.v, a.k && b.k); }
+inline Fc operator-(Fc a, Fc b) { if (!(a.k && b.k)) g_flops.add++; return Fc(a.v - b.v, a.k && b.k); }
+inline Fc operator*(Fc a, Fc b) { if (!(a.k && b.k)) g_flops.mul++; return Fc(a.v * b.v, a.k && b.k); }
+inline Fc operator/(Fc a, Fc b) { if (!(a.k && b.k)) g_flops.div++; return Fc(a.v / b.v, a.k && b.k); }
+inline Fc operator-(Fc a) { return Fc(-a.v, a.k); }
 inline Fc& operator+=(Fc& a, Fc b) { a = a + b; return a; }
 inline Fc& operator-=(Fc& a, Fc b) { a = a - b; return a; }
 inline Fc& operator*=(Fc& a, Fc b) { a = a * b; return a; }
@@ -79,8 +84,8 @@ inline bool operator<=(Fc a, Fc b) { return a.v <= b.v; }
 inline bool operator>=(Fc a, Fc b) { return a.v >= b.v; }
 inline bool operator==(Fc a, Fc b) { return a.v == b.v; }
 inline bool operator!=(Fc a, Fc b) { return a.v != b.v; }
-inline Fc sqrt(Fc a) { g_flops.sqrt++; return Fc(std::sqrt(a.v)); }
-inline Fc fabs(Fc a) { return Fc(std::fabs(a.v)); }
+inline Fc sqrt(Fc a) { if (!a.k) g_flops.sqrt++; return Fc(std::sqrt(a.v), a.k); }
+inline Fc fabs(Fc a) { return Fc(std::fabs(a.v), a.k); }
 inline double val(Fc a) { return a.v; }
 inline double val(double a) { return a; }
 inline bool finite(double a) { return std::isfinite(a); }
@@ -739,12 +744,16 @@ template <class R> void noble_residual(R z, R v2, R D, R tau, R S2, R B2, R BS, 
   J[1][1] = R(-0.5) * B2 + dp_dv2;
 }
 
+// A state-derived input of the recovery as a scalar of type R (a data value for the flop-counting scalar).
+template <class R> inline R datum(double x) { return R(x); }
+template <> inline Fc datum<Fc>(double x) { return fc_data(x); }
+
 // velocity from Eq. (Noble2D v): v^i = gamma^ij S_j / (z + B^2) + (B^j S_j) B^i / (z (z + B^2))
 template <class R>
 static void noble_velocity(const Metric3<R>& m, const C2PIn& in, R z, R B2, R BS, R v[3]) {
   for (int a = 0; a < 3; a++) {
-    R Su = m.gu[a][0] * R(in.S[0]) + m.gu[a][1] * R(in.S[1]) + m.gu[a][2] * R(in.S[2]);
-    v[a] = Su / (z + B2) + BS * R(in.B[a]) / (z * (z + B2));
+    R Su = m.gu[a][0] * datum<R>(in.S[0]) + m.gu[a][1] * datum<R>(in.S[1]) + m.gu[a][2] * datum<R>(in.S[2]);
+    v[a] = Su / (z + B2) + BS * datum<R>(in.B[a]) / (z * (z + B2));
   }
 }
 
@@ -767,20 +776,20 @@ static bool c2p_noble(const Metric3<R>& m, const C2PIn& in, const OParams& P, R 
   // initial guess from the previous primitives
   R gv2 = R(0.0);
   for (int a = 0; a < 3; a++)
-    for (int b = 0; b < 3; b++) gv2 += m.g[a][b] * R(in.guess_vel[a]) * R(in.guess_vel[b]);
+    for (int b = 0; b < 3; b++) gv2 += m.g[a][b] * datum<R>(in.guess_vel[a]) * datum<R>(in.guess_vel[b]);
   if (!(gv2 >= R(0.0))) gv2 = R(0.0);
   if (gv2 > R(v2max)) gv2 = R(v2max);
   const R gW = R(1.0) / sqrt(R(1.0) - gv2);
-  const R geps = R(in.guess_press) / (R(gamma - 1.0) * R(in.guess_rho));
-  const R gh = R(1.0) + geps + R(in.guess_press) / R(in.guess_rho);
-  R z = R(in.guess_rho) * gh * gW * gW;
+  const R geps = datum<R>(in.guess_press) / (R(gamma - 1.0) * datum<R>(in.guess_rho));
+  const R gh = R(1.0) + geps + datum<R>(in.guess_press) / datum<R>(in.guess_rho);
+  R z = datum<R>(in.guess_rho) * gh * gW * gW;
   R v2 = gv2;
   if (!(z > R(0.0)) || !finite(z)) return false;
   bool conv = false;
   int it;
   for (it = 1; it <= P.c2p_maxiter; it++) {
     R f[2], J[2][2];
-    noble_residual<R>(z, v2, R(in.D), R(in.tau), S2, B2, BS, gamma, f, J);
+    noble_residual<R>(z, v2, datum<R>(in.D), datum<R>(in.tau), S2, B2, BS, gamma, f, J);
     const R det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
     const R dz = (-f[0] * J[1][1] + J[0][1] * f[1]) / det;
     const R dv2 = (-J[0][0] * f[1] + J[1][0] * f[0]) / det;
@@ -799,7 +808,7 @@ static bool c2p_noble(const Metric3<R>& m, const C2PIn& in, const OParams& P, R 
   out->iters = (it > P.c2p_maxiter) ? P.c2p_maxiter : it;
   if (!conv || !(z > R(0.0)) || !(v2 >= R(0.0)) || !(v2 < R(1.0))) return false;
   const R W = R(1.0) / sqrt(R(1.0) - v2);
-  const R rho = R(in.D) / W;
+  const R rho = datum<R>(in.D) / W;
   R v[3];
   noble_velocity<R>(m, in, z, B2, BS, v);
   const R eps = (z / (rho * W * W) - R(1.0)) / R(gamma);  // Eq. (Noble2D epsilon) with the adiabatic index
@@ -899,8 +908,8 @@ template <class R>
 static bool c2p_palenzuela(const Metric3<R>& m, const C2PIn& in, const OParams& P, R S2, R B2, R BS,
                            C2POut* out) {
   PalenzuelaFn<R> f;
-  const R D = R(in.D);
-  f.q = R(in.tau) / D;
+  const R D = datum<R>(in.D);
+  f.q = datum<R>(in.tau) / D;
   f.r = S2 / (D * D);
   f.s = B2 / D;
   f.t = BS / pow15(D);
@@ -940,7 +949,7 @@ template <class R> static C2POut c2p_cell(const Metric3<R>& m, const C2PIn& in, 
   out.iters = 0;
   out.reset = false;
   // atmosphere test on the densitised density before the recovery: D~ < sqrt(gamma) rho_atm
-  if (!(R(in.Dtilde) >= m.sqrtg * R(P.rho_atm))) {
+  if (!(datum<R>(in.Dtilde) >= m.sqrtg * R(P.rho_atm))) {
     atmosphere(P, &out);
     out.flag = 2;
     return out;
@@ -948,10 +957,10 @@ template <class R> static C2POut c2p_cell(const Metric3<R>& m, const C2PIn& in, 
   R S2 = R(0.0), B2 = R(0.0), BS = R(0.0);
   for (int a = 0; a < 3; a++)
     for (int b = 0; b < 3; b++) {
-      S2 += m.gu[a][b] * R(in.S[a]) * R(in.S[b]);
-      B2 += m.g[a][b] * R(in.B[a]) * R(in.B[b]);
+      S2 += m.gu[a][b] * datum<R>(in.S[a]) * datum<R>(in.S[b]);
+      B2 += m.g[a][b] * datum<R>(in.B[a]) * datum<R>(in.B[b]);
     }
-  for (int a = 0; a < 3; a++) BS += R(in.B[a]) * R(in.S[a]);
+  for (int a = 0; a < 3; a++) BS += datum<R>(in.B[a]) * datum<R>(in.S[a]);
   bool ok = c2p_noble<R>(m, in, P, S2, B2, BS, &out);
   if (ok) {
     out.flag = 0;
@@ -2177,7 +2186,17 @@ void oracle_face_flops(const OParams* p, const OBlock* b, const double* const* m
             mf.K[a][q] = Fc(md.K[a][q]);
           }
         }
-        FaceOut<Fc> o = face_solve<Fc>(mf, in, p->gamma, d);
+        FaceInputT<Fc> fin;  // the reconstructed states are data
+        for (int sd = 0; sd < 2; sd++) {
+          fin.rho[sd] = fc_data(in.rho[sd]);
+          fin.press[sd] = fc_data(in.press[sd]);
+          for (int a = 0; a < 3; a++) {
+            fin.u[sd][a] = fc_data(in.u[sd][a]);
+            fin.Bt[sd][a] = fc_data(in.Bt[sd][a]);
+          }
+        }
+        fin.Bn = fc_data(in.Bn);
+        FaceOut<Fc> o = face_solve<Fc>(mf, fin, p->gamma, d);
         faces += 1;
         iters += o.iters;
       }
@@ -2193,7 +2212,7 @@ void oracle_face_flops(const OParams* p, const OBlock* b, const double* const* m
 void oracle_recon_flops(int scheme, const double* a5, double* out) {
   Flops before = g_flops;
   Fc a[5];
-  for (int t = 0; t < 5; t++) a[t] = Fc(a5[t]);
+  for (int t = 0; t < 5; t++) a[t] = fc_data(a5[t]);
   Fc lo, hi;
   recon_cell<Fc>(scheme, a, &lo, &hi);
   out[0] = (double)(g_flops.add - before.add);
@@ -2228,13 +2247,13 @@ void oracle_stage_flops(const OParams* p, const OBlock* b, const double* const* 
   for (int v = 0; v < 9; v++) {
     Uv[v].resize(G.size());
     kv[v].assign(G.size(), Fc(0.0));
-    for (long c = 0; c < G.size(); c++) Uv[v][c] = Fc(U[v][c]);
+    for (long c = 0; c < G.size(); c++) Uv[v][c] = fc_data(U[v][c]);
     Up[v] = Uv[v].data();
     kp[v] = kv[v].data();
   }
   for (int v = 0; v < 5; v++) {
     Pv[v].resize(G.size());
-    for (long c = 0; c < G.size(); c++) Pv[v][c] = Fc(prim[v][c]);
+    for (long c = 0; c < G.size(); c++) Pv[v][c] = fc_data(prim[v][c]);
     Pp[v] = Pv[v].data();
   }
   auto put = [&](int at, const Flops& a, const Flops& z) {
@@ -2271,9 +2290,9 @@ void oracle_stage_flops(const OParams* p, const OBlock* b, const double* const* 
         C2POut o = c2p_cell<Fc>(m, in, *p);
         iters += o.iters;
         nflag[o.flag == 0 ? 0 : o.flag == 1 ? 1 : o.flag == 2 ? 2 : 3] += 1;
-        Pp[0][c] = Fc(o.rho);
-        Pp[1][c] = Fc(o.press);
-        for (int a = 0; a < 3; a++) Pp[2 + a][c] = Fc(o.vel[a]);
+        Pp[0][c] = fc_data(o.rho);
+        Pp[1][c] = fc_data(o.press);
+        for (int a = 0; a < 3; a++) Pp[2 + a][c] = fc_data(o.vel[a]);
         if (o.reset) {
           Prim<Fc> pr;
           pr.rho = Fc(o.rho);

@@ -2,8 +2,13 @@
 256^3 torus-and-jet workload (WENO-Z, Schwarzschild M = 0.1, Gamma = 4/3), part by part and per kernel unit,
 counted by the oracle's flop-counting scalar.  Calls only the oracle.
 
-Counting convention (+ - * / sqrt one flop each; x^1.5 one product and one square root; metric interpolation not
-counted, the metric being frozen):
+Counting convention (+ - * / sqrt one flop each; x^1.5 one product and one square root; arithmetic whose operands
+are all constants -- literals, parameters and the frozen metric, its interpolation included -- is not counted,
+because a frozen metric's arithmetic is done once, not every stage):
+  * the oracle evaluates each formula in the paper's order, so a product such as T^00 beta^i beta^j K_ij is
+    charged as three products of data although beta^i beta^j K_ij is constant, and symmetric contractions are
+    summed over all nine (j, k) pairs; the right-hand side's cell part (flux divergence and sources) is
+    therefore an upper estimate of the work an implementation that folds those constants needs;
   * the oracle is literal, so it repeats some steps an implementation does once: u = W v is formed for each of
     the three directions, every cell is reconstructed for both of its faces, every PPM interface of the edge
     fields for both edges that share the face value, and the right-hand side forms the face and centre field
