@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch measurement")
     ap.add_argument("--batch-blocks", type=int, default=512)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward measurement")
+    ap.add_argument("--no-balsara", action="store_true",
+                    help="skip the 128^3 Balsara block (and the tiled and two-level runs measured against it)")
     ap.add_argument("--adjoint-n", type=int, default=64, help="cells per axis of the adjoint workload")
     ap.add_argument("--no-refined", action="store_true",
                     help="skip the two-level (refined box) measurement")
@@ -184,6 +186,15 @@ def read_traffic(n):
 
 def cpu_model():
     try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                if name and name != "-":
+                    return name
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
         with open("/proc/cpuinfo") as f:
             for line in f:
                 low = line.lower()
@@ -260,6 +271,11 @@ def _upload_block(w, dev):
     return M, U, P
 
 
+def counters(t):
+    c = t.cpu().tolist()
+    return {"n_noble": c[0], "n_fallback": c[1], "n_atm": c[2], "n_failed": c[3], "noble_iters": c[4]}
+
+
 def run_batched(args, dev, stream):
     """Uneven batch of the magnetised-star workload (512 blocks, n per axis in {16,24,32,48,64}, dx = 1/256,
     PPM, Schwarzschild M = 0.2) in one batched step, against one block of equal total interior volume with the
@@ -284,9 +300,10 @@ def run_batched(args, dev, stream):
     steps = max(1, min(args.steps, 3))
     batch.step(dt, nsteps=1)
     torch.cuda.synchronize(dev)
+    stats_b = torch.zeros(5, dtype=torch.int64, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    batch.step(dt, nsteps=steps)
+    batch.step(dt, nsteps=steps, stats=stats_b)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms_b = e0.elapsed_time(e1) / steps
@@ -309,9 +326,10 @@ def run_batched(args, dev, stream):
     s.prim2con(U, P)
     s.rk4_step(U, P, w.dt)
     torch.cuda.synchronize(dev)
+    stats_s = torch.zeros(5, dtype=torch.int64, device=dev)
     e0.record(stream)
     for _ in range(steps):
-        s.rk4_step(U, P, w.dt)
+        s.rk4_step(U, P, w.dt, stats=stats_s)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms_s = e0.elapsed_time(e1) / steps
@@ -329,7 +347,9 @@ def run_batched(args, dev, stream):
                         f"Schwarzschild M=0.2, one batched launch per kernel",
             "blocks": len(lay), "interior_cells": cells, "value": rate_b, "unit": UNIT, "ms_per_step": ms_b,
             "steps": steps, "pool_bytes": int(pool_bytes),
-            "single_equal_volume": {"n": side, "interior_cells": single_cells, "value": rate_s, "ms_per_step": ms_s},
+            "c2p_counters": counters(stats_b),
+            "single_equal_volume": {"n": side, "interior_cells": single_cells, "value": rate_s, "ms_per_step": ms_s,
+                                    "c2p_counters": counters(stats_s)},
             "batched_vs_single": rate_b / rate_s}
 
 
@@ -599,10 +619,10 @@ def run_coupling(args, s, U, P, M, w, dev, stream):
                             "overhead": ms_dyn / ms_frozen - 1.0, "steps": steps}}
 
 
-def run_variants(args, s, U, P, w, dev, stream):
+def run_variants(args, s, U, P, w, dev, stream, U0=None, P0=None):
     """The paper's alternative schemes on the benchmark block: one RK4 step with the Lax-Friedrichs flux, with flux
-    constrained transport, with both, with the algebraic gauge, and one RK2 step of the default scheme (rates per
-    RK stage)."""
+    constrained transport, with both, with the algebraic gauge, with MP5 and with PPM reconstruction, and one RK2
+    step of the default scheme (rates per RK stage)."""
     import torch
 
     from paper_2406_11669_gb300 import asterx as A
@@ -611,22 +631,30 @@ def run_variants(args, s, U, P, w, dev, stream):
     out = {}
     steps = max(1, min(args.steps, 3))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for name, flux, efield, rk2, gauge in (("lxf", 1, 0, False, 0), ("fct", 0, 1, False, 0),
-                                           ("lxf_fct", 1, 1, False, 0), ("rk2", 0, 0, True, 0),
-                                           ("algebraic_gauge", 0, 0, False, 1)):
-        s.p = A.params_struct(dict(s.params, flux=flux, efield=efield, gauge=gauge))
+    recon0 = s.params["recon"]
+    for name, flux, efield, rk2, gauge, recon in (("lxf", 1, 0, False, 0, recon0), ("fct", 0, 1, False, 0, recon0),
+                                                  ("lxf_fct", 1, 1, False, 0, recon0), ("rk2", 0, 0, True, 0, recon0),
+                                                  ("algebraic_gauge", 0, 0, False, 1, recon0),
+                                                  ("mp5", 0, 0, False, 0, 3), ("ppm", 0, 0, False, 0, 1)):
+        s.p = A.params_struct(dict(s.params, flux=flux, efield=efield, gauge=gauge, recon=recon))
         step = s.rk2_step if rk2 else s.rk4_step
+        if U0 is not None:  # every variant starts from the state the headline was timed on
+            U.copy_(U0)
+            P.copy_(P0)
+        stats = torch.zeros(5, dtype=torch.int64, device=dev)
         step(U, P, w.dt)
         torch.cuda.synchronize(dev)
         e0.record(stream)
         for _ in range(steps):
-            step(U, P, w.dt)
+            step(U, P, w.dt, stats=stats)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / steps
         stages = 2 if rk2 else 4
+        c = stats.cpu().tolist()
         out[name] = {"ms_per_step": ms, "value": w.interior_cells * stages / (ms / 1e3), "unit": UNIT,
-                     "stages_per_step": stages}
+                     "stages_per_step": stages, "steps": steps,
+                     "c2p_counters": {"n_noble": c[0], "n_fallback": c[1], "n_atm": c[2], "n_failed": c[3]}}
     s.p = base
     return out
 
@@ -735,6 +763,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         s.rk4_step(U, P, w.dt, stats=stats)
     torch.cuda.synchronize(dev)
+    U_warm, P_warm = U.clone(), P.clone()  # the variants start from this state
     stats.zero_()
     A.profile_enable(args.steps * 4 * 3)
     barrier(world)
@@ -838,16 +867,17 @@ def run_ours(args):
     if not args.no_coupling:
         result["coupling"] = run_coupling(args, s, U, P, M, w, dev, stream)
     if not args.no_variants:
-        result["variants"] = run_variants(args, s, U, P, w, dev, stream)
-    del s, U, P, M
+        result["variants"] = run_variants(args, s, U, P, w, dev, stream, U_warm, P_warm)
+    del s, U, P, M, U_warm, P_warm
     torch.cuda.empty_cache()
-    b128 = run_balsara(args, dev, stream)
-    result["balsara_128"] = b128
+    b128 = None if args.no_balsara else run_balsara(args, dev, stream)
+    if b128:
+        result["balsara_128"] = b128
     if not args.no_batched:
         result["batched"] = run_batched(args, dev, stream)
-    if not args.no_tiled:
+    if b128 and not args.no_tiled:
         result["tiled"] = run_tiled(args, dev, stream, b128["ms_per_step"])
-    if not args.no_refined:
+    if b128 and not args.no_refined:
         result["refined"] = run_refined(args, dev, stream, b128["ms_per_step"])
     if not args.no_adjoint:
         result["adjoint"] = run_adjoint(args, dev, stream)

@@ -4,7 +4,7 @@
  *
  * Method (paper sections): Valencia conservative form (Sec. 2.2, Eqs. fluxconseqs, grmhdeqs, grmhdsrc, cons);
  * vector potential on edges with B~ = curl A on faces and the generalised Lorenz gauge (Sec. 2.3, 3.4, Eqs.
- * BEulerian, Ainductioneqs, recastedAvec, recastedScalarPot); minmod / PPM / WENO-Z reconstruction and HLLE
+ * BEulerian, Ainductioneqs, recastedAvec, recastedScalarPot); minmod / PPM / WENO-Z / MP5 reconstruction and HLLE
  * fluxes with magnetosonic speeds (Sec. 3.3, Eq. HLLEfluxes); upwind constrained transport (Sec. 3.4, Eqs.
  * uct1, uct2, eq3.20); Noble 2D recovery with a Palenzuela 1D fallback and atmosphere (Sec. 3.5, 3.6);
  * ideal-gas EOS (Sec. 3.7); 4th-order vertex-metric interpolation (Sec. 3.2); classical RK4 (Sec. 5).
@@ -52,7 +52,13 @@ typedef enum {
   ASTERX_ETIMEOUT = 5  /* a bounded device-side wait gave up */
 } asterx_status;
 
-typedef enum { ASTERX_RECON_MINMOD = 0, ASTERX_RECON_PPM = 1, ASTERX_RECON_WENOZ = 2 } asterx_recon;
+/* Reconstruction of the face states (Sec. 3.3 lists minmod, PPM, WENO-Z and MP5 among its methods). */
+typedef enum {
+  ASTERX_RECON_MINMOD = 0,
+  ASTERX_RECON_PPM = 1,
+  ASTERX_RECON_WENOZ = 2,
+  ASTERX_RECON_MP5 = 3 /* Suresh & Huynh 1997, alpha = 4 */
+} asterx_recon;
 typedef enum { ASTERX_BC_PERIODIC = 0, ASTERX_BC_COPY = 1 } asterx_bc;
 typedef enum { ASTERX_GAUGE_LORENZ = 0, ASTERX_GAUGE_ALGEBRAIC = 1 } asterx_gauge;
 typedef enum { ASTERX_FLUX_HLLE = 0, ASTERX_FLUX_LXF = 1 } asterx_flux;

@@ -308,6 +308,8 @@ __global__ void ka_faces(Blk b, Ws w, AdjWs a, double gamma, double gfac, int lx
   ALOOP(t, count) {
     int p[3];
     decode(t, lo[0], ex[0], lo[1], ex[1], lo[2], p[0], p[1], p[2]);
+    // the corner columns (both transverse indices in the ghost layers) feed nothing: no roots were kept there
+    if ((p[T1] < b.g || p[T1] >= b.g + b.n[T1]) && (p[T2] < b.g || p[T2] >= b.g + b.n[T2])) continue;
     const long c = alin(b, p[0], p[1], p[2]);
     Geo m;
     m.alp = fg[FG_ALP * b.V + c];
@@ -490,7 +492,7 @@ __global__ void ka_recon(Blk b, Ws w, AdjWs a) {
         double a5[5];
         for (int s = 0; s < 5; s++) a5[s] = src[v][c + (s - 2) * st];
         recon5_vjp<SCHEME>(a5, glo, ghi, g);
-      } else {  // WENO-Z: dual numbers through the forward code
+      } else {  // WENO-Z, MP5: dual numbers through the forward code
         typedef Dual<5> D5;
         D5 s5[5];
         for (int s = 0; s < 5; s++) s5[s] = D5::seed(src[v][c + (s - 2) * st], s);
@@ -855,6 +857,7 @@ static void adjoint_dir(const StageArgs& sa, const AdjWs& a, cudaStream_t s) {
   const long rc = (long)b.N[0] * b.N[1] * b.N[2] / b.N[D] * (b.n[D] + 2);
   if (sa.recon == 0) ka_recon<D, 0><<<agrid(rc, T), T, 0, s>>>(b, w, a);
   else if (sa.recon == 1) ka_recon<D, 1><<<agrid(rc, T), T, 0, s>>>(b, w, a);
+  else if (sa.recon == 3) ka_recon<D, 3><<<agrid(rc, T), T, 0, s>>>(b, w, a);
   else ka_recon<D, 2><<<agrid(rc, T), T, 0, s>>>(b, w, a);
 }
 

@@ -136,7 +136,7 @@ enum Kind {
   KIND_CELLS_ALL,    // N^3: centre B, u, prim->cons
   KIND_INTERIOR,     // n^3: recovery, cell update
   KIND_RECON_X, KIND_RECON_Y, KIND_RECON_Z,
-  KIND_FACES_X, KIND_FACES_Y, KIND_FACES_Z,
+  KIND_FACES_X, KIND_FACES_Y, KIND_FACES_Z,  // faces g..g+n along the axis, without the corner columns
   KIND_VERTEX,       // (n+3)^3: G_A, F_Psi
   KIND_EDGES_X, KIND_EDGES_Y, KIND_EDGES_Z,
   KIND_PSI,          // (n+1)^3
@@ -159,9 +159,11 @@ __host__ __device__ inline long kind_count(int kind, const Blk& b) {
     case KIND_RECON_X: return (n0 + 2) * N1 * N2;
     case KIND_RECON_Y: return N0 * (n1 + 2) * N2;
     case KIND_RECON_Z: return N0 * N1 * (n2 + 2);
-    case KIND_FACES_X: return (n0 + 1) * N1 * N2;
-    case KIND_FACES_Y: return N0 * (n1 + 1) * N2;
-    case KIND_FACES_Z: return N0 * N1 * (n2 + 1);
+    // faces along D whose transverse indices are not both in the ghost layers (the (2g)^2 corner columns feed
+    // nothing): n_T1 n_T2 interior columns, then 2g (n_T1 + n_T2) columns read by the edge fields only
+    case KIND_FACES_X: return (n0 + 1) * (n1 * n2 + 2L * b.g * (n1 + n2));
+    case KIND_FACES_Y: return (n1 + 1) * (n2 * n0 + 2L * b.g * (n2 + n0));
+    case KIND_FACES_Z: return (n2 + 1) * (n0 * n1 + 2L * b.g * (n0 + n1));
     case KIND_VERTEX: return (n0 + 3) * (n1 + 3) * (n2 + 3);
     case KIND_EDGES_X: return n0 * (n1 + 1) * (n2 + 1);
     case KIND_EDGES_Y: return (n0 + 1) * n1 * (n2 + 1);

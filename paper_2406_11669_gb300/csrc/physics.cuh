@@ -154,10 +154,12 @@ struct QuarticT {
 // gfac = Gamma / (Gamma - 1), ia = 1 / alpha, width = alpha sqrt(gamma^dd) (hoisted by the caller).  kSpeeds =
 // false skips the magnetosonic speeds (o.lm, o.lp unset: prim->cons and fluxes only); `roots`, when given, holds
 // the two speeds (lambda_+, lambda_-) already found for these inputs, and replaces the Newton iteration.
+// fluxes = false skips prim->cons and the fluxes (o.U, o.F unset: speeds and v~ only), for faces whose fluxes
+// nothing reads.
 template <class T, bool kSpeeds = true>
 __host__ __device__ __forceinline__ void face_side(const Geo& m, double ia, double width, int d, T rho, T press,
                                           const T u[3], const T B[3], double gamma, double gfac,
-                                          SideOutT<T>& o, const double* roots = nullptr) {
+                                          SideOutT<T>& o, const double* roots = nullptr, bool fluxes = true) {
   const T uu = contract_sym(m.g, u, u);
   const T W = sqrt(1.0 + uu);
   const T iW = 1.0 / W;
@@ -171,23 +173,25 @@ __host__ __device__ __forceinline__ void face_side(const Geo& m, double ia, doub
   const T b2 = B2 * iW2 + Bv * Bv;
   const T rhoh = rho + gfac * press;
   const T W2 = W * W;
-  const T z = rhoh * W2;
-  const double sg = m.sqg;
-  const double asg = m.alp * sg;
-  o.U[0] = sg * rho * W;
-  for (int a = 0; a < 3; a++) o.U[1 + a] = sg * ((z + B2) * vl[a] - Bv * Bl[a]);
-  o.U[4] = sg * (z - press - rho * W + B2 - 0.5 * b2);
   for (int a = 0; a < 3; a++) o.vt[a] = m.alp * v[a] - m.beta[a];
-  const T vt = o.vt[d];
-  const T pt = press + 0.5 * b2;
   const T Bd = B[d];
-  o.F[0] = o.U[0] * vt;
-  for (int a = 0; a < 3; a++) {
-    const T bl = Bl[a] * iW + W * Bv * vl[a];
-    o.F[1 + a] = o.U[1 + a] * vt - asg * bl * Bd * iW;
+  if (fluxes) {
+    const double sg = m.sqg;
+    const double asg = m.alp * sg;
+    const T z = rhoh * W2;
+    o.U[0] = sg * rho * W;
+    for (int a = 0; a < 3; a++) o.U[1 + a] = sg * ((z + B2) * vl[a] - Bv * Bl[a]);
+    o.U[4] = sg * (z - press - rho * W + B2 - 0.5 * b2);
+    const T vt = o.vt[d];
+    const T pt = press + 0.5 * b2;
+    o.F[0] = o.U[0] * vt;
+    for (int a = 0; a < 3; a++) {
+      const T bl = Bl[a] * iW + W * Bv * vl[a];
+      o.F[1 + a] = o.U[1 + a] * vt - asg * bl * Bd * iW;
+    }
+    o.F[1 + d] += asg * pt;
+    o.F[4] = o.U[4] * vt + asg * (pt * v[d] - Bv * Bd);
   }
-  o.F[1 + d] += asg * pt;
-  o.F[4] = o.U[4] * vt + asg * (pt * v[d] - Bv * Bd);
 
   if constexpr (!kSpeeds) return;
   // magnetosonic speeds
@@ -512,6 +516,41 @@ __host__ __device__ __forceinline__ void wenoz_both(const T s[5], T& lo, T& hi) 
   wenoz_from_indicators(s, e0, e1, e2, lo, hi);
 }
 
+// MP5, the monotonicity-preserving fifth-order reconstruction of Suresh & Huynh (1997): the fifth-order interface
+// value is kept where it lies between the cell value and the monotonicity-preserving bound a_i + minmod(a_i+1 -
+// a_i, 4 (a_i - a_i-1)); otherwise it is clipped to the interval the limited curvatures allow (the median of the
+// value and the interval's ends, formed as value + minmod(lower - value, upper - value)).  mp5_face gives the
+// upper face of the middle cell of (s0 .. s4); the lower face is mp5_face of the reversed stencil.
+template <class T>
+__host__ __device__ __forceinline__ T minmod4(T w, T x, T y, T z) {
+  if (val(w) > 0.0 && val(x) > 0.0 && val(y) > 0.0 && val(z) > 0.0) return fmin(fmin(w, x), fmin(y, z));
+  if (val(w) < 0.0 && val(x) < 0.0 && val(y) < 0.0 && val(z) < 0.0) return fmax(fmax(w, x), fmax(y, z));
+  return T(0.0);
+}
+
+template <class T>
+__host__ __device__ __forceinline__ T minmod2v(T x, T y) {  // minmod with the tests on values (dual-safe)
+  if (val(x) * val(y) <= 0.0) return T(0.0);
+  return (fabs(val(x)) <= fabs(val(y))) ? x : y;
+}
+
+template <class T>
+__host__ __device__ __forceinline__ T mp5_face(T s0, T s1, T s2, T s3, T s4) {
+  const T up = s2 - s1;  // a_i - a_i-1
+  const T v5 = (2.0 * s0 - 13.0 * s1 + 47.0 * s2 + 27.0 * s3 - 3.0 * s4) * (1.0 / 60.0);
+  const T vb = s2 + minmod2v(s3 - s2, 4.0 * up);
+  if (val(v5 - s2) * val(v5 - vb) <= 0.0) return v5;
+  const T c_m = s0 - 2.0 * s1 + s2, c_0 = s1 - 2.0 * s2 + s3, c_p = s2 - 2.0 * s3 + s4;
+  const T k_up = minmod4(4.0 * c_0 - c_p, 4.0 * c_p - c_0, c_0, c_p);  // limited curvature at the upper face
+  const T k_lo = minmod4(4.0 * c_m - c_0, 4.0 * c_0 - c_m, c_m, c_0);  // and at the lower face
+  const T v_ul = s2 + 4.0 * up;
+  const T v_md = 0.5 * (s2 + s3) - 0.5 * k_up;
+  const T v_lc = s2 + 0.5 * up + (4.0 / 3.0) * k_lo;
+  const T lower = fmax(fmin(fmin(s2, s3), v_md), fmin(fmin(s2, v_ul), v_lc));
+  const T upper = fmin(fmax(fmax(s2, s3), v_md), fmax(fmax(s2, v_ul), v_lc));
+  return v5 + minmod2v(lower - v5, upper - v5);
+}
+
 template <int SCHEME, class T>
 __host__ __device__ __forceinline__ void recon5(const T a[5], T& lo, T& hi) {
   if (SCHEME == 0) {
@@ -527,6 +566,9 @@ __host__ __device__ __forceinline__ void recon5(const T a[5], T& lo, T& hi) {
     ppm_limit(a[2], l, r);
     lo = l;
     hi = r;
+  } else if (SCHEME == 3) {
+    hi = mp5_face(a[0], a[1], a[2], a[3], a[4]);
+    lo = mp5_face(a[4], a[3], a[2], a[1], a[0]);
   } else {
     wenoz_both(a, lo, hi);
   }

@@ -508,7 +508,7 @@ struct UVel {
 // ----------------------------------------------------------------------------------------------------------
 // Reconstruction along D of each cell once (cells g-1 .. g+n along D, all transverse cells): the values at the
 // cell's lower and upper D-faces of rho, p, u^x, u^y, u^z and the two transverse centre B components.  Minmod
-// runs per cell; PPM and WENO-Z run as ReconPPM and ReconWENO below (chunks with a sliding stencil).
+// and MP5 run per cell; PPM and WENO-Z run as ReconPPM and ReconWENO below (chunks with a sliding stencil).
 
 template <int D, int SCHEME>
 struct Recon {
@@ -590,21 +590,54 @@ struct ReconPPM {
 // f-1, right state = lower value of cell f; HLLE (Eq. HLLEfluxes) and the upwind velocities of Eq. uct1.
 // ALT: the alternative schemes (Lax-Friedrichs fluxes, flux constrained transport), a separate instantiation
 // (FacesAlt) so that the default kernel (Faces) keeps its register budget.
+// Item t of the faces along D (faces g..g+n along D): first the faces whose two transverse indices are interior
+// (returns true: their fluxes feed the cell update), then those with one transverse index in the ghost layers
+// (returns false: only the edge fields read them, through c_max, c_min, the upwind velocities and, for flux
+// constrained transport, the induction fluxes).  The (2g)^2 corner columns, which nothing reads, have no items.
+// The first axis of each range varies fastest across items.
+template <int D>
+__device__ __forceinline__ bool face_item(const Blk& b, long t, int p[3]) {
+  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+  const int gw = 2 * b.g;
+  int e[3];
+  e[D] = b.n[D] + 1;
+  e[T1] = b.n[T1];
+  e[T2] = b.n[T2];
+  int ghost = -1;  // the transverse axis whose index lies in the ghost layers
+  const long nint = (long)e[0] * e[1] * e[2];
+  if (t >= nint) {
+    t -= nint;
+    e[T1] = gw;
+    const long na = (long)e[0] * e[1] * e[2];
+    if (t < na) {
+      ghost = T1;
+    } else {
+      t -= na;
+      e[T1] = b.n[T1];
+      e[T2] = gw;
+      ghost = T2;
+    }
+  }
+  unflatten3(t, (unsigned)e[0], (unsigned)e[1], p[0], p[1], p[2]);
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    if (a == ghost) p[a] = p[a] < b.g ? p[a] : p[a] + b.n[a];  // 0..g-1, then g+n..n+2g-1
+    else p[a] += b.g;
+  }
+  return ghost < 0;
+}
+
 template <int D, bool ALT>
 struct FaceSolve {
   static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts& k, long t) {
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     const Blk& b = r.b;
-    int lo[3] = {0, 0, 0}, hi[3] = {b.N[0] - 1, b.N[1] - 1, b.N[2] - 1};
-    lo[D] = b.g;
-    hi[D] = b.g + b.n[D];
-    Box box = make_box(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
     const long st = stride(b, D);
     const double* __restrict__ fg = r.w.fg + (long)D * NFG * b.V;
     double* __restrict__ fd = r.w.face + (long)D * NFD * b.V;
-    int i, j, kk;
-    box.at(t, i, j, kk);
-    const long c = lin(b, i, j, kk);
+    int p[3];
+    const bool full = face_item<D>(b, t, p);
+    const long c = lin(b, p[0], p[1], p[2]);
     Geo m;
     m.alp = fg[FG_ALP * b.V + c];
     for (int a = 0; a < 3; a++) m.beta[a] = fg[(FG_BETA + a) * b.V + c];
@@ -625,26 +658,29 @@ struct FaceSolve {
       B[D] = Bn;
       B[T1] = Bt[side][0] = rr[5 * b.V];
       B[T2] = Bt[side][1] = rr[6 * b.V];
-      face_side(m, ia, width, D, rr[0], rr[b.V], u, B, k.gamma, k.gfac, s[side]);
+      face_side(m, ia, width, D, rr[0], rr[b.V], u, B, k.gamma, k.gfac, s[side], nullptr, full);
     }
     const double cmax = fmax(0.0, fmax(s[0].lp, s[1].lp));
     const double cmin = -fmin(0.0, fmin(s[0].lm, s[1].lm));
     const double den = cmax + cmin;
     if (den > 0.0) {
       const double iden = 1.0 / den;
-      if (ALT && k.lxf) {  // Eq. LxFfluxes: c_wave = max(c_max, c_min)
-        const double cw = fmax(cmax, cmin);
-        for (int v = 0; v < 5; v++)
-          fd[(FD_F + v) * b.V + c] = 0.5 * (s[1].F[v] + s[0].F[v] - cw * (s[1].U[v] - s[0].U[v]));
-      } else {
-        for (int v = 0; v < 5; v++)
-          fd[(FD_F + v) * b.V + c] =
-              (cmin * s[1].F[v] + cmax * s[0].F[v] - cmax * cmin * (s[1].U[v] - s[0].U[v])) * iden;
+      if (full) {
+        if (ALT && k.lxf) {  // Eq. LxFfluxes: c_wave = max(c_max, c_min)
+          const double cw = fmax(cmax, cmin);
+          for (int v = 0; v < 5; v++)
+            fd[(FD_F + v) * b.V + c] = 0.5 * (s[1].F[v] + s[0].F[v] - cw * (s[1].U[v] - s[0].U[v]));
+        } else {
+          for (int v = 0; v < 5; v++)
+            fd[(FD_F + v) * b.V + c] =
+                (cmin * s[1].F[v] + cmax * s[0].F[v] - cmax * cmin * (s[1].U[v] - s[0].U[v])) * iden;
+        }
       }
       fd[FD_VB1 * b.V + c] = (cmax * s[0].vt[T1] + cmin * s[1].vt[T1]) * iden;
       fd[FD_VB2 * b.V + c] = (cmax * s[0].vt[T2] + cmin * s[1].vt[T2]) * iden;
     } else {
-      for (int v = 0; v < 5; v++) fd[(FD_F + v) * b.V + c] = 0.5 * (s[0].F[v] + s[1].F[v]);
+      if (full)
+        for (int v = 0; v < 5; v++) fd[(FD_F + v) * b.V + c] = 0.5 * (s[0].F[v] + s[1].F[v]);
       fd[FD_VB1 * b.V + c] = 0.5 * (s[0].vt[T1] + s[1].vt[T1]);
       fd[FD_VB2 * b.V + c] = 0.5 * (s[0].vt[T2] + s[1].vt[T2]);
     }
@@ -1051,6 +1087,7 @@ template <int D, class T>
 static void seq_dir(const T& t, const StageConsts& k, int recon, cudaStream_t s) {
   if (recon == 0) launch<Recon<D, 0>>(t, k, KIND_RECON_X + D, s);
   else if (recon == 1) launch<ReconPPM<D>>(t, k, KIND_RCHUNK_X + D, s);
+  else if (recon == 3) launch<Recon<D, 3>>(t, k, KIND_RECON_X + D, s);
   else launch<ReconWENO<D>>(t, k, KIND_RCHUNK_X + D, s);
   const bool mark = g_prof.on && g_prof.n < g_prof.cap && !capturing(s);
   if (mark) cudaEventRecord(g_prof.ev[2 * g_prof.n], s);

@@ -39,7 +39,7 @@ inline bool params_ok(const asterx_params* p) {
   if (!(std::isfinite(p->gamma_atm) && p->gamma_atm > 1.0)) return false;
   if (!finite_pos(p->c2p_tol) || p->c2p_maxiter < 1 || p->brent_maxiter < 1) return false;
   if (!(std::isfinite(p->W_max) && p->W_max > 1.0)) return false;
-  if (p->recon < ASTERX_RECON_MINMOD || p->recon > ASTERX_RECON_WENOZ) return false;
+  if (p->recon < ASTERX_RECON_MINMOD || p->recon > ASTERX_RECON_MP5) return false;
   if (p->gauge != ASTERX_GAUGE_LORENZ && p->gauge != ASTERX_GAUGE_ALGEBRAIC) return false;
   if (!(std::isfinite(p->xi_lorenz) && p->xi_lorenz >= 0.0)) return false;
   if (p->flux != ASTERX_FLUX_HLLE && p->flux != ASTERX_FLUX_LXF) return false;
