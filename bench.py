@@ -313,7 +313,23 @@ def run_batched(args, dev, stream):
         torch.cuda.synchronize(dev)
         torch.cuda.profiler.stop()
     pool_bytes = batch.ws_bytes
-    del batch, entries
+    del batch
+    torch.cuda.empty_cache()
+    # the same blocks stepped one at a time through the single-block path (one launch sequence per block, as a
+    # code that loops over its blocks does): the sum of the blocks' step times
+    loop_ms = 0.0
+    for (n, g, x0, dx_, bc, M, U, P) in entries:
+        sb = A.Solver(params, n, g, x0, dx_, bc, device=dev)
+        sb.prepare(M)
+        sb.rk4_step(U, P, dt)  # warm-up (and the autotuner's first launch at this size)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        sb.rk4_step(U, P, dt)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        loop_ms += e0.elapsed_time(e1)
+        del sb
+    del entries
     torch.cuda.empty_cache()
     # one block of the same total interior volume, centred on the star
     side = int(round(cells ** (1.0 / 3.0)))
@@ -348,6 +364,8 @@ def run_batched(args, dev, stream):
             "blocks": len(lay), "interior_cells": cells, "value": rate_b, "unit": UNIT, "ms_per_step": ms_b,
             "steps": steps, "pool_bytes": int(pool_bytes),
             "c2p_counters": counters(stats_b),
+            "per_block_loop": {"ms_per_step": loop_ms, "value": cells * 4 / (loop_ms / 1e3),
+                               "batched_vs_loop": loop_ms / ms_b},
             "single_equal_volume": {"n": side, "interior_cells": single_cells, "value": rate_s, "ms_per_step": ms_s,
                                     "c2p_counters": counters(stats_s)},
             "batched_vs_single": rate_b / rate_s}
@@ -725,7 +743,7 @@ def run_balsara(args, dev, stream):
     torch.cuda.empty_cache()
     return {"workload": WORKLOAD_128, "ms_per_step": ms / steps, "steps": steps,
             "value": w.interior_cells * 4 * steps / (ms / 1e3), "unit": UNIT,
-            "face_launch_ms": face_ms / max(nface, 1), "faces_per_launch": (w.n[0] + 1) * (w.n[0] + 6) ** 2}
+            "face_launch_ms": face_ms / max(nface, 1), "faces_per_launch": (w.n[0] + 1) * (w.n[0] ** 2 + 12 * w.n[0])}
 
 
 def run_ours(args):
@@ -823,7 +841,7 @@ def run_ours(args):
 
     if rank != 0:
         return
-    faces_per_launch = (args.n + 1) * (args.n + 6) ** 2
+    faces_per_launch = (args.n + 1) * (args.n ** 2 + 12 * args.n)  # faces g..g+n, corner columns excluded
     sf = read_stage_flops(args.n) or {}
     flops_per_face = sf.get("face_solve_flops_per_face")
     face_avg_ms = face_ms / max(nface, 1)

@@ -165,10 +165,9 @@ void drop_graphs(void* ws) {
   }
 }
 
-// the cached step graph for these launch parameters, captured on a private stream if there is none (null if
-// capture is not possible, e.g. inside the caller's own capture)
-cudaGraphExec_t step_graph(const StageArgs& a, const asterx_params* p, void* ws, const BlockRec* tab, const long* off,
-                           const long* totals, int nb, double dt, unsigned long long* stats, const Tiling* til) {
+// the cached step graph for these launch parameters (null if there is none)
+cudaGraphExec_t cached_graph(const asterx_params* p, void* ws, const long* totals, int nb, double dt,
+                             unsigned long long* stats) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
   std::lock_guard<std::mutex> lock(g_graph_mu);
@@ -176,6 +175,17 @@ cudaGraphExec_t step_graph(const StageArgs& a, const asterx_params* p, void* ws,
     if (g.device == dev && g.ws == ws && g.nb == nb && g.dt == dt && g.stats == stats &&
         std::memcmp(&g.p, p, sizeof(*p)) == 0 && std::equal(g.totals.begin(), g.totals.end(), totals))
       return g.exec;
+  return nullptr;
+}
+
+// the cached step graph for these launch parameters, captured on a private stream if there is none (null if
+// capture is not possible, e.g. inside the caller's own capture)
+cudaGraphExec_t step_graph(const StageArgs& a, const asterx_params* p, void* ws, const BlockRec* tab, const long* off,
+                           const long* totals, int nb, double dt, unsigned long long* stats, const Tiling* til) {
+  if (cudaGraphExec_t g = cached_graph(p, ws, totals, nb, dt, stats)) return g;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lock(g_graph_mu);
   cudaStream_t ps = nullptr;
   if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
   cudaGraph_t graph = nullptr;
@@ -877,15 +887,25 @@ asterx_status asterx_batched_step(const asterx_params* p, const asterx_batch_blo
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(stats);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  int first = 0;  // steps launched directly
   if (nsteps > 0 && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+    if (!cached_graph(p, ws, totals, nb, dt, cnt)) {
+      // the first step of new launch parameters runs directly, which lets the launch autotuner time its
+      // kernels on the live data; the graph captured after it bakes in the chosen launch shapes
+      for (int stage = 0; stage < 4; stage++) {
+        cudaError_t e = launch_batch_stage(a, tab + (size_t)stage * nb, off, totals, nb, stage, dt, cnt, s, til);
+        if (e != cudaSuccess) return ASTERX_ECUDA;
+      }
+      first = 1;
+    }
     cudaGraphExec_t exec = step_graph(a, p, ws, tab, off, totals, nb, dt, cnt, til);
     if (exec) {
-      for (int step = 0; step < nsteps; step++)
+      for (int step = first; step < nsteps; step++)
         if (cudaGraphLaunch(exec, s) != cudaSuccess) return ASTERX_ECUDA;
       return ASTERX_OK;
     }
   }
-  for (int step = 0; step < nsteps; step++)
+  for (int step = first; step < nsteps; step++)
     for (int stage = 0; stage < 4; stage++) {
       cudaError_t e = launch_batch_stage(a, tab + (size_t)stage * nb, off, totals, nb, stage, dt, cnt, s, til);
       if (e != cudaSuccess) return ASTERX_ECUDA;

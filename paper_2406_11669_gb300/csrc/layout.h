@@ -126,7 +126,11 @@ __host__ __device__ __forceinline__ void unflatten2(long t, unsigned e0, int& i,
   j = (int)r;
 }
 
-constexpr int RCHUNK = 8;  // cells per work item of the chunked (sliding-stencil) PPM reconstruction
+// Cells per work item of the chunked (sliding-stencil) kernels: PPM and WENO-Z reconstruction along an axis and
+// the PPM of the edge inputs.  Each chunked item space exists for two pencil lengths; the launch autotuner picks
+// one per kernel (the kernels take the length at run time, so both give the same results bit for bit).
+constexpr int RCHUNK = 8;
+constexpr int RCHUNK_LONG = 16;
 
 // Item spaces of the kernels (per block).  The batched launches concatenate the blocks' item spaces in
 // table order; off[kind][blk] is the first item of block blk.
@@ -142,8 +146,15 @@ enum Kind {
   KIND_PSI,          // (n+1)^3
   KIND_RCHUNK_X, KIND_RCHUNK_Y, KIND_RCHUNK_Z,  // PPM reconstruction by chunks of RCHUNK cells along the axis
   KIND_EREC,  // 6 kinds KIND_EREC + 2 df + k: face data of faces normal to df along dr = (df + 1 + k) % 3, by chunks
-  NKIND = KIND_EREC + 6
+  KIND_RCHUNK16_X = KIND_EREC + 6, KIND_RCHUNK16_Y, KIND_RCHUNK16_Z,  // the same with pencils of RCHUNK_LONG cells
+  KIND_EREC16,  // 6 kinds, as KIND_EREC with pencils of RCHUNK_LONG cells
+  NKIND = KIND_EREC16 + 6
 };
+
+// pencil length of a chunked item space
+__host__ __device__ inline int kind_chunk(int kind) {
+  return (kind >= KIND_RCHUNK16_X && kind < KIND_EREC16 + 6) ? RCHUNK_LONG : RCHUNK;
+}
 
 __host__ __device__ inline long kind_count(int kind, const Blk& b) {
   const long N0 = b.N[0], N1 = b.N[1], N2 = b.N[2];
@@ -169,16 +180,33 @@ __host__ __device__ inline long kind_count(int kind, const Blk& b) {
     case KIND_EDGES_Y: return (n0 + 1) * n1 * (n2 + 1);
     case KIND_EDGES_Z: return (n0 + 1) * (n1 + 1) * n2;
     case KIND_PSI: return (n0 + 1) * (n1 + 1) * (n2 + 1);
-    case KIND_RCHUNK_X: return ((n0 + 2 + RCHUNK - 1) / RCHUNK) * N1 * N2;
-    case KIND_RCHUNK_Y: return N0 * ((n1 + 2 + RCHUNK - 1) / RCHUNK) * N2;
-    case KIND_RCHUNK_Z: return N0 * N1 * ((n2 + 2 + RCHUNK - 1) / RCHUNK);
-    default:
-      if (kind >= KIND_EREC && kind < KIND_EREC + 6) {
-        const int df = (kind - KIND_EREC) / 2, dr = (df + 1 + (kind - KIND_EREC) % 2) % 3, de = 3 - df - dr;
+    case KIND_RCHUNK_X:
+    case KIND_RCHUNK16_X: {
+      const long ch = kind_chunk(kind);
+      return ((n0 + 2 + ch - 1) / ch) * N1 * N2;
+    }
+    case KIND_RCHUNK_Y:
+    case KIND_RCHUNK16_Y: {
+      const long ch = kind_chunk(kind);
+      return N0 * ((n1 + 2 + ch - 1) / ch) * N2;
+    }
+    case KIND_RCHUNK_Z:
+    case KIND_RCHUNK16_Z: {
+      const long ch = kind_chunk(kind);
+      return N0 * N1 * ((n2 + 2 + ch - 1) / ch);
+    }
+    default: {
+      int e = -1;
+      if (kind >= KIND_EREC && kind < KIND_EREC + 6) e = kind - KIND_EREC;
+      if (kind >= KIND_EREC16 && kind < KIND_EREC16 + 6) e = kind - KIND_EREC16;
+      if (e >= 0) {
+        const int df = e / 2, dr = (df + 1 + e % 2) % 3, de = 3 - df - dr;
         const long n[3] = {n0, n1, n2};
+        const long ch = kind_chunk(kind);
         // faces g-1..g+n along dr (chunks), g..g+n along df, g..g+n-1 along de
-        return ((n[dr] + 2 + RCHUNK - 1) / RCHUNK) * (n[df] + 1) * n[de];
+        return ((n[dr] + 2 + ch - 1) / ch) * (n[df] + 1) * n[de];
       }
+    }
   }
   return 0;
 }

@@ -19,6 +19,10 @@
 #include "kernels.h"
 #include "physics.cuh"
 
+#include <cstdlib>
+#include <mutex>
+#include <vector>
+
 namespace asterx {
 
 static __host__ int grid_for(long count, int threads) {
@@ -61,6 +65,7 @@ struct StageConsts {
   unsigned long long* stats;
   const BlockRec* tab;  // tiled batch: this stage's block records (device), else null
   const Tiling* til;    // tiled batch: the tiling (device), else null
+  int chunk;            // cells per item of the chunked kernels (set per launch)
 };
 
 // ----------------------------------------------------------------------------------------------------------
@@ -104,16 +109,167 @@ struct Batch {
   long count(int kind) const { return host_total[kind]; }
 };
 
+// ----------------------------------------------------------------------------------------------------------
+// Launch-configuration autotuner.  Every work item is independent of the launch shape (grid-stride loops; the
+// only warp-level code, the recovery's counter reduction, needs whole warps), so a launch may use any block size
+// and grid, and the chunked kernels (sliding-stencil reconstruction and edge inputs) may walk their lines in
+// pencils of RCHUNK or RCHUNK_LONG cells (separate item spaces, the same compiled kernel, so the same results).
+// The candidates are 64 or 128 threads per block (the kernels are compiled for at most 128, which keeps single
+// and batched launches of a body the same compiled code) with an oversubscribed grid (one thread per item up to
+// 64 blocks per SM) or a persistent grid (as many blocks as are resident on the SMs at once, each looping over
+// the items), times the pencil lengths.  For the kernel bodies whose outputs are a pure function of their inputs
+// (reconstruction, face solve, edge inputs, u, face and centre field, vertex potentials), the first launch of a
+// kernel at a given item count on a device, outside stream capture, times every candidate on the live data (each
+// writes the same outputs) with CUDA events, and the fastest is cached for later launches of that kernel and item
+// count; the other bodies, and launches during stream capture before tuning, take 128 threads, the
+// oversubscribed grid and pencils of RCHUNK cells.  Tuning synchronises the host with the stream once per kernel
+// and item count.  ASTERX_AUTOTUNE=0 in the environment turns it off.
+
+struct LaunchCfg {
+  int threads;
+  int persistent;
+  int variant;  // pencil length index of the chunked kernels (0: RCHUNK, 1: RCHUNK_LONG)
+};
+constexpr LaunchCfg kDefaultCfg = {128, 0, 0};
+constexpr LaunchCfg kShapes[] = {{128, 0, 0}, {64, 0, 0}, {128, 1, 0}, {64, 1, 0}};
+
+template <class Body> struct Tunable { static constexpr bool value = false; };
+template <int D, int S> struct Recon;
+template <int D> struct ReconPPM;
+template <int D> struct ReconWENO;
+template <int D> struct Faces;
+template <int D> struct FacesAlt;
+template <int DF, int K> struct EdgeRecon;
+struct UVel;
+struct BFace;
+struct BCentre;
+struct Vertex;
+template <int D, int S> struct Tunable<Recon<D, S>> { static constexpr bool value = true; };
+template <int D> struct Tunable<ReconPPM<D>> { static constexpr bool value = true; };
+template <int D> struct Tunable<ReconWENO<D>> { static constexpr bool value = true; };
+template <int D> struct Tunable<Faces<D>> { static constexpr bool value = true; };
+template <int D> struct Tunable<FacesAlt<D>> { static constexpr bool value = true; };
+template <int DF, int K> struct Tunable<EdgeRecon<DF, K>> { static constexpr bool value = true; };
+template <> struct Tunable<UVel> { static constexpr bool value = true; };
+template <> struct Tunable<BFace> { static constexpr bool value = true; };
+template <> struct Tunable<BCentre> { static constexpr bool value = true; };
+template <> struct Tunable<Vertex> { static constexpr bool value = true; };
+
+namespace {
+struct TuneEntry {
+  int dev;
+  const void* fn;
+  long n;
+  LaunchCfg cfg;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tuned;
+
+bool autotune_on() {
+  static const bool on = [] {
+    const char* e = std::getenv("ASTERX_AUTOTUNE");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &st);
+  return st != cudaStreamCaptureStatusNone;
+}
+}  // namespace
+
+template <class Kern>
+int grid_of(Kern kern, LaunchCfg c, long n) {
+  if (!c.persistent) return grid_for(n, c.threads);
+  const long want = (n + c.threads - 1) / c.threads;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c.threads, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const long cap = (long)per_sm * device_sm_count();
+  return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+// The cached configuration of kernel fn at item count n, or the timed choice among the launch shapes times
+// `variants` pencil lengths (run(cfg) launches the kernel with cfg on stream s).
+template <class Run>
+LaunchCfg choose_cfg(const void* fn, long n, int variants, cudaStream_t s, Run run) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return kDefaultCfg;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const TuneEntry& e : g_tuned)
+      if (e.dev == dev && e.fn == fn && e.n == n) return e.cfg;
+  }
+  if (stream_capturing(s)) return kDefaultCfg;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return kDefaultCfg;
+  }
+  LaunchCfg best = kDefaultCfg;
+  float best_ms = 3.0e38f;
+  run(kDefaultCfg);  // untimed: first-touch effects
+  for (int v = 0; v < variants; v++)
+    for (LaunchCfg c : kShapes) {
+      c.variant = v;
+      cudaEventRecord(e0, s);
+      run(c);
+      cudaEventRecord(e1, s);
+      float ms = 0.0f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
+          cudaGetLastError() != cudaSuccess)
+        continue;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tuned.push_back({dev, fn, n, best});
+  return best;
+}
+
+// One launch of Body over the item space `kind`; for a chunked body, `kind_long` is the same item space in
+// pencils of RCHUNK_LONG cells (-1: no choice of pencil length).
 template <class Body>
-void launch(const Single& t, const StageConsts& k, int kind, cudaStream_t s) {
+void launch(const Single& t, const StageConsts& k0, int kind, cudaStream_t s, int kind_long = -1) {
   const long n = t.count(kind);
-  if (n > 0) k_single<Body><<<grid_for(n, 128), 128, 0, s>>>(t.r, k, n);
+  if (n <= 0) return;
+  auto kern = k_single<Body>;
+  auto run = [&](LaunchCfg q) {
+    StageConsts k = k0;
+    const int kd = q.variant ? kind_long : kind;
+    k.chunk = kind_chunk(kd);
+    const long m = t.count(kd);
+    kern<<<grid_of(kern, q, m), q.threads, 0, s>>>(t.r, k, m);
+  };
+  LaunchCfg c = kDefaultCfg;
+  if (Tunable<Body>::value && autotune_on())
+    c = choose_cfg(reinterpret_cast<const void*>(kern), n, kind_long >= 0 ? 2 : 1, s, run);
+  run(c);
 }
 
 template <class Body>
-void launch(const Batch& t, const StageConsts& k, int kind, cudaStream_t s) {
+void launch(const Batch& t, const StageConsts& k0, int kind, cudaStream_t s, int kind_long = -1) {
   const long n = t.count(kind);
-  if (n > 0) k_batch<Body><<<grid_for(n, 128), 128, 0, s>>>(t.tab, t.off + (long)kind * (t.nb + 1), t.nb, k);
+  if (n <= 0) return;
+  auto kern = k_batch<Body>;
+  auto run = [&](LaunchCfg q) {
+    StageConsts k = k0;
+    const int kd = q.variant ? kind_long : kind;
+    k.chunk = kind_chunk(kd);
+    const long m = t.count(kd);
+    const long* off = t.off + (long)kd * (t.nb + 1);
+    kern<<<grid_of(kern, q, m), q.threads, 0, s>>>(t.tab, off, t.nb, k);
+  };
+  LaunchCfg c = kDefaultCfg;
+  if (Tunable<Body>::value && autotune_on())
+    c = choose_cfg(reinterpret_cast<const void*>(kern), n, kind_long >= 0 ? 2 : 1, s, run);
+  run(c);
 }
 
 // ----------------------------------------------------------------------------------------------------------
@@ -544,7 +700,7 @@ struct Recon {
 // results are those of Recon<D, 1>.  The transverse axis of smaller stride varies fastest across threads.
 template <int D>
 struct ReconPPM {
-  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts&, long t) {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts& k, long t) {
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     constexpr int TA = (D == 0) ? 1 : 0, TB = (D == 2) ? 1 : 2;
     const Blk& b = r.b;
@@ -552,8 +708,8 @@ struct ReconPPM {
     int p[3];
     int ch;
     unflatten3(t, (unsigned)b.N[TA], (unsigned)b.N[TB], p[TA], p[TB], ch);
-    const int i0 = b.g - 1 + ch * RCHUNK;
-    const int i1 = min(b.g - 1 + lenD, i0 + RCHUNK);
+    const int i0 = b.g - 1 + ch * k.chunk;
+    const int i1 = min(b.g - 1 + lenD, i0 + k.chunk);
     p[D] = i0;
     const long st = stride(b, D);
     const long c0 = lin(b, p[0], p[1], p[2]);
@@ -777,7 +933,7 @@ struct Vertex {
 // cells, so each cell forms one new curvature term and the rest of its indicators and weights (wenoz_both).
 template <int D>
 struct ReconWENO {
-  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts&, long t) {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts& k, long t) {
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     constexpr int TA = (D == 0) ? 1 : 0, TB = (D == 2) ? 1 : 2;
     const Blk& b = r.b;
@@ -785,8 +941,8 @@ struct ReconWENO {
     int p[3];
     int ch;
     unflatten3(t, (unsigned)b.N[TA], (unsigned)b.N[TB], p[TA], p[TB], ch);
-    const int i0 = b.g - 1 + ch * RCHUNK;
-    const int i1 = min(b.g - 1 + lenD, i0 + RCHUNK);
+    const int i0 = b.g - 1 + ch * k.chunk;
+    const int i1 = min(b.g - 1 + lenD, i0 + k.chunk);
     p[D] = i0;
     const long st = stride(b, D);
     const long c0 = lin(b, p[0], p[1], p[2]);
@@ -828,7 +984,7 @@ struct ReconWENO {
 // along DR takes the upper value of f-1 and the lower value of f: the values ppm_pair forms from f-3..f+2.
 template <int DF, int K>
 struct EdgeRecon {
-  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts&, long t) {
+  static __device__ __forceinline__ void run(const BlockRec& r, const StageConsts& k, long t) {
     constexpr int DR = (DF + 1 + K) % 3, DE = 3 - DF - DR;
     constexpr int TA = (DF < DE) ? DF : DE, TB = (DF < DE) ? DE : DF;  // transverse axes, smaller stride first
     const Blk& b = r.b;
@@ -839,8 +995,8 @@ struct EdgeRecon {
     unflatten3(t, (unsigned)ea, (unsigned)eb, p[TA], p[TB], ch);
     p[TA] += b.g;
     p[TB] += b.g;
-    const int i0 = b.g - 1 + ch * RCHUNK;
-    const int i1 = min(b.g + b.n[DR] + 1, i0 + RCHUNK);
+    const int i0 = b.g - 1 + ch * k.chunk;
+    const int i1 = min(b.g + b.n[DR] + 1, i0 + k.chunk);
     p[DR] = i0;
     const long st = stride(b, DR);
     const long c0 = lin(b, p[0], p[1], p[2]);
@@ -1060,6 +1216,7 @@ static StageConsts consts_of(const StageArgs& a, int stage, double dt, unsigned 
   k.stats = stats;
   k.tab = nullptr;
   k.til = nullptr;
+  k.chunk = RCHUNK;
   return k;
 }
 
@@ -1086,9 +1243,9 @@ static void seq_bfield(const T& t, const StageConsts& k, cudaStream_t s) {
 template <int D, class T>
 static void seq_dir(const T& t, const StageConsts& k, int recon, cudaStream_t s) {
   if (recon == 0) launch<Recon<D, 0>>(t, k, KIND_RECON_X + D, s);
-  else if (recon == 1) launch<ReconPPM<D>>(t, k, KIND_RCHUNK_X + D, s);
+  else if (recon == 1) launch<ReconPPM<D>>(t, k, KIND_RCHUNK_X + D, s, KIND_RCHUNK16_X + D);
   else if (recon == 3) launch<Recon<D, 3>>(t, k, KIND_RECON_X + D, s);
-  else launch<ReconWENO<D>>(t, k, KIND_RCHUNK_X + D, s);
+  else launch<ReconWENO<D>>(t, k, KIND_RCHUNK_X + D, s, KIND_RCHUNK16_X + D);
   const bool mark = g_prof.on && g_prof.n < g_prof.cap && !capturing(s);
   if (mark) cudaEventRecord(g_prof.ev[2 * g_prof.n], s);
   if (k.lxf || k.fct) launch<FacesAlt<D>>(t, k, KIND_FACES_X + D, s);
@@ -1098,12 +1255,12 @@ static void seq_dir(const T& t, const StageConsts& k, int recon, cudaStream_t s)
 
 template <class T>
 static void seq_erec(const T& t, const StageConsts& k, cudaStream_t s) {
-  launch<EdgeRecon<0, 0>>(t, k, KIND_EREC + 0, s);
-  launch<EdgeRecon<0, 1>>(t, k, KIND_EREC + 1, s);
-  launch<EdgeRecon<1, 0>>(t, k, KIND_EREC + 2, s);
-  launch<EdgeRecon<1, 1>>(t, k, KIND_EREC + 3, s);
-  launch<EdgeRecon<2, 0>>(t, k, KIND_EREC + 4, s);
-  launch<EdgeRecon<2, 1>>(t, k, KIND_EREC + 5, s);
+  launch<EdgeRecon<0, 0>>(t, k, KIND_EREC + 0, s, KIND_EREC16 + 0);
+  launch<EdgeRecon<0, 1>>(t, k, KIND_EREC + 1, s, KIND_EREC16 + 1);
+  launch<EdgeRecon<1, 0>>(t, k, KIND_EREC + 2, s, KIND_EREC16 + 2);
+  launch<EdgeRecon<1, 1>>(t, k, KIND_EREC + 3, s, KIND_EREC16 + 3);
+  launch<EdgeRecon<2, 0>>(t, k, KIND_EREC + 4, s, KIND_EREC16 + 4);
+  launch<EdgeRecon<2, 1>>(t, k, KIND_EREC + 5, s, KIND_EREC16 + 5);
 }
 
 template <class T>
@@ -1154,6 +1311,7 @@ static Single single_of(const Blk& b, const Ws& w) {
 static StageConsts zero_consts() {
   StageConsts k;
   std::memset(&k, 0, sizeof(k));
+  k.chunk = RCHUNK;
   return k;
 }
 

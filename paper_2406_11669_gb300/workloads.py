@@ -190,9 +190,10 @@ def _eval_vector_sin(modes, X, Y, Z, shape):
     return out
 
 
-def _fourier_potential(rng: Rng, nmodes: int, n, g, x0, dx, shape, Bmax):
+def _fourier_potential(rng: Rng, nmodes: int, n, g, x0, dx, shape, Bmax, with_b2=False):
     """A = sum_m c_m cos(2 pi k_m . x + phi_m) sampled at the three edge families; amplitudes rescaled so that
-    the analytic |curl A| peaks at Bmax over the cell centres (the discrete field is then close to Bmax)."""
+    the analytic |curl A| peaks at Bmax over the cell centres (the discrete field is then close to Bmax).  With
+    with_b2, also returns |curl A|^2 at the cell centres."""
     modes = _fourier_vector_modes(rng, nmodes, transverse=False)
     Xc, Yc, Zc = positions(n, g, x0, dx, CELL)
     Bc = [np.zeros(shape) for _ in range(3)]
@@ -210,6 +211,8 @@ def _fourier_potential(rng: Rng, nmodes: int, n, g, x0, dx, shape, Bmax):
         for k, c, phi in modes:
             acc += scale * c[d] * np.cos(2.0 * math.pi * (k[0] * X + k[1] * Y + k[2] * Z) + phi)
         A[name] = acc
+    if with_b2:
+        return A, scale ** 2 * (Bc[0] ** 2 + Bc[1] ** 2 + Bc[2] ** 2)
     return A
 
 
@@ -606,8 +609,9 @@ def recovery_states(n=(48, 48, 48), seed=107, Bmax=0.03) -> Workload:
     """A block whose cells hold independent seeded states for the primitive recovery, over the ranges of the
     recovery's round-trip check: rho log-uniform in [1e-10, 1], p / rho log-uniform in [1e-4, 10], Lorentz factor
     uniform in [1, 10] in a random direction; the field comes from a smooth seeded potential (|B| up to about
-    Bmax), so b^2 / rho spans many decades across the cells.  Isotropic Schwarzschild M = 0.1 at (-1, 0, 0) on
-    [-1/2, 1/2]^3; Gamma = 4/3, atmosphere floor 1e-12 (below every drawn density)."""
+    Bmax), and rho is raised where needed to keep b^2 / rho <= 100 (b^2 <= B^2 at rest, taken from the
+    potential's analytic curl).  Isotropic Schwarzschild M = 0.1 at (-1, 0, 0) on [-1/2, 1/2]^3; Gamma = 4/3,
+    atmosphere floor 1e-12 (below every drawn density)."""
     g = 3
     x0 = (-0.5, -0.5, -0.5)
     dx = tuple(1.0 / m for m in n)
@@ -628,7 +632,10 @@ def recovery_states(n=(48, 48, 48), seed=107, Bmax=0.03) -> Workload:
     psi2 = (1.0 + M / (2.0 * rr)) ** 2
     speed = np.sqrt(1.0 - 1.0 / Wl ** 2) / psi2  # gamma_ij v^i v^j = psi^4 |v|^2 = 1 - 1/W^2
     vel = [dirs[d] / norm * speed for d in range(3)]
-    A = _fourier_potential(rng, 4, n, g, x0, dx, shape, Bmax)
+    A, B2 = _fourier_potential(rng, 4, n, g, x0, dx, shape, Bmax, with_b2=True)
+    scale = np.maximum(1.0, 1.2 * B2 * psi2 ** 2 / (100.0 * rho))  # gamma_ij B^i B^j = psi^4 |B|^2
+    rho = rho * scale
+    press = press * scale
     Xv, Yv, Zv = positions(n, g, x0, dx, VERTEX)
     metric = schwarzschild_isotropic(Xv, Yv, Zv, M, centre, shape)
     params = default_params(gamma=4.0 / 3.0, gamma_atm=4.0 / 3.0, rho_atm=1e-12, K_atm=0.1, recon=RECON_PPM)
