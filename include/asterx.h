@@ -422,6 +422,12 @@ asterx_status asterx_dfma_probe(double *out, int blocks, int threads, long iters
  * error; not part of the method's interface.  d and out: device, n doubles each, caller-owned. */
 asterx_status asterx_newton_rcp(const double *d, double *out, long n, asterx_stream stream);
 
+/* The reciprocal the face solve, the WENO-Z weights and the Noble iteration use where a correctly rounded
+ * quotient is not needed: out[i] ~ 1/d[i] for n device doubles (the estimate refined by two Newton-Raphson steps
+ * for binary exponents within +-960, the quotient 1/d elsewhere).  Lets tests bound its error; not part of the
+ * method's interface.  d and out: device, n doubles each, caller-owned. */
+asterx_status asterx_recip(const double *d, double *out, long n, asterx_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

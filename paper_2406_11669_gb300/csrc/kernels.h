@@ -150,5 +150,7 @@ int device_sm_count();
 cudaError_t launch_dfma_probe(double* out, int blocks, int threads, long iters, cudaStream_t s);
 // the quartic solver's Newton-correction reciprocal on n values (measurement helper)
 cudaError_t launch_newton_rcp(const double* d, double* out, long n, cudaStream_t s);
+// the two-step reciprocal of the face solve, the WENO-Z weights and the Noble iteration (measurement helper)
+cudaError_t launch_recip(const double* d, double* out, long n, cudaStream_t s);
 
 }  // namespace asterx

@@ -89,6 +89,27 @@ __host__ __device__ __forceinline__ double newton_rcp(double d) {
 #endif
 }
 
+// Reciprocal to within about one unit in the last place where a correctly rounded quotient is not needed: the
+// reciprocal estimate refined by two Newton-Raphson steps (each squares the relative error), inside the range
+// where the estimate is normal (binary exponent within +-960, read from the bits on the integer pipe); the
+// quotient 1 / d elsewhere.  Dual numbers divide.
+__host__ __device__ __forceinline__ double recip(double d) {
+#ifdef __CUDA_ARCH__
+  const unsigned ex = ((unsigned)__double2hiint(d) >> 20) & 0x7ffu;
+  if (ex > 63u && ex < 1983u) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    r = fma(r, fma(-d, r, 1.0), r);
+    return fma(r, fma(-d, r, 1.0), r);
+  }
+#endif
+  return 1.0 / d;
+}
+template <int N>
+__host__ __device__ __forceinline__ Dual<N> recip(const Dual<N>& d) {
+  return 1.0 / d;
+}
+
 // Extreme roots of the magnetosonic quartic (Sec. 3.3): with phi = (-lambda, e_d),
 //   a = u^mu phi_mu = ud - lambda u0,  Bc = b^mu phi_mu = bd - lambda b0,
 //   G = g^{mu nu} phi_mu phi_nu = gamma^dd - (lambda + beta^d)^2 / alpha^2,
@@ -162,7 +183,7 @@ __host__ __device__ __forceinline__ void face_side(const Geo& m, double ia, doub
                                           SideOutT<T>& o, const double* roots = nullptr, bool fluxes = true) {
   const T uu = contract_sym(m.g, u, u);
   const T W = sqrt(1.0 + uu);
-  const T iW = 1.0 / W;
+  const T iW = recip(W);
   T v[3] = {u[0] * iW, u[1] * iW, u[2] * iW};
   T vl[3], Bl[3];
   lower(m.g, v, vl);
@@ -200,7 +221,7 @@ __host__ __device__ __forceinline__ void face_side(const Geo& m, double ia, doub
   const T b0 = W * Bv * ia;
   const T bd = (Bd + m.alp * b0 * ud) * iW;
   // one division for cs^2 = Gamma p / (rho h) (= Gamma (Gamma - 1) eps / h) and cA^2 = b^2 / (rho h + b^2)
-  const T ihb = 1.0 / (rhoh * (rhoh + b2));
+  const T ihb = recip(rhoh * (rhoh + b2));
   const T cs2 = gamma * press * (rhoh + b2) * ihb;
   const T ca2 = b2 * rhoh * ihb;
   Quartic Q;
@@ -229,7 +250,7 @@ __host__ __device__ __forceinline__ void face_side(const Geo& m, double ia, doub
     const double vd = val(v[d]);
     const double disc = fmax((1.0 - v2) * (Q.gdd * den - vd * vd * (1.0 - c2)), 0.0);
     const double spread = sqrt(c2 * disc);
-    const double idn = m.alp / den;
+    const double idn = m.alp * recip(den);
     const double mid = vd * (1.0 - c2);
     const double lc = -m.beta[d];
     const double lp0 = fmin((mid + spread) * idn - m.beta[d] + 1e-12 * width, lc + width);
@@ -491,7 +512,7 @@ __host__ __device__ __forceinline__ void wenoz_from_indicators(const T s[5], T e
   // both normalisations from one division where the product of the two sums is in range
   const T DD = Dh * Dl;
   if (val(DD) > 1e-290 && val(DD) < 1e290) {
-    const T r = 1.0 / (6.0 * DD);
+    const T r = recip(6.0 * DD);
     hi = Nh * Dl * r;
     lo = Nl * Dh * r;
   } else {
@@ -927,7 +948,7 @@ __host__ __device__ inline bool c2p_noble(const Geo& m, double D, const double S
   for (it = 1; it <= P.maxiter; it++) {
     const double sq = sqrt(1.0 - v2);
     const double Bz = B2 + z;
-    const double iz = 1.0 / z;
+    const double iz = recip(z);
     const double iz2 = iz * iz;
     const double p = gf * (z * (1.0 - v2) - D * sq);
     const double f0 = v2 * Bz * Bz - BS2 * (B2 + 2.0 * z) * iz2 - S2;
@@ -936,7 +957,7 @@ __host__ __device__ inline bool c2p_noble(const Geo& m, double D, const double S
     const double J01 = Bz * Bz;
     const double J10 = -BS2 * iz2 * iz - 1.0 + gf * (1.0 - v2);
     const double J11 = -0.5 * B2 + gf * (-z + 0.5 * D / sq);
-    const double idet = 1.0 / (J00 * J11 - J01 * J10);
+    const double idet = recip(J00 * J11 - J01 * J10);
     const double dz = (-f0 * J11 + J01 * f1) * idet;
     const double dv2 = (-J00 * f1 + J10 * f0) * idet;
     const bool damped = !(z + dz > 0.0);

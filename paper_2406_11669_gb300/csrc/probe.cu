@@ -56,4 +56,18 @@ cudaError_t launch_newton_rcp(const double* d, double* out, long n, cudaStream_t
   return cudaGetLastError();
 }
 
+// the two-step reciprocal applied to n values (its error bound is tested)
+__global__ void k_recip(const double* __restrict__ d, double* __restrict__ out, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = recip(d[i]);
+}
+
+cudaError_t launch_recip(const double* d, double* out, long n, cudaStream_t s) {
+  long blocks = (n + 255) / 256;
+  const long cap = 16L * device_sm_count();
+  if (blocks > cap) blocks = cap;
+  k_recip<<<(int)blocks, 256, 0, s>>>(d, out, n);
+  return cudaGetLastError();
+}
+
 }  // namespace asterx

@@ -820,7 +820,7 @@ struct FaceSolve {
     const double cmin = -fmin(0.0, fmin(s[0].lm, s[1].lm));
     const double den = cmax + cmin;
     if (den > 0.0) {
-      const double iden = 1.0 / den;
+      const double iden = recip(den);
       if (full) {
         if (ALT && k.lxf) {  // Eq. LxFfluxes: c_wave = max(c_max, c_min)
           const double cw = fmax(cmax, cmin);

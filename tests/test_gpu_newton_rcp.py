@@ -34,3 +34,32 @@ def test_newton_reciprocal_relative_error():
     print(f"largest relative error {rel.max():.3e} over {d.size} values")
     assert np.all(np.isfinite(got))
     assert rel.max() <= 1e-11
+
+
+def test_two_step_reciprocal_is_within_an_ulp_or_two():
+    """The reciprocal used where a correctly rounded quotient is not needed (face solve, WENO-Z weights, Noble
+    iteration): the estimate refined by two Newton-Raphson steps inside binary exponents +-960, 1/d outside.
+    Against numpy's correctly rounded 1/d it must be within two units in the last place everywhere, and exact
+    outside the refined range (the quotient itself)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_11669_gb300 import asterx as A
+    rng = np.random.default_rng(2407)
+    mags = 10.0 ** rng.uniform(-300.0, 300.0, 1 << 20)
+    d = mags * rng.choice([-1.0, 1.0], mags.size)
+    p2 = 2.0 ** np.arange(-1000, 1001, 7, dtype=np.float64)
+    special = np.concatenate([p2, np.nextafter(p2, 0), np.nextafter(p2, np.inf), -p2, 1.0 + 2.0 ** -np.arange(1, 53),
+                              [1.0, -1.0, 3.0, 1.0 / 3.0, 0.1, 6.0, 7.0e-289, 6.0e289, 1e-305, 1e305]])
+    d = np.concatenate([d, special])
+    dd = torch.from_numpy(d).cuda()
+    out = torch.empty_like(dd)
+    A.recip(dd, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    ref = 1.0 / d
+    ulps = np.abs(got - ref) / np.spacing(np.abs(ref))
+    print(f"largest error {ulps.max():.2f} ulp over {d.size} values")
+    assert np.all(np.isfinite(got))
+    assert ulps.max() <= 2.0
+    outside = np.abs(np.frexp(d)[1] - 1) >= 960
+    assert np.array_equal(got[outside], ref[outside])
