@@ -1,8 +1,11 @@
 """The gradient the benchmark times, checked on its own data: J = 1/2 sum_interior (D~_10 - T)^2 after ten RK4
 steps of the 64^3 weak-field block (PPM, periodic, lapse 1 - 0.01 sin 2 pi x; seeded modes and target), with
 respect to the initial primitives and potentials, against central differences of the forward steps at h = 1e-6
-(other step sizes, or a one-sided quotient, where a limiter's switching surface lies within h of the state or
-where the quotient's rounding, about 1e-16 sqrt(#cells) |D - T| / h, is not small against a small gradient).
+(other step sizes, or a one-sided quotient, where a limiter's switching surface lies within h of the state, or
+where the forward map's own small jumps are not small against the quotient: the recovery stops its Newton
+iteration at a tolerance of 1e-13, so its result jumps by about that much where the iteration count changes
+between x - h and x + h, which puts jumps of order 1e-13 / h into the quotient, summed over the cells the probe
+reaches in 40 stages; a larger h shrinks them).
 
 64 seeded probes (16 on rho, 8 on each velocity component, 8 on each potential component) and 4 seeded random
 directions over rho, v^i and A_i at once must agree to 1e-5 relative: each probe against the larger of its own
@@ -23,7 +26,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 NSTEPS = 10
-HS = (1e-6, 1e-5, 1e-4, 1e-7)
+HS = (1e-6, 1e-5, 1e-4, 1e-3, 1e-7)
 RTOL = 1e-5
 
 
