@@ -428,6 +428,12 @@ asterx_status asterx_newton_rcp(const double *d, double *out, long n, asterx_str
  * method's interface.  d and out: device, n doubles each, caller-owned. */
 asterx_status asterx_recip(const double *d, double *out, long n, asterx_stream stream);
 
+/* The corrected quotient the recovery and the centre field use to divide by sqrt(gamma) like a division:
+ * out[i] = a[i] / b[i] formed from the correctly rounded 1 / b[i] and one correction.  Lets tests check that it
+ * equals the correctly rounded quotient; not part of the method's interface.  a, b, out: device, n doubles
+ * each, caller-owned. */
+asterx_status asterx_quotient(const double *a, const double *b, double *out, long n, asterx_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

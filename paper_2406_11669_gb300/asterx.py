@@ -134,11 +134,13 @@ def lib():
         L.asterx_dfma_probe.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_long, st]
         L.asterx_newton_rcp.argtypes = [vp, vp, ctypes.c_long, st]
         L.asterx_recip.argtypes = [vp, vp, ctypes.c_long, st]
+        L.asterx_quotient.argtypes = [vp, vp, vp, ctypes.c_long, st]
         for name in ("asterx_prepare", "asterx_prim2con", "asterx_con2prim", "asterx_fill_ghosts", "asterx_rhs",
                      "asterx_rk_stage", "asterx_rk4_step", "asterx_rk2_step", "asterx_rk4_step_host", "asterx_tmunu",
                      "asterx_rk4_step_metrics", "asterx_prolong", "asterx_rk4_step_refined", "asterx_rk4_step_subcycled",
                      "asterx_profile_enable",
-                     "asterx_profile_read", "asterx_dfma_probe", "asterx_newton_rcp", "asterx_recip"):
+                     "asterx_profile_read", "asterx_dfma_probe", "asterx_newton_rcp", "asterx_recip",
+                     "asterx_quotient"):
             getattr(L, name).restype = ctypes.c_int
         if L.asterx_abi_version() != ABI_VERSION:
             raise ImportError(f"libasterx ABI {L.asterx_abi_version()} != binding ABI {ABI_VERSION}")
@@ -409,6 +411,12 @@ def profile_disable():
 def dfma_probe(out, blocks, threads, iters, stream=None):
     _check(lib().asterx_dfma_probe(ctypes.c_void_p(out.data_ptr()), int(blocks), int(threads), int(iters),
                                    _stream(stream)), "asterx_dfma_probe")
+
+
+def quotient(a, b, out, stream=None):
+    """The corrected quotient a / b (from 1 / b and one correction) of device doubles, into out."""
+    _check(lib().asterx_quotient(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                 ctypes.c_void_p(out.data_ptr()), int(a.numel()), _stream(stream)), "asterx_quotient")
 
 
 def recip(d, out, stream=None):

@@ -1231,6 +1231,12 @@ asterx_status asterx_newton_rcp(const double* d, double* out, long n, asterx_str
   return cuda_status(launch_newton_rcp(d, out, n, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+asterx_status asterx_quotient(const double* a, const double* b, double* out, long n, asterx_stream stream) {
+  if (n < 0 || (n > 0 && (!ptr_ok(a) || !ptr_ok(b) || !ptr_ok(out)))) return ASTERX_EINVAL;
+  if (n == 0) return ASTERX_OK;
+  return cuda_status(launch_quotient(a, b, out, n, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 asterx_status asterx_recip(const double* d, double* out, long n, asterx_stream stream) {
   if (n < 0 || (n > 0 && (!ptr_ok(d) || !ptr_ok(out)))) return ASTERX_EINVAL;
   if (n == 0) return ASTERX_OK;

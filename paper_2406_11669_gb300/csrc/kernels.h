@@ -152,5 +152,7 @@ cudaError_t launch_dfma_probe(double* out, int blocks, int threads, long iters, 
 cudaError_t launch_newton_rcp(const double* d, double* out, long n, cudaStream_t s);
 // the two-step reciprocal of the face solve, the WENO-Z weights and the Noble iteration (measurement helper)
 cudaError_t launch_recip(const double* d, double* out, long n, cudaStream_t s);
+// the corrected quotient a / b from 1 / b (measurement helper)
+cudaError_t launch_quotient(const double* a, const double* b, double* out, long n, cudaStream_t s);
 
 }  // namespace asterx

@@ -110,6 +110,17 @@ __host__ __device__ __forceinline__ Dual<N> recip(const Dual<N>& d) {
   return 1.0 / d;
 }
 
+// Correctly rounded a / b from y = 1 / b (itself a correctly rounded quotient), for several quotients by the same
+// b at one division: q = a y is within one ulp of a / b, the remainder a - b q is exact in one fused multiply-add,
+// and q + (a - b q) y rounds to the correctly rounded quotient (Markstein 1990; Muller et al., Handbook of
+// Floating-Point Arithmetic, the theorem on correcting a faithful quotient with a correctly rounded
+// reciprocal).  Valid away from overflow and underflow of the intermediate values; the callers divide by
+// sqrt(gamma) of a metric (about 1) values far inside the range.
+__host__ __device__ __forceinline__ double quotient_by(double a, double b, double y) {
+  const double q = a * y;
+  return fma(fma(-b, q, a), y, q);
+}
+
 // Extreme roots of the magnetosonic quartic (Sec. 3.3): with phi = (-lambda, e_d),
 //   a = u^mu phi_mu = ud - lambda u0,  Bc = b^mu phi_mu = bd - lambda b0,
 //   G = g^{mu nu} phi_mu phi_nu = gamma^dd - (lambda + beta^d)^2 / alpha^2,

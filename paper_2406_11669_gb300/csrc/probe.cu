@@ -62,6 +62,21 @@ __global__ void k_recip(const double* __restrict__ d, double* __restrict__ out, 
     out[i] = recip(d[i]);
 }
 
+// the corrected quotient applied to n pairs (checked against the correctly rounded quotient)
+__global__ void k_quotient(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out,
+                           long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = quotient_by(a[i], b[i], 1.0 / b[i]);
+}
+
+cudaError_t launch_quotient(const double* a, const double* b, double* out, long n, cudaStream_t s) {
+  long blocks = (n + 255) / 256;
+  const long cap = 16L * device_sm_count();
+  if (blocks > cap) blocks = cap;
+  k_quotient<<<(int)blocks, 256, 0, s>>>(a, b, out, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_recip(const double* d, double* out, long n, cudaStream_t s) {
   long blocks = (n + 255) / 256;
   const long cap = 16L * device_sm_count();

@@ -439,11 +439,12 @@ struct BCentre {
     box.at(t, i, j, k);
     const long c = lin(b, i, j, k);
     const double sqg = r.w.cg[CG_SQG * b.V + c];
-    // divided, not multiplied by a reciprocal: the same rounding as the oracle's, so that the centre field (and
-    // the reconstruction of its transverse components) matches bit for bit given the same face field
-    bc[c] = 0.5 * (bf[c] + bf[c + 1]) / sqg;
-    bc[b.V + c] = 0.5 * (bf[b.V + c] + bf[b.V + c + b.sy]) / sqg;
-    bc[2 * b.V + c] = 0.5 * (bf[2 * b.V + c] + bf[2 * b.V + c + b.sz]) / sqg;
+    // correctly rounded quotients, as the oracle divides, so that the centre field (and the reconstruction of its
+    // transverse components) matches bit for bit given the same face field: one division, then corrections
+    const double isqg = 1.0 / sqg;
+    bc[c] = quotient_by(0.5 * (bf[c] + bf[c + 1]), sqg, isqg);
+    bc[b.V + c] = quotient_by(0.5 * (bf[b.V + c] + bf[b.V + c + b.sy]), sqg, isqg);
+    bc[2 * b.V + c] = quotient_by(0.5 * (bf[2 * b.V + c] + bf[2 * b.V + c + b.sz]), sqg, isqg);
   }
 };
 
@@ -503,11 +504,13 @@ __device__ __forceinline__ C2PCount c2p_at(const BlockRec& r, const C2PParams& c
   bool atm = !(Dt >= m.sqg * cp.rho_atm);
   int flag = 2;
   if (!atm) {
-    // divided, as the oracle does: on the rim of the torus workload the stage's right-hand side amplifies
-    // one-ulp differences of the recovered primitives to about 1e-12 of its magnitude
-    const double D = Dt / m.sqg;
-    const double S[3] = {U.f[1][c] / m.sqg, U.f[2][c] / m.sqg, U.f[3][c] / m.sqg};
-    const double tau = U.f[4][c] / m.sqg;
+    // correctly rounded quotients, as the oracle divides: on the rim of the torus workload the stage's
+    // right-hand side amplifies one-ulp differences of the recovered primitives to about 1e-12 of its magnitude
+    const double isqg = 1.0 / m.sqg;
+    const double D = quotient_by(Dt, m.sqg, isqg);
+    const double S[3] = {quotient_by(U.f[1][c], m.sqg, isqg), quotient_by(U.f[2][c], m.sqg, isqg),
+                         quotient_by(U.f[3][c], m.sqg, isqg)};
+    const double tau = quotient_by(U.f[4][c], m.sqg, isqg);
     double Bl[3];
     lower(m.g, B, Bl);
     const double B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];

@@ -63,3 +63,27 @@ def test_two_step_reciprocal_is_within_an_ulp_or_two():
     assert ulps.max() <= 2.0
     outside = np.abs(np.frexp(d)[1] - 1) >= 960
     assert np.array_equal(got[outside], ref[outside])
+
+
+def test_corrected_quotient_is_the_correctly_rounded_quotient():
+    """Division by sqrt(gamma) in the recovery and the centre field: the quotient formed from the correctly rounded
+    1 / b and one fused correction must equal the correctly rounded a / b bit for bit (so those kernels divide
+    exactly as the oracle does), on random pairs over many decades, on b near 1 (metric determinants) and on
+    pairs whose quotients are near rounding ties."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_11669_gb300 import asterx as A
+    rng = np.random.default_rng(2408)
+    n = 1 << 21
+    a = 10.0 ** rng.uniform(-150.0, 150.0, n) * rng.choice([-1.0, 1.0], n)
+    b = 10.0 ** rng.uniform(-100.0, 100.0, n) * rng.choice([-1.0, 1.0], n)
+    b[: n // 4] = 1.0 + rng.uniform(-0.5, 2.0, n // 4)  # sqrt(gamma) of the workloads' metrics
+    m = np.arange(1, 1 << 16, dtype=np.float64)
+    a = np.concatenate([a, m * 2.0 ** -20, 1.0 + m * 2.0 ** -52])
+    b = np.concatenate([b, np.full(m.size, 3.0), 1.0 + m[::-1] * 2.0 ** -40])
+    ad, bd = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    out = torch.empty_like(ad)
+    A.quotient(ad, bd, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert np.array_equal(got, a / b), int(np.sum(got != a / b))

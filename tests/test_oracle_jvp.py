@@ -19,6 +19,7 @@ CASES = {
     "ppm_periodic_lorenz": dict(recon=W.RECON_PPM, bc=W.BC_PERIODIC, gauge=W.GAUGE_LORENZ),
     "minmod_copy_lorenz": dict(recon=W.RECON_MINMOD, bc=W.BC_COPY, gauge=W.GAUGE_LORENZ),
     "wenoz_periodic_algebraic": dict(recon=W.RECON_WENOZ, bc=W.BC_PERIODIC, gauge=W.GAUGE_ALGEBRAIC),
+    "mp5_copy_lorenz": dict(recon=W.RECON_MP5, bc=W.BC_COPY, gauge=W.GAUGE_LORENZ),
 }
 GROUPS = [(0,), (1, 2, 3), (1, 2, 3), (1, 2, 3), (4,), (5, 6, 7), (5, 6, 7), (5, 6, 7), (8,)]
 
