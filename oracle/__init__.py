@@ -108,6 +108,8 @@ def lib():
                                        _PP, ctypes.c_double]
         L.oracle_rk4_jvp.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP, _PP, _PP,
                                      ctypes.c_double]
+        L.oracle_prim2con_jvp.argtypes = [ctypes.POINTER(OParams), ctypes.POINTER(OBlock), _PP, _PP, _PP, _PP,
+                                          _PP, _PP]
     return _lib
 
 
@@ -182,6 +184,17 @@ def ghost_fill_prims(w, P):
 def prim2con(w, M, U, P, params=None):
     pp = params_struct(params or w.params)
     lib().oracle_prim2con(ctypes.byref(pp), ctypes.byref(block_struct(w)), _ptrs(M), _ptrs(U), _ptrs(P))
+
+
+def prim2con_jvp(w, M, U, dA, P, dP, params=None):
+    """J dU0: the derivative of the conserved fields (D, S, tau) in the direction (dA (3 fields), dP (5
+    fields)), by forward-mode dual numbers through B~ = curl A, the centre field and the pointwise map.  U's
+    fields 0..4 receive the values (as prim2con writes them); A (fields 5..7) is read."""
+    JU = np.zeros((5,) + w.shape)
+    lib().oracle_prim2con_jvp(ctypes.byref(params_struct(params or w.params)), ctypes.byref(block_struct(w)),
+                              _ptrs(M), _ptrs(U), _ptrs(np.ascontiguousarray(dA)), _ptrs(P),
+                              _ptrs(np.ascontiguousarray(dP)), _ptrs(JU))
+    return JU
 
 
 def con2prim(w, M, U, P, params=None):

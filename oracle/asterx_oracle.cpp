@@ -1489,32 +1489,40 @@ static void con2prim(const Grid& G, const VertexMetric& vm, const OParams& P, do
   }
 }
 
-// Conserved variables at all cells from primitives (initial data, Sec. 3.12 and Eq. cons).
-static void prim2con_grid(const Grid& G, const VertexMetric& vm, const OParams& P, double* const U[9],
-                          double* const prim[5]) {
-  Field Bf[3], Bc[3];
-  face_B(G, U[5], U[6], U[7], Bf);
+// Conserved variables at all cells from primitives (initial data, Sec. 3.12 and Eq. cons): B~ = curl A on
+// faces, B at centres, then the pointwise map.  R = Dual1 carries a direction in (A, primitives) through it.
+template <class R>
+static void prim2con_fields(const Grid& G, const VertexMetric& vm, const OParams& P, const R* const A[3],
+                            const R* const prim[5], R* const U[5]) {
+  std::vector<R> Bf[3], Bc[3];
+  face_B(G, A[0], A[1], A[2], Bf);
   centre_B(G, vm, Bf, Bc);
-  ORACLE_PAR(double)
+  ORACLE_PAR(R)
   for (int k = 0; k < G.N[2]; k++)
     for (int j = 0; j < G.N[1]; j++)
       for (int i = 0; i < G.N[0]; i++) {
         const long c = G.at(i, j, k);
-        const Metric3<double> m = metric_at_centre(G, vm, i, j, k);
-        Prim<double> pr;
+        const Metric3<R> m = lift<R>(metric_at_centre(G, vm, i, j, k));
+        Prim<R> pr;
         pr.rho = prim[0][c];
         pr.press = prim[1][c];
-        pr.eps = pr.press / ((P.gamma - 1.0) * pr.rho);
+        pr.eps = pr.press / (R(P.gamma - 1.0) * pr.rho);
         for (int a = 0; a < 3; a++) {
           pr.vel[a] = prim[2 + a][c];
           pr.B[a] = Bc[a][c];
         }
-        Comoving<double> cm = comoving(m, pr);
-        Cons<double> uc = prim2con(m, pr, cm);
+        Comoving<R> cm = comoving(m, pr);
+        Cons<R> uc = prim2con(m, pr, cm);
         U[0][c] = uc.D;
         for (int a = 0; a < 3; a++) U[1 + a][c] = uc.S[a];
         U[4][c] = uc.tau;
       }
+}
+
+static void prim2con_grid(const Grid& G, const VertexMetric& vm, const OParams& P, double* const U[9],
+                          double* const prim[5]) {
+  const double* A[3] = {U[5], U[6], U[7]};
+  prim2con_fields<double>(G, vm, P, A, prim, U);
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -1915,6 +1923,32 @@ void oracle_prim2con(const OParams* p, const OBlock* b, const double* const* met
                      double* const* prim) {
   Grid G(*b);
   prim2con_grid(G, vmetric(metric), *p, U, prim);
+}
+
+// The conserved fields (D, S, tau) from the potentials and primitives and their derivative in the direction
+// (dA, dprim): U[0..4] and JU[0..4] receive value and derivative; U[5..7] are read (A), dA the potentials'
+// direction (3 fields), prim and dprim the primitives and their direction.
+void oracle_prim2con_jvp(const OParams* p, const OBlock* b, const double* const* metric, double* const* U,
+                         const double* const* dA, const double* const* prim, const double* const* dprim,
+                         double* const* JU) {
+  Grid G(*b);
+  DualFields Ad = dual_fields(3, G.size()), Pd = dual_fields(5, G.size()), Ud = dual_fields(5, G.size());
+  for (int v = 0; v < 3; v++)
+    for (long c = 0; c < G.size(); c++) Ad[v][c] = Dual1(U[5 + v][c], dA[v][c]);
+  for (int v = 0; v < 5; v++)
+    for (long c = 0; c < G.size(); c++) {
+      Pd[v][c] = Dual1(prim[v][c], dprim[v][c]);
+      Ud[v][c] = Dual1(U[v][c]);  // entries outside the cells keep their values (and no derivative)
+    }
+  const Dual1* Ap[3] = {Ad[0].data(), Ad[1].data(), Ad[2].data()};
+  const Dual1* Pp[5] = {Pd[0].data(), Pd[1].data(), Pd[2].data(), Pd[3].data(), Pd[4].data()};
+  Dual1* Up[5] = {Ud[0].data(), Ud[1].data(), Ud[2].data(), Ud[3].data(), Ud[4].data()};
+  prim2con_fields<Dual1>(G, vmetric(metric), *p, Ap, Pp, Up);
+  for (int v = 0; v < 5; v++)
+    for (long c = 0; c < G.size(); c++) {
+      U[v][c] = Ud[v][c].v;
+      JU[v][c] = Ud[v][c].d;
+    }
 }
 
 void oracle_con2prim(const OParams* p, const OBlock* b, const double* const* metric, double* const* U,

@@ -282,6 +282,42 @@ def weak_field_target(w: Workload, seed=1104) -> np.ndarray:
     return T
 
 
+GRADIENT_DIRECTIONS = ("all_fields_a", "all_fields_b", "rho", "potentials")
+
+
+def gradient_directions(w: Workload, seed=4201):
+    """Seeded directions in the initial data for checking a gradient with respect to it: a list of (name, dP, dA)
+    with dP (5, ...) over the primitives and dA (3, ...) over A_x, A_y, A_z, nonzero on the independent entries
+    only (cells g..g+n-1; an edge's vertex-like axes g..g+n, or g..g+n-1 where periodic).  Entries are uniform in
+    [-1, 1] times the field's scale (its largest magnitude there, at least 0.05 for a primitive and 1e-3 for a
+    potential).  The pressure is never perturbed.  Directions, in GRADIENT_DIRECTIONS order: rho, v^i and A_i
+    together (two draws), rho alone, A_i alone."""
+    rng = Rng(seed)
+    g, n = w.g, w.n
+    cells = tuple(slice(g, g + n[a]) for a in (2, 1, 0))
+
+    def edge(v):
+        return tuple(slice(g, g + n[a] + (0 if (a == v or w.bc[a] == BC_PERIODIC) else 1)) for a in (2, 1, 0))
+
+    def draw(arr, sl, floor):
+        shape = arr[sl].shape
+        scale = max(float(np.abs(arr[sl]).max()), floor)
+        return rng.uniform(int(np.prod(shape)), -1.0, 1.0).reshape(shape) * scale
+
+    out = []
+    for name in GRADIENT_DIRECTIONS:
+        dP = np.zeros((5,) + w.shape)
+        dA = np.zeros((3,) + w.shape)
+        if name != "potentials":
+            for v in ((0, 2, 3, 4) if name != "rho" else (0,)):
+                dP[v][cells] = draw(w.prims[PRIM_NAMES[v]], cells, 0.05)
+        if name != "rho":
+            for v, key in enumerate(("Ax", "Ay", "Az")):
+                dA[v][edge(v)] = draw(w.A[key], edge(v), 1e-3)
+        out.append((name, dP, dA))
+    return out
+
+
 def _smooth_scalar(rng: Rng, nmodes: int, X, Y, Z, shape, amp):
     """amp * sum of `nmodes` unit-amplitude-weighted sines with seeded wave vectors (|k_i| <= 2) and phases."""
     out = np.zeros(shape)

@@ -1,21 +1,32 @@
 """The gradient the benchmark times, checked on its own data: J = 1/2 sum_interior (D~_10 - T)^2 after ten RK4
 steps of the 64^3 weak-field block (PPM, periodic, lapse 1 - 0.01 sin 2 pi x; seeded modes and target), with
-respect to the initial primitives and potentials, against central differences of the forward steps at h = 1e-6
-(other step sizes, or a one-sided quotient, where a limiter's switching surface lies within h of the state, or
-where the forward map's own small jumps are not small against the quotient: the recovery stops its Newton
-iteration at a tolerance of 1e-13, so its result jumps by about that much where the iteration count changes
-between x - h and x + h, which puts jumps of order 1e-13 / h into the quotient, summed over the cells the probe
-reaches in 40 stages; a larger h shrinks them).
+respect to the initial primitives and potentials, formed as the benchmark forms it (checkpointed forward, the
+adjoint of ten steps, the adjoint of prim->cons).
 
-64 seeded probes (16 on rho, 8 on each velocity component, 8 on each potential component) and 4 seeded random
-directions over rho, v^i and A_i at once must agree to 1e-5 relative: each probe against the larger of its own
-magnitude and 5% of its field's largest gradient entry (a probe whose gradient is tiny is judged on the field's
-scale, which keeps limiter switching in the reach of the difference quotient from deciding it), and at least
-95% of the probes also against their own magnitude alone.  The pressure is left out: it is uniform
-in this workload (p = 1), so PPM's limiter sits exactly on its switching surface in p, where the derivative is
-one-sided and no difference quotient is linear in h.  The forward steps run through the same library entry points
-the gradient's forward pass uses (each verified against the oracle elsewhere); the loss difference is formed as
+Exact check.  Four seeded directions in (rho, v^i, A_i) (two over all of them, one over rho, one over A_i; the
+pressure is held fixed) against the oracle's derivative along the same direction, carried by forward-mode dual
+numbers through prim->cons and the ten steps (tests/golden/weak_field_gradient.txt, written by the script beside
+it from the oracle alone).  Both are the derivative of the branch every limiter is on, so they agree to the
+rounding of two different evaluation orders: within 1e-12 of sum_i |g_i d_i| (measured on GB300: 2e-17 to 3e-16
+of it, 2e-14 to 5e-13 of the value itself), and J itself to 1e-11.
+
+Finite differences of the library's own forward steps.  64 seeded single-entry probes (16 on rho, 8 on each v^i,
+8 on each A_i) and 4 seeded directions over rho, v^i, A_i at once, against central and one-sided difference
+quotients at h = 1e-6, 1e-5, 1e-4, 1e-3, 1e-7 (times the field's scale).  The forward map is only piecewise smooth:
+PPM's limiter has kinks (where a slope changes branch), its extremum clipping is discontinuous (a face value jumps
+to the cell average when the data become monotone), and in this workload some limiter inputs are exactly flat at
+the state (the pressure is uniform, p = 1), so the map is one-sided there.  A perturbation of size h crosses a
+number of such surfaces proportional to h, so jumps leave an error in the quotient that does not shrink with h; on
+a single-entry probe few surfaces lie within reach, on a whole-domain direction many do.  Measured on GB300,
+against max(|fd|, 5% of the field's largest gradient entry): median probe 2.6e-6, 50 of 64 within 1e-5, the worst
+5.5e-4 (a probe whose one-sided quotients differ at every h: a surface at the state); the whole-domain directions
+agree to 4e-9 to 2.7e-7 of sum_i |g_i d_i| (up to 1e-4 of the cancelling sum itself), with quotients that wander
+by that much between h = 1e-6 and 1e-8 instead of converging.  The assertions are set at that resolution: every
+probe within 2e-3, the median within 1e-5, at least 70% within 1e-5, the directions within 2e-6 of
+sum_i |g_i d_i|.  The exact check above is what pins the gradient's precision.  The loss difference is formed as
 1/2 sum (D+ - D-)(D+ + D- - 2T), which avoids the cancellation of two nearly equal sums of squares."""
+import os
+
 import numpy as np
 import pytest
 
@@ -28,73 +39,120 @@ pytestmark = pytest.mark.gpu
 NSTEPS = 10
 HS = (1e-6, 1e-5, 1e-4, 1e-3, 1e-7)
 RTOL = 1e-5
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "weak_field_gradient.txt")
 
 
-def test_ten_step_gradient_matches_central_differences():
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    from paper_2406_11669_gb300 import asterx as A
-    w = W.weak_field_modes()
-    dev = torch.device("cuda")
-    M = torch.from_numpy(np.ascontiguousarray(np.stack([w.metric[k] for k in W.METRIC_NAMES]))).to(dev)
-    P0 = torch.from_numpy(np.ascontiguousarray(np.stack([w.prims[k] for k in W.PRIM_NAMES]))).to(dev)
-    base = torch.zeros((9,) + w.shape, dtype=torch.float64, device=dev)
-    for v, name in ((5, "Ax"), (6, "Ay"), (7, "Az")):
-        base[v] = torch.from_numpy(w.A[name]).to(dev)
-    base[8] = torch.from_numpy(w.Psi).to(dev)
-    T = torch.from_numpy(W.weak_field_target(w)).to(dev)
-    g, n = w.g, w.n
-    inter = (slice(g, g + n[2]), slice(g, g + n[1]), slice(g, g + n[0]))
-    s = A.Solver.for_workload(w, device=dev)
-    s.prepare(M)
+class Problem:
+    """The workload on the device, its gradient as the benchmark forms it, and the forward map for differences."""
 
-    def final_density(P, pot):
-        U = pot.clone()
+    def __init__(self):
+        from paper_2406_11669_gb300 import asterx as A
+        w = W.weak_field_modes()
+        dev = torch.device("cuda")
+        self.w, self.dev = w, dev
+        M = torch.from_numpy(np.ascontiguousarray(np.stack([w.metric[k] for k in W.METRIC_NAMES]))).to(dev)
+        self.P0 = torch.from_numpy(np.ascontiguousarray(np.stack([w.prims[k] for k in W.PRIM_NAMES]))).to(dev)
+        self.base = torch.zeros((9,) + w.shape, dtype=torch.float64, device=dev)
+        for v, name in ((5, "Ax"), (6, "Ay"), (7, "Az")):
+            self.base[v] = torch.from_numpy(w.A[name]).to(dev)
+        self.base[8] = torch.from_numpy(w.Psi).to(dev)
+        self.T = torch.from_numpy(W.weak_field_target(w)).to(dev)
+        g, n = w.g, w.n
+        self.inter = (slice(g, g + n[2]), slice(g, g + n[1]), slice(g, g + n[0]))
+        s = A.Solver.for_workload(w, device=dev)
+        s.prepare(M)
+        self.s = s
+        U = self.base.clone()
         s.fill_ghosts(U)
+        P = self.P0.clone()
+        s.prim2con(U, P)
+        U0 = U.clone()
+        ckpt = [torch.empty_like(U) for _ in range(NSTEPS)]
+        s.rk4_steps_checkpointed(U, P, w.dt, ckpt)
+        lam = torch.zeros_like(U)
+        lam[(0,) + self.inter] = U[(0,) + self.inter] - self.T[self.inter]
+        s.rk4_adjoint_steps(ckpt, P, lam, w.dt)
+        lamP = torch.zeros_like(self.P0)
+        s.prim2con_adjoint(U0, self.P0, lam, lamP)
+        torch.cuda.synchronize()
+        self.gP, self.gU = lamP.cpu().numpy(), lam.cpu().numpy()
+        self.D_last = U[0][self.inter].clone()
+        r = self.D_last - self.T[self.inter]
+        self.J = 0.5 * float(torch.sum(r * r))
+
+    def final_density(self, P, pot):
+        U = pot.clone()
+        self.s.fill_ghosts(U)
         Pw = P.clone()
-        s.prim2con(U, Pw)
+        self.s.prim2con(U, Pw)
         for _ in range(NSTEPS):
-            s.rk4_step(U, Pw, w.dt)
-        return U[0][inter].clone()
+            self.s.rk4_step(U, Pw, self.w.dt)
+        return U[0][self.inter].clone()
 
-    # the gradient, as the benchmark forms it
-    U = base.clone()
-    s.fill_ghosts(U)
-    P = P0.clone()
-    s.prim2con(U, P)
-    U0 = U.clone()
-    ckpt = [torch.empty_like(U) for _ in range(NSTEPS)]
-    s.rk4_steps_checkpointed(U, P, w.dt, ckpt)
-    lam = torch.zeros_like(U)
-    lam[(0,) + inter] = U[(0,) + inter] - T[inter]
-    s.rk4_adjoint_steps(ckpt, P, lam, w.dt)
-    lamP = torch.zeros_like(P0)
-    s.prim2con_adjoint(U0, P0, lam, lamP)
-    torch.cuda.synchronize()
-    gP, gU = lamP.cpu().numpy(), lam.cpu().numpy()
-    # forward without checkpoints reproduces the checkpointed forward
-    D_ref = final_density(P0, base)
-    assert torch.equal(D_ref, U[0][inter])
-
-    def dJ(dP, dpot):
-        """(J(x + d) - J(x), J(x) - J(x - d)) for the direction d = (dP, dpot) (device arrays), each formed as
-        1/2 sum (D1 - D0)(D1 + D0 - 2T)."""
-        Dp = final_density(P0 + dP, base + dpot)
-        Dm = final_density(P0 - dP, base - dpot)
-        up = float(torch.sum(0.5 * (Dp - D_ref) * (Dp + D_ref - 2.0 * T[inter])))
-        down = float(torch.sum(0.5 * (D_ref - Dm) * (D_ref + Dm - 2.0 * T[inter])))
+    def dJ(self, dP, dpot, D_ref):
+        """(J(x + d) - J(x), J(x) - J(x - d)) for the direction d = (dP, dpot) (device arrays)."""
+        T = self.T[self.inter]
+        Dp = self.final_density(self.P0 + dP, self.base + dpot)
+        Dm = self.final_density(self.P0 - dP, self.base - dpot)
+        up = float(torch.sum(0.5 * (Dp - D_ref) * (Dp + D_ref - 2.0 * T)))
+        down = float(torch.sum(0.5 * (D_ref - Dm) * (D_ref + Dm - 2.0 * T)))
         return up, down
 
+
+@pytest.fixture(scope="module")
+def problem():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return Problem()
+
+
+def read_golden():
+    rows = {}
+    with open(GOLDEN) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, J, dJ = line.split()
+            rows[name] = (float(J), float(dJ))
+    return rows
+
+
+def test_ten_step_gradient_matches_oracle_dual_numbers(problem):
+    pb = problem
+    gold = read_golden()
+    assert set(gold) == set(W.GRADIENT_DIRECTIONS)
+    Jo = next(iter(gold.values()))[0]
+    print("J", pb.J, "oracle", Jo)
+    assert abs(pb.J - Jo) <= 1e-11 * Jo, (pb.J, Jo)
+    report = []
+    for name, dP, dA in W.gradient_directions(pb.w):
+        ad = float(np.sum(pb.gP * dP) + np.sum(pb.gU[5:8] * dA))
+        mag = float(np.sum(np.abs(pb.gP * dP)) + np.sum(np.abs(pb.gU[5:8] * dA)))
+        ref = gold[name][1]
+        report.append((name, ad, ref, abs(ad - ref) / mag, abs(ad - ref) / abs(ref)))
+    print("directions (name, adjoint, oracle, |diff| / sum|g d|, |diff| / |oracle|):", report)
+    for name, ad, ref, rel_mag, _ in report:
+        assert rel_mag <= 1e-12, (name, ad, ref, rel_mag)
+
+
+def test_ten_step_gradient_matches_differences(problem):
+    pb = problem
+    w, P0, base, gP, gU = pb.w, pb.P0, pb.base, pb.gP, pb.gU
+    inter = pb.inter
+    # forward without checkpoints reproduces the checkpointed forward
+    D_ref = pb.final_density(P0, base)
+    assert torch.equal(D_ref, pb.D_last)
+
     def closest(ad, quotient, floor):
-        """(error against max(|fd|, floor), error against |fd| alone, h): the smallest relative differences of ad
-        from the difference quotients over HS, stopping at the first step size that agrees.  PPM's limiters make
-        the map piecewise smooth: where a switching surface lies within h of the state, the central quotient
-        mixes two branches, and the adjoint (the derivative of the branch the state is on) equals one of the
-        one-sided quotients instead; where the gradient entry is small, a larger h keeps the quotient's rounding
-        below it.  An adjoint error shows in all three quotients at every h."""
-        best, own = None, None
+        """(error against max(|fd|, floor), error against |fd| alone, h, one_sided): the smallest relative
+        differences of ad from the central and one-sided quotients over HS, stopping at the first step size that
+        agrees to RTOL; one_sided: the one-sided quotients differ by more than 1e-3 of their size at every
+        h >= 1e-6 (a limiter's switching surface within reach at every usable h)."""
+        best, own, one_sided = None, None, True
         for h in HS:
             up, down = quotient(h)
+            if h >= 1e-6:
+                one_sided = one_sided and abs(up - down) > 100.0 * RTOL * max(abs(up), abs(down), floor)
             for fd in (0.5 * (up + down), up, down):
                 e = abs(ad - fd)
                 b, o = e / max(abs(fd), floor), e / max(abs(fd), 1e-300)
@@ -102,14 +160,12 @@ def test_ten_step_gradient_matches_central_differences():
                 own = o if own is None else min(own, o)
             if own <= RTOL:
                 break
-        return best, own, h
+        return best, own, h, one_sided
 
     rng = W.Rng(4104)
     pick = lambda lo, hi: int(lo + min(int(rng.uniform(1)[0] * (hi - lo)), hi - lo - 1))
     probes = [(0, 16)] + [(v, 8) for v in (2, 3, 4)] + [(v, 8) for v in (5, 6, 7)]
-    worst = 0.0
-    smaller = 0
-    tight = 0  # probes within RTOL of their own magnitude
+    records = []
     for v, count in probes:
         sl = inter if v < 5 else independent(w, v)
         arr, grad = (P0, gP[v]) if v < 5 else (base, gU[v])
@@ -121,32 +177,36 @@ def test_ten_step_gradient_matches_central_differences():
             def quotient(h):
                 d = torch.zeros_like(arr)
                 d[(v,) + idx] = h * scale
-                up, down = dJ(d, torch.zeros_like(base)) if v < 5 else dJ(torch.zeros_like(P0), d)
+                up, down = (pb.dJ(d, torch.zeros_like(base), D_ref) if v < 5 else
+                            pb.dJ(torch.zeros_like(P0), d, D_ref))
                 return up / (h * scale), down / (h * scale)
 
-            err, own, h = closest(grad[idx], quotient, 0.05 * gmax)
-            worst = max(worst, err)
-            smaller += h != HS[0]
-            tight += own <= RTOL
-            assert err <= RTOL, (v, idx, grad[idx], err)
-    # random directions over rho, v^i and A_i together
+            err, own, h, one_sided = closest(grad[idx], quotient, 0.05 * gmax)
+            records.append((v, idx, float(grad[idx]), float(err), float(own), h, bool(one_sided)))
+    directions = []
     for q in range(4):
         dP = torch.zeros_like(P0)
         dA = torch.zeros_like(base)
-        ad = 0.0
+        ad, mag = 0.0, 0.0
         for v in (0, 2, 3, 4, 5, 6, 7):
             sl = inter if v < 5 else independent(w, v)
             arr = P0 if v < 5 else base
             scale = max(float(arr[v][sl].abs().max()), 0.05 if v < 5 else 1e-3)
             shape = arr[v][sl].shape
             r = rng.uniform(int(np.prod(shape)), -1.0, 1.0).reshape(shape) * scale
-            tgt = dP if v < 5 else dA
-            tgt[v][sl] = torch.from_numpy(r).to(dev)
-            ad += float(np.sum((gP[v] if v < 5 else gU[v])[sl] * r))
-        err, _, h = closest(ad, lambda h: tuple(x / h for x in dJ(h * dP, h * dA)), 0.0)
-        worst = max(worst, err)
-        smaller += h != HS[0]
-        assert err <= RTOL, (q, ad, err)
-    assert tight >= 0.95 * 64, tight
-    print(f"worst relative difference {worst:.2e} over 64 probes and 4 directions; {smaller} needed another h; "
-          f"{tight} of 64 probes within {RTOL} of their own magnitude")
+            (dP if v < 5 else dA)[v][sl] = torch.from_numpy(r).to(pb.dev)
+            gr = (gP[v] if v < 5 else gU[v])[sl] * r
+            ad += float(np.sum(gr))
+            mag += float(np.sum(np.abs(gr)))
+        err, _, h, _ = closest(ad, lambda h: tuple(x / h for x in pb.dJ(h * dP, h * dA, D_ref)), 0.0)
+        directions.append((q, ad, mag, err * abs(ad) / mag, h))
+    for r in records:
+        print("probe", r)
+    print("directions (q, adjoint, sum|g d|, |diff| / sum|g d|, h):", directions)
+    errs = np.array([r[3] for r in records])
+    print(f"probes: median {np.median(errs):.2e}, max {errs.max():.2e}, within {RTOL}: {(errs <= RTOL).sum()} "
+          f"of 64; one-sided at every h: {sum(r[6] for r in records)}")
+    assert errs.max() <= 2e-3, [r for r in records if r[3] > 2e-3]
+    assert np.median(errs) <= RTOL, np.median(errs)
+    assert (errs <= RTOL).sum() >= 0.7 * len(errs), (errs <= RTOL).sum()
+    assert max(d[3] for d in directions) <= 2e-6, directions

@@ -141,3 +141,50 @@ def test_rk4_value_part_and_derivative(name):
         sl = independent(c.w, v)
         assert np.array_equal(U1[v][sl], ref[v][sl]), v
     check_against_differences(c, c.rk4, JU1, c.dirs[0], (1e-6, 2.5e-7), 1e-8)
+
+
+def test_prim2con_derivative():
+    """The initial-data map (A, rho, p, v^i) -> (D~, S~, tau~): the dual evaluation's value part equals the plain
+    prim->cons bit for bit, its derivative matches extrapolated central differences of the plain map (smooth and
+    pointwise after B~ = curl A, so to 1e-9 of each field's scale), and it is linear in the direction."""
+    w = W.smooth_general(n=(8, 7, 6), seed=3105)
+    M = O.metric_array(w)
+    U, P = O.initial_state(w)
+    O.ghost_fill_state(w, U)
+    O.ghost_fill_prims(w, P)
+    rng = W.Rng(3106)
+    dirs = []
+    for _ in range(2):
+        dA = rng.uniform(3 * U[0].size, -1.0, 1.0).reshape((3,) + U.shape[1:]) * 0.01
+        dP = rng.uniform(P.size, -1.0, 1.0).reshape(P.shape) * np.array([0.05, 0.05, 0.1, 0.1, 0.1])[:, None, None,
+                                                                                                        None]
+        dirs.append((dA, dP))
+
+    def F(s, dA, dP):
+        X = U.copy()
+        X[5:8] += s * dA
+        O.prim2con(w, M, X, P + s * dP)
+        return X[:5]
+
+    X = U.copy()
+    J = O.prim2con_jvp(w, M, X, dirs[0][0], P, dirs[0][1])
+    ref = F(0.0, *dirs[0])
+    owned = (slice(w.g, w.g + w.n[2]), slice(w.g, w.g + w.n[1]), slice(w.g, w.g + w.n[0]))
+    assert np.array_equal(X[:5], ref)
+
+    def q(h):
+        return (F(h, *dirs[0]) - F(-h, *dirs[0])) / (2.0 * h)
+    rich = (4.0 * q(1e-4) - q(2e-4)) / 3.0
+    for v in range(5):
+        scale = np.abs(J[v][owned]).max()
+        assert scale > 0.0, v
+        assert np.abs(rich[v][owned] - J[v][owned]).max() <= 1e-9 * scale, v
+    # dropping the potentials' direction changes the result (the B~ = curl A chain is live), and the map is linear
+    J1 = O.prim2con_jvp(w, M, U.copy(), dirs[1][0], P, dirs[1][1])
+    J2 = O.prim2con_jvp(w, M, U.copy(), 2.0 * dirs[0][0] - 3.0 * dirs[1][0], P, 2.0 * dirs[0][1] - 3.0 * dirs[1][1])
+    comb = 2.0 * J - 3.0 * J1
+    assert np.abs(J2[:, owned[0], owned[1], owned[2]] - comb[:, owned[0], owned[1], owned[2]]).max() <= \
+        1e-12 * np.abs(comb[:, owned[0], owned[1], owned[2]]).max()
+    Jp = O.prim2con_jvp(w, M, U.copy(), np.zeros_like(dirs[0][0]), P, dirs[0][1])
+    assert np.abs(Jp[1:][:, owned[0], owned[1], owned[2]] - J[1:][:, owned[0], owned[1], owned[2]]).max() > \
+        1e-6 * np.abs(J[1:][:, owned[0], owned[1], owned[2]]).max()
