@@ -130,6 +130,14 @@ __host__ __device__ __forceinline__ double quotient_by(double a, double b, doubl
 struct Quartic {
   double A4, C2, cs2, u0, ud, b0, bd, betad, ia2, gdd;
   __host__ __device__ __forceinline__ double newton(double lam, double width) const {
+    return newton_cut<0>(lam, width, 0.0);
+  }
+  // The iteration, ended early once the iterate has passed `cut` in the direction of travel (kDir = +1 for the
+  // largest root, approached from above; kDir = -1 for the smallest, from below; 0: no cut).  Every iterate lies
+  // outside the root, so an iterate past `cut` shows that the root is past it too: the caller, which only needs
+  // the larger (smaller) of this root and `cut`, has its answer without the rest of the iteration.
+  template <int kDir>
+  __host__ __device__ __forceinline__ double newton_cut(double lam, double width, double cut) const {
     // loop-invariant factors of Q' (Q itself keeps its factored form; Q' only scales the correction):
     //   dr/dlam = ka a + kb bc,  dG/dlam = kg (lam + beta^d),  d(A4 a^4)/dlam = k4 a^3
     const double ka = 2.0 * C2 * u0, kb = -2.0 * cs2 * b0, kg = -2.0 * ia2, k4 = -4.0 * A4 * u0;
@@ -139,6 +147,8 @@ struct Quartic {
     const double thr = 3e-9 * (fabs(lam) + width);
 #pragma unroll 1
     for (int it = 0; it < 60; it++) {
+      if (kDir > 0 && lam <= cut) break;
+      if (kDir < 0 && lam >= cut) break;
       const double a = ud - lam * u0;
       const double bc = bd - lam * b0;
       const double lb = lam + betad;
@@ -187,11 +197,14 @@ struct QuarticT {
 // false skips the magnetosonic speeds (o.lm, o.lp unset: prim->cons and fluxes only); `roots`, when given, holds
 // the two speeds (lambda_+, lambda_-) already found for these inputs, and replaces the Newton iteration.
 // fluxes = false skips prim->cons and the fluxes (o.U, o.F unset: speeds and v~ only), for faces whose fluxes
-// nothing reads.
-template <class T, bool kSpeeds = true>
+// nothing reads.  With kCut, the Newton iterations of lambda_+ and lambda_- stop once they pass cut_p and cut_m
+// (Quartic::newton_cut): for a caller that needs only max(cut_p, lambda_+) and min(cut_m, lambda_-), the result
+// then carries the same information.
+template <class T, bool kSpeeds = true, bool kCut = false>
 __host__ __device__ __forceinline__ void face_side(const Geo& m, double ia, double width, int d, T rho, T press,
                                           const T u[3], const T B[3], double gamma, double gfac,
-                                          SideOutT<T>& o, const double* roots = nullptr, bool fluxes = true) {
+                                          SideOutT<T>& o, const double* roots = nullptr, bool fluxes = true,
+                                          double cut_p = 0.0, double cut_m = 0.0) {
   const T uu = contract_sym(m.g, u, u);
   const T W = sqrt(1.0 + uu);
   const T iW = recip(W);
@@ -266,8 +279,8 @@ __host__ __device__ __forceinline__ void face_side(const Geo& m, double ia, doub
     const double lc = -m.beta[d];
     const double lp0 = fmin((mid + spread) * idn - m.beta[d] + 1e-12 * width, lc + width);
     const double lm0 = fmax((mid - spread) * idn - m.beta[d] - 1e-12 * width, lc - width);
-    lp = Q.newton(lp0, width);
-    lm = Q.newton(lm0, width);
+    lp = Q.newton_cut<kCut ? 1 : 0>(lp0, width, cut_p);
+    lm = Q.newton_cut<kCut ? -1 : 0>(lm0, width, cut_m);
   }
   if constexpr (sizeof(T) == sizeof(double)) {
     o.lp = lp;

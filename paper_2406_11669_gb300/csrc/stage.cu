@@ -807,17 +807,41 @@ struct FaceSolve {
     const double width = fg[FG_WIDTH * b.V + c];
     const double Bn = r.w.bf[D * b.V + c] * fg[FG_ISQG * b.V + c];
     SideOut s[2];
+    // Where the two sides' reconstructed inputs are equal bit for bit (uniform data), the second side's outputs are
+    // the first side's, and are copied.  Otherwise, unless the adjoint keeps the four roots, the second side's
+    // speeds are iterated only as far as HLLE needs them: it reads c_max = max(0, lambda_+^L, lambda_+^R) and
+    // c_min = -min(0, lambda_-^L, lambda_-^R), so lambda_+^R stops once its iterate passes max(0, lambda_+^L) and
+    // lambda_-^R once it passes min(0, lambda_-^L); c_max and c_min are those of the full iteration.
+    const double* __restrict__ rside[2] = {r.w.rec + NREC * b.V + (c - st), r.w.rec + c};
     double Bt[2][2];  // transverse B^T1, B^T2 (undensitised) of each side
 #pragma unroll
     for (int side = 0; side < 2; side++) {
-      const long cc = side == 0 ? c - st : c;
-      const double* __restrict__ rr = r.w.rec + (side == 0 ? NREC : 0) * b.V + cc;
-      const double u[3] = {rr[2 * b.V], rr[3 * b.V], rr[4 * b.V]};
+      const double* __restrict__ rr = rside[side];
+      double in[7];  // rho, p, u^x, u^y, u^z, B^T1, B^T2
+#pragma unroll
+      for (int v = 0; v < 7; v++) in[v] = rr[v * b.V];
+      Bt[side][0] = in[5];
+      Bt[side][1] = in[6];
+      const double u[3] = {in[2], in[3], in[4]};
       double B[3];
       B[D] = Bn;
-      B[T1] = Bt[side][0] = rr[5 * b.V];
-      B[T2] = Bt[side][1] = rr[6 * b.V];
-      face_side(m, ia, width, D, rr[0], rr[b.V], u, B, k.gamma, k.gfac, s[side], nullptr, full);
+      B[T1] = in[5];
+      B[T2] = in[6];
+      if (side == 0) {
+        face_side(m, ia, width, D, in[0], in[1], u, B, k.gamma, k.gfac, s[0], nullptr, full);
+        continue;
+      }
+      bool same = true;  // bitwise, on the integer pipe
+#pragma unroll
+      for (int v = 0; v < 7; v++)
+        same = same && __double_as_longlong(in[v]) == __double_as_longlong(rside[0][v * b.V]);
+      if (same) {
+        s[1] = s[0];
+      } else {
+        const bool keep = r.w.roots != nullptr;  // no cut: the roots are kept
+        face_side<double, true, true>(m, ia, width, D, in[0], in[1], u, B, k.gamma, k.gfac, s[1], nullptr, full,
+                                      keep ? -INFINITY : fmax(0.0, s[0].lp), keep ? INFINITY : fmin(0.0, s[0].lm));
+      }
     }
     const double cmax = fmax(0.0, fmax(s[0].lp, s[1].lp));
     const double cmin = -fmin(0.0, fmin(s[0].lm, s[1].lm));
