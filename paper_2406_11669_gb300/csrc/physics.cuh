@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <type_traits>
 
 #include "dual.cuh"
 #include "layout.h"
@@ -507,58 +508,135 @@ __host__ __device__ __forceinline__ void ppm_limit(T ai, T& l, T& r) {
   }
 }
 
-// WENO-Z values at both faces of the middle cell of s[0..4].  The lower face uses the mirrored stencil, whose
-// smoothness indicators are those of the upper face in reverse order, so the indicators are shared.  With
-// e_k = beta_k + eps and p = 2 the nonlinear weights alpha_k = d_k (1 + (tau5 / e_k)^2) are proportional to
+// WENO-Z arithmetic in double is written as explicit fused multiply-adds throughout, so that the compiler cannot
+// fuse the same expression differently in different kernels or contexts: a value formed at a pencil's first cell
+// equals the value carried into it bit for bit, and a block stepped alone, in a batch or as a tile of a domain
+// reconstructs bit for bit alike.  Dual numbers (the adjoint) take the plain expressions.
+template <class T>
+__host__ __device__ __forceinline__ T fmadd(T a, T b, T c) {
+  if constexpr (std::is_same<T, double>::value) return fma(a, b, c);
+  else return a * b + c;
+}
+
+// The three-point WENO candidates (times 6): c0(a, b, c) = 2 a - 7 b + 11 c and the two that are mirror images of
+// each other, cp(a, b, c) = -a + 5 b + 2 c and cm(a, b, c) = 2 a + 5 b - c.  The upper face's cp on (s1, s2, s3) is
+// the next cell's lower-face cp on its (s0, s1, s2), and the upper face's cm on (s2, s3, s4) the next cell's
+// lower-face cm on its (s1, s2, s3), so a sliding pencil carries them from one cell to the next.
+template <class T>
+__host__ __device__ __forceinline__ T weno_cand_0(T a, T b, T c) {
+  return fmadd(T(11.0), c, fmadd(T(-7.0), b, 2.0 * a));
+}
+template <class T>
+__host__ __device__ __forceinline__ T weno_cand_p(T a, T b, T c) {
+  return fmadd(T(2.0), c, fmadd(T(5.0), b, -a));
+}
+template <class T>
+__host__ __device__ __forceinline__ T weno_cand_m(T a, T b, T c) {
+  return fmadd(T(2.0), a, fmadd(T(5.0), b, -c));
+}
+
+// WENO-Z values at both faces of the middle cell of s[0..4], from tau5 = |beta_0 - beta_2| and e_k = beta_k + eps
+// (wenoz_indicators).  The lower face uses the mirrored stencil, whose smoothness indicators are those of the
+// upper face in reverse order, so the indicators are shared.  With p = 2 the nonlinear weights alpha_k = d_k (1 + (tau5 / e_k)^2) are proportional to
 // d_k (e_k^2 + tau5^2) prod_{j != k} e_j^2, which needs no division before the normalisation (e_k >= eps keeps the
 // products above the smallest normal double; out-of-range products take the form with the quotients).
+// Candidates: upper face h0 = c0(s0, s1, s2), h1 = cp(s1, s2, s3), h2 = cm(s2, s3, s4); lower face
+// l0 = c0(s4, s3, s2), l1 = cm(s1, s2, s3), l2 = cp(s0, s1, s2).
 template <class T>
-__host__ __device__ __forceinline__ void wenoz_from_indicators(const T s[5], T e0, T e1, T e2, T& lo, T& hi) {
-  const T tau5 = fabs(e0 - e2);
-  const T tt = tau5 * tau5;
+__host__ __device__ __forceinline__ void wenoz_combine(T tau5, T e0, T e1, T e2, T h0, T h1, T h2, T l0, T l1, T l2,
+                                                       T& lo, T& hi) {
   const T E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
-  T a0 = (E0 + tt) * (E1 * E2), a1 = (E1 + tt) * (E0 * E2), a2 = (E2 + tt) * (E0 * E1);
+  T a0 = fmadd(tau5, tau5, E0) * (E1 * E2), a1 = fmadd(tau5, tau5, E1) * (E0 * E2),
+    a2 = fmadd(tau5, tau5, E2) * (E0 * E1);
   if (!(isfinite(val(a0 + a1 + a2)) && val(a0 + a1 + a2) > 0.0)) {  // products out of range
     const T r0 = tau5 / e0, r1 = tau5 / e1, r2 = tau5 / e2;
-    a0 = 1.0 + r0 * r0;
-    a1 = 1.0 + r1 * r1;
-    a2 = 1.0 + r2 * r2;
+    a0 = fmadd(r0, r0, T(1.0));
+    a1 = fmadd(r1, r1, T(1.0));
+    a2 = fmadd(r2, r2, T(1.0));
   }
   // upper face: linear weights (1/10, 6/10, 3/10) on the sub-stencils ending at, centred on, starting at i, with the
   // candidates' common factor 1/6 and the weights' 1/10 taken out of numerator and denominator; lower face: the
   // mirrored stencil, whose indicator k is indicator 2-k here
   const T w1 = 6.0 * a1;
-  const T Nh = a0 * (2.0 * s[0] - 7.0 * s[1] + 11.0 * s[2]) + w1 * (-s[1] + 5.0 * s[2] + 2.0 * s[3]) +
-               (3.0 * a2) * (2.0 * s[2] + 5.0 * s[3] - s[4]);
-  const T Nl = a2 * (2.0 * s[4] - 7.0 * s[3] + 11.0 * s[2]) + w1 * (-s[3] + 5.0 * s[2] + 2.0 * s[1]) +
-               (3.0 * a0) * (2.0 * s[2] + 5.0 * s[1] - s[0]);
-  const T Dh = a0 + w1 + 3.0 * a2, Dl = a2 + w1 + 3.0 * a0;
+  const T Nh = fmadd(3.0 * a2, h2, fmadd(w1, h1, a0 * h0));
+  const T Nl = fmadd(3.0 * a0, l2, fmadd(w1, l1, a2 * l0));
+  const T Dh = fmadd(T(3.0), a2, a0 + w1), Dl = fmadd(T(3.0), a0, a2 + w1);
   // both normalisations from one division where the product of the two sums is in range
   const T DD = Dh * Dl;
   if (val(DD) > 1e-290 && val(DD) < 1e290) {
     const T r = recip(6.0 * DD);
-    hi = Nh * Dl * r;
-    lo = Nl * Dh * r;
+    hi = (Nh * Dl) * r;
+    lo = (Nl * Dh) * r;
   } else {
     hi = Nh / (6.0 * Dh);
     lo = Nl / (6.0 * Dl);
   }
 }
 
-// the (13/12) (second difference)^2 part of a Jiang-Shu indicator, for the three-point sub-stencil centred at b
+template <class T>
+__host__ __device__ __forceinline__ void wenoz_from_indicators(const T s[5], T tau5, T e0, T e1, T e2, T& lo, T& hi) {
+  wenoz_combine(tau5, e0, e1, e2, weno_cand_0(s[0], s[1], s[2]), weno_cand_p(s[1], s[2], s[3]),
+                weno_cand_m(s[2], s[3], s[4]), weno_cand_0(s[4], s[3], s[2]), weno_cand_m(s[1], s[2], s[3]),
+                weno_cand_p(s[0], s[1], s[2]), lo, hi);
+}
+
+// The Jiang-Shu indicators beta_k = (13/12) ta_k^2 + (1/4) tb_k^2, in double with every operation rounded on its
+// own in the order the formula is written (no fused multiply-add).  Where the data are symmetric about the middle
+// cell (an extremum), beta_0 and beta_2 agree up to rounding and tau5 = |beta_0 - beta_2| is rounding noise,
+// which nevertheless decides the weights when beta_1 is near eps: the indicators are therefore formed exactly as
+// the plain formula rounds them, independently of how the compiler would fuse them in a given kernel.
+// wenoz_curv is the (13/12) ta^2 part for the three-point sub-stencil centred at b, shared by consecutive cells of
+// a pencil.
 template <class T>
 __host__ __device__ __forceinline__ T wenoz_curv(T a, T b, T c) {
+#ifdef __CUDA_ARCH__
+  if constexpr (std::is_same<T, double>::value) {
+    const double t = __dadd_rn(fma(-2.0, b, a), c);  // the product 2 b is exact: one rounding, as a - 2 b
+    return __dmul_rn(__dmul_rn(13.0 / 12.0, t), t);
+  }
+#endif
   const T t = a - 2.0 * b + c;
   return (13.0 / 12.0) * t * t;
 }
 
+// tau5 and e_k = beta_k + eps from the curvature parts k_k (wenoz_curv) and the stencil values.
+template <class T>
+__host__ __device__ __forceinline__ void wenoz_indicators(const T s[5], T k0, T k1, T k2, T& tau5, T& e0, T& e1,
+                                                          T& e2) {
+#ifdef __CUDA_ARCH__
+  if constexpr (std::is_same<T, double>::value) {
+    // products by 4 and 1/4 are exact, so a fused multiply-add rounds them as the plain formula does; the
+    // products by 3 are rounded on their own
+    const double s3x = __dmul_rn(3.0, s[2]);
+    const double t0b = __dadd_rn(fma(-4.0, s[1], s[0]), s3x);
+    const double t1b = __dsub_rn(s[1], s[3]);
+    const double t2b = __dadd_rn(fma(-4.0, s[3], s3x), s[4]);
+    const double b0 = fma(0.25, __dmul_rn(t0b, t0b), k0);
+    const double b1 = fma(0.25, __dmul_rn(t1b, t1b), k1);
+    const double b2 = fma(0.25, __dmul_rn(t2b, t2b), k2);
+    tau5 = fabs(__dsub_rn(b0, b2));
+    e0 = __dadd_rn(b0, 1e-40);
+    e1 = __dadd_rn(b1, 1e-40);
+    e2 = __dadd_rn(b2, 1e-40);
+    return;
+  }
+#endif
+  const T t0b = s[0] - 4.0 * s[1] + 3.0 * s[2];
+  const T t1b = s[1] - s[3];
+  const T t2b = 3.0 * s[2] - 4.0 * s[3] + s[4];
+  const T b0 = k0 + 0.25 * t0b * t0b, b1 = k1 + 0.25 * t1b * t1b, b2 = k2 + 0.25 * t2b * t2b;
+  tau5 = fabs(b0 - b2);
+  e0 = b0 + 1e-40;
+  e1 = b1 + 1e-40;
+  e2 = b2 + 1e-40;
+}
+
 template <class T>
 __host__ __device__ __forceinline__ void wenoz_both(const T s[5], T& lo, T& hi) {
-  const T t0b = s[0] - 4.0 * s[1] + 3.0 * s[2], t1b = s[1] - s[3], t2b = 3.0 * s[2] - 4.0 * s[3] + s[4];
-  const T e0 = wenoz_curv(s[0], s[1], s[2]) + 0.25 * t0b * t0b + 1e-40;
-  const T e1 = wenoz_curv(s[1], s[2], s[3]) + 0.25 * t1b * t1b + 1e-40;
-  const T e2 = wenoz_curv(s[2], s[3], s[4]) + 0.25 * t2b * t2b + 1e-40;
-  wenoz_from_indicators(s, e0, e1, e2, lo, hi);
+  T tau5, e0, e1, e2;
+  wenoz_indicators(s, wenoz_curv(s[0], s[1], s[2]), wenoz_curv(s[1], s[2], s[3]), wenoz_curv(s[2], s[3], s[4]), tau5,
+                   e0, e1, e2);
+  wenoz_from_indicators(s, tau5, e0, e1, e2, lo, hi);
 }
 
 // MP5, the monotonicity-preserving fifth-order reconstruction of Suresh & Huynh (1997): the fifth-order interface

@@ -173,6 +173,16 @@ bool autotune_on() {
   return on;
 }
 
+// With the autotuner off, ASTERX_PENCIL=16 runs the sliding-stencil kernels on the long pencils instead of the
+// default ones (the results are the same bit for bit; the tests check that).
+bool long_pencils() {
+  static const bool on = [] {
+    const char* e = std::getenv("ASTERX_PENCIL");
+    return e && std::strcmp(e, "16") == 0;
+  }();
+  return on;
+}
+
 bool stream_capturing(cudaStream_t s) {
   cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &st);
@@ -250,6 +260,8 @@ void launch(const Single& t, const StageConsts& k0, int kind, cudaStream_t s, in
   LaunchCfg c = kDefaultCfg;
   if (Tunable<Body>::value && autotune_on())
     c = choose_cfg(reinterpret_cast<const void*>(kern), n, kind_long >= 0 ? 2 : 1, s, run);
+  else if (kind_long >= 0 && long_pencils())
+    c.variant = 1;
   run(c);
 }
 
@@ -269,6 +281,8 @@ void launch(const Batch& t, const StageConsts& k0, int kind, cudaStream_t s, int
   LaunchCfg c = kDefaultCfg;
   if (Tunable<Body>::value && autotune_on())
     c = choose_cfg(reinterpret_cast<const void*>(kern), n, kind_long >= 0 ? 2 : 1, s, run);
+  else if (kind_long >= 0 && long_pencils())
+    c.variant = 1;
   run(c);
 }
 
@@ -980,13 +994,16 @@ struct ReconWENO {
       long c = c0;
       double s[5] = {a[c - 2 * st], a[c - st], a[c], a[c + st], a[c + 2 * st]};
       double k0 = wenoz_curv(s[0], s[1], s[2]), k1 = wenoz_curv(s[1], s[2], s[3]), k2 = wenoz_curv(s[2], s[3], s[4]);
+      // the lower face's mirrored candidates: formed here at the pencil's first cell, then carried over from the
+      // previous cell's upper-face candidates (the same expressions on the same values, so the same bits)
+      double l1 = weno_cand_m(s[1], s[2], s[3]), l2 = weno_cand_p(s[0], s[1], s[2]);
       for (int i = i0; i < i1; i++) {
-        const double t0b = s[0] - 4.0 * s[1] + 3.0 * s[2], t1b = s[1] - s[3], t2b = 3.0 * s[2] - 4.0 * s[3] + s[4];
-        const double e0 = k0 + 0.25 * t0b * t0b + 1e-40;
-        const double e1 = k1 + 0.25 * t1b * t1b + 1e-40;
-        const double e2 = k2 + 0.25 * t2b * t2b + 1e-40;
+        double tau5, e0, e1, e2;
+        wenoz_indicators(s, k0, k1, k2, tau5, e0, e1, e2);
+        const double h1 = weno_cand_p(s[1], s[2], s[3]), h2 = weno_cand_m(s[2], s[3], s[4]);
         double l, h;
-        wenoz_from_indicators(s, e0, e1, e2, l, h);
+        wenoz_combine(tau5, e0, e1, e2, weno_cand_0(s[0], s[1], s[2]), h1, h2, weno_cand_0(s[4], s[3], s[2]), l1, l2,
+                      l, h);
         r.w.rec[v * b.V + c] = l;
         r.w.rec[(NREC + v) * b.V + c] = h;
         if (i + 1 < i1) {
@@ -998,6 +1015,8 @@ struct ReconWENO {
           k0 = k1;
           k1 = k2;
           k2 = wenoz_curv(s[2], s[3], s[4]);
+          l1 = h2;
+          l2 = h1;
           c += st;
         }
       }
