@@ -25,7 +25,10 @@
  * Execution.  Every call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy default stream) and
  * returns after enqueueing.  Device-side counters are written to device memory and read only after the caller
  * synchronises.  Calls on different streams with different workspaces are independent; calls that share a
- * workspace must be ordered by the caller.
+ * workspace must be ordered by the caller.  The first launch of a kernel at a new item count outside stream
+ * capture times the launch shapes the library can use (threads per block, grid, pencil length) and so waits for
+ * the stream once; every shape computes the same results bit for bit.  Environment: ASTERX_AUTOTUNE=0 turns the
+ * timing off (default shapes); with it off, ASTERX_PENCIL=16 selects the long pencils.
  *
  * Errors.  Argument errors are detected on the host before any launch (ASTERX_EINVAL); launch failures return
  * ASTERX_ECUDA.  Nothing aborts, throws across the ABI or traps on the device.  Recovery failures are soft: a
