@@ -172,7 +172,9 @@ asterx_status asterx_rk4_step(const asterx_params *p, const asterx_block *blk, d
 
 /* HOST-buffer variant of asterx_rk4_step for callers without device memory management: copies U and P from
  * host (pinned for asynchrony) to the device buffers dU/dP, runs the step and copies U and P back.  The
- * device buffers have the same layout; `h_*` are HOST pointers.  Synchronous on `stream` at return. */
+ * device buffers have the same layout; `h_*` are HOST pointers.  The copy of P back to the host starts on an
+ * internal second stream as soon as the last stage's primitives are final, while that stage's right-hand side
+ * and the state update still run.  Synchronous at return (both streams). */
 asterx_status asterx_rk4_step_host(const asterx_params *p, const asterx_block *blk, double dt,
                                    double *const *h_U9, double *const *h_P5, asterx_state *dU, asterx_prims *dP,
                                    asterx_c2p_stats *stats, void *ws, size_t ws_bytes, asterx_stream stream);

@@ -307,13 +307,16 @@ asterx_status asterx_rhs(const asterx_params* p, const asterx_block* blk, const 
   return cuda_status(e);
 }
 
+// prims_ready, when given, is recorded once the stage's primitives are final (after the recovery and their ghost
+// fill; the right-hand side only reads them).
 static asterx_status stage_impl(const StageArgs& a, int stage, double dt, const F9& un, const F9& us,
                                 const F9& unext, const F9& uacc, const F5& pr, signed char* flags,
-                                unsigned long long* stats, cudaStream_t s) {
+                                unsigned long long* stats, cudaStream_t s, cudaEvent_t prims_ready = nullptr) {
   cudaError_t e = launch_ghost_state(a.b, us, s);
   if (e == cudaSuccess) e = launch_bfield(a.b, a.w, us, s);
   if (e == cudaSuccess) e = launch_c2p(a, us, pr, flags, stats, s);
   if (e == cudaSuccess) e = launch_ghost_prims(a.b, pr, s);
+  if (e == cudaSuccess && prims_ready) e = cudaEventRecord(prims_ready, s);
   if (e == cudaSuccess) e = launch_rhs(a, us, pr, stage, dt, un, unext, uacc, unext, s);
   return cuda_status(e);
 }
@@ -334,13 +337,11 @@ asterx_status asterx_rk_stage(const asterx_params* p, const asterx_block* blk, i
                     reinterpret_cast<unsigned long long*>(stats), reinterpret_cast<cudaStream_t>(stream));
 }
 
-asterx_status asterx_rk4_step(const asterx_params* p, const asterx_block* blk, double dt, asterx_state* U,
+// The four stages of one classical RK4 step; prims_ready (optional) is recorded when the last stage's primitives
+// are final.
+static asterx_status rk4_impl(const asterx_params* p, const asterx_block* blk, double dt, asterx_state* U,
                               asterx_prims* P, signed char* flags, asterx_c2p_stats* stats, void* ws,
-                              size_t ws_bytes, asterx_stream stream) {
-  asterx_status st = common_checks(p, blk, ws, ws_bytes);
-  if (st != ASTERX_OK) return st;
-  if (!finite_pos(dt) || !set_ok<asterx_state, 9>(U) || !set_ok<asterx_prims, 5>(P)) return ASTERX_EINVAL;
-  if (stats && ((uintptr_t)stats % 8) != 0) return ASTERX_EINVAL;
+                              cudaStream_t s, cudaEvent_t prims_ready) {
   StageArgs a = make_args(p, blk, ws);
   const long V = a.b.V;
   F9 un = f9(U), acc, sb[2];
@@ -349,15 +350,25 @@ asterx_status asterx_rk4_step(const asterx_params* p, const asterx_block* blk, d
     sb[0].f[v] = a.w.ustage + v * V;
     sb[1].f[v] = a.w.ustage + (9 + v) * V;
   }
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(stats);
   for (int stage = 0; stage < 4; stage++) {
     const F9& us = stage == 0 ? un : sb[(stage - 1) % 2];
     const F9& unext = stage == 3 ? un : sb[stage % 2];
-    st = stage_impl(a, stage, dt, un, us, unext, acc, f5(P), flags, cnt, s);
+    const asterx_status st =
+        stage_impl(a, stage, dt, un, us, unext, acc, f5(P), flags, cnt, s, stage == 3 ? prims_ready : nullptr);
     if (st != ASTERX_OK) return st;
   }
   return ASTERX_OK;
+}
+
+asterx_status asterx_rk4_step(const asterx_params* p, const asterx_block* blk, double dt, asterx_state* U,
+                              asterx_prims* P, signed char* flags, asterx_c2p_stats* stats, void* ws,
+                              size_t ws_bytes, asterx_stream stream) {
+  asterx_status st = common_checks(p, blk, ws, ws_bytes);
+  if (st != ASTERX_OK) return st;
+  if (!finite_pos(dt) || !set_ok<asterx_state, 9>(U) || !set_ok<asterx_prims, 5>(P)) return ASTERX_EINVAL;
+  if (stats && ((uintptr_t)stats % 8) != 0) return ASTERX_EINVAL;
+  return rk4_impl(p, blk, dt, U, P, flags, stats, ws, reinterpret_cast<cudaStream_t>(stream), nullptr);
 }
 
 // the fine block nested in the coarse one as asterx_prolong requires; L = the coarse cell of the fine corner
@@ -629,33 +640,55 @@ asterx_status asterx_rk4_step_host(const asterx_params* p, const asterx_block* b
                                    asterx_c2p_stats* stats, void* ws, size_t ws_bytes, asterx_stream stream) {
   asterx_status st = common_checks(p, blk, ws, ws_bytes);
   if (st != ASTERX_OK) return st;
-  if (!h_U9 || !h_P5 || !set_ok<asterx_state, 9>(dU) || !set_ok<asterx_prims, 5>(dP)) return ASTERX_EINVAL;
+  if (!finite_pos(dt) || !h_U9 || !h_P5 || !set_ok<asterx_state, 9>(dU) || !set_ok<asterx_prims, 5>(dP))
+    return ASTERX_EINVAL;
   for (int v = 0; v < 9; v++)
     if (!h_U9[v]) return ASTERX_EINVAL;
   for (int v = 0; v < 5; v++)
     if (!h_P5[v]) return ASTERX_EINVAL;
+  if (stats && ((uintptr_t)stats % 8) != 0) return ASTERX_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)padded_V(blk) * sizeof(double);
   F9 u = f9(dU);
   F5 pr = f5(dP);
   // one copy per run of fields that are consecutive on both sides (a stacked array is one copy)
-  auto copy_fields = [&](double* const* dst, double* const* src, int nf, cudaMemcpyKind kind) {
+  auto copy_fields = [&](double* const* dst, double* const* src, int nf, cudaMemcpyKind kind, cudaStream_t q) {
     for (int v = 0; v < nf;) {
       int e = v + 1;
       while (e < nf && dst[e] == dst[e - 1] + bytes / sizeof(double) && src[e] == src[e - 1] + bytes / sizeof(double))
         e++;
-      if (cudaMemcpyAsync(dst[v], src[v], (size_t)(e - v) * bytes, kind, s) != cudaSuccess) return false;
+      if (cudaMemcpyAsync(dst[v], src[v], (size_t)(e - v) * bytes, kind, q) != cudaSuccess) return false;
       v = e;
     }
     return true;
   };
-  if (!copy_fields(u.f, h_U9, 9, cudaMemcpyHostToDevice) || !copy_fields(pr.f, h_P5, 5, cudaMemcpyHostToDevice))
+  // The primitives are final once the last stage's recovery has run (its right-hand side only reads them), so
+  // their copy to the host runs on a second stream while that right-hand side and the state update run.
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t prims_ready = nullptr;
+  if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) return ASTERX_ECUDA;
+  if (cudaEventCreateWithFlags(&prims_ready, cudaEventDisableTiming) != cudaSuccess) {
+    cudaStreamDestroy(s2);
     return ASTERX_ECUDA;
-  st = asterx_rk4_step(p, blk, dt, dU, dP, nullptr, stats, ws, ws_bytes, stream);
-  if (st != ASTERX_OK) return st;
-  if (!copy_fields(h_U9, u.f, 9, cudaMemcpyDeviceToHost) || !copy_fields(h_P5, pr.f, 5, cudaMemcpyDeviceToHost))
-    return ASTERX_ECUDA;
-  return cuda_status(cudaStreamSynchronize(s));
+  }
+  auto finish = [&](asterx_status r) {
+    cudaStreamSynchronize(s2);
+    cudaEventDestroy(prims_ready);
+    cudaStreamDestroy(s2);
+    return r;
+  };
+  if (!copy_fields(u.f, h_U9, 9, cudaMemcpyHostToDevice, s) ||
+      !copy_fields(pr.f, h_P5, 5, cudaMemcpyHostToDevice, s))
+    return finish(ASTERX_ECUDA);
+  st = rk4_impl(p, blk, dt, dU, dP, nullptr, stats, ws, s, prims_ready);
+  if (st != ASTERX_OK) return finish(st);
+  if (cudaStreamWaitEvent(s2, prims_ready, 0) != cudaSuccess ||
+      !copy_fields(h_P5, pr.f, 5, cudaMemcpyDeviceToHost, s2) ||
+      !copy_fields(h_U9, u.f, 9, cudaMemcpyDeviceToHost, s))
+    return finish(ASTERX_ECUDA);
+  const cudaError_t e1 = cudaStreamSynchronize(s);
+  const cudaError_t e2 = cudaStreamSynchronize(s2);
+  return finish(cuda_status(e1 != cudaSuccess ? e1 : e2));
 }
 
 // ----------------------------------------------------------------------------------------------------------
