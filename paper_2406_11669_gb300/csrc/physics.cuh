@@ -548,29 +548,35 @@ __host__ __device__ __forceinline__ void wenoz_combine(T tau5, T e0, T e1, T e2,
   const T E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
   T a0 = fmadd(tau5, tau5, E0) * (E1 * E2), a1 = fmadd(tau5, tau5, E1) * (E0 * E2),
     a2 = fmadd(tau5, tau5, E2) * (E0 * E1);
-  if (!(isfinite(val(a0 + a1 + a2)) && val(a0 + a1 + a2) > 0.0)) {  // products out of range
-    const T r0 = tau5 / e0, r1 = tau5 / e1, r2 = tau5 / e2;
-    a0 = fmadd(r0, r0, T(1.0));
-    a1 = fmadd(r1, r1, T(1.0));
-    a2 = fmadd(r2, r2, T(1.0));
-  }
   // upper face: linear weights (1/10, 6/10, 3/10) on the sub-stencils ending at, centred on, starting at i, with the
   // candidates' common factor 1/6 and the weights' 1/10 taken out of numerator and denominator; lower face: the
   // mirrored stencil, whose indicator k is indicator 2-k here
-  const T w1 = 6.0 * a1;
-  const T Nh = fmadd(3.0 * a2, h2, fmadd(w1, h1, a0 * h0));
-  const T Nl = fmadd(3.0 * a0, l2, fmadd(w1, l1, a2 * l0));
-  const T Dh = fmadd(T(3.0), a2, a0 + w1), Dl = fmadd(T(3.0), a0, a2 + w1);
-  // both normalisations from one division where the product of the two sums is in range
+  T w1 = 6.0 * a1;
+  T Nh = fmadd(3.0 * a2, h2, fmadd(w1, h1, a0 * h0));
+  T Nl = fmadd(3.0 * a0, l2, fmadd(w1, l1, a2 * l0));
+  T Dh = fmadd(T(3.0), a2, a0 + w1), Dl = fmadd(T(3.0), a0, a2 + w1);
+  // both normalisations from one division where the product of the two sums is in range (which also shows that
+  // the weights are finite and not all zero)
   const T DD = Dh * Dl;
   if (val(DD) > 1e-290 && val(DD) < 1e290) {
     const T r = recip(6.0 * DD);
     hi = (Nh * Dl) * r;
     lo = (Nl * Dh) * r;
-  } else {
-    hi = Nh / (6.0 * Dh);
-    lo = Nl / (6.0 * Dl);
+    return;
   }
+  if (!(isfinite(val(a0 + a1 + a2)) && val(a0 + a1 + a2) > 0.0)) {  // products out of range: the quotient form
+    const T r0 = tau5 / e0, r1 = tau5 / e1, r2 = tau5 / e2;
+    a0 = fmadd(r0, r0, T(1.0));
+    a1 = fmadd(r1, r1, T(1.0));
+    a2 = fmadd(r2, r2, T(1.0));
+    w1 = 6.0 * a1;
+    Nh = fmadd(3.0 * a2, h2, fmadd(w1, h1, a0 * h0));
+    Nl = fmadd(3.0 * a0, l2, fmadd(w1, l1, a2 * l0));
+    Dh = fmadd(T(3.0), a2, a0 + w1);
+    Dl = fmadd(T(3.0), a0, a2 + w1);
+  }
+  hi = Nh / (6.0 * Dh);
+  lo = Nl / (6.0 * Dl);
 }
 
 template <class T>
