@@ -87,6 +87,29 @@ def test_small_workspace_and_bad_pointers_rejected():
     assert rc == A.ASTERX_EINVAL  # workspace not 256-byte aligned
 
 
+def test_host_buffer_step_rejects_bad_arguments_on_host():
+    """asterx_rk4_step_host checks dt, the host pointers, the device fields and the stats alignment before it
+    creates its second stream or copies anything."""
+    L = A.lib()
+    p = _params()
+    b = A.block_struct((8, 8, 8), 3, (0, 0, 0), (0.1,) * 3, (0, 0, 0))
+    st = A.State(*([8] * 9))
+    pr = A.Prims(*([8] * 5))
+    need = A.workspace_size(b)
+    hu = (ctypes.c_void_p * 9)(*([16] * 9))
+    hp = (ctypes.c_void_p * 5)(*([16] * 5))
+
+    def call(dt=0.01, hu=hu, hp=hp, st=st, stats=None):
+        return L.asterx_rk4_step_host(ctypes.byref(p), ctypes.byref(b), ctypes.c_double(dt), hu, hp, ctypes.byref(st),
+                                      ctypes.byref(pr), stats, ctypes.c_void_p(256), need, None)
+    for dt in (0.0, -1.0, float("nan"), float("inf")):
+        assert call(dt=dt) == A.ASTERX_EINVAL, dt
+    assert call(hu=(ctypes.c_void_p * 9)(*([16] * 8 + [0]))) == A.ASTERX_EINVAL
+    assert call(hp=(ctypes.c_void_p * 5)(*([0] + [16] * 4))) == A.ASTERX_EINVAL
+    assert call(st=A.State(*([8] * 8 + [0]))) == A.ASTERX_EINVAL
+    assert call(stats=ctypes.c_void_p(12)) == A.ASTERX_EINVAL  # not 8-byte aligned
+
+
 def test_batch_workspace_size_and_validation():
     L = A.lib()
     arr = (A.BatchBlock * 2)()
