@@ -76,10 +76,22 @@ struct SideOutT {
 };
 using SideOut = SideOutT<double>;
 
+// 2^-959 < |x| < 2^960 (about 1e-289 .. 1e289), read from the exponent bits on the integer pipe (NaN, infinities,
+// zeros and subnormals are outside): the range where the reciprocal estimates below are normal.
+__host__ __device__ __forceinline__ bool exponent_in_range(double x) {
+#ifdef __CUDA_ARCH__
+  const unsigned ex = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
+  return ex > 63u && ex < 1983u;
+#else
+  const double a = fabs(x);
+  return a >= 0x1p-959 && a < 0x1p960;
+#endif
+}
+
 // Reciprocal for Newton corrections, where a relative error far below the correction's own accuracy is enough:
 // the PTX reciprocal estimate (rcp.approx.ftz.f64) refined by one Newton-Raphson step r <- r + r (1 - d r), the
 // textbook iteration for 1/d (Flynn 1970), which squares the estimate's relative error.  Meant for
-// 1e-290 < |d| < 1e290 (the caller divides outside that range); the host build divides.
+// exponent_in_range(d) (the caller divides outside that range); the host build divides.
 __host__ __device__ __forceinline__ double newton_rcp(double d) {
 #ifdef __CUDA_ARCH__
   double r;
@@ -158,12 +170,11 @@ struct Quartic {
       const double r = cs2 * bc * bc - C2 * a2;
       const double q = A4 * a2 * a2 + r * G;
       const double dq = k4 * a2 * a + (ka * a + kb * bc) * G + r * (kg * lb);
-      const double adq = fabs(dq);
       double step;
-      if (adq > 1e-290 && adq < 1e290) {
+      if (exponent_in_range(dq)) {
         step = q * newton_rcp(dq);
       } else {
-        if (adq == 0.0) break;
+        if (dq == 0.0) break;
         step = q / dq;
       }
       lam -= step;
@@ -555,10 +566,10 @@ __host__ __device__ __forceinline__ void wenoz_combine(T tau5, T e0, T e1, T e2,
   T Nh = fmadd(3.0 * a2, h2, fmadd(w1, h1, a0 * h0));
   T Nl = fmadd(3.0 * a0, l2, fmadd(w1, l1, a2 * l0));
   T Dh = fmadd(T(3.0), a2, a0 + w1), Dl = fmadd(T(3.0), a0, a2 + w1);
-  // both normalisations from one division where the product of the two sums is in range (which also shows that
+  // both normalisations from one reciprocal where the product of the two sums is in range (which also shows that
   // the weights are finite and not all zero)
   const T DD = Dh * Dl;
-  if (val(DD) > 1e-290 && val(DD) < 1e290) {
+  if (exponent_in_range(val(DD))) {
     const T r = recip(6.0 * DD);
     hi = (Nh * Dl) * r;
     lo = (Nl * Dh) * r;
